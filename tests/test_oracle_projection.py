@@ -1,0 +1,127 @@
+"""Pins of the oracle's projection (Eq. 2-3, EWA generalisation) to closed forms and to
+numerical differentiation of the pinhole map -- nothing here re-types the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from oracle import P
+
+
+def one(mean, log_scale, quat=(1, 0, 0, 0), logit=2.0, n_sem=4):
+    return dict(mean=np.array([mean], float), log_scale=np.array([log_scale], float),
+                quat=np.array([quat], float), opacity_logit=np.array([logit], float),
+                rgb=np.array([[0.2, 0.5, 0.9]]), sem=np.arange(n_sem, dtype=float)[None] / n_sem)
+
+
+def test_isotropic_on_axis_matches_eq2():
+    """Eq. 2: r2D = f r / d for an isotropic Gaussian on the optical axis (no dilation)."""
+    cam = synthetic.make_camera(200, 100, 150.0, 150.0, 100.0, 50.0)
+    for r, d in [(0.01, 1.0), (0.05, 2.5), (0.2, 7.0)]:
+        g = one([0, 0, d], [math.log(r)] * 3, quat=(0.3, -0.5, 0.7, 0.1))
+        pr = oracle.project(g, cam, dict(dilation=0.0))[0]
+        r2d = 150.0 * r / d
+        assert pr[P["VALID"]] == 1
+        assert pr[P["S00"]] == pytest.approx(r2d ** 2, rel=1e-12)
+        assert pr[P["S11"]] == pytest.approx(r2d ** 2, rel=1e-12)
+        assert abs(pr[P["S01"]]) < 1e-12 * r2d ** 2
+        assert pr[P["U"]] == pytest.approx(100.0) and pr[P["V"]] == pytest.approx(50.0)
+        assert pr[P["DEPTH"]] == pytest.approx(d)
+
+
+def test_axis_aligned_on_axis_closed_form():
+    """Sigma2D = diag(fx^2 e^{2 s0}/z^2, fy^2 e^{2 s1}/z^2) + b I on the axis."""
+    cam = synthetic.make_camera(320, 240, 300.0, 250.0, 160.0, 120.0)
+    s = np.log([0.03, 0.01, 0.2])
+    z = 3.0
+    g = one([0, 0, z], s)
+    pr = oracle.project(g, cam, dict(dilation=0.3))[0]
+    assert pr[P["S00"]] == pytest.approx(300.0 ** 2 * math.exp(2 * s[0]) / z ** 2 + 0.3, rel=1e-12)
+    assert pr[P["S11"]] == pytest.approx(250.0 ** 2 * math.exp(2 * s[1]) / z ** 2 + 0.3, rel=1e-12)
+    det = pr[P["S00"]] * pr[P["S11"]] - pr[P["S01"]] ** 2
+    assert pr[P["CA"]] == pytest.approx(pr[P["S11"]] / det)
+    assert pr[P["CC"]] == pytest.approx(pr[P["S00"]] / det)
+
+
+def _pinhole(cam, pw):
+    t = cam["R_cw"] @ pw + cam["t_cw"]
+    return np.array([cam["fx"] * t[0] / t[2] + cam["cx"], cam["fy"] * t[1] / t[2] + cam["cy"]])
+
+
+def test_ewa_matches_numerical_jacobian_off_axis():
+    """Off-axis, rotated camera: Sigma2D = A Sigma A^T + bI with A = d(u,v)/d(world point),
+    A taken by central differences of the pinhole map (independent of the oracle's J)."""
+    rng = np.random.default_rng(3)
+    cam = synthetic.look_camera(synthetic.SCANNET_LIKE, [1.0, 2.0, 1.5], 0.4, -0.2)
+    for _ in range(20):
+        ahead = np.array([math.cos(0.4), math.sin(0.4), -0.1])
+        mu = np.array([1.0, 2.0, 1.5]) + rng.uniform(1.0, 4.0) * ahead + rng.normal(0, 0.3, 3)
+        s = rng.uniform(math.log(0.005), math.log(0.1), 3)
+        q = rng.normal(size=4)
+        g = one(mu, s, q)
+        pr = oracle.project(g, cam, dict(dilation=0.3))[0]
+        if pr[P["CLX"]] or pr[P["CLY"]]:
+            continue
+        h = 1e-6
+        A = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3); e[k] = h
+            A[:, k] = (_pinhole(cam, mu + e) - _pinhole(cam, mu - e)) / (2 * h)
+        qn = q / np.linalg.norm(q)
+        w, x, y, z = qn
+        R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                      [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+        # independent check that R is a rotation taking e_k to its columns
+        assert np.allclose(R @ R.T, np.eye(3)) and np.linalg.det(R) == pytest.approx(1.0)
+        Sig = R @ np.diag(np.exp(2 * s)) @ R.T
+        S2 = A @ Sig @ A.T + 0.3 * np.eye(2)
+        assert pr[P["S00"]] == pytest.approx(S2[0, 0], rel=1e-6)
+        assert pr[P["S11"]] == pytest.approx(S2[1, 1], rel=1e-6)
+        assert pr[P["S01"]] == pytest.approx(S2[0, 1], rel=1e-6, abs=1e-9 * abs(S2).max())
+        uv = _pinhole(cam, mu)
+        assert pr[P["U"]] == pytest.approx(uv[0]) and pr[P["V"]] == pytest.approx(uv[1])
+
+
+def test_quaternion_sign_and_scale_invariance():
+    g = synthetic.cloud_scene(50, 4, seed=9)
+    cam = synthetic.cloud_camera()
+    base = oracle.project(g, cam)
+    for f in (-1.0, 3.7, -0.2):
+        g2 = dict(g, quat=g["quat"].astype(np.float64) * f)
+        assert np.allclose(oracle.project(g2, cam), base, rtol=1e-12, atol=1e-12)
+
+
+def test_near_plane_and_tiny_opacity_cull():
+    cam = synthetic.cloud_camera()
+    assert oracle.project(one([0, 0, 0.2], [-3] * 3), cam)[0][P["VALID"]] == 0
+    assert oracle.project(one([0, 0, -1.0], [-3] * 3), cam)[0][P["VALID"]] == 0
+    assert oracle.project(one([0, 0, 0.2001], [-3] * 3), cam)[0][P["VALID"]] == 1
+    # o = sigmoid(-6) < 1/255: can never reach the skip threshold
+    assert oracle.project(one([0, 0, 2.0], [-3] * 3, logit=-6.0), cam)[0][P["VALID"]] == 0
+
+
+def test_extents_are_exact_bounds():
+    """Outside the half extents alpha < 1/255 (checked by brute force on a fine grid);
+    on the boundary's extreme point alpha equals 1/255."""
+    rng = np.random.default_rng(1)
+    cam = synthetic.cloud_camera()
+    for _ in range(10):
+        g = one(rng.uniform([-0.3, -0.3, 1.5], [0.3, 0.3, 3]), rng.uniform(-4, -2.5, 3),
+                rng.normal(size=4), logit=rng.normal(1, 1))
+        pr = oracle.project(g, cam)[0]
+        if not pr[P["VALID"]]:
+            continue
+        a, b, c, o = pr[P["CA"]], pr[P["CB"]], pr[P["CC"]], pr[P["OPAC"]]
+        ex, ey = pr[P["EXTX"]], pr[P["EXTY"]]
+        dy = np.linspace(-3 * ey, 3 * ey, 4001)
+        # on the vertical line dx = ex the largest alpha is attained at dy* = -b ex / c
+        for sgn in (1, -1):
+            dx = sgn * ex * (1 + 1e-6)
+            sig = 0.5 * (a * dx * dx + c * dy * dy) + b * dx * dy
+            assert (o * np.exp(-sig)).max() < 1 / 255
+            dstar = -b * (sgn * ex) / c
+            sig_star = 0.5 * (a * ex * ex + c * dstar ** 2) + b * (sgn * ex) * dstar
+            assert o * math.exp(-sig_star) == pytest.approx(1 / 255, rel=1e-6)
