@@ -1,0 +1,452 @@
+#!/usr/bin/env python
+"""Benchmark of the pyramid-splatting mapping iteration on one GB300 (or N replicas).
+
+Workload (Replica-like, three-level pyramid): one 1200x680 RGB-D-semantic keyframe with
+its 600x340 and 300x170 pyramid levels, 300k Gaussians sampled on the surfaces of a
+seeded 6x5x3 m room with 20 boxes, C = 16 semantic features decoded to 32 classes.  One
+step = one full mapping iteration over every pyramid level: EWA projection, tile lists,
+compositing, loss (L1 + D-SSIM RGB, masked depth L1, cross-entropy), adjoint to every
+Gaussian parameter, Adam -- replayed as one CUDA graph.  L2 is flushed (a 256 MiB write)
+before every timed step; the flush is outside each step's event pair.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead (the
+reference arm: a bounded pixel sample of the same workload per step, extrapolated).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd pyramid-splat iters/s"
+UNIT = "iters/s"
+WORKLOAD = dict(workload="replica-like room, 1 keyframe x 3 pyramid levels (1200x680, 600x340, 300x170)",
+                gaussians=300_000, sem_features=16, classes=32, tile="16x16", levels=3)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--gaussians", type=int, default=300_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-baseline sample time")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# workload
+# ------------------------------------------------------------------------------------------
+
+def build_inputs(n_gauss, seed_offset=0):
+    import synthetic
+    room = synthetic.Room(n_classes=32, seed=3)
+    cams = room.trajectory(8, synthetic.REPLICA_LIKE, seed=7)
+    cam = cams[(1 + seed_offset) % len(cams)]
+    g = room.sample_gaussians(n_gauss, 16, seed=4 + seed_offset, sem_mode="random")
+    g["sem"] *= 0.5
+    frame = room.raycast(cam)
+    rng = np.random.default_rng(11)
+    decoder = rng.normal(size=(32, 16)).astype(np.float32) * 0.3
+    return room, cam, g, frame, decoder
+
+
+# ------------------------------------------------------------------------------------------
+# algorithmic traffic / flops model (per step)
+# ------------------------------------------------------------------------------------------
+
+def step_stats(r):
+    """Counts measured from the last forward: visible records, instances, pixels, list
+    entries examined up to the last contributor and contributors."""
+    import torch
+    torch.cuda.synchronize()
+    rect = r.rect.view(-1, 2)
+    n_vis = int((rect[:, 0] != rect[:, 1]).sum().item())
+    K = r.instance_count()
+    last = r.last.to(torch.int64)
+    E = int(last.sum().item())
+    contrib = int(r.n_contrib.to(torch.int64).sum().item())
+    return dict(N=r.N, V=r.V, n_vis=n_vis, K=K, P=r.P, E=E, contrib=contrib, C=r.C)
+
+
+def algorithmic_bytes(s):
+    """HBM bytes one iteration must move (float32), by kernel:
+    projection fwd 44 N V + 32 R + 8 R (params read per view-level, records + rects written),
+    tile lists: compaction 8 R + 8 n_vis, depth sort 24 n_vis, emission 16 n_vis + 8 K,
+    tile sort 24 K, ranges 8 K, raster fwd K_r (4 + 24 + 12 + 4C) + P (4 (4 + C) + 12),
+    loss P (8 (4 + C) + 24), raster bwd P (4 (4 + C) + 12) + K_r (44 + 4 C) + 2 n_vis 32 +
+    atomics, projection bwd n_vis (32 + 32) + N 44 + N 4 (10 + C) grads, Adam N (14 + C) 16."""
+    N, V, nv, K, P, C = s["N"], s["V"], s["n_vis"], s["K"], s["P"], s["C"]
+    R = N * V
+    Kr = K  # instances read (upper bound: tiles stop early)
+    b = {}
+    b["project_fwd"] = 44 * N + (32 + 8) * R
+    b["tile_lists"] = 8 * R + 8 * nv + 24 * nv + 16 * nv + 8 * K + 24 * K + 8 * K
+    b["raster_fwd"] = Kr * (4 + 24 + 12 + 4 * C) + P * (4 * (4 + C) + 12)
+    b["loss"] = P * (8 * (4 + C) + 24)
+    b["raster_bwd"] = P * (4 * (4 + C) + 12) + Kr * (44 + 4 * C) + 2 * nv * 32
+    b["project_bwd"] = nv * 64 + N * 44 + N * 4 * (10 + C)
+    b["adam"] = N * (14 + C) * 16
+    return b
+
+
+def raster_flops(s):
+    """Algorithmic FP32 flops: alpha evaluation ~13 per examined (pixel, entry) pair and
+    3 + 2 (4 + C) per contributor in the forward; the backward re-evaluates alpha (13),
+    and per contributor spends 2 (4 + C) on g.f, (4 + C) on feature gradients, ~25 on the
+    geometric gradients and 2 (10 + C) - 2 on the warp reduction."""
+    E, c, C = s["E"], s["contrib"], s["C"]
+    nf = 4 + C
+    fwd = 13 * E + (3 + 2 * nf) * c
+    bwd = 13 * E + (2 * nf + nf + 25) * c
+    return fwd, bwd
+
+
+# ------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--id={self.index}",
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU baseline (the oracle, as it stands)
+# ------------------------------------------------------------------------------------------
+
+def oracle_sample_time(g, cam, levels, stride, seed=0):
+    """Oracle forward + backward over every stride-th row and column of every level.
+    Returns (seconds, sampled pixels, total pixels)."""
+    import oracle
+    g64 = {k: np.asarray(v, np.float64) for k, v in g.items() if k != "label"}
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    n_s, n_t = 0, 0
+    for oc in oracle.level_cameras(cam, levels):
+        ys, xs = np.meshgrid(np.arange(0, oc["H"], stride), np.arange(0, oc["W"], stride), indexing="ij")
+        pix = np.stack([xs.ravel(), ys.ravel()], 1)
+        f = oracle.render(g64, oc, pixels=pix)
+        C = g64["sem"].shape[1]
+        oracle.render_backward(g64, oc, rng.normal(size=(3, len(pix))), rng.normal(size=len(pix)),
+                               rng.normal(size=(C, len(pix))), pixels=pix)
+        n_s += len(pix)
+        n_t += oc["W"] * oc["H"]
+    return time.perf_counter() - t0, n_s, n_t
+
+
+def cpu_baseline(g, cam, target_s):
+    import oracle
+    oracle.build()
+    # pick a stride whose sample costs about target_s: probe with a coarse stride
+    t, ns, nt = oracle_sample_time(g, cam, 3, 64)
+    per_px = t / max(1, ns)
+    want = max(1, int(target_s / per_px))
+    stride = max(1, int(np.sqrt(nt / want)))
+    t, ns, nt = oracle_sample_time(g, cam, 3, stride)
+    full = t * nt / ns
+    return {"value": 1.0 / full, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle forward+backward on every {stride}th row/column of all 3 levels "
+                      f"({ns} of {nt} pixels, {t:.1f} s), extrapolated linearly to the full iteration",
+            "seconds_per_iter": full}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, each step one bounded sample."""
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    oracle.build()
+    room, cam, g, frame, dec = build_inputs(args.gaussians)
+    probe_t, ns, nt = oracle_sample_time(g, cam, 3, 96)
+    per_px = probe_t / max(1, ns)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    stride = max(8, int(np.sqrt(nt * per_px / max(0.5, budget))))
+    for _ in range(args.warmup):
+        oracle_sample_time(g, cam, 3, stride)
+    times = []
+    for k in range(args.steps):
+        t, ns, nt = oracle_sample_time(g, cam, 3, stride, seed=k)
+        times.append(t * nt / ns)
+    per = float(np.mean(times))
+    value = 1.0 / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, l2="n/a (CPU)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"every {stride}th row/column of all 3 levels per step ({ns} of {nt} px), "
+                                       f"extrapolated linearly"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2412_01217_gb300 import (LossConfig, MappingStep, PyramidRasterizer, RenderConfig,
+                                        build_pyramid, load_library, to_device_params)
+    lib = load_library()
+    tw, th = (int(x) for x in args.tile.split("x"))
+    room, cam, g, frame, dec = build_inputs(args.gaussians, seed_offset=rank)
+    cfg = RenderConfig(tile_w=tw, tile_h=th, batch=args.batch)
+    r = PyramidRasterizer(args.gaussians, 16, [cam], levels=3, cfg=cfg,
+                          loss_cfg=LossConfig(n_classes=32), device=dev)
+    p = to_device_params(g, dev)
+    gt = build_pyramid(r, [frame["rgb"]], [frame["depth"]], [frame["label"]])
+    decoder = torch.tensor(dec, device=dev)
+    ms = MappingStep(r, p, gt, decoder=decoder)
+    ms.step()
+    torch.cuda.synchronize()
+    r.check_status()
+    stats = step_stats(r)
+
+    # ---- capture the iteration with timing events around the two raster calls ------------
+    ev = {k: torch.cuda.Event(enable_timing=True, external=True) for k in
+          ("s0", "fwd0", "fwd1", "bwd0", "bwd1", "s1")}
+    n0 = lib.sg_kernel_launch_count()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        ms.step()
+    torch.cuda.current_stream().wait_stream(side)
+    from paper_2412_01217_gb300.splat import PARAM_KEYS, _ptr, _stream
+    from paper_2412_01217_gb300._lib import call
+
+    def body(t):
+        for gk in ms.grads.values():
+            gk.zero_()
+        ms.decoder_grad.zero_()
+        ev["s0"].record()
+        r.project(p)
+        r.build_lists()
+        ev["fwd0"].record()
+        r.rasterize(p)
+        ev["fwd1"].record()
+        r.loss(gt, decoder=decoder, decoder_grad=ms.decoder_grad)
+        ev["bwd0"].record()
+        r.backward(p, ms.grads)
+        ev["bwd1"].record()
+        for k in PARAM_KEYS:
+            call("sg_adam_step", _ptr(p[k]), _ptr(ms.grads[k]), _ptr(ms.m[k]), _ptr(ms.v[k]), p[k].numel(),
+                 ms.lr[k], 0.9, 0.999, 1e-15, t, _stream())
+        ev["s1"].record()
+
+    with torch.cuda.graph(graph):
+        body(2)
+    launches_per_step = lib.sg_kernel_launch_count() - n0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        graph.replay()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    step_ms, fwd_ms, bwd_ms = [], [], []
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record()
+        graph.replay()
+        ends[i].record()
+        ends[i].synchronize()
+        fwd_ms.append(ev["fwd0"].elapsed_time(ev["fwd1"]))
+        bwd_ms.append(ev["bwd0"].elapsed_time(ev["bwd1"]))
+    torch.cuda.synchronize()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    clk = clocks.stop()
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = args.steps * world / total_s
+    ms_per = total_s * 1e3 / args.steps
+
+    # ---- end to end through the public API with host buffers ----------------------------
+    e2e = None
+    if not args.no_e2e:
+        host = {k: p[k].detach().cpu().pin_memory() for k in PARAM_KEYS}
+        v0 = r.view_slice(gt["rgb"], 0, 3)
+        h_rgb = torch.as_tensor(frame["rgb"]).pin_memory()
+        h_depth = torch.as_tensor(frame["depth"]).pin_memory()
+        h_label = torch.as_tensor(frame["label"]).pin_memory()
+        h_terms = torch.empty(r.terms.numel(), dtype=torch.float32).pin_memory()
+        from paper_2412_01217_gb300._lib import call as _call
+        import ctypes as C
+
+        def e2e_step():
+            for k in PARAM_KEYS:
+                p[k].copy_(host[k], non_blocking=True)
+            v0.copy_(h_rgb, non_blocking=True)
+            r.view_slice(gt["depth"], 0, 1)[0].copy_(h_depth, non_blocking=True)
+            r.view_slice(gt["label"], 0, 1)[0].copy_(h_label, non_blocking=True)
+            _call("sg_build_pyramid", _ptr(gt["rgb"]), _ptr(gt["depth"]), _ptr(gt["label"]), C.c_void_p(0), 0,
+                  r.views_host, r.V, _stream())
+            graph.replay()
+            h_terms.copy_(r.terms, non_blocking=True)
+            for k in PARAM_KEYS:
+                host[k].copy_(p[k], non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        es.record()
+        for _ in range(args.steps):
+            e2e_step()
+        ee.record()
+        torch.cuda.synchronize()
+        e2e_s = es.elapsed_time(ee) / 1e3
+        h2d = sum(host[k].numel() * 4 for k in PARAM_KEYS) + h_rgb.numel() * 4 + h_depth.numel() * 4 + h_label.numel() * 4
+        d2h = h_terms.numel() * 4 + sum(host[k].numel() * 4 for k in PARAM_KEYS)
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": args.steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # ---- roofline of the dominant kernel ---------------------------------------------------
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    f_fwd, f_bwd = raster_flops(stats)
+    fwd_avg = float(np.mean(fwd_ms)) / 1e3
+    bwd_avg = float(np.mean(bwd_ms)) / 1e3
+    bytes_model = algorithmic_bytes(stats)
+    step_bytes = sum(bytes_model.values())
+    dominant = "raster_bwd" if bwd_avg >= fwd_avg else "raster_fwd"
+    d_flops = f_bwd if dominant == "raster_bwd" else f_fwd
+    d_time = bwd_avg if dominant == "raster_bwd" else fwd_avg
+    achieved = d_flops / d_time / 1e12
+    roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                "launch_ms": d_time * 1e3}
+    evals = 2 * stats["E"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(WORKLOAD, tile=args.tile, batch=args.batch, gaussians=args.gaussians,
+                       l2="flushed (256 MiB write) before every timed step", parallelism="replicas"),
+        "gpu_launches": int(launches_per_step * args.steps),
+        "launches_per_step": int(launches_per_step),
+        "gaussian_pixel_evals_per_s": evals * value / world * world if world else evals * value,
+        "hbm": {"algorithmic_bytes_per_step": int(step_bytes), "achieved_GBps": step_bytes / (ms_per / 1e3) / 1e9,
+                "peak_GBps": hbm_peak, "frac": step_bytes / (ms_per / 1e3) / 1e9 / hbm_peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"},
+        "phases_ms": {"raster_fwd": fwd_avg * 1e3, "loss+lists+proj": None,
+                      "raster_bwd+proj_bwd": bwd_avg * 1e3},
+        "counts": stats,
+        "roofline": roofline,
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, cam, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

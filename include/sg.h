@@ -1,0 +1,267 @@
+/*
+ * sg.h -- C ABI of the GB300 (sm_103a) multi-level-pyramid Gaussian splatting library.
+ *
+ * The library implements the data-parallel hot path of RGBDS-SLAM's mapping step
+ * (Sec. III-B..D): project 3D Gaussians into every (view, pyramid level), build per-tile
+ * depth-sorted instance lists, composite RGB / depth / semantic images front to back,
+ * evaluate the tightly coupled reconstruction loss per level, and run the hand-written
+ * adjoint back to every Gaussian parameter.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All pointers in the structs below are DEVICE pointers owned by the caller.  The
+ *    library never allocates or frees device memory; scratch space is passed in as a
+ *    workspace sized by the matching *_workspace_size() call.
+ *  - float tensors are FP32, contiguous, row-major; arrays read with 16-byte vector loads
+ *    (quat, sem, geo, images of a view) must be 16-byte aligned (checked).
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream)
+ *    and capturable into a CUDA graph: no call synchronises or copies to the host.
+ *  - Host-checkable problems return an error code before anything is launched.  Problems
+ *    found on the device (instance capacity exceeded, non-finite values) set bits of the
+ *    caller's device status word (SG_STATUS_*), which the caller reads after the stream
+ *    work completes; the kernels themselves always exit normally.
+ *  - sg_last_error() returns a thread-local message for the last failing call.
+ *
+ * Images are planar and packed per view-level: view-level v (see sg_view) with W x H
+ * pixels starting at pixel offset p0 stores channel c of an image with K channels at
+ * base + K*p0 + c*W*H + y*W + x.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sg_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    SG_OK = 0,
+    SG_ERR_INVALID_ARG = 1, /* null/misaligned pointer, bad size, unsupported C, ...     */
+    SG_ERR_CAPACITY = 2,    /* a caller buffer or workspace is too small                */
+    SG_ERR_TIMEOUT = 3,     /* a bounded device wait gave up                            */
+    SG_ERR_NUMERIC = 4,     /* non-finite values detected                               */
+    SG_ERR_CUDA = 5         /* a CUDA launch or runtime call failed                     */
+} sg_status;
+
+/* Bits of the caller's device status word (uint32). */
+#define SG_STATUS_CAPACITY 1u /* more tile instances than sg_tile_lists.capacity  */
+#define SG_STATUS_NUMERIC 2u  /* non-finite value met                              */
+
+#define SG_MAX_VIEWS 64
+
+/* Pinhole camera of pyramid level 0 (Eq. 2: K and T_cw).  Pixel (x, y) is evaluated at
+ * the point (x, y): pixel centres sit at integer coordinates. */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t W, H;
+    float R_cw[9]; /* world -> camera rotation, row-major */
+    float t_cw[3]; /* world -> camera translation         */
+} sg_camera;
+
+/* One (view, pyramid level) render target.  Built on the host by sg_make_views and copied
+ * by the caller into a device array (the `views` argument of the calls below). */
+typedef struct {
+    float fx, fy, cx, cy; /* intrinsics of this level (Eq. 4-6 pyramid, see sg_make_views) */
+    float R[9], t[3];     /* world -> camera                                             */
+    int32_t W, H;         /* level image size                                            */
+    int32_t tiles_x, tiles_y;
+    int32_t tile_offset;  /* first global tile id of this view-level                     */
+    int32_t pixel_offset; /* first pixel of this view-level in packed image buffers      */
+    int32_t level;        /* pyramid level (0 = full resolution)                         */
+    int32_t camera;       /* index of the source camera                                  */
+} sg_view;
+
+/* Gaussian parameters (Sec. III-B: position, shape, colour, semantic feature, opacity);
+ * shape is anisotropic: log-scale (3) + unit quaternion (w, x, y, z). */
+typedef struct {
+    const float *mean;          /* N x 3                                  */
+    const float *log_scale;     /* N x 3                                  */
+    const float *quat;          /* N x 4 (w, x, y, z), 16-byte aligned    */
+    const float *opacity_logit; /* N; opacity = sigmoid(logit)            */
+    const float *rgb;           /* N x 3                                  */
+    const float *sem;           /* N x C semantic feature, 16-byte aligned */
+    int32_t N, C;               /* C % 4 == 0, C in {4, 8, 16, 32, 40}    */
+} sg_gaussians;
+
+/* Gradients with respect to every Gaussian parameter; same layouts as sg_gaussians.
+ * The backward call ADDS into these (the caller zeroes them). */
+typedef struct {
+    float *mean, *log_scale, *quat, *opacity_logit, *rgb, *sem;
+    int32_t N, C;
+} sg_gaussian_grads;
+
+/* Rendering constants (3D Gaussian splatting conventions, Sec. III-C) and launch shape. */
+typedef struct {
+    float alpha_max; /* 0.99:   alpha = min(alpha_max, o * exp(-sigma))              */
+    float alpha_min; /* 1/255:  a Gaussian with alpha < alpha_min is skipped           */
+    float T_min;     /* 1e-4:   stop before a Gaussian that would make T < T_min       */
+    float z_near;    /* 0.2:    Gaussians with camera z <= z_near are culled           */
+    float dilation;  /* 0.3:    added to the 2D covariance diagonal (pixels^2)         */
+    float fov_clamp; /* 1.3:    Jacobian evaluated at t_x/t_z clamped to fov_clamp*W/2fx */
+    float bg[3];     /* background RGB (depth and semantic background are 0)          */
+    int32_t tile_w, tile_h; /* screen tile: 8x8, 16x16 or 32x8                        */
+    int32_t batch;          /* Gaussians staged per shared-memory batch: 32..256      */
+    int32_t persistent;     /* 1: persistent grid with an atomic work queue           */
+} sg_config;
+
+/* Projected records of all (view-level, Gaussian) pairs: record r = v*N + g. */
+typedef struct {
+    float *geo;     /* R x 8: u, v, depth, opacity, m00, m10, m11, 0 (16-B aligned), where
+                       1/2 d^T Sigma2D^{-1} d = (m00 dx)^2 + (m10 dx + m11 dy)^2            */
+    uint32_t *rect; /* R x 2: tile rectangle [tx0,tx1) x [ty0,ty1) as (tx0|ty0<<16, tx1|ty1<<16);
+                       an empty rectangle means the record is culled                    */
+} sg_projected;
+
+/* Per-tile depth-sorted instance lists (the set N of Eq. 7-9, restricted to a tile). */
+typedef struct {
+    int32_t capacity; /* K_cap: instances the arrays below can hold                      */
+    uint32_t *tile;   /* K_cap: global tile id of each instance, ascending               */
+    uint32_t *record; /* K_cap: record id v*N+g; within a tile by (depth, record id)     */
+    int32_t *ranges;  /* n_tiles x 2: [start, end) of each tile's instances              */
+    int32_t *count;   /* device scalar: K = instances emitted (may exceed capacity)      */
+} sg_tile_lists;
+
+/* Rendered images (all view-levels packed, planar). */
+typedef struct {
+    float *rgb;   /* 3 planes per view-level */
+    float *depth; /* 1 plane                 */
+    float *sem;   /* C planes                */
+} sg_images;
+
+/* Per-pixel state saved by the forward pass for the backward pass (no per-Gaussian
+ * intermediates are stored). */
+typedef struct {
+    float *T_final;     /* transmittance after the last contributor                      */
+    int32_t *last;      /* list entries examined up to and including the last contributor */
+    int32_t *n_contrib; /* number of contributing Gaussians                              */
+} sg_saved;
+
+/* Ground-truth pyramid of every view-level, same packing as sg_images. */
+typedef struct {
+    const float *rgb;     /* 3 planes                                  */
+    const float *depth;   /* 1 plane; <= 0 marks missing depth          */
+    const int32_t *label; /* 1 plane; < 0 = ignore (sem_mode 0)         */
+    const float *sem;     /* C planes of semantic colour (sem_mode 1)    */
+} sg_targets;
+
+/* Eq. 10-13 weights and the semantic term. */
+typedef struct {
+    float lambda_r;        /* 0.2: weight of D-SSIM in the RGB term (Eq. 10)             */
+    float lambda_s;        /* 0.2: weight of D-SSIM in the semantic term (Eq. 12)        */
+    float w_depth, w_sem;  /* 1, 1: weights of the depth and semantic terms (Eq. 13)     */
+    int32_t sem_mode;      /* 0: cross-entropy of softmax(decoder * S) vs label;
+                              1: (1-lambda_s) L1 + lambda_s (1 - SSIM) vs semantic colour */
+    int32_t n_classes;     /* K (sem_mode 0)                                              */
+    const float *decoder;  /* K x C linear decoder, or NULL for identity (K == C)         */
+    float *decoder_grad;   /* K x C gradient (added), or NULL                             */
+} sg_loss_config;
+
+/* ---------------------------------------------------------------------------------- */
+/* Host helpers                                                                         */
+/* ---------------------------------------------------------------------------------- */
+
+const char *sg_last_error(void);
+const char *sg_version(void);
+/* Number of kernels this library has launched (or recorded into a graph) since it was
+ * loaded; a diagnostic used by the benchmark to report its launch count. */
+uint64_t sg_kernel_launch_count(void);
+void sg_default_config(sg_config *cfg);
+void sg_default_loss_config(sg_loss_config *cfg);
+
+/* Eq. 4-6 / Sec. IV-A (3 levels): expand n_cams level-0 cameras into n_cams*levels
+ * view-levels (camera-major, level-minor).  Level l+1 halves the size (floor) and maps
+ * pixel centres consistently: f' = f/2, c' = (c - 0.5)/2.  Writes out[n_cams*levels];
+ * returns total pixels and tiles.  SG_ERR_INVALID_ARG when a level would be empty or
+ * n_cams*levels > SG_MAX_VIEWS. */
+sg_status sg_make_views(const sg_camera *cams, int32_t n_cams, int32_t levels, int32_t tile_w,
+                        int32_t tile_h, sg_view *out, int64_t *total_pixels,
+                        int32_t *total_tiles);
+
+/* ---------------------------------------------------------------------------------- */
+/* Forward path                                                                         */
+/* ---------------------------------------------------------------------------------- */
+
+/* Eq. 2-3 generalised by the EWA covariance projection: for every view-level and every
+ * Gaussian writes the 2D mean, depth, opacity, conic and the tile rectangle covering every
+ * pixel where alpha can reach alpha_min.  views: device array of n_views sg_view. */
+sg_status sg_project_gaussians(const sg_gaussians *g, const sg_view *views, int32_t n_views,
+                               const sg_config *cfg, sg_projected *out, sg_stream_t stream);
+
+/* Scratch bytes sg_build_tile_lists needs for n_records = n_views*N records and the
+ * lists' capacity. */
+size_t sg_tile_lists_workspace_size(int64_t n_records, int32_t capacity);
+
+/* Sec. III-C "sorted 2D gaussian primitives": instances (tile, record) of every non-culled
+ * record, ordered by global tile id, then float32 depth bits, then record id (a stable,
+ * deterministic radix sort), plus each tile's [start, end).  n_tiles: total tiles of the
+ * views (sg_make_views).  If more than capacity instances arise, the surplus is dropped,
+ * *count holds the required number and SG_STATUS_CAPACITY is set in *status. */
+sg_status sg_build_tile_lists(const sg_projected *proj, int32_t N, int32_t n_views,
+                              const sg_view *views, int32_t n_tiles, const sg_config *cfg,
+                              sg_tile_lists *lists, void *workspace, size_t workspace_bytes,
+                              uint32_t *status, sg_stream_t stream);
+
+/* Eq. 7-9 for every view-level in one launch: per tile, front-to-back compositing of RGB,
+ * depth and C semantic channels.  work_counter: device int32 scratch (zeroed by the call)
+ * for the persistent work queue. */
+sg_status sg_render_pyramid(const sg_gaussians *g, const sg_projected *proj,
+                            const sg_tile_lists *lists, const sg_view *views, int32_t n_views,
+                            int32_t n_tiles, const sg_config *cfg, sg_images *out,
+                            sg_saved *saved, int32_t *work_counter, sg_stream_t stream);
+
+/* Scratch bytes sg_pyramid_loss needs for the view-levels in views_host (host table). */
+size_t sg_loss_workspace_size(const sg_view *views_host, int32_t n_views);
+
+/* Eq. 10-13 at every view-level: writes terms[4*v + {0,1,2,3}] = L_r, L_d, L_s, total of
+ * view-level v (device floats) and the gradient of sum_v total_v with respect to the
+ * rendered images into dL (same packing as sg_images).  views_host: host copy of the
+ * view table (sizes are needed to size the launch).  SSIM uses an 11x11 Gaussian window
+ * (sigma 1.5) with zero padding. */
+sg_status sg_pyramid_loss(const sg_images *rendered, const sg_targets *gt, const sg_view *views,
+                          const sg_view *views_host, int32_t n_views, int32_t C,
+                          const sg_loss_config *lcfg, float *terms, sg_images *dL,
+                          void *workspace, size_t workspace_bytes, sg_stream_t stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* Backward path                                                                        */
+/* ---------------------------------------------------------------------------------- */
+
+/* Scratch bytes sg_render_pyramid_backward needs. */
+size_t sg_backward_workspace_size(int64_t n_records);
+
+/* Adjoint of sg_render_pyramid followed by the adjoint of sg_project_gaussians (Sec. III-D
+ * backpropagation): back-to-front per tile from each pixel's saved `last`, warp-level
+ * reductions before the atomics, then the chain rule through the EWA projection.  ADDS
+ * dL/d{mean, log_scale, quat, opacity_logit, rgb, sem} into grads. */
+sg_status sg_render_pyramid_backward(const sg_gaussians *g, const sg_projected *proj,
+                                     const sg_tile_lists *lists, const sg_view *views,
+                                     int32_t n_views, int32_t n_tiles, const sg_config *cfg,
+                                     const sg_saved *saved, const sg_images *dL,
+                                     sg_gaussian_grads *grads, void *workspace,
+                                     size_t workspace_bytes, int32_t *work_counter,
+                                     sg_stream_t stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* Support: pyramid construction and the optimizer                                      */
+/* ---------------------------------------------------------------------------------- */
+
+/* Eq. 4-6 "PyramidImageExtraction": fills levels 1..L-1 of every camera in `tgt` (packed
+ * like the views) from level 0: 2x2 box mean for RGB, mean of the valid (> 0) depths,
+ * majority label of the valid (>= 0) labels with ties to the lowest id.  n_sem_ch planes of
+ * semantic colour (may be 0) are box-averaged like RGB. */
+sg_status sg_build_pyramid(float *rgb, float *depth, int32_t *label, float *sem, int32_t n_sem_ch,
+                           const sg_view *views_host, int32_t n_views, sg_stream_t stream);
+
+/* Adam (the paper leaves the optimizer unspecified): for i < n
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr * mhat / (sqrt(vhat) + eps). */
+sg_status sg_adam_step(float *param, const float *grad, float *m, float *v, int64_t n, float lr,
+                       float beta1, float beta2, float eps, int32_t step, sg_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SG_H */

@@ -1,0 +1,586 @@
+// loss.cu -- Eq. 10-13 per pyramid level, the Eq. 4-6 image pyramid, and Adam.
+//
+// RGB term (Eq. 10) and, in semantic-colour mode, the semantic term (Eq. 12):
+//   (1 - lambda) mean|I - I_gt| + lambda (1 - SSIM(I, I_gt)),
+// SSIM with an 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2, zero padding.
+// One CTA owns a 32x16 output tile of one view-level and one group of planes.  It stages
+// the planes with a 10-pixel halo, forms the five window moments (separable, horizontal
+// then vertical) on the tile plus a 5-pixel halo, turns them into the three per-pixel
+// partials of SSIM (w.r.t. the window mean, E[x^2] and E[xy]), and convolves those once
+// more to get dL/dI for the tile -- one read of I and I_gt and one write of dL/dI per
+// pixel, no intermediate maps in HBM.
+// Depth term (Eq. 11): mean |D - D_gt| over pixels with D_gt > 0.
+// Semantic term, cross-entropy mode: mean CE(softmax(decoder * S), label) over label >= 0.
+// Sums are per-CTA partials reduced in a fixed order (deterministic).
+#include <cstdio>
+
+#include "sg_common.cuh"
+
+namespace sg {
+
+constexpr int kLTW = 32, kLTH = 16;           // loss tile
+constexpr int kXW = kLTW + 20, kXH = kLTH + 20;  // staged planes (10-px halo)
+constexpr int kMW = kLTW + 10, kMH = kLTH + 10;  // moment / partial maps (5-px halo)
+constexpr int kLossThreads = 256;
+
+struct LossViews {
+    int n;
+    int tile_off[SG_MAX_VIEWS + 1];  // loss tiles (32x16) per view, prefix
+    int pix_blk_off[SG_MAX_VIEWS + 1];  // 256-pixel blocks per view, prefix
+};
+
+__device__ __forceinline__ void gauss_window(float *w) {
+    float s = 0.f;
+    for (int i = 0; i < 11; ++i) {
+        w[i] = expf(-(float)((i - 5) * (i - 5)) / (2.f * 1.5f * 1.5f));
+        s += w[i];
+    }
+    for (int i = 0; i < 11; ++i) w[i] /= s;
+}
+
+__device__ __forceinline__ int find_prefix(const int *off, int n, int x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float block_sum(float v, float *s_red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(SG_FULL_MASK, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kLossThreads / 32; ++w) t += s_red[w];
+    return t;  // valid in thread 0
+}
+
+struct SsimArgs {
+    const float *x, *y;  // planar images (rendered, target), nch planes per view
+    float *grad;         // dL/dx
+    int nch;
+    float l1_coef_num;   // (1 - lambda) * weight  (divided by n = nch*W*H per view)
+    float ssim_coef_num; // lambda * weight
+    const sg_view *views;
+    LossViews lv;
+    float *partials;     // per CTA: (sum |x - y|, sum ssim)
+};
+
+__global__ void __launch_bounds__(kLossThreads) ssim_l1_kernel(SsimArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    float *X = sm;                   // kXH x kXW
+    float *Y = X + kXH * kXW;        // kXH x kXW
+    float *Hm = Y + kXH * kXW;       // 5 x kXH x kMW (later: 3 x kMH x kLTW)
+    float *Mp = Hm + 5 * kXH * kMW;  // 3 x kMH x kMW
+    __shared__ float w[11];
+    __shared__ float s_red[kLossThreads / 32];
+    if (threadIdx.x == 0) gauss_window(w);
+    const int item = blockIdx.x;
+    const int v = find_prefix(a.lv.tile_off, a.lv.n, item);
+    const sg_view &vw = a.views[v];
+    const int W = vw.W, H = vw.H;
+    const int tiles_x = (W + kLTW - 1) / kLTW;
+    const int local = item - a.lv.tile_off[v];
+    const int bx = local % tiles_x, by = local / tiles_x;
+    const int ox = bx * kLTW - 10, oy = by * kLTH - 10;
+    const size_t HW = (size_t)W * H;
+    const float n = (float)a.nch * (float)HW;
+    const float l1c = a.l1_coef_num / n, sc = -a.ssim_coef_num / n;
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    float l1_sum = 0.f, ssim_sum = 0.f;
+    __syncthreads();
+    for (int ch = 0; ch < a.nch; ++ch) {
+        const float *xs = a.x + (size_t)a.nch * vw.pixel_offset + ch * HW;
+        const float *ys = a.y + (size_t)a.nch * vw.pixel_offset + ch * HW;
+        for (int i = threadIdx.x; i < kXH * kXW; i += kLossThreads) {
+            const int r = i / kXW, c = i % kXW;
+            const int gy = oy + r, gx = ox + c;
+            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            X[i] = in ? xs[(size_t)gy * W + gx] : 0.f;
+            Y[i] = in ? ys[(size_t)gy * W + gx] : 0.f;
+        }
+        __syncthreads();
+        // horizontal window sums of x, y, x^2, y^2, xy
+        for (int i = threadIdx.x; i < kXH * kMW; i += kLossThreads) {
+            const int r = i / kMW, c = i % kMW;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 11; ++j) {
+                const float xv = X[r * kXW + c + j], yv = Y[r * kXW + c + j], wj = w[j];
+                s0 = fmaf(wj, xv, s0);
+                s1 = fmaf(wj, yv, s1);
+                s2 = fmaf(wj, xv * xv, s2);
+                s3 = fmaf(wj, yv * yv, s3);
+                s4 = fmaf(wj, xv * yv, s4);
+            }
+            Hm[0 * kXH * kMW + i] = s0;
+            Hm[1 * kXH * kMW + i] = s1;
+            Hm[2 * kXH * kMW + i] = s2;
+            Hm[3 * kXH * kMW + i] = s3;
+            Hm[4 * kXH * kMW + i] = s4;
+        }
+        __syncthreads();
+        // vertical window sums -> SSIM and its partials (zero outside the image)
+        for (int i = threadIdx.x; i < kMH * kMW; i += kLossThreads) {
+            const int r = i / kMW, c = i % kMW;
+            const int gy = by * kLTH - 5 + r, gx = bx * kLTW - 5 + c;
+            float P = 0.f, Q = 0.f, R = 0.f;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < 5; ++k)
+#pragma unroll
+                    for (int j = 0; j < 11; ++j) m[k] = fmaf(w[j], Hm[k * kXH * kMW + (r + j) * kMW + c], m[k]);
+                const float mx = m[0], my = m[1];
+                const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
+                const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
+                const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
+                const float s = (A1 * A2) / (B1 * B2);
+                if (r >= 5 && r < kLTH + 5 && c >= 5 && c < kLTW + 5) ssim_sum += s;
+                const float d_mx = 2.f * my * A2 / (B1 * B2) - s * 2.f * mx / B1;
+                const float d_sxx = -s / B2;
+                const float d_sxy = 2.f * A1 / (B1 * B2);
+                P = sc * (d_mx - 2.f * mx * d_sxx - my * d_sxy);
+                Q = sc * d_sxx;
+                R = sc * d_sxy;
+            }
+            Mp[0 * kMH * kMW + i] = P;
+            Mp[1 * kMH * kMW + i] = Q;
+            Mp[2 * kMH * kMW + i] = R;
+        }
+        __syncthreads();
+        float *Hp = Hm;  // 3 x kMH x kLTW, reuses the moment buffer
+        for (int i = threadIdx.x; i < kMH * kLTW; i += kLossThreads) {
+            const int r = i / kLTW, c = i % kLTW;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float s = 0.f;
+#pragma unroll
+                for (int j = 0; j < 11; ++j) s = fmaf(w[j], Mp[k * kMH * kMW + r * kMW + c + j], s);
+                Hp[k * kMH * kLTW + i] = s;
+            }
+        }
+        __syncthreads();
+        float *gs = a.grad + (size_t)a.nch * vw.pixel_offset + ch * HW;
+        for (int i = threadIdx.x; i < kLTH * kLTW; i += kLossThreads) {
+            const int r = i / kLTW, c = i % kLTW;
+            const int gy = by * kLTH + r, gx = bx * kLTW + c;
+            if (gx >= W || gy >= H) continue;
+            float cv[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float s = 0.f;
+#pragma unroll
+                for (int j = 0; j < 11; ++j) s = fmaf(w[j], Hp[k * kMH * kLTW + (r + j) * kLTW + c], s);
+                cv[k] = s;
+            }
+            const float xv = X[(r + 10) * kXW + c + 10], yv = Y[(r + 10) * kXW + c + 10];
+            const float d = xv - yv;
+            l1_sum += fabsf(d);
+            const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+            gs[(size_t)gy * W + gx] = l1c * sg + cv[0] + 2.f * xv * cv[1] + yv * cv[2];
+        }
+        __syncthreads();
+    }
+    const float t1 = block_sum(l1_sum, s_red);
+    const float t2 = block_sum(ssim_sum, s_red);
+    if (threadIdx.x == 0) {
+        a.partials[2 * item] = t1;
+        a.partials[2 * item + 1] = t2;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// valid-pixel counts, depth L1, cross-entropy
+// ---------------------------------------------------------------------------------------
+
+__global__ void loss_count_kernel(const float *gt_depth, const int *label, const sg_view *views,
+                                  LossViews lv, int *counts) {
+    const int blk = blockIdx.x;
+    const int v = find_prefix(lv.pix_blk_off, lv.n, blk);
+    const sg_view &vw = views[v];
+    const int p = (blk - lv.pix_blk_off[v]) * kLossThreads + threadIdx.x;
+    const int HW = vw.W * vw.H;
+    int cd = 0, cl = 0;
+    if (p < HW) {
+        cd = gt_depth[(size_t)vw.pixel_offset + p] > 0.f;
+        cl = label ? label[(size_t)vw.pixel_offset + p] >= 0 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        cd += __shfl_xor_sync(SG_FULL_MASK, cd, o);
+        cl += __shfl_xor_sync(SG_FULL_MASK, cl, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cd) atomicAdd(counts + 2 * v, cd);
+        if (cl) atomicAdd(counts + 2 * v + 1, cl);
+    }
+}
+
+struct PixelArgs {
+    const float *depth, *gt_depth, *sem;
+    const int *label;
+    float *g_depth, *g_sem;
+    const float *decoder;   // K x C or null
+    float *decoder_grad;    // K x C or null
+    int C, K, ce;           // ce: cross-entropy mode
+    float w_depth, w_sem;
+    const int *counts;
+    const sg_view *views;
+    LossViews lv;
+    float *partials;        // per CTA: (sum |D - D_gt| over valid, sum CE over valid)
+};
+
+template <int C, int K>
+__global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
+    __shared__ float s_dec[K * C];
+    __shared__ float s_red[kLossThreads / 32];
+    // only used when the decoder gradient is requested (dynamic: 256 * (K + C) floats)
+    extern __shared__ __align__(16) float s_dyn[];
+    float *s_dz = s_dyn;
+    float *s_S = s_dyn + kLossThreads * K;
+    const bool has_dec = a.decoder != nullptr;
+    for (int i = threadIdx.x; i < K * C; i += kLossThreads) s_dec[i] = has_dec ? a.decoder[i] : (i / C == i % C ? 1.f : 0.f);
+    const int blk = blockIdx.x;
+    const int v = find_prefix(a.lv.pix_blk_off, a.lv.n, blk);
+    const sg_view &vw = a.views[v];
+    const int HW = vw.W * vw.H;
+    const int p = (blk - a.lv.pix_blk_off[v]) * kLossThreads + threadIdx.x;
+    const bool in = p < HW;
+    const size_t p0 = (size_t)vw.pixel_offset;
+    const int nd = a.counts[2 * v], nl = a.counts[2 * v + 1];
+    __syncthreads();
+    float l1d = 0.f, ce = 0.f;
+    if (in) {
+        const float gd = a.gt_depth[p0 + p];
+        float gdep = 0.f;
+        if (gd > 0.f) {
+            const float d = a.depth[p0 + p] - gd;
+            l1d = fabsf(d);
+            gdep = a.w_depth * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) / (float)nd;
+        }
+        a.g_depth[p0 + p] = gdep;
+    }
+    if (a.ce) {
+        float S[C], z[K];
+        const int lab = in ? a.label[p0 + p] : -1;
+#pragma unroll
+        for (int c = 0; c < C; ++c) S[c] = in ? a.sem[(size_t)C * p0 + (size_t)c * HW + p] : 0.f;
+        float zmax = -INFINITY;
+        if (has_dec) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                float s = 0.f;
+#pragma unroll
+                for (int c = 0; c < C; ++c) s = fmaf(s_dec[k * C + c], S[c], s);
+                z[k] = s;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) z[k] = S[k < C ? k : 0];
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) zmax = fmaxf(zmax, z[k]);
+        float se = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) se += expf(z[k] - zmax);
+        const float lse = zmax + logf(se);
+        float dS[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) dS[c] = 0.f;
+        const bool valid = in && lab >= 0;
+        const float sc = valid ? a.w_sem / (float)nl : 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float pk = expf(z[k] - lse);
+            const float dz = sc * (pk - (k == lab ? 1.f : 0.f));
+            if (valid && k == lab) ce = lse - z[k];
+            if (has_dec) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) dS[c] = fmaf(s_dec[k * C + c], dz, dS[c]);
+            } else if (k < C) {
+                dS[k] = dz;
+            }
+            if (a.decoder_grad) s_dz[threadIdx.x * K + k] = dz;
+        }
+        if (in)
+#pragma unroll
+            for (int c = 0; c < C; ++c) a.g_sem[(size_t)C * p0 + (size_t)c * HW + p] = dS[c];
+        if (a.decoder_grad) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) s_S[threadIdx.x * C + c] = S[c];
+            __syncthreads();
+            for (int o = threadIdx.x; o < K * C; o += kLossThreads) {
+                const int k = o / C, c = o % C;
+                float s = 0.f;
+                for (int t = 0; t < kLossThreads; ++t) s = fmaf(s_dz[t * K + k], s_S[t * C + c], s);
+                if (s != 0.f) atomicAdd(a.decoder_grad + o, s);
+            }
+        }
+    }
+    const float t1 = block_sum(l1d, s_red);
+    const float t2 = block_sum(ce, s_red);
+    if (threadIdx.x == 0) {
+        a.partials[2 * blk] = t1;
+        a.partials[2 * blk + 1] = t2;
+    }
+}
+
+struct FinalArgs {
+    const float *ssim_rgb, *ssim_sem, *pix;  // partial arrays
+    const int *counts;
+    const sg_view *views;
+    LossViews lv;
+    int C, sem_mode;
+    float lambda_r, lambda_s, w_depth, w_sem;
+    float *terms;
+};
+
+__global__ void loss_finalize_kernel(FinalArgs a) {
+    const int v = blockIdx.x;
+    const sg_view &vw = a.views[v];
+    const double HW = (double)vw.W * vw.H;
+    __shared__ double s_red[4][kLossThreads];
+    double acc[4] = {0, 0, 0, 0};
+    for (int i = a.lv.tile_off[v] + threadIdx.x; i < a.lv.tile_off[v + 1]; i += kLossThreads) {
+        acc[0] += a.ssim_rgb[2 * i];
+        acc[1] += a.ssim_rgb[2 * i + 1];
+        if (a.ssim_sem) {
+            acc[2] += a.ssim_sem[2 * i];
+            acc[3] += a.ssim_sem[2 * i + 1];
+        }
+    }
+    for (int k = 0; k < 4; ++k) s_red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = kLossThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 4; ++k) s_red[k][threadIdx.x] += s_red[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    double r[4];
+    for (int k = 0; k < 4; ++k) r[k] = s_red[k][0];
+    __syncthreads();
+    double b[2] = {0, 0};
+    for (int i = a.lv.pix_blk_off[v] + threadIdx.x; i < a.lv.pix_blk_off[v + 1]; i += kLossThreads) {
+        b[0] += a.pix[2 * i];
+        b[1] += a.pix[2 * i + 1];
+    }
+    for (int k = 0; k < 2; ++k) s_red[k][threadIdx.x] = b[k];
+    __syncthreads();
+    for (int s = kLossThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 2; ++k) s_red[k][threadIdx.x] += s_red[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double l1d = s_red[0][0], ce = s_red[1][0];
+        const int nd = a.counts[2 * v], nl = a.counts[2 * v + 1];
+        const double n_rgb = 3.0 * HW;
+        const double L_r = (1.0 - a.lambda_r) * r[0] / n_rgb + a.lambda_r * (1.0 - r[1] / n_rgb);
+        const double L_d = nd > 0 ? a.w_depth * l1d / nd : 0.0;
+        double L_s;
+        if (a.sem_mode == 0) {
+            L_s = nl > 0 ? a.w_sem * ce / nl : 0.0;
+        } else {
+            const double n_s = (double)a.C * HW;
+            L_s = a.w_sem * ((1.0 - a.lambda_s) * r[2] / n_s + a.lambda_s * (1.0 - r[3] / n_s));
+        }
+        a.terms[4 * v + 0] = (float)L_r;
+        a.terms[4 * v + 1] = (float)L_d;
+        a.terms[4 * v + 2] = (float)L_s;
+        a.terms[4 * v + 3] = (float)(L_r + L_d + L_s);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+
+static size_t ssim_smem() { return sizeof(float) * (2 * kXH * kXW + 5 * kXH * kMW + 3 * kMH * kMW); }
+
+static void make_loss_views(const sg_view *vh, int n_views, LossViews &lv) {
+    lv.n = n_views;
+    lv.tile_off[0] = 0;
+    lv.pix_blk_off[0] = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const int tx = (vh[v].W + kLTW - 1) / kLTW, ty = (vh[v].H + kLTH - 1) / kLTH;
+        lv.tile_off[v + 1] = lv.tile_off[v] + tx * ty;
+        lv.pix_blk_off[v + 1] = lv.pix_blk_off[v] + (vh[v].W * vh[v].H + kLossThreads - 1) / kLossThreads;
+    }
+}
+
+static size_t loss_ws_bytes(int n_views, int n_tiles, int n_blocks) {
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    return al(sizeof(int) * 2 * n_views) + 2 * al(sizeof(float) * 2 * n_tiles) +
+           al(sizeof(float) * 2 * n_blocks);
+}
+
+size_t loss_workspace_size(const sg_view *vh, int n_views) {
+    LossViews lv;
+    make_loss_views(vh, n_views, lv);
+    return loss_ws_bytes(n_views, lv.tile_off[n_views], lv.pix_blk_off[n_views]);
+}
+
+template <int C, int K>
+static void launch_pixel_t(PixelArgs &pa, int blocks, cudaStream_t st) {
+    const size_t dyn = pa.decoder_grad ? sizeof(float) * kLossThreads * (K + C) : 0;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(loss_pixel_kernel<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float) * kLossThreads * (K + C)));
+        attr = true;
+    }
+    loss_pixel_kernel<C, K><<<blocks, kLossThreads, dyn, st>>>(pa);
+}
+
+static bool launch_pixel(PixelArgs &pa, int blocks, cudaStream_t st) {
+    const int C = pa.C, K = pa.K;
+#define SG_PIX(c, k) if (C == c && K == k) { launch_pixel_t<c, k>(pa, blocks, st); return true; }
+    SG_PIX(4, 4) SG_PIX(8, 8) SG_PIX(16, 16) SG_PIX(16, 32) SG_PIX(32, 32) SG_PIX(40, 40)
+#undef SG_PIX
+    return false;
+}
+
+sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *views,
+                      const sg_view *vh, int n_views, int C, const sg_loss_config *lc,
+                      float *terms, sg_images *dL, void *ws, size_t ws_bytes, cudaStream_t st) {
+    LossViews lv;
+    make_loss_views(vh, n_views, lv);
+    const int n_tiles = lv.tile_off[n_views], n_blocks = lv.pix_blk_off[n_views];
+    char *base = (char *)ws;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char *p = base + off; off += (bytes + 255) & ~(size_t)255; return p; };
+    int *counts = (int *)take(sizeof(int) * 2 * n_views);
+    float *p_rgb = (float *)take(sizeof(float) * 2 * n_tiles);
+    float *p_sem = (float *)take(sizeof(float) * 2 * n_tiles);
+    float *p_pix = (float *)take(sizeof(float) * 2 * n_blocks);
+    if (loss_ws_bytes(n_views, n_tiles, n_blocks) > ws_bytes) {
+        set_error("pyramid_loss: workspace %zu bytes < %zu needed", ws_bytes,
+                  loss_ws_bytes(n_views, n_tiles, n_blocks));
+        return SG_ERR_CAPACITY;
+    }
+    const int ce = lc->sem_mode == 0;
+    const int K = ce ? lc->n_classes : C;
+    cudaMemsetAsync(counts, 0, sizeof(int) * 2 * n_views, st);
+    loss_count_kernel<<<n_blocks, kLossThreads, 0, st>>>(gt->depth, ce ? gt->label : nullptr, views, lv, counts);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(ssim_l1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssim_smem());
+        attr = true;
+    }
+    SsimArgs sa{r->rgb, gt->rgb, dL->rgb, 3, 1.f - lc->lambda_r, lc->lambda_r, views, lv, p_rgb};
+    ssim_l1_kernel<<<n_tiles, kLossThreads, ssim_smem(), st>>>(sa);
+    if (!ce) {
+        SsimArgs ss{r->sem, gt->sem, dL->sem, C, lc->w_sem * (1.f - lc->lambda_s), lc->w_sem * lc->lambda_s,
+                    views, lv, p_sem};
+        ssim_l1_kernel<<<n_tiles, kLossThreads, ssim_smem(), st>>>(ss);
+    }
+    PixelArgs pa{r->depth, gt->depth, r->sem, gt->label, dL->depth, dL->sem, lc->decoder,
+                 lc->decoder_grad, C, K, ce, lc->w_depth, lc->w_sem, counts, views, lv, p_pix};
+    if (!launch_pixel(pa, n_blocks, st)) {
+        set_error("pyramid_loss: unsupported (C=%d, classes=%d)", C, K);
+        return SG_ERR_INVALID_ARG;
+    }
+    FinalArgs fa{p_rgb, ce ? nullptr : p_sem, p_pix, counts, views, lv, C, lc->sem_mode,
+                 lc->lambda_r, lc->lambda_s, lc->w_depth, lc->w_sem, terms};
+    loss_finalize_kernel<<<n_views, kLossThreads, 0, st>>>(fa);
+    count_launches(ce ? 4 : 5);
+    return check_launch("pyramid_loss");
+}
+
+// ---------------------------------------------------------------------------------------
+// Eq. 4-6 pyramid: level l+1 from level l of the same camera
+// ---------------------------------------------------------------------------------------
+
+__global__ void pyramid_down_kernel(float *rgb, float *depth, int *label, float *sem, int n_sem,
+                                    sg_view src, sg_view dst) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= dst.W || y >= dst.H) return;
+    const size_t sHW = (size_t)src.W * src.H, dHW = (size_t)dst.W * dst.H;
+    const size_t s00 = (size_t)(2 * y) * src.W + 2 * x;
+    const size_t idx[4] = {s00, s00 + 1, s00 + src.W, s00 + src.W + 1};
+    const size_t o = (size_t)y * dst.W + x;
+    for (int c = 0; c < 3; ++c) {
+        const float *s = rgb + 3 * (size_t)src.pixel_offset + c * sHW;
+        rgb[3 * (size_t)dst.pixel_offset + c * dHW + o] = 0.25f * ((s[idx[0]] + s[idx[1]]) + (s[idx[2]] + s[idx[3]]));
+    }
+    for (int c = 0; c < n_sem; ++c) {
+        const float *s = sem + (size_t)n_sem * src.pixel_offset + c * sHW;
+        sem[(size_t)n_sem * dst.pixel_offset + c * dHW + o] = 0.25f * ((s[idx[0]] + s[idx[1]]) + (s[idx[2]] + s[idx[3]]));
+    }
+    float ds = 0.f;
+    int dn = 0;
+    for (int k = 0; k < 4; ++k) {
+        const float d = depth[src.pixel_offset + idx[k]];
+        if (d > 0.f) { ds += d; ++dn; }
+    }
+    depth[dst.pixel_offset + o] = dn ? ds / (float)dn : 0.f;
+    if (label) {
+        int l[4];
+        for (int k = 0; k < 4; ++k) l[k] = label[src.pixel_offset + idx[k]];
+        int best = -1, bc = 0;
+        for (int k = 0; k < 4; ++k) {
+            if (l[k] < 0) continue;
+            int c = 0;
+            for (int j = 0; j < 4; ++j) c += l[j] == l[k];
+            if (c > bc || (c == bc && l[k] < best)) { best = l[k]; bc = c; }
+        }
+        label[dst.pixel_offset + o] = best;
+    }
+}
+
+sg_status launch_pyramid(float *rgb, float *depth, int *label, float *sem, int n_sem,
+                         const sg_view *vh, int n_views, cudaStream_t st) {
+    int max_level = 0;
+    for (int v = 0; v < n_views; ++v) max_level = vh[v].level > max_level ? vh[v].level : max_level;
+    for (int l = 1; l <= max_level; ++l)
+        for (int v = 0; v < n_views; ++v) {
+            if (vh[v].level != l) continue;
+            int s = -1;
+            for (int u = 0; u < n_views; ++u)
+                if (vh[u].camera == vh[v].camera && vh[u].level == l - 1) s = u;
+            if (s < 0) {
+                set_error("build_pyramid: view %d (camera %d, level %d) has no parent level", v, vh[v].camera, l);
+                return SG_ERR_INVALID_ARG;
+            }
+            const dim3 blk(32, 8), grd((vh[v].W + 31) / 32, (vh[v].H + 7) / 8);
+            pyramid_down_kernel<<<grd, blk, 0, st>>>(rgb, depth, label, sem, n_sem, vh[s], vh[v]);
+            count_launches(1);
+        }
+    return check_launch("build_pyramid");
+}
+
+// ---------------------------------------------------------------------------------------
+// Adam
+// ---------------------------------------------------------------------------------------
+
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                            float bc1, float bc2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+sg_status launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1,
+                      float b2, float eps, int step, cudaStream_t st) {
+    const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 8 * (int64_t)sms) blocks = 8 * (int64_t)sms;
+    if (blocks > 0) {
+        adam_kernel<<<(int)blocks, 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
+        count_launches(1);
+    }
+    return check_launch("adam");
+}
+
+}  // namespace sg

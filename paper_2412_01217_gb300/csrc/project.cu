@@ -1,0 +1,327 @@
+// project.cu -- EWA projection of 3D Gaussians into every (view, pyramid level) and its
+// adjoint (Eq. 2-3 generalised to anisotropic Gaussians; Sec. III-D backpropagation).
+//
+// One thread per Gaussian loops over the view-levels: the Gaussian's parameters (44 B) are
+// read once and its 3D covariance is formed once, then one 32-byte record and one 8-byte
+// tile rectangle are written per view-level.  The view table sits in shared memory.
+#include "sg_common.cuh"
+
+namespace sg {
+
+struct ProjConsts {
+    float z_near, dilation, fov_clamp, alpha_min;
+    int tile_w, tile_h;
+};
+
+// Rotation (row-major) of the unit quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+struct GaussianFrame {
+    float q[4];    // normalised quaternion
+    float qn;      // |q| before normalisation
+    float R[9];    // rotation
+    float S[3];    // exp(log_scale)
+    float Sig[6];  // 3D covariance: xx xy xz yy yz zz
+};
+
+__device__ __forceinline__ void gaussian_frame(const float *log_scale, float4 q4, int g,
+                                               GaussianFrame &f) {
+    f.qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float r = 1.f / f.qn;
+    f.q[0] = q4.x * r; f.q[1] = q4.y * r; f.q[2] = q4.z * r; f.q[3] = q4.w * r;
+    quat_rot(f.q[0], f.q[1], f.q[2], f.q[3], f.R);
+    f.S[0] = expf(log_scale[3 * g + 0]);
+    f.S[1] = expf(log_scale[3 * g + 1]);
+    f.S[2] = expf(log_scale[3 * g + 2]);
+    float M[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = f.R[3 * i + j] * f.S[j];
+    f.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    f.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    f.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    f.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    f.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    f.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+}
+
+__device__ __forceinline__ float sym3(const float *S, int i, int j) {
+    // index into xx xy xz yy yz zz
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    const int idx = a == 0 ? b : (a == 1 ? 2 + b : 5);
+    return S[idx];
+}
+
+// Camera-space mean, Jacobian rows of T = J W and the clamp flags of one view-level.
+struct ViewGeom {
+    float t[3];
+    float T0[3], T1[3];
+    float J00, J02, J11, J12;
+    bool clx, cly;
+};
+
+__device__ __forceinline__ void view_geom(const sg_view &vw, const float mu[3], float fov_clamp,
+                                          ViewGeom &q) {
+    for (int i = 0; i < 3; ++i)
+        q.t[i] = vw.R[3 * i] * mu[0] + vw.R[3 * i + 1] * mu[1] + vw.R[3 * i + 2] * mu[2] + vw.t[i];
+    const float tz = q.t[2];
+    const float limx = fov_clamp * 0.5f * (float)vw.W / vw.fx;
+    const float limy = fov_clamp * 0.5f * (float)vw.H / vw.fy;
+    float rx = q.t[0] / tz, ry = q.t[1] / tz;
+    q.clx = rx > limx || rx < -limx;
+    q.cly = ry > limy || ry < -limy;
+    rx = fminf(limx, fmaxf(-limx, rx));
+    ry = fminf(limy, fmaxf(-limy, ry));
+    q.J00 = vw.fx / tz;
+    q.J11 = vw.fy / tz;
+    q.J02 = -vw.fx * rx / tz;  // = -fx * x~ / tz^2 with x~ = rx * tz
+    q.J12 = -vw.fy * ry / tz;
+    for (int j = 0; j < 3; ++j) {
+        q.T0[j] = q.J00 * vw.R[j] + q.J02 * vw.R[6 + j];
+        q.T1[j] = q.J11 * vw.R[3 + j] + q.J12 * vw.R[6 + j];
+    }
+}
+
+__device__ __forceinline__ float quad3(const float *a, const float *S, const float *b) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) s += a[i] * sym3(S, i, j) * b[j];
+    return s;
+}
+
+// Sigma2D = A A^T + dil I with A = T M (M = R diag(S)); det by Cauchy-Binet,
+// det(A A^T) = |a0 x a1|^2, so it is a sum of non-negative terms.
+__device__ __forceinline__ void cov2d(const ViewGeom &q, const GaussianFrame &f, float dil,
+                                      float &s00, float &s01, float &s11, float &det) {
+    float a0[3], a1[3];
+    for (int j = 0; j < 3; ++j) {
+        a0[j] = (q.T0[0] * f.R[j] + q.T0[1] * f.R[3 + j] + q.T0[2] * f.R[6 + j]) * f.S[j];
+        a1[j] = (q.T1[0] * f.R[j] + q.T1[1] * f.R[3 + j] + q.T1[2] * f.R[6 + j]) * f.S[j];
+    }
+    const float n0 = a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2];
+    const float n1 = a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2];
+    s00 = n0 + dil;
+    s11 = n1 + dil;
+    s01 = a0[0] * a1[0] + a0[1] * a1[1] + a0[2] * a1[2];
+    const float c0 = diff_of_products(a0[1], a1[2], a0[2], a1[1]);
+    const float c1 = diff_of_products(a0[2], a1[0], a0[0], a1[2]);
+    const float c2 = diff_of_products(a0[0], a1[1], a0[1], a1[0]);
+    det = (c0 * c0 + c1 * c1 + c2 * c2) + dil * (n0 + n1) + dil * dil;
+}
+
+__global__ void __launch_bounds__(256) project_fwd_kernel(
+    const float *__restrict__ mean, const float *__restrict__ log_scale,
+    const float4 *__restrict__ quat, const float *__restrict__ ologit, int N,
+    const sg_view *__restrict__ views, int n_views, ProjConsts pc, float4 *__restrict__ geo,
+    uint2 *__restrict__ rect) {
+    __shared__ sg_view s_views[SG_MAX_VIEWS];
+    for (int i = threadIdx.x; i < n_views; i += blockDim.x) s_views[i] = views[i];
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N) return;
+    const float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
+    GaussianFrame f;
+    gaussian_frame(log_scale, quat[g], g, f);
+    const float o = 1.f / (1.f + expf(-ologit[g]));
+    for (int v = 0; v < n_views; ++v) {
+        const sg_view &vw = s_views[v];
+        const size_t r = (size_t)v * N + g;
+        ViewGeom q;
+        view_geom(vw, mu, pc.fov_clamp, q);
+        float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+        uint2 rc = make_uint2(0u, 0u);
+        const float tz = q.t[2];
+        if (tz > pc.z_near && o >= pc.alpha_min) {
+            const float u = vw.fx * q.t[0] / tz + vw.cx;
+            const float vv = vw.fy * q.t[1] / tz + vw.cy;
+            float s00, s01, s11, det;
+            cov2d(q, f, pc.dilation, s00, s01, s11, det);
+            if (det > 0.f && s00 > 0.f) {
+                // alpha >= alpha_min needs sigma <= ln(o/alpha_min); the smallest sigma at a
+                // horizontal offset dx is dx^2/(2 s00): half extents (with float32 slack)
+                const float thr = logf(o / pc.alpha_min);
+                const float ex = sqrtf(2.f * thr * s00) * 1.002f + 0.01f;
+                const float ey = sqrtf(2.f * thr * s11) * 1.002f + 0.01f;
+                const float xmin = fmaxf(ceilf(u - ex), 0.f);
+                const float xmax = fminf(floorf(u + ex), (float)(vw.W - 1));
+                const float ymin = fmaxf(ceilf(vv - ey), 0.f);
+                const float ymax = fminf(floorf(vv + ey), (float)(vw.H - 1));
+                if (xmin <= xmax && ymin <= ymax) {
+                    const int tx0 = (int)xmin / pc.tile_w, tx1 = (int)xmax / pc.tile_w + 1;
+                    const int ty0 = (int)ymin / pc.tile_h, ty1 = (int)ymax / pc.tile_h + 1;
+                    rc = make_uint2(pack16(tx0, ty0), pack16(tx1, ty1));
+                    g0 = make_float4(u, vv, tz, o);
+                    // conditional form of 1/2 d^T Sigma2D^{-1} d (see eval_alpha)
+                    const float m00 = rsqrtf(2.f * s00);
+                    const float m11 = sqrtf(s00 / (2.f * det));
+                    const float m10 = -s01 / sqrtf(2.f * s00 * det);
+                    g1 = make_float4(m00, m10, m11, 0.f);
+                }
+            }
+        }
+        geo[2 * r] = g0;
+        geo[2 * r + 1] = g1;
+        rect[r] = rc;
+    }
+}
+
+// Adjoint.  g2d: per record (u, v, conic a, conic b, conic c, opacity, depth, 0).
+__global__ void __launch_bounds__(256) project_bwd_kernel(
+    const float *__restrict__ mean, const float *__restrict__ log_scale,
+    const float4 *__restrict__ quat, const float *__restrict__ ologit, int N,
+    const sg_view *__restrict__ views, int n_views, ProjConsts pc,
+    const uint2 *__restrict__ rect, const float4 *__restrict__ g2d, float *__restrict__ g_mean, float *__restrict__ g_ls,
+    float *__restrict__ g_quat, float *__restrict__ g_ologit) {
+    __shared__ sg_view s_views[SG_MAX_VIEWS];
+    for (int i = threadIdx.x; i < n_views; i += blockDim.x) s_views[i] = views[i];
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N) return;
+    const float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
+    GaussianFrame f;
+    gaussian_frame(log_scale, quat[g], g, f);
+    const float o = 1.f / (1.f + expf(-ologit[g]));
+    float gmu[3] = {0.f, 0.f, 0.f};
+    float gSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // full-entry gradient, symmetric
+    float go_total = 0.f;
+    for (int v = 0; v < n_views; ++v) {
+        const size_t r = (size_t)v * N + g;
+        const uint2 rc = rect[r];
+        if (rc.x == rc.y) continue;  // culled (empty rectangle)
+        const float4 a = g2d[2 * r], b = g2d[2 * r + 1];
+        const float gu = a.x, gv = a.y, ga = a.z, gb = a.w, gc = b.x, go = b.y, gd = b.z;
+        const sg_view &vw = s_views[v];
+        ViewGeom q;
+        view_geom(vw, mu, pc.fov_clamp, q);
+        // conic = Sigma2D^{-1} of this view-level, recomputed in float32
+        float ca, cb, cc;
+        {
+            float s00, s01, s11, det;
+            cov2d(q, f, pc.dilation, s00, s01, s11, det);
+            const float id = 1.f / det;
+            ca = s11 * id;
+            cb = -s01 * id;
+            cc = s00 * id;
+        }
+        const float tz = q.t[2], tz2 = tz * tz;
+        // conic = Sigma2D^{-1}: dQ = -Q dS Q
+        const float gS00 = -(ca * ca * ga + ca * cb * gb + cb * cb * gc);
+        const float gS01 = -(2.f * ca * cb * ga + (ca * cc + cb * cb) * gb + 2.f * cb * cc * gc);
+        const float gS11 = -(cb * cb * ga + cb * cc * gb + cc * cc * gc);
+        const float G00 = gS00, G01 = 0.5f * gS01, G11 = gS11;
+        // Sigma2D = T Sig T^T: dSig += T^T G T; dT = 2 G T Sig
+        const float *T0 = q.T0, *T1 = q.T1;
+        {
+            int k = 0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = i; j < 3; ++j, ++k)
+                    gSig[k] += T0[i] * G00 * T0[j] + T0[i] * G01 * T1[j] + T1[i] * G01 * T0[j] +
+                               T1[i] * G11 * T1[j];
+        }
+        float TS0[3], TS1[3];  // T Sig
+        for (int j = 0; j < 3; ++j) {
+            TS0[j] = T0[0] * sym3(f.Sig, 0, j) + T0[1] * sym3(f.Sig, 1, j) + T0[2] * sym3(f.Sig, 2, j);
+            TS1[j] = T1[0] * sym3(f.Sig, 0, j) + T1[1] * sym3(f.Sig, 1, j) + T1[2] * sym3(f.Sig, 2, j);
+        }
+        float gT0[3], gT1[3];
+        for (int j = 0; j < 3; ++j) {
+            gT0[j] = 2.f * (G00 * TS0[j] + G01 * TS1[j]);
+            gT1[j] = 2.f * (G01 * TS0[j] + G11 * TS1[j]);
+        }
+        // T0 = J00 W0 + J02 W2, T1 = J11 W1 + J12 W2 (W rows)
+        const float *W = vw.R;
+        const float gJ00 = gT0[0] * W[0] + gT0[1] * W[1] + gT0[2] * W[2];
+        const float gJ02 = gT0[0] * W[6] + gT0[1] * W[7] + gT0[2] * W[8];
+        const float gJ11 = gT1[0] * W[3] + gT1[1] * W[4] + gT1[2] * W[5];
+        const float gJ12 = gT1[0] * W[6] + gT1[1] * W[7] + gT1[2] * W[8];
+        float gt0 = 0.f, gt1 = 0.f, gt2 = 0.f;
+        gt2 += -gJ00 * q.J00 / tz - gJ11 * q.J11 / tz;
+        if (!q.clx) {
+            gt0 += gJ02 * (-vw.fx / tz2);
+            gt2 += gJ02 * (2.f * vw.fx * q.t[0] / (tz2 * tz));
+        } else {
+            gt2 += gJ02 * (-q.J02 / tz);
+        }
+        if (!q.cly) {
+            gt1 += gJ12 * (-vw.fy / tz2);
+            gt2 += gJ12 * (2.f * vw.fy * q.t[1] / (tz2 * tz));
+        } else {
+            gt2 += gJ12 * (-q.J12 / tz);
+        }
+        gt0 += gu * vw.fx / tz;
+        gt1 += gv * vw.fy / tz;
+        gt2 += -gu * vw.fx * q.t[0] / tz2 - gv * vw.fy * q.t[1] / tz2 + gd;
+        for (int j = 0; j < 3; ++j) gmu[j] += W[j] * gt0 + W[3 + j] * gt1 + W[6 + j] * gt2;
+        go_total += go;
+    }
+    // Sig = M M^T with M = R diag(S): dM = 2 gSig M
+    float M[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = f.R[3 * i + j] * f.S[j];
+    float gR[9], gls[3] = {0.f, 0.f, 0.f};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const float gM = 2.f * (sym3(gSig, i, 0) * M[j] + sym3(gSig, i, 1) * M[3 + j] +
+                                    sym3(gSig, i, 2) * M[6 + j]);
+            gR[3 * i + j] = gM * f.S[j];
+            gls[j] += gM * f.R[3 * i + j] * f.S[j];
+        }
+    const float w = f.q[0], x = f.q[1], y = f.q[2], z = f.q[3];
+    float gq[4];
+    gq[0] = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    gq[1] = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] +
+                   w * gR[7] - 2.f * x * gR[8]);
+    gq[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] +
+                   z * gR[7] - 2.f * y * gR[8]);
+    gq[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] +
+                   y * gR[5] + x * gR[6] + y * gR[7]);
+    const float dot = f.q[0] * gq[0] + f.q[1] * gq[1] + f.q[2] * gq[2] + f.q[3] * gq[3];
+    const float rq = 1.f / f.qn;
+    for (int i = 0; i < 4; ++i) g_quat[4 * g + i] += (gq[i] - f.q[i] * dot) * rq;
+    for (int j = 0; j < 3; ++j) {
+        g_mean[3 * g + j] += gmu[j];
+        g_ls[3 * g + j] += gls[j];
+    }
+    g_ologit[g] += go_total * o * (1.f - o);
+}
+
+sg_status launch_project_fwd(const sg_gaussians *g, const sg_view *views, int n_views,
+                             const sg_config *cfg, sg_projected *out, cudaStream_t st) {
+    ProjConsts pc{cfg->z_near, cfg->dilation, cfg->fov_clamp, cfg->alpha_min, cfg->tile_w,
+                  cfg->tile_h};
+    const int threads = 256;
+    const int blocks = (g->N + threads - 1) / threads;
+    if (blocks > 0)
+        project_fwd_kernel<<<blocks, threads, 0, st>>>(
+            g->mean, g->log_scale, reinterpret_cast<const float4 *>(g->quat), g->opacity_logit,
+            g->N, views, n_views, pc, reinterpret_cast<float4 *>(out->geo),
+            reinterpret_cast<uint2 *>(out->rect));
+    if (blocks > 0) count_launches(1);
+    return check_launch("project_fwd");
+}
+
+sg_status launch_project_bwd(const sg_gaussians *g, const sg_view *views, int n_views,
+                             const sg_config *cfg, const sg_projected *proj, const float *g2d,
+                             sg_gaussian_grads *gr, cudaStream_t st) {
+    ProjConsts pc{cfg->z_near, cfg->dilation, cfg->fov_clamp, cfg->alpha_min, cfg->tile_w,
+                  cfg->tile_h};
+    const int threads = 256;
+    const int blocks = (g->N + threads - 1) / threads;
+    if (blocks > 0)
+        project_bwd_kernel<<<blocks, threads, 0, st>>>(
+            g->mean, g->log_scale, reinterpret_cast<const float4 *>(g->quat), g->opacity_logit,
+            g->N, views, n_views, pc, reinterpret_cast<const uint2 *>(proj->rect),
+            reinterpret_cast<const float4 *>(g2d),
+            gr->mean, gr->log_scale, gr->quat, gr->opacity_logit);
+    if (blocks > 0) count_launches(1);
+    return check_launch("project_bwd");
+}
+
+}  // namespace sg

@@ -1,0 +1,59 @@
+// raster.cuh -- launch arguments of the tile compositing kernels (raster.cu), shared with
+// the C-ABI layer.
+#pragma once
+
+#include "sg_common.cuh"
+
+namespace sg {
+
+struct RasterArgs {
+    const float4 *geo;
+    const uint32_t *record;
+    const int2 *ranges;
+    const float *rgb;
+    const float *sem;
+    const sg_view *views;
+    int n_views, n_tiles, N;
+    float alpha_max, alpha_min, T_min;
+    float bg0, bg1, bg2;
+    int tile_w, tile_h, batch;
+    int *work_counter;
+    int persistent;
+    // forward outputs / backward inputs
+    float *img_rgb, *img_depth, *img_sem;
+    float *T_final;
+    int *last, *n_contrib;
+    // backward
+    const float *dL_rgb, *dL_depth, *dL_sem;
+    float *g2d, *g_rgb, *g_sem;
+};
+
+inline void fill_raster_args(RasterArgs &a, const sg_gaussians *g, const sg_projected *proj,
+                             const sg_tile_lists *lists, const sg_view *views, int n_views,
+                             int n_tiles, const sg_config *cfg, int *work_counter) {
+    a.geo = reinterpret_cast<const float4 *>(proj->geo);
+    a.record = lists->record;
+    a.ranges = reinterpret_cast<const int2 *>(lists->ranges);
+    a.rgb = g->rgb;
+    a.sem = g->sem;
+    a.views = views;
+    a.n_views = n_views;
+    a.n_tiles = n_tiles;
+    a.N = g->N;
+    a.alpha_max = cfg->alpha_max;
+    a.alpha_min = cfg->alpha_min;
+    a.T_min = cfg->T_min;
+    a.bg0 = cfg->bg[0];
+    a.bg1 = cfg->bg[1];
+    a.bg2 = cfg->bg[2];
+    a.tile_w = cfg->tile_w;
+    a.tile_h = cfg->tile_h;
+    a.batch = cfg->batch;
+    a.work_counter = work_counter;
+    a.persistent = cfg->persistent;
+}
+
+sg_status launch_raster(RasterArgs &a, int C, bool backward, cudaStream_t st);
+bool raster_supports(int C);
+
+}  // namespace sg

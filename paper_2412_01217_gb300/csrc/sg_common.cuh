@@ -1,0 +1,103 @@
+// sg_common.cuh -- device helpers shared by the sm_103a kernels of the pyramid splatting
+// library.  Nothing here is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sg.h"
+
+#define SG_FULL_MASK 0xffffffffu
+
+namespace sg {
+
+// Largest tile: 32x8 or 16x16 pixels = 256 threads per CTA.
+constexpr int kMaxTileThreads = 256;
+
+struct Float3 {
+    float x, y, z;
+};
+
+// ----------------------------------------------------------------------------------------
+// alpha of one Gaussian at one pixel (Eq. 3 with the anisotropic 2D covariance S).  The
+// exponent sigma = 1/2 d^T S^{-1} d is evaluated in its conditional (Schur complement)
+// form  sigma = (m00 dx)^2 + (m10 dx + m11 dy)^2  with m00 = 1/sqrt(2 s00),
+// m10 = -s01/sqrt(2 s00 det), m11 = sqrt(s00/(2 det)): a sum of squares, so no
+// cancellation for elongated footprints, and 7 flops.  The forward and backward kernels
+// must take bit-identical skip/stop decisions, so every rounding step is spelled out with
+// _rn intrinsics (no compiler contraction can differ between kernels).
+// ----------------------------------------------------------------------------------------
+struct AlphaEval {
+    float dx, dy;  // pixel - mean2D
+    float p1, p2;  // m00 dx, m10 dx + m11 dy
+    float G;       // exp(-sigma)
+    float raw;     // o * G
+    float alpha;   // min(alpha_max, raw)
+};
+
+__device__ __forceinline__ bool eval_alpha(float px, float py, float u, float v, float m00, float m10,
+                                           float m11, float o, float alpha_max, float alpha_min,
+                                           AlphaEval &e) {
+    e.dx = __fsub_rn(px, u);
+    e.dy = __fsub_rn(py, v);
+    e.p1 = __fmul_rn(m00, e.dx);
+    e.p2 = __fmaf_rn(m10, e.dx, __fmul_rn(m11, e.dy));
+    const float sigma = __fmaf_rn(e.p2, e.p2, __fmul_rn(e.p1, e.p1));
+    if (!(sigma >= 0.f)) return false;
+    e.G = __expf(-sigma);
+    e.raw = __fmul_rn(o, e.G);
+    e.alpha = fminf(alpha_max, e.raw);
+    return e.alpha >= alpha_min;
+}
+
+// a*b - c*d with one rounding error (Kahan's algorithm with FMA).
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+    const float w = c * d;
+    const float err = __fmaf_rn(-c, d, w);
+    const float dop = __fmaf_rn(a, b, -w);
+    return dop + err;
+}
+
+// ----------------------------------------------------------------------------------------
+// Lane-transposed warp reduction: NV (power of two, >= 32) values per lane are summed over
+// the warp with NV-1 shuffles; afterwards lane l holds the sums of values
+// [l*NV/32, (l+1)*NV/32) in v[0 .. NV/32).
+// ----------------------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void warp_transpose_reduce(float (&v)[NV], int lane) {
+    static_assert(NV >= 32 && (NV & (NV - 1)) == 0, "NV must be a power of two >= 32");
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int s = 16 >> step;
+        const int half = NV >> (step + 1);
+        const bool upper = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = upper ? v[i] : v[i + half];
+            const float keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(SG_FULL_MASK, send, s);
+        }
+    }
+}
+
+__device__ __forceinline__ int find_view(const sg_view *views, int n_views, int tile) {
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].tile_offset <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t pack16(int a, int b) {
+    return (uint32_t)a | ((uint32_t)b << 16);
+}
+
+}  // namespace sg
+
+// Internal launch helpers (defined in api.cu / the kernel files).
+namespace sg {
+void set_error(const char *fmt, ...);
+void count_launches(int n);  // kernel launches issued by the library (diagnostics)
+sg_status check_launch(const char *what);
+}  // namespace sg

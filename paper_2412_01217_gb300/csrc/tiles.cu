@@ -1,0 +1,398 @@
+// tiles.cu -- per-tile depth-sorted instance lists (the sorted set N of Eq. 7-9).
+//
+// Pipeline (all counts stay on the device, so the whole sequence can be captured in a
+// CUDA graph with a fixed launch shape):
+//   1. compact:  visible records r (non-empty tile rectangle) -> (depth bits, r), in r order
+//   2. sort:     stable LSD radix sort by the 32 float32 depth bits (depths are > z_near > 0
+//                so their bit patterns order like the values); ties keep record order
+//   3. emit:     exclusive scan of the tile counts in depth order, then each record writes
+//                (global tile id, r) for every tile of its rectangle, row-major
+//   4. sort:     stable LSD radix sort of the instances by global tile id (only the bits
+//                n_tiles needs), which keeps the (depth, record) order inside each tile
+//   5. ranges:   [start, end) of every tile
+// The result equals sorting all instances by (tile, depth bits, record id).  Every radix
+// pass is three kernels: per-block digit histograms, per-digit scans over the blocks, and
+// a stable scatter that ranks equal digits inside a block by warp match + prefix counts.
+#include <cstdio>
+
+#include "sg_common.cuh"
+
+namespace sg {
+
+constexpr int kScanThreads = 256;
+
+__device__ __forceinline__ void block_range(int n, int G, int b, int &beg, int &end) {
+    const int tiles = (n + kScanThreads - 1) / kScanThreads;
+    const int per = (tiles + G - 1) / G;
+    beg = min(n, b * per * kScanThreads);
+    end = min(n, beg + per * kScanThreads);
+}
+
+// Exclusive block scan of one value per thread (blockDim == kScanThreads).
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t &total) {
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(SG_FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = kScanThreads / 32;
+        uint32_t w = lane < nw ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(SG_FULL_MASK, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < nw) s_warp[lane] = wi - w;
+        if (lane == nw - 1) s_warp[nw] = wi;
+    }
+    __syncthreads();
+    const uint32_t res = incl - v + s_warp[warp];
+    total = s_warp[kScanThreads / 32];
+    __syncthreads();
+    return res;
+}
+
+// ---------------------------------------------------------------------------------------
+// Device-wide exclusive scan (reduce / scan block sums / apply) with a device-side count.
+// ---------------------------------------------------------------------------------------
+
+struct VisibleCount {  // 1 if the record's tile rectangle is non-empty
+    const uint2 *rect;
+    __device__ uint32_t operator()(int i) const {
+        const uint2 r = rect[i];
+        return r.x != r.y ? 1u : 0u;
+    }
+};
+
+__device__ __forceinline__ uint32_t rect_tiles(uint2 r) {
+    const uint32_t tx0 = r.x & 0xffffu, ty0 = r.x >> 16, tx1 = r.y & 0xffffu, ty1 = r.y >> 16;
+    return (tx1 > tx0 && ty1 > ty0) ? (tx1 - tx0) * (ty1 - ty0) : 0u;
+}
+
+struct SortedTileCount {  // tiles of the record at sorted position i
+    const uint2 *rect;
+    const uint32_t *rec;
+    __device__ uint32_t operator()(int i) const { return rect_tiles(rect[rec[i]]); }
+};
+
+template <class F>
+__global__ void scan_reduce_kernel(F f, const int *n_ptr, int n_host, uint32_t *bsum, int G) {
+    const int n = n_ptr ? *n_ptr : n_host;
+    int beg, end;
+    block_range(n, G, blockIdx.x, beg, end);
+    uint32_t s = 0;
+    for (int i = beg + threadIdx.x; i < end; i += kScanThreads) s += f(i);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(SG_FULL_MASK, s, o);
+    __shared__ uint32_t sw[kScanThreads / 32];
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += sw[w];
+        bsum[blockIdx.x] = t;
+    }
+}
+
+// One block: exclusive scan of G block sums (G <= 4096); writes the grand total.
+__global__ void scan_blocks_kernel(uint32_t *bsum, int G, int *total) {
+    uint32_t run = 0;
+    for (int base = 0; base < G; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < G ? bsum[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, tot);
+        if (i < G) bsum[i] = ex + run;
+        run += tot;
+    }
+    if (threadIdx.x == 0) *total = (int)run;
+}
+
+// Apply for the compaction: write (depth bits, record) of every visible record.
+__global__ void compact_apply_kernel(const uint2 *__restrict__ rect, const float4 *__restrict__ geo,
+                                     int n, const uint32_t *__restrict__ boff, int G,
+                                     uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
+    int beg, end;
+    block_range(n, G, blockIdx.x, beg, end);
+    uint32_t run = boff[blockIdx.x];
+    for (int base = beg; base < end; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        uint32_t f = 0;
+        uint2 r = make_uint2(0, 0);
+        if (i < end) {
+            r = rect[i];
+            f = r.x != r.y ? 1u : 0u;
+        }
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(f, tot);
+        if (f) {
+            const float depth = geo[2 * (size_t)i].z;
+            key[run + ex] = __float_as_uint(depth);
+            val[run + ex] = (uint32_t)i;
+        }
+        run += tot;
+    }
+}
+
+// Apply for the emission: record at sorted position m writes its tiles at offset.
+__global__ void emit_apply_kernel(const uint2 *__restrict__ rect, const uint32_t *__restrict__ rec,
+                                  const int *__restrict__ m_ptr, const uint32_t *__restrict__ boff,
+                                  int G, int N, const sg_view *__restrict__ views,
+                                  uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval,
+                                  int capacity, uint32_t *__restrict__ status) {
+    const int n = *m_ptr;
+    int beg, end;
+    block_range(n, G, blockIdx.x, beg, end);
+    uint32_t run = boff[blockIdx.x];
+    bool overflow = false;
+    for (int base = beg; base < end; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        uint32_t c = 0, r = 0;
+        uint2 rc = make_uint2(0, 0);
+        if (i < end) {
+            r = rec[i];
+            rc = rect[r];
+            c = rect_tiles(rc);
+        }
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(c, tot);
+        if (c) {
+            const int v = (int)(r / (uint32_t)N);
+            const int tiles_x = views[v].tiles_x, toff = views[v].tile_offset;
+            const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16, tx1 = rc.y & 0xffffu, ty1 = rc.y >> 16;
+            uint32_t o = run + ex;
+            for (uint32_t ty = ty0; ty < ty1; ++ty)
+                for (uint32_t tx = tx0; tx < tx1; ++tx, ++o) {
+                    if (o < (uint32_t)capacity) {
+                        tkey[o] = (uint32_t)toff + ty * (uint32_t)tiles_x + tx;
+                        tval[o] = r;
+                    } else {
+                        overflow = true;
+                    }
+                }
+        }
+        run += tot;
+    }
+    if (overflow) atomicOr(status, SG_STATUS_CAPACITY);
+}
+
+// ---------------------------------------------------------------------------------------
+// Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits (or fewer).
+// ---------------------------------------------------------------------------------------
+
+__global__ void rs_hist_kernel(const uint32_t *__restrict__ keys, const int *__restrict__ n_ptr,
+                               int cap, int shift, uint32_t mask, uint32_t *__restrict__ hist, int G) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int n = min(*n_ptr, cap);
+    int beg, end;
+    block_range(n, G, blockIdx.x, beg, end);
+    for (int i = beg + threadIdx.x; i < end; i += kScanThreads)
+        atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+    __syncthreads();
+    hist[threadIdx.x * G + blockIdx.x] = h[threadIdx.x];
+}
+
+// Block d: exclusive scan of digit d's per-block counts; totals[d] = digit d's count.
+__global__ void rs_digit_scan_kernel(uint32_t *__restrict__ hist, uint32_t *__restrict__ totals, int G) {
+    const int d = blockIdx.x;
+    uint32_t run = 0;
+    for (int base = 0; base < G; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < G ? hist[d * G + i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, tot);
+        if (i < G) hist[d * G + i] = ex + run;
+        run += tot;
+    }
+    if (threadIdx.x == 0) totals[d] = run;
+}
+
+__global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
+    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, const int *__restrict__ n_ptr, int cap, int shift, uint32_t mask,
+    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, int G) {
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wcnt[kWarps][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // digit base = exclusive scan of the digit totals (+ this block's offset)
+    {
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(totals[tid], tot);
+        run[tid] = ex + hist[tid * G + blockIdx.x];
+    }
+    const int n = min(*n_ptr, cap);
+    int beg, end;
+    block_range(n, G, blockIdx.x, beg, end);
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (int base = beg; base < end; base += kScanThreads) {
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+        const int i = base + tid;
+        const bool valid = i < end;
+        const uint32_t key = valid ? kin[i] : 0u;
+        const uint32_t d = valid ? ((key >> shift) & mask) : 256u;
+        const uint32_t peers = __match_any_sync(SG_FULL_MASK, d);
+        const uint32_t rank = __popc(peers & lt_mask);
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t t = wcnt[w][tid];
+            wcnt[w][tid] = s;
+            s += t;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = run[d] + wcnt[warp][d] + rank;
+            kout[pos] = key;
+            vout[pos] = vin[i];
+        }
+        __syncthreads();
+        run[tid] += s;
+    }
+}
+
+// Sorts n (device count, clamped to cap) pairs on bits [0, bits) from (kin, vin) into
+// (kout, vout) using (ktmp, vtmp) as ping-pong; kin/vin are not modified.
+static void radix_sort(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+                       uint32_t *ktmp, uint32_t *vtmp, const int *n_ptr, int cap, int bits,
+                       uint32_t *hist, uint32_t *totals, int G, cudaStream_t st) {
+    const int passes = (bits + 7) / 8;
+    const uint32_t *ks = kin, *vs = vin;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        const int nb = min(8, bits - shift);
+        const uint32_t mask = (1u << nb) - 1u;
+        uint32_t *kd = ((passes - 1 - p) % 2 == 0) ? kout : ktmp;
+        uint32_t *vd = ((passes - 1 - p) % 2 == 0) ? vout : vtmp;
+        rs_hist_kernel<<<G, kScanThreads, 0, st>>>(ks, n_ptr, cap, shift, mask, hist, G);
+        rs_digit_scan_kernel<<<256, kScanThreads, 0, st>>>(hist, totals, G);
+        rs_scatter_kernel<<<G, kScanThreads, 0, st>>>(ks, vs, kd, vd, n_ptr, cap, shift, mask, hist,
+                                                      totals, G);
+        count_launches(3);
+        ks = kd;
+        vs = vd;
+    }
+}
+
+__global__ void clamp_count_kernel(const int *in, int cap, int *out) { *out = min(*in, cap); }
+
+__global__ void ranges_kernel(const uint32_t *__restrict__ tile, const int *__restrict__ k_ptr,
+                              int2 *__restrict__ ranges) {
+    const int K = *k_ptr;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) {
+        const uint32_t t = tile[i];
+        if (i == 0 || tile[i - 1] != t) ranges[t].x = i;
+        if (i == K - 1 || tile[i + 1] != t) ranges[t].y = i + 1;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Workspace layout
+// ---------------------------------------------------------------------------------------
+
+struct TileWorkspace {
+    uint32_t *dkey_in, *dval_in, *dkey_out, *dval_out, *dkey_tmp, *dval_tmp;
+    uint32_t *tkey_in, *tval_in, *tkey_tmp, *tval_tmp;
+    uint32_t *bsum, *hist, *totals;
+    int *counts;  // [0] visible records M, [1] K clamped
+};
+
+static int sort_grid() {
+    static int G = 0;
+    if (!G) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        G = sms > 0 ? 4 * sms : 512;
+        if (G > 4096) G = 4096;
+    }
+    return G;
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t tile_ws_layout(int64_t R, int32_t cap, int G, TileWorkspace *ws, char *base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *p = base ? base + off : nullptr;
+        off += align_up(bytes);
+        return p;
+    };
+    const size_t r4 = (size_t)R * 4, c4 = (size_t)cap * 4;
+    TileWorkspace w{};
+    w.dkey_in = (uint32_t *)take(r4);
+    w.dval_in = (uint32_t *)take(r4);
+    w.dkey_out = (uint32_t *)take(r4);
+    w.dval_out = (uint32_t *)take(r4);
+    w.dkey_tmp = (uint32_t *)take(r4);
+    w.dval_tmp = (uint32_t *)take(r4);
+    w.tkey_in = (uint32_t *)take(c4);
+    w.tval_in = (uint32_t *)take(c4);
+    w.tkey_tmp = (uint32_t *)take(c4);
+    w.tval_tmp = (uint32_t *)take(c4);
+    w.bsum = (uint32_t *)take((size_t)G * 4);
+    w.hist = (uint32_t *)take((size_t)G * 256 * 4);
+    w.totals = (uint32_t *)take(256 * 4);
+    w.counts = (int *)take(4 * sizeof(int));
+    if (ws) *ws = w;
+    return off;
+}
+
+size_t tile_lists_workspace_size(int64_t R, int32_t cap) {
+    return tile_ws_layout(R, cap, sort_grid(), nullptr, nullptr);
+}
+
+sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
+                                  const sg_view *views, int n_tiles, sg_tile_lists *lists,
+                                  void *workspace, size_t ws_bytes, uint32_t *status,
+                                  cudaStream_t st) {
+    const int G = sort_grid();
+    const int64_t R = (int64_t)N * n_views;
+    TileWorkspace w;
+    const size_t need = tile_ws_layout(R, lists->capacity, G, &w, (char *)workspace);
+    if (ws_bytes < need) {
+        set_error("build_tile_lists: workspace %zu bytes < %zu needed", ws_bytes, need);
+        return SG_ERR_CAPACITY;
+    }
+    const uint2 *rect = reinterpret_cast<const uint2 *>(proj->rect);
+    const float4 *geo = reinterpret_cast<const float4 *>(proj->geo);
+    // 1. compaction of visible records (count -> counts[0])
+    scan_reduce_kernel<<<G, kScanThreads, 0, st>>>(VisibleCount{rect}, nullptr, (int)R, w.bsum, G);
+    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.bsum, G, w.counts + 0);
+    compact_apply_kernel<<<G, kScanThreads, 0, st>>>(rect, geo, (int)R, w.bsum, G, w.dkey_in, w.dval_in);
+    // 2. depth sort (32 bits)
+    radix_sort(w.dkey_in, w.dval_in, w.dkey_out, w.dval_out, w.dkey_tmp, w.dval_tmp, w.counts + 0,
+               (int)R, 32, w.hist, w.totals, G, st);
+    // 3. emission in depth order (K -> lists->count)
+    scan_reduce_kernel<<<G, kScanThreads, 0, st>>>(SortedTileCount{rect, w.dval_out}, w.counts + 0, 0,
+                                                   w.bsum, G);
+    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.bsum, G, lists->count);
+    emit_apply_kernel<<<G, kScanThreads, 0, st>>>(rect, w.dval_out, w.counts + 0, w.bsum, G, N, views,
+                                                  w.tkey_in, w.tval_in, lists->capacity, status);
+    // 4. stable sort by tile id
+    int bits = 1;
+    while ((1ll << bits) < (long long)n_tiles) ++bits;
+    radix_sort(w.tkey_in, w.tval_in, lists->tile, lists->record, w.tkey_tmp, w.tval_tmp,
+               lists->count, lists->capacity, bits, w.hist, w.totals, G, st);
+    // 5. tile ranges
+    cudaMemsetAsync(lists->ranges, 0, sizeof(int) * 2 * (size_t)n_tiles, st);
+    clamp_count_kernel<<<1, 1, 0, st>>>(lists->count, lists->capacity, w.counts + 1);
+    ranges_kernel<<<G, kScanThreads, 0, st>>>(lists->tile, w.counts + 1,
+                                              reinterpret_cast<int2 *>(lists->ranges));
+    count_launches(3 + 3 + 2);  // compaction, emission, clamp + ranges
+    return check_launch("build_tile_lists");
+}
+
+}  // namespace sg

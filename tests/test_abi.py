@@ -1,0 +1,85 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point include/sg.h
+declares, the ctypes layouts match, and host-side argument validation rejects bad input
+before any launch (none of these calls touches a GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "sg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2412_01217_gb300 import _lib
+    lib = _lib.load()
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in _lib.SIGNATURES, f"{n} has no ctypes signature"
+
+
+def test_struct_sizes_match_header_layout():
+    from paper_2412_01217_gb300 import _lib
+    assert C.sizeof(_lib.SgCamera) == 72
+    assert C.sizeof(_lib.SgView) == 96
+    assert C.sizeof(_lib.SgGaussians) == 56
+    assert C.sizeof(_lib.SgConfig) == 52
+    assert C.sizeof(_lib.SgLossConfig) == 40
+
+
+def test_defaults_and_version():
+    from paper_2412_01217_gb300 import _lib
+    lib = _lib.load()
+    c = _lib.SgConfig()
+    lib.sg_default_config(C.byref(c))
+    assert c.alpha_max == pytest.approx(0.99) and c.alpha_min == pytest.approx(1 / 255)
+    assert c.T_min == pytest.approx(1e-4) and c.tile_w == 16 and c.tile_h == 16
+    lc = _lib.SgLossConfig()
+    lib.sg_default_loss_config(C.byref(lc))
+    assert lc.lambda_r == pytest.approx(0.2) and lc.lambda_s == pytest.approx(0.2)
+    assert b"sm_103a" in lib.sg_version()
+
+
+def test_make_views_pyramid_geometry():
+    import numpy as np
+    from paper_2412_01217_gb300 import make_views
+    import synthetic
+    cam = synthetic.make_camera(1200, 680, 600.0, 600.0, 599.5, 339.5)
+    views, P, T = make_views([cam, cam], 3)
+    assert [(v.W, v.H) for v in views][:3] == [(1200, 680), (600, 340), (300, 170)]
+    assert views[1].cx == 299.5 and views[2].cx == 149.5 and views[2].fx == 150.0
+    assert P == 2 * (1200 * 680 + 600 * 340 + 300 * 170)
+    assert T == 2 * (75 * 43 + 38 * 22 + 19 * 11)
+    assert [v.pixel_offset for v in views] == list(np.cumsum([0] + [v.W * v.H for v in views])[:-1])
+
+
+def test_host_validation_rejects_bad_arguments():
+    from paper_2412_01217_gb300 import _lib
+    from paper_2412_01217_gb300.splat import make_views
+    lib = _lib.load()
+    import synthetic
+    cam = synthetic.make_camera(4, 4, 4.0, 4.0, 2.0, 2.0)
+    with pytest.raises(_lib.SgError) as e:
+        make_views([cam], 4)          # level 3 would be 0 x 0
+    assert e.value.code == 1
+    cfg = _lib.SgConfig()
+    lib.sg_default_config(C.byref(cfg))
+    cfg.tile_w = 12
+    g = _lib.SgGaussians()
+    g.N, g.C = 10, 7                  # C not supported
+    proj = _lib.SgProjected()
+    assert lib.sg_project_gaussians(C.byref(g), None, 1, C.byref(cfg), C.byref(proj), None) == 1
+    assert b"C=7" in lib.sg_last_error()
+    g.C = 8
+    assert lib.sg_project_gaussians(C.byref(g), None, 1, C.byref(cfg), C.byref(proj), None) == 1
+    assert b"NULL" in lib.sg_last_error()
+    assert lib.sg_adam_step(None, None, None, None, 5, 1e-3, 0.9, 0.999, 1e-8, 0, None) == 1
+    assert lib.sg_adam_step(None, None, None, None, 0, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 0

@@ -1,0 +1,335 @@
+"""GPU parity of the CUDA path (called through the C ABI) against the FP64 oracle.
+
+Forward: |gpu - oracle| <= 1e-4 |oracle| + 1e-5 per pixel and channel.  Gradients:
+|gpu - oracle| <= 2e-3 |oracle| + 1e-5 max|oracle| per element.  Tile lists: bit-exact
+against the oracle's integer reference built from the GPU's own float32 records.  Pixels
+whose skip (alpha vs 1/255), stop (T vs 1e-4) or depth-order decision lies within 1e-3
+(relative) of the threshold in the oracle are excluded (a float32 evaluation may take the
+other branch there); their count is asserted to be small.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+from helpers import AMBIGUOUS, AMBIGUOUS_GRAD, FWD_ABS, FWD_REL, check_close, check_grads
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("mean", "log_scale", "quat", "opacity_logit", "rgb", "sem")
+
+
+def f32_camera(cam):
+    c = dict(cam)
+    c["R_cw"] = np.asarray(cam["R_cw"], np.float32).astype(np.float64)
+    c["t_cw"] = np.asarray(cam["t_cw"], np.float32).astype(np.float64)
+    for k in ("fx", "fy", "cx", "cy"):
+        c[k] = float(np.float32(cam[k]))
+    return c
+
+
+def make(g, cams, levels=1, capacity=None, **kw):
+    from paper_2412_01217_gb300 import PyramidRasterizer, RenderConfig, to_device_params
+    C = g["sem"].shape[1]
+    r = PyramidRasterizer(g["mean"].shape[0], C, cams, levels, RenderConfig(**kw), capacity=capacity)
+    return r, to_device_params(g)
+
+
+def view_images(r, v, C):
+    return dict(rgb=r.view_slice(r.img_rgb, v, 3).cpu().numpy(),
+                depth=r.view_slice(r.img_depth, v, 1)[0].cpu().numpy(),
+                sem=r.view_slice(r.img_sem, v, C).cpu().numpy(),
+                T=r.view_slice(r.T_final, v, 1)[0].cpu().numpy(),
+                n_contrib=r.view_slice(r.n_contrib, v, 1)[0].cpu().numpy())
+
+
+def oracle_cams(cams, levels):
+    out = []
+    for c in cams:
+        out.extend(oracle.level_cameras(c, levels))
+    return out
+
+
+@pytest.fixture(scope="module")
+def cloud():
+    g = synthetic.cloud_scene(2000, 8, seed=1)
+    cam = f32_camera(synthetic.cloud_camera())
+    return g, cam
+
+
+def test_projection_matches_oracle(cloud):
+    g, cam = cloud
+    r, p = make(g, [cam])
+    r.project(p)
+    torch.cuda.synchronize()
+    geo = r.geo.view(-1, 8).cpu().numpy().astype(np.float64)
+    rect = r.rect.view(-1, 2).cpu().numpy().view(np.uint32)
+    pr = oracle.project(g, cam)
+    P = oracle.P
+    vg = rect[:, 0] != rect[:, 1]
+    vo = pr[:, P["VALID"]] == 1
+    assert vg.sum() > 1000
+    assert not (vg & ~vo).any(), "GPU keeps a Gaussian the oracle culls"
+    m = vg
+    check_close("u", geo[m, 0], pr[m, P["U"]], 0, 2e-4)
+    check_close("v", geo[m, 1], pr[m, P["V"]], 0, 2e-4)
+    check_close("depth", geo[m, 2], pr[m, P["DEPTH"]], 1e-6, 0)
+    check_close("opacity", geo[m, 3], pr[m, P["OPAC"]], 1e-6, 1e-7)
+    # the record stores the conditional factors: conic = 2 [[m00^2 + m10^2, m10 m11], [., m11^2]]
+    m00, m10, m11 = geo[m, 4], geo[m, 5], geo[m, 6]
+    conic = {"CA": 2 * (m00 ** 2 + m10 ** 2), "CB": 2 * m10 * m11, "CC": 2 * m11 ** 2}
+    scale = np.maximum(np.abs(pr[m, P["CA"]]), np.abs(pr[m, P["CC"]]))
+    for k, val in conic.items():
+        check_close(f"conic {k}", val / scale, pr[m, P[k]] / scale, 0, 2e-5)
+    # every pixel where alpha can reach 1/255 lies inside the GPU tile rectangle
+    tx0, ty0 = rect[:, 0] & 0xFFFF, rect[:, 0] >> 16
+    tx1, ty1 = rect[:, 1] & 0xFFFF, rect[:, 1] >> 16
+    for i in np.where(vo)[0]:
+        x0 = max(0, int(np.ceil(pr[i, P["U"]] - pr[i, P["EXTX"]])))
+        x1 = min(cam["W"] - 1, int(np.floor(pr[i, P["U"]] + pr[i, P["EXTX"]])))
+        y0 = max(0, int(np.ceil(pr[i, P["V"]] - pr[i, P["EXTY"]])))
+        y1 = min(cam["H"] - 1, int(np.floor(pr[i, P["V"]] + pr[i, P["EXTY"]])))
+        if x0 > x1 or y0 > y1:
+            continue
+        assert vg[i], i
+        assert tx0[i] <= x0 // 16 and tx1[i] >= x1 // 16 + 1 and ty0[i] <= y0 // 16 and ty1[i] >= y1 // 16 + 1, i
+        assert tx1[i] - tx0[i] <= (x1 // 16 + 1 - x0 // 16) + 1 and ty1[i] - ty0[i] <= (y1 // 16 + 1 - y0 // 16) + 1
+
+
+def _lists_vs_reference(r):
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
+    K = r.instance_count()
+    tiles = r.tile[:K].cpu().numpy().view(np.uint32).astype(np.int64)
+    recs = r.record[:K].cpu().numpy().view(np.uint32).astype(np.int64)
+    ranges = r.ranges.view(-1, 2).cpu().numpy().astype(np.int64)
+    rect = r.rect.view(-1, 2).cpu().numpy().view(np.uint32)
+    rects = np.stack([rect[:, 0] & 0xFFFF, rect[:, 0] >> 16, rect[:, 1] & 0xFFFF, rect[:, 1] >> 16], 1)
+    depth = r.geo.view(-1, 8)[:, 2].cpu().numpy()
+    tx = [r.views_host[v].tiles_x for v in range(r.V)]
+    to = [r.views_host[v].tile_offset for v in range(r.V)]
+    rt, rr, rg = oracle.tile_lists(rects, depth, tx, to, r.n_tiles, r.N)
+    assert K == len(rt)
+    assert np.array_equal(tiles, rt)
+    assert np.array_equal(recs, rr)
+    assert np.array_equal(ranges, rg)
+    return K
+
+
+def test_tile_lists_bit_exact_single_view(cloud):
+    g, cam = cloud
+    for tw, th in ((16, 16), (8, 8), (32, 8)):
+        r, p = make(g, [cam], tile_w=tw, tile_h=th)
+        r.project(p)
+        r.build_lists()
+        assert _lists_vs_reference(r) > 2000
+
+
+def room_small(n=20000, C=16, seed=4, ncam=2, W=320, H=180):
+    room = synthetic.Room(n_classes=32, seed=3)
+    intr = dict(W=W, H=H, fx=W / 2.0, fy=W / 2.0, cx=W / 2 - 0.5, cy=H / 2 - 0.5)
+    cams = [f32_camera(c) for c in room.trajectory(ncam, intr, seed=7)]
+    g = room.sample_gaussians(n, C, seed=seed, sem_mode="random")
+    return room, g, cams
+
+
+def test_tile_lists_bit_exact_pyramid_multi_view():
+    room, g, cams = room_small()
+    r, p = make(g, cams, levels=3)
+    r.project(p)
+    r.build_lists()
+    assert _lists_vs_reference(r) > 10000
+
+
+def test_forward_matches_oracle_cloud(cloud):
+    g, cam = cloud
+    r, p = make(g, [cam])
+    r.forward(p)
+    got = view_images(r, 0, 8)
+    ref = oracle.render(g, cam)
+    amb = (ref["flags"] & AMBIGUOUS) != 0
+    assert amb.mean() < 0.02
+    ok = ~amb
+    for k in ("rgb", "depth", "sem", "T"):
+        check_close(k, got[k], ref[k], FWD_REL, FWD_ABS, mask=ok)
+    assert np.array_equal(got["n_contrib"][ok], ref["n_contrib"][ok])
+
+
+def test_forward_bitwise_identical_across_tiles_batches_and_runs(cloud):
+    g, cam = cloud
+    base = None
+    for tw, th, batch, pers in ((16, 16, 128, True), (8, 8, 32, True), (32, 8, 256, False),
+                                (16, 8, 64, True), (16, 16, 128, True)):
+        r, p = make(g, [cam], tile_w=tw, tile_h=th, batch=batch, persistent=pers)
+        r.forward(p)
+        im = view_images(r, 0, 8)
+        if base is None:
+            base = im
+            continue
+        for k in ("rgb", "depth", "sem", "T", "n_contrib"):
+            assert np.array_equal(im[k], base[k]), (k, tw, th, batch, pers)
+
+
+def test_backward_matches_oracle_cloud(cloud):
+    g, cam = cloud
+    r, p = make(g, [cam])
+    r.forward(p)
+    ref_f = oracle.render(g, cam)
+    keep = ((ref_f["flags"] & AMBIGUOUS_GRAD) == 0).astype(np.float64)
+    rng = np.random.default_rng(11)
+    H, W, C = cam["H"], cam["W"], 8
+    up_rgb = rng.normal(size=(3, H, W)) * keep
+    up_d = rng.normal(size=(H, W)) * keep
+    up_s = rng.normal(size=(C, H, W)) * keep
+    dl = (torch.tensor(up_rgb.reshape(-1), dtype=torch.float32, device="cuda"),
+          torch.tensor(up_d.reshape(-1), dtype=torch.float32, device="cuda"),
+          torch.tensor(up_s.reshape(-1), dtype=torch.float32, device="cuda"))
+    grads = {k: torch.zeros_like(v) for k, v in p.items()}
+    r.backward(p, grads, dL=dl)
+    got = {k: v.cpu().numpy() for k, v in grads.items()}
+    # the float32 inputs the GPU saw are exactly what the oracle gets
+    up_rgb32 = dl[0].cpu().numpy().astype(np.float64).reshape(3, H, W)
+    up_d32 = dl[1].cpu().numpy().astype(np.float64).reshape(H, W)
+    up_s32 = dl[2].cpu().numpy().astype(np.float64).reshape(C, H, W)
+    ref = oracle.render_backward(g, cam, up_rgb32, up_d32, up_s32)
+    check_grads(got, ref, KEYS)
+
+
+def test_pyramid_build_matches_oracle():
+    room, g, cams = room_small(ncam=2, W=322, H=183)
+    from paper_2412_01217_gb300 import build_pyramid
+    r, p = make(g, cams, levels=3)
+    frames = [room.raycast(c) for c in cams]
+    for f in frames:
+        f["label"][:3, :5] = -1
+        f["depth"][10:14, 20:30] = 0.0
+    gt = build_pyramid(r, [f["rgb"] for f in frames], [f["depth"] for f in frames],
+                       [f["label"] for f in frames])
+    torch.cuda.synchronize()
+    for c, f in enumerate(frames):
+        ref = oracle.build_pyramid(f["rgb"], f["depth"], f["label"], 3)
+        for l in range(3):
+            v = c * 3 + l
+            check_close(f"rgb c{c} l{l}", r.view_slice(gt["rgb"], v, 3).cpu().numpy(), ref[l][0], 1e-6, 1e-6)
+            check_close(f"depth c{c} l{l}", r.view_slice(gt["depth"], v, 1)[0].cpu().numpy(), ref[l][1], 1e-6, 1e-6)
+            assert np.array_equal(r.view_slice(gt["label"], v, 1)[0].cpu().numpy(), ref[l][2])
+
+
+@pytest.mark.parametrize("mode", ["ce", "ce_decoder", "paper"])
+def test_loss_matches_oracle(mode):
+    from paper_2412_01217_gb300 import LossConfig
+    rng = np.random.default_rng(5)
+    room, g, cams = room_small(ncam=2, W=100, H=70, C=8)
+    r, p = make(g, cams, levels=2)
+    P = r.P
+    rend = (torch.tensor(rng.uniform(size=3 * P), dtype=torch.float32, device="cuda"),
+            torch.tensor(rng.uniform(1, 3, size=P), dtype=torch.float32, device="cuda"),
+            torch.tensor(rng.normal(size=8 * P), dtype=torch.float32, device="cuda"))
+    gdepth = rng.uniform(1, 3, size=P)
+    gdepth[rng.uniform(size=P) < 0.2] = 0.0
+    gt = dict(rgb=torch.tensor(rng.uniform(size=3 * P), dtype=torch.float32, device="cuda"),
+              depth=torch.tensor(gdepth, dtype=torch.float32, device="cuda"),
+              label=torch.tensor(rng.integers(-1, 8, size=P), dtype=torch.int32, device="cuda"),
+              sem=torch.tensor(rng.uniform(size=8 * P), dtype=torch.float32, device="cuda"))
+    dec = dgrad = None
+    if mode == "ce_decoder":
+        dec = torch.tensor(rng.normal(size=(8, 8)), dtype=torch.float32, device="cuda")
+        dgrad = torch.zeros_like(dec)
+    lc = LossConfig(sem_mode="paper" if mode == "paper" else "ce", n_classes=8)
+    r.loss(gt, rendered=rend, decoder=dec, decoder_grad=dgrad, loss_cfg=lc)
+    torch.cuda.synchronize()
+    terms = r.terms.view(-1, 4).cpu().numpy()
+    dec_ref_total = np.zeros((8, 8))
+    for v in range(r.V):
+        sl = lambda t, n: r.view_slice(t, v, n).cpu().numpy().astype(np.float64)
+        tot, tm, gr = oracle.level_loss(sl(rend[0], 3), sl(rend[1], 1)[0], sl(rend[2], 8), sl(gt["rgb"], 3),
+                                        sl(gt["depth"], 1)[0],
+                                        sl(gt["sem"], 8) if mode == "paper" else r.view_slice(gt["label"], v, 1)[0].cpu().numpy(),
+                                        sem_mode="paper" if mode == "paper" else "ce",
+                                        decoder=dec.cpu().numpy() if dec is not None else None)
+        assert terms[v, 0] == pytest.approx(tm["L_r"], rel=1e-5)
+        assert terms[v, 1] == pytest.approx(tm["L_d"], rel=1e-5)
+        assert terms[v, 2] == pytest.approx(tm["L_s"], rel=1e-5)
+        assert terms[v, 3] == pytest.approx(tot, rel=1e-5)
+        for name, buf, n in (("rgb", r.dL_rgb, 3), ("depth", r.dL_depth, 1), ("sem", r.dL_sem, 8)):
+            got = r.view_slice(buf, v, n).cpu().numpy()
+            ref = gr[name].reshape(got.shape)
+            check_close(f"dL/d{name} v{v}", got, ref, 1e-4, 1e-4 * np.abs(ref).max())
+        if dec is not None:
+            dec_ref_total += gr["decoder"]
+    if dec is not None:
+        check_close("dL/ddecoder", dgrad.cpu().numpy(), dec_ref_total, 1e-4, 1e-6)
+
+
+def test_multiview_pyramid_forward_backward_matches_oracle():
+    """Two keyframes x three levels rendered in ONE persistent launch: every pixel of
+    every view-level against the oracle, and all parameter gradients."""
+    room, g, cams = room_small(n=6000, ncam=2, W=160, H=96)
+    r, p = make(g, cams, levels=3)
+    r.forward(p)
+    ocams = oracle_cams(cams, 3)
+    rng = np.random.default_rng(2)
+    ups = []
+    for v, oc in enumerate(ocams):
+        got = view_images(r, v, 16)
+        ref = oracle.render(g, oc)
+        amb = (ref["flags"] & AMBIGUOUS) != 0
+        assert amb.mean() < 0.03
+        for k in ("rgb", "depth", "sem", "T"):
+            check_close(f"v{v} {k}", got[k], ref[k], FWD_REL, FWD_ABS, mask=~amb)
+        keep = ((ref["flags"] & AMBIGUOUS_GRAD) == 0).astype(np.float64)
+        H, W = oc["H"], oc["W"]
+        ups.append((rng.normal(size=(3, H, W)) * keep, rng.normal(size=(H, W)) * keep,
+                    rng.normal(size=(16, H, W)) * keep))
+    dl = [torch.zeros(3 * r.P, device="cuda"), torch.zeros(r.P, device="cuda"), torch.zeros(16 * r.P, device="cuda")]
+    for v, (a, b, c) in enumerate(ups):
+        r.view_slice(dl[0], v, 3).copy_(torch.tensor(a, dtype=torch.float32))
+        r.view_slice(dl[1], v, 1).copy_(torch.tensor(b[None], dtype=torch.float32))
+        r.view_slice(dl[2], v, 16).copy_(torch.tensor(c, dtype=torch.float32))
+    grads = {k: torch.zeros_like(t) for k, t in p.items()}
+    r.backward(p, grads, dL=tuple(dl))
+    got = {k: t.cpu().numpy() for k, t in grads.items()}
+    ref = {k: 0.0 for k in KEYS}
+    for v, oc in enumerate(ocams):
+        a = r.view_slice(dl[0], v, 3).cpu().numpy().astype(np.float64)
+        b = r.view_slice(dl[1], v, 1)[0].cpu().numpy().astype(np.float64)
+        c = r.view_slice(dl[2], v, 16).cpu().numpy().astype(np.float64)
+        rv = oracle.render_backward(g, oc, a, b, c)
+        for k in KEYS:
+            ref[k] = ref[k] + rv[k]
+    check_grads(got, ref, KEYS)
+
+
+def test_capacity_overflow_sets_status_and_reports_need(cloud):
+    g, cam = cloud
+    r, p = make(g, [cam], capacity=500)
+    r.forward(p)
+    torch.cuda.synchronize()
+    assert int(r.status.item()) & 1
+    full, _ = make(g, [cam])
+    full.project(p)
+    full.build_lists()
+    torch.cuda.synchronize()
+    assert r.instance_count() == full.instance_count() > 500
+    from paper_2412_01217_gb300 import SgError
+    with pytest.raises(SgError):
+        r.check_status()
+
+
+def test_adam_step_matches_numpy():
+    import ctypes as C
+    from paper_2412_01217_gb300._lib import call
+    rng = np.random.default_rng(0)
+    n = 10007
+    p0, g0 = rng.normal(size=n), rng.normal(size=n)
+    m0, v0 = rng.normal(size=n) * 0.1, rng.uniform(size=n) * 0.1
+    t = [torch.tensor(a, dtype=torch.float32, device="cuda") for a in (p0, g0, m0, v0)]
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    call("sg_adam_step", *[C.c_void_p(x.data_ptr()) for x in t], n, 1e-2, 0.9, 0.999, 1e-8, 3, s)
+    torch.cuda.synchronize()
+    m = 0.9 * m0 + 0.1 * g0
+    v = 0.999 * v0 + 0.001 * g0 ** 2
+    p = p0 - 1e-2 * (m / (1 - 0.9 ** 3)) / (np.sqrt(v / (1 - 0.999 ** 3)) + 1e-8)
+    assert np.allclose(t[0].cpu().numpy(), p, rtol=1e-5, atol=1e-6)
+    assert np.allclose(t[2].cpu().numpy(), m, rtol=1e-5, atol=1e-7)
