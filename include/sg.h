@@ -110,7 +110,9 @@ typedef struct {
 
 /* Projected records of all (view-level, Gaussian) pairs: record r = v*N + g. */
 typedef struct {
-    float *geo;     /* R x 8: u, v, depth, opacity, m00, m10, m11, 0 (16-B aligned), where
+    float *geo;     /* R x 8 (16-B aligned): u_frac, v_frac, depth, opacity, m00, m10, m11,
+                       (u_int | v_int << 16) as int16 bits; the 2D mean is
+                       (u_int + u_frac, v_int + v_frac) and
                        1/2 d^T Sigma2D^{-1} d = (m00 dx)^2 + (m10 dx + m11 dy)^2            */
     uint32_t *rect; /* R x 2: tile rectangle [tx0,tx1) x [ty0,ty1) as (tx0|ty0<<16, tx1|ty1<<16);
                        an empty rectangle means the record is culled                    */
@@ -213,8 +215,11 @@ sg_status sg_render_pyramid(const sg_gaussians *g, const sg_projected *proj,
                             int32_t n_tiles, const sg_config *cfg, sg_images *out,
                             sg_saved *saved, int32_t *work_counter, sg_stream_t stream);
 
-/* Scratch bytes sg_pyramid_loss needs for the view-levels in views_host (host table). */
-size_t sg_loss_workspace_size(const sg_view *views_host, int32_t n_views);
+/* Scratch bytes sg_pyramid_loss needs for the view-levels in views_host (host table), C
+ * semantic channels and n_classes decoder outputs (covers the decoder gradient's
+ * per-block partials). */
+size_t sg_loss_workspace_size(const sg_view *views_host, int32_t n_views, int32_t C,
+                              int32_t n_classes);
 
 /* Eq. 10-13 at every view-level: writes terms[4*v + {0,1,2,3}] = L_r, L_d, L_s, total of
  * view-level v (device floats) and the gradient of sum_v total_v with respect to the
@@ -256,10 +261,105 @@ sg_status sg_render_pyramid_backward(const sg_gaussians *g, const sg_projected *
 sg_status sg_build_pyramid(float *rgb, float *depth, int32_t *label, float *sem, int32_t n_sem_ch,
                            const sg_view *views_host, int32_t n_views, sg_stream_t stream);
 
+/* One parameter tensor for sg_adam_multi. */
+typedef struct {
+    float *param, *grad, *m, *v;
+    int64_t n;
+    float lr;
+} sg_adam_group;
+#define SG_ADAM_MAX_GROUPS 8
+
+/* Adam over up to SG_ADAM_MAX_GROUPS tensors in one launch (same update as sg_adam_step,
+ * per-group learning rate); with zero_grad != 0 every gradient is set to 0 after use. */
+sg_status sg_adam_multi(const sg_adam_group *groups, int32_t n_groups, float beta1, float beta2,
+                        float eps, int32_t step, int32_t zero_grad, sg_stream_t stream);
+
 /* Adam (the paper leaves the optimizer unspecified): for i < n
  * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr * mhat / (sqrt(vhat) + eps). */
 sg_status sg_adam_step(float *param, const float *grad, float *m, float *v, int64_t n, float lr,
                        float beta1, float beta2, float eps, int32_t step, sg_stream_t stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* Learned initializer (not in the paper; its only counterpart is Sec. III-A's insertion  */
+/* of new Gaussians from a keyframe): a 3-layer BF16 MLP with FP32 accumulation on the    */
+/* tcgen05 tensor cores, 2048 (2009 used) -> 128 -> ReLU -> 128 -> ReLU -> 32 (20 used).   */
+/* ---------------------------------------------------------------------------------- */
+
+#define SG_MLP_IN 2048
+#define SG_MLP_HIDDEN 128
+#define SG_MLP_OUT 32
+#define SG_STATUS_TIMEOUT 4u /* a bounded wait inside a tensor-core kernel gave up      */
+
+/* bf16 operands are passed as uint16_t bit patterns. */
+typedef struct {
+    const uint16_t *W1, *W2, *W3; /* bf16 [128][2048], [128][128], [32][128]  ([out][in])      */
+    const uint16_t *W2t, *W3t;    /* bf16 W2^T [128][128]; W3^T zero-padded to [128][64]      */
+    const float *b1, *b2, *b3;    /* [128], [128], [32]                                        */
+} sg_mlp;
+
+typedef struct {
+    uint16_t *H1, *H1t, *H2, *H2t; /* bf16 [B][128] and transposed [128][B]                  */
+    float *Y;                      /* fp32 [B][32]                                            */
+    uint16_t *dY, *dYt;            /* bf16 [B][64] (columns >= 32 written as 0), [32][B]      */
+    uint16_t *dH2, *dH2t, *dH1t;   /* bf16 [B][128], [128][B], [128][B]                       */
+} sg_mlp_acts;
+
+typedef struct {
+    float *W1, *W2, *W3, *b1, *b2, *b3; /* fp32, same shapes as the weights; ADDED into      */
+} sg_mlp_grads;
+
+/* D[M][N] (+)= A[M][K] B[N][K]^T on the tensor cores (A, B bf16 with K contiguous, rows
+ * 16-byte aligned, K % 64 == 0; D fp32 row-major with leading dimension ldd).  accumulate:
+ * 0 stores D, 1 atomically adds (the K range is then split over CTAs).  Timeouts of the
+ * kernel's bounded waits set SG_STATUS_TIMEOUT in *status (may be NULL). */
+sg_status sg_gemm_bf16(const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb, int32_t M,
+                       int32_t N, int32_t K, float *D, int64_t ldd, int32_t accumulate,
+                       uint32_t *status, sg_stream_t stream);
+
+/* fp32 master weights ([out][in]) -> the bf16 operand copies of sg_mlp.  W3t's padding
+ * columns 32..63 are not written: the caller zeroes W3t once. */
+sg_status sg_mlp_pack_weights(const float *W1, const float *W2, const float *W3, uint16_t *W1b,
+                              uint16_t *W2b, uint16_t *W3b, uint16_t *W2t, uint16_t *W3t,
+                              sg_stream_t stream);
+
+/* Y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 for B rows of X (bf16 [B][2048], B % 128 == 0).
+ * Writes acts->H1/H1t/H2/H2t (bf16, needed by the backward; H1t/H2t may be NULL for
+ * inference) and acts->Y (fp32). */
+sg_status sg_mlp_forward(const sg_mlp *net, const uint16_t *X, int32_t B, sg_mlp_acts *acts,
+                         uint32_t *status, sg_stream_t stream);
+
+/* Gradient of L = sum_o out_weight[o] * mean_b (Y[b][o] - target[b][o])^2 after
+ * sg_mlp_forward on the same batch.  Xt: bf16 [2048][B] (the transposed input).  ADDS the
+ * weight and bias gradients into grads and L into *loss (device float). */
+sg_status sg_mlp_backward(const sg_mlp *net, const uint16_t *Xt, const float *target,
+                          const float *out_weight, int32_t B, sg_mlp_acts *acts,
+                          sg_mlp_grads *grads, float *loss, uint32_t *status, sg_stream_t stream);
+
+/* Sec. III-A (the mapping thread converts keyframe data into Gaussian primitives): for B
+ * pixels (x, y) of a level-0 frame (planar rgb 3 x H x W, depth H x W, label H x W or NULL)
+ * with valid depth, writes B new Gaussians into out (device arrays with room for B; out->C
+ * is the semantic width): mean = back-projection, rgb = pixel colour, log-scale = ln(D/fx)
+ * on every axis, identity rotation, opacity logit 0, semantic feature =
+ * kappa * sem_code[label] (sem_code: n_classes x C, or NULL for zeros).  pixels: int32 (x, y)
+ * pairs. */
+sg_status sg_init_gaussians(const float *rgb, const float *depth, const int32_t *label,
+                            const sg_camera *cam, const int32_t *pixels, int32_t B,
+                            const float *sem_code, int32_t n_classes, float kappa,
+                            sg_gaussian_grads *out, sg_stream_t stream);
+
+/* Input features of the learned initializer: the 7 x 7 patch around each pixel, 41
+ * channels per patch pixel (rgb 3, depth 1, one-hot label 32, unit camera ray 3, depth
+ * valid 1, 1/fx 1) = 2009 features, zero-padded to SG_MLP_IN; pixels outside the image
+ * give zeros; rows b >= B of the B_pad (multiple of 128) output rows are zero.  X: bf16
+ * [B_pad][2048] and/or Xt: bf16 [2048][B_pad] (either may be NULL). */
+sg_status sg_extract_patches(const float *rgb, const float *depth, const int32_t *label,
+                             const sg_camera *cam, const int32_t *pixels, int32_t B, int32_t B_pad,
+                             uint16_t *X, uint16_t *Xt, sg_stream_t stream);
+
+/* Overwrites log-scale (3), opacity logit (1) and semantic feature (C) of B Gaussians in
+ * out with the MLP output Y ([B][32], standardised): value = Y * y_std + y_mean. */
+sg_status sg_apply_mlp_init(const float *Y, int32_t B, const float *y_mean, const float *y_std,
+                            sg_gaussian_grads *out, sg_stream_t stream);
 
 #ifdef __cplusplus
 }

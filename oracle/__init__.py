@@ -42,7 +42,7 @@ DEFAULT_CFG = dict(alpha_max=0.99, alpha_min=1.0 / 255.0, T_min=1e-4, z_near=0.2
 
 # projection record fields (must match the enum in sg_oracle.c)
 P = dict(VALID=0, U=1, V=2, DEPTH=3, OPAC=4, CA=5, CB=6, CC=7, S00=8, S01=9, S11=10,
-         TX=11, TY=12, TZ=13, CLX=14, CLY=15, EXTX=16, EXTY=17, LIMX=18, LIMY=19)
+         TX=11, TY=12, TZ=13, CLX=14, CLY=15, EXTX=16, EXTY=17, LIMX=18, LIMY=19, DKEY=20)
 FLAG_SKIP, FLAG_STOP, FLAG_DEPTH, FLAG_CLAMP = 1, 2, 4, 8
 
 

@@ -11,7 +11,7 @@
  *                       covariance projection that Sec. III-C defers to (3D Gaussian
  *                       splatting); reduces to Eq. 2 for isotropic Gaussians on the axis.
  *   oc_render           Eq. 7-9: per-pixel brute force over all Gaussians, sorted by
- *                       depth (float32-rounded depth, then ascending Gaussian id),
+ *                       depth (the float32 key of depth_key, then ascending Gaussian id),
  *                       front-to-back compositing of RGB, depth and C semantic channels.
  *   oc_render_backward  hand-derived adjoint of oc_render followed by the adjoint of
  *                       oc_project (Sec. III-D "perform backpropagation"), giving
@@ -50,7 +50,8 @@ enum {
     P_TX, P_TY, P_TZ,           /* camera-space mean */
     P_CLX, P_CLY,               /* Jacobian clamp active in x / y (0 or 1) */
     P_EXTX, P_EXTY,             /* half extents outside which alpha < alpha_min */
-    P_LIMX, P_LIMY              /* clamp limits of t_x/t_z and t_y/t_z */
+    P_LIMX, P_LIMY,             /* clamp limits of t_x/t_z and t_y/t_z */
+    P_DKEY                      /* depth ordering key (float32, see depth_key) */
 };
 
 /* Per-pixel ambiguity flags (reported, never used to change a result). */
@@ -122,6 +123,21 @@ static void jacobian(const cam_t *cam, const double t[3], double limx, double li
             T[3 * i + j] = J[3 * i] * W[j] + J[3 * i + 1] * W[3 + j] + J[3 * i + 2] * W[6 + j];
 }
 
+/* The sorted set N of Eq. 7-9 is ordered by depth.  The order is decided in float32 --
+ * the precision of the GPU kernels -- so both sides take the same decision: the key is
+ * t_z = ((R20 x + R21 y) + R22 z) + t_z0 evaluated with float32 inputs and a float32
+ * rounding after every operation, in exactly this order.  Ties break by Gaussian id.  The
+ * depth VALUE composited in Eq. 8 stays the double-precision t_z. */
+static float depth_key(const double *mean, const cam_t *cam) {
+    volatile float a = (float)cam->R[6] * (float)mean[0];
+    volatile float b = (float)cam->R[7] * (float)mean[1];
+    volatile float c = (float)cam->R[8] * (float)mean[2];
+    volatile float ab = a + b;
+    volatile float abc = ab + c;
+    volatile float key = abc + (float)cam->t[2];
+    return key;
+}
+
 /* Projection of one Gaussian (Eq. 2-3 via EWA).  Writes OC_PROJ_STRIDE values. */
 static void project_one(const double *mean, const double *log_scale, const double *quat,
                         double opacity_logit, const cam_t *cam, const cfg_t *cfg, double *out) {
@@ -131,6 +147,7 @@ static void project_one(const double *mean, const double *log_scale, const doubl
     for (int i = 0; i < 3; ++i)
         t[i] = W[3 * i] * mean[0] + W[3 * i + 1] * mean[1] + W[3 * i + 2] * mean[2] + cam->t[i];
     out[P_TX] = t[0]; out[P_TY] = t[1]; out[P_TZ] = t[2];
+    out[P_DKEY] = (double)depth_key(mean, cam);
     if (!(t[2] > cfg->z_near)) return;                    /* at or behind the near plane */
     double o = 1.0 / (1.0 + exp(-opacity_logit));
     out[P_OPAC] = o;
@@ -218,7 +235,7 @@ static int gather(double x, double y, int N, const double *proj, const cfg_t *cf
         /* keep the near-threshold ones too: the flags below need them */
         if (alpha < cfg->alpha_min * 0.5) continue;
         cand_t c;
-        c.dkey = (float)p[P_DEPTH]; c.id = i; c.raw = raw; c.alpha = alpha; c.G = G;
+        c.dkey = (float)p[P_DKEY]; c.id = i; c.raw = raw; c.alpha = alpha; c.G = G;
         c.dx = dx; c.dy = dy;
         buf[n++] = c;
     }

@@ -65,6 +65,23 @@ class SgLossConfig(C.Structure):
                 ("sem_mode", c_i), ("n_classes", c_i), ("decoder", c_p), ("decoder_grad", c_p)]
 
 
+class SgAdamGroup(C.Structure):
+    _fields_ = [("param", c_p), ("grad", c_p), ("m", c_p), ("v", c_p), ("n", C.c_int64), ("lr", c_f)]
+
+
+class SgMlp(C.Structure):
+    _fields_ = [("W1", c_p), ("W2", c_p), ("W3", c_p), ("W2t", c_p), ("W3t", c_p), ("b1", c_p), ("b2", c_p),
+                ("b3", c_p)]
+
+
+class SgMlpActs(C.Structure):
+    _fields_ = [(k, c_p) for k in ("H1", "H1t", "H2", "H2t", "Y", "dY", "dYt", "dH2", "dH2t", "dH1t")]
+
+
+class SgMlpGrads(C.Structure):
+    _fields_ = [(k, c_p) for k in ("W1", "W2", "W3", "b1", "b2", "b3")]
+
+
 STATUS = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CAPACITY", 3: "SG_ERR_TIMEOUT",
           4: "SG_ERR_NUMERIC", 5: "SG_ERR_CUDA"}
 STATUS_CAPACITY = 1
@@ -86,7 +103,7 @@ SIGNATURES = {
                                   c_p, C.c_size_t, c_p, c_p]),
     "sg_render_pyramid": (c_i, [P(SgGaussians), P(SgProjected), P(SgTileLists), c_p, c_i, c_i,
                                 P(SgConfig), P(SgImages), P(SgSaved), c_p, c_p]),
-    "sg_loss_workspace_size": (C.c_size_t, [P(SgView), c_i]),
+    "sg_loss_workspace_size": (C.c_size_t, [P(SgView), c_i, c_i, c_i]),
     "sg_pyramid_loss": (c_i, [P(SgImages), P(SgTargets), c_p, P(SgView), c_i, c_i,
                               P(SgLossConfig), c_p, P(SgImages), c_p, C.c_size_t, c_p]),
     "sg_backward_workspace_size": (C.c_size_t, [C.c_int64]),
@@ -95,6 +112,14 @@ SIGNATURES = {
                                          P(SgGaussianGrads), c_p, C.c_size_t, c_p, c_p]),
     "sg_build_pyramid": (c_i, [c_p, c_p, c_p, c_p, c_i, P(SgView), c_i, c_p]),
     "sg_adam_step": (c_i, [c_p, c_p, c_p, c_p, C.c_int64, c_f, c_f, c_f, c_f, c_i, c_p]),
+    "sg_adam_multi": (c_i, [P(SgAdamGroup), c_i, c_f, c_f, c_f, c_i, c_i, c_p]),
+    "sg_gemm_bf16": (c_i, [c_p, C.c_int64, c_p, C.c_int64, c_i, c_i, c_i, c_p, C.c_int64, c_i, c_p, c_p]),
+    "sg_mlp_pack_weights": (c_i, [c_p] * 8 + [c_p]),
+    "sg_mlp_forward": (c_i, [P(SgMlp), c_p, c_i, P(SgMlpActs), c_p, c_p]),
+    "sg_mlp_backward": (c_i, [P(SgMlp), c_p, c_p, c_p, c_i, P(SgMlpActs), P(SgMlpGrads), c_p, c_p, c_p]),
+    "sg_extract_patches": (c_i, [c_p, c_p, c_p, P(SgCamera), c_p, c_i, c_i, c_p, c_p, c_p]),
+    "sg_init_gaussians": (c_i, [c_p, c_p, c_p, P(SgCamera), c_p, c_i, c_p, c_i, c_f, P(SgGaussians), c_p]),
+    "sg_apply_mlp_init": (c_i, [c_p, c_i, c_p, c_p, P(SgGaussians), c_p]),
 }
 
 _lib = None

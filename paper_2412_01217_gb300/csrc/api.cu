@@ -37,12 +37,13 @@ sg_status launch_project_bwd(const sg_gaussians *, const sg_view *, int, const s
 size_t tile_lists_workspace_size(int64_t R, int32_t cap);
 sg_status launch_build_tile_lists(const sg_projected *, int, int, const sg_view *, int,
                                   sg_tile_lists *, void *, size_t, uint32_t *, cudaStream_t);
-size_t loss_workspace_size(const sg_view *vh, int n_views);
+size_t loss_workspace_size(const sg_view *vh, int n_views, int C, int n_classes);
 sg_status launch_loss(const sg_images *, const sg_targets *, const sg_view *, const sg_view *, int,
                       int, const sg_loss_config *, float *, sg_images *, void *, size_t, cudaStream_t);
 sg_status launch_pyramid(float *, float *, int *, float *, int, const sg_view *, int, cudaStream_t);
 sg_status launch_adam(float *, const float *, float *, float *, int64_t, float, float, float, float, int,
                       cudaStream_t);
+sg_status launch_adam_multi(const sg_adam_group *, int, float, float, float, int, int, cudaStream_t);
 
 }  // namespace sg
 
@@ -231,9 +232,10 @@ sg_status sg_render_pyramid(const sg_gaussians *g, const sg_projected *proj,
     return launch_raster(a, g->C, false, (cudaStream_t)stream);
 }
 
-size_t sg_loss_workspace_size(const sg_view *views_host, int32_t n_views) {
+size_t sg_loss_workspace_size(const sg_view *views_host, int32_t n_views, int32_t C,
+                              int32_t n_classes) {
     if (!views_host || n_views < 1 || n_views > SG_MAX_VIEWS) return 0;
-    return loss_workspace_size(views_host, n_views);
+    return loss_workspace_size(views_host, n_views, C, n_classes);
 }
 
 sg_status sg_pyramid_loss(const sg_images *rendered, const sg_targets *gt, const sg_view *views,
@@ -318,6 +320,19 @@ sg_status sg_adam_step(float *param, const float *grad, float *m, float *v, int6
     SG_REQUIRE(param && grad && m && v, "NULL argument");
     SG_REQUIRE(step >= 1, "step must be >= 1");
     return launch_adam(param, grad, m, v, n, lr, beta1, beta2, eps, step, (cudaStream_t)stream);
+}
+
+sg_status sg_adam_multi(const sg_adam_group *groups, int32_t n_groups, float beta1, float beta2, float eps,
+                        int32_t step, int32_t zero_grad, sg_stream_t stream) {
+    SG_REQUIRE(groups && n_groups >= 1 && n_groups <= SG_ADAM_MAX_GROUPS, "n_groups must be in [1, %d]",
+               SG_ADAM_MAX_GROUPS);
+    SG_REQUIRE(step >= 1, "step must be >= 1");
+    for (int k = 0; k < n_groups; ++k) {
+        SG_REQUIRE(groups[k].n >= 0, "group %d: n < 0", k);
+        SG_REQUIRE(groups[k].n == 0 || (groups[k].param && groups[k].grad && groups[k].m && groups[k].v),
+                   "group %d: NULL pointer", k);
+    }
+    return launch_adam_multi(groups, n_groups, beta1, beta2, eps, step, zero_grad, (cudaStream_t)stream);
 }
 
 }  // extern "C"

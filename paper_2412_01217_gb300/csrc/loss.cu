@@ -231,7 +231,30 @@ struct PixelArgs {
     const sg_view *views;
     LossViews lv;
     float *partials;        // per CTA: (sum |D - D_gt| over valid, sum CE over valid)
+    float *dec_partials;    // per CTA: K x C share of the decoder gradient
 };
+
+// Two-level, fixed-order reduction of the per-CTA decoder-gradient shares:
+// level 1: chunk c of kDecChunks sums CTAs [c n / kDecChunks, (c+1) n / kDecChunks);
+// level 2: decoder_grad[o] += sum over chunks.
+constexpr int kDecChunks = 128;
+__global__ void decoder_reduce1_kernel(const float *__restrict__ part, int n_blocks, int KC,
+                                       float *__restrict__ chunk_sums) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (o >= KC) return;
+    const int b0 = (int)((long long)c * n_blocks / kDecChunks), b1 = (int)((long long)(c + 1) * n_blocks / kDecChunks);
+    float s = 0.f;
+    for (int b = b0; b < b1; ++b) s += part[(size_t)b * KC + o];
+    chunk_sums[(size_t)c * KC + o] = s;
+}
+__global__ void decoder_reduce2_kernel(const float *__restrict__ chunk_sums, int KC, float *__restrict__ out) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= KC) return;
+    float s = 0.f;
+    for (int c = 0; c < kDecChunks; ++c) s += chunk_sums[(size_t)c * KC + o];
+    out[o] += s;
+}
 
 template <int C, int K>
 __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
@@ -316,7 +339,7 @@ __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
                 const int k = o / C, c = o % C;
                 float s = 0.f;
                 for (int t = 0; t < kLossThreads; ++t) s = fmaf(s_dz[t * K + k], s_S[t * C + c], s);
-                if (s != 0.f) atomicAdd(a.decoder_grad + o, s);
+                a.dec_partials[(size_t)blk * K * C + o] = s;  // reduced later in block order
             }
         }
     }
@@ -409,16 +432,18 @@ static void make_loss_views(const sg_view *vh, int n_views, LossViews &lv) {
     }
 }
 
-static size_t loss_ws_bytes(int n_views, int n_tiles, int n_blocks) {
+static size_t loss_ws_bytes(int n_views, int n_tiles, int n_blocks, int KC) {
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     return al(sizeof(int) * 2 * n_views) + 2 * al(sizeof(float) * 2 * n_tiles) +
-           al(sizeof(float) * 2 * n_blocks);
+           al(sizeof(float) * 2 * n_blocks) + al(sizeof(float) * (size_t)n_blocks * KC) +
+           al(sizeof(float) * (size_t)kDecChunks * KC);
 }
 
-size_t loss_workspace_size(const sg_view *vh, int n_views) {
+size_t loss_workspace_size(const sg_view *vh, int n_views, int C, int n_classes) {
     LossViews lv;
     make_loss_views(vh, n_views, lv);
-    return loss_ws_bytes(n_views, lv.tile_off[n_views], lv.pix_blk_off[n_views]);
+    const int K = n_classes > C ? n_classes : C;
+    return loss_ws_bytes(n_views, lv.tile_off[n_views], lv.pix_blk_off[n_views], K * C);
 }
 
 template <int C, int K>
@@ -454,13 +479,16 @@ sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *v
     float *p_rgb = (float *)take(sizeof(float) * 2 * n_tiles);
     float *p_sem = (float *)take(sizeof(float) * 2 * n_tiles);
     float *p_pix = (float *)take(sizeof(float) * 2 * n_blocks);
-    if (loss_ws_bytes(n_views, n_tiles, n_blocks) > ws_bytes) {
-        set_error("pyramid_loss: workspace %zu bytes < %zu needed", ws_bytes,
-                  loss_ws_bytes(n_views, n_tiles, n_blocks));
-        return SG_ERR_CAPACITY;
-    }
     const int ce = lc->sem_mode == 0;
     const int K = ce ? lc->n_classes : C;
+    const int KC = lc->decoder_grad ? K * C : 0;
+    float *p_dec = (float *)take(sizeof(float) * (size_t)n_blocks * KC);
+    float *p_dec2 = (float *)take(sizeof(float) * (size_t)kDecChunks * KC);
+    if (loss_ws_bytes(n_views, n_tiles, n_blocks, KC) > ws_bytes) {
+        set_error("pyramid_loss: workspace %zu bytes < %zu needed", ws_bytes,
+                  loss_ws_bytes(n_views, n_tiles, n_blocks, KC));
+        return SG_ERR_CAPACITY;
+    }
     cudaMemsetAsync(counts, 0, sizeof(int) * 2 * n_views, st);
     loss_count_kernel<<<n_blocks, kLossThreads, 0, st>>>(gt->depth, ce ? gt->label : nullptr, views, lv, counts);
     static bool attr = false;
@@ -476,10 +504,15 @@ sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *v
         ssim_l1_kernel<<<n_tiles, kLossThreads, ssim_smem(), st>>>(ss);
     }
     PixelArgs pa{r->depth, gt->depth, r->sem, gt->label, dL->depth, dL->sem, lc->decoder,
-                 lc->decoder_grad, C, K, ce, lc->w_depth, lc->w_sem, counts, views, lv, p_pix};
+                 lc->decoder_grad, C, K, ce, lc->w_depth, lc->w_sem, counts, views, lv, p_pix, p_dec};
     if (!launch_pixel(pa, n_blocks, st)) {
         set_error("pyramid_loss: unsupported (C=%d, classes=%d)", C, K);
         return SG_ERR_INVALID_ARG;
+    }
+    if (ce && lc->decoder_grad) {
+        decoder_reduce1_kernel<<<dim3((KC + 127) / 128, kDecChunks), 128, 0, st>>>(p_dec, n_blocks, KC, p_dec2);
+        decoder_reduce2_kernel<<<(KC + 127) / 128, 128, 0, st>>>(p_dec2, KC, lc->decoder_grad);
+        count_launches(2);
     }
     FinalArgs fa{p_rgb, ce ? nullptr : p_sem, p_pix, counts, views, lv, C, lc->sem_mode,
                  lc->lambda_r, lc->lambda_s, lc->w_depth, lc->w_sem, terms};
@@ -566,6 +599,55 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
         v[i] = vi;
         p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
     }
+}
+
+// All parameter groups in one launch; the gradient is zeroed after it is read, ready for
+// the next iteration's accumulation.
+struct AdamGroups {
+    sg_adam_group g[SG_ADAM_MAX_GROUPS];
+    int64_t start[SG_ADAM_MAX_GROUPS + 1];  // prefix of element counts
+    int n;
+};
+
+__global__ void adam_multi_kernel(AdamGroups G, float b1, float b2, float eps, float bc1, float bc2,
+                                  int zero_grad) {
+    const int64_t total = G.start[G.n];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (k + 1 < G.n && i >= G.start[k + 1]) ++k;
+        const sg_adam_group &q = G.g[k];
+        const int64_t j = i - G.start[k];
+        const float gi = q.grad[j];
+        const float mi = b1 * q.m[j] + (1.f - b1) * gi;
+        const float vi = b2 * q.v[j] + (1.f - b2) * gi * gi;
+        q.m[j] = mi;
+        q.v[j] = vi;
+        q.param[j] -= q.lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        if (zero_grad) q.grad[j] = 0.f;
+    }
+}
+
+sg_status launch_adam_multi(const sg_adam_group *groups, int n, float b1, float b2, float eps, int step,
+                            int zero_grad, cudaStream_t st) {
+    AdamGroups G{};
+    G.n = n;
+    G.start[0] = 0;
+    for (int k = 0; k < n; ++k) {
+        G.g[k] = groups[k];
+        G.start[k + 1] = G.start[k] + groups[k].n;
+    }
+    const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (G.start[n] + 255) / 256;
+    if (blocks > 8 * (int64_t)sms) blocks = 8 * (int64_t)sms;
+    if (blocks > 0) {
+        adam_multi_kernel<<<(int)blocks, 256, 0, st>>>(G, b1, b2, eps, bc1, bc2, zero_grad);
+        count_launches(1);
+    }
+    return check_launch("adam_multi");
 }
 
 sg_status launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1,

@@ -67,8 +67,13 @@ struct ViewGeom {
 
 __device__ __forceinline__ void view_geom(const sg_view &vw, const float mu[3], float fov_clamp,
                                           ViewGeom &q) {
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 2; ++i)
         q.t[i] = vw.R[3 * i] * mu[0] + vw.R[3 * i + 1] * mu[1] + vw.R[3 * i + 2] * mu[2] + vw.t[i];
+    // camera z is also the depth ordering key of the tile lists: a fixed float32 evaluation
+    // order, ((R20 x + R21 y) + R22 z) + t_z, rounded after every operation
+    q.t[2] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(vw.R[6], mu[0]), __fmul_rn(vw.R[7], mu[1])),
+                                 __fmul_rn(vw.R[8], mu[2])),
+                       vw.t[2]);
     const float tz = q.t[2];
     const float limx = fov_clamp * 0.5f * (float)vw.W / vw.fx;
     const float limy = fov_clamp * 0.5f * (float)vw.H / vw.fy;
@@ -139,30 +144,48 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
         uint2 rc = make_uint2(0u, 0u);
         const float tz = q.t[2];
         if (tz > pc.z_near && o >= pc.alpha_min) {
-            const float u = vw.fx * q.t[0] / tz + vw.cx;
-            const float vv = vw.fy * q.t[1] / tz + vw.cy;
+            // the 2D mean in double-float: t = R mu + t_cw and (fx t_x / t_z + cx, ...)
+            // carry ~1e-4 px of float32 error at 1200 px otherwise
+            DF tdf[3];
+            for (int i = 0; i < 3; ++i) {
+                DF acc = two_prod(vw.R[3 * i], mu[0]);
+                acc = df_add(acc, two_prod(vw.R[3 * i + 1], mu[1]));
+                acc = df_add(acc, two_prod(vw.R[3 * i + 2], mu[2]));
+                tdf[i] = df_add_f(acc, vw.t[i]);
+            }
+            const DF udf = df_add_f(df_mul_f(df_div(tdf[0], tdf[2]), vw.fx), vw.cx);
+            const DF vdf = df_add_f(df_mul_f(df_div(tdf[1], tdf[2]), vw.fy), vw.cy);
+            const float u = udf.hi, vv = vdf.hi;
             float s00, s01, s11, det;
             cov2d(q, f, pc.dilation, s00, s01, s11, det);
             if (det > 0.f && s00 > 0.f) {
                 // alpha >= alpha_min needs sigma <= ln(o/alpha_min); the smallest sigma at a
                 // horizontal offset dx is dx^2/(2 s00): half extents (with float32 slack)
-                const float thr = logf(o / pc.alpha_min);
+                // (thr + 1e-3: at the boundary alpha is at least 0.1% below alpha_min, far
+                // beyond float32 rounding, so no pixel outside can pass the alpha test)
+                const float thr = logf(o / pc.alpha_min) + 1e-3f;
                 const float ex = sqrtf(2.f * thr * s00) * 1.002f + 0.01f;
                 const float ey = sqrtf(2.f * thr * s11) * 1.002f + 0.01f;
                 const float xmin = fmaxf(ceilf(u - ex), 0.f);
                 const float xmax = fminf(floorf(u + ex), (float)(vw.W - 1));
                 const float ymin = fmaxf(ceilf(vv - ey), 0.f);
                 const float ymax = fminf(floorf(vv + ey), (float)(vw.H - 1));
-                if (xmin <= xmax && ymin <= ymax) {
+                if (xmin <= xmax && ymin <= ymax && fabsf(u) < 32000.f && fabsf(vv) < 32000.f) {
                     const int tx0 = (int)xmin / pc.tile_w, tx1 = (int)xmax / pc.tile_w + 1;
                     const int ty0 = (int)ymin / pc.tile_h, ty1 = (int)ymax / pc.tile_h + 1;
                     rc = make_uint2(pack16(tx0, ty0), pack16(tx1, ty1));
-                    g0 = make_float4(u, vv, tz, o);
+                    // 2D mean = integer part + float fraction, so that the compositing kernels
+                    // can form tile-relative offsets without losing bits
+                    const float ui = rintf(u), vi = rintf(vv);
+                    const float uf = __fadd_rn(__fsub_rn(udf.hi, ui), udf.lo);
+                    const float vf = __fadd_rn(__fsub_rn(vdf.hi, vi), vdf.lo);
+                    g0 = make_float4(uf, vf, tz, o);
                     // conditional form of 1/2 d^T Sigma2D^{-1} d (see eval_alpha)
                     const float m00 = rsqrtf(2.f * s00);
                     const float m11 = sqrtf(s00 / (2.f * det));
                     const float m10 = -s01 / sqrtf(2.f * s00 * det);
-                    g1 = make_float4(m00, m10, m11, 0.f);
+                    const uint32_t packed = ((uint32_t)(int)ui & 0xffffu) | (((uint32_t)(int)vi & 0xffffu) << 16);
+                    g1 = make_float4(m00, m10, m11, __uint_as_float(packed));
                 }
             }
         }

@@ -27,16 +27,34 @@ namespace sg {
 
 
 
+// Stages entries [b0, b0 + cnt) of a tile's list.  Per entry:
+//   s_geo0 = (ui - px0, vi - py0, uf, vf): integer part of the 2D mean relative to the tile
+//            origin (exact in float) and its float fraction,
+//   s_geo1 = (m00, m10, m11, opacity),
+//   s_geo2 = (u, v, ex, ey): approximate tile-relative mean and conservative half extents of
+//            the alpha >= alpha_min region, used only by the warp-level skip test,
+// and the 4 + C features.
 template <int NF>
 __device__ __forceinline__ void load_batch(const RasterArgs &a, int C, int list_start, int b0,
-                                           int cnt, float4 *s_geo0, float2 *s_geo1, float *s_feat,
+                                           int cnt, int px0, int py0, float4 *s_geo0,
+                                           float4 *s_geo1, float4 *s_geo2, float *s_feat,
                                            uint32_t *s_rec, int nthreads) {
     for (int j = threadIdx.x; j < cnt; j += nthreads) {
         const uint32_t rec = a.record[list_start + b0 + j];
         const float4 g0 = a.geo[2 * (size_t)rec];
         const float4 g1 = a.geo[2 * (size_t)rec + 1];
-        s_geo0[j] = make_float4(g0.x, g0.y, g1.x, g1.y);  // u, v, m00, m10
-        s_geo1[j] = make_float2(g1.z, g0.w);              // m11, opacity
+        const uint32_t packed = __float_as_uint(g1.w);
+        const float uI = (float)((int)(short)(packed & 0xffffu) - px0);
+        const float vI = (float)((int)(short)(packed >> 16) - py0);
+        // sigma > thr outside |dx| > sqrt(thr)/m00 and |dy| > sqrt(thr (1 + (m10/m00)^2))/m11;
+        // thr + 1e-3 and the 1% / 0.05 px margins keep the test strictly conservative
+        const float thr = logf(g0.w / a.alpha_min) + 1e-3f;
+        const float r = g1.y / g1.x;
+        const float ex = sqrtf(thr) / g1.x * 1.01f + 0.05f;
+        const float ey = sqrtf(thr * (1.f + r * r)) / g1.z * 1.01f + 0.05f;
+        s_geo0[j] = make_float4(uI, vI, g0.x, g0.y);
+        s_geo1[j] = make_float4(g1.x, g1.y, g1.z, g0.w);
+        s_geo2[j] = make_float4(uI + g0.x, vI + g0.y, ex, ey);
         const uint32_t gi = rec % (uint32_t)a.N;
         float *f = s_feat + (size_t)j * NF;
         f[0] = a.rgb[3 * (size_t)gi];
@@ -58,6 +76,26 @@ __device__ __forceinline__ int next_item(const RasterArgs &a, int &s_item) {
     return s_item;
 }
 
+// Thread -> pixel map: each warp owns an 8 x 4 sub-tile, so that a Gaussian's footprint
+// touches few warps and whole warps can skip it with one uniform test.
+struct WarpTile {
+    int lx, ly;        // pixel relative to the tile origin
+    float cxw, cyw;    // centre of the warp's 8 x 4 sub-tile
+    __device__ WarpTile(int tile_w) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int warps_x = tile_w >> 3;
+        const int wx = (warp % warps_x) * 8, wy = (warp / warps_x) * 4;
+        lx = wx + (lane & 7);
+        ly = wy + (lane >> 3);
+        cxw = wx + 3.5f;
+        cyw = wy + 1.5f;
+    }
+    // true if no pixel of the warp's sub-tile can reach alpha_min (g2 = u, v, ex, ey)
+    __device__ __forceinline__ bool misses(const float4 &g2) const {
+        return fabsf(g2.x - cxw) > g2.z + 3.5f || fabsf(g2.y - cyw) > g2.w + 1.5f;
+    }
+};
+
 template <int C>
 __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs a) {
     constexpr int NF = 4 + C;
@@ -65,10 +103,12 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
     __shared__ int s_item;
     const int batch = a.batch;
     float4 *s_geo0 = reinterpret_cast<float4 *>(smem_raw);
-    float2 *s_geo1 = reinterpret_cast<float2 *>(s_geo0 + batch);
-    float *s_feat = reinterpret_cast<float *>(s_geo1 + batch);
+    float4 *s_geo1 = s_geo0 + batch;
+    float4 *s_geo2 = s_geo1 + batch;
+    float *s_feat = reinterpret_cast<float *>(s_geo2 + batch);
     const int nthreads = a.tile_w * a.tile_h;
-    const int lx = threadIdx.x % a.tile_w, ly = threadIdx.x / a.tile_w;
+    const WarpTile wt(a.tile_w);
+    const float fx = (float)wt.lx, fy = (float)wt.ly;
     for (int iter = 0;; ++iter) {
         if (!a.persistent && iter > 0) break;
         const int item = next_item(a, s_item);
@@ -76,10 +116,9 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
         const int v = find_view(a.views, a.n_views, item);
         const sg_view &vw = a.views[v];
         const int local = item - vw.tile_offset;
-        const int tx = local % vw.tiles_x, ty = local / vw.tiles_x;
-        const int px = tx * a.tile_w + lx, py = ty * a.tile_h + ly;
+        const int px0 = (local % vw.tiles_x) * a.tile_w, py0 = (local / vw.tiles_x) * a.tile_h;
+        const int px = px0 + wt.lx, py = py0 + wt.ly;
         const bool inside = px < vw.W && py < vw.H;
-        const float fx = (float)px, fy = (float)py;
         const int2 range = a.ranges[item];
         const int n = range.y - range.x;
         float acc[NF];
@@ -91,35 +130,37 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
         for (int b0 = 0; b0 < n; b0 += batch) {
             if (__syncthreads_count(done) == nthreads) break;
             const int cnt = min(batch, n - b0);
-            load_batch<NF>(a, C, range.x, b0, cnt, s_geo0, s_geo1, s_feat, nullptr, nthreads);
+            load_batch<NF>(a, C, range.x, b0, cnt, px0, py0, s_geo0, s_geo1, s_geo2, s_feat, nullptr,
+                           nthreads);
             __syncthreads();
-            if (!done) {
-                for (int j = 0; j < cnt; ++j) {
-                    const float4 g0 = s_geo0[j];
-                    const float2 g1 = s_geo1[j];
-                    AlphaEval e;
-                    if (!eval_alpha(fx, fy, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, a.alpha_max,
-                                    a.alpha_min, e))
-                        continue;
-                    const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
-                    if (Tn < a.T_min) {
-                        done = true;
-                        break;
-                    }
-                    const float w = e.alpha * T;
-                    const float4 *f4 = reinterpret_cast<const float4 *>(s_feat + (size_t)j * NF);
-#pragma unroll
-                    for (int k = 0; k < NF / 4; ++k) {
-                        const float4 f = f4[k];
-                        acc[4 * k + 0] = fmaf(w, f.x, acc[4 * k + 0]);
-                        acc[4 * k + 1] = fmaf(w, f.y, acc[4 * k + 1]);
-                        acc[4 * k + 2] = fmaf(w, f.z, acc[4 * k + 2]);
-                        acc[4 * k + 3] = fmaf(w, f.w, acc[4 * k + 3]);
-                    }
-                    T = Tn;
-                    last = b0 + j + 1;
-                    ++nc;
+            if (__all_sync(SG_FULL_MASK, done)) continue;
+            for (int j = 0; j < cnt; ++j) {
+                if (wt.misses(s_geo2[j])) continue;  // warp-uniform
+                if (done) continue;
+                const float4 g0 = s_geo0[j];
+                const float4 g1 = s_geo1[j];
+                AlphaEval e;
+                if (!eval_alpha(fx - g0.x, fy - g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, a.alpha_max,
+                                a.alpha_min, e))
+                    continue;
+                const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
+                if (Tn < a.T_min) {
+                    done = true;
+                    continue;
                 }
+                const float w = e.alpha * T;
+                const float4 *f4 = reinterpret_cast<const float4 *>(s_feat + (size_t)j * NF);
+#pragma unroll
+                for (int k = 0; k < NF / 4; ++k) {
+                    const float4 f = f4[k];
+                    acc[4 * k + 0] = fmaf(w, f.x, acc[4 * k + 0]);
+                    acc[4 * k + 1] = fmaf(w, f.y, acc[4 * k + 1]);
+                    acc[4 * k + 2] = fmaf(w, f.z, acc[4 * k + 2]);
+                    acc[4 * k + 3] = fmaf(w, f.w, acc[4 * k + 3]);
+                }
+                T = Tn;
+                last = b0 + j + 1;
+                ++nc;
             }
         }
         if (inside) {
@@ -155,12 +196,14 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
     __shared__ int s_item, s_max_last;
     const int batch = a.batch;
     float4 *s_geo0 = reinterpret_cast<float4 *>(smem_raw);
-    float2 *s_geo1 = reinterpret_cast<float2 *>(s_geo0 + batch);
-    float *s_feat = reinterpret_cast<float *>(s_geo1 + batch);
+    float4 *s_geo1 = s_geo0 + batch;
+    float4 *s_geo2 = s_geo1 + batch;
+    float *s_feat = reinterpret_cast<float *>(s_geo2 + batch);
     uint32_t *s_rec = reinterpret_cast<uint32_t *>(s_feat + (size_t)batch * NF);
     const int nthreads = a.tile_w * a.tile_h;
     const int lane = threadIdx.x & 31;
-    const int lx = threadIdx.x % a.tile_w, ly = threadIdx.x / a.tile_w;
+    const WarpTile wt(a.tile_w);
+    const float fx = (float)wt.lx, fy = (float)wt.ly;
     for (int iter = 0;; ++iter) {
         if (!a.persistent && iter > 0) break;
         const int item = next_item(a, s_item);
@@ -168,10 +211,9 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
         const int v = find_view(a.views, a.n_views, item);
         const sg_view &vw = a.views[v];
         const int local = item - vw.tile_offset;
-        const int tx = local % vw.tiles_x, ty = local / vw.tiles_x;
-        const int px = tx * a.tile_w + lx, py = ty * a.tile_h + ly;
+        const int px0 = (local % vw.tiles_x) * a.tile_w, py0 = (local / vw.tiles_x) * a.tile_h;
+        const int px = px0 + wt.lx, py = py0 + wt.ly;
         const bool inside = px < vw.W && py < vw.H;
-        const float fx = (float)px, fy = (float)py;
         const int2 range = a.ranges[item];
         const size_t HW = (size_t)vw.W * vw.H;
         const size_t p = (size_t)py * vw.W + px;
@@ -193,9 +235,10 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
 #pragma unroll
             for (int k = 0; k < NF; ++k) g[k] = 0.f;
         }
+        const int warp_last = __reduce_max_sync(SG_FULL_MASK, my_last);
         if (threadIdx.x == 0) s_max_last = 0;
         __syncthreads();
-        if (my_last > 0) atomicMax(&s_max_last, my_last);
+        if (lane == 0 && warp_last > 0) atomicMax(&s_max_last, warp_last);
         __syncthreads();
         const int max_last = s_max_last;
         const int n_batches = (max_last + batch - 1) / batch;
@@ -203,16 +246,19 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
             const int b0 = b * batch;
             const int cnt = min(batch, max_last - b0);
             __syncthreads();
-            load_batch<NF>(a, C, range.x, b0, cnt, s_geo0, s_geo1, s_feat, s_rec, nthreads);
+            load_batch<NF>(a, C, range.x, b0, cnt, px0, py0, s_geo0, s_geo1, s_geo2, s_feat, s_rec,
+                           nthreads);
             __syncthreads();
-            for (int j = cnt - 1; j >= 0; --j) {
-                const int pos = b0 + j;
+            const int jmax = min(cnt, warp_last - b0);  // warp-uniform
+            for (int j = jmax - 1; j >= 0; --j) {
+                if (wt.misses(s_geo2[j])) continue;  // warp-uniform
                 const float4 g0 = s_geo0[j];
-                const float2 g1 = s_geo1[j];
+                const float4 g1 = s_geo1[j];
+                const int pos = b0 + j;
                 AlphaEval e;
                 const bool contributed =
-                    pos < my_last && eval_alpha(fx, fy, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y,
-                                                a.alpha_max, a.alpha_min, e);
+                    pos < my_last && eval_alpha(fx - g0.x, fy - g0.y, g0.z, g0.w, g1.x, g1.y, g1.z,
+                                                g1.w, a.alpha_max, a.alpha_min, e);
                 if (!__any_sync(SG_FULL_MASK, contributed)) continue;
                 float vals[NV];
 #pragma unroll
@@ -242,8 +288,8 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
                         // sigma = p1^2 + p2^2, p1 = m00 dx, p2 = m10 dx + m11 dy; d(dx)/du = -1.
                         // Conic gradients: d sigma / d(a, b, c) = (dx^2/2, dx dy, dy^2/2).
                         const float gsig = -dalpha * e.raw;
-                        vals[0] = -2.f * gsig * (e.p1 * g0.z + e.p2 * g0.w);
-                        vals[1] = -2.f * gsig * (e.p2 * g1.x);
+                        vals[0] = -2.f * gsig * (e.p1 * g1.x + e.p2 * g1.y);
+                        vals[1] = -2.f * gsig * (e.p2 * g1.z);
                         vals[2] = 0.5f * gsig * e.dx * e.dx;
                         vals[3] = gsig * e.dx * e.dy;
                         vals[4] = 0.5f * gsig * e.dy * e.dy;
@@ -273,7 +319,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
 
 template <int C>
 static size_t fwd_smem(int batch) {
-    return (size_t)batch * (16 + 8 + 4 * (4 + C));
+    return (size_t)batch * (3 * 16 + 4 * (4 + C));
 }
 template <int C>
 static size_t bwd_smem(int batch) {

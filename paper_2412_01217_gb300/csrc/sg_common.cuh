@@ -35,11 +35,13 @@ struct AlphaEval {
     float alpha;   // min(alpha_max, raw)
 };
 
-__device__ __forceinline__ bool eval_alpha(float px, float py, float u, float v, float m00, float m10,
-                                           float m11, float o, float alpha_max, float alpha_min,
-                                           AlphaEval &e) {
-    e.dx = __fsub_rn(px, u);
-    e.dy = __fsub_rn(py, v);
+// (px - ui) and (py - vi) are exact integers held in floats, (uf, vf) the float fractions of
+// the 2D mean: dx = (px - ui) - uf is the correctly rounded offset, whatever the tile.
+__device__ __forceinline__ bool eval_alpha(float px_ui, float py_vi, float uf, float vf, float m00,
+                                           float m10, float m11, float o, float alpha_max,
+                                           float alpha_min, AlphaEval &e) {
+    e.dx = __fsub_rn(px_ui, uf);
+    e.dy = __fsub_rn(py_vi, vf);
     e.p1 = __fmul_rn(m00, e.dx);
     e.p2 = __fmaf_rn(m10, e.dx, __fmul_rn(m11, e.dy));
     const float sigma = __fmaf_rn(e.p2, e.p2, __fmul_rn(e.p1, e.p1));
@@ -48,6 +50,48 @@ __device__ __forceinline__ bool eval_alpha(float px, float py, float u, float v,
     e.raw = __fmul_rn(o, e.G);
     e.alpha = fminf(alpha_max, e.raw);
     return e.alpha >= alpha_min;
+}
+
+// ---- double-float (unevaluated sum hi + lo of two floats) helpers --------------------
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_add_f(DF a, float b) {
+    DF s = two_sum(a.hi, b);
+    s.lo = __fadd_rn(s.lo, a.lo);
+    return two_sum(s.hi, s.lo);
+}
+// (a.hi + a.lo) * f, f a float
+__device__ __forceinline__ DF df_mul_f(DF a, float f) {
+    DF p = two_prod(a.hi, f);
+    p.lo = __fmaf_rn(a.lo, f, p.lo);
+    return two_sum(p.hi, p.lo);
+}
+// a / b for double-floats (one Newton-style correction of the float quotient)
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float q0 = __fdiv_rn(a.hi, b.hi);
+    const DF p = two_prod(q0, b.hi);
+    float r = __fsub_rn(a.hi, p.hi);
+    r = __fsub_rn(r, p.lo);
+    r = __fadd_rn(r, a.lo);
+    r = __fmaf_rn(-q0, b.lo, r);
+    const float q1 = __fdiv_rn(r, b.hi);
+    return two_sum(q0, q1);
 }
 
 // a*b - c*d with one rounding error (Kahan's algorithm with FMA).

@@ -144,6 +144,7 @@ class PyramidRasterizer:
         self.views_host, self.P, self.n_tiles = make_views(cams, levels, self.cfg.tile_w, self.cfg.tile_h)
         self.V = self.n_cams * self.levels
         self.views = views_to_device(self.views_host, self.device)
+        self.N_max = self.N
         self.R = self.N * self.V
         dev = self.device
         f32 = dict(dtype=torch.float32, device=dev)
@@ -172,13 +173,22 @@ class PyramidRasterizer:
         self.dL_depth = torch.zeros(P, **f32)
         self.dL_sem = torch.zeros(self.C * P, **f32)
         self.terms = torch.zeros(4 * self.V, **f32)
-        self.loss_ws = torch.zeros(lib.sg_loss_workspace_size(self.views_host, self.V), dtype=torch.uint8, device=dev)
+        self.loss_ws = torch.zeros(lib.sg_loss_workspace_size(self.views_host, self.V, self.C,
+                                                              max(self.C, self.loss_cfg.n_classes)),
+                                   dtype=torch.uint8, device=dev)
         self.bwd_ws = torch.zeros(lib.sg_backward_workspace_size(max(1, self.R)), dtype=torch.uint8, device=dev)
         self._ccfg = self.cfg.to_c()
         self._proj = SgProjected(self.geo.data_ptr(), self.rect.data_ptr())
         self._lists = SgTileLists(self.capacity, self.tile.data_ptr(), self.record.data_ptr(),
                                   self.ranges.data_ptr(), self.count.data_ptr())
         self._saved = SgSaved(self.T_final.data_ptr(), self.last.data_ptr(), self.n_contrib.data_ptr())
+
+    def set_count(self, N):
+        """Use the first N <= capacity Gaussians (buffers keep their maximum size)."""
+        if N > self.N_max:
+            raise ValueError(f"N = {N} exceeds the rasterizer's capacity {self.N_max}")
+        self.N = int(N)
+        self.R = self.N * self.V
 
     # ---- view table ------------------------------------------------------------------
     def set_cameras(self, cams):
@@ -227,7 +237,11 @@ class PyramidRasterizer:
     def loss(self, gt, rendered=None, decoder=None, decoder_grad=None, loss_cfg=None):
         """Eq. 10-13 for every view-level; gt: dict(rgb, depth, label[, sem]) packed like the
         images.  Fills self.terms (V x 4: L_r, L_d, L_s, total) and self.dL_*."""
-        lc = (loss_cfg or self.loss_cfg).to_c(decoder, decoder_grad)
+        lcfg = loss_cfg or self.loss_cfg
+        lc = lcfg.to_c(decoder, decoder_grad)
+        need = _lib.load().sg_loss_workspace_size(self.views_host, self.V, self.C, max(self.C, lcfg.n_classes))
+        if need > self.loss_ws.numel():
+            self.loss_ws = torch.zeros(need, dtype=torch.uint8, device=self.device)
         r = rendered or (self.img_rgb, self.img_depth, self.img_sem)
         ri = SgImages(r[0].data_ptr(), r[1].data_ptr(), r[2].data_ptr())
         ti = SgTargets(gt["rgb"].data_ptr(), gt["depth"].data_ptr(),
@@ -348,19 +362,23 @@ class MappingStep:
         self.t = 0
         self.graph = None
 
+    def _adam_groups(self):
+        from ._lib import SgAdamGroup
+        groups = [SgAdamGroup(self.p[k].data_ptr(), self.grads[k].data_ptr(), self.m[k].data_ptr(),
+                              self.v[k].data_ptr(), self.p[k].numel(), self.lr[k]) for k in PARAM_KEYS]
+        return (SgAdamGroup * len(groups))(*groups), len(groups)
+
     def _step_kernels(self, t):
+        """One iteration.  Gradients are zero on entry (allocated zeroed; the fused Adam
+        zeroes each one after reading it)."""
         r = self.rast
-        for gk in self.grads.values():
-            gk.zero_()
         if self.decoder_grad is not None:
             self.decoder_grad.zero_()
         r.forward(self.p)
         r.loss(self.gt, decoder=self.decoder, decoder_grad=self.decoder_grad)
         r.backward(self.p, self.grads)
-        for k in PARAM_KEYS:
-            n = self.p[k].numel()
-            call("sg_adam_step", _ptr(self.p[k]), _ptr(self.grads[k]), _ptr(self.m[k]), _ptr(self.v[k]), n,
-                 self.lr[k], 0.9, 0.999, 1e-15, t, _stream())
+        groups, n = self._adam_groups()
+        call("sg_adam_multi", groups, n, 0.9, 0.999, 1e-15, t, 1, _stream())
 
     def step(self):
         self.t += 1

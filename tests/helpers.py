@@ -10,7 +10,8 @@ FWD_REL, FWD_ABS = 1e-4, 1e-5
 # is the size of that summation's rounding relative to the group's largest entry).
 GRAD_REL, GRAD_FLOOR = 2e-3, 1e-5
 
-AMBIGUOUS = oracle.FLAG_SKIP | oracle.FLAG_STOP | oracle.FLAG_DEPTH
+# Depth order is decided on the same float32 key on both sides (no ambiguity left there).
+AMBIGUOUS = oracle.FLAG_SKIP | oracle.FLAG_STOP
 AMBIGUOUS_GRAD = AMBIGUOUS | oracle.FLAG_CLAMP
 
 

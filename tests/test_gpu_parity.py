@@ -72,8 +72,12 @@ def test_projection_matches_oracle(cloud):
     assert vg.sum() > 1000
     assert not (vg & ~vo).any(), "GPU keeps a Gaussian the oracle culls"
     m = vg
-    check_close("u", geo[m, 0], pr[m, P["U"]], 0, 2e-4)
-    check_close("v", geo[m, 1], pr[m, P["V"]], 0, 2e-4)
+    # the 2D mean is stored as int16 integer part + float fraction
+    packed = r.geo.view(-1, 8)[:, 7].cpu().numpy().view(np.uint32)
+    ui = (packed & 0xFFFF).astype(np.uint16).view(np.int16).astype(np.float64)
+    vi = (packed >> 16).astype(np.uint16).view(np.int16).astype(np.float64)
+    check_close("u", ui[m] + geo[m, 0], pr[m, P["U"]], 0, 2e-6)
+    check_close("v", vi[m] + geo[m, 1], pr[m, P["V"]], 0, 2e-6)
     check_close("depth", geo[m, 2], pr[m, P["DEPTH"]], 1e-6, 0)
     check_close("opacity", geo[m, 3], pr[m, P["OPAC"]], 1e-6, 1e-7)
     # the record stores the conditional factors: conic = 2 [[m00^2 + m10^2, m10 m11], [., m11^2]]
