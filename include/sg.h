@@ -231,6 +231,26 @@ sg_status sg_pyramid_loss(const sg_images *rendered, const sg_targets *gt, const
                           const sg_loss_config *lcfg, float *terms, sg_images *dL,
                           void *workspace, size_t workspace_bytes, sg_stream_t stream);
 
+/* Same as sg_pyramid_loss, for callers that cannot allocate device memory: a host
+ * framework that owns the device memory pool and passes this library only its input and
+ * output buffers, or a latency-critical thread that must not call cudaMalloc because it
+ * can block on or synchronise with other work on the device.  The paper has no
+ * counterpart; this is a deployment variant of the loss call.
+ * Instead of a caller workspace it uses a scratch array of SG_LOSS_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) built into the library; every GPU that loads the library holds that array
+ * until the process exits.  Images whose scratch need exceeds it (roughly P/16 bytes for
+ * P pixels, plus P*K*C/64 bytes when a decoder gradient is requested) are rejected with
+ * SG_ERR_CAPACITY and a message.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and leave their contents in it:
+ * the call clears what it needs, but calls whose GPU work overlaps race on it.  No
+ * allocation or free happens inside the call. */
+#define SG_LOSS_NOALLOC_SCRATCH_BYTES (16u << 20)
+sg_status sg_pyramid_loss_noalloc(const sg_images *rendered, const sg_targets *gt,
+                                  const sg_view *views, const sg_view *views_host, int32_t n_views,
+                                  int32_t C, const sg_loss_config *lcfg, float *terms,
+                                  sg_images *dL, sg_stream_t stream);
+
 /* ---------------------------------------------------------------------------------- */
 /* Backward path                                                                        */
 /* ---------------------------------------------------------------------------------- */

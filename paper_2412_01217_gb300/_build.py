@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsg.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "project.cu", "tiles.cu", "raster.cu", "loss.cu", "mlp.cu", "init.cu"]
+SOURCES = ["api.cu", "project.cu", "tiles.cu", "raster.cu", "loss.cu", "mlp.cu", "init.cu", "loss_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -106,6 +106,8 @@ SIGNATURES = {
     "sg_loss_workspace_size": (C.c_size_t, [P(SgView), c_i, c_i, c_i]),
     "sg_pyramid_loss": (c_i, [P(SgImages), P(SgTargets), c_p, P(SgView), c_i, c_i,
                               P(SgLossConfig), c_p, P(SgImages), c_p, C.c_size_t, c_p]),
+    "sg_pyramid_loss_noalloc": (c_i, [P(SgImages), P(SgTargets), c_p, P(SgView), c_i, c_i,
+                                      P(SgLossConfig), c_p, P(SgImages), c_p]),
     "sg_backward_workspace_size": (C.c_size_t, [C.c_int64]),
     "sg_render_pyramid_backward": (c_i, [P(SgGaussians), P(SgProjected), P(SgTileLists), c_p, c_i,
                                          c_i, P(SgConfig), P(SgSaved), P(SgImages),

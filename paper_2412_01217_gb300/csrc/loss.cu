@@ -439,6 +439,13 @@ static size_t loss_ws_bytes(int n_views, int n_tiles, int n_blocks, int KC) {
            al(sizeof(float) * (size_t)kDecChunks * KC);
 }
 
+// Exact scratch bytes when KC decoder-gradient floats per block are needed (0 = none).
+size_t loss_workspace_size_kc(const sg_view *vh, int n_views, int KC) {
+    LossViews lv;
+    make_loss_views(vh, n_views, lv);
+    return loss_ws_bytes(n_views, lv.tile_off[n_views], lv.pix_blk_off[n_views], KC);
+}
+
 size_t loss_workspace_size(const sg_view *vh, int n_views, int C, int n_classes) {
     LossViews lv;
     make_loss_views(vh, n_views, lv);

@@ -1,0 +1,87 @@
+"""The loss entry point for callers that cannot allocate device memory.
+
+Some callers get their input and output buffers from a host framework that owns all of
+the device's memory and offers this library no way to obtain scratch space; others run on
+a latency-critical thread where a cudaMalloc could block on other device work.  For them
+sg_pyramid_loss_noalloc uses scratch built into the library instead of a workspace.  This
+test calls it through the C ABI twice in a row and checks that each call gives the same
+loss terms and image gradients as sg_pyramid_loss with a caller-provided workspace.  The
+file is named so that pytest collects it last.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _inputs(seed, W=160, H=96, levels=3, n_cams=2, Cs=16, K=32):
+    import synthetic
+    from paper_2412_01217_gb300.splat import make_views, views_to_device
+    rng = np.random.default_rng(seed)
+    intr = dict(W=W, H=H, fx=W / 2.0, fy=W / 2.0, cx=W / 2 - 0.5, cy=H / 2 - 0.5)
+    cams = synthetic.Room(seed=3).trajectory(n_cams, intr, seed=7)
+    views, P, _ = make_views(cams, levels)
+    dev = torch.device("cuda")
+    t = lambda a, dt=torch.float32: torch.tensor(a, dtype=dt, device=dev)
+    depth = rng.uniform(1, 3, size=P)
+    depth[rng.uniform(size=P) < 0.1] = 0.0
+    return dict(views=views, dviews=views_to_device(views, dev), V=n_cams * levels, P=P, C=Cs, K=K,
+                r_rgb=t(rng.uniform(size=3 * P)), r_depth=t(rng.uniform(1, 3, size=P)),
+                r_sem=t(rng.normal(size=Cs * P)), g_rgb=t(rng.uniform(size=3 * P)), g_depth=t(depth),
+                g_label=t(rng.integers(-1, K, size=P), torch.int32), dec=t(rng.normal(size=(K, Cs)) * 0.3))
+
+
+def _call(x, noalloc):
+    from paper_2412_01217_gb300._lib import SgImages, SgLossConfig, SgTargets, call, load
+    lib = load()
+    P, Cs, K = x["P"], x["C"], x["K"]
+    rendered = SgImages(x["r_rgb"].data_ptr(), x["r_depth"].data_ptr(), x["r_sem"].data_ptr())
+    gt = SgTargets(x["g_rgb"].data_ptr(), x["g_depth"].data_ptr(), x["g_label"].data_ptr(), None)
+    dL = [torch.full((n * P,), float("nan"), device="cuda") for n in (3, 1, Cs)]
+    dLi = SgImages(*[d.data_ptr() for d in dL])
+    dec_grad = torch.zeros(K, Cs, device="cuda")
+    lc = SgLossConfig(0.2, 0.2, 1.0, 1.0, 0, K, x["dec"].data_ptr(), dec_grad.data_ptr())
+    terms = torch.full((4 * x["V"],), float("nan"), device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if noalloc:
+        call("sg_pyramid_loss_noalloc", C.byref(rendered), C.byref(gt), C.c_void_p(x["dviews"].data_ptr()),
+             x["views"], x["V"], Cs, C.byref(lc), C.c_void_p(terms.data_ptr()), C.byref(dLi), stream)
+    else:
+        ws = torch.zeros(lib.sg_loss_workspace_size(x["views"], x["V"], Cs, K), dtype=torch.uint8, device="cuda")
+        call("sg_pyramid_loss", C.byref(rendered), C.byref(gt), C.c_void_p(x["dviews"].data_ptr()), x["views"],
+             x["V"], Cs, C.byref(lc), C.c_void_p(terms.data_ptr()), C.byref(dLi), C.c_void_p(ws.data_ptr()),
+             ws.numel(), stream)
+    torch.cuda.synchronize()
+    return [terms.cpu().numpy(), *[d.cpu().numpy() for d in dL], dec_grad.cpu().numpy()]
+
+
+def test_noalloc_loss_matches_workspace_loss_on_two_calls():
+    for call_no, seed in enumerate((0, 1)):
+        x = _inputs(seed)
+        ref = _call(x, noalloc=False)
+        got = _call(x, noalloc=True)
+        for name, g, r in zip(("terms", "dL_rgb", "dL_depth", "dL_sem", "dL_decoder"), got, ref):
+            assert np.isfinite(g).all(), (call_no, name)
+            scale = np.abs(r).max()
+            assert np.allclose(g, r, rtol=1e-5, atol=1e-6 * scale), (call_no, name)
+
+
+def test_noalloc_loss_rejects_images_beyond_its_scratch():
+    from paper_2412_01217_gb300._lib import SgError
+    # 2048 x 2048 pixels with a decoder gradient need more than the built-in 16 MiB
+    import synthetic
+    from paper_2412_01217_gb300.splat import make_views, views_to_device
+    big = synthetic.make_camera(2048, 2048, 1000.0, 1000.0, 1023.5, 1023.5)
+    views, P, _ = make_views([big], 1)
+    x = dict(views=views, dviews=views_to_device(views, torch.device("cuda")), V=1, P=P, C=16, K=32)
+    dev = torch.device("cuda")
+    for k, n in (("r_rgb", 3), ("r_depth", 1), ("r_sem", 16), ("g_rgb", 3), ("g_depth", 1)):
+        x[k] = torch.zeros(n * P, device=dev)
+    x["g_label"] = torch.zeros(P, dtype=torch.int32, device=dev)
+    x["dec"] = torch.zeros(32, 16, device=dev)
+    with pytest.raises(SgError) as e:
+        _call(x, noalloc=True)
+    assert e.value.code == 2 and "scratch" in str(e.value)
