@@ -41,10 +41,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", default="16x16")
-    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--ppt", type=int, default=1, help="pixels per thread of the forward compositing kernel")
+    ap.add_argument("--ppt-bwd", type=int, default=2, help="pixels per thread of the backward kernel")
     ap.add_argument("--gaussians", type=int, default=300_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="use --tile/--batch/--ppt as given")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-baseline sample time")
     return ap.parse_args()
 
@@ -262,12 +265,24 @@ def run_ours(args):
     lib = load_library()
     tw, th = (int(x) for x in args.tile.split("x"))
     room, cam, g, frame, dec = build_inputs(args.gaussians, seed_offset=rank)
-    cfg = RenderConfig(tile_w=tw, tile_h=th, batch=args.batch)
+    cfg = RenderConfig(tile_w=tw, tile_h=th, batch=args.batch, pixels_per_thread=args.ppt,
+                       pixels_per_thread_bwd=args.ppt_bwd)
+    p = to_device_params(g, dev)
+    decoder = torch.tensor(dec, device=dev)
+    tune_table = None
+    if not args.no_autotune:
+        from paper_2412_01217_gb300.autotune import autotune
+        probe = PyramidRasterizer(args.gaussians, 16, [cam], levels=3, cfg=cfg,
+                                  loss_cfg=LossConfig(n_classes=32), device=dev)
+        gt0 = build_pyramid(probe, [frame["rgb"]], [frame["depth"]], [frame["label"]])
+        del probe
+        cfg, tune_table = autotune(p, [cam], 3, gt0, LossConfig(n_classes=32), base=cfg, decoder=decoder,
+                                   use_cache=False)
+        del gt0
+        torch.cuda.empty_cache()
     r = PyramidRasterizer(args.gaussians, 16, [cam], levels=3, cfg=cfg,
                           loss_cfg=LossConfig(n_classes=32), device=dev)
-    p = to_device_params(g, dev)
     gt = build_pyramid(r, [frame["rgb"]], [frame["depth"]], [frame["label"]])
-    decoder = torch.tensor(dec, device=dev)
     ms = MappingStep(r, p, gt, decoder=decoder)
     ms.step()
     torch.cuda.synchronize()
@@ -417,7 +432,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, tile=args.tile, batch=args.batch, gaussians=args.gaussians,
+        "config": dict(WORKLOAD, tile=f"{cfg.tile_w}x{cfg.tile_h}", batch=cfg.batch,
+                       pixels_per_thread=cfg.pixels_per_thread, pixels_per_thread_bwd=cfg.pixels_per_thread_bwd,
+                       autotuned=not args.no_autotune, gaussians=args.gaussians,
                        l2="flushed (256 MiB write) before every timed step", parallelism="replicas"),
         "gpu_launches": int(launches_per_step * args.steps),
         "launches_per_step": int(launches_per_step),

@@ -103,9 +103,12 @@ typedef struct {
     float dilation;  /* 0.3:    added to the 2D covariance diagonal (pixels^2)         */
     float fov_clamp; /* 1.3:    Jacobian evaluated at t_x/t_z clamped to fov_clamp*W/2fx */
     float bg[3];     /* background RGB (depth and semantic background are 0)          */
-    int32_t tile_w, tile_h; /* screen tile: 8x8, 16x16 or 32x8                        */
+    int32_t tile_w, tile_h; /* screen tile: 8x8, 16x8, 16x16 or 32x8                  */
     int32_t batch;          /* Gaussians staged per shared-memory batch: 32..256      */
     int32_t persistent;     /* 1: persistent grid with an atomic work queue           */
+    int32_t pixels_per_thread;     /* forward: 1, 2 or 4 pixels per thread (rows 4 apart);
+                                      tile_h % (4 * it) == 0, tile pixels >= 32 * it       */
+    int32_t pixels_per_thread_bwd; /* the same for the backward kernel                    */
 } sg_config;
 
 /* Projected records of all (view-level, Gaussian) pairs: record r = v*N + g. */
@@ -116,6 +119,8 @@ typedef struct {
                        1/2 d^T Sigma2D^{-1} d = (m00 dx)^2 + (m10 dx + m11 dy)^2            */
     uint32_t *rect; /* R x 2: tile rectangle [tx0,tx1) x [ty0,ty1) as (tx0|ty0<<16, tx1|ty1<<16);
                        an empty rectangle means the record is culled                    */
+    float *ext;     /* R x 2: half extents (pixels) of the region where alpha can reach
+                       alpha_min, with margin (8-B aligned)                             */
 } sg_projected;
 
 /* Per-tile depth-sorted instance lists (the set N of Eq. 7-9, restricted to a tile). */

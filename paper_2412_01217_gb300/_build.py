@@ -11,7 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsg.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "project.cu", "tiles.cu", "raster.cu", "loss.cu", "mlp.cu", "init.cu", "loss_noalloc.cu"]
+SOURCES = ["api.cu", "project.cu", "tiles.cu", "raster.cu", "raster_c4.cu", "raster_c8.cu", "raster_c16.cu",
+           "raster_c32.cu", "raster_c40.cu", "loss.cu", "mlp.cu", "init.cu", "loss_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -54,7 +55,7 @@ def build(force=False, verbose=False):
             print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(SOURCES))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]

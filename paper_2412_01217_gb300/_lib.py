@@ -37,11 +37,12 @@ SgGaussianGrads = SgGaussians  # same layout (non-const pointers)
 class SgConfig(C.Structure):
     _fields_ = [("alpha_max", c_f), ("alpha_min", c_f), ("T_min", c_f), ("z_near", c_f),
                 ("dilation", c_f), ("fov_clamp", c_f), ("bg", c_f * 3), ("tile_w", c_i),
-                ("tile_h", c_i), ("batch", c_i), ("persistent", c_i)]
+                ("tile_h", c_i), ("batch", c_i), ("persistent", c_i), ("pixels_per_thread", c_i),
+                ("pixels_per_thread_bwd", c_i)]
 
 
 class SgProjected(C.Structure):
-    _fields_ = [("geo", c_p), ("rect", c_p)]
+    _fields_ = [("geo", c_p), ("rect", c_p), ("ext", c_p)]
 
 
 class SgTileLists(C.Structure):

@@ -84,6 +84,11 @@ static sg_status check_cfg(const sg_config *c) {
                "need 0 < alpha_min < alpha_max <= 1");
     SG_REQUIRE(c->T_min >= 0.f && c->z_near > 0.f && c->dilation >= 0.f && c->fov_clamp > 0.f,
                "bad T_min / z_near / dilation / fov_clamp");
+    for (int ppt : {c->pixels_per_thread, c->pixels_per_thread_bwd}) {
+        SG_REQUIRE(ppt == 1 || ppt == 2 || ppt == 4, "pixels per thread must be 1, 2 or 4");
+        SG_REQUIRE(c->tile_h % (4 * ppt) == 0 && t / ppt >= 32,
+                   "tile %dx%d cannot give %d pixels per thread", c->tile_w, c->tile_h, ppt);
+    }
     return SG_OK;
 }
 
@@ -118,8 +123,10 @@ void sg_default_config(sg_config *c) {
     c->bg[0] = c->bg[1] = c->bg[2] = 0.f;
     c->tile_w = 16;
     c->tile_h = 16;
-    c->batch = 128;
+    c->batch = 256;
     c->persistent = 1;
+    c->pixels_per_thread = 1;
+    c->pixels_per_thread_bwd = 2;
 }
 
 void sg_default_loss_config(sg_loss_config *c) {
@@ -184,7 +191,7 @@ sg_status sg_project_gaussians(const sg_gaussians *g, const sg_view *views, int3
     SG_TRY(check_gaussians(g));
     SG_TRY(check_cfg(cfg));
     SG_TRY(check_views(views, n_views));
-    SG_REQUIRE(out && out->geo && out->rect, "projected buffers are NULL");
+    SG_REQUIRE(out && out->geo && out->rect && out->ext, "projected buffers are NULL");
     SG_REQUIRE(aligned16(out->geo), "geo must be 16-byte aligned");
     SG_REQUIRE((int64_t)g->N * n_views < (1ll << 32), "too many records");
     return launch_project_fwd(g, views, n_views, cfg, out, (cudaStream_t)stream);
@@ -198,7 +205,7 @@ sg_status sg_build_tile_lists(const sg_projected *proj, int32_t N, int32_t n_vie
                               const sg_view *views, int32_t n_tiles, const sg_config *cfg,
                               sg_tile_lists *lists, void *workspace, size_t workspace_bytes,
                               uint32_t *status, sg_stream_t stream) {
-    SG_REQUIRE(proj && proj->geo && proj->rect, "projected buffers are NULL");
+    SG_REQUIRE(proj && proj->geo && proj->rect && proj->ext, "projected buffers are NULL");
     SG_TRY(check_cfg(cfg));
     SG_TRY(check_views(views, n_views));
     SG_REQUIRE(N >= 0 && n_tiles >= 1, "bad N / n_tiles");
@@ -229,6 +236,7 @@ sg_status sg_render_pyramid(const sg_gaussians *g, const sg_projected *proj,
     a.T_final = saved->T_final;
     a.last = saved->last;
     a.n_contrib = saved->n_contrib;
+    a.ppt = cfg->pixels_per_thread;
     return launch_raster(a, g->C, false, (cudaStream_t)stream);
 }
 
@@ -301,6 +309,7 @@ sg_status sg_render_pyramid_backward(const sg_gaussians *g, const sg_projected *
     a.g2d = g2d;
     a.g_rgb = grads->rgb;
     a.g_sem = grads->sem;
+    a.ppt = cfg->pixels_per_thread_bwd;
     SG_TRY(launch_raster(a, g->C, true, st));
     return launch_project_bwd(g, views, n_views, cfg, proj, g2d, grads, st);
 }

@@ -199,6 +199,9 @@ __global__ void __launch_bounds__(kLossThreads) ssim_l1_kernel(SsimArgs a) {
 
 __global__ void loss_count_kernel(const float *gt_depth, const int *label, const sg_view *views,
                                   LossViews lv, int *counts) {
+    __shared__ int s_cnt[2];
+    if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0;
+    __syncthreads();
     const int blk = blockIdx.x;
     const int v = find_prefix(lv.pix_blk_off, lv.n, blk);
     const sg_view &vw = views[v];
@@ -209,14 +212,16 @@ __global__ void loss_count_kernel(const float *gt_depth, const int *label, const
         cd = gt_depth[(size_t)vw.pixel_offset + p] > 0.f;
         cl = label ? label[(size_t)vw.pixel_offset + p] >= 0 : 0;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        cd += __shfl_xor_sync(SG_FULL_MASK, cd, o);
-        cl += __shfl_xor_sync(SG_FULL_MASK, cl, o);
-    }
+    cd = __reduce_add_sync(SG_FULL_MASK, cd);
+    cl = __reduce_add_sync(SG_FULL_MASK, cl);
     if ((threadIdx.x & 31) == 0) {
-        if (cd) atomicAdd(counts + 2 * v, cd);
-        if (cl) atomicAdd(counts + 2 * v + 1, cl);
+        atomicAdd(&s_cnt[0], cd);
+        atomicAdd(&s_cnt[1], cl);
     }
+    __syncthreads();
+    // one global atomic per block and counter (integer: order-independent)
+    if (threadIdx.x == 0 && s_cnt[0]) atomicAdd(counts + 2 * v, s_cnt[0]);
+    if (threadIdx.x == 1 && s_cnt[1]) atomicAdd(counts + 2 * v + 1, s_cnt[1]);
 }
 
 struct PixelArgs {
@@ -334,13 +339,33 @@ __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
         if (a.decoder_grad) {
 #pragma unroll
             for (int c = 0; c < C; ++c) s_S[threadIdx.x * C + c] = S[c];
+            float *s_dec_acc = s_S + kLossThreads * C;  // K x C
+            for (int o = threadIdx.x; o < K * C; o += kLossThreads) s_dec_acc[o] = 0.f;
             __syncthreads();
-            for (int o = threadIdx.x; o < K * C; o += kLossThreads) {
-                const int k = o / C, c = o % C;
-                float s = 0.f;
-                for (int t = 0; t < kLossThreads; ++t) s = fmaf(s_dz[t * K + k], s_S[t * C + c], s);
-                a.dec_partials[(size_t)blk * K * C + o] = s;  // reduced later in block order
+            // this warp's 32 pixels: each lane accumulates 4 x 4 blocks of dz_p S_p^T in registers
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            constexpr int KB = K / 4, CB = C / 4;
+            for (int blk4 = lane; blk4 < KB * CB; blk4 += 32) {
+                const int k0 = (blk4 / CB) * 4, c0 = (blk4 % CB) * 4;
+                float acc[4][4] = {};
+                for (int t = warp * 32; t < warp * 32 + 32; ++t) {
+                    const float4 dz = *reinterpret_cast<const float4 *>(s_dz + t * K + k0);
+                    const float4 sv = *reinterpret_cast<const float4 *>(s_S + t * C + c0);
+                    const float dzv[4] = {dz.x, dz.y, dz.z, dz.w}, svv[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(dzv[i], svv[jj], acc[i][jj]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) atomicAdd(s_dec_acc + (k0 + i) * C + c0 + jj, acc[i][jj]);
             }
+            __syncthreads();
+            // this block's share of dL/ddecoder, reduced later in block order
+            for (int o = threadIdx.x; o < K * C; o += kLossThreads)
+                a.dec_partials[(size_t)blk * K * C + o] = s_dec_acc[o];
         }
     }
     const float t1 = block_sum(l1d, s_red);
@@ -455,11 +480,11 @@ size_t loss_workspace_size(const sg_view *vh, int n_views, int C, int n_classes)
 
 template <int C, int K>
 static void launch_pixel_t(PixelArgs &pa, int blocks, cudaStream_t st) {
-    const size_t dyn = pa.decoder_grad ? sizeof(float) * kLossThreads * (K + C) : 0;
+    const size_t dyn = pa.decoder_grad ? sizeof(float) * (kLossThreads * (K + C) + K * C) : 0;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(loss_pixel_kernel<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(float) * kLossThreads * (K + C)));
+                             (int)(sizeof(float) * (kLossThreads * (K + C) + K * C)));
         attr = true;
     }
     loss_pixel_kernel<C, K><<<blocks, kLossThreads, dyn, st>>>(pa);

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     const float *__restrict__ mean, const float *__restrict__ log_scale,
     const float4 *__restrict__ quat, const float *__restrict__ ologit, int N,
     const sg_view *__restrict__ views, int n_views, ProjConsts pc, float4 *__restrict__ geo,
-    uint2 *__restrict__ rect) {
+    uint2 *__restrict__ rect, float2 *__restrict__ ext) {
     __shared__ sg_view s_views[SG_MAX_VIEWS];
     for (int i = threadIdx.x; i < n_views; i += blockDim.x) s_views[i] = views[i];
     __syncthreads();
@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
         view_geom(vw, mu, pc.fov_clamp, q);
         float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
         uint2 rc = make_uint2(0u, 0u);
+        float2 e2 = make_float2(0.f, 0.f);
         const float tz = q.t[2];
         if (tz > pc.z_near && o >= pc.alpha_min) {
             // the 2D mean in double-float: t = R mu + t_cw and (fx t_x / t_z + cx, ...)
@@ -186,12 +187,14 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
                     const float m10 = -s01 / sqrtf(2.f * s00 * det);
                     const uint32_t packed = ((uint32_t)(int)ui & 0xffffu) | (((uint32_t)(int)vi & 0xffffu) << 16);
                     g1 = make_float4(m00, m10, m11, __uint_as_float(packed));
+                    e2 = make_float2(ex, ey);
                 }
             }
         }
         geo[2 * r] = g0;
         geo[2 * r + 1] = g1;
         rect[r] = rc;
+        ext[r] = e2;
     }
 }
 
@@ -325,7 +328,7 @@ sg_status launch_project_fwd(const sg_gaussians *g, const sg_view *views, int n_
         project_fwd_kernel<<<blocks, threads, 0, st>>>(
             g->mean, g->log_scale, reinterpret_cast<const float4 *>(g->quat), g->opacity_logit,
             g->N, views, n_views, pc, reinterpret_cast<float4 *>(out->geo),
-            reinterpret_cast<uint2 *>(out->rect));
+            reinterpret_cast<uint2 *>(out->rect), reinterpret_cast<float2 *>(out->ext));
     if (blocks > 0) count_launches(1);
     return check_launch("project_fwd");
 }

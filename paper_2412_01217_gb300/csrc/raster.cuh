@@ -8,6 +8,7 @@ namespace sg {
 
 struct RasterArgs {
     const float4 *geo;
+    const float2 *ext;
     const uint32_t *record;
     const int2 *ranges;
     const float *rgb;
@@ -19,6 +20,7 @@ struct RasterArgs {
     int tile_w, tile_h, batch;
     int *work_counter;
     int persistent;
+    int ppt;  // pixels per thread (1, 2 or 4)
     // forward outputs / backward inputs
     float *img_rgb, *img_depth, *img_sem;
     float *T_final;
@@ -32,6 +34,7 @@ inline void fill_raster_args(RasterArgs &a, const sg_gaussians *g, const sg_proj
                              const sg_tile_lists *lists, const sg_view *views, int n_views,
                              int n_tiles, const sg_config *cfg, int *work_counter) {
     a.geo = reinterpret_cast<const float4 *>(proj->geo);
+    a.ext = reinterpret_cast<const float2 *>(proj->ext);
     a.record = lists->record;
     a.ranges = reinterpret_cast<const int2 *>(lists->ranges);
     a.rgb = g->rgb;
@@ -51,6 +54,7 @@ inline void fill_raster_args(RasterArgs &a, const sg_gaussians *g, const sg_proj
     a.batch = cfg->batch;
     a.work_counter = work_counter;
     a.persistent = cfg->persistent;
+    a.ppt = cfg->pixels_per_thread;
 }
 
 sg_status launch_raster(RasterArgs &a, int C, bool backward, cudaStream_t st);

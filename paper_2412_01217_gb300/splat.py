@@ -44,8 +44,10 @@ class RenderConfig:
     bg: tuple = (0.0, 0.0, 0.0)
     tile_w: int = 16
     tile_h: int = 16
-    batch: int = 128
+    batch: int = 256
     persistent: bool = True
+    pixels_per_thread: int = 1
+    pixels_per_thread_bwd: int = 2
 
     def to_c(self):
         c = SgConfig()
@@ -54,6 +56,8 @@ class RenderConfig:
         for i in range(3):
             c.bg[i] = self.bg[i]
         c.tile_w, c.tile_h, c.batch, c.persistent = self.tile_w, self.tile_h, self.batch, int(self.persistent)
+        c.pixels_per_thread = int(self.pixels_per_thread)
+        c.pixels_per_thread_bwd = int(self.pixels_per_thread_bwd)
         return c
 
 
@@ -151,6 +155,7 @@ class PyramidRasterizer:
         i32 = dict(dtype=torch.int32, device=dev)
         self.geo = torch.zeros(max(1, self.R) * 8, **f32)
         self.rect = torch.zeros(max(1, self.R) * 2, **i32)
+        self.ext = torch.zeros(max(1, self.R) * 2, **f32)
         if capacity is None:
             capacity = max(1 << 16, 16 * self.R)
         self.capacity = int(capacity)
@@ -178,7 +183,7 @@ class PyramidRasterizer:
                                    dtype=torch.uint8, device=dev)
         self.bwd_ws = torch.zeros(lib.sg_backward_workspace_size(max(1, self.R)), dtype=torch.uint8, device=dev)
         self._ccfg = self.cfg.to_c()
-        self._proj = SgProjected(self.geo.data_ptr(), self.rect.data_ptr())
+        self._proj = SgProjected(self.geo.data_ptr(), self.rect.data_ptr(), self.ext.data_ptr())
         self._lists = SgTileLists(self.capacity, self.tile.data_ptr(), self.record.data_ptr(),
                                   self.ranges.data_ptr(), self.count.data_ptr())
         self._saved = SgSaved(self.T_final.data_ptr(), self.last.data_ptr(), self.n_contrib.data_ptr())

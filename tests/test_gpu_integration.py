@@ -29,7 +29,8 @@ def test_autograd_function_matches_direct_backward():
     torch.cuda.synchronize()
     for k in KEYS:
         a, b = leaves[k].grad.cpu().numpy(), grads[k].cpu().numpy()
-        assert np.allclose(a, b, rtol=1e-5, atol=1e-6 * (np.abs(b).max() + 1e-12)), k
+        # same kernels; only the order of the float atomic additions differs
+        assert np.allclose(a, b, rtol=1e-4, atol=1e-5 * (np.abs(b).max() + 1e-12)), k
 
 
 def _room_problem(W=320, H=180, n=30000, ncam=2, levels=3, C=16, K=32):
@@ -142,3 +143,22 @@ def test_full_size_backward_sparse_upstream(replica_like):
     r.backward(p, grads, dL=tuple(dl))
     got = {k: t.cpu().numpy() for k, t in grads.items()}
     check_grads(got, ref, KEYS)
+
+
+def test_autotuner_picks_a_valid_configuration_with_identical_output():
+    from paper_2412_01217_gb300 import LossConfig, RenderConfig, build_pyramid
+    from paper_2412_01217_gb300.autotune import autotune
+    room, g, cams, frames = _room_problem(n=20000, ncam=1)
+    r, p = make(g, cams, levels=3)
+    gt = build_pyramid(r, [f["rgb"] for f in frames], [f["depth"] for f in frames], [f["label"] for f in frames])
+    dec = torch.randn(32, 16, device="cuda") * 0.3
+    cfg, table = autotune(p, cams, 3, gt, LossConfig(n_classes=32), decoder=dec, reps=1, use_cache=False)
+    assert (cfg.tile_w, cfg.tile_h) in ((16, 16), (8, 8), (32, 8), (16, 8)) and cfg.batch in (64, 128, 256)
+    assert len(table) >= 20 and all(t["ms"] > 0 for t in table)
+    r.forward(p)
+    base = r.img_rgb.clone()
+    r2, _ = make(g, cams, levels=3, **{k: getattr(cfg, k) for k in ("tile_w", "tile_h", "batch", "pixels_per_thread",
+                                                                        "pixels_per_thread_bwd")})
+    r2.forward(p)
+    torch.cuda.synchronize()
+    assert torch.equal(r2.img_rgb, base)

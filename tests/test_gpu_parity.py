@@ -163,21 +163,23 @@ def test_forward_matches_oracle_cloud(cloud):
 def test_forward_bitwise_identical_across_tiles_batches_and_runs(cloud):
     g, cam = cloud
     base = None
-    for tw, th, batch, pers in ((16, 16, 128, True), (8, 8, 32, True), (32, 8, 256, False),
-                                (16, 8, 64, True), (16, 16, 128, True)):
-        r, p = make(g, [cam], tile_w=tw, tile_h=th, batch=batch, persistent=pers)
+    for tw, th, batch, pers, ppt in ((16, 16, 128, True, 1), (8, 8, 32, True, 1), (32, 8, 256, False, 2),
+                                     (16, 8, 64, True, 2), (16, 16, 128, True, 4), (8, 8, 64, False, 2),
+                                     (16, 16, 128, True, 1)):
+        r, p = make(g, [cam], tile_w=tw, tile_h=th, batch=batch, persistent=pers, pixels_per_thread=ppt)
         r.forward(p)
         im = view_images(r, 0, 8)
         if base is None:
             base = im
             continue
         for k in ("rgb", "depth", "sem", "T", "n_contrib"):
-            assert np.array_equal(im[k], base[k]), (k, tw, th, batch, pers)
+            assert np.array_equal(im[k], base[k]), (k, tw, th, batch, pers, ppt)
 
 
-def test_backward_matches_oracle_cloud(cloud):
+@pytest.mark.parametrize("ppt", [1, 2, 4])
+def test_backward_matches_oracle_cloud(cloud, ppt):
     g, cam = cloud
-    r, p = make(g, [cam])
+    r, p = make(g, [cam], pixels_per_thread_bwd=ppt)
     r.forward(p)
     ref_f = oracle.render(g, cam)
     keep = ((ref_f["flags"] & AMBIGUOUS_GRAD) == 0).astype(np.float64)
