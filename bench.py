@@ -121,6 +121,42 @@ def raster_flops(s):
 
 
 # ------------------------------------------------------------------------------------------
+# DRAM traffic of the dominant kernel, from a committed ncu summary
+# ------------------------------------------------------------------------------------------
+
+KERNEL_SOURCES = ["paper_2412_01217_gb300/csrc/raster_impl.cuh", "paper_2412_01217_gb300/csrc/raster.cuh",
+                  "paper_2412_01217_gb300/csrc/sg_common.cuh"]
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, units_now):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch from profiles/<kernel>_*.md
+    (lines 'source_sha: ...', 'dram_bytes_per_launch: ...', 'units: ...'), scaled by the
+    units processed if the capture ran a different case; None when the kernel sources
+    changed since the capture."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md"))):
+        kv = {}
+        for line in open(path):
+            if ":" in line and line.strip().startswith(("source_sha", "dram_bytes_per_launch", "units")):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip().strip("`")
+        if kv.get("source_sha") != kernel_source_sha() or "dram_bytes_per_launch" not in kv:
+            continue
+        b = float(kv["dram_bytes_per_launch"])
+        u = float(kv.get("units", units_now) or units_now)
+        return b * units_now / u if u else b
+    return None
+
+
+# ------------------------------------------------------------------------------------------
 # clocks
 # ------------------------------------------------------------------------------------------
 
@@ -424,7 +460,9 @@ def run_ours(args):
     d_time = bwd_avg if dominant == "raster_bwd" else fwd_avg
     achieved = d_flops / d_time / 1e12
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+                "traffic": profiled_traffic(dominant, stats["E"]),
+                "traffic_unit": "DRAM bytes per launch (ncu), scaled by list entries examined",
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                 "launch_ms": d_time * 1e3}
     evals = 2 * stats["E"]

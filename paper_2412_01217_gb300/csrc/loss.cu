@@ -18,9 +18,10 @@
 
 namespace sg {
 
-constexpr int kLTW = 32, kLTH = 16;           // loss tile
+constexpr int kLTW = 32, kLTH = 32;           // loss tile (outputs)
 constexpr int kXW = kLTW + 20, kXH = kLTH + 20;  // staged planes (10-px halo)
 constexpr int kMW = kLTW + 10, kMH = kLTH + 10;  // moment / partial maps (5-px halo)
+constexpr int kXP = kXW + 1, kMP = kMW + 1;      // padded row pitches (odd: no bank conflicts)
 constexpr int kLossThreads = 256;
 
 struct LossViews {
@@ -69,12 +70,14 @@ struct SsimArgs {
     float *partials;     // per CTA: (sum |x - y|, sum ssim)
 };
 
+// Sliding-window separable passes: each thread produces a run of consecutive outputs of one
+// row (horizontal) or column (vertical) from a register window of input values.
 __global__ void __launch_bounds__(kLossThreads) ssim_l1_kernel(SsimArgs a) {
     extern __shared__ __align__(16) float sm[];
-    float *X = sm;                   // kXH x kXW
-    float *Y = X + kXH * kXW;        // kXH x kXW
-    float *Hm = Y + kXH * kXW;       // 5 x kXH x kMW (later: 3 x kMH x kLTW)
-    float *Mp = Hm + 5 * kXH * kMW;  // 3 x kMH x kMW
+    float *X = sm;                   // kXH x kXP
+    float *Y = X + kXH * kXP;        // kXH x kXP
+    float *Hm = Y + kXH * kXP;       // 5 x kXH x kMP (later: 3 x kMH x kMP)
+    float *Mp = Hm + 5 * kXH * kMP;  // 3 x kMH x kMP
     __shared__ float w[11];
     __shared__ float s_red[kLossThreads / 32];
     if (threadIdx.x == 0) gauss_window(w);
@@ -92,96 +95,159 @@ __global__ void __launch_bounds__(kLossThreads) ssim_l1_kernel(SsimArgs a) {
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
     float l1_sum = 0.f, ssim_sum = 0.f;
     __syncthreads();
+    float wr[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) wr[i] = w[i];
     for (int ch = 0; ch < a.nch; ++ch) {
         const float *xs = a.x + (size_t)a.nch * vw.pixel_offset + ch * HW;
         const float *ys = a.y + (size_t)a.nch * vw.pixel_offset + ch * HW;
+        // stage x, y with a 10-pixel halo (zero outside the image)
         for (int i = threadIdx.x; i < kXH * kXW; i += kLossThreads) {
-            const int r = i / kXW, c = i % kXW;
+            const int r = i / kXW, c = i - r * kXW;
             const int gy = oy + r, gx = ox + c;
             const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-            X[i] = in ? xs[(size_t)gy * W + gx] : 0.f;
-            Y[i] = in ? ys[(size_t)gy * W + gx] : 0.f;
+            X[r * kXP + c] = in ? xs[(size_t)gy * W + gx] : 0.f;
+            Y[r * kXP + c] = in ? ys[(size_t)gy * W + gx] : 0.f;
         }
         __syncthreads();
-        // horizontal window sums of x, y, x^2, y^2, xy
-        for (int i = threadIdx.x; i < kXH * kMW; i += kLossThreads) {
-            const int r = i / kMW, c = i % kMW;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+        // horizontal window sums of x, y, x^2, y^2, xy: rows kXH, outputs kMW in runs of 6
+        {
+            constexpr int RUN = 6, SEGS = kMW / RUN;  // 42 = 7 * 6
+            for (int it = threadIdx.x; it < SEGS * kXH; it += kLossThreads) {
+                const int seg = it / kXH, r = it - seg * kXH;
+                const int c0 = seg * RUN;
+                float xv[RUN + 10], yv[RUN + 10];
 #pragma unroll
-            for (int j = 0; j < 11; ++j) {
-                const float xv = X[r * kXW + c + j], yv = Y[r * kXW + c + j], wj = w[j];
-                s0 = fmaf(wj, xv, s0);
-                s1 = fmaf(wj, yv, s1);
-                s2 = fmaf(wj, xv * xv, s2);
-                s3 = fmaf(wj, yv * yv, s3);
-                s4 = fmaf(wj, xv * yv, s4);
-            }
-            Hm[0 * kXH * kMW + i] = s0;
-            Hm[1 * kXH * kMW + i] = s1;
-            Hm[2 * kXH * kMW + i] = s2;
-            Hm[3 * kXH * kMW + i] = s3;
-            Hm[4 * kXH * kMW + i] = s4;
-        }
-        __syncthreads();
-        // vertical window sums -> SSIM and its partials (zero outside the image)
-        for (int i = threadIdx.x; i < kMH * kMW; i += kLossThreads) {
-            const int r = i / kMW, c = i % kMW;
-            const int gy = by * kLTH - 5 + r, gx = bx * kLTW - 5 + c;
-            float P = 0.f, Q = 0.f, R = 0.f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int i = 0; i < RUN + 10; ++i) {
+                    xv[i] = X[r * kXP + c0 + i];
+                    yv[i] = Y[r * kXP + c0 + i];
+                }
 #pragma unroll
-                for (int k = 0; k < 5; ++k)
+                for (int o = 0; o < RUN; ++o) {
+                    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
 #pragma unroll
-                    for (int j = 0; j < 11; ++j) m[k] = fmaf(w[j], Hm[k * kXH * kMW + (r + j) * kMW + c], m[k]);
-                const float mx = m[0], my = m[1];
-                const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
-                const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
-                const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
-                const float s = (A1 * A2) / (B1 * B2);
-                if (r >= 5 && r < kLTH + 5 && c >= 5 && c < kLTW + 5) ssim_sum += s;
-                const float d_mx = 2.f * my * A2 / (B1 * B2) - s * 2.f * mx / B1;
-                const float d_sxx = -s / B2;
-                const float d_sxy = 2.f * A1 / (B1 * B2);
-                P = sc * (d_mx - 2.f * mx * d_sxx - my * d_sxy);
-                Q = sc * d_sxx;
-                R = sc * d_sxy;
-            }
-            Mp[0 * kMH * kMW + i] = P;
-            Mp[1 * kMH * kMW + i] = Q;
-            Mp[2 * kMH * kMW + i] = R;
-        }
-        __syncthreads();
-        float *Hp = Hm;  // 3 x kMH x kLTW, reuses the moment buffer
-        for (int i = threadIdx.x; i < kMH * kLTW; i += kLossThreads) {
-            const int r = i / kLTW, c = i % kLTW;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float s = 0.f;
-#pragma unroll
-                for (int j = 0; j < 11; ++j) s = fmaf(w[j], Mp[k * kMH * kMW + r * kMW + c + j], s);
-                Hp[k * kMH * kLTW + i] = s;
+                    for (int j = 0; j < 11; ++j) {
+                        const float x = xv[o + j], y = yv[o + j];
+                        s0 = fmaf(wr[j], x, s0);
+                        s1 = fmaf(wr[j], y, s1);
+                        s2 = fmaf(wr[j], x * x, s2);
+                        s3 = fmaf(wr[j], y * y, s3);
+                        s4 = fmaf(wr[j], x * y, s4);
+                    }
+                    const int idx = r * kMP + c0 + o;
+                    Hm[0 * kXH * kMP + idx] = s0;
+                    Hm[1 * kXH * kMP + idx] = s1;
+                    Hm[2 * kXH * kMP + idx] = s2;
+                    Hm[3 * kXH * kMP + idx] = s3;
+                    Hm[4 * kXH * kMP + idx] = s4;
+                }
             }
         }
         __syncthreads();
+        // vertical window sums -> SSIM and its partials (zero outside the image): columns
+        // kMW, output rows kMH in runs of 6
+        {
+            constexpr int RUN = 6, SEGS = kMH / RUN;  // 42 = 7 * 6
+            for (int it = threadIdx.x; it < SEGS * kMW; it += kLossThreads) {
+                const int seg = it / kMW, c = it - seg * kMW;
+                const int r0 = seg * RUN;
+                float m[5][RUN];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    float col[RUN + 10];
+#pragma unroll
+                    for (int i = 0; i < RUN + 10; ++i) col[i] = Hm[k * kXH * kMP + (r0 + i) * kMP + c];
+#pragma unroll
+                    for (int o = 0; o < RUN; ++o) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 11; ++j) acc = fmaf(wr[j], col[o + j], acc);
+                        m[k][o] = acc;
+                    }
+                }
+#pragma unroll
+                for (int o = 0; o < RUN; ++o) {
+                    const int r = r0 + o;
+                    const int gy = by * kLTH - 5 + r, gx = bx * kLTW - 5 + c;
+                    float P = 0.f, Q = 0.f, R = 0.f;
+                    if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                        const float mx = m[0][o], my = m[1][o];
+                        const float sxx = m[2][o] - mx * mx, syy = m[3][o] - my * my, sxy = m[4][o] - mx * my;
+                        const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
+                        const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
+                        const float inv = 1.f / (B1 * B2);
+                        const float s = A1 * A2 * inv;
+                        if (r >= 5 && r < kLTH + 5 && c >= 5 && c < kLTW + 5) ssim_sum += s;
+                        const float d_mx = 2.f * my * A2 * inv - s * 2.f * mx / B1;
+                        const float d_sxx = -s / B2;
+                        const float d_sxy = 2.f * A1 * inv;
+                        P = sc * (d_mx - 2.f * mx * d_sxx - my * d_sxy);
+                        Q = sc * d_sxx;
+                        R = sc * d_sxy;
+                    }
+                    Mp[0 * kMH * kMP + r * kMP + c] = P;
+                    Mp[1 * kMH * kMP + r * kMP + c] = Q;
+                    Mp[2 * kMH * kMP + r * kMP + c] = R;
+                }
+            }
+        }
+        __syncthreads();
+        float *Hp = Hm;  // 3 x kMH x kMP, reuses the moment buffer
+        // horizontal sums of the partials: rows kMH, outputs kLTW in runs of 8
+        {
+            constexpr int RUN = 8, SEGS = kLTW / RUN;
+            for (int it = threadIdx.x; it < SEGS * kMH; it += kLossThreads) {
+                const int seg = it / kMH, r = it - seg * kMH;
+                const int c0 = seg * RUN;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    float row[RUN + 10];
+#pragma unroll
+                    for (int i = 0; i < RUN + 10; ++i) row[i] = Mp[k * kMH * kMP + r * kMP + c0 + i];
+#pragma unroll
+                    for (int o = 0; o < RUN; ++o) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 11; ++j) acc = fmaf(wr[j], row[o + j], acc);
+                        Hp[k * kMH * kMP + r * kMP + c0 + o] = acc;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // vertical sums of the partials -> dL/dx on the tile: columns kLTW, rows in runs of 8
         float *gs = a.grad + (size_t)a.nch * vw.pixel_offset + ch * HW;
-        for (int i = threadIdx.x; i < kLTH * kLTW; i += kLossThreads) {
-            const int r = i / kLTW, c = i % kLTW;
-            const int gy = by * kLTH + r, gx = bx * kLTW + c;
-            if (gx >= W || gy >= H) continue;
-            float cv[3];
+        {
+            constexpr int RUN = 8, SEGS = kLTH / RUN;
+            for (int it = threadIdx.x; it < SEGS * kLTW; it += kLossThreads) {
+                const int seg = it / kLTW, c = it - seg * kLTW;
+                const int r0 = seg * RUN;
+                float cv[3][RUN];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float s = 0.f;
+                for (int k = 0; k < 3; ++k) {
+                    float col[RUN + 10];
 #pragma unroll
-                for (int j = 0; j < 11; ++j) s = fmaf(w[j], Hp[k * kMH * kLTW + (r + j) * kLTW + c], s);
-                cv[k] = s;
+                    for (int i = 0; i < RUN + 10; ++i) col[i] = Hp[k * kMH * kMP + (r0 + i) * kMP + c];
+#pragma unroll
+                    for (int o = 0; o < RUN; ++o) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 11; ++j) acc = fmaf(wr[j], col[o + j], acc);
+                        cv[k][o] = acc;
+                    }
+                }
+#pragma unroll
+                for (int o = 0; o < RUN; ++o) {
+                    const int r = r0 + o;
+                    const int gy = by * kLTH + r, gx = bx * kLTW + c;
+                    if (gx >= W || gy >= H) continue;
+                    const float xv = X[(r + 10) * kXP + c + 10], yv = Y[(r + 10) * kXP + c + 10];
+                    const float d = xv - yv;
+                    l1_sum += fabsf(d);
+                    const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+                    gs[(size_t)gy * W + gx] = l1c * sg + cv[0][o] + 2.f * xv * cv[1][o] + yv * cv[2][o];
+                }
             }
-            const float xv = X[(r + 10) * kXW + c + 10], yv = Y[(r + 10) * kXW + c + 10];
-            const float d = xv - yv;
-            l1_sum += fabsf(d);
-            const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-            gs[(size_t)gy * W + gx] = l1c * sg + cv[0] + 2.f * xv * cv[1] + yv * cv[2];
         }
         __syncthreads();
     }
@@ -261,16 +327,27 @@ __global__ void decoder_reduce2_kernel(const float *__restrict__ chunk_sums, int
     out[o] += s;
 }
 
+// Row pitches of the per-thread stashes of dz (K floats) and S (C floats).  Rows stay
+// 16-byte aligned, and the 8 rows written by a quarter-warp's 16-byte stores start in 8
+// different 4-bank groups, so neither the stores nor the 16-byte reads of the decoder
+// gradient loop have bank conflicts.
+template <int K> __host__ __device__ constexpr int stash_pitch() { return K + 4; }
+
 template <int C, int K>
 __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
-    __shared__ float s_dec[K * C];
+    static_assert(C % 4 == 0 && K % 4 == 0, "float4 stashes");
+    constexpr int KP = stash_pitch<K>(), CP = stash_pitch<C>();
+    __shared__ __align__(16) float s_dec[K * C];
     __shared__ float s_red[kLossThreads / 32];
-    // only used when the decoder gradient is requested (dynamic: 256 * (K + C) floats)
+    // only used when the decoder gradient is requested
     extern __shared__ __align__(16) float s_dyn[];
-    float *s_dz = s_dyn;
-    float *s_S = s_dyn + kLossThreads * K;
+    float *s_dz = s_dyn;                          // kLossThreads x KP
+    float *s_S = s_dyn + kLossThreads * KP;       // kLossThreads x CP
+    float *s_dec_acc = s_S + kLossThreads * CP;   // K x C
     const bool has_dec = a.decoder != nullptr;
     for (int i = threadIdx.x; i < K * C; i += kLossThreads) s_dec[i] = has_dec ? a.decoder[i] : (i / C == i % C ? 1.f : 0.f);
+    if (a.decoder_grad)
+        for (int o = threadIdx.x; o < K * C; o += kLossThreads) s_dec_acc[o] = 0.f;
     const int blk = blockIdx.x;
     const int v = find_prefix(a.lv.pix_blk_off, a.lv.n, blk);
     const sg_view &vw = a.views[v];
@@ -296,7 +373,6 @@ __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
         const int lab = in ? a.label[p0 + p] : -1;
 #pragma unroll
         for (int c = 0; c < C; ++c) S[c] = in ? a.sem[(size_t)C * p0 + (size_t)c * HW + p] : 0.f;
-        float zmax = -INFINITY;
         if (has_dec) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -309,48 +385,57 @@ __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
 #pragma unroll
             for (int k = 0; k < K; ++k) z[k] = S[k < C ? k : 0];
         }
+        float zmax = -INFINITY;
 #pragma unroll
         for (int k = 0; k < K; ++k) zmax = fmaxf(zmax, z[k]);
-        float se = 0.f;
+        // z <- exp(z - max); softmax = z / sum
+        float se = 0.f, zl = 0.f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) se += expf(z[k] - zmax);
-        const float lse = zmax + logf(se);
+        for (int k = 0; k < K; ++k) {
+            if (k == lab) zl = z[k] - zmax;
+            z[k] = expf(z[k] - zmax);
+            se += z[k];
+        }
+        const float lse_rel = logf(se);   // log-sum-exp minus zmax
+        const bool valid = in && lab >= 0;
+        if (valid) ce = lse_rel - zl;
+        const float sc = valid ? a.w_sem / (float)nl : 0.f;
+        const float inv = 1.f / se;
         float dS[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) dS[c] = 0.f;
-        const bool valid = in && lab >= 0;
-        const float sc = valid ? a.w_sem / (float)nl : 0.f;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float pk = expf(z[k] - lse);
-            const float dz = sc * (pk - (k == lab ? 1.f : 0.f));
-            if (valid && k == lab) ce = lse - z[k];
+            const float dz = sc * (z[k] * inv - (k == lab ? 1.f : 0.f));
+            z[k] = dz;
             if (has_dec) {
 #pragma unroll
                 for (int c = 0; c < C; ++c) dS[c] = fmaf(s_dec[k * C + c], dz, dS[c]);
             } else if (k < C) {
                 dS[k] = dz;
             }
-            if (a.decoder_grad) s_dz[threadIdx.x * K + k] = dz;
         }
         if (in)
 #pragma unroll
             for (int c = 0; c < C; ++c) a.g_sem[(size_t)C * p0 + (size_t)c * HW + p] = dS[c];
         if (a.decoder_grad) {
+            float4 *dz4 = reinterpret_cast<float4 *>(s_dz + threadIdx.x * KP);
+            float4 *S4 = reinterpret_cast<float4 *>(s_S + threadIdx.x * CP);
 #pragma unroll
-            for (int c = 0; c < C; ++c) s_S[threadIdx.x * C + c] = S[c];
-            float *s_dec_acc = s_S + kLossThreads * C;  // K x C
-            for (int o = threadIdx.x; o < K * C; o += kLossThreads) s_dec_acc[o] = 0.f;
-            __syncthreads();
+            for (int k = 0; k < K; k += 4) dz4[k / 4] = make_float4(z[k], z[k + 1], z[k + 2], z[k + 3]);
+#pragma unroll
+            for (int c = 0; c < C; c += 4) S4[c / 4] = make_float4(S[c], S[c + 1], S[c + 2], S[c + 3]);
+            __syncwarp();
             // this warp's 32 pixels: each lane accumulates 4 x 4 blocks of dz_p S_p^T in registers
             const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
             constexpr int KB = K / 4, CB = C / 4;
             for (int blk4 = lane; blk4 < KB * CB; blk4 += 32) {
                 const int k0 = (blk4 / CB) * 4, c0 = (blk4 % CB) * 4;
                 float acc[4][4] = {};
+#pragma unroll 4
                 for (int t = warp * 32; t < warp * 32 + 32; ++t) {
-                    const float4 dz = *reinterpret_cast<const float4 *>(s_dz + t * K + k0);
-                    const float4 sv = *reinterpret_cast<const float4 *>(s_S + t * C + c0);
+                    const float4 dz = *reinterpret_cast<const float4 *>(s_dz + t * KP + k0);
+                    const float4 sv = *reinterpret_cast<const float4 *>(s_S + t * CP + c0);
                     const float dzv[4] = {dz.x, dz.y, dz.z, dz.w}, svv[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
@@ -444,7 +529,7 @@ __global__ void loss_finalize_kernel(FinalArgs a) {
 
 // ---------------------------------------------------------------------------------------
 
-static size_t ssim_smem() { return sizeof(float) * (2 * kXH * kXW + 5 * kXH * kMW + 3 * kMH * kMW); }
+static size_t ssim_smem() { return sizeof(float) * (2 * kXH * kXP + 5 * kXH * kMP + 3 * kMH * kMP); }
 
 static void make_loss_views(const sg_view *vh, int n_views, LossViews &lv) {
     lv.n = n_views;
@@ -480,11 +565,11 @@ size_t loss_workspace_size(const sg_view *vh, int n_views, int C, int n_classes)
 
 template <int C, int K>
 static void launch_pixel_t(PixelArgs &pa, int blocks, cudaStream_t st) {
-    const size_t dyn = pa.decoder_grad ? sizeof(float) * (kLossThreads * (K + C) + K * C) : 0;
+    const size_t full = sizeof(float) * (kLossThreads * (stash_pitch<K>() + stash_pitch<C>()) + K * C);
+    const size_t dyn = pa.decoder_grad ? full : 0;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(loss_pixel_kernel<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(float) * (kLossThreads * (K + C) + K * C)));
+        cudaFuncSetAttribute(loss_pixel_kernel<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
         attr = true;
     }
     loss_pixel_kernel<C, K><<<blocks, kLossThreads, dyn, st>>>(pa);

@@ -222,43 +222,44 @@ def test_pyramid_build_matches_oracle():
             assert np.array_equal(r.view_slice(gt["label"], v, 1)[0].cpu().numpy(), ref[l][2])
 
 
-@pytest.mark.parametrize("mode", ["ce", "ce_decoder", "paper"])
+@pytest.mark.parametrize("mode", ["ce", "ce_decoder", "ce_decoder32", "paper"])
 def test_loss_matches_oracle(mode):
     from paper_2412_01217_gb300 import LossConfig
     rng = np.random.default_rng(5)
-    room, g, cams = room_small(ncam=2, W=100, H=70, C=8)
+    Cs, K = (16, 32) if mode == "ce_decoder32" else (8, 8)
+    room, g, cams = room_small(ncam=2, W=100, H=70, C=Cs)
     r, p = make(g, cams, levels=2)
     P = r.P
     rend = (torch.tensor(rng.uniform(size=3 * P), dtype=torch.float32, device="cuda"),
             torch.tensor(rng.uniform(1, 3, size=P), dtype=torch.float32, device="cuda"),
-            torch.tensor(rng.normal(size=8 * P), dtype=torch.float32, device="cuda"))
+            torch.tensor(rng.normal(size=Cs * P), dtype=torch.float32, device="cuda"))
     gdepth = rng.uniform(1, 3, size=P)
     gdepth[rng.uniform(size=P) < 0.2] = 0.0
     gt = dict(rgb=torch.tensor(rng.uniform(size=3 * P), dtype=torch.float32, device="cuda"),
               depth=torch.tensor(gdepth, dtype=torch.float32, device="cuda"),
-              label=torch.tensor(rng.integers(-1, 8, size=P), dtype=torch.int32, device="cuda"),
-              sem=torch.tensor(rng.uniform(size=8 * P), dtype=torch.float32, device="cuda"))
+              label=torch.tensor(rng.integers(-1, K, size=P), dtype=torch.int32, device="cuda"),
+              sem=torch.tensor(rng.uniform(size=Cs * P), dtype=torch.float32, device="cuda"))
     dec = dgrad = None
-    if mode == "ce_decoder":
-        dec = torch.tensor(rng.normal(size=(8, 8)), dtype=torch.float32, device="cuda")
+    if mode.startswith("ce_decoder"):
+        dec = torch.tensor(rng.normal(size=(K, Cs)) * 0.5, dtype=torch.float32, device="cuda")
         dgrad = torch.zeros_like(dec)
-    lc = LossConfig(sem_mode="paper" if mode == "paper" else "ce", n_classes=8)
+    lc = LossConfig(sem_mode="paper" if mode == "paper" else "ce", n_classes=K)
     r.loss(gt, rendered=rend, decoder=dec, decoder_grad=dgrad, loss_cfg=lc)
     torch.cuda.synchronize()
     terms = r.terms.view(-1, 4).cpu().numpy()
-    dec_ref_total = np.zeros((8, 8))
+    dec_ref_total = np.zeros((K, Cs))
     for v in range(r.V):
         sl = lambda t, n: r.view_slice(t, v, n).cpu().numpy().astype(np.float64)
-        tot, tm, gr = oracle.level_loss(sl(rend[0], 3), sl(rend[1], 1)[0], sl(rend[2], 8), sl(gt["rgb"], 3),
+        tot, tm, gr = oracle.level_loss(sl(rend[0], 3), sl(rend[1], 1)[0], sl(rend[2], Cs), sl(gt["rgb"], 3),
                                         sl(gt["depth"], 1)[0],
-                                        sl(gt["sem"], 8) if mode == "paper" else r.view_slice(gt["label"], v, 1)[0].cpu().numpy(),
+                                        sl(gt["sem"], Cs) if mode == "paper" else r.view_slice(gt["label"], v, 1)[0].cpu().numpy(),
                                         sem_mode="paper" if mode == "paper" else "ce",
                                         decoder=dec.cpu().numpy() if dec is not None else None)
         assert terms[v, 0] == pytest.approx(tm["L_r"], rel=1e-5)
         assert terms[v, 1] == pytest.approx(tm["L_d"], rel=1e-5)
         assert terms[v, 2] == pytest.approx(tm["L_s"], rel=1e-5)
         assert terms[v, 3] == pytest.approx(tot, rel=1e-5)
-        for name, buf, n in (("rgb", r.dL_rgb, 3), ("depth", r.dL_depth, 1), ("sem", r.dL_sem, 8)):
+        for name, buf, n in (("rgb", r.dL_rgb, 3), ("depth", r.dL_depth, 1), ("sem", r.dL_sem, Cs)):
             got = r.view_slice(buf, v, n).cpu().numpy()
             ref = gr[name].reshape(got.shape)
             check_close(f"dL/d{name} v{v}", got, ref, 1e-4, 1e-4 * np.abs(ref).max())
