@@ -313,7 +313,7 @@ def run_ours(args):
         gt0 = build_pyramid(probe, [frame["rgb"]], [frame["depth"]], [frame["label"]])
         del probe
         cfg, tune_table = autotune(p, [cam], 3, gt0, LossConfig(n_classes=32), base=cfg, decoder=decoder,
-                                   use_cache=False)
+                                   use_cache=False, log=lambda m: print("autotune:", m, file=sys.stderr))
         del gt0
         torch.cuda.empty_cache()
     r = PyramidRasterizer(args.gaussians, 16, [cam], levels=3, cfg=cfg,

@@ -130,6 +130,11 @@ typedef struct {
     uint32_t *record; /* K_cap: record id v*N+g; within a tile by (depth, record id)     */
     int32_t *ranges;  /* n_tiles x 2: [start, end) of each tile's instances              */
     int32_t *count;   /* device scalar: K = instances emitted (may exceed capacity)      */
+    int32_t *order;   /* n_tiles or NULL: every tile id once, by descending instance count
+                         in power-of-two half-octave buckets (ascending id within a
+                         bucket); the compositing kernels take tiles in this order, so the
+                         longest lists start first and the short ones fill the tail.  NULL:
+                         tiles in id order.                                             */
 } sg_tile_lists;
 
 /* Rendered images (all view-levels packed, planar). */

@@ -46,7 +46,7 @@ class SgProjected(C.Structure):
 
 
 class SgTileLists(C.Structure):
-    _fields_ = [("capacity", c_i), ("tile", c_p), ("record", c_p), ("ranges", c_p), ("count", c_p)]
+    _fields_ = [("capacity", c_i), ("tile", c_p), ("record", c_p), ("ranges", c_p), ("count", c_p), ("order", c_p)]
 
 
 class SgImages(C.Structure):

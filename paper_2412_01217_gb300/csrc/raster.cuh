@@ -11,6 +11,7 @@ struct RasterArgs {
     const float2 *ext;
     const uint32_t *record;
     const int2 *ranges;
+    const int *order;  // work order of the tiles (null: id order)
     const float *rgb;
     const float *sem;
     const sg_view *views;
@@ -37,6 +38,7 @@ inline void fill_raster_args(RasterArgs &a, const sg_gaussians *g, const sg_proj
     a.ext = reinterpret_cast<const float2 *>(proj->ext);
     a.record = lists->record;
     a.ranges = reinterpret_cast<const int2 *>(lists->ranges);
+    a.order = lists->order;
     a.rgb = g->rgb;
     a.sem = g->sem;
     a.views = views;

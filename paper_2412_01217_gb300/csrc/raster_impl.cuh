@@ -17,9 +17,12 @@
 //
 // Backward: back to front from the tile's largest `last`.  Each pixel rebuilds T by
 // dividing by (1 - alpha) and tracks only the scalar a = g . A of the background-weighted
-// suffix colour A.  A thread sums its pixels' 10 + C partial gradients of a Gaussian; the
-// warp then adds its 32 lanes with a lane-transposed butterfly (NV - 1 shuffles for NV
-// values) and issues one warp-wide set of atomics.
+// suffix colour A.  The 6 geometric partials of a Gaussian (2D mean, conic, opacity) are
+// summed per thread over its pixels and over the warp by an 8-value lane-transposed
+// butterfly (9 shuffles).  The 4 + C feature gradients (colour, depth, semantics) are a
+// contraction, dF = W^T G over the warp's pixels: every lane writes its weights w = alpha T
+// into a 16-Gaussian chunk buffer, and each full chunk goes through the tensor cores
+// (mma.m16n8k8, TF32 split into hi + lo parts for FP32-level accuracy).
 #pragma once
 
 #include "raster.cuh"
@@ -119,8 +122,9 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
     const float fx = (float)wt.lx;
     for (int iter = 0;; ++iter) {
         if (!a.persistent && iter > 0) break;
-        const int item = next_item(a, s_item);
-        if (item >= a.n_tiles) break;
+        const int slot = next_item(a, s_item);
+        if (slot >= a.n_tiles) break;
+        const int item = a.order ? a.order[slot] : slot;  // tile id
         const TileInfo ti = tile_info(a, item);
         const sg_view &vw = *ti.vw;
         const int px = ti.px0 + wt.lx;
@@ -212,17 +216,105 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
     }
 }
 
-template <int X>
-struct NextPow2 {
-    static constexpr int v = X <= 32 ? 32 : (X <= 64 ? 64 : (X <= 128 ? 128 : 256));
-};
+// ---------------------------------------------------------------------------------------
+// Backward helpers
+// ---------------------------------------------------------------------------------------
+
+// The backward works on chunks of 16 consecutive list entries.  Three of its sums are
+// contractions over the warp's pixels and run on the tensor cores (mma.m16n8k8, TF32
+// operands split as x = hi + lo, hi = x with its 13 low mantissa bits cleared, lo = x - hi
+// exactly; hi*hi + hi*lo + lo*hi keeps about 22 mantissa bits of every product, i.e.
+// FP32-level accuracy):
+//   gf[p][r] = sum_f g[p][f] F[r][f]          (pixel gradient . Gaussian features)
+//   dF[r][f] = sum_p w[p][r] g[p][f]          (colour / depth / semantic gradients)
+//   M[r][m]  = sum_p s[p][r] P_m(X_p, Y_p)    (moments of s = dL/dsigma)
+// with w = alpha T and P = (1, X, Y, X^2, XY, Y^2) the pixel offsets from the warp centre.
+// The 2D-mean, conic and opacity gradients are linear in the moments (see moment_grads).
+constexpr int kChunk = 16;
+
+template <int NPX>
+__host__ __device__ constexpr int chunk_pitch() { return NPX + 4; }  // 4 mod 32: conflict-free fragments
+
+template <int NF>
+__host__ __device__ constexpr int padded_features() { return (NF + 7) / 8 * 8; }
+
+template <int NF>
+__host__ __device__ constexpr int g_pitch() { return padded_features<NF>() + 4; }  // odd multiple of 4
+
+// shared memory of one warp: G (NPX x g_pitch) and two chunk buffers (16 x chunk_pitch)
+template <int C, int PPT>
+__host__ __device__ constexpr int bwd_warp_floats() {
+    return 32 * PPT * g_pitch<4 + C>() + 2 * kChunk * chunk_pitch<32 * PPT>();
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    const uint32_t h = __float_as_uint(x) & 0xffffe000u;
+    hi = h;
+    lo = __float_as_uint(x - __uint_as_float(h));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// a * b with both split (3 MMAs, small terms first)
+__device__ __forceinline__ void mma_tf32x3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                           uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+    mma_tf32(d, al, bh0, bh1);
+    mma_tf32(d, ah, bl0, bl1);
+    mma_tf32(d, ah, bh0, bh1);
+}
+
+// A fragment (16 x 8, row-major, pitch ld) at column k0: a0 (gid, tig), a1 (gid + 8, tig),
+// a2 (gid, tig + 4), a3 (gid + 8, tig + 4); rows outside `keep` read as zero.
+__device__ __forceinline__ void load_a_split(const float *m, int ld, int k0, int gid, int tig, bool keep0,
+                                             bool keep1, uint32_t (&ah)[4], uint32_t (&al)[4]) {
+    const float *p = m + gid * ld + k0 + tig;
+    const float v[4] = {keep0 ? p[0] : 0.f, keep1 ? p[8 * ld] : 0.f, keep0 ? p[4] : 0.f, keep1 ? p[8 * ld + 4] : 0.f};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) split_tf32(v[i], ah[i], al[i]);
+}
+
+// Gradients of the 2D mean (u, v), the conic (a, b, c) and the opacity from the moments
+// M = (sum s, sum s X, sum s Y, sum s X^2, sum s XY, sum s Y^2) of s = dL/dsigma over the
+// pixels (X, Y offsets from the warp centre; U, V the mean's offset from it, so that
+// dx = X - U, dy = Y - V).  With sigma = p1^2 + p2^2, p1 = m00 dx, p2 = m10 dx + m11 dy:
+//   dL/du = -2 ((m00^2 + m10^2) S_x + m10 m11 S_y),  dL/dv = -2 (m10 m11 S_x + m11^2 S_y),
+//   dL/d(a, b, c) = (S_xx / 2, S_xy, S_yy / 2),       dL/do = -S_1 / o,
+// S_x = sum s dx, S_xx = sum s dx^2, ...; the last because s = -dL/dalpha alpha and
+// dalpha/do = alpha / o wherever s is non-zero (alpha not clamped).  `part` (0..2) picks
+// the pair this lane writes.
+__device__ __forceinline__ void moment_grads(const float (&M)[6], float U, float V, const float4 &g1, int part,
+                                             float &r0, float &r1) {
+    const float M0 = M[0], Mx = M[1], My = M[2], Mxx = M[3], Mxy = M[4], Myy = M[5];
+    if (part == 0) {
+        const float Sx = fmaf(-U, M0, Mx), Sy = fmaf(-V, M0, My);
+        const float m00 = g1.x, m10 = g1.y, m11 = g1.z;
+        r0 = -2.f * ((m00 * m00 + m10 * m10) * Sx + m10 * m11 * Sy);
+        r1 = -2.f * (m10 * m11 * Sx + m11 * m11 * Sy);
+    } else if (part == 1) {
+        r0 = 0.5f * (Mxx - 2.f * U * Mx + U * U * M0);
+        r1 = Mxy - V * Mx - U * My + U * V * M0;
+    } else {
+        r0 = 0.5f * (Myy - 2.f * V * My + V * V * M0);
+        r1 = -M0 / g1.w;
+    }
+}
 
 template <int C, int PPT>
 __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs a) {
-    constexpr int NF = 4 + C;
-    constexpr int NRAW = 10 + C;  // u v ca cb cc o depth | rgb(3) | sem(C)
-    constexpr int NV = NextPow2<NRAW>::v;
-    constexpr int PER = NV / 32;
+    constexpr int NF = 4 + C;                     // rgb(3) depth | sem(C)
+    constexpr int NFP = padded_features<NF>();    // features padded to 8
+    constexpr int NT = NFP / 8;                   // 8-feature tiles
+    constexpr int NPX = 32 * PPT;                 // pixels of one warp (pixel q = 32 k + lane)
+    constexpr int KS = NPX / 8;                   // 8-pixel steps
+    constexpr int MT = NPX / 16;                  // 16-pixel tiles
+    constexpr int WQ = chunk_pitch<NPX>();
+    constexpr int GP = g_pitch<NF>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item, s_max_last;
     const int batch = a.batch;
@@ -232,13 +324,27 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
     float *s_feat = reinterpret_cast<float *>(s_geo2 + batch);
     uint32_t *s_rec = reinterpret_cast<uint32_t *>(s_feat + (size_t)batch * NF);
     const int nthreads = a.tile_w * a.tile_h / PPT;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *s_G = reinterpret_cast<float *>(s_rec + batch) + (size_t)warp * bwd_warp_floats<C, PPT>();
+    float *s_gw = s_G + NPX * GP;     // per chunk row: gf, then overwritten with w = alpha T
+    float *s_sg = s_gw + kChunk * WQ; // per chunk row: s = dL/dsigma
+    const int gid = lane >> 2, tig = lane & 3;
     const WarpTile<PPT> wt(a.tile_w);
     const float fx = (float)wt.lx;
+    // moment polynomials at the B-fragment pixels: pixel 8 ks + tig (+ 4) has X = tig - 3.5
+    // (tig + 0.5), Y = (ks % 4) + 4 (ks / 4) - (2 PPT - 0.5); P_gid = P0 + Y (P1 + Y P2)
+    // (all values small multiples of 1/4: exact in TF32, so B needs no split)
+    const float X0 = tig - 3.5f, X1 = tig + 0.5f;
+    const float P0a = gid == 0 ? 1.f : gid == 1 ? X0 : gid == 3 ? X0 * X0 : 0.f;
+    const float P0b = gid == 0 ? 1.f : gid == 1 ? X1 : gid == 3 ? X1 * X1 : 0.f;
+    const float P1a = gid == 2 ? 1.f : gid == 4 ? X0 : 0.f;
+    const float P1b = gid == 2 ? 1.f : gid == 4 ? X1 : 0.f;
+    const float P2 = gid == 5 ? 1.f : 0.f;
     for (int iter = 0;; ++iter) {
         if (!a.persistent && iter > 0) break;
-        const int item = next_item(a, s_item);
-        if (item >= a.n_tiles) break;
+        const int slot = next_item(a, s_item);
+        if (slot >= a.n_tiles) break;
+        const int item = a.order ? a.order[slot] : slot;  // tile id
         const TileInfo ti = tile_info(a, item);
         const sg_view &vw = *ti.vw;
         const int px = ti.px0 + wt.lx;
@@ -246,7 +352,6 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
         const size_t HW = (size_t)vw.W * vw.H;
         const size_t p0 = (size_t)vw.pixel_offset;
         const uint32_t rec_base = (uint32_t)ti.v * (uint32_t)a.N;
-        float g[PPT][NF];
         float T[PPT], acc_a[PPT];
         int my_last[PPT];
         int thread_last = 0;
@@ -255,24 +360,26 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
             const int py = ti.py0 + wt.ly + 4 * k;
             const bool inside = px < vw.W && py < vw.H;
             const size_t p = (size_t)py * vw.W + px;
-            if (inside) {
-                g[k][0] = a.dL_rgb[3 * p0 + p];
-                g[k][1] = a.dL_rgb[3 * p0 + HW + p];
-                g[k][2] = a.dL_rgb[3 * p0 + 2 * HW + p];
-                g[k][3] = a.dL_depth[p0 + p];
+            float g[NFP];
 #pragma unroll
-                for (int c = 0; c < C; ++c) g[k][4 + c] = a.dL_sem[(size_t)C * p0 + c * HW + p];
+            for (int f = 0; f < NFP; ++f) g[f] = 0.f;
+            T[k] = 1.f;
+            my_last[k] = 0;
+            if (inside) {
+                g[0] = a.dL_rgb[3 * p0 + p];
+                g[1] = a.dL_rgb[3 * p0 + HW + p];
+                g[2] = a.dL_rgb[3 * p0 + 2 * HW + p];
+                g[3] = a.dL_depth[p0 + p];
+#pragma unroll
+                for (int c = 0; c < C; ++c) g[4 + c] = a.dL_sem[(size_t)C * p0 + c * HW + p];
                 T[k] = a.T_final[p0 + p];
                 my_last[k] = a.last[p0 + p];
-                acc_a[k] = g[k][0] * a.bg0 + g[k][1] * a.bg1 + g[k][2] * a.bg2;
-            } else {
-#pragma unroll
-                for (int c = 0; c < NF; ++c) g[k][c] = 0.f;
-                T[k] = 1.f;
-                my_last[k] = 0;
-                acc_a[k] = 0.f;
             }
+            acc_a[k] = g[0] * a.bg0 + g[1] * a.bg1 + g[2] * a.bg2;
             thread_last = max(thread_last, my_last[k]);
+            float4 *row = reinterpret_cast<float4 *>(s_G + (32 * k + lane) * GP);
+#pragma unroll
+            for (int f = 0; f < NFP; f += 4) row[f / 4] = make_float4(g[f], g[f + 1], g[f + 2], g[f + 3]);
         }
         const int warp_last = __reduce_max_sync(SG_FULL_MASK, thread_last);
         if (threadIdx.x == 0) s_max_last = 0;
@@ -289,81 +396,152 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
                            s_rec, nthreads);
             __syncthreads();
             const int jmax = min(cnt, warp_last - b0);  // warp-uniform
-            for (int j = jmax - 1; j >= 0; --j) {
-                if (wt.misses(s_geo2[j])) continue;  // warp-uniform
-                const float4 g0 = s_geo0[j];
-                const float4 g1 = s_geo1[j];
-                const int pos = b0 + j;
-                AlphaEval e[PPT];
-                bool hit[PPT];
-                bool any = false;
+            for (int jc0 = jmax > 0 ? (jmax - 1) & ~(kChunk - 1) : -kChunk; jc0 >= 0; jc0 -= kChunk) {
+                // entries of the chunk whose footprint reaches the warp (lane r tests entry jc0 + r)
+                bool cand = false;
+                if (lane < kChunk) cand = jc0 + lane < jmax && !wt.misses(s_geo2[jc0 + lane]);
+                uint32_t cmask = __ballot_sync(SG_FULL_MASK, cand);
+                if (!cmask) continue;
+                // ---- gf = G F^T for the chunk (M = pixels, N = entries, K = features) ----
+#pragma unroll 1
+                for (int mt = 0; mt < MT; ++mt) {
+                    float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    hit[k] = pos < my_last[k] &&
-                             eval_alpha(fx - g0.x, (float)(wt.ly + 4 * k) - g0.y, g0.z, g0.w, g1.x, g1.y, g1.z,
-                                        g1.w, a.alpha_max, a.alpha_min, e[k]);
-                    any |= hit[k];
-                }
-                if (!__any_sync(SG_FULL_MASK, any)) continue;
-                float vals[NV];
+                    for (int kk = 0; kk < NT; ++kk) {
+                        // B (8 x 8): b0 (tig, gid), b1 (tig + 4, gid) = F[entry][feature]
+                        const int f0 = 8 * kk + tig;
+                        uint32_t ah[4], al[4];
+                        load_a_split(s_G + 16 * mt * GP, GP, 8 * kk, gid, tig, true, true, ah, al);
 #pragma unroll
-                for (int q = 0; q < NV; ++q) vals[q] = 0.f;
-                if (any) {
-                    const float4 *f4 = reinterpret_cast<const float4 *>(s_feat + (size_t)j * NF);
-                    float gf[PPT];
-#pragma unroll
-                    for (int k = 0; k < PPT; ++k) gf[k] = 0.f;
-#pragma unroll
-                    for (int q = 0; q < NF / 4; ++q) {
-                        const float4 f = f4[q];
-#pragma unroll
-                        for (int k = 0; k < PPT; ++k) {
-                            gf[k] = fmaf(g[k][4 * q + 0], f.x, gf[k]);
-                            gf[k] = fmaf(g[k][4 * q + 1], f.y, gf[k]);
-                            gf[k] = fmaf(g[k][4 * q + 2], f.z, gf[k]);
-                            gf[k] = fmaf(g[k][4 * q + 3], f.w, gf[k]);
+                        for (int nt = 0; nt < 2; ++nt) {
+                            const float *fr = s_feat + (size_t)(jc0 + 8 * nt + gid) * NF;
+                            uint32_t bh0, bl0, bh1, bl1;
+                            split_tf32(f0 < NF ? fr[f0] : 0.f, bh0, bl0);
+                            split_tf32(f0 + 4 < NF ? fr[f0 + 4] : 0.f, bh1, bl1);
+                            mma_tf32x3(d[nt], ah, al, bh0, bh1, bl0, bl1);
                         }
                     }
+                    // D (16 x 8): d0 (gid, 2 tig), d1 (gid, 2 tig + 1), d2 (gid + 8, 2 tig), d3 (gid + 8, 2 tig + 1)
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            s_gw[(8 * nt + 2 * tig + (i & 1)) * WQ + 16 * mt + gid + 8 * (i >> 1)] = d[nt][i];
+                }
+                __syncwarp();
+                // ---- back to front over the candidates: T, dL/dalpha, w and s per pixel ----
+                uint32_t mask = 0;
+                while (cmask) {
+                    const int r = 31 - __clz(cmask);
+                    cmask &= ~(1u << r);
+                    const int j = jc0 + r;
+                    const float4 g0 = s_geo0[j];
+                    const float4 g1 = s_geo1[j];
+                    const int pos = b0 + j;
+                    AlphaEval e[PPT];
+                    bool hit[PPT];
+                    bool any = false;
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
-                        if (!hit[k]) continue;
-                        // transmittance before this Gaussian (only gradients depend on it)
-                        T[k] = __fdividef(T[k], __fsub_rn(1.f, e[k].alpha));
-                        const float dalpha = T[k] * (gf[k] - acc_a[k]);
-                        acc_a[k] = e[k].alpha * gf[k] + (1.f - e[k].alpha) * acc_a[k];
-                        const float w = e[k].alpha * T[k];
-                        vals[6] = fmaf(w, g[k][3], vals[6]);
-                        vals[7] = fmaf(w, g[k][0], vals[7]);
-                        vals[8] = fmaf(w, g[k][1], vals[8]);
-                        vals[9] = fmaf(w, g[k][2], vals[9]);
+                        hit[k] = pos < my_last[k] &&
+                                 eval_alpha(fx - g0.x, (float)(wt.ly + 4 * k) - g0.y, g0.z, g0.w, g1.x, g1.y, g1.z,
+                                            g1.w, a.alpha_max, a.alpha_min, e[k]);
+                        any |= hit[k];
+                    }
+                    if (!__any_sync(SG_FULL_MASK, any)) continue;
+                    mask |= 1u << r;
 #pragma unroll
-                        for (int c = 0; c < C; ++c) vals[10 + c] = fmaf(w, g[k][4 + c], vals[10 + c]);
-                        if (e[k].raw < a.alpha_max) {
-                            // sigma = p1^2 + p2^2, p1 = m00 dx, p2 = m10 dx + m11 dy; d(dx)/du = -1;
-                            // d sigma / d(conic a, b, c) = (dx^2/2, dx dy, dy^2/2)
-                            const float gsig = -dalpha * e[k].raw;
-                            vals[0] -= 2.f * gsig * (e[k].p1 * g1.x + e[k].p2 * g1.y);
-                            vals[1] -= 2.f * gsig * (e[k].p2 * g1.z);
-                            vals[2] += 0.5f * gsig * e[k].dx * e[k].dx;
-                            vals[3] += gsig * e[k].dx * e[k].dy;
-                            vals[4] += 0.5f * gsig * e[k].dy * e[k].dy;
-                            vals[5] += dalpha * e[k].G;
+                    for (int k = 0; k < PPT; ++k) {
+                        float *gw = s_gw + r * WQ + 32 * k + lane;
+                        float w = 0.f, sg = 0.f;
+                        if (hit[k]) {
+                            const float gf = *gw;
+                            // transmittance before this Gaussian (only gradients depend on it)
+                            T[k] = __fdividef(T[k], __fsub_rn(1.f, e[k].alpha));
+                            const float dalpha = T[k] * (gf - acc_a[k]);
+                            acc_a[k] = e[k].alpha * gf + (1.f - e[k].alpha) * acc_a[k];
+                            w = e[k].alpha * T[k];
+                            if (e[k].raw < a.alpha_max) sg = -dalpha * e[k].raw;
+                        }
+                        *gw = w;
+                        s_sg[r * WQ + 32 * k + lane] = sg;
+                    }
+                }
+                if (!mask) continue;  // (warp-uniform)
+                __syncwarp();
+                // ---- dF = W G (M = entries, N = features, K = pixels), moments M = S P ----
+                const bool keep0 = (mask >> gid) & 1u, keep1 = (mask >> (gid + 8)) & 1u;
+                float df[NT][4], mom[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) df[nt][0] = df[nt][1] = df[nt][2] = df[nt][3] = 0.f;
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks) {
+                    uint32_t ah[4], al[4];
+                    load_a_split(s_gw, WQ, 8 * ks, gid, tig, keep0, keep1, ah, al);
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) {
+                        // B (8 x 8): b0 (tig, gid), b1 (tig + 4, gid) = G[pixel][feature]
+                        const float *gp = s_G + (8 * ks + tig) * GP + 8 * nt + gid;
+                        uint32_t bh0, bl0, bh1, bl1;
+                        split_tf32(gp[0], bh0, bl0);
+                        split_tf32(gp[4 * GP], bh1, bl1);
+                        mma_tf32x3(df[nt], ah, al, bh0, bh1, bl0, bl1);
+                    }
+                    load_a_split(s_sg, WQ, 8 * ks, gid, tig, keep0, keep1, ah, al);
+                    const float Y = (float)((ks & 3) + 4 * (ks >> 2)) - (2.f * PPT - 0.5f);
+                    const uint32_t pb0 = __float_as_uint(fmaf(Y, fmaf(Y, P2, P1a), P0a));
+                    const uint32_t pb1 = __float_as_uint(fmaf(Y, fmaf(Y, P2, P1b), P0b));
+                    mma_tf32(mom, al, pb0, pb1);
+                    mma_tf32(mom, ah, pb0, pb1);
+                }
+                // feature gradients: D rows gid, gid + 8 (entries), columns 2 tig, 2 tig + 1 (features)
+#pragma unroll
+                for (int hr = 0; hr < 2; ++hr) {
+                    if (!(hr ? keep1 : keep0)) continue;
+                    const uint32_t rec = s_rec[jc0 + gid + 8 * hr];
+                    const uint32_t gi = rec - rec_base;
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) {
+#pragma unroll
+                        for (int c2 = 0; c2 < 2; ++c2) {
+                            const int f = 8 * nt + 2 * tig + c2;
+                            const float val = df[nt][2 * hr + c2];
+                            if (f >= NF) continue;
+                            if (f < 3)
+                                atomicAdd(a.g_rgb + 3 * (size_t)gi + f, val);
+                            else if (f == 3)
+                                atomicAdd(a.g2d + 8 * (size_t)rec + 6, val);
+                            else
+                                atomicAdd(a.g_sem + (size_t)C * gi + (f - 4), val);
                         }
                     }
                 }
-                warp_transpose_reduce<NV>(vals, lane);
-                const uint32_t rec = s_rec[j];
-                const uint32_t gi = rec - rec_base;
+                // geometric gradients: lane tig of a quad holds moments (2 tig, 2 tig + 1) of its rows
+                float Mr[2][6];
 #pragma unroll
-                for (int q = 0; q < PER; ++q) {
-                    const int idx = lane * PER + q;
-                    if (idx < 7)
-                        atomicAdd(a.g2d + 8 * (size_t)rec + idx, vals[q]);
-                    else if (idx < 10)
-                        atomicAdd(a.g_rgb + 3 * (size_t)gi + (idx - 7), vals[q]);
-                    else if (idx < NRAW)
-                        atomicAdd(a.g_sem + (size_t)C * gi + (idx - 10), vals[q]);
+                for (int t = 0; t < 3; ++t) {
+                    const int src = (lane & ~3) | t;
+                    Mr[0][2 * t] = __shfl_sync(SG_FULL_MASK, mom[0], src);
+                    Mr[0][2 * t + 1] = __shfl_sync(SG_FULL_MASK, mom[1], src);
+                    Mr[1][2 * t] = __shfl_sync(SG_FULL_MASK, mom[2], src);
+                    Mr[1][2 * t + 1] = __shfl_sync(SG_FULL_MASK, mom[3], src);
                 }
+                if (tig < 3) {
+#pragma unroll
+                    for (int hr = 0; hr < 2; ++hr) {
+                        if (!(hr ? keep1 : keep0)) continue;
+                        const int j = jc0 + gid + 8 * hr;
+                        const float4 g0 = s_geo0[j];
+                        const float4 g1 = s_geo1[j];
+                        const float U = (g0.x - wt.cxw) + g0.z, V = (g0.y - wt.cyw) + g0.w;
+                        float r0, r1;
+                        moment_grads(Mr[hr], U, V, g1, tig, r0, r1);
+                        float *dst = a.g2d + 8 * (size_t)s_rec[j] + 2 * tig;
+                        atomicAdd(dst, r0);
+                        atomicAdd(dst + 1, r1);
+                    }
+                }
+                __syncwarp();  // the chunk buffers are rewritten next
             }
         }
         __syncthreads();
@@ -376,9 +554,9 @@ template <int C>
 inline size_t fwd_smem(int batch) {
     return (size_t)batch * (3 * 16 + 4 * (4 + C));
 }
-template <int C>
-inline size_t bwd_smem(int batch) {
-    return fwd_smem<C>(batch) + (size_t)batch * 4;
+template <int C, int PPT>
+inline size_t bwd_smem(int batch, int threads) {
+    return fwd_smem<C>(batch) + (size_t)batch * 4 + sizeof(float) * (threads / 32) * bwd_warp_floats<C, PPT>();
 }
 
 inline int resident_grid(const void *fn, int threads, size_t smem) {
@@ -393,7 +571,7 @@ inline int resident_grid(const void *fn, int threads, size_t smem) {
 template <int C, int PPT>
 sg_status launch_raster_cp(RasterArgs &a, bool backward, cudaStream_t st) {
     const int threads = a.tile_w * a.tile_h / PPT;
-    const size_t smem = backward ? bwd_smem<C>(a.batch) : fwd_smem<C>(a.batch);
+    const size_t smem = backward ? bwd_smem<C, PPT>(a.batch, threads) : fwd_smem<C>(a.batch);
     const void *fn = backward ? (const void *)raster_bwd_kernel<C, PPT> : (const void *)raster_fwd_kernel<C, PPT>;
     static size_t configured[2] = {0, 0};
     if (smem > 48 * 1024 && configured[backward] < smem) {

@@ -186,16 +186,38 @@ __global__ void emit_apply_kernel(const uint2 *__restrict__ rect, const uint32_t
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits (or fewer).
 // ---------------------------------------------------------------------------------------
 
-__global__ void rs_hist_kernel(const uint32_t *__restrict__ keys, const int *__restrict__ n_ptr,
-                               int cap, int shift, uint32_t mask, uint32_t *__restrict__ hist, int G) {
+// Key sources of the radix sort: pairs held in arrays, or the tiles' list lengths.
+struct ArrayPairs {
+    const uint32_t *k, *v;
+    __device__ uint32_t key(int i) const { return k[i]; }
+    __device__ uint32_t val(int i) const { return v[i]; }
+};
+// key = 63 - bucket of the tile's instance count n (bucket 0 for n = 0, else
+// 1 + 2 floor(log2 n) + the bit below the leading one): descending length, 6 bits
+struct TileLengthKeys {
+    const int2 *ranges;
+    __device__ uint32_t key(int i) const {
+        const int2 r = ranges[i];
+        const uint32_t n = (uint32_t)max(r.y - r.x, 0);
+        if (n == 0) return 63u;
+        const int lz = 31 - __clz(n);
+        const uint32_t sub = lz >= 1 ? (n >> (lz - 1)) & 1u : 0u;
+        return 63u - (1u + 2u * (uint32_t)lz + sub);
+    }
+    __device__ uint32_t val(int i) const { return (uint32_t)i; }
+};
+
+template <class Src>
+__global__ void rs_hist_kernel(Src src, const int *__restrict__ n_ptr, int cap, int shift, uint32_t mask,
+                               uint32_t *__restrict__ hist, int G) {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
-    const int n = min(*n_ptr, cap);
+    const int n = n_ptr ? min(*n_ptr, cap) : cap;
     int beg, end;
     block_range(n, G, blockIdx.x, beg, end);
     for (int i = beg + threadIdx.x; i < end; i += kScanThreads)
-        atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+        atomicAdd(&h[(src.key(i) >> shift) & mask], 1u);
     __syncthreads();
     hist[threadIdx.x * G + blockIdx.x] = h[threadIdx.x];
 }
@@ -215,8 +237,9 @@ __global__ void rs_digit_scan_kernel(uint32_t *__restrict__ hist, uint32_t *__re
     if (threadIdx.x == 0) totals[d] = run;
 }
 
+template <class Src>
 __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
-    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+    Src src, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ n_ptr, int cap, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, int G) {
     constexpr int kWarps = kScanThreads / 32;
@@ -229,7 +252,7 @@ __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
         const uint32_t ex = block_exclusive_scan(totals[tid], tot);
         run[tid] = ex + hist[tid * G + blockIdx.x];
     }
-    const int n = min(*n_ptr, cap);
+    const int n = n_ptr ? min(*n_ptr, cap) : cap;
     int beg, end;
     block_range(n, G, blockIdx.x, beg, end);
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -239,7 +262,7 @@ __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
         __syncthreads();
         const int i = base + tid;
         const bool valid = i < end;
-        const uint32_t key = valid ? kin[i] : 0u;
+        const uint32_t key = valid ? src.key(i) : 0u;
         const uint32_t d = valid ? ((key >> shift) & mask) : 256u;
         const uint32_t peers = __match_any_sync(SG_FULL_MASK, d);
         const uint32_t rank = __popc(peers & lt_mask);
@@ -255,8 +278,8 @@ __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
         __syncthreads();
         if (valid) {
             const uint32_t pos = run[d] + wcnt[warp][d] + rank;
-            kout[pos] = key;
-            vout[pos] = vin[i];
+            if (kout) kout[pos] = key;
+            vout[pos] = src.val(i);
         }
         __syncthreads();
         run[tid] += s;
@@ -276,10 +299,10 @@ static void radix_sort(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
         const uint32_t mask = (1u << nb) - 1u;
         uint32_t *kd = ((passes - 1 - p) % 2 == 0) ? kout : ktmp;
         uint32_t *vd = ((passes - 1 - p) % 2 == 0) ? vout : vtmp;
-        rs_hist_kernel<<<G, kScanThreads, 0, st>>>(ks, n_ptr, cap, shift, mask, hist, G);
+        const ArrayPairs src{ks, vs};
+        rs_hist_kernel<<<G, kScanThreads, 0, st>>>(src, n_ptr, cap, shift, mask, hist, G);
         rs_digit_scan_kernel<<<256, kScanThreads, 0, st>>>(hist, totals, G);
-        rs_scatter_kernel<<<G, kScanThreads, 0, st>>>(ks, vs, kd, vd, n_ptr, cap, shift, mask, hist,
-                                                      totals, G);
+        rs_scatter_kernel<<<G, kScanThreads, 0, st>>>(src, kd, vd, n_ptr, cap, shift, mask, hist, totals, G);
         count_launches(3);
         ks = kd;
         vs = vd;
@@ -392,6 +415,15 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     ranges_kernel<<<G, kScanThreads, 0, st>>>(lists->tile, w.counts + 1,
                                               reinterpret_cast<int2 *>(lists->ranges));
     count_launches(3 + 3 + 2);  // compaction, emission, clamp + ranges
+    // 6. work order: one stable counting pass over the 6-bit length keys
+    if (lists->order) {
+        const TileLengthKeys src{reinterpret_cast<const int2 *>(lists->ranges)};
+        rs_hist_kernel<<<G, kScanThreads, 0, st>>>(src, nullptr, n_tiles, 0, 63u, w.hist, G);
+        rs_digit_scan_kernel<<<256, kScanThreads, 0, st>>>(w.hist, w.totals, G);
+        rs_scatter_kernel<<<G, kScanThreads, 0, st>>>(src, nullptr, reinterpret_cast<uint32_t *>(lists->order),
+                                                      nullptr, n_tiles, 0, 63u, w.hist, w.totals, G);
+        count_launches(3);
+    }
     return check_launch("build_tile_lists");
 }
 

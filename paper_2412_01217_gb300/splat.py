@@ -162,6 +162,7 @@ class PyramidRasterizer:
         self.tile = torch.zeros(self.capacity, **i32)
         self.record = torch.zeros(self.capacity, **i32)
         self.ranges = torch.zeros(self.n_tiles * 2, **i32)
+        self.order = torch.zeros(self.n_tiles, **i32)
         self.count = torch.zeros(1, **i32)
         self.status = torch.zeros(1, **i32)
         self.work_counter = torch.zeros(1, **i32)
@@ -185,7 +186,7 @@ class PyramidRasterizer:
         self._ccfg = self.cfg.to_c()
         self._proj = SgProjected(self.geo.data_ptr(), self.rect.data_ptr(), self.ext.data_ptr())
         self._lists = SgTileLists(self.capacity, self.tile.data_ptr(), self.record.data_ptr(),
-                                  self.ranges.data_ptr(), self.count.data_ptr())
+                                  self.ranges.data_ptr(), self.count.data_ptr(), self.order.data_ptr())
         self._saved = SgSaved(self.T_final.data_ptr(), self.last.data_ptr(), self.n_contrib.data_ptr())
 
     def set_count(self, N):

