@@ -461,6 +461,231 @@ __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
     }
 }
 
+// Cross-entropy through a linear decoder on the tensor cores.  One warp owns 32 consecutive
+// pixels; with S (32 x C) their semantic features and W (K x C) the decoder:
+//   Z = S W^T (logits), softmax and CE per pixel row on the accumulator fragments (a row's
+//   K logits sit in the 4 lanes of a quad), dZ = scale (softmax - onehot) in place,
+//   dS = dZ W with dZ taken from registers as the A operand (the k index of each 8-class
+//   step is permuted so that A column tig / tig + 4 is class 2 tig / 2 tig + 1, and the B
+//   rows follow the same permutation), and dW = dZ^T S with dZ transposed through shared
+//   memory.  All three run as 3xTF32 MMAs (FP32-level accuracy).
+template <int C, int K>
+__host__ __device__ constexpr int ce_mma_smem_floats() {
+    return 2 * K * (C + 4) + K * C + (kLossThreads / 32) * 32 * (K + 8);
+}
+
+template <int C, int K>
+__global__ void __launch_bounds__(kLossThreads) ce_decoder_mma_kernel(PixelArgs a) {
+    static_assert(C % 8 == 0 && K % 16 == 0, "MMA tiles");
+    constexpr int CP = C + 4;   // decoder row pitch: 4 mod 8, conflict-free B fragments
+    constexpr int KP = K + 8;   // dZ row pitch: 8 or 24 mod 32, conflict-free A fragments
+    constexpr int NK = K / 8, NC = C / 8;
+    extern __shared__ __align__(16) float s_dyn[];
+    __shared__ float s_red[kLossThreads / 32];
+    float *s_whi = s_dyn, *s_wlo = s_whi + K * CP;
+    float *s_acc = s_wlo + K * CP;  // K x C: this block's share of dL/dW
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
+    float *s_dz = s_acc + K * C + warp * 32 * KP;
+    for (int i = threadIdx.x; i < K * C; i += kLossThreads) {
+        uint32_t h, l;
+        split_tf32(a.decoder[i], h, l);
+        s_whi[(i / C) * CP + i % C] = __uint_as_float(h);
+        s_wlo[(i / C) * CP + i % C] = __uint_as_float(l);
+        s_acc[i] = 0.f;
+    }
+    const int blk = blockIdx.x;
+    const int v = find_prefix(a.lv.pix_blk_off, a.lv.n, blk);
+    const sg_view &vw = a.views[v];
+    const int HW = vw.W * vw.H;
+    const int pw = (blk - a.lv.pix_blk_off[v]) * kLossThreads + warp * 32;  // the warp's first pixel
+    const size_t p0 = (size_t)vw.pixel_offset;
+    const float *semv = a.sem + (size_t)C * p0;
+    const int nd = a.counts[2 * v], nl = a.counts[2 * v + 1];
+    __syncthreads();
+    float l1d = 0.f, ce = 0.f;
+    {
+        const int p = pw + lane;
+        if (p < HW) {
+            const float gd = a.gt_depth[p0 + p];
+            float gdep = 0.f;
+            if (gd > 0.f) {
+                const float d = a.depth[p0 + p] - gd;
+                l1d = fabsf(d);
+                gdep = a.w_depth * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) / (float)nd;
+            }
+            a.g_depth[p0 + p] = gdep;
+        }
+    }
+    auto S = [&](int px, int f) -> float {
+        const int p = pw + px;
+        return p < HW ? semv[(size_t)f * HW + p] : 0.f;
+    };
+    // ---- Z = S W^T: M = pixels (2 x 16), N = classes, K = features ----
+    float z[2][NK][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NK; ++nt) z[mt][nt][0] = z[mt][nt][1] = z[mt][nt][2] = z[mt][nt][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < NC; ++ks) {
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            uint32_t ah[4], al[4];
+            const int r0 = 16 * mt + gid, f0 = 8 * ks + tig;
+            split_tf32(S(r0, f0), ah[0], al[0]);
+            split_tf32(S(r0 + 8, f0), ah[1], al[1]);
+            split_tf32(S(r0, f0 + 4), ah[2], al[2]);
+            split_tf32(S(r0 + 8, f0 + 4), ah[3], al[3]);
+#pragma unroll
+            for (int nt = 0; nt < NK; ++nt) {
+                const int w0 = (8 * nt + gid) * CP + f0;
+                mma_tf32x3(z[mt][nt], ah, al, __float_as_uint(s_whi[w0]), __float_as_uint(s_whi[w0 + 4]),
+                           __float_as_uint(s_wlo[w0]), __float_as_uint(s_wlo[w0 + 4]));
+            }
+        }
+    }
+    // ---- softmax, CE and dZ per pixel row (row 16 mt + gid + 8 h; classes 8 nt + 2 tig + c) ----
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int p = pw + 16 * mt + gid + 8 * h;
+            const int lab = p < HW ? a.label[p0 + p] : -1;
+            float m = -INFINITY;
+#pragma unroll
+            for (int nt = 0; nt < NK; ++nt) m = fmaxf(m, fmaxf(z[mt][nt][2 * h], z[mt][nt][2 * h + 1]));
+            m = fmaxf(m, __shfl_xor_sync(SG_FULL_MASK, m, 1));
+            m = fmaxf(m, __shfl_xor_sync(SG_FULL_MASK, m, 2));
+            float se = 0.f, zl = 0.f;
+            bool has_lab = false;
+#pragma unroll
+            for (int nt = 0; nt < NK; ++nt)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int cls = 8 * nt + 2 * tig + c;
+                    if (cls == lab) {
+                        zl = z[mt][nt][2 * h + c] - m;
+                        has_lab = true;
+                    }
+                    const float e = expf(z[mt][nt][2 * h + c] - m);
+                    z[mt][nt][2 * h + c] = e;
+                    se += e;
+                }
+            se += __shfl_xor_sync(SG_FULL_MASK, se, 1);
+            se += __shfl_xor_sync(SG_FULL_MASK, se, 2);
+            const bool valid = lab >= 0;
+            if (valid && has_lab) ce += logf(se) - zl;
+            const float sc = valid ? a.w_sem / (float)nl : 0.f;
+            const float inv = 1.f / se;
+#pragma unroll
+            for (int nt = 0; nt < NK; ++nt)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int cls = 8 * nt + 2 * tig + c;
+                    z[mt][nt][2 * h + c] = sc * (z[mt][nt][2 * h + c] * inv - (cls == lab ? 1.f : 0.f));
+                }
+        }
+    }
+    // ---- dS = dZ W: M = pixels, N = features, K = classes (permuted within each 8-class step) ----
+    {
+        float ds[2][NC][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NC; ++nt) ds[mt][nt][0] = ds[mt][nt][1] = ds[mt][nt][2] = ds[mt][nt][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < NK; ++ks) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                uint32_t ah[4], al[4];
+                // A column tig = class 8 ks + 2 tig (d0 / d2), column tig + 4 = class 8 ks + 2 tig + 1 (d1 / d3)
+                split_tf32(z[mt][ks][0], ah[0], al[0]);
+                split_tf32(z[mt][ks][2], ah[1], al[1]);
+                split_tf32(z[mt][ks][1], ah[2], al[2]);
+                split_tf32(z[mt][ks][3], ah[3], al[3]);
+#pragma unroll
+                for (int nt = 0; nt < NC; ++nt) {
+                    const int w0 = (8 * ks + 2 * tig) * CP + 8 * nt + gid;
+                    mma_tf32x3(ds[mt][nt], ah, al, __float_as_uint(s_whi[w0]), __float_as_uint(s_whi[w0 + CP]),
+                               __float_as_uint(s_wlo[w0]), __float_as_uint(s_wlo[w0 + CP]));
+                }
+            }
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NC; ++nt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int p = pw + 16 * mt + gid + 8 * (i >> 1);
+                    const int f = 8 * nt + 2 * tig + (i & 1);
+                    if (p < HW) a.g_sem[(size_t)C * p0 + (size_t)f * HW + p] = ds[mt][nt][i];
+                }
+    }
+    // ---- dW += dZ^T S: M = classes, N = features, K = pixels ----
+    if (a.decoder_grad) {
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NK; ++nt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    s_dz[(16 * mt + gid + 8 * (i >> 1)) * KP + 8 * nt + 2 * tig + (i & 1)] = z[mt][nt][i];
+        __syncwarp();
+        float dw[K / 16][NC][4];
+#pragma unroll
+        for (int mt = 0; mt < K / 16; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NC; ++nt) dw[mt][nt][0] = dw[mt][nt][1] = dw[mt][nt][2] = dw[mt][nt][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+            uint32_t bh[NC][2], bl[NC][2];
+#pragma unroll
+            for (int nt = 0; nt < NC; ++nt) {
+                split_tf32(S(8 * ks + tig, 8 * nt + gid), bh[nt][0], bl[nt][0]);
+                split_tf32(S(8 * ks + tig + 4, 8 * nt + gid), bh[nt][1], bl[nt][1]);
+            }
+#pragma unroll
+            for (int mt = 0; mt < K / 16; ++mt) {
+                const float *d0 = s_dz + (8 * ks + tig) * KP + 16 * mt + gid;
+                uint32_t ah[4], al[4];
+                split_tf32(d0[0], ah[0], al[0]);
+                split_tf32(d0[8], ah[1], al[1]);
+                split_tf32(d0[4 * KP], ah[2], al[2]);
+                split_tf32(d0[4 * KP + 8], ah[3], al[3]);
+#pragma unroll
+                for (int nt = 0; nt < NC; ++nt) mma_tf32x3(dw[mt][nt], ah, al, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
+            }
+        }
+#pragma unroll
+        for (int mt = 0; mt < K / 16; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NC; ++nt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    atomicAdd(s_acc + (16 * mt + gid + 8 * (i >> 1)) * C + 8 * nt + 2 * tig + (i & 1), dw[mt][nt][i]);
+        __syncthreads();
+        for (int o = threadIdx.x; o < K * C; o += kLossThreads) a.dec_partials[(size_t)blk * K * C + o] = s_acc[o];
+    }
+    const float t1 = block_sum(l1d, s_red);
+    const float t2 = block_sum(ce, s_red);
+    if (threadIdx.x == 0) {
+        a.partials[2 * blk] = t1;
+        a.partials[2 * blk + 1] = t2;
+    }
+}
+
+template <int C, int K>
+static void launch_ce_mma(PixelArgs &pa, int blocks, cudaStream_t st) {
+    const size_t smem = sizeof(float) * ce_mma_smem_floats<C, K>();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(ce_decoder_mma_kernel<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    ce_decoder_mma_kernel<C, K><<<blocks, kLossThreads, smem, st>>>(pa);
+}
+
 struct FinalArgs {
     const float *ssim_rgb, *ssim_sem, *pix;  // partial arrays
     const int *counts;
@@ -577,6 +802,11 @@ static void launch_pixel_t(PixelArgs &pa, int blocks, cudaStream_t st) {
 
 static bool launch_pixel(PixelArgs &pa, int blocks, cudaStream_t st) {
     const int C = pa.C, K = pa.K;
+    if (pa.ce && pa.decoder) {
+#define SG_CE(c, k) if (C == c && K == k) { launch_ce_mma<c, k>(pa, blocks, st); return true; }
+        SG_CE(16, 16) SG_CE(16, 32) SG_CE(32, 32)
+#undef SG_CE
+    }
 #define SG_PIX(c, k) if (C == c && K == k) { launch_pixel_t<c, k>(pa, blocks, st); return true; }
     SG_PIX(4, 4) SG_PIX(8, 8) SG_PIX(16, 16) SG_PIX(16, 32) SG_PIX(32, 32) SG_PIX(40, 40)
 #undef SG_PIX

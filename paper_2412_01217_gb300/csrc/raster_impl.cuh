@@ -247,28 +247,6 @@ __host__ __device__ constexpr int bwd_warp_floats() {
     return 32 * PPT * g_pitch<4 + C>() + 2 * kChunk * chunk_pitch<32 * PPT>();
 }
 
-__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
-    const uint32_t h = __float_as_uint(x) & 0xffffe000u;
-    hi = h;
-    lo = __float_as_uint(x - __uint_as_float(h));
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// a * b with both split (3 MMAs, small terms first)
-__device__ __forceinline__ void mma_tf32x3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
-                                           uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
-    mma_tf32(d, al, bh0, bh1);
-    mma_tf32(d, ah, bl0, bl1);
-    mma_tf32(d, ah, bh0, bh1);
-}
-
 // A fragment (16 x 8, row-major, pitch ld) at column k0: a0 (gid, tig), a1 (gid + 8, tig),
 // a2 (gid, tig + 4), a3 (gid + 8, tig + 4); rows outside `keep` read as zero.
 __device__ __forceinline__ void load_a_split(const float *m, int ld, int k0, int gid, int tig, bool keep0,

@@ -124,6 +124,37 @@ __device__ __forceinline__ void warp_transpose_reduce(float (&v)[NV], int lane) 
     }
 }
 
+// ----------------------------------------------------------------------------------------
+// TF32 tensor-core products with FP32-level accuracy: x = hi + lo with hi = x with its 13
+// low mantissa bits cleared and lo = x - hi (exact); a*b ~ hi*hi + hi*lo + lo*hi keeps about
+// 22 mantissa bits of every product (the dropped lo*lo term is below 2^-22 relative).
+// mma.m16n8k8 fragments (gid = lane / 4, tig = lane % 4):
+//   A (16 x 8): a0 (gid, tig), a1 (gid + 8, tig), a2 (gid, tig + 4), a3 (gid + 8, tig + 4)
+//   B (8 x 8):  b0 (tig, gid), b1 (tig + 4, gid)
+//   D (16 x 8): d0 (gid, 2 tig), d1 (gid, 2 tig + 1), d2 (gid + 8, 2 tig), d3 (gid + 8, 2 tig + 1)
+// ----------------------------------------------------------------------------------------
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    const uint32_t h = __float_as_uint(x) & 0xffffe000u;
+    hi = h;
+    lo = __float_as_uint(x - __uint_as_float(h));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// a * b with both split (3 MMAs, small terms first)
+__device__ __forceinline__ void mma_tf32x3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                           uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+    mma_tf32(d, al, bh0, bh1);
+    mma_tf32(d, ah, bl0, bl1);
+    mma_tf32(d, ah, bh0, bh1);
+}
+
 __device__ __forceinline__ int find_view(const sg_view *views, int n_views, int tile) {
     int lo = 0, hi = n_views - 1;
     while (lo < hi) {
