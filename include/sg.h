@@ -280,6 +280,26 @@ sg_status sg_render_pyramid_backward(const sg_gaussians *g, const sg_projected *
                                      size_t workspace_bytes, int32_t *work_counter,
                                      sg_stream_t stream);
 
+/* The two halves of sg_render_pyramid_backward, for callers that time or schedule them
+ * apart (same arguments, same workspace):
+ *   sg_render_pyramid_backward_raster: the compositing adjoint.  Overwrites the workspace
+ *     with dL/d(2D mean, conic, opacity, depth) per record (8 floats per record) and ADDS
+ *     dL/d{rgb, sem} into grads.
+ *   sg_project_gaussians_backward: the chain rule through the EWA projection from those
+ *     per-record gradients; ADDS dL/d{mean, log_scale, quat, opacity_logit} into grads.
+ * Calling both in this order on one stream equals sg_render_pyramid_backward. */
+sg_status sg_render_pyramid_backward_raster(const sg_gaussians *g, const sg_projected *proj,
+                                            const sg_tile_lists *lists, const sg_view *views,
+                                            int32_t n_views, int32_t n_tiles, const sg_config *cfg,
+                                            const sg_saved *saved, const sg_images *dL,
+                                            sg_gaussian_grads *grads, void *workspace,
+                                            size_t workspace_bytes, int32_t *work_counter,
+                                            sg_stream_t stream);
+sg_status sg_project_gaussians_backward(const sg_gaussians *g, const sg_projected *proj,
+                                        const sg_view *views, int32_t n_views, const sg_config *cfg,
+                                        const void *workspace, size_t workspace_bytes,
+                                        sg_gaussian_grads *grads, sg_stream_t stream);
+
 /* ---------------------------------------------------------------------------------- */
 /* Support: pyramid construction and the optimizer                                      */
 /* ---------------------------------------------------------------------------------- */

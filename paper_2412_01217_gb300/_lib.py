@@ -113,6 +113,11 @@ SIGNATURES = {
     "sg_render_pyramid_backward": (c_i, [P(SgGaussians), P(SgProjected), P(SgTileLists), c_p, c_i,
                                          c_i, P(SgConfig), P(SgSaved), P(SgImages),
                                          P(SgGaussianGrads), c_p, C.c_size_t, c_p, c_p]),
+    "sg_render_pyramid_backward_raster": (c_i, [P(SgGaussians), P(SgProjected), P(SgTileLists), c_p, c_i,
+                                                c_i, P(SgConfig), P(SgSaved), P(SgImages),
+                                                P(SgGaussianGrads), c_p, C.c_size_t, c_p, c_p]),
+    "sg_project_gaussians_backward": (c_i, [P(SgGaussians), P(SgProjected), c_p, c_i, P(SgConfig), c_p,
+                                            C.c_size_t, P(SgGaussianGrads), c_p]),
     "sg_build_pyramid": (c_i, [c_p, c_p, c_p, c_p, c_i, P(SgView), c_i, c_p]),
     "sg_adam_step": (c_i, [c_p, c_p, c_p, c_p, C.c_int64, c_f, c_f, c_f, c_f, c_i, c_p]),
     "sg_adam_multi": (c_i, [P(SgAdamGroup), c_i, c_f, c_f, c_f, c_i, c_i, c_p]),

@@ -274,17 +274,12 @@ size_t sg_backward_workspace_size(int64_t n_records) {
     return (size_t)n_records * 8 * sizeof(float);
 }
 
-sg_status sg_render_pyramid_backward(const sg_gaussians *g, const sg_projected *proj,
-                                     const sg_tile_lists *lists, const sg_view *views,
-                                     int32_t n_views, int32_t n_tiles, const sg_config *cfg,
-                                     const sg_saved *saved, const sg_images *dL,
-                                     sg_gaussian_grads *grads, void *workspace,
-                                     size_t workspace_bytes, int32_t *work_counter,
-                                     sg_stream_t stream) {
+static sg_status check_backward(const sg_gaussians *g, const sg_view *views, int32_t n_views, const sg_config *cfg,
+                                const void *workspace, size_t workspace_bytes, const sg_gaussian_grads *grads) {
     SG_TRY(check_gaussians(g));
     SG_TRY(check_cfg(cfg));
     SG_TRY(check_views(views, n_views));
-    SG_REQUIRE(proj && lists && saved && dL && grads && workspace, "NULL argument");
+    SG_REQUIRE(grads && workspace, "NULL argument");
     SG_REQUIRE(grads->mean && grads->log_scale && grads->quat && grads->opacity_logit && grads->rgb &&
                    grads->sem, "gradient buffers are NULL");
     SG_REQUIRE(grads->N == g->N && grads->C == g->C, "grads shape differs from gaussians");
@@ -294,10 +289,22 @@ sg_status sg_render_pyramid_backward(const sg_gaussians *g, const sg_projected *
         set_error("render_pyramid_backward: workspace %zu bytes < %zu needed", workspace_bytes, need);
         return SG_ERR_CAPACITY;
     }
+    return SG_OK;
+}
+
+sg_status sg_render_pyramid_backward_raster(const sg_gaussians *g, const sg_projected *proj,
+                                            const sg_tile_lists *lists, const sg_view *views,
+                                            int32_t n_views, int32_t n_tiles, const sg_config *cfg,
+                                            const sg_saved *saved, const sg_images *dL,
+                                            sg_gaussian_grads *grads, void *workspace,
+                                            size_t workspace_bytes, int32_t *work_counter,
+                                            sg_stream_t stream) {
+    SG_TRY(check_backward(g, views, n_views, cfg, workspace, workspace_bytes, grads));
+    SG_REQUIRE(proj && lists && saved && dL, "NULL argument");
     SG_REQUIRE(!cfg->persistent || work_counter, "persistent launch needs work_counter");
     cudaStream_t st = (cudaStream_t)stream;
     float *g2d = (float *)workspace;
-    cudaMemsetAsync(g2d, 0, need, st);
+    cudaMemsetAsync(g2d, 0, sg_backward_workspace_size((int64_t)g->N * n_views), st);
     RasterArgs a{};
     fill_raster_args(a, g, proj, lists, views, n_views, n_tiles, cfg, work_counter);
     a.T_final = saved->T_final;
@@ -310,8 +317,29 @@ sg_status sg_render_pyramid_backward(const sg_gaussians *g, const sg_projected *
     a.g_rgb = grads->rgb;
     a.g_sem = grads->sem;
     a.ppt = cfg->pixels_per_thread_bwd;
-    SG_TRY(launch_raster(a, g->C, true, st));
-    return launch_project_bwd(g, views, n_views, cfg, proj, g2d, grads, st);
+    return launch_raster(a, g->C, true, st);
+}
+
+sg_status sg_project_gaussians_backward(const sg_gaussians *g, const sg_projected *proj,
+                                        const sg_view *views, int32_t n_views, const sg_config *cfg,
+                                        const void *workspace, size_t workspace_bytes,
+                                        sg_gaussian_grads *grads, sg_stream_t stream) {
+    SG_TRY(check_backward(g, views, n_views, cfg, workspace, workspace_bytes, grads));
+    SG_REQUIRE(proj, "NULL argument");
+    return launch_project_bwd(g, views, n_views, cfg, proj, (const float *)workspace, grads,
+                              (cudaStream_t)stream);
+}
+
+sg_status sg_render_pyramid_backward(const sg_gaussians *g, const sg_projected *proj,
+                                     const sg_tile_lists *lists, const sg_view *views,
+                                     int32_t n_views, int32_t n_tiles, const sg_config *cfg,
+                                     const sg_saved *saved, const sg_images *dL,
+                                     sg_gaussian_grads *grads, void *workspace,
+                                     size_t workspace_bytes, int32_t *work_counter,
+                                     sg_stream_t stream) {
+    SG_TRY(sg_render_pyramid_backward_raster(g, proj, lists, views, n_views, n_tiles, cfg, saved, dL, grads,
+                                             workspace, workspace_bytes, work_counter, stream));
+    return sg_project_gaussians_backward(g, proj, views, n_views, cfg, workspace, workspace_bytes, grads, stream);
 }
 
 sg_status sg_build_pyramid(float *rgb, float *depth, int32_t *label, float *sem, int32_t n_sem_ch,

@@ -475,7 +475,7 @@ __host__ __device__ constexpr int ce_mma_smem_floats() {
 }
 
 template <int C, int K>
-__global__ void __launch_bounds__(kLossThreads) ce_decoder_mma_kernel(PixelArgs a) {
+__global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder_mma_kernel(PixelArgs a) {
     static_assert(C % 8 == 0 && K % 16 == 0, "MMA tiles");
     constexpr int CP = C + 4;   // decoder row pitch: 4 mod 8, conflict-free B fragments
     constexpr int KP = K + 8;   // dZ row pitch: 8 or 24 mod 32, conflict-free A fragments
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(kLossThreads) ce_decoder_mma_kernel(PixelArgs 
                         zl = z[mt][nt][2 * h + c] - m;
                         has_lab = true;
                     }
-                    const float e = expf(z[mt][nt][2 * h + c] - m);
+                    const float e = __expf(z[mt][nt][2 * h + c] - m);
                     z[mt][nt][2 * h + c] = e;
                     se += e;
                 }
@@ -975,6 +975,41 @@ __global__ void adam_multi_kernel(AdamGroups G, float b1, float b2, float eps, f
     }
 }
 
+// The same update, four elements per thread with 16-byte loads and stores: start[] counts
+// quads (every group holds a multiple of 4 elements, all arrays 16-byte aligned).
+__device__ __forceinline__ float adam_one(float &m, float &v, float p, float g, float lr, float b1, float b2,
+                                          float eps, float bc1, float bc2) {
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    return p - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+}
+
+__global__ void adam_multi4_kernel(AdamGroups G, float b1, float b2, float eps, float bc1, float bc2,
+                                   int zero_grad) {
+    const int64_t total = G.start[G.n];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (k + 1 < G.n && i >= G.start[k + 1]) ++k;
+        const sg_adam_group &q = G.g[k];
+        const int64_t j = i - G.start[k];
+        float4 *gp = reinterpret_cast<float4 *>(q.grad) + j;
+        float4 *mp = reinterpret_cast<float4 *>(q.m) + j;
+        float4 *vp = reinterpret_cast<float4 *>(q.v) + j;
+        float4 *pp = reinterpret_cast<float4 *>(q.param) + j;
+        const float4 g = *gp;
+        float4 m = *mp, v = *vp, p = *pp;
+        p.x = adam_one(m.x, v.x, p.x, g.x, q.lr, b1, b2, eps, bc1, bc2);
+        p.y = adam_one(m.y, v.y, p.y, g.y, q.lr, b1, b2, eps, bc1, bc2);
+        p.z = adam_one(m.z, v.z, p.z, g.z, q.lr, b1, b2, eps, bc1, bc2);
+        p.w = adam_one(m.w, v.w, p.w, g.w, q.lr, b1, b2, eps, bc1, bc2);
+        *mp = m;
+        *vp = v;
+        *pp = p;
+        if (zero_grad) *gp = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 sg_status launch_adam_multi(const sg_adam_group *groups, int n, float b1, float b2, float eps, int step,
                             int zero_grad, cudaStream_t st) {
     AdamGroups G{};
@@ -988,10 +1023,21 @@ sg_status launch_adam_multi(const sg_adam_group *groups, int n, float b1, float 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    bool quads = true;
+    for (int k = 0; k < n; ++k) {
+        const sg_adam_group &q = groups[k];
+        quads = quads && q.n % 4 == 0 && ((uintptr_t)q.param | (uintptr_t)q.grad | (uintptr_t)q.m |
+                                          (uintptr_t)q.v) % 16 == 0;
+    }
+    if (quads)
+        for (int k = 0; k <= n; ++k) G.start[k] /= 4;
     int64_t blocks = (G.start[n] + 255) / 256;
     if (blocks > 8 * (int64_t)sms) blocks = 8 * (int64_t)sms;
     if (blocks > 0) {
-        adam_multi_kernel<<<(int)blocks, 256, 0, st>>>(G, b1, b2, eps, bc1, bc2, zero_grad);
+        if (quads)
+            adam_multi4_kernel<<<(int)blocks, 256, 0, st>>>(G, b1, b2, eps, bc1, bc2, zero_grad);
+        else
+            adam_multi_kernel<<<(int)blocks, 256, 0, st>>>(G, b1, b2, eps, bc1, bc2, zero_grad);
         count_launches(1);
     }
     return check_launch("adam_multi");

@@ -258,16 +258,22 @@ class PyramidRasterizer:
              C.byref(lc), _ptr(self.terms), C.byref(di), _ptr(self.loss_ws), self.loss_ws.numel(), _stream())
 
     # ---- backward ------------------------------------------------------------------------
-    def backward(self, g, grads, dL=None):
-        """ADDS dL/dparams into grads (dict like g); dL defaults to self.dL_* (from loss)."""
+    def backward(self, g, grads, dL=None, between=None):
+        """ADDS dL/dparams into grads (dict like g); dL defaults to self.dL_* (from loss).
+        The compositing adjoint and the projection adjoint are two library calls;
+        `between` (optional) is called on the host between them (e.g. to record an event)."""
         gs = gaussians_struct(g)
         gr = gaussians_struct(grads)
         d = dL or (self.dL_rgb, self.dL_depth, self.dL_sem)
         di = SgImages(d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr())
-        call("sg_render_pyramid_backward", C.byref(gs), C.byref(self._proj), C.byref(self._lists),
+        call("sg_render_pyramid_backward_raster", C.byref(gs), C.byref(self._proj), C.byref(self._lists),
              _ptr(self.views), self.V, self.n_tiles, C.byref(self._ccfg), C.byref(self._saved),
              C.byref(di), C.byref(gr), _ptr(self.bwd_ws), self.bwd_ws.numel(), _ptr(self.work_counter),
              _stream())
+        if between is not None:
+            between()
+        call("sg_project_gaussians_backward", C.byref(gs), C.byref(self._proj), _ptr(self.views), self.V,
+             C.byref(self._ccfg), _ptr(self.bwd_ws), self.bwd_ws.numel(), C.byref(gr), _stream())
 
     # ---- diagnostics --------------------------------------------------------------------
     def instance_count(self):
