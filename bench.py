@@ -11,6 +11,11 @@ before every timed step; the flush is outside each step's event pair.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead (the
 reference arm: a bounded pixel sample of the same workload per step, extrapolated).
+
+--workload batched: 8 keyframes of uneven size (4 x 1200x680, 4 x 640x480) x 3 levels = 24
+images over 500k shared Gaussians in one persistent launch per kernel.  --workload scannet:
+one 640x480 keyframe x 4 levels (down to 80x60), 1M Gaussians, C = 40 class logits (no
+decoder), depth noise 1 cm.  The default is the Replica-like workload above.
 """
 from __future__ import annotations
 
@@ -30,8 +35,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd pyramid-splat iters/s"
 UNIT = "iters/s"
-WORKLOAD = dict(workload="replica-like room, 1 keyframe x 3 pyramid levels (1200x680, 600x340, 300x170)",
-                gaussians=300_000, sem_features=16, classes=32, tile="16x16", levels=3)
+WORKLOADS = {
+    "replica": dict(workload="replica-like room, 1 keyframe x 3 pyramid levels (1200x680, 600x340, 300x170)",
+                    gaussians=300_000, sem_features=16, classes=32, levels=3),
+    "batched": dict(workload="replica-like room, 8 keyframes of uneven size (4 x 1200x680, 4 x 640x480) "
+                             "x 3 pyramid levels = 24 images in one launch per kernel",
+                    gaussians=500_000, sem_features=16, classes=32, levels=3),
+    "scannet": dict(workload="scannet-like room, 1 keyframe x 4 pyramid levels (640x480 .. 80x60), "
+                             "40 class logits, depth noise 1 cm",
+                    gaussians=1_000_000, sem_features=40, classes=40, levels=4),
+}
 
 
 def parse():
@@ -44,7 +57,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--ppt", type=int, default=1, help="pixels per thread of the forward compositing kernel")
     ap.add_argument("--ppt-bwd", type=int, default=2, help="pixels per thread of the backward kernel")
-    ap.add_argument("--gaussians", type=int, default=300_000)
+    ap.add_argument("--workload", default="replica", choices=sorted(WORKLOADS))
+    ap.add_argument("--gaussians", type=int, default=None, help="default: the workload's count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use --tile/--batch/--ppt as given")
@@ -56,17 +70,30 @@ def parse():
 # workload
 # ------------------------------------------------------------------------------------------
 
-def build_inputs(n_gauss, seed_offset=0):
+def build_inputs(workload, n_gauss, seed_offset=0):
+    """(cameras, ray-cast level-0 frames, Gaussians, decoder or None) of a workload."""
     import synthetic
-    room = synthetic.Room(n_classes=32, seed=3)
-    cams = room.trajectory(8, synthetic.REPLICA_LIKE, seed=7)
-    cam = cams[(1 + seed_offset) % len(cams)]
-    g = room.sample_gaussians(n_gauss, 16, seed=4 + seed_offset, sem_mode="random")
+    w = WORKLOADS[workload]
+    if workload == "scannet":
+        room = synthetic.Room(n_classes=40, seed=3)
+        cams = [room.trajectory(8, synthetic.SCANNET_LIKE, seed=7)[(1 + seed_offset) % 8]]
+        frames = [room.raycast(c, depth_noise=0.01) for c in cams]
+    else:
+        room = synthetic.Room(n_classes=32, seed=3)
+        traj = room.trajectory(8, synthetic.REPLICA_LIKE, seed=7)
+        if workload == "batched":
+            cams = traj[:4] + room.trajectory(4, synthetic.SCANNET_LIKE, seed=8)
+        else:
+            cams = [traj[(1 + seed_offset) % 8]]
+        frames = [room.raycast(c) for c in cams]
+    C = w["sem_features"]
+    g = room.sample_gaussians(n_gauss, C, seed=4 + seed_offset, sem_mode="random")
     g["sem"] *= 0.5
-    frame = room.raycast(cam)
-    rng = np.random.default_rng(11)
-    decoder = rng.normal(size=(32, 16)).astype(np.float32) * 0.3
-    return room, cam, g, frame, decoder
+    decoder = None
+    if C != w["classes"]:
+        rng = np.random.default_rng(11)
+        decoder = rng.normal(size=(w["classes"], C)).astype(np.float32) * 0.3
+    return cams, frames, g, decoder
 
 
 # ------------------------------------------------------------------------------------------
@@ -136,13 +163,13 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel, units_now):
+def profiled_traffic(kernel, units_now, workload="replica"):
     """dram__bytes_read.sum + dram__bytes_write.sum per launch from profiles/<kernel>_*.md
     (lines 'source_sha: ...', 'dram_bytes_per_launch: ...', 'units: ...'), scaled by the
     units processed if the capture ran a different case; None when the kernel sources
     changed since the capture."""
     import glob
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md"))):
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_{workload}_*.md"))):
         kv = {}
         for line in open(path):
             if ":" in line and line.strip().startswith(("source_sha", "dram_bytes_per_launch", "units")):
@@ -215,15 +242,15 @@ class ClockSampler:
 # CPU baseline (the oracle, as it stands)
 # ------------------------------------------------------------------------------------------
 
-def oracle_sample_time(g, cam, levels, stride, seed=0):
-    """Oracle forward + backward over every stride-th row and column of every level.
-    Returns (seconds, sampled pixels, total pixels)."""
+def oracle_sample_time(g, cams, levels, stride, seed=0):
+    """Oracle forward + backward over every stride-th row and column of every level of every
+    camera.  Returns (seconds, sampled pixels, total pixels)."""
     import oracle
     g64 = {k: np.asarray(v, np.float64) for k, v in g.items() if k != "label"}
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
     n_s, n_t = 0, 0
-    for oc in oracle.level_cameras(cam, levels):
+    for oc in [lc for cam in cams for lc in oracle.level_cameras(cam, levels)]:
         ys, xs = np.meshgrid(np.arange(0, oc["H"], stride), np.arange(0, oc["W"], stride), indexing="ij")
         pix = np.stack([xs.ravel(), ys.ravel()], 1)
         f = oracle.render(g64, oc, pixels=pix)
@@ -235,18 +262,18 @@ def oracle_sample_time(g, cam, levels, stride, seed=0):
     return time.perf_counter() - t0, n_s, n_t
 
 
-def cpu_baseline(g, cam, target_s):
+def cpu_baseline(g, cams, levels, target_s):
     import oracle
     oracle.build()
     # pick a stride whose sample costs about target_s: probe with a coarse stride
-    t, ns, nt = oracle_sample_time(g, cam, 3, 64)
+    t, ns, nt = oracle_sample_time(g, cams, levels, 64)
     per_px = t / max(1, ns)
     want = max(1, int(target_s / per_px))
     stride = max(1, int(np.sqrt(nt / want)))
-    t, ns, nt = oracle_sample_time(g, cam, 3, stride)
+    t, ns, nt = oracle_sample_time(g, cams, levels, stride)
     full = t * nt / ns
     return {"value": 1.0 / full, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle forward+backward on every {stride}th row/column of all 3 levels "
+            "sample": f"FP64 oracle forward+backward on every {stride}th row/column of all {levels} levels "
                       f"({ns} of {nt} pixels, {t:.1f} s), extrapolated linearly to the full iteration",
             "seconds_per_iter": full}
 
@@ -258,25 +285,27 @@ def run_reference(args):
     if rank != 0:
         return
     oracle.build()
-    room, cam, g, frame, dec = build_inputs(args.gaussians)
-    probe_t, ns, nt = oracle_sample_time(g, cam, 3, 96)
+    W = WORKLOADS[args.workload]
+    L = W["levels"]
+    cams, frames, g, dec = build_inputs(args.workload, args.gaussians or W["gaussians"])
+    probe_t, ns, nt = oracle_sample_time(g, cams, L, 96)
     per_px = probe_t / max(1, ns)
     budget = 150.0 / max(1, args.steps + args.warmup)
     stride = max(8, int(np.sqrt(nt * per_px / max(0.5, budget))))
     for _ in range(args.warmup):
-        oracle_sample_time(g, cam, 3, stride)
+        oracle_sample_time(g, cams, L, stride)
     times = []
     for k in range(args.steps):
-        t, ns, nt = oracle_sample_time(g, cam, 3, stride, seed=k)
+        t, ns, nt = oracle_sample_time(g, cams, L, stride, seed=k)
         times.append(t * nt / ns)
     per = float(np.mean(times))
     value = 1.0 / per
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, l2="n/a (CPU)"),
+            "config": dict(W, l2="n/a (CPU)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"every {stride}th row/column of all 3 levels per step ({ns} of {nt} px), "
+                             "sample": f"every {stride}th row/column of all {L} levels per step ({ns} of {nt} px), "
                                        f"extrapolated linearly"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -300,25 +329,29 @@ def run_ours(args):
                                         build_pyramid, load_library, to_device_params)
     lib = load_library()
     tw, th = (int(x) for x in args.tile.split("x"))
-    room, cam, g, frame, dec = build_inputs(args.gaussians, seed_offset=rank)
+    W = WORKLOADS[args.workload]
+    L, C_sem, n_cls = W["levels"], W["sem_features"], W["classes"]
+    n_gauss = args.gaussians or W["gaussians"]
+    cams, frames, g, dec = build_inputs(args.workload, n_gauss, seed_offset=rank)
+    fr = lambda key: [f[key] for f in frames]
     cfg = RenderConfig(tile_w=tw, tile_h=th, batch=args.batch, pixels_per_thread=args.ppt,
                        pixels_per_thread_bwd=args.ppt_bwd)
     p = to_device_params(g, dev)
-    decoder = torch.tensor(dec, device=dev)
+    decoder = torch.tensor(dec, device=dev) if dec is not None else None
     tune_table = None
     if not args.no_autotune:
         from paper_2412_01217_gb300.autotune import autotune
-        probe = PyramidRasterizer(args.gaussians, 16, [cam], levels=3, cfg=cfg,
-                                  loss_cfg=LossConfig(n_classes=32), device=dev)
-        gt0 = build_pyramid(probe, [frame["rgb"]], [frame["depth"]], [frame["label"]])
+        probe = PyramidRasterizer(n_gauss, C_sem, cams, levels=L, cfg=cfg,
+                                  loss_cfg=LossConfig(n_classes=n_cls), device=dev)
+        gt0 = build_pyramid(probe, fr("rgb"), fr("depth"), fr("label"))
         del probe
-        cfg, tune_table = autotune(p, [cam], 3, gt0, LossConfig(n_classes=32), base=cfg, decoder=decoder,
+        cfg, tune_table = autotune(p, cams, L, gt0, LossConfig(n_classes=n_cls), base=cfg, decoder=decoder,
                                    use_cache=False, log=lambda m: print("autotune:", m, file=sys.stderr))
         del gt0
         torch.cuda.empty_cache()
-    r = PyramidRasterizer(args.gaussians, 16, [cam], levels=3, cfg=cfg,
-                          loss_cfg=LossConfig(n_classes=32), device=dev)
-    gt = build_pyramid(r, [frame["rgb"]], [frame["depth"]], [frame["label"]])
+    r = PyramidRasterizer(n_gauss, C_sem, cams, levels=L, cfg=cfg,
+                          loss_cfg=LossConfig(n_classes=n_cls), device=dev)
+    gt = build_pyramid(r, fr("rgb"), fr("depth"), fr("label"))
     ms = MappingStep(r, p, gt, decoder=decoder)
     ms.step()
     torch.cuda.synchronize()
@@ -341,7 +374,8 @@ def run_ours(args):
     groups, n_groups = ms._adam_groups()
 
     def body(t):
-        ms.decoder_grad.zero_()
+        if ms.decoder_grad is not None:
+            ms.decoder_grad.zero_()
         ev["s0"].record()
         r.project(p)
         r.build_lists()
@@ -400,10 +434,8 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         host = {k: p[k].detach().cpu().pin_memory() for k in PARAM_KEYS}
-        v0 = r.view_slice(gt["rgb"], 0, 3)
-        h_rgb = torch.as_tensor(frame["rgb"]).pin_memory()
-        h_depth = torch.as_tensor(frame["depth"]).pin_memory()
-        h_label = torch.as_tensor(frame["label"]).pin_memory()
+        h_frames = [(torch.as_tensor(f["rgb"]).pin_memory(), torch.as_tensor(f["depth"]).pin_memory(),
+                     torch.as_tensor(f["label"]).pin_memory()) for f in frames]
         h_terms = torch.empty(r.terms.numel(), dtype=torch.float32).pin_memory()
         from paper_2412_01217_gb300._lib import call as _call
         import ctypes as C
@@ -411,9 +443,11 @@ def run_ours(args):
         def e2e_step():
             for k in PARAM_KEYS:
                 p[k].copy_(host[k], non_blocking=True)
-            v0.copy_(h_rgb, non_blocking=True)
-            r.view_slice(gt["depth"], 0, 1)[0].copy_(h_depth, non_blocking=True)
-            r.view_slice(gt["label"], 0, 1)[0].copy_(h_label, non_blocking=True)
+            for c, (h_rgb, h_depth, h_label) in enumerate(h_frames):  # level 0 of every keyframe
+                v = c * L
+                r.view_slice(gt["rgb"], v, 3).copy_(h_rgb, non_blocking=True)
+                r.view_slice(gt["depth"], v, 1)[0].copy_(h_depth, non_blocking=True)
+                r.view_slice(gt["label"], v, 1)[0].copy_(h_label, non_blocking=True)
             _call("sg_build_pyramid", _ptr(gt["rgb"]), _ptr(gt["depth"]), _ptr(gt["label"]), C.c_void_p(0), 0,
                   r.views_host, r.V, _stream())
             graph.replay()
@@ -431,7 +465,7 @@ def run_ours(args):
         ee.record()
         torch.cuda.synchronize()
         e2e_s = es.elapsed_time(ee) / 1e3
-        h2d = sum(host[k].numel() * 4 for k in PARAM_KEYS) + h_rgb.numel() * 4 + h_depth.numel() * 4 + h_label.numel() * 4
+        h2d = sum(host[k].numel() * 4 for k in PARAM_KEYS) + sum(t.numel() * 4 for f in h_frames for t in f)
         d2h = h_terms.numel() * 4 + sum(host[k].numel() * 4 for k in PARAM_KEYS)
         if world > 1:
             t = torch.tensor([e2e_s], device=dev)
@@ -462,7 +496,7 @@ def run_ours(args):
     achieved = d_flops / d_time / 1e12
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
-                "traffic": profiled_traffic(dominant, stats["E"]),
+                "traffic": profiled_traffic(dominant, stats["E"], args.workload),
                 "traffic_unit": "DRAM bytes per launch (ncu), scaled by list entries examined",
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                 "launch_ms": d_time * 1e3}
@@ -471,9 +505,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, tile=f"{cfg.tile_w}x{cfg.tile_h}", batch=cfg.batch,
+        "config": dict(W, tile=f"{cfg.tile_w}x{cfg.tile_h}", batch=cfg.batch,
                        pixels_per_thread=cfg.pixels_per_thread, pixels_per_thread_bwd=cfg.pixels_per_thread_bwd,
-                       autotuned=not args.no_autotune, gaussians=args.gaussians,
+                       autotuned=not args.no_autotune, gaussians=n_gauss,
                        l2="flushed (256 MiB write) before every timed step", parallelism="replicas"),
         "gpu_launches": int(launches_per_step * args.steps),
         "launches_per_step": int(launches_per_step),
@@ -491,7 +525,7 @@ def run_ours(args):
         "e2e": e2e,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(g, cam, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(g, cams, L, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

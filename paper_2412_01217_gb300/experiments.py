@@ -105,38 +105,35 @@ def training_pairs(m, inserted, frames_dev_fn):
     return torch.cat(Xs), torch.cat(Ts)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--quick", action="store_true", help="small images and Gaussian counts")
-    ap.add_argument("--out", default=None)
-    ap.add_argument("--train-rooms", type=int, default=3)
-    ap.add_argument("--iters-per-kf", type=int, default=150)
-    ap.add_argument("--keyframes", type=int, default=8)
-    ap.add_argument("--epochs", type=int, default=4)
-    args = ap.parse_args()
+def run(quick=False, train_rooms=3, iters_per_kf=150, keyframes=8, epochs=4, workers=16, log=None):
+    """The whole experiment; returns the result dict (see module docstring)."""
     import synthetic
-    ctx = mp.get_context("spawn")
-    pool = ctx.Pool(min(16, mp.cpu_count()))
-    if args.quick:
+    pool = None
+    if workers > 1:
+        ctx = mp.get_context("spawn")
+        pool = ctx.Pool(min(workers, mp.cpu_count()))
+    if quick:
         intr = dict(W=320, H=180, fx=160.0, fy=160.0, cx=159.5, cy=89.5)
         n_max, new_per_kf = 40_000, 5_000
     else:
         intr = dict(synthetic.REPLICA_LIKE)
         n_max, new_per_kf = 300_000, 37_500
-    n_kf = args.keyframes
+    n_kf = keyframes
     t0 = time.time()
     # ---- 1. training pairs ----
     Xs, Ts = [], []
     g = torch.Generator().manual_seed(5)
     decoder = torch.randn(32, 16, generator=g) * 0.3
-    for r in range(args.train_rooms):
+    for r in range(train_rooms):
         kf, frames, _, _ = room_views(100 + r, intr, n_kf, 0, pool)
-        m, ins, _ = run_mapper(kf, frames, n_max, args.iters_per_kf, new_per_kf, seed=100 + r, decoder=decoder)
+        m, ins, _ = run_mapper(kf, frames, n_max, iters_per_kf, new_per_kf, seed=100 + r, decoder=decoder)
         X, T = training_pairs(m, ins, m.frame_dev)
         Xs.append(X)
         Ts.append(T)
         del m
         torch.cuda.empty_cache()
+        if log:
+            log(f"room {100 + r}: {X.shape[0]} pairs")
     X = torch.cat(Xs)
     T = torch.cat(Ts)
     n = (X.shape[0] // 4096) * 4096
@@ -147,24 +144,25 @@ def main():
     mlp = MLPInit(seed=0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    hist = mlp.fit(X, Xt, T, epochs=args.epochs, batch=4096)
+    hist = mlp.fit(X, Xt, T, epochs=epochs, batch=4096)
     e1.record()
     e1.synchronize()
     train_s = e0.elapsed_time(e1) / 1e3
     # ---- 3. time-to-PSNR on the held-out room ----
     kf, frames, ev, ev_frames = room_views(999, intr, n_kf, 4, pool)
-    pool.close()
-    eval_every = max(10, args.iters_per_kf // 3)
-    _, _, plain = run_mapper(kf, frames, n_max, args.iters_per_kf, new_per_kf, init="heuristic", ev=ev,
+    if pool is not None:
+        pool.close()
+    eval_every = max(10, iters_per_kf // 3)
+    _, _, plain = run_mapper(kf, frames, n_max, iters_per_kf, new_per_kf, init="heuristic", ev=ev,
                              ev_frames=ev_frames, eval_every=eval_every, seed=999, decoder=decoder)
-    _, _, learned = run_mapper(kf, frames, n_max, args.iters_per_kf, new_per_kf, init="learned", mlp=mlp, ev=ev,
+    _, _, learned = run_mapper(kf, frames, n_max, iters_per_kf, new_per_kf, init="learned", mlp=mlp, ev=ev,
                                ev_frames=ev_frames, eval_every=eval_every, seed=999, decoder=decoder)
     p_star = plain[-1][2]
     reach = next((c for c in learned if c[2] >= p_star), None)
-    out = {
+    return {
         "experiment": "learned vs heuristic initializer, time-to-PSNR",
         "images": f"{intr['W']}x{intr['H']} x 3 levels", "gaussians": n_max, "keyframes": n_kf,
-        "iters_per_keyframe": args.iters_per_kf, "train_pairs": int(n), "train_epochs": args.epochs,
+        "iters_per_keyframe": iters_per_kf, "train_pairs": int(n), "train_epochs": epochs,
         "train_loss_per_epoch": hist, "train_gpu_seconds": train_s, "data_wall_seconds": t_data,
         "plain_final_psnr": p_star, "plain_gpu_seconds": plain[-1][0],
         "learned_final_psnr": learned[-1][2], "learned_gpu_seconds_total": learned[-1][0],
@@ -172,6 +170,19 @@ def main():
         "speedup_to_plain_final_psnr": (plain[-1][0] / reach[0]) if reach else None,
         "plain_curve": plain, "learned_curve": learned,
     }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--quick", action="store_true", help="small images and Gaussian counts")
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--train-rooms", type=int, default=3)
+    ap.add_argument("--iters-per-kf", type=int, default=150)
+    ap.add_argument("--keyframes", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=4)
+    args = ap.parse_args()
+    out = run(quick=args.quick, train_rooms=args.train_rooms, iters_per_kf=args.iters_per_kf,
+              keyframes=args.keyframes, epochs=args.epochs)
     s = json.dumps(out)
     print(s)
     if args.out:
