@@ -15,6 +15,8 @@
 // a stable scatter that ranks equal digits inside a block by warp match + prefix counts.
 #include <cstdio>
 
+#include <algorithm>
+
 #include "sg_common.cuh"
 
 namespace sg {
@@ -162,20 +164,42 @@ __global__ void emit_apply_kernel(const uint2 *__restrict__ rect, const uint32_t
         }
         uint32_t tot;
         const uint32_t ex = block_exclusive_scan(c, tot);
+        // The warp's instances occupy [run + w0, run + w1) in lane order; the warp writes them
+        // together, lane i taking slot i of each 32-slot step (coalesced stores).  The owner of
+        // slot o is the last lane whose offset is <= o (lanes with no instance share their
+        // offset with the next lane, so the last one found owns at least one instance).
+        const int lane = threadIdx.x & 31;
+        const uint32_t w0 = __shfl_sync(SG_FULL_MASK, ex, 0);
+        const uint32_t w1 = __shfl_sync(SG_FULL_MASK, ex + c, 31);
+        uint32_t tile0 = 0, tiles_x = 0, tw = 1;
         if (c) {
             const int v = (int)(r / (uint32_t)N);
-            const int tiles_x = views[v].tiles_x, toff = views[v].tile_offset;
-            const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16, tx1 = rc.y & 0xffffu, ty1 = rc.y >> 16;
-            uint32_t o = run + ex;
-            for (uint32_t ty = ty0; ty < ty1; ++ty)
-                for (uint32_t tx = tx0; tx < tx1; ++tx, ++o) {
-                    if (o < (uint32_t)capacity) {
-                        tkey[o] = (uint32_t)toff + ty * (uint32_t)tiles_x + tx;
-                        tval[o] = r;
-                    } else {
-                        overflow = true;
-                    }
+            const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16;
+            tiles_x = (uint32_t)views[v].tiles_x;
+            tile0 = (uint32_t)views[v].tile_offset + ty0 * tiles_x + tx0;
+            tw = (rc.y & 0xffffu) - tx0;
+        }
+        for (uint32_t ob = w0; ob < w1; ob += 32) {  // warp-uniform trip count
+            const uint32_t o = ob + lane;
+            int own = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1)
+                if (__shfl_sync(SG_FULL_MASK, ex, own + step) <= o) own += step;
+            const uint32_t q = o - __shfl_sync(SG_FULL_MASK, ex, own);
+            const uint32_t ow = __shfl_sync(SG_FULL_MASK, tw, own);
+            const uint32_t ot = __shfl_sync(SG_FULL_MASK, tile0, own);
+            const uint32_t ox = __shfl_sync(SG_FULL_MASK, tiles_x, own);
+            const uint32_t orec = __shfl_sync(SG_FULL_MASK, r, own);
+            if (o < w1) {
+                const uint32_t row = q / ow;
+                const uint32_t g = run + o;
+                if (g < (uint32_t)capacity) {
+                    tkey[g] = ot + row * ox + (q - row * ow);
+                    tval[g] = orec;
+                } else {
+                    overflow = true;
                 }
+            }
         }
         run += tot;
     }
@@ -237,14 +261,25 @@ __global__ void rs_digit_scan_kernel(uint32_t *__restrict__ hist, uint32_t *__re
     if (threadIdx.x == 0) totals[d] = run;
 }
 
+// Scatter of one digit pass.  Each block walks its input range in chunks of kScatterChunk
+// elements: a stable rank per digit inside the chunk (warp match_any + per-warp counts, 256
+// elements at a time), a reorder of the chunk by digit in shared memory, and a write-out in
+// which consecutive threads store consecutive elements of one digit run (coalesced stores
+// instead of one scattered sector per element).
+constexpr int kScatterIPT = 8;
+constexpr int kScatterChunk = kScanThreads * kScatterIPT;
+
 template <class Src>
 __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
     Src src, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ n_ptr, int cap, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, int G) {
     constexpr int kWarps = kScanThreads / 32;
-    __shared__ uint32_t run[256];
+    __shared__ uint32_t run[256];   // global position of the next element of each digit
+    __shared__ uint32_t sub[256];   // elements of each digit so far in this chunk
+    __shared__ uint32_t loc[256];   // first slot of each digit in the reordered chunk
     __shared__ uint32_t wcnt[kWarps][256];
+    __shared__ uint32_t skey[kScatterChunk], sval[kScatterChunk];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // digit base = exclusive scan of the digit totals (+ this block's offset)
     {
@@ -256,33 +291,63 @@ __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
     int beg, end;
     block_range(n, G, blockIdx.x, beg, end);
     const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int base = beg; base < end; base += kScanThreads) {
+    for (int cbase = beg; cbase < end; cbase += kScatterChunk) {
+        sub[tid] = 0;
+        const int nit = min(kScatterIPT, (end - cbase + kScanThreads - 1) / kScanThreads);  // block-uniform
+        uint32_t key[kScatterIPT], val[kScatterIPT], lrank[kScatterIPT];
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
-        __syncthreads();
-        const int i = base + tid;
-        const bool valid = i < end;
-        const uint32_t key = valid ? src.key(i) : 0u;
-        const uint32_t d = valid ? ((key >> shift) & mask) : 256u;
-        const uint32_t peers = __match_any_sync(SG_FULL_MASK, d);
-        const uint32_t rank = __popc(peers & lt_mask);
-        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        uint32_t s = 0;
+        for (int it = 0; it < kScatterIPT; ++it) {
+            if (it >= nit) break;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t t = wcnt[w][tid];
-            wcnt[w][tid] = s;
-            s += t;
+            for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+            __syncthreads();
+            const int i = cbase + it * kScanThreads + tid;
+            const bool valid = i < end;
+            key[it] = valid ? src.key(i) : 0u;
+            val[it] = valid ? src.val(i) : 0u;
+            const uint32_t d = valid ? ((key[it] >> shift) & mask) : 256u;
+            const uint32_t peers = __match_any_sync(SG_FULL_MASK, d);
+            const uint32_t rank = __popc(peers & lt_mask);
+            if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = __popc(peers);
+            __syncthreads();
+            uint32_t s = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t t = wcnt[w][tid];
+                wcnt[w][tid] = s;
+                s += t;
+            }
+            __syncthreads();
+            lrank[it] = valid ? sub[d] + wcnt[warp][d] + rank : 0u;
+            __syncthreads();
+            sub[tid] += s;
         }
         __syncthreads();
-        if (valid) {
-            const uint32_t pos = run[d] + wcnt[warp][d] + rank;
-            if (kout) kout[pos] = key;
-            vout[pos] = src.val(i);
+        {
+            uint32_t tot;
+            loc[tid] = block_exclusive_scan(sub[tid], tot);
         }
         __syncthreads();
-        run[tid] += s;
+#pragma unroll
+        for (int it = 0; it < kScatterIPT; ++it) {
+            if (it < nit && cbase + it * kScanThreads + tid < end) {
+                const uint32_t li = loc[(key[it] >> shift) & mask] + lrank[it];
+                skey[li] = key[it];
+                sval[li] = val[it];
+            }
+        }
+        __syncthreads();
+        const int cn = min(kScatterChunk, end - cbase);
+        for (int j = tid; j < cn; j += kScanThreads) {
+            const uint32_t k = skey[j];
+            const uint32_t d = (k >> shift) & mask;
+            const uint32_t pos = run[d] + ((uint32_t)j - loc[d]);
+            if (kout) kout[pos] = k;
+            vout[pos] = sval[j];
+        }
+        __syncthreads();
+        run[tid] += sub[tid];
+        __syncthreads();
     }
 }
 
@@ -395,9 +460,11 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     scan_reduce_kernel<<<G, kScanThreads, 0, st>>>(VisibleCount{rect}, nullptr, (int)R, w.bsum, G);
     scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.bsum, G, w.counts + 0);
     compact_apply_kernel<<<G, kScanThreads, 0, st>>>(rect, geo, (int)R, w.bsum, G, w.dkey_in, w.dval_in);
-    // 2. depth sort (32 bits)
+    // 2. depth sort (32 bits).  Its input (the visible records) is a small fraction of R, so it
+    // runs on a grid of about one scatter chunk per block for R / 4, between G / 4 and G.
+    const int Gd = (int)std::min<int64_t>(G, std::max<int64_t>(G / 4, R / (4 * kScatterChunk)));
     radix_sort(w.dkey_in, w.dval_in, w.dkey_out, w.dval_out, w.dkey_tmp, w.dval_tmp, w.counts + 0,
-               (int)R, 32, w.hist, w.totals, G, st);
+               (int)R, 32, w.hist, w.totals, Gd, st);
     // 3. emission in depth order (K -> lists->count)
     scan_reduce_kernel<<<G, kScanThreads, 0, st>>>(SortedTileCount{rect, w.dval_out}, w.counts + 0, 0,
                                                    w.bsum, G);

@@ -105,7 +105,7 @@ def training_pairs(m, inserted, frames_dev_fn):
     return torch.cat(Xs), torch.cat(Ts)
 
 
-def run(quick=False, train_rooms=3, iters_per_kf=150, keyframes=8, epochs=4, workers=16, log=None):
+def run(quick=False, train_rooms=3, iters_per_kf=150, keyframes=8, epochs=4, workers=16, max_pairs=None, log=None):
     """The whole experiment; returns the result dict (see module docstring)."""
     import synthetic
     pool = None
@@ -136,7 +136,8 @@ def run(quick=False, train_rooms=3, iters_per_kf=150, keyframes=8, epochs=4, wor
             log(f"room {100 + r}: {X.shape[0]} pairs")
     X = torch.cat(Xs)
     T = torch.cat(Ts)
-    n = (X.shape[0] // 4096) * 4096
+    n = min(X.shape[0], max_pairs or X.shape[0])
+    n = (n // 4096) * 4096
     X, T = X[:n].contiguous(), T[:n].contiguous()
     Xt = X.T.contiguous()
     t_data = time.time() - t0
@@ -180,9 +181,10 @@ def main():
     ap.add_argument("--iters-per-kf", type=int, default=150)
     ap.add_argument("--keyframes", type=int, default=8)
     ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--max-pairs", type=int, default=None, help="train on at most this many pairs")
     args = ap.parse_args()
     out = run(quick=args.quick, train_rooms=args.train_rooms, iters_per_kf=args.iters_per_kf,
-              keyframes=args.keyframes, epochs=args.epochs)
+              keyframes=args.keyframes, epochs=args.epochs, max_pairs=args.max_pairs)
     s = json.dumps(out)
     print(s)
     if args.out:
