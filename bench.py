@@ -312,6 +312,28 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------------------
+# Multi-rank aggregation (N independent replicas, one per GPU)
+# ------------------------------------------------------------------------------------------
+
+def max_over_ranks(seconds, device):
+    """The slowest rank's time (every rank returns the same value); the local value when
+    torch.distributed is not initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(seconds)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps, world, seconds):
+    """Iterations per second of the whole job: every rank ran `steps` iterations of its own
+    replica, and the job took the slowest rank's time."""
+    return steps * world / seconds
+
+
+# ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
 
@@ -423,11 +445,8 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     clk = clocks.stop()
     total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = args.steps * world / total_s
+    total_s = max_over_ranks(total_s, dev)
+    value = whole_job_rate(args.steps, world, total_s)
     ms_per = total_s * 1e3 / args.steps
 
     # ---- end to end through the public API with host buffers ----------------------------
@@ -467,11 +486,8 @@ def run_ours(args):
         e2e_s = es.elapsed_time(ee) / 1e3
         h2d = sum(host[k].numel() * 4 for k in PARAM_KEYS) + sum(t.numel() * 4 for f in h_frames for t in f)
         d2h = h_terms.numel() * 4 + sum(host[k].numel() * 4 for k in PARAM_KEYS)
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": args.steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e_s = max_over_ranks(e2e_s, dev)
+        e2e = {"value": whole_job_rate(args.steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     # ---- roofline of the dominant kernel ---------------------------------------------------
