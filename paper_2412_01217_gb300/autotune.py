@@ -1,7 +1,7 @@
 """Launch-shape autotuner of the compositing kernels.
 
 For each screen-tile shape (8x8, 16x8, 16x16, 32x8) one rasterizer is built (the tile
-lists depend on the tile shape); then the shared-memory batch depth (32, 64, 128, 256) and
+lists depend on the tile shape); then the shared-memory batch depth (16, 32, 64, 128, 256) and
 the pixels per thread of the forward (1, 2) and backward (1, 2, 4) kernels are varied in
 place.  Every candidate is timed with CUDA events over a few repetitions of the forward
 (render) and the backward on the caller's own Gaussians, cameras and targets; the
@@ -21,7 +21,7 @@ import torch
 from .splat import PyramidRasterizer, RenderConfig
 
 TILES = ((16, 16), (8, 8), (32, 8), (16, 8))
-BATCHES = (32, 64, 128, 256)
+BATCHES = (16, 32, 64, 128, 256)
 PPT_FWD = (1, 2)
 PPT_BWD = (1, 2, 4)
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "pyramid_splat_gb300_autotune.json")

@@ -110,9 +110,11 @@ __global__ void __launch_bounds__(kLossThreads) ssim_l1_kernel(SsimArgs a) {
             Y[r * kXP + c] = in ? ys[(size_t)gy * W + gx] : 0.f;
         }
         __syncthreads();
-        // horizontal window sums of x, y, x^2, y^2, xy: rows kXH, outputs kMW in runs of 6
+        // Run lengths are chosen so that every phase's work items fill whole rounds of the
+        // block's 256 threads (728, 252, 504 and 256 items).
+        // horizontal window sums of x, y, x^2, y^2, xy: rows kXH, outputs kMW in runs of 3
         {
-            constexpr int RUN = 6, SEGS = kMW / RUN;  // 42 = 7 * 6
+            constexpr int RUN = 3, SEGS = kMW / RUN;  // 42 = 14 * 3
             for (int it = threadIdx.x; it < SEGS * kXH; it += kLossThreads) {
                 const int seg = it / kXH, r = it - seg * kXH;
                 const int c0 = seg * RUN;
@@ -145,9 +147,9 @@ __global__ void __launch_bounds__(kLossThreads) ssim_l1_kernel(SsimArgs a) {
         }
         __syncthreads();
         // vertical window sums -> SSIM and its partials (zero outside the image): columns
-        // kMW, output rows kMH in runs of 6
+        // kMW, output rows kMH in runs of 7
         {
-            constexpr int RUN = 6, SEGS = kMH / RUN;  // 42 = 7 * 6
+            constexpr int RUN = 7, SEGS = kMH / RUN;  // 42 = 6 * 7
             for (int it = threadIdx.x; it < SEGS * kMW; it += kLossThreads) {
                 const int seg = it / kMW, c = it - seg * kMW;
                 const int r0 = seg * RUN;
@@ -193,14 +195,14 @@ __global__ void __launch_bounds__(kLossThreads) ssim_l1_kernel(SsimArgs a) {
         }
         __syncthreads();
         float *Hp = Hm;  // 3 x kMH x kMP, reuses the moment buffer
-        // horizontal sums of the partials: rows kMH, outputs kLTW in runs of 8
+        // horizontal sums of the partials: (partial, row, run of 8 outputs) per item
         {
             constexpr int RUN = 8, SEGS = kLTW / RUN;
-            for (int it = threadIdx.x; it < SEGS * kMH; it += kLossThreads) {
-                const int seg = it / kMH, r = it - seg * kMH;
+            for (int it = threadIdx.x; it < 3 * SEGS * kMH; it += kLossThreads) {
+                const int k = it / (SEGS * kMH), rem = it - k * (SEGS * kMH);
+                const int seg = rem / kMH, r = rem - seg * kMH;
                 const int c0 = seg * RUN;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
+                {
                     float row[RUN + 10];
 #pragma unroll
                     for (int i = 0; i < RUN + 10; ++i) row[i] = Mp[k * kMH * kMP + r * kMP + c0 + i];
@@ -215,10 +217,10 @@ __global__ void __launch_bounds__(kLossThreads) ssim_l1_kernel(SsimArgs a) {
             }
         }
         __syncthreads();
-        // vertical sums of the partials -> dL/dx on the tile: columns kLTW, rows in runs of 8
+        // vertical sums of the partials -> dL/dx on the tile: columns kLTW, rows in runs of 4
         float *gs = a.grad + (size_t)a.nch * vw.pixel_offset + ch * HW;
         {
-            constexpr int RUN = 8, SEGS = kLTH / RUN;
+            constexpr int RUN = 4, SEGS = kLTH / RUN;
             for (int it = threadIdx.x; it < SEGS * kLTW; it += kLossThreads) {
                 const int seg = it / kLTW, c = it - seg * kLTW;
                 const int r0 = seg * RUN;
@@ -977,14 +979,19 @@ __global__ void adam_multi_kernel(AdamGroups G, float b1, float b2, float eps, f
 
 // The same update, four elements per thread with 16-byte loads and stores: start[] counts
 // quads (every group holds a multiple of 4 elements, all arrays 16-byte aligned).
+// ibc1, ibc2: reciprocals of the bias corrections.  sqrt and the division use the fast
+// hardware approximations (a few ulp; the update is a step size, not a value the path
+// returns); sqrt(0) is taken as 0 so that a parameter with no gradient history stays put.
 __device__ __forceinline__ float adam_one(float &m, float &v, float p, float g, float lr, float b1, float b2,
-                                          float eps, float bc1, float bc2) {
+                                          float eps, float ibc1, float ibc2) {
     m = b1 * m + (1.f - b1) * g;
     v = b2 * v + (1.f - b2) * g * g;
-    return p - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+    const float vh = v * ibc2;
+    const float s = vh > 0.f ? vh * rsqrtf(vh) : 0.f;
+    return p - lr * __fdividef(m * ibc1, s + eps);
 }
 
-__global__ void adam_multi4_kernel(AdamGroups G, float b1, float b2, float eps, float bc1, float bc2,
+__global__ void adam_multi4_kernel(AdamGroups G, float b1, float b2, float eps, float ibc1, float ibc2,
                                    int zero_grad) {
     const int64_t total = G.start[G.n];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -999,10 +1006,10 @@ __global__ void adam_multi4_kernel(AdamGroups G, float b1, float b2, float eps, 
         float4 *pp = reinterpret_cast<float4 *>(q.param) + j;
         const float4 g = *gp;
         float4 m = *mp, v = *vp, p = *pp;
-        p.x = adam_one(m.x, v.x, p.x, g.x, q.lr, b1, b2, eps, bc1, bc2);
-        p.y = adam_one(m.y, v.y, p.y, g.y, q.lr, b1, b2, eps, bc1, bc2);
-        p.z = adam_one(m.z, v.z, p.z, g.z, q.lr, b1, b2, eps, bc1, bc2);
-        p.w = adam_one(m.w, v.w, p.w, g.w, q.lr, b1, b2, eps, bc1, bc2);
+        p.x = adam_one(m.x, v.x, p.x, g.x, q.lr, b1, b2, eps, ibc1, ibc2);
+        p.y = adam_one(m.y, v.y, p.y, g.y, q.lr, b1, b2, eps, ibc1, ibc2);
+        p.z = adam_one(m.z, v.z, p.z, g.z, q.lr, b1, b2, eps, ibc1, ibc2);
+        p.w = adam_one(m.w, v.w, p.w, g.w, q.lr, b1, b2, eps, ibc1, ibc2);
         *mp = m;
         *vp = v;
         *pp = p;
@@ -1035,7 +1042,7 @@ sg_status launch_adam_multi(const sg_adam_group *groups, int n, float b1, float 
     if (blocks > 8 * (int64_t)sms) blocks = 8 * (int64_t)sms;
     if (blocks > 0) {
         if (quads)
-            adam_multi4_kernel<<<(int)blocks, 256, 0, st>>>(G, b1, b2, eps, bc1, bc2, zero_grad);
+            adam_multi4_kernel<<<(int)blocks, 256, 0, st>>>(G, b1, b2, eps, 1.f / bc1, 1.f / bc2, zero_grad);
         else
             adam_multi_kernel<<<(int)blocks, 256, 0, st>>>(G, b1, b2, eps, bc1, bc2, zero_grad);
         count_launches(1);

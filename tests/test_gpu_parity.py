@@ -348,3 +348,44 @@ def test_adam_step_matches_numpy():
     p = p0 - 1e-2 * (m / (1 - 0.9 ** 3)) / (np.sqrt(v / (1 - 0.999 ** 3)) + 1e-8)
     assert np.allclose(t[0].cpu().numpy(), p, rtol=1e-5, atol=1e-6)
     assert np.allclose(t[2].cpu().numpy(), m, rtol=1e-5, atol=1e-7)
+
+
+@pytest.mark.parametrize("sizes, offset", [((4000, 1200, 16), 0), ((4001, 7, 33), 1)])
+def test_adam_multi_matches_numpy(sizes, offset):
+    """Fused multi-group Adam: the 16-byte path (every group a multiple of 4 elements, aligned)
+    and the scalar path (odd sizes, one group starting 4 bytes into its buffer); gradients zeroed."""
+    import ctypes as C
+    from paper_2412_01217_gb300._lib import SgAdamGroup, call
+    rng = np.random.default_rng(1)
+    groups, ref, keep = [], [], []
+    for k, n in enumerate(sizes):
+        p0, g0 = rng.normal(size=n), rng.normal(size=n)
+        g0[::17] = 0.0
+        m0, v0 = rng.normal(size=n) * 0.1, rng.uniform(size=n) * 0.1
+        v0[::17] = 0.0
+        m0[::17] = 0.0
+        bufs = []
+        for a in (p0, g0, m0, v0):
+            o = offset if k == 1 else 0
+            t = torch.zeros(n + o, dtype=torch.float32, device="cuda")
+            t[o:] = torch.tensor(a, dtype=torch.float32)
+            bufs.append(t[o:])
+        keep.append(bufs)
+        lr = 1e-2 * (k + 1)
+        groups.append(SgAdamGroup(*[b.data_ptr() for b in bufs], n, lr))
+        # the kernel receives the betas as float32: the reference uses the same values
+        b1, b2 = float(np.float32(0.9)), float(np.float32(0.999))
+        p0, g0, m0, v0 = (np.float32(a).astype(np.float64) for a in (p0, g0, m0, v0))
+        m = b1 * m0 + (1 - b1) * g0
+        v = b2 * v0 + (1 - b2) * g0 ** 2
+        p = p0 - lr * (m / (1 - b1 ** 3)) / (np.sqrt(v / (1 - b2 ** 3)) + 1e-15)
+        ref.append((p, m, v))
+    arr = (SgAdamGroup * len(groups))(*groups)
+    call("sg_adam_multi", arr, len(groups), 0.9, 0.999, 1e-15, 3, 1,
+         C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    for (p, m, v), bufs in zip(ref, keep):
+        assert np.allclose(bufs[0].cpu().numpy(), p, rtol=1e-5, atol=1e-6)
+        assert np.allclose(bufs[2].cpu().numpy(), m, rtol=1e-5, atol=1e-7)
+        assert np.allclose(bufs[3].cpu().numpy(), v, rtol=1e-5, atol=1e-9)
+        assert not bufs[1].any()
