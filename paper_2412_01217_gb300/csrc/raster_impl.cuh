@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
     float4 *s_geo2 = s_geo1 + batch;
     float *s_feat = reinterpret_cast<float *>(s_geo2 + batch);
     const int nthreads = a.tile_w * a.tile_h / PPT;
+    const int lane = threadIdx.x & 31;
     const WarpTile<PPT> wt(a.tile_w);
     const float fx = (float)wt.lx;
     for (int iter = 0;; ++iter) {
@@ -154,8 +155,15 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
                            nullptr, nthreads);
             __syncthreads();
             if (__all_sync(SG_FULL_MASK, n_done == PPT)) continue;
-            for (int j = 0; j < cnt; ++j) {
-                if (wt.misses(s_geo2[j])) continue;  // warp-uniform
+            // 32 entries at a time: lane l tests entry j0 + l against the warp's sub-tile, and
+            // the warp walks the entries that can reach it, front to back
+            for (int j0 = 0; j0 < cnt; j0 += 32) {
+                if (__all_sync(SG_FULL_MASK, n_done == PPT)) break;
+                const int jl = j0 + lane;
+                uint32_t cm = __ballot_sync(SG_FULL_MASK, jl < cnt && !wt.misses(s_geo2[jl]));
+            while (cm) {
+                const int j = j0 + __ffs(cm) - 1;
+                cm &= cm - 1;
                 const float4 g0 = s_geo0[j];
                 const float4 g1 = s_geo1[j];
                 float w[PPT];
@@ -193,6 +201,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
                         acc[k][4 * q + 3] = fmaf(w[k], f.w, acc[k][4 * q + 3]);
                     }
                 }
+            }
             }
         }
         const size_t HW = (size_t)vw.W * vw.H;
