@@ -523,6 +523,26 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
         return p < HW ? semv[(size_t)f * HW + p] : 0.f;
     };
     // ---- Z = S W^T: M = pixels (2 x 16), N = classes, K = features ----
+    // all of the warp's feature loads are issued before the first MMA (memory-level parallelism)
+    float sa[NC][2][4];
+#pragma unroll
+    for (int ks = 0; ks < NC; ++ks)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int r0 = 16 * mt + gid, f0 = 8 * ks + tig;
+            sa[ks][mt][0] = S(r0, f0);
+            sa[ks][mt][1] = S(r0 + 8, f0);
+            sa[ks][mt][2] = S(r0, f0 + 4);
+            sa[ks][mt][3] = S(r0 + 8, f0 + 4);
+        }
+    int labs[2][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int p = pw + 16 * mt + gid + 8 * h;
+            labs[mt][h] = p < HW ? a.label[p0 + p] : -1;
+        }
     float z[2][NK][4];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
@@ -533,11 +553,9 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
             uint32_t ah[4], al[4];
-            const int r0 = 16 * mt + gid, f0 = 8 * ks + tig;
-            split_tf32(S(r0, f0), ah[0], al[0]);
-            split_tf32(S(r0 + 8, f0), ah[1], al[1]);
-            split_tf32(S(r0, f0 + 4), ah[2], al[2]);
-            split_tf32(S(r0 + 8, f0 + 4), ah[3], al[3]);
+            const int f0 = 8 * ks + tig;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) split_tf32(sa[ks][mt][i], ah[i], al[i]);
 #pragma unroll
             for (int nt = 0; nt < NK; ++nt) {
                 const int w0 = (8 * nt + gid) * CP + f0;
@@ -551,8 +569,7 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
     for (int mt = 0; mt < 2; ++mt) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int p = pw + 16 * mt + gid + 8 * h;
-            const int lab = p < HW ? a.label[p0 + p] : -1;
+            const int lab = labs[mt][h];
             float m = -INFINITY;
 #pragma unroll
             for (int nt = 0; nt < NK; ++nt) m = fmaxf(m, fmaxf(z[mt][nt][2 * h], z[mt][nt][2 * h + 1]));
