@@ -104,11 +104,12 @@ typedef struct {
     float fov_clamp; /* 1.3:    Jacobian evaluated at t_x/t_z clamped to fov_clamp*W/2fx */
     float bg[3];     /* background RGB (depth and semantic background are 0)          */
     int32_t tile_w, tile_h; /* screen tile: 8x8, 16x8, 16x16 or 32x8                  */
-    int32_t batch;          /* Gaussians staged per shared-memory batch: 32..256      */
+    int32_t batch;          /* Gaussians staged per shared-memory batch: 16..512, step 16 */
     int32_t persistent;     /* 1: persistent grid with an atomic work queue           */
     int32_t pixels_per_thread;     /* forward: 1, 2 or 4 pixels per thread (rows 4 apart);
                                       tile_h % (4 * it) == 0, tile pixels >= 32 * it       */
     int32_t pixels_per_thread_bwd; /* the same for the backward kernel                    */
+    int32_t batch_bwd;      /* batch of the backward kernel; 0: the same as `batch`    */
 } sg_config;
 
 /* Projected records of all (view-level, Gaussian) pairs: record r = v*N + g. */

@@ -2,8 +2,8 @@
 
 For each screen-tile shape (8x8, 16x8, 16x16, 32x8) one rasterizer is built (the tile
 lists depend on the tile shape); then the shared-memory batch depth (16, 32, 64, 128, 256) and
-the pixels per thread of the forward (1, 2) and backward (1, 2, 4) kernels are varied in
-place.  Every candidate is timed with CUDA events over a few repetitions of the forward
+the pixels per thread are varied in place, for the forward (1, 2 pixels per thread) and, with
+its own batch depth, for the backward (1, 2, 4).  Every candidate is timed with CUDA events over a few repetitions of the forward
 (render) and the backward on the caller's own Gaussians, cameras and targets; the
 configuration with the smallest forward + backward time wins.  The forward output does
 not depend on any of these choices (bit-identical across them, which the tests check), so
@@ -63,7 +63,7 @@ def autotune(params, cams, levels, gt, loss_cfg, base: RenderConfig | None = Non
     table = []
     best = None
     for tw, th in TILES:
-        cfg0 = replace(base, tile_w=tw, tile_h=th, pixels_per_thread=1, pixels_per_thread_bwd=1)
+        cfg0 = replace(base, tile_w=tw, tile_h=th, pixels_per_thread=1, pixels_per_thread_bwd=1, batch_bwd=0)
         r = PyramidRasterizer(N, C, cams, levels, cfg0, loss_cfg=loss_cfg)
         grads = {k: torch.zeros_like(v) for k, v in params.items()}
         r.project(params)
@@ -73,8 +73,9 @@ def autotune(params, cams, levels, gt, loss_cfg, base: RenderConfig | None = Non
         r.loss(gt, decoder=decoder, decoder_grad=dec_grad)
         torch.cuda.synchronize()
         r.check_status()
+        # forward: batch x pixels per thread
+        fwd_best = None
         for batch in BATCHES:
-            fwd_best = None
             for ppt in PPT_FWD:
                 if not _valid(tw, th, ppt):
                     continue
@@ -83,27 +84,30 @@ def autotune(params, cams, levels, gt, loss_cfg, base: RenderConfig | None = Non
                 t = _time(lambda: r.rasterize(params), reps)
                 table.append(dict(tile=f"{tw}x{th}", batch=batch, kernel="fwd", ppt=ppt, ms=t))
                 if fwd_best is None or t < fwd_best[0]:
-                    fwd_best = (t, ppt)
-            r.cfg = replace(cfg0, batch=batch, pixels_per_thread=fwd_best[1])
-            r._ccfg = r.cfg.to_c()
-            r.rasterize(params)
-            bwd_best = None
+                    fwd_best = (t, batch, ppt)
+        # backward (its own batch and pixels per thread; the saved state does not depend on them)
+        r.cfg = replace(cfg0, batch=fwd_best[1], pixels_per_thread=fwd_best[2])
+        r._ccfg = r.cfg.to_c()
+        r.rasterize(params)
+        bwd_best = None
+        for batch in BATCHES:
             for ppt in PPT_BWD:
                 if not _valid(tw, th, ppt):
                     continue
-                r.cfg = replace(cfg0, batch=batch, pixels_per_thread=fwd_best[1], pixels_per_thread_bwd=ppt)
+                r.cfg = replace(cfg0, batch=fwd_best[1], pixels_per_thread=fwd_best[2], batch_bwd=batch,
+                                pixels_per_thread_bwd=ppt)
                 r._ccfg = r.cfg.to_c()
                 t = _time(lambda: r.backward(params, grads), reps)
                 table.append(dict(tile=f"{tw}x{th}", batch=batch, kernel="bwd", ppt=ppt, ms=t))
                 if bwd_best is None or t < bwd_best[0]:
-                    bwd_best = (t, ppt)
-            total = fwd_best[0] + bwd_best[0]
-            if log:
-                log(f"tile {tw}x{th} batch {batch}: fwd {fwd_best[0]:.3f} ms (ppt {fwd_best[1]}), "
-                    f"bwd {bwd_best[0]:.3f} ms (ppt {bwd_best[1]})")
-            if best is None or total < best[0]:
-                best = (total, dict(tile_w=tw, tile_h=th, batch=batch, pixels_per_thread=fwd_best[1],
-                                    pixels_per_thread_bwd=bwd_best[1]))
+                    bwd_best = (t, batch, ppt)
+        total = fwd_best[0] + bwd_best[0]
+        if log:
+            log(f"tile {tw}x{th}: fwd {fwd_best[0]:.3f} ms (batch {fwd_best[1]}, ppt {fwd_best[2]}), "
+                f"bwd {bwd_best[0]:.3f} ms (batch {bwd_best[1]}, ppt {bwd_best[2]})")
+        if best is None or total < best[0]:
+            best = (total, dict(tile_w=tw, tile_h=th, batch=fwd_best[1], pixels_per_thread=fwd_best[2],
+                                batch_bwd=bwd_best[1], pixels_per_thread_bwd=bwd_best[2]))
         del r, grads
         torch.cuda.empty_cache()
     chosen = replace(base, **best[1])

@@ -80,6 +80,8 @@ static sg_status check_cfg(const sg_config *c) {
     SG_REQUIRE(t <= kMaxTileThreads, "tile too large");
     SG_REQUIRE(c->batch >= 16 && c->batch <= 512 && (c->batch % 16) == 0, "batch %d not in [16, 512] step 16",
                c->batch);
+    SG_REQUIRE(c->batch_bwd == 0 || (c->batch_bwd >= 16 && c->batch_bwd <= 512 && (c->batch_bwd % 16) == 0),
+               "batch_bwd %d not 0 or in [16, 512] step 16", c->batch_bwd);
     SG_REQUIRE(c->alpha_min > 0.f && c->alpha_max <= 1.f && c->alpha_min < c->alpha_max,
                "need 0 < alpha_min < alpha_max <= 1");
     SG_REQUIRE(c->T_min >= 0.f && c->z_near > 0.f && c->dilation >= 0.f && c->fov_clamp > 0.f,
@@ -127,6 +129,7 @@ void sg_default_config(sg_config *c) {
     c->persistent = 1;
     c->pixels_per_thread = 1;
     c->pixels_per_thread_bwd = 2;
+    c->batch_bwd = 0;
 }
 
 void sg_default_loss_config(sg_loss_config *c) {
@@ -317,6 +320,7 @@ sg_status sg_render_pyramid_backward_raster(const sg_gaussians *g, const sg_proj
     a.g_rgb = grads->rgb;
     a.g_sem = grads->sem;
     a.ppt = cfg->pixels_per_thread_bwd;
+    if (cfg->batch_bwd) a.batch = cfg->batch_bwd;
     return launch_raster(a, g->C, true, st);
 }
 

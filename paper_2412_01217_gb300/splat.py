@@ -48,6 +48,7 @@ class RenderConfig:
     persistent: bool = True
     pixels_per_thread: int = 1
     pixels_per_thread_bwd: int = 2
+    batch_bwd: int = 0  # 0: same as batch
 
     def to_c(self):
         c = SgConfig()
@@ -58,6 +59,7 @@ class RenderConfig:
         c.tile_w, c.tile_h, c.batch, c.persistent = self.tile_w, self.tile_h, self.batch, int(self.persistent)
         c.pixels_per_thread = int(self.pixels_per_thread)
         c.pixels_per_thread_bwd = int(self.pixels_per_thread_bwd)
+        c.batch_bwd = int(self.batch_bwd)
         return c
 
 

@@ -163,12 +163,14 @@ def test_autotuner_picks_a_valid_configuration_with_identical_output():
     gt = build_pyramid(r, [f["rgb"] for f in frames], [f["depth"] for f in frames], [f["label"] for f in frames])
     dec = torch.randn(32, 16, device="cuda") * 0.3
     cfg, table = autotune(p, cams, 3, gt, LossConfig(n_classes=32), decoder=dec, reps=1, use_cache=False)
-    assert (cfg.tile_w, cfg.tile_h) in ((16, 16), (8, 8), (32, 8), (16, 8)) and cfg.batch in (64, 128, 256)
+    from paper_2412_01217_gb300.autotune import BATCHES
+    assert (cfg.tile_w, cfg.tile_h) in ((16, 16), (8, 8), (32, 8), (16, 8))
+    assert cfg.batch in BATCHES and cfg.batch_bwd in BATCHES
     assert len(table) >= 20 and all(t["ms"] > 0 for t in table)
     r.forward(p)
     base = r.img_rgb.clone()
     r2, _ = make(g, cams, levels=3, **{k: getattr(cfg, k) for k in ("tile_w", "tile_h", "batch", "pixels_per_thread",
-                                                                        "pixels_per_thread_bwd")})
+                                                                        "pixels_per_thread_bwd", "batch_bwd")})
     r2.forward(p)
     torch.cuda.synchronize()
     assert torch.equal(r2.img_rgb, base)

@@ -184,10 +184,10 @@ def test_forward_bitwise_identical_across_tiles_batches_and_runs(cloud):
             assert np.array_equal(im[k], base[k]), (k, tw, th, batch, pers, ppt)
 
 
-@pytest.mark.parametrize("ppt", [1, 2, 4])
-def test_backward_matches_oracle_cloud(cloud, ppt):
+@pytest.mark.parametrize("ppt, batch_bwd", [(1, 0), (2, 0), (4, 0), (1, 16), (2, 64)])
+def test_backward_matches_oracle_cloud(cloud, ppt, batch_bwd):
     g, cam = cloud
-    r, p = make(g, [cam], pixels_per_thread_bwd=ppt)
+    r, p = make(g, [cam], pixels_per_thread_bwd=ppt, batch_bwd=batch_bwd)
     r.forward(p)
     ref_f = oracle.render(g, cam)
     keep = ((ref_f["flags"] & AMBIGUOUS_GRAD) == 0).astype(np.float64)
