@@ -68,16 +68,24 @@ struct SsimArgs {
     const sg_view *views;
     LossViews lv;
     float *partials;     // per CTA: (sum |x - y|, sum ssim)
+    // valid-pixel counts (counts[2v]: target depth > 0, counts[2v+1]: label >= 0) gathered
+    // on the side, or null
+    const float *gt_depth;
+    const int *label;
+    int *counts;
 };
 
 // Sliding-window separable passes: each thread produces a run of consecutive outputs of one
 // row (horizontal) or column (vertical) from a register window of input values.
-__global__ void __launch_bounds__(kLossThreads) ssim_l1_kernel(SsimArgs a) {
+__global__ void __launch_bounds__(kLossThreads, 3) ssim_l1_kernel(SsimArgs a) {
     extern __shared__ __align__(16) float sm[];
     float *X = sm;                   // kXH x kXP
     float *Y = X + kXH * kXP;        // kXH x kXP
     float *Hm = Y + kXH * kXP;       // 5 x kXH x kMP (later: 3 x kMH x kMP)
-    float *Mp = Hm + 5 * kXH * kMP;  // 3 x kMH x kMP
+    float *Mp = X;                   // 3 x kMH x kMP: reuses the staged planes once the
+                                     // horizontal pass has consumed them
+    static_assert(3 * kMH * kMP <= 2 * kXH * kXP, "partials must fit the staged planes");
+    __shared__ int s_cnt[2];
     __shared__ float w[11];
     __shared__ float s_red[kLossThreads / 32];
     if (threadIdx.x == 0) gauss_window(w);
@@ -94,6 +102,8 @@ __global__ void __launch_bounds__(kLossThreads) ssim_l1_kernel(SsimArgs a) {
     const float l1c = a.l1_coef_num / n, sc = -a.ssim_coef_num / n;
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
     float l1_sum = 0.f, ssim_sum = 0.f;
+    int n_depth = 0, n_label = 0;
+    if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     float wr[11];
 #pragma unroll
@@ -243,7 +253,12 @@ __global__ void __launch_bounds__(kLossThreads) ssim_l1_kernel(SsimArgs a) {
                     const int r = r0 + o;
                     const int gy = by * kLTH + r, gx = bx * kLTW + c;
                     if (gx >= W || gy >= H) continue;
-                    const float xv = X[(r + 10) * kXP + c + 10], yv = Y[(r + 10) * kXP + c + 10];
+                    const size_t gp = (size_t)gy * W + gx;
+                    const float xv = xs[gp], yv = ys[gp];  // the staged planes now hold partials
+                    if (ch == 0 && a.counts) {
+                        n_depth += a.gt_depth[(size_t)vw.pixel_offset + gp] > 0.f;
+                        if (a.label) n_label += a.label[(size_t)vw.pixel_offset + gp] >= 0;
+                    }
                     const float d = xv - yv;
                     l1_sum += fabsf(d);
                     const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
@@ -253,44 +268,29 @@ __global__ void __launch_bounds__(kLossThreads) ssim_l1_kernel(SsimArgs a) {
         }
         __syncthreads();
     }
-    const float t1 = block_sum(l1_sum, s_red);
+    if (a.counts) {
+        n_depth = __reduce_add_sync(SG_FULL_MASK, n_depth);
+        n_label = __reduce_add_sync(SG_FULL_MASK, n_label);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&s_cnt[0], n_depth);
+            atomicAdd(&s_cnt[1], n_label);
+        }
+    }
+    const float t1 = block_sum(l1_sum, s_red);  // (its barriers also order the counts above)
     const float t2 = block_sum(ssim_sum, s_red);
     if (threadIdx.x == 0) {
         a.partials[2 * item] = t1;
         a.partials[2 * item + 1] = t2;
+        // integer atomics: the totals do not depend on the order
+        if (a.counts && s_cnt[0]) atomicAdd(a.counts + 2 * v, s_cnt[0]);
+        if (a.counts && s_cnt[1]) atomicAdd(a.counts + 2 * v + 1, s_cnt[1]);
     }
 }
 
 // ---------------------------------------------------------------------------------------
-// valid-pixel counts, depth L1, cross-entropy
+// depth L1, cross-entropy
 // ---------------------------------------------------------------------------------------
 
-__global__ void loss_count_kernel(const float *gt_depth, const int *label, const sg_view *views,
-                                  LossViews lv, int *counts) {
-    __shared__ int s_cnt[2];
-    if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0;
-    __syncthreads();
-    const int blk = blockIdx.x;
-    const int v = find_prefix(lv.pix_blk_off, lv.n, blk);
-    const sg_view &vw = views[v];
-    const int p = (blk - lv.pix_blk_off[v]) * kLossThreads + threadIdx.x;
-    const int HW = vw.W * vw.H;
-    int cd = 0, cl = 0;
-    if (p < HW) {
-        cd = gt_depth[(size_t)vw.pixel_offset + p] > 0.f;
-        cl = label ? label[(size_t)vw.pixel_offset + p] >= 0 : 0;
-    }
-    cd = __reduce_add_sync(SG_FULL_MASK, cd);
-    cl = __reduce_add_sync(SG_FULL_MASK, cl);
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&s_cnt[0], cd);
-        atomicAdd(&s_cnt[1], cl);
-    }
-    __syncthreads();
-    // one global atomic per block and counter (integer: order-independent)
-    if (threadIdx.x == 0 && s_cnt[0]) atomicAdd(counts + 2 * v, s_cnt[0]);
-    if (threadIdx.x == 1 && s_cnt[1]) atomicAdd(counts + 2 * v + 1, s_cnt[1]);
-}
 
 struct PixelArgs {
     const float *depth, *gt_depth, *sem;
@@ -773,7 +773,7 @@ __global__ void loss_finalize_kernel(FinalArgs a) {
 
 // ---------------------------------------------------------------------------------------
 
-static size_t ssim_smem() { return sizeof(float) * (2 * kXH * kXP + 5 * kXH * kMP + 3 * kMH * kMP); }
+static size_t ssim_smem() { return sizeof(float) * (2 * kXH * kXP + 5 * kXH * kMP); }
 
 static void make_loss_views(const sg_view *vh, int n_views, LossViews &lv) {
     lv.n = n_views;
@@ -856,17 +856,17 @@ sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *v
         return SG_ERR_CAPACITY;
     }
     cudaMemsetAsync(counts, 0, sizeof(int) * 2 * n_views, st);
-    loss_count_kernel<<<n_blocks, kLossThreads, 0, st>>>(gt->depth, ce ? gt->label : nullptr, views, lv, counts);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(ssim_l1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssim_smem());
         attr = true;
     }
-    SsimArgs sa{r->rgb, gt->rgb, dL->rgb, 3, 1.f - lc->lambda_r, lc->lambda_r, views, lv, p_rgb};
+    SsimArgs sa{r->rgb, gt->rgb, dL->rgb, 3, 1.f - lc->lambda_r, lc->lambda_r, views, lv, p_rgb,
+                gt->depth, ce ? gt->label : nullptr, counts};
     ssim_l1_kernel<<<n_tiles, kLossThreads, ssim_smem(), st>>>(sa);
     if (!ce) {
         SsimArgs ss{r->sem, gt->sem, dL->sem, C, lc->w_sem * (1.f - lc->lambda_s), lc->w_sem * lc->lambda_s,
-                    views, lv, p_sem};
+                    views, lv, p_sem, nullptr, nullptr, nullptr};
         ssim_l1_kernel<<<n_tiles, kLossThreads, ssim_smem(), st>>>(ss);
     }
     PixelArgs pa{r->depth, gt->depth, r->sem, gt->label, dL->depth, dL->sem, lc->decoder,
@@ -883,7 +883,7 @@ sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *v
     FinalArgs fa{p_rgb, ce ? nullptr : p_sem, p_pix, counts, views, lv, C, lc->sem_mode,
                  lc->lambda_r, lc->lambda_s, lc->w_depth, lc->w_sem, terms};
     loss_finalize_kernel<<<n_views, kLossThreads, 0, st>>>(fa);
-    count_launches(ce ? 4 : 5);
+    count_launches(ce ? 3 : 4);
     return check_launch("pyramid_loss");
 }
 
