@@ -78,6 +78,7 @@ struct SsimArgs {
 // Sliding-window separable passes: each thread produces a run of consecutive outputs of one
 // row (horizontal) or column (vertical) from a register window of input values.
 __global__ void __launch_bounds__(kLossThreads, 3) ssim_l1_kernel(SsimArgs a) {
+    pdl_begin();
     extern __shared__ __align__(16) float sm[];
     float *X = sm;                   // kXH x kXP
     float *Y = X + kXH * kXP;        // kXH x kXP
@@ -313,6 +314,7 @@ struct PixelArgs {
 constexpr int kDecChunks = 128;
 __global__ void decoder_reduce1_kernel(const float *__restrict__ part, int n_blocks, int KC,
                                        float *__restrict__ chunk_sums) {
+    pdl_begin();
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (o >= KC) return;
@@ -322,6 +324,7 @@ __global__ void decoder_reduce1_kernel(const float *__restrict__ part, int n_blo
     chunk_sums[(size_t)c * KC + o] = s;
 }
 __global__ void decoder_reduce2_kernel(const float *__restrict__ chunk_sums, int KC, float *__restrict__ out) {
+    pdl_begin();
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= KC) return;
     float s = 0.f;
@@ -337,6 +340,7 @@ template <int K> __host__ __device__ constexpr int stash_pitch() { return K + 4;
 
 template <int C, int K>
 __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
+    pdl_begin();
     static_assert(C % 4 == 0 && K % 4 == 0, "float4 stashes");
     constexpr int KP = stash_pitch<K>(), CP = stash_pitch<C>();
     __shared__ __align__(16) float s_dec[K * C];
@@ -478,6 +482,7 @@ __host__ __device__ constexpr int ce_mma_smem_floats() {
 
 template <int C, int K>
 __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder_mma_kernel(PixelArgs a) {
+    pdl_begin();
     static_assert(C % 8 == 0 && K % 16 == 0, "MMA tiles");
     constexpr int CP = C + 4;   // decoder row pitch: 4 mod 8, conflict-free B fragments
     constexpr int KP = K + 8;   // dZ row pitch: 8 or 24 mod 32, conflict-free A fragments
@@ -702,7 +707,7 @@ static void launch_ce_mma(PixelArgs &pa, int blocks, cudaStream_t st) {
         cudaFuncSetAttribute(ce_decoder_mma_kernel<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    ce_decoder_mma_kernel<C, K><<<blocks, kLossThreads, smem, st>>>(pa);
+    launch_pdl(ce_decoder_mma_kernel<C, K>, blocks, kLossThreads, smem, st, pa);
 }
 
 struct FinalArgs {
@@ -715,11 +720,25 @@ struct FinalArgs {
     float *terms;
 };
 
+// Sum of v over the block in double, in a fixed order (warp butterflies, then the warps in
+// order); the result is valid in thread 0.
+__device__ __forceinline__ double block_sum_d(double v, double *s_w) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(SG_FULL_MASK, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kLossThreads / 32; ++w) t += s_w[w];
+    return t;
+}
+
 __global__ void loss_finalize_kernel(FinalArgs a) {
+    pdl_begin();
     const int v = blockIdx.x;
     const sg_view &vw = a.views[v];
     const double HW = (double)vw.W * vw.H;
-    __shared__ double s_red[4][kLossThreads];
+    __shared__ double s_w[kLossThreads / 32];
     double acc[4] = {0, 0, 0, 0};
     for (int i = a.lv.tile_off[v] + threadIdx.x; i < a.lv.tile_off[v + 1]; i += kLossThreads) {
         acc[0] += a.ssim_rgb[2 * i];
@@ -729,30 +748,17 @@ __global__ void loss_finalize_kernel(FinalArgs a) {
             acc[3] += a.ssim_sem[2 * i + 1];
         }
     }
-    for (int k = 0; k < 4; ++k) s_red[k][threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int s = kLossThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int k = 0; k < 4; ++k) s_red[k][threadIdx.x] += s_red[k][threadIdx.x + s];
-        __syncthreads();
-    }
-    double r[4];
-    for (int k = 0; k < 4; ++k) r[k] = s_red[k][0];
-    __syncthreads();
     double b[2] = {0, 0};
     for (int i = a.lv.pix_blk_off[v] + threadIdx.x; i < a.lv.pix_blk_off[v + 1]; i += kLossThreads) {
         b[0] += a.pix[2 * i];
         b[1] += a.pix[2 * i + 1];
     }
-    for (int k = 0; k < 2; ++k) s_red[k][threadIdx.x] = b[k];
-    __syncthreads();
-    for (int s = kLossThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int k = 0; k < 2; ++k) s_red[k][threadIdx.x] += s_red[k][threadIdx.x + s];
-        __syncthreads();
-    }
+    double r[4];
+    for (int k = 0; k < 4; ++k) r[k] = block_sum_d(acc[k], s_w);
+    const double l1d_sum = block_sum_d(b[0], s_w);
+    const double ce_sum = block_sum_d(b[1], s_w);
     if (threadIdx.x == 0) {
-        const double l1d = s_red[0][0], ce = s_red[1][0];
+        const double l1d = l1d_sum, ce = ce_sum;
         const int nd = a.counts[2 * v], nl = a.counts[2 * v + 1];
         const double n_rgb = 3.0 * HW;
         const double L_r = (1.0 - a.lambda_r) * r[0] / n_rgb + a.lambda_r * (1.0 - r[1] / n_rgb);
@@ -816,7 +822,7 @@ static void launch_pixel_t(PixelArgs &pa, int blocks, cudaStream_t st) {
         cudaFuncSetAttribute(loss_pixel_kernel<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
         attr = true;
     }
-    loss_pixel_kernel<C, K><<<blocks, kLossThreads, dyn, st>>>(pa);
+    launch_pdl(loss_pixel_kernel<C, K>, blocks, kLossThreads, dyn, st, pa);
 }
 
 static bool launch_pixel(PixelArgs &pa, int blocks, cudaStream_t st) {
@@ -863,11 +869,11 @@ sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *v
     }
     SsimArgs sa{r->rgb, gt->rgb, dL->rgb, 3, 1.f - lc->lambda_r, lc->lambda_r, views, lv, p_rgb,
                 gt->depth, ce ? gt->label : nullptr, counts};
-    ssim_l1_kernel<<<n_tiles, kLossThreads, ssim_smem(), st>>>(sa);
+    launch_pdl(ssim_l1_kernel, n_tiles, kLossThreads, ssim_smem(), st, sa);
     if (!ce) {
         SsimArgs ss{r->sem, gt->sem, dL->sem, C, lc->w_sem * (1.f - lc->lambda_s), lc->w_sem * lc->lambda_s,
                     views, lv, p_sem, nullptr, nullptr, nullptr};
-        ssim_l1_kernel<<<n_tiles, kLossThreads, ssim_smem(), st>>>(ss);
+        launch_pdl(ssim_l1_kernel, n_tiles, kLossThreads, ssim_smem(), st, ss);
     }
     PixelArgs pa{r->depth, gt->depth, r->sem, gt->label, dL->depth, dL->sem, lc->decoder,
                  lc->decoder_grad, C, K, ce, lc->w_depth, lc->w_sem, counts, views, lv, p_pix, p_dec};
@@ -876,13 +882,13 @@ sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *v
         return SG_ERR_INVALID_ARG;
     }
     if (ce && lc->decoder_grad) {
-        decoder_reduce1_kernel<<<dim3((KC + 127) / 128, kDecChunks), 128, 0, st>>>(p_dec, n_blocks, KC, p_dec2);
-        decoder_reduce2_kernel<<<(KC + 127) / 128, 128, 0, st>>>(p_dec2, KC, lc->decoder_grad);
+        launch_pdl(decoder_reduce1_kernel, dim3((KC + 127) / 128, kDecChunks), 128, 0, st, p_dec, n_blocks, KC, p_dec2);
+        launch_pdl(decoder_reduce2_kernel, (KC + 127) / 128, 128, 0, st, p_dec2, KC, lc->decoder_grad);
         count_launches(2);
     }
     FinalArgs fa{p_rgb, ce ? nullptr : p_sem, p_pix, counts, views, lv, C, lc->sem_mode,
                  lc->lambda_r, lc->lambda_s, lc->w_depth, lc->w_sem, terms};
-    loss_finalize_kernel<<<n_views, kLossThreads, 0, st>>>(fa);
+    launch_pdl(loss_finalize_kernel, n_views, kLossThreads, 0, st, fa);
     count_launches(ce ? 3 : 4);
     return check_launch("pyramid_loss");
 }
@@ -893,6 +899,7 @@ sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *v
 
 __global__ void pyramid_down_kernel(float *rgb, float *depth, int *label, float *sem, int n_sem,
                                     sg_view src, sg_view dst) {
+    pdl_begin();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= dst.W || y >= dst.H) return;
@@ -944,7 +951,7 @@ sg_status launch_pyramid(float *rgb, float *depth, int *label, float *sem, int n
                 return SG_ERR_INVALID_ARG;
             }
             const dim3 blk(32, 8), grd((vh[v].W + 31) / 32, (vh[v].H + 7) / 8);
-            pyramid_down_kernel<<<grd, blk, 0, st>>>(rgb, depth, label, sem, n_sem, vh[s], vh[v]);
+            launch_pdl(pyramid_down_kernel, grd, blk, 0, st, rgb, depth, label, sem, n_sem, vh[s], vh[v]);
             count_launches(1);
         }
     return check_launch("build_pyramid");
@@ -957,6 +964,7 @@ sg_status launch_pyramid(float *rgb, float *depth, int *label, float *sem, int n
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                             float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
                             float bc1, float bc2) {
+    pdl_begin();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -977,6 +985,7 @@ struct AdamGroups {
 
 __global__ void adam_multi_kernel(AdamGroups G, float b1, float b2, float eps, float bc1, float bc2,
                                   int zero_grad) {
+    pdl_begin();
     const int64_t total = G.start[G.n];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -1010,6 +1019,7 @@ __device__ __forceinline__ float adam_one(float &m, float &v, float p, float g, 
 
 __global__ void adam_multi4_kernel(AdamGroups G, float b1, float b2, float eps, float ibc1, float ibc2,
                                    int zero_grad) {
+    pdl_begin();
     const int64_t total = G.start[G.n];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -1059,9 +1069,9 @@ sg_status launch_adam_multi(const sg_adam_group *groups, int n, float b1, float 
     if (blocks > 8 * (int64_t)sms) blocks = 8 * (int64_t)sms;
     if (blocks > 0) {
         if (quads)
-            adam_multi4_kernel<<<(int)blocks, 256, 0, st>>>(G, b1, b2, eps, 1.f / bc1, 1.f / bc2, zero_grad);
+            launch_pdl(adam_multi4_kernel, (int)blocks, 256, 0, st, G, b1, b2, eps, 1.f / bc1, 1.f / bc2, zero_grad);
         else
-            adam_multi_kernel<<<(int)blocks, 256, 0, st>>>(G, b1, b2, eps, bc1, bc2, zero_grad);
+            launch_pdl(adam_multi_kernel, (int)blocks, 256, 0, st, G, b1, b2, eps, bc1, bc2, zero_grad);
         count_launches(1);
     }
     return check_launch("adam_multi");
@@ -1076,7 +1086,7 @@ sg_status launch_adam(float *p, const float *g, float *m, float *v, int64_t n, f
     int64_t blocks = (n + 255) / 256;
     if (blocks > 8 * (int64_t)sms) blocks = 8 * (int64_t)sms;
     if (blocks > 0) {
-        adam_kernel<<<(int)blocks, 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
+        launch_pdl(adam_kernel, (int)blocks, 256, 0, st, p, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
         count_launches(1);
     }
     return check_launch("adam");

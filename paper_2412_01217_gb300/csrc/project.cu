@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     const float4 *__restrict__ quat, const float *__restrict__ ologit, int N,
     const sg_view *__restrict__ views, int n_views, ProjConsts pc, float4 *__restrict__ geo,
     uint2 *__restrict__ rect, float2 *__restrict__ ext) {
+    pdl_begin();
     __shared__ sg_view s_views[SG_MAX_VIEWS];
     for (int i = threadIdx.x; i < n_views; i += blockDim.x) s_views[i] = views[i];
     __syncthreads();
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     const sg_view *__restrict__ views, int n_views, ProjConsts pc,
     const uint2 *__restrict__ rect, const float4 *__restrict__ g2d, float *__restrict__ g_mean, float *__restrict__ g_ls,
     float *__restrict__ g_quat, float *__restrict__ g_ologit) {
+    pdl_begin();
     __shared__ sg_view s_views[SG_MAX_VIEWS];
     for (int i = threadIdx.x; i < n_views; i += blockDim.x) s_views[i] = views[i];
     __syncthreads();
@@ -325,7 +327,7 @@ sg_status launch_project_fwd(const sg_gaussians *g, const sg_view *views, int n_
     const int threads = 256;
     const int blocks = (g->N + threads - 1) / threads;
     if (blocks > 0)
-        project_fwd_kernel<<<blocks, threads, 0, st>>>(
+        launch_pdl(project_fwd_kernel, blocks, threads, 0, st,
             g->mean, g->log_scale, reinterpret_cast<const float4 *>(g->quat), g->opacity_logit,
             g->N, views, n_views, pc, reinterpret_cast<float4 *>(out->geo),
             reinterpret_cast<uint2 *>(out->rect), reinterpret_cast<float2 *>(out->ext));
@@ -341,7 +343,7 @@ sg_status launch_project_bwd(const sg_gaussians *g, const sg_view *views, int n_
     const int threads = 256;
     const int blocks = (g->N + threads - 1) / threads;
     if (blocks > 0)
-        project_bwd_kernel<<<blocks, threads, 0, st>>>(
+        launch_pdl(project_bwd_kernel, blocks, threads, 0, st,
             g->mean, g->log_scale, reinterpret_cast<const float4 *>(g->quat), g->opacity_logit,
             g->N, views, n_views, pc, reinterpret_cast<const uint2 *>(proj->rect),
             reinterpret_cast<const float4 *>(g2d),

@@ -109,6 +109,7 @@ __device__ __forceinline__ TileInfo tile_info(const RasterArgs &a, int item) {
 
 template <int C, int PPT>
 __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs a) {
+    pdl_begin();
     constexpr int NF = 4 + C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
@@ -294,6 +295,7 @@ __device__ __forceinline__ void moment_grads(const float (&M)[6], float U, float
 
 template <int C, int PPT>
 __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs a) {
+    pdl_begin();
     constexpr int NF = 4 + C;                     // rgb(3) depth | sem(C)
     constexpr int NFP = padded_features<NF>();    // features padded to 8
     constexpr int NT = NFP / 8;                   // 8-feature tiles
@@ -574,9 +576,9 @@ sg_status launch_raster_cp(RasterArgs &a, bool backward, cudaStream_t st) {
     }
     if (grid <= 0) return SG_OK;
     if (backward)
-        raster_bwd_kernel<C, PPT><<<grid, threads, smem, st>>>(a);
+        launch_pdl(raster_bwd_kernel<C, PPT>, grid, threads, smem, st, a);
     else
-        raster_fwd_kernel<C, PPT><<<grid, threads, smem, st>>>(a);
+        launch_pdl(raster_fwd_kernel<C, PPT>, grid, threads, smem, st, a);
     count_launches(1);
     return check_launch(backward ? "raster_bwd" : "raster_fwd");
 }

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/sg.h"
 
 #define SG_FULL_MASK 0xffffffffu
@@ -153,6 +155,36 @@ __device__ __forceinline__ void mma_tf32x3(float (&d)[4], const uint32_t (&ah)[4
     mma_tf32(d, al, bh0, bh1);
     mma_tf32(d, ah, bl0, bl1);
     mma_tf32(d, ah, bh0, bh1);
+}
+
+// ----------------------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of one iteration are launched with
+// launch_pdl() (programmatic stream serialisation), and every kernel starts with
+// pdl_begin(): griddepcontrol.wait, which returns once the grids it depends on have completed
+// and their writes are visible (at once when the launch has no such dependency).  Nothing
+// before it touches global memory, so the ordering is that of plain stream order; the
+// launch of each kernel is prepared while its predecessor runs.  (Letting dependents start
+// early with griddepcontrol.launch_dependents was measured slower: their waiting blocks take
+// SM slots from the running kernel.)
+// ----------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 __device__ __forceinline__ int find_view(const sg_view *views, int n_views, int tile) {

@@ -86,6 +86,7 @@ struct SortedTileCount {  // tiles of the record at sorted position i
 
 template <class F>
 __global__ void scan_reduce_kernel(F f, const int *n_ptr, int n_host, uint32_t *bsum, int G) {
+    pdl_begin();
     const int n = n_ptr ? *n_ptr : n_host;
     int beg, end;
     block_range(n, G, blockIdx.x, beg, end);
@@ -104,6 +105,7 @@ __global__ void scan_reduce_kernel(F f, const int *n_ptr, int n_host, uint32_t *
 
 // One block: exclusive scan of G block sums (G <= 4096); writes the grand total.
 __global__ void scan_blocks_kernel(uint32_t *bsum, int G, int *total) {
+    pdl_begin();
     uint32_t run = 0;
     for (int base = 0; base < G; base += kScanThreads) {
         const int i = base + threadIdx.x;
@@ -120,6 +122,7 @@ __global__ void scan_blocks_kernel(uint32_t *bsum, int G, int *total) {
 __global__ void compact_apply_kernel(const uint2 *__restrict__ rect, const float4 *__restrict__ geo,
                                      int n, const uint32_t *__restrict__ boff, int G,
                                      uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
+    pdl_begin();
     int beg, end;
     block_range(n, G, blockIdx.x, beg, end);
     uint32_t run = boff[blockIdx.x];
@@ -148,6 +151,7 @@ __global__ void emit_apply_kernel(const uint2 *__restrict__ rect, const uint32_t
                                   int G, int N, const sg_view *__restrict__ views,
                                   uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval,
                                   int capacity, uint32_t *__restrict__ status) {
+    pdl_begin();
     const int n = *m_ptr;
     int beg, end;
     block_range(n, G, blockIdx.x, beg, end);
@@ -234,6 +238,7 @@ struct TileLengthKeys {
 template <class Src>
 __global__ void rs_hist_kernel(Src src, const int *__restrict__ n_ptr, int cap, int shift, uint32_t mask,
                                uint32_t *__restrict__ hist, int G) {
+    pdl_begin();
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -248,6 +253,7 @@ __global__ void rs_hist_kernel(Src src, const int *__restrict__ n_ptr, int cap, 
 
 // Block d: exclusive scan of digit d's per-block counts; totals[d] = digit d's count.
 __global__ void rs_digit_scan_kernel(uint32_t *__restrict__ hist, uint32_t *__restrict__ totals, int G) {
+    pdl_begin();
     const int d = blockIdx.x;
     uint32_t run = 0;
     for (int base = 0; base < G; base += kScanThreads) {
@@ -274,6 +280,7 @@ __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
     Src src, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ n_ptr, int cap, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, int G) {
+    pdl_begin();
     constexpr int kWarps = kScanThreads / 32;
     __shared__ uint32_t run[256];   // global position of the next element of each digit
     __shared__ uint32_t sub[256];   // elements of each digit so far in this chunk
@@ -365,19 +372,23 @@ static void radix_sort(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
         uint32_t *kd = ((passes - 1 - p) % 2 == 0) ? kout : ktmp;
         uint32_t *vd = ((passes - 1 - p) % 2 == 0) ? vout : vtmp;
         const ArrayPairs src{ks, vs};
-        rs_hist_kernel<<<G, kScanThreads, 0, st>>>(src, n_ptr, cap, shift, mask, hist, G);
-        rs_digit_scan_kernel<<<256, kScanThreads, 0, st>>>(hist, totals, G);
-        rs_scatter_kernel<<<G, kScanThreads, 0, st>>>(src, kd, vd, n_ptr, cap, shift, mask, hist, totals, G);
+        launch_pdl(rs_hist_kernel<ArrayPairs>, G, kScanThreads, 0, st, src, n_ptr, cap, shift, mask, hist, G);
+        launch_pdl(rs_digit_scan_kernel, 256, kScanThreads, 0, st, hist, totals, G);
+        launch_pdl(rs_scatter_kernel<ArrayPairs>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap, shift, mask, hist, totals, G);
         count_launches(3);
         ks = kd;
         vs = vd;
     }
 }
 
-__global__ void clamp_count_kernel(const int *in, int cap, int *out) { *out = min(*in, cap); }
+__global__ void clamp_count_kernel(const int *in, int cap, int *out) {
+    pdl_begin();
+    *out = min(*in, cap);
+}
 
 __global__ void ranges_kernel(const uint32_t *__restrict__ tile, const int *__restrict__ k_ptr,
                               int2 *__restrict__ ranges) {
+    pdl_begin();
     const int K = *k_ptr;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) {
         const uint32_t t = tile[i];
@@ -457,19 +468,19 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     const uint2 *rect = reinterpret_cast<const uint2 *>(proj->rect);
     const float4 *geo = reinterpret_cast<const float4 *>(proj->geo);
     // 1. compaction of visible records (count -> counts[0])
-    scan_reduce_kernel<<<G, kScanThreads, 0, st>>>(VisibleCount{rect}, nullptr, (int)R, w.bsum, G);
-    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.bsum, G, w.counts + 0);
-    compact_apply_kernel<<<G, kScanThreads, 0, st>>>(rect, geo, (int)R, w.bsum, G, w.dkey_in, w.dval_in);
+    launch_pdl(scan_reduce_kernel<VisibleCount>, G, kScanThreads, 0, st, VisibleCount{rect}, nullptr, (int)R, w.bsum, G);
+    launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.bsum, G, w.counts + 0);
+    launch_pdl(compact_apply_kernel, G, kScanThreads, 0, st, rect, geo, (int)R, w.bsum, G, w.dkey_in, w.dval_in);
     // 2. depth sort (32 bits).  Its input (the visible records) is a small fraction of R, so it
     // runs on a grid of about one scatter chunk per block for R / 4, between G / 4 and G.
     const int Gd = (int)std::min<int64_t>(G, std::max<int64_t>(G / 4, R / (4 * kScatterChunk)));
     radix_sort(w.dkey_in, w.dval_in, w.dkey_out, w.dval_out, w.dkey_tmp, w.dval_tmp, w.counts + 0,
                (int)R, 32, w.hist, w.totals, Gd, st);
     // 3. emission in depth order (K -> lists->count)
-    scan_reduce_kernel<<<G, kScanThreads, 0, st>>>(SortedTileCount{rect, w.dval_out}, w.counts + 0, 0,
+    launch_pdl(scan_reduce_kernel<SortedTileCount>, G, kScanThreads, 0, st, SortedTileCount{rect, w.dval_out}, w.counts + 0, 0,
                                                    w.bsum, G);
-    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(w.bsum, G, lists->count);
-    emit_apply_kernel<<<G, kScanThreads, 0, st>>>(rect, w.dval_out, w.counts + 0, w.bsum, G, N, views,
+    launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.bsum, G, lists->count);
+    launch_pdl(emit_apply_kernel, G, kScanThreads, 0, st, rect, w.dval_out, w.counts + 0, w.bsum, G, N, views,
                                                   w.tkey_in, w.tval_in, lists->capacity, status);
     // 4. stable sort by tile id
     int bits = 1;
@@ -478,16 +489,16 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
                lists->count, lists->capacity, bits, w.hist, w.totals, G, st);
     // 5. tile ranges
     cudaMemsetAsync(lists->ranges, 0, sizeof(int) * 2 * (size_t)n_tiles, st);
-    clamp_count_kernel<<<1, 1, 0, st>>>(lists->count, lists->capacity, w.counts + 1);
-    ranges_kernel<<<G, kScanThreads, 0, st>>>(lists->tile, w.counts + 1,
+    launch_pdl(clamp_count_kernel, 1, 1, 0, st, lists->count, lists->capacity, w.counts + 1);
+    launch_pdl(ranges_kernel, G, kScanThreads, 0, st, lists->tile, w.counts + 1,
                                               reinterpret_cast<int2 *>(lists->ranges));
     count_launches(3 + 3 + 2);  // compaction, emission, clamp + ranges
     // 6. work order: one stable counting pass over the 6-bit length keys
     if (lists->order) {
         const TileLengthKeys src{reinterpret_cast<const int2 *>(lists->ranges)};
-        rs_hist_kernel<<<G, kScanThreads, 0, st>>>(src, nullptr, n_tiles, 0, 63u, w.hist, G);
-        rs_digit_scan_kernel<<<256, kScanThreads, 0, st>>>(w.hist, w.totals, G);
-        rs_scatter_kernel<<<G, kScanThreads, 0, st>>>(src, nullptr, reinterpret_cast<uint32_t *>(lists->order),
+        launch_pdl(rs_hist_kernel<TileLengthKeys>, G, kScanThreads, 0, st, src, nullptr, n_tiles, 0, 63u, w.hist, G);
+        launch_pdl(rs_digit_scan_kernel, 256, kScanThreads, 0, st, w.hist, w.totals, G);
+        launch_pdl(rs_scatter_kernel<TileLengthKeys>, G, kScanThreads, 0, st, src, nullptr, reinterpret_cast<uint32_t *>(lists->order),
                                                       nullptr, n_tiles, 0, 63u, w.hist, w.totals, G);
         count_launches(3);
     }
