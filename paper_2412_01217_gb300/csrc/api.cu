@@ -319,6 +319,7 @@ sg_status sg_render_pyramid_backward_raster(const sg_gaussians *g, const sg_proj
     a.g2d = g2d;
     a.g_rgb = grads->rgb;
     a.g_sem = grads->sem;
+    a.sem_v2 = ((uintptr_t)grads->sem % 8) == 0 && (g->C % 2) == 0;
     a.ppt = cfg->pixels_per_thread_bwd;
     if (cfg->batch_bwd) a.batch = cfg->batch_bwd;
     return launch_raster(a, g->C, true, st);

@@ -29,6 +29,7 @@ struct RasterArgs {
     // backward
     const float *dL_rgb, *dL_depth, *dL_sem;
     float *g2d, *g_rgb, *g_sem;
+    int sem_v2;  // g_sem is 8-byte aligned (pairs of semantic gradients in one vector reduction)
 };
 
 inline void fill_raster_args(RasterArgs &a, const sg_gaussians *g, const sg_projected *proj,

@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
                 uint32_t cmask = __ballot_sync(SG_FULL_MASK, cand);
                 if (!cmask) continue;
                 // ---- gf = G F^T for the chunk (M = pixels, N = entries, K = features) ----
-#pragma unroll 1
+#pragma unroll(MT <= 2 ? 2 : 1)
                 for (int mt = 0; mt < MT; ++mt) {
                     float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
@@ -491,9 +491,16 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
                     const uint32_t gi = rec - rec_base;
 #pragma unroll
                     for (int nt = 0; nt < NT; ++nt) {
+                        // features 2 tig, 2 tig + 1 of this n-tile: both semantic (C even) ->
+                        // one 8-byte vector reduction when the buffer allows it
+                        const int f0 = 8 * nt + 2 * tig;
+                        if (a.sem_v2 && f0 >= 4 && f0 + 1 < NF) {
+                            red_add_v2(a.g_sem + (size_t)C * gi + (f0 - 4), df[nt][2 * hr], df[nt][2 * hr + 1]);
+                            continue;
+                        }
 #pragma unroll
                         for (int c2 = 0; c2 < 2; ++c2) {
-                            const int f = 8 * nt + 2 * tig + c2;
+                            const int f = f0 + c2;
                             const float val = df[nt][2 * hr + c2];
                             if (f >= NF) continue;
                             if (f < 3)

@@ -157,6 +157,11 @@ __device__ __forceinline__ void mma_tf32x3(float (&d)[4], const uint32_t (&ah)[4
     mma_tf32(d, ah, bh0, bh1);
 }
 
+// Two float additions to consecutive, 8-byte aligned addresses in one vector reduction.
+__device__ __forceinline__ void red_add_v2(float *addr, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};\n" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
+
 // ----------------------------------------------------------------------------------------
 // Programmatic dependent launch.  The kernels of one iteration are launched with
 // launch_pdl() (programmatic stream serialisation), and every kernel starts with
