@@ -367,6 +367,15 @@ sg_status sg_gemm_bf16(const uint16_t *A, int64_t lda, const uint16_t *B, int64_
                        int32_t N, int32_t K, float *D, int64_t ldd, int32_t accumulate,
                        uint32_t *status, sg_stream_t stream);
 
+/* Self-test of the failure detection of the tensor-core kernels (no counterpart in the
+ * paper).  Launches sg_gemm_bf16's kernel (store mode) whose CTAs first wait on an mbarrier
+ * that nothing arrives on, bounded by `polls` polls (1..2^20).  Each CTA must give up, set
+ * SG_STATUS_TIMEOUT in *status, skip its output (D is left untouched), release its tensor
+ * memory and return, so the context stays usable.  Arguments as for sg_gemm_bf16. */
+sg_status sg_gemm_bf16_timeout_probe(const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb,
+                                     int32_t M, int32_t N, int32_t K, float *D, int64_t ldd,
+                                     uint32_t polls, uint32_t *status, sg_stream_t stream);
+
 /* fp32 master weights ([out][in]) -> the bf16 operand copies of sg_mlp.  W3t's padding
  * columns 32..63 are not written: the caller zeroes W3t once. */
 sg_status sg_mlp_pack_weights(const float *W1, const float *W2, const float *W3, uint16_t *W1b,

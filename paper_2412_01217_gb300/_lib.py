@@ -87,6 +87,7 @@ STATUS = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CAPACITY", 3: "SG_ERR_
           4: "SG_ERR_NUMERIC", 5: "SG_ERR_CUDA"}
 STATUS_CAPACITY = 1
 STATUS_NUMERIC = 2
+STATUS_TIMEOUT = 4
 MAX_VIEWS = 64
 
 # every entry point declared in include/sg.h: name -> (restype, argtypes)
@@ -122,6 +123,8 @@ SIGNATURES = {
     "sg_adam_step": (c_i, [c_p, c_p, c_p, c_p, C.c_int64, c_f, c_f, c_f, c_f, c_i, c_p]),
     "sg_adam_multi": (c_i, [P(SgAdamGroup), c_i, c_f, c_f, c_f, c_i, c_i, c_p]),
     "sg_gemm_bf16": (c_i, [c_p, C.c_int64, c_p, C.c_int64, c_i, c_i, c_i, c_p, C.c_int64, c_i, c_p, c_p]),
+    "sg_gemm_bf16_timeout_probe": (c_i, [c_p, C.c_int64, c_p, C.c_int64, c_i, c_i, c_i, c_p, C.c_int64, C.c_uint32,
+                                         c_p, c_p]),
     "sg_mlp_pack_weights": (c_i, [c_p] * 8 + [c_p]),
     "sg_mlp_forward": (c_i, [P(SgMlp), c_p, c_i, P(SgMlpActs), c_p, c_p]),
     "sg_mlp_backward": (c_i, [P(SgMlp), c_p, c_p, c_p, c_i, P(SgMlpActs), P(SgMlpGrads), c_p, c_p, c_p]),

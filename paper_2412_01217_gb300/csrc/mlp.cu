@@ -170,6 +170,21 @@ sg_status sg_gemm_bf16(const uint16_t *A, int64_t lda, const uint16_t *B, int64_
     return launch_gemm(p, (cudaStream_t)stream);
 }
 
+sg_status sg_gemm_bf16_timeout_probe(const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb, int32_t M,
+                                     int32_t N, int32_t K, float *D, int64_t ldd, uint32_t polls,
+                                     uint32_t *status, sg_stream_t stream) {
+    MLP_REQUIRE(A && B && D, "gemm: NULL operand");
+    MLP_REQUIRE(M > 0 && N > 0 && K > 0 && K % 64 == 0, "gemm: need M, N > 0 and K %% 64 == 0");
+    MLP_REQUIRE(lda % 8 == 0 && ldb % 8 == 0 && ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0,
+                "gemm: operands need 16-byte aligned rows");
+    MLP_REQUIRE(polls >= 1 && polls <= (1u << 20), "timeout probe: polls must be in [1, 2^20]");
+    tc::GemmParams p = gemm_params((const bf16 *)A, lda, (const bf16 *)B, ldb, M, N, K, status);
+    p.out_f32 = D;
+    p.ld_f32 = ldd;
+    p.probe_polls = polls;
+    return launch_gemm(p, (cudaStream_t)stream);
+}
+
 sg_status sg_mlp_pack_weights(const float *W1, const float *W2, const float *W3, uint16_t *W1b, uint16_t *W2b,
                               uint16_t *W3b, uint16_t *W2t, uint16_t *W3t, sg_stream_t stream) {
     MLP_REQUIRE(W1 && W2 && W3 && W1b && W2b && W3b && W2t && W3t, "pack_weights: NULL argument");

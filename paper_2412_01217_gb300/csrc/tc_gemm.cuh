@@ -60,8 +60,8 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *bar, uint32_t parity
     return ok;
 }
 // Bounded wait for the phase with the given parity; false after kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kSpinLimit) {
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -147,6 +147,9 @@ struct GemmParams {
     int f32_transposed;
     int f32_atomic;  // 1: atomicAdd (split-K / accumulation), 0: store
     uint32_t *status;
+    // failure-detection self-test: before its main loop the CTA waits on a barrier that
+    // nothing arrives on, bounded by probe_polls polls; 0 = no such wait
+    uint32_t probe_polls;
 };
 
 template <int BN, int STAGES>
@@ -159,6 +162,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const GemmParams p) {
     constexpr uint32_t IDESC = idesc_bf16_f32(128, BN);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ uint64_t bars[STAGES];
+    __shared__ uint64_t probe_bar;
     __shared__ uint32_t tmem_base_s;
     __shared__ int s_timeout;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -171,6 +175,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const GemmParams p) {
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        mbar_init(&probe_bar, 1);
         s_timeout = 0;
         fence_mbar_init();
     }
@@ -182,6 +187,14 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const GemmParams p) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_s;
+    if (p.probe_polls) {
+        // phase 0 of probe_bar never completes: the wait gives up after probe_polls polls
+        if (tid == 0 && !mbar_wait(&probe_bar, 0, p.probe_polls)) {
+            s_timeout = 1;
+            if (p.status) atomicOr(p.status, SG_STATUS_TIMEOUT_BIT);
+        }
+        __syncthreads();
+    }
 
     auto load_stage = [&](int kc, int s) {
         const int k0 = k_begin + kc * 64;

@@ -83,3 +83,15 @@ def test_host_validation_rejects_bad_arguments():
     assert b"NULL" in lib.sg_last_error()
     assert lib.sg_adam_step(None, None, None, None, 5, 1e-3, 0.9, 0.999, 1e-8, 0, None) == 1
     assert lib.sg_adam_step(None, None, None, None, 0, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 0
+
+
+def test_timeout_probe_validates_on_the_host():
+    """The failure-detection self-test refuses bad arguments before any launch."""
+    from paper_2412_01217_gb300 import _lib
+    lib = _lib.load()
+    assert lib.sg_gemm_bf16_timeout_probe(None, 64, None, 64, 128, 32, 64, None, 32, 1000, None, None) == 1
+    # a poll bound of 0 would disable the probe's wait: rejected
+    import ctypes as C
+    buf = (C.c_uint16 * 64)()
+    fbuf = (C.c_float * 64)()
+    assert lib.sg_gemm_bf16_timeout_probe(buf, 64, buf, 64, 128, 32, 64, fbuf, 32, 0, None, None) == 1

@@ -49,6 +49,29 @@ def test_tcgen05_gemm_split_k_accumulate():
     assert (D.double() - ref).abs().max().item() <= 1e-5 * ref.abs().max().item() + 1e-3
 
 
+def test_tcgen05_bounded_wait_times_out_reports_and_leaves_context_usable():
+    """Failure detection without a fault: every CTA waits on an mbarrier nothing arrives on,
+    gives up after 1000 polls, sets SG_STATUS_TIMEOUT, writes nothing, frees its tensor
+    memory and returns; the next GEMM on the same stream is correct."""
+    from paper_2412_01217_gb300._lib import STATUS_TIMEOUT, call
+    torch.manual_seed(7)
+    M, N, K = 256, 128, 256
+    A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda").to(torch.bfloat16)
+    D = torch.full((M, N), 7.0, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    call("sg_gemm_bf16_timeout_probe", _p(A), K, _p(B), K, M, N, K, _p(D), N, 1000, _p(status), _s())
+    torch.cuda.synchronize()
+    assert int(status.item()) & STATUS_TIMEOUT
+    assert torch.all(D == 7.0)
+    status.zero_()
+    call("sg_gemm_bf16", _p(A), K, _p(B), K, M, N, K, _p(D), N, 0, _p(status), _s())
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = A.double() @ B.double().T
+    assert (D.double() - ref).abs().max().item() <= 1e-5 * ref.abs().max().item() + 1e-4
+
+
 class Net:
     def __init__(self, seed=0):
         g = torch.Generator().manual_seed(seed)
