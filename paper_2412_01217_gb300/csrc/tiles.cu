@@ -302,6 +302,14 @@ __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
         sub[tid] = 0;
         const int nit = min(kScatterIPT, (end - cbase + kScanThreads - 1) / kScanThreads);  // block-uniform
         uint32_t key[kScatterIPT], val[kScatterIPT], lrank[kScatterIPT];
+        // all of the chunk's loads first (their latencies overlap), then the ranking
+#pragma unroll
+        for (int it = 0; it < kScatterIPT; ++it) {
+            const int i = cbase + it * kScanThreads + tid;
+            const bool valid = it < nit && i < end;
+            key[it] = valid ? src.key(i) : 0u;
+            val[it] = valid ? src.val(i) : 0u;
+        }
 #pragma unroll
         for (int it = 0; it < kScatterIPT; ++it) {
             if (it >= nit) break;
@@ -310,8 +318,6 @@ __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
             __syncthreads();
             const int i = cbase + it * kScanThreads + tid;
             const bool valid = i < end;
-            key[it] = valid ? src.key(i) : 0u;
-            val[it] = valid ? src.val(i) : 0u;
             const uint32_t d = valid ? ((key[it] >> shift) & mask) : 256u;
             const uint32_t peers = __match_any_sync(SG_FULL_MASK, d);
             const uint32_t rank = __popc(peers & lt_mask);
@@ -441,7 +447,7 @@ static size_t tile_ws_layout(int64_t R, int32_t cap, int G, TileWorkspace *ws, c
     w.tval_in = (uint32_t *)take(c4);
     w.tkey_tmp = (uint32_t *)take(c4);
     w.tval_tmp = (uint32_t *)take(c4);
-    w.bsum = (uint32_t *)take((size_t)G * 4);
+    w.bsum = (uint32_t *)take((size_t)4 * G * 4);  // up to 4 G blocks (the emission grid)
     w.hist = (uint32_t *)take((size_t)G * 256 * 4);
     w.totals = (uint32_t *)take(256 * 4);
     w.counts = (int *)take(4 * sizeof(int));
@@ -477,10 +483,14 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     radix_sort(w.dkey_in, w.dval_in, w.dkey_out, w.dval_out, w.dkey_tmp, w.dval_tmp, w.counts + 0,
                (int)R, 32, w.hist, w.totals, Gd, st);
     // 3. emission in depth order (K -> lists->count)
-    launch_pdl(scan_reduce_kernel<SortedTileCount>, G, kScanThreads, 0, st, SortedTileCount{rect, w.dval_out}, w.counts + 0, 0,
-                                                   w.bsum, G);
-    launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.bsum, G, lists->count);
-    launch_pdl(emit_apply_kernel, G, kScanThreads, 0, st, rect, w.dval_out, w.counts + 0, w.bsum, G, N, views,
+    // The emission runs on a finer grid for large inputs (up to 4 G blocks, about one per 2048
+    // records): its blocks own ranges of depth-sorted records, and the near (large) ones,
+    // which emit most of the instances, come first.
+    const int Ge = (int)std::min<int64_t>(4 * G, std::max<int64_t>(G, R / 2048));
+    launch_pdl(scan_reduce_kernel<SortedTileCount>, Ge, kScanThreads, 0, st, SortedTileCount{rect, w.dval_out},
+               w.counts + 0, 0, w.bsum, Ge);
+    launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.bsum, Ge, lists->count);
+    launch_pdl(emit_apply_kernel, Ge, kScanThreads, 0, st, rect, w.dval_out, w.counts + 0, w.bsum, Ge, N, views,
                                                   w.tkey_in, w.tval_in, lists->capacity, status);
     // 4. stable sort by tile id
     int bits = 1;
