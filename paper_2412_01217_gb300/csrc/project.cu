@@ -219,11 +219,31 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     float gmu[3] = {0.f, 0.f, 0.f};
     float gSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // full-entry gradient, symmetric
     float go_total = 0.f;
-    for (int v = 0; v < n_views; ++v) {
-        const size_t r = (size_t)v * N + g;
-        const uint2 rc = rect[r];
-        if (rc.x == rc.y) continue;  // culled (empty rectangle)
-        const float4 a = g2d[2 * r], b = g2d[2 * r + 1];
+    // Visible view-levels first, 32 at a time, with all tile-rectangle loads in flight
+    // together; then the visible ones, each one's 2D gradients loaded one view ahead.
+    for (int v0 = 0; v0 < n_views; v0 += 32) {
+    uint32_t vis = 0;
+    const int nv = min(32, n_views - v0);
+#pragma unroll 8
+    for (int i = 0; i < nv; ++i) {
+        const uint2 rc = rect[(size_t)(v0 + i) * N + g];
+        vis |= (rc.x != rc.y ? 1u : 0u) << i;  // an empty rectangle means culled
+    }
+    float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
+    if (vis) {
+        const size_t r = (size_t)(v0 + __ffs(vis) - 1) * N + g;
+        na = g2d[2 * r];
+        nb = g2d[2 * r + 1];
+    }
+    while (vis) {
+        const int v = v0 + __ffs(vis) - 1;
+        vis &= vis - 1;
+        const float4 a = na, b = nb;
+        if (vis) {
+            const size_t rn = (size_t)(v0 + __ffs(vis) - 1) * N + g;
+            na = g2d[2 * rn];
+            nb = g2d[2 * rn + 1];
+        }
         const float gu = a.x, gv = a.y, ga = a.z, gb = a.w, gc = b.x, go = b.y, gd = b.z;
         const sg_view &vw = s_views[v];
         ViewGeom q;
@@ -288,6 +308,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
         gt2 += -gu * vw.fx * q.t[0] / tz2 - gv * vw.fy * q.t[1] / tz2 + gd;
         for (int j = 0; j < 3; ++j) gmu[j] += W[j] * gt0 + W[3 + j] * gt1 + W[6 + j] * gt2;
         go_total += go;
+    }
     }
     // Sig = M M^T with M = R diag(S): dM = 2 gSig M
     float M[9];
