@@ -1,9 +1,12 @@
 // project.cu -- EWA projection of 3D Gaussians into every (view, pyramid level) and its
 // adjoint (Eq. 2-3 generalised to anisotropic Gaussians; Sec. III-D backpropagation).
 //
-// One thread per Gaussian loops over the view-levels: the Gaussian's parameters (44 B) are
-// read once and its 3D covariance is formed once, then one 32-byte record and one 8-byte
-// tile rectangle are written per view-level.  The view table sits in shared memory.
+// One thread per Gaussian loops over the view-levels.  Forward: the Gaussian's parameters
+// (44 B) are read once and its 3D covariance is formed once, then one 32-byte record, one
+// 8-byte tile rectangle and the 8-byte extents are written per view-level.  Backward: the
+// view-levels where it is visible are gathered first (all rectangle loads in flight at once),
+// then the chain rule runs on each with the next one's 2D gradients already loading.  The
+// view table sits in shared memory.
 #include "sg_common.cuh"
 
 namespace sg {
