@@ -219,8 +219,9 @@ sg_status sg_build_tile_lists(const sg_projected *proj, int32_t N, int32_t n_vie
                               uint32_t *status, sg_stream_t stream);
 
 /* Eq. 7-9 for every view-level in one launch: per tile, front-to-back compositing of RGB,
- * depth and C semantic channels.  work_counter: device int32 scratch (zeroed by the call)
- * for the persistent work queue. */
+ * depth and C semantic channels.  work_counter: 2 int32 of device scratch for the persistent
+ * work queue, zero before the first call; every call leaves them zero (the last CTA resets
+ * them), so one pair can serve all calls on a stream. */
 sg_status sg_render_pyramid(const sg_gaussians *g, const sg_projected *proj,
                             const sg_tile_lists *lists, const sg_view *views, int32_t n_views,
                             int32_t n_tiles, const sg_config *cfg, sg_images *out,
@@ -266,7 +267,8 @@ sg_status sg_pyramid_loss_noalloc(const sg_images *rendered, const sg_targets *g
 /* Backward path                                                                        */
 /* ---------------------------------------------------------------------------------- */
 
-/* Scratch bytes sg_render_pyramid_backward needs. */
+/* Scratch bytes sg_render_pyramid_backward needs.  Zero the workspace once after allocating
+ * it; every backward leaves it zero (see sg_render_pyramid_backward_raster below). */
 size_t sg_backward_workspace_size(int64_t n_records);
 
 /* Adjoint of sg_render_pyramid followed by the adjoint of sg_project_gaussians (Sec. III-D
@@ -283,12 +285,16 @@ sg_status sg_render_pyramid_backward(const sg_gaussians *g, const sg_projected *
 
 /* The two halves of sg_render_pyramid_backward, for callers that time or schedule them
  * apart (same arguments, same workspace):
- *   sg_render_pyramid_backward_raster: the compositing adjoint.  Overwrites the workspace
- *     with dL/d(2D mean, conic, opacity, depth) per record (8 floats per record) and ADDS
- *     dL/d{rgb, sem} into grads.
+ *   sg_render_pyramid_backward_raster: the compositing adjoint.  ADDS dL/d(2D mean, conic,
+ *     opacity, depth) per record into the workspace (8 floats per record) and dL/d{rgb, sem}
+ *     into grads.
  *   sg_project_gaussians_backward: the chain rule through the EWA projection from those
- *     per-record gradients; ADDS dL/d{mean, log_scale, quat, opacity_logit} into grads.
- * Calling both in this order on one stream equals sg_render_pyramid_backward. */
+ *     per-record gradients; ADDS dL/d{mean, log_scale, quat, opacity_logit} into grads and
+ *     zeroes the per-record slots it consumed.
+ * The workspace must be all zero when the compositing adjoint starts: zero it once after
+ * allocating it; each projection adjoint then leaves it zero again (only records visible in
+ * some view-level are ever written, and those are the ones it consumes).  Calling both in
+ * this order on one stream equals sg_render_pyramid_backward. */
 sg_status sg_render_pyramid_backward_raster(const sg_gaussians *g, const sg_projected *proj,
                                             const sg_tile_lists *lists, const sg_view *views,
                                             int32_t n_views, int32_t n_tiles, const sg_config *cfg,
@@ -298,7 +304,7 @@ sg_status sg_render_pyramid_backward_raster(const sg_gaussians *g, const sg_proj
                                             sg_stream_t stream);
 sg_status sg_project_gaussians_backward(const sg_gaussians *g, const sg_projected *proj,
                                         const sg_view *views, int32_t n_views, const sg_config *cfg,
-                                        const void *workspace, size_t workspace_bytes,
+                                        void *workspace, size_t workspace_bytes,
                                         sg_gaussian_grads *grads, sg_stream_t stream);
 
 /* ---------------------------------------------------------------------------------- */

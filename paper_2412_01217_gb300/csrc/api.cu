@@ -33,7 +33,7 @@ sg_status check_launch(const char *what) {
 sg_status launch_project_fwd(const sg_gaussians *, const sg_view *, int, const sg_config *,
                              sg_projected *, cudaStream_t);
 sg_status launch_project_bwd(const sg_gaussians *, const sg_view *, int, const sg_config *,
-                             const sg_projected *, const float *, sg_gaussian_grads *, cudaStream_t);
+                             const sg_projected *, float *, sg_gaussian_grads *, cudaStream_t);
 size_t tile_lists_workspace_size(int64_t R, int32_t cap);
 sg_status launch_build_tile_lists(const sg_projected *, int, int, const sg_view *, int,
                                   sg_tile_lists *, void *, size_t, uint32_t *, cudaStream_t);
@@ -306,8 +306,7 @@ sg_status sg_render_pyramid_backward_raster(const sg_gaussians *g, const sg_proj
     SG_REQUIRE(proj && lists && saved && dL, "NULL argument");
     SG_REQUIRE(!cfg->persistent || work_counter, "persistent launch needs work_counter");
     cudaStream_t st = (cudaStream_t)stream;
-    float *g2d = (float *)workspace;
-    cudaMemsetAsync(g2d, 0, sg_backward_workspace_size((int64_t)g->N * n_views), st);
+    float *g2d = (float *)workspace;  // zero on entry (see sg.h)
     RasterArgs a{};
     fill_raster_args(a, g, proj, lists, views, n_views, n_tiles, cfg, work_counter);
     a.T_final = saved->T_final;
@@ -327,11 +326,11 @@ sg_status sg_render_pyramid_backward_raster(const sg_gaussians *g, const sg_proj
 
 sg_status sg_project_gaussians_backward(const sg_gaussians *g, const sg_projected *proj,
                                         const sg_view *views, int32_t n_views, const sg_config *cfg,
-                                        const void *workspace, size_t workspace_bytes,
+                                        void *workspace, size_t workspace_bytes,
                                         sg_gaussian_grads *grads, sg_stream_t stream) {
     SG_TRY(check_backward(g, views, n_views, cfg, workspace, workspace_bytes, grads));
     SG_REQUIRE(proj, "NULL argument");
-    return launch_project_bwd(g, views, n_views, cfg, proj, (const float *)workspace, grads,
+    return launch_project_bwd(g, views, n_views, cfg, proj, (float *)workspace, grads,
                               (cudaStream_t)stream);
 }
 

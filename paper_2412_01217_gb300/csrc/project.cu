@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     const float *__restrict__ mean, const float *__restrict__ log_scale,
     const float4 *__restrict__ quat, const float *__restrict__ ologit, int N,
     const sg_view *__restrict__ views, int n_views, ProjConsts pc,
-    const uint2 *__restrict__ rect, const float4 *__restrict__ g2d, float *__restrict__ g_mean, float *__restrict__ g_ls,
+    const uint2 *__restrict__ rect, float4 *__restrict__ g2d, float *__restrict__ g_mean, float *__restrict__ g_ls,
     float *__restrict__ g_quat, float *__restrict__ g_ologit) {
     pdl_begin();
     __shared__ sg_view s_views[SG_MAX_VIEWS];
@@ -242,6 +242,13 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
         const int v = v0 + __ffs(vis) - 1;
         vis &= vis - 1;
         const float4 a = na, b = nb;
+        {
+            // consumed: zero the record's slots, so the workspace is all zero for the next
+            // compositing adjoint (only visible records are ever written)
+            const size_t r = (size_t)v * N + g;
+            g2d[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            g2d[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         if (vis) {
             const size_t rn = (size_t)(v0 + __ffs(vis) - 1) * N + g;
             na = g2d[2 * rn];
@@ -360,7 +367,7 @@ sg_status launch_project_fwd(const sg_gaussians *g, const sg_view *views, int n_
 }
 
 sg_status launch_project_bwd(const sg_gaussians *g, const sg_view *views, int n_views,
-                             const sg_config *cfg, const sg_projected *proj, const float *g2d,
+                             const sg_config *cfg, const sg_projected *proj, float *g2d,
                              sg_gaussian_grads *gr, cudaStream_t st) {
     ProjConsts pc{cfg->z_near, cfg->dilation, cfg->fov_clamp, cfg->alpha_min, cfg->tile_w,
                   cfg->tile_h};
@@ -370,7 +377,7 @@ sg_status launch_project_bwd(const sg_gaussians *g, const sg_view *views, int n_
         launch_pdl(project_bwd_kernel, blocks, threads, 0, st,
             g->mean, g->log_scale, reinterpret_cast<const float4 *>(g->quat), g->opacity_logit,
             g->N, views, n_views, pc, reinterpret_cast<const uint2 *>(proj->rect),
-            reinterpret_cast<const float4 *>(g2d),
+            reinterpret_cast<float4 *>(g2d),
             gr->mean, gr->log_scale, gr->quat, gr->opacity_logit);
     if (blocks > 0) count_launches(1);
     return check_launch("project_bwd");

@@ -66,9 +66,19 @@ __device__ __forceinline__ void load_batch(const RasterArgs &a, int C, int list_
     }
 }
 
+// Persistent work queue: work_counter[0] hands out slots, work_counter[1] counts the CTAs
+// that have drawn their terminating slot; the last of them zeroes both, so the queue is
+// ready for the next launch without a memset.
 __device__ __forceinline__ int next_item(const RasterArgs &a, int &s_item) {
     if (!a.persistent) return blockIdx.x;
-    if (threadIdx.x == 0) s_item = atomicAdd(a.work_counter, 1);
+    if (threadIdx.x == 0) {
+        const int slot = atomicAdd(a.work_counter, 1);
+        if (slot >= a.n_tiles && atomicAdd(a.work_counter + 1, 1) == (int)gridDim.x - 1) {
+            a.work_counter[0] = 0;
+            a.work_counter[1] = 0;
+        }
+        s_item = slot;
+    }
     __syncthreads();
     return s_item;
 }
@@ -579,7 +589,6 @@ sg_status launch_raster_cp(RasterArgs &a, bool backward, cudaStream_t st) {
     if (a.persistent) {
         grid = resident_grid(fn, threads, smem);
         if (grid > a.n_tiles) grid = a.n_tiles;
-        cudaMemsetAsync(a.work_counter, 0, sizeof(int), st);
     }
     if (grid <= 0) return SG_OK;
     if (backward)

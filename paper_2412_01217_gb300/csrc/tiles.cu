@@ -392,14 +392,24 @@ __global__ void clamp_count_kernel(const int *in, int cap, int *out) {
     *out = min(*in, cap);
 }
 
-__global__ void ranges_kernel(const uint32_t *__restrict__ tile, const int *__restrict__ k_ptr,
+// [start, end) of every tile by binary search in the sorted tile ids ((0, 0) for a tile with
+// no instance): one thread per tile, no prior zeroing.
+__device__ __forceinline__ int lower_bound_u32(const uint32_t *__restrict__ a, int n, uint32_t key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+__global__ void ranges_kernel(const uint32_t *__restrict__ tile, const int *__restrict__ k_ptr, int n_tiles,
                               int2 *__restrict__ ranges) {
     pdl_begin();
     const int K = *k_ptr;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) {
-        const uint32_t t = tile[i];
-        if (i == 0 || tile[i - 1] != t) ranges[t].x = i;
-        if (i == K - 1 || tile[i + 1] != t) ranges[t].y = i + 1;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+        const int lo = lower_bound_u32(tile, K, (uint32_t)t);
+        const int hi = lower_bound_u32(tile, K, (uint32_t)t + 1u);
+        ranges[t] = lo < hi ? make_int2(lo, hi) : make_int2(0, 0);
     }
 }
 
@@ -498,10 +508,9 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     radix_sort(w.tkey_in, w.tval_in, lists->tile, lists->record, w.tkey_tmp, w.tval_tmp,
                lists->count, lists->capacity, bits, w.hist, w.totals, G, st);
     // 5. tile ranges
-    cudaMemsetAsync(lists->ranges, 0, sizeof(int) * 2 * (size_t)n_tiles, st);
     launch_pdl(clamp_count_kernel, 1, 1, 0, st, lists->count, lists->capacity, w.counts + 1);
-    launch_pdl(ranges_kernel, G, kScanThreads, 0, st, lists->tile, w.counts + 1,
-                                              reinterpret_cast<int2 *>(lists->ranges));
+    launch_pdl(ranges_kernel, (n_tiles + kScanThreads - 1) / kScanThreads, kScanThreads, 0, st, lists->tile,
+               w.counts + 1, n_tiles, reinterpret_cast<int2 *>(lists->ranges));
     count_launches(3 + 3 + 2);  // compaction, emission, clamp + ranges
     // 6. work order: one stable counting pass over the 6-bit length keys
     if (lists->order) {

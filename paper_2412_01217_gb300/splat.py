@@ -167,7 +167,7 @@ class PyramidRasterizer:
         self.order = torch.zeros(self.n_tiles, **i32)
         self.count = torch.zeros(1, **i32)
         self.status = torch.zeros(1, **i32)
-        self.work_counter = torch.zeros(1, **i32)
+        self.work_counter = torch.zeros(2, **i32)
         lib = _lib.load()
         self.tile_ws = torch.zeros(lib.sg_tile_lists_workspace_size(self.R, self.capacity), dtype=torch.uint8, device=dev)
         P = self.P

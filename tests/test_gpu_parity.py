@@ -208,6 +208,14 @@ def test_backward_matches_oracle_cloud(cloud, ppt, batch_bwd):
     up_s32 = dl[2].cpu().numpy().astype(np.float64).reshape(C, H, W)
     ref = oracle.render_backward(g, cam, up_rgb32, up_d32, up_s32)
     check_grads(got, ref, KEYS)
+    # the persistent work queue and the per-record gradient workspace are left zero, so the
+    # next launch needs no memset; a second backward adds exactly the same gradients
+    assert not r.work_counter.any() and not r.bwd_ws.any()
+    again = {k: torch.zeros_like(v) for k, v in p.items()}
+    r.backward(p, again, dL=dl)
+    for k in KEYS:
+        a, b = again[k].cpu().numpy(), got[k]
+        assert np.allclose(a, b, rtol=1e-4, atol=1e-6 * (np.abs(b).max() + 1e-12)), k
 
 
 def test_pyramid_build_matches_oracle():
