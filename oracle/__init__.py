@@ -38,7 +38,7 @@ _LIB = os.path.join(_HERE, "libsg_oracle.so")
 _lib = None
 
 DEFAULT_CFG = dict(alpha_max=0.99, alpha_min=1.0 / 255.0, T_min=1e-4, z_near=0.2,
-                   dilation=0.3, bg=(0.0, 0.0, 0.0), fov_clamp=1.3)
+                   dilation=0.3, bg=(0.0, 0.0, 0.0), fov_clamp=1.3, isotropic=0)
 
 # projection record fields (must match the enum in sg_oracle.c)
 P = dict(VALID=0, U=1, V=2, DEPTH=3, OPAC=4, CA=5, CB=6, CC=7, S00=8, S01=9, S11=10,
@@ -107,7 +107,7 @@ def pack_cfg(cfg=None):
         c.update(cfg)
     bg = c["bg"]
     return np.array([c["alpha_max"], c["alpha_min"], c["T_min"], c["z_near"], c["dilation"],
-                     bg[0], bg[1], bg[2], c["fov_clamp"]], dtype=np.float64)
+                     bg[0], bg[1], bg[2], c["fov_clamp"], float(c["isotropic"])], dtype=np.float64)
 
 
 # ------------------------------------------------------------------------------------------

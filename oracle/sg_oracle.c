@@ -10,6 +10,10 @@
  *   oc_project          Eq. 2-3, generalised to anisotropic Gaussians by the EWA
  *                       covariance projection that Sec. III-C defers to (3D Gaussian
  *                       splatting); reduces to Eq. 2 for isotropic Gaussians on the axis.
+ *                       With cfg isotropic = 1 it is Eq. 2 itself: an isotropic Gaussian of
+ *                       radius r = exp(log_scale[0]) projects to a circle of radius
+ *                       f r / d (fx along x, fy along y), i.e. Sigma2D = diag((fx r/d)^2,
+ *                       (fy r/d)^2) + dilation; quaternion and log_scale[1..2] are unused.
  *   oc_render           Eq. 7-9: per-pixel brute force over all Gaussians, sorted by
  *                       depth (the float32 key of depth_key, then ascending Gaussian id),
  *                       front-to-back compositing of RGB, depth and C semantic channels.
@@ -28,8 +32,8 @@
  *   Derivatives at the clamp and skip branches are those of the branch taken (zero).
  *
  * Camera packing (18 doubles): fx fy cx cy W H R_cw[9, row-major] t_cw[3].
- * Config packing (9 doubles):  alpha_max alpha_min T_min z_near dilation bg_r bg_g bg_b
- *                              fov_clamp.
+ * Config packing (10 doubles): alpha_max alpha_min T_min z_near dilation bg_r bg_g bg_b
+ *                              fov_clamp isotropic.
  * Image/pixel-list outputs are planar: channel ch of list entry k is at [ch*n_pix + k].
  */
 #include <math.h>
@@ -65,6 +69,7 @@ typedef struct {
 
 typedef struct {
     double alpha_max, alpha_min, T_min, z_near, dilation, bg[3], fov_clamp;
+    int isotropic;
 } cfg_t;
 
 static cam_t unpack_cam(const double *c) {
@@ -80,6 +85,7 @@ static cfg_t unpack_cfg(const double *c) {
     cfg_t g;
     g.alpha_max = c[0]; g.alpha_min = c[1]; g.T_min = c[2]; g.z_near = c[3];
     g.dilation = c[4]; g.bg[0] = c[5]; g.bg[1] = c[6]; g.bg[2] = c[7]; g.fov_clamp = c[8];
+    g.isotropic = c[9] != 0.0;
     return g;
 }
 
@@ -157,19 +163,25 @@ static void project_one(const double *mean, const double *log_scale, const doubl
     double limx = cfg->fov_clamp * 0.5 * cam->W / cam->fx;
     double limy = cfg->fov_clamp * 0.5 * cam->H / cam->fy;
     out[P_LIMX] = limx; out[P_LIMY] = limy;
-    double J[6], T[6], qh[4], R[9], M[9], Sig[9];
-    int clx, cly;
-    jacobian(cam, t, limx, limy, J, &clx, &cly, T);
-    out[P_CLX] = clx; out[P_CLY] = cly;
-    scale_rot(log_scale, quat, qh, R, M, Sig);
-    double S[4];                                          /* T Sig T^T */
-    for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j) {
-            double s = 0;
-            for (int k = 0; k < 3; ++k)
-                for (int l = 0; l < 3; ++l) s += T[3 * i + k] * Sig[3 * k + l] * T[3 * j + l];
-            S[2 * i + j] = s;
-        }
+    double S[4];                                          /* projected covariance */
+    if (cfg->isotropic) {                                 /* Eq. 2: radius f r / d */
+        double r = exp(log_scale[0]);
+        double rx = cam->fx * r / t[2], ry = cam->fy * r / t[2];
+        S[0] = rx * rx; S[1] = S[2] = 0.0; S[3] = ry * ry;
+    } else {                                              /* EWA: T Sig T^T */
+        double J[6], T[6], qh[4], R[9], M[9], Sig[9];
+        int clx, cly;
+        jacobian(cam, t, limx, limy, J, &clx, &cly, T);
+        out[P_CLX] = clx; out[P_CLY] = cly;
+        scale_rot(log_scale, quat, qh, R, M, Sig);
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                double s = 0;
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l) s += T[3 * i + k] * Sig[3 * k + l] * T[3 * j + l];
+                S[2 * i + j] = s;
+            }
+    }
     double s00 = S[0] + cfg->dilation, s01 = 0.5 * (S[1] + S[2]), s11 = S[3] + cfg->dilation;
     out[P_S00] = s00; out[P_S01] = s01; out[P_S11] = s11;
     double det = s00 * s11 - s01 * s01;
@@ -319,7 +331,7 @@ void oc_render(int N, int C, const double *proj, const double *rgb, const double
 
 /* g2: dL/d{u, v, conic a, conic b, conic c, opacity, depth} of one Gaussian. */
 static void project_backward_one(const double *mean, const double *log_scale, const double *quat,
-                                 const double *p, const cam_t *cam, const double *g2,
+                                 const double *p, const cam_t *cam, int isotropic, const double *g2,
                                  double *g_mean, double *g_ls, double *g_q, double *g_ol) {
     (void)mean;
     double gu = g2[0], gv = g2[1], ga = g2[2], gb = g2[3], gc = g2[4], go = g2[5], gd = g2[6];
@@ -328,6 +340,23 @@ static void project_backward_one(const double *mean, const double *log_scale, co
     double gS00 = -(a * a * ga + a * b * gb + b * b * gc);
     double gS01 = -(2 * a * b * ga + (a * c + b * b) * gb + 2 * b * c * gc);
     double gS11 = -(b * b * ga + b * c * gb + c * c * gc);
+    if (isotropic) {
+        /* S00 = (fx r/tz)^2 + b, S11 = (fy r/tz)^2 + b, r = e^{s0}, S01 = 0 (constant) */
+        const double *W = cam->R;
+        double t[3] = {p[P_TX], p[P_TY], p[P_TZ]};
+        double fx = cam->fx, fy = cam->fy, tz = t[2], tz2 = tz * tz, tz3 = tz2 * tz;
+        double r = exp(log_scale[0]);
+        double gr = gS00 * 2.0 * fx * fx * r / tz2 + gS11 * 2.0 * fy * fy * r / tz2;
+        g_ls[0] += gr * r;
+        double gt[3] = {gu * fx / tz, gv * fy / tz,
+                        -gu * fx * t[0] / tz2 - gv * fy * t[1] / tz2 + gd
+                            - gS00 * 2.0 * fx * fx * r * r / tz3 - gS11 * 2.0 * fy * fy * r * r / tz3};
+        for (int j = 0; j < 3; ++j) g_mean[j] += W[j] * gt[0] + W[3 + j] * gt[1] + W[6 + j] * gt[2];
+        double o = p[P_OPAC];
+        *g_ol += go * o * (1.0 - o);
+        (void)quat; (void)g_q;
+        return;
+    }
     double G[4] = {gS00, 0.5 * gS01, 0.5 * gS01, gS11};   /* full-entry symmetric gradient */
     double t[3] = {p[P_TX], p[P_TY], p[P_TZ]};
     double J[6], T[6], qh[4], R[9], M[9], Sig[9];
@@ -499,8 +528,8 @@ void oc_render_backward(int N, int C, const double *mean, const double *log_scal
     for (int i = 0; i < N; ++i) {
         const double *p = proj + (size_t)OC_PROJ_STRIDE * i;
         if (p[P_VALID] == 0.0) continue;
-        project_backward_one(mean + 3 * i, log_scale + 3 * i, quat + 4 * i, p, &cam, g2 + 8 * (size_t)i,
-                             gm + 3 * i, gls + 3 * i, gq + 4 * i, gol + i);
+        project_backward_one(mean + 3 * i, log_scale + 3 * i, quat + 4 * i, p, &cam, cfg.isotropic,
+                             g2 + 8 * (size_t)i, gm + 3 * i, gls + 3 * i, gq + 4 * i, gol + i);
     }
     if (g2d)
         for (size_t i = 0; i < (size_t)N * 8; ++i) g2d[i] += g2[i];

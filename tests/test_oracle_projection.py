@@ -125,3 +125,38 @@ def test_extents_are_exact_bounds():
             dstar = -b * (sgn * ex) / c
             sig_star = 0.5 * (a * ex * ex + c * dstar ** 2) + b * (sgn * ex) * dstar
             assert o * math.exp(-sig_star) == pytest.approx(1 / 255, rel=1e-6)
+
+
+def test_eq2_isotropic_mode_equals_ewa_on_axis():
+    """Eq. 2 mode (isotropic = 1) and the EWA projection are different code paths; for an
+    isotropic Gaussian on the optical axis they must give the same 2D Gaussian."""
+    cam = synthetic.make_camera(240, 160, 180.0, 170.0, 120.0, 80.0)
+    for r, d, dil in [(0.02, 1.5, 0.3), (0.1, 4.0, 0.0), (0.3, 9.0, 0.3)]:
+        g = one([0, 0, d], [math.log(r)] * 3, quat=(0.2, 0.4, -0.6, 0.3))
+        ewa = oracle.project(g, cam, dict(dilation=dil))[0]
+        iso = oracle.project(g, cam, dict(dilation=dil, isotropic=1))[0]
+        for k in ("VALID", "U", "V", "DEPTH", "S00", "S11", "CA", "CB", "CC", "EXTX", "EXTY"):
+            assert iso[P[k]] == pytest.approx(ewa[P[k]], rel=1e-9, abs=1e-12), k
+
+
+def test_eq2_isotropic_mode_invariances():
+    """Eq. 2 uses only the radius e^{s0}: rotation and the other log-scales do not matter,
+    and the 2D radius is invariant to scaling radius and camera distance together."""
+    rng = np.random.default_rng(9)
+    cam = synthetic.look_camera(synthetic.SCANNET_LIKE, [0.5, -1.0, 1.2], 0.7, 0.1)
+    ahead = np.array([math.cos(0.7), math.sin(0.7), 0.1])
+    for _ in range(10):
+        mu = np.array([0.5, -1.0, 1.2]) + rng.uniform(1.5, 3.0) * ahead + rng.normal(0, 0.2, 3)
+        s0 = math.log(rng.uniform(0.01, 0.1))
+        a = oracle.project(one(mu, [s0, -3.0, -1.0], quat=(1, 0, 0, 0)), cam, dict(isotropic=1, dilation=0.0))[0]
+        b = oracle.project(one(mu, [s0, -0.5, -6.0], quat=tuple(rng.normal(size=4))), cam,
+                           dict(isotropic=1, dilation=0.0))[0]
+        for k in ("S00", "S01", "S11", "CA", "CB", "CC", "EXTX", "EXTY", "U", "V"):
+            assert a[P[k]] == pytest.approx(b[P[k]], rel=1e-12, abs=1e-15), k
+        # the same Gaussian twice as large and twice as far along its viewing ray
+        c_w = -cam["R_cw"].T @ cam["t_cw"]
+        mu2 = c_w + 2.0 * (mu - c_w)
+        c = oracle.project(one(mu2, [s0 + math.log(2.0), 0, 0]), cam, dict(isotropic=1, dilation=0.0))[0]
+        assert c[P["S00"]] == pytest.approx(a[P["S00"]], rel=1e-9)
+        assert c[P["S11"]] == pytest.approx(a[P["S11"]], rel=1e-9)
+        assert abs(a[P["S01"]]) == 0.0
