@@ -110,6 +110,12 @@ typedef struct {
                                       tile_h % (4 * it) == 0, tile pixels >= 32 * it       */
     int32_t pixels_per_thread_bwd; /* the same for the backward kernel                    */
     int32_t batch_bwd;      /* batch of the backward kernel; 0: the same as `batch`    */
+    int32_t isotropic;      /* 0: EWA projection of the anisotropic Gaussian (log_scale,
+                               quat); 1: Eq. 2 as printed: an isotropic Gaussian of radius
+                               r = exp(log_scale[0]) projects to a circle of radius f r / d
+                               (fx along x, fy along y), Sigma2D = diag((fx r/d)^2,
+                               (fy r/d)^2) + dilation; quat and log_scale[1..2] are unused
+                               and get zero gradient                                    */
 } sg_config;
 
 /* Projected records of all (view-level, Gaussian) pairs: record r = v*N + g. */

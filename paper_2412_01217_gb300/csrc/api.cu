@@ -82,6 +82,7 @@ static sg_status check_cfg(const sg_config *c) {
                c->batch);
     SG_REQUIRE(c->batch_bwd == 0 || (c->batch_bwd >= 16 && c->batch_bwd <= 512 && (c->batch_bwd % 16) == 0),
                "batch_bwd %d not 0 or in [16, 512] step 16", c->batch_bwd);
+    SG_REQUIRE(c->isotropic == 0 || c->isotropic == 1, "isotropic must be 0 or 1");
     SG_REQUIRE(c->alpha_min > 0.f && c->alpha_max <= 1.f && c->alpha_min < c->alpha_max,
                "need 0 < alpha_min < alpha_max <= 1");
     SG_REQUIRE(c->T_min >= 0.f && c->z_near > 0.f && c->dilation >= 0.f && c->fov_clamp > 0.f,
@@ -130,6 +131,7 @@ void sg_default_config(sg_config *c) {
     c->pixels_per_thread = 1;
     c->pixels_per_thread_bwd = 2;
     c->batch_bwd = 0;
+    c->isotropic = 0;
 }
 
 void sg_default_loss_config(sg_loss_config *c) {

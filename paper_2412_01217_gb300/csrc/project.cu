@@ -14,7 +14,9 @@ namespace sg {
 struct ProjConsts {
     float z_near, dilation, fov_clamp, alpha_min;
     int tile_w, tile_h;
+    int isotropic;  // Eq. 2 projection instead of EWA
 };
+
 
 // Rotation (row-major) of the unit quaternion (w, x, y, z).
 __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
@@ -124,6 +126,16 @@ __device__ __forceinline__ void cov2d(const ViewGeom &q, const GaussianFrame &f,
     det = (c0 * c0 + c1 * c1 + c2 * c2) + dil * (n0 + n1) + dil * dil;
 }
 
+// Eq. 2 as printed: radius r = exp(log_scale[0]) projects to f r / t_z along each axis.
+__device__ __forceinline__ void cov2d_eq2(const sg_view &vw, float tz, const GaussianFrame &f, float dil,
+                                          float &s00, float &s01, float &s11, float &det) {
+    const float rx = vw.fx * f.S[0] / tz, ry = vw.fy * f.S[0] / tz;
+    s00 = rx * rx + dil;
+    s11 = ry * ry + dil;
+    s01 = 0.f;
+    det = s00 * s11;
+}
+
 __global__ void __launch_bounds__(256) project_fwd_kernel(
     const float *__restrict__ mean, const float *__restrict__ log_scale,
     const float4 *__restrict__ quat, const float *__restrict__ ologit, int N,
@@ -162,7 +174,10 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
             const DF vdf = df_add_f(df_mul_f(df_div(tdf[1], tdf[2]), vw.fy), vw.cy);
             const float u = udf.hi, vv = vdf.hi;
             float s00, s01, s11, det;
-            cov2d(q, f, pc.dilation, s00, s01, s11, det);
+            if (pc.isotropic)
+                cov2d_eq2(vw, tz, f, pc.dilation, s00, s01, s11, det);
+            else
+                cov2d(q, f, pc.dilation, s00, s01, s11, det);
             if (det > 0.f && s00 > 0.f) {
                 // alpha >= alpha_min needs sigma <= ln(o/alpha_min); the smallest sigma at a
                 // horizontal offset dx is dx^2/(2 s00): half extents (with float32 slack)
@@ -222,6 +237,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     float gmu[3] = {0.f, 0.f, 0.f};
     float gSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // full-entry gradient, symmetric
     float go_total = 0.f;
+    float gls0 = 0.f;  // Eq. 2 mode: dL/dlog_scale[0]
     // Visible view-levels first, 32 at a time, with all tile-rectangle loads in flight
     // together; then the visible ones, each one's 2D gradients loaded one view ahead.
     for (int v0 = 0; v0 < n_views; v0 += 32) {
@@ -262,7 +278,10 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
         float ca, cb, cc;
         {
             float s00, s01, s11, det;
-            cov2d(q, f, pc.dilation, s00, s01, s11, det);
+            if (pc.isotropic)
+                cov2d_eq2(vw, q.t[2], f, pc.dilation, s00, s01, s11, det);
+            else
+                cov2d(q, f, pc.dilation, s00, s01, s11, det);
             const float id = 1.f / det;
             ca = s11 * id;
             cb = -s01 * id;
@@ -273,6 +292,18 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
         const float gS00 = -(ca * ca * ga + ca * cb * gb + cb * cb * gc);
         const float gS01 = -(2.f * ca * cb * ga + (ca * cc + cb * cb) * gb + 2.f * cb * cc * gc);
         const float gS11 = -(cb * cb * ga + cb * cc * gb + cc * cc * gc);
+        if (pc.isotropic) {
+            // Eq. 2: S00 = (fx r/tz)^2 + b, S11 = (fy r/tz)^2 + b with r = e^{s0}; S01 = 0
+            const float r = f.S[0];
+            const float q2 = (gS00 * vw.fx * vw.fx + gS11 * vw.fy * vw.fy) * 2.f * r * r / tz2;
+            gls0 += q2;  // dL/ds0 = dL/dr * r
+            const float gt0 = gu * vw.fx / tz, gt1 = gv * vw.fy / tz;
+            const float gt2 = -gu * vw.fx * q.t[0] / tz2 - gv * vw.fy * q.t[1] / tz2 + gd - q2 / tz;
+            const float *W = vw.R;
+            for (int j = 0; j < 3; ++j) gmu[j] += W[j] * gt0 + W[3 + j] * gt1 + W[6 + j] * gt2;
+            go_total += go;
+            continue;
+        }
         const float G00 = gS00, G01 = 0.5f * gS01, G11 = gS11;
         // Sigma2D = T Sig T^T: dSig += T^T G T; dT = 2 G T Sig
         const float *T0 = q.T0, *T1 = q.T1;
@@ -344,6 +375,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     const float dot = f.q[0] * gq[0] + f.q[1] * gq[1] + f.q[2] * gq[2] + f.q[3] * gq[3];
     const float rq = 1.f / f.qn;
     for (int i = 0; i < 4; ++i) g_quat[4 * g + i] += (gq[i] - f.q[i] * dot) * rq;
+    gls[0] += gls0;
     for (int j = 0; j < 3; ++j) {
         g_mean[3 * g + j] += gmu[j];
         g_ls[3 * g + j] += gls[j];
@@ -354,7 +386,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
 sg_status launch_project_fwd(const sg_gaussians *g, const sg_view *views, int n_views,
                              const sg_config *cfg, sg_projected *out, cudaStream_t st) {
     ProjConsts pc{cfg->z_near, cfg->dilation, cfg->fov_clamp, cfg->alpha_min, cfg->tile_w,
-                  cfg->tile_h};
+                  cfg->tile_h, cfg->isotropic};
     const int threads = 256;
     const int blocks = (g->N + threads - 1) / threads;
     if (blocks > 0)
@@ -370,7 +402,7 @@ sg_status launch_project_bwd(const sg_gaussians *g, const sg_view *views, int n_
                              const sg_config *cfg, const sg_projected *proj, float *g2d,
                              sg_gaussian_grads *gr, cudaStream_t st) {
     ProjConsts pc{cfg->z_near, cfg->dilation, cfg->fov_clamp, cfg->alpha_min, cfg->tile_w,
-                  cfg->tile_h};
+                  cfg->tile_h, cfg->isotropic};
     const int threads = 256;
     const int blocks = (g->N + threads - 1) / threads;
     if (blocks > 0)

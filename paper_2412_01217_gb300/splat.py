@@ -49,6 +49,7 @@ class RenderConfig:
     pixels_per_thread: int = 1
     pixels_per_thread_bwd: int = 2
     batch_bwd: int = 0  # 0: same as batch
+    isotropic: bool = False  # Eq. 2 projection (radius f r / d) instead of EWA
 
     def to_c(self):
         c = SgConfig()
@@ -60,6 +61,7 @@ class RenderConfig:
         c.pixels_per_thread = int(self.pixels_per_thread)
         c.pixels_per_thread_bwd = int(self.pixels_per_thread_bwd)
         c.batch_bwd = int(self.batch_bwd)
+        c.isotropic = int(self.isotropic)
         return c
 
 

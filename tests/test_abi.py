@@ -31,7 +31,7 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(_lib.SgCamera) == 72
     assert C.sizeof(_lib.SgView) == 96
     assert C.sizeof(_lib.SgGaussians) == 56
-    assert C.sizeof(_lib.SgConfig) == 64
+    assert C.sizeof(_lib.SgConfig) == 68
     assert C.sizeof(_lib.SgLossConfig) == 40
 
 

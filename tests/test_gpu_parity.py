@@ -154,12 +154,13 @@ def test_tile_lists_bit_exact_pyramid_multi_view():
     assert _lists_vs_reference(r) > 10000
 
 
-def test_forward_matches_oracle_cloud(cloud):
+@pytest.mark.parametrize("isotropic", [False, True])
+def test_forward_matches_oracle_cloud(cloud, isotropic):
     g, cam = cloud
-    r, p = make(g, [cam])
+    r, p = make(g, [cam], isotropic=isotropic)
     r.forward(p)
     got = view_images(r, 0, 8)
-    ref = oracle.render(g, cam)
+    ref = oracle.render(g, cam, dict(isotropic=int(isotropic)))
     amb = (ref["flags"] & AMBIGUOUS) != 0
     assert amb.mean() < 0.02
     ok = ~amb
@@ -184,12 +185,14 @@ def test_forward_bitwise_identical_across_tiles_batches_and_runs(cloud):
             assert np.array_equal(im[k], base[k]), (k, tw, th, batch, pers, ppt)
 
 
-@pytest.mark.parametrize("ppt, batch_bwd", [(1, 0), (2, 0), (4, 0), (1, 16), (2, 64)])
-def test_backward_matches_oracle_cloud(cloud, ppt, batch_bwd):
+@pytest.mark.parametrize("ppt, batch_bwd, isotropic", [(1, 0, False), (2, 0, False), (4, 0, False), (1, 16, False),
+                                                     (2, 64, False), (1, 0, True)])
+def test_backward_matches_oracle_cloud(cloud, ppt, batch_bwd, isotropic):
     g, cam = cloud
-    r, p = make(g, [cam], pixels_per_thread_bwd=ppt, batch_bwd=batch_bwd)
+    r, p = make(g, [cam], pixels_per_thread_bwd=ppt, batch_bwd=batch_bwd, isotropic=isotropic)
     r.forward(p)
-    ref_f = oracle.render(g, cam)
+    ocfg = dict(isotropic=int(isotropic))
+    ref_f = oracle.render(g, cam, ocfg)
     keep = ((ref_f["flags"] & AMBIGUOUS_GRAD) == 0).astype(np.float64)
     rng = np.random.default_rng(11)
     H, W, C = cam["H"], cam["W"], 8
@@ -206,8 +209,10 @@ def test_backward_matches_oracle_cloud(cloud, ppt, batch_bwd):
     up_rgb32 = dl[0].cpu().numpy().astype(np.float64).reshape(3, H, W)
     up_d32 = dl[1].cpu().numpy().astype(np.float64).reshape(H, W)
     up_s32 = dl[2].cpu().numpy().astype(np.float64).reshape(C, H, W)
-    ref = oracle.render_backward(g, cam, up_rgb32, up_d32, up_s32)
+    ref = oracle.render_backward(g, cam, up_rgb32, up_d32, up_s32, cfg=ocfg)
     check_grads(got, ref, KEYS)
+    if isotropic:  # Eq. 2 uses only log_scale[0]: rotation and the other scales get zero
+        assert not got["quat"].any() and not got["log_scale"][:, 1:].any()
     # the persistent work queue and the per-record gradient workspace are left zero, so the
     # next launch needs no memset; a second backward adds exactly the same gradients
     assert not r.work_counter.any() and not r.bwd_ws.any()
