@@ -53,10 +53,12 @@ def room_views(room_seed, intr, n_kf, n_eval, pool=None):
 
 
 def run_mapper(kf, frames, n_max, iters_per_kf, new_per_kf, init="heuristic", mlp=None, ev=None, ev_frames=None,
-               eval_every=0, seed=0, decoder=None):
+               eval_every=0, seed=0, decoder=None, mapper_factory=None, kappa=1.0):
     """Insert from every keyframe in turn and optimise; returns the mapper, insertion
-    records and the PSNR curve [(gpu_seconds, iteration, psnr)]."""
-    m = Mapper(frames, kf, n_max, decoder=decoder, seed=seed)
+    records and the PSNR curve [(gpu_seconds, iteration, psnr)].  mapper_factory(frames, kf,
+    n_max, decoder=, seed=) builds the Mapper (default: Mapper with its defaults); kappa scales
+    the label one-hot the heuristic initializer writes into new semantic features."""
+    m = (mapper_factory or Mapper)(frames, kf, n_max, decoder=decoder, seed=seed)
     rng = np.random.default_rng(seed + 1000)
     inserted = []
     curve = []
@@ -67,7 +69,7 @@ def run_mapper(kf, frames, n_max, iters_per_kf, new_per_kf, init="heuristic", ml
         e0.record()
         mlp_before = m.mlp_seconds
         start = m.N
-        B, pix = m.insert(k, new_per_kf, init=init, mlp=mlp)
+        B, pix = m.insert(k, new_per_kf, init=init, mlp=mlp, kappa=kappa)
         e1.record()
         e1.synchronize()
         # the learned form's patch + MLP time is inside this interval already

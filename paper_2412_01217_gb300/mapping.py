@@ -38,12 +38,13 @@ class Mapper:
     """
 
     def __init__(self, frames, cams, n_max, C=16, n_classes=32, levels=3, cfg=None, decoder=None,
-                 lr=None, device="cuda", seed=0):
+                 lr=None, device="cuda", seed=0, loss_cfg=None):
         self.dev = torch.device(device)
         self.frames, self.cams = frames, cams
         self.levels, self.C, self.n_classes = levels, C, n_classes
         self.rast = PyramidRasterizer(n_max, C, [cams[0]], levels, cfg or RenderConfig(),
-                                      capacity=24 * n_max, loss_cfg=LossConfig(n_classes=n_classes),
+                                      capacity=24 * n_max,
+                                      loss_cfg=loss_cfg or LossConfig(n_classes=n_classes),
                                       device=self.dev)
         self.n_max = n_max
         z = lambda *s: torch.zeros(*s, dtype=torch.float32, device=self.dev)
@@ -179,6 +180,36 @@ class Mapper:
             mse = float(((img.clamp(0, 1) - gt) ** 2).mean().item())
             vals.append(-10.0 * math.log10(max(mse, 1e-12)))
         return float(np.mean(vals))
+
+    def evaluate(self, cams, frames):
+        """Level-0 quality on held-out views: RGB PSNR, depth L1 (over valid target depth) and
+        semantic mIoU (argmax of the decoded features against the labels, over the classes
+        present in prediction or target).  Evaluation only, not part of the optimised path."""
+        psnr, l1, inter, union = [], [], None, None
+        K = self.decoder.shape[0]
+        for cam, f in zip(cams, frames):
+            self.rast.set_cameras([cam])
+            self.rast.forward(self.params())
+            img = self.rast.view_slice(self.rast.img_rgb, 0, 3)
+            gt = torch.as_tensor(f["rgb"]).to(self.dev)
+            mse = float(((img.clamp(0, 1) - gt) ** 2).mean().item())
+            psnr.append(-10.0 * math.log10(max(mse, 1e-12)))
+            d = self.rast.view_slice(self.rast.img_depth, 0, 1)[0]
+            gd = torch.as_tensor(f["depth"]).to(self.dev)
+            m = gd > 0
+            l1.append(float((d[m] - gd[m]).abs().mean().item()))
+            S = self.rast.view_slice(self.rast.img_sem, 0, self.C).reshape(self.C, -1)
+            pred = (self.decoder @ S).argmax(0)
+            lab = torch.as_tensor(f["label"]).to(self.dev).reshape(-1).long()
+            ok = lab >= 0
+            pi = torch.bincount(pred[ok] * K + lab[ok], minlength=K * K).reshape(K, K)
+            i_ = pi.diag().double()
+            u_ = pi.sum(0).double() + pi.sum(1).double() - i_
+            inter = i_ if inter is None else inter + i_
+            union = u_ if union is None else union + u_
+        present = union > 0
+        miou = float((inter[present] / union[present]).mean().item())
+        return dict(psnr=float(np.mean(psnr)), depth_l1=float(np.mean(l1)), miou=miou)
 
     def converged(self, start, count):
         """[count][32] targets of the learned initializer: log-scale (3), opacity logit (1),
