@@ -9,6 +9,10 @@ Pieces and the passages they follow:
 * ``project``            Eq. 2-3 (EWA covariance projection; C file ``sg_oracle.c``).
 * ``render``             Eq. 7-9 brute-force compositing per pixel (C).
 * ``render_backward``    hand-derived adjoint of Eq. 7-9 and Eq. 2-3 (Sec. III-D) (C).
+* ``sh_basis``,          view-dependent colour of Sec. III-B: rgb + sum of real spherical
+  ``view_colours``       harmonics of degree 1..3 of the camera-to-mean direction (numpy);
+                         ``render`` and ``render_backward`` take it, and its adjoint to the SH
+                         coefficients, rgb and the mean, when the parameters carry ``sh``.
 * ``ssim``               SSIM of Wang et al. 2004 used by Eq. 10 and 12 (C).
 * ``level_cameras``,     Eq. 4-6 image pyramid: 2x2 box mean for RGB, valid-only mean for
   ``build_pyramid``      depth, 2x2 majority for labels; per-level intrinsics keep pixel
@@ -125,6 +129,99 @@ def project(g, cam, cfg=None):
     return out
 
 
+# ------------------------------------------------------------------------------------------
+# View-dependent colour: real spherical harmonics of degree 1..3 (the SH colour of Sec. III-B)
+# ------------------------------------------------------------------------------------------
+
+def sh_basis(d, degree):
+    """Real spherical harmonics Y_1 .. Y_K, K = (degree+1)^2 - 1, at unit directions d (n, 3),
+    in the usual graphics order (m = -l..l within each degree l, Condon-Shortley signs):
+      l = 1: -c1 y, c1 z, -c1 x                                        c1 = sqrt(3 / 4pi)
+      l = 2: a xy, -a yz, b (2z^2 - x^2 - y^2), -a xz, c (x^2 - y^2)
+             a = sqrt(15/pi)/2, b = sqrt(5/pi)/4, c = sqrt(15/pi)/4
+      l = 3: -e y (3x^2 - y^2), f xyz, -h y (4z^2 - x^2 - y^2), k z (2z^2 - 3x^2 - 3y^2),
+             -h x (4z^2 - x^2 - y^2), m z (x^2 - y^2), -e x (x^2 - 3y^2)
+             e = sqrt(35/2pi)/4, f = sqrt(105/pi)/2, h = sqrt(21/2pi)/4, k = sqrt(7/pi)/4,
+             m = sqrt(105/pi)/4.
+    Returns (n, K)."""
+    d = np.asarray(d, np.float64)
+    x, y, z = d[:, 0], d[:, 1], d[:, 2]
+    pi = np.pi
+    out = []
+    if degree >= 1:
+        c1 = np.sqrt(3 / (4 * pi))
+        out += [-c1 * y, c1 * z, -c1 * x]
+    if degree >= 2:
+        a, b, c = np.sqrt(15 / pi) / 2, np.sqrt(5 / pi) / 4, np.sqrt(15 / pi) / 4
+        out += [a * x * y, -a * y * z, b * (2 * z * z - x * x - y * y), -a * x * z, c * (x * x - y * y)]
+    if degree >= 3:
+        e, f, h = np.sqrt(35 / (2 * pi)) / 4, np.sqrt(105 / pi) / 2, np.sqrt(21 / (2 * pi)) / 4
+        k, m = np.sqrt(7 / pi) / 4, np.sqrt(105 / pi) / 4
+        out += [-e * y * (3 * x * x - y * y), f * x * y * z, -h * y * (4 * z * z - x * x - y * y),
+                k * z * (2 * z * z - 3 * x * x - 3 * y * y), -h * x * (4 * z * z - x * x - y * y),
+                m * z * (x * x - y * y), -e * x * (x * x - 3 * y * y)]
+    return np.stack(out, 1) if out else np.zeros((len(d), 0))
+
+
+def sh_basis_grad(d, degree):
+    """d Y_k / d(x, y, z) of the polynomials of sh_basis (before restriction to the sphere):
+    (n, K, 3)."""
+    d = np.asarray(d, np.float64)
+    x, y, z = d[:, 0], d[:, 1], d[:, 2]
+    o = np.zeros_like(x)
+    pi = np.pi
+    g = []
+    if degree >= 1:
+        c1 = np.sqrt(3 / (4 * pi))
+        g += [(o, -c1 + o, o), (o, o, c1 + o), (-c1 + o, o, o)]
+    if degree >= 2:
+        a, b, c = np.sqrt(15 / pi) / 2, np.sqrt(5 / pi) / 4, np.sqrt(15 / pi) / 4
+        g += [(a * y, a * x, o), (o, -a * z, -a * y), (-2 * b * x, -2 * b * y, 4 * b * z), (-a * z, o, -a * x),
+              (2 * c * x, -2 * c * y, o)]
+    if degree >= 3:
+        e, f, h = np.sqrt(35 / (2 * pi)) / 4, np.sqrt(105 / pi) / 2, np.sqrt(21 / (2 * pi)) / 4
+        k, m = np.sqrt(7 / pi) / 4, np.sqrt(105 / pi) / 4
+        g += [(-6 * e * x * y, -e * (3 * x * x - 3 * y * y), o),
+              (f * y * z, f * x * z, f * x * y),
+              (2 * h * x * y, -h * (4 * z * z - x * x - 3 * y * y), -8 * h * y * z),
+              (-6 * k * x * z, -6 * k * y * z, k * (6 * z * z - 3 * x * x - 3 * y * y)),
+              (-h * (4 * z * z - 3 * x * x - y * y), 2 * h * x * y, -8 * h * x * z),
+              (2 * m * x * z, -2 * m * y * z, m * (x * x - y * y)),
+              (-e * (3 * x * x - 3 * y * y), 6 * e * x * y, o)]
+    if not g:
+        return np.zeros((len(d), 0, 3))
+    return np.stack([np.stack(t, 1) for t in g], 1)
+
+
+def sh_degree_of(g):
+    """SH degree D of a parameter dict (g["sh"]: N x ((D+1)^2 - 1) x 3), 0 without "sh"."""
+    sh = g.get("sh")
+    if sh is None or np.asarray(sh).shape[1] == 0:
+        return 0
+    K = np.asarray(sh).shape[1]
+    D = int(round(np.sqrt(K + 1))) - 1
+    assert (D + 1) ** 2 - 1 == K and 1 <= D <= 3, K
+    return D
+
+
+def view_colours(g, cam):
+    """Colour of every Gaussian seen from cam: rgb + sum_k sh_k Y_k(d), d the unit direction
+    from the camera centre c = -R_cw^T t_cw to the mean (no offset, no clamp: degree 0 is
+    rgb itself).  Returns (colour (N, 3), d (N, 3), |mean - c| (N,), Y (N, K))."""
+    D = sh_degree_of(g)
+    rgb = np.asarray(g["rgb"], np.float64)
+    if D == 0:
+        return rgb, None, None, None
+    R = np.asarray(cam["R_cw"], np.float64).reshape(3, 3)
+    c = -R.T @ np.asarray(cam["t_cw"], np.float64).reshape(3)
+    v = np.asarray(g["mean"], np.float64) - c
+    n = np.linalg.norm(v, axis=1)
+    d = v / n[:, None]
+    Y = sh_basis(d, D)
+    sh = np.asarray(g["sh"], np.float64)
+    return rgb + np.einsum("nk,nkc->nc", Y, sh), d, n, Y
+
+
 def render(g, cam, cfg=None, pixels=None, tol=1e-3):
     """Render RGB, depth and C semantic channels.
 
@@ -138,7 +235,8 @@ def render(g, cam, cfg=None, pixels=None, tol=1e-3):
     proj = project(g, cam, cfg)
     N = proj.shape[0]
     C = g["sem"].shape[1]
-    pr, ppr = _d(proj); rgb, prgb = _d(g["rgb"]); sem, psem = _d(g["sem"].reshape(N, C))
+    colour = view_colours(g, cam)[0]
+    pr, ppr = _d(proj); rgb, prgb = _d(colour); sem, psem = _d(g["sem"].reshape(N, C))
     c, pc = _d(pack_camera(cam)); f, pf = _d(pack_cfg(cfg))
     if pixels is None:
         n = cam["W"] * cam["H"]
@@ -169,8 +267,9 @@ def render_backward(g, cam, g_rgb, g_depth, g_sem, cfg=None, pixels=None):
     proj = project(g, cam, cfg)
     N = proj.shape[0]
     C = g["sem"].shape[1]
+    colour, sh_d, sh_n, sh_Y = view_colours(g, cam)
     m, pm = _d(g["mean"]); s, ps = _d(g["log_scale"]); q, pq = _d(g["quat"])
-    pr, ppr = _d(proj); rgb, prgb = _d(g["rgb"]); sem, psem = _d(g["sem"].reshape(N, C))
+    pr, ppr = _d(proj); rgb, prgb = _d(colour); sem, psem = _d(g["sem"].reshape(N, C))
     c, pc = _d(pack_camera(cam)); f, pf = _d(pack_cfg(cfg))
     if pixels is None:
         n = cam["W"] * cam["H"]
@@ -187,6 +286,15 @@ def render_backward(g, cam, g_rgb, g_depth, g_sem, cfg=None, pixels=None):
     lib.oc_render_backward(N, C, pm, ps, pq, ppr, prgb, psem, pc, pf, n, pix_ptr, pgr, pgd, pgs,
                            P_(out["mean"]), P_(out["log_scale"]), P_(out["quat"]),
                            P_(out["opacity_logit"]), P_(out["rgb"]), P_(out["sem"]), P_(out["g2d"]))
+    if sh_Y is not None:
+        # colour = rgb + sum_k sh_k Y_k(d): dL/dsh_k = Y_k dL/dcolour; dL/drgb = dL/dcolour (as
+        # computed); dL/dmean += (I - d d^T) / |v| * sum_k (sh_k . dL/dcolour) grad Y_k(d)
+        gcol = out["rgb"]
+        out["sh"] = np.einsum("nk,nc->nkc", sh_Y, gcol)
+        w = np.einsum("nkc,nc->nk", np.asarray(g["sh"], np.float64), gcol)
+        gdir = np.einsum("nk,nkj->nj", w, sh_basis_grad(sh_d, sh_degree_of(g)))
+        gdir -= sh_d * (gdir * sh_d).sum(1, keepdims=True)
+        out["mean"] += gdir / sh_n[:, None]
     return out
 
 
