@@ -85,13 +85,25 @@ typedef struct {
     const float *rgb;           /* N x 3                                  */
     const float *sem;           /* N x C semantic feature, 16-byte aligned */
     int32_t N, C;               /* C % 4 == 0, C in {4, 8, 16, 32, 40}    */
+    /* View-dependent colour (Sec. III-B, spherical-harmonic colour): with sh_degree D in
+     * 1..3, the colour of Gaussian i seen from a view whose camera centre is
+     * c = -R^T t is rgb_i + sum_k sh[i][k][:] Y_k(d), k = 1 .. (D+1)^2 - 1, where
+     * d = (mean_i - c) / |mean_i - c| and Y_k are the real spherical harmonics of degree
+     * 1..D in the usual graphics order (m = -l..l within a degree, Condon-Shortley signs;
+     * Y_1 = -sqrt(3/4pi) y, sqrt(3/4pi) z, -sqrt(3/4pi) x).  The constant term is rgb
+     * itself (no offset, no clamp).  sh_degree 0: sh is unused (may be NULL).        */
+    const float *sh;            /* N x ((D+1)^2 - 1) x 3                  */
+    int32_t sh_degree;          /* D in 0..3                              */
 } sg_gaussians;
 
 /* Gradients with respect to every Gaussian parameter; same layouts as sg_gaussians.
- * The backward call ADDS into these (the caller zeroes them). */
+ * The backward call ADDS into these (the caller zeroes them).  sh and sh_degree as in
+ * sg_gaussians (the degree must match). */
 typedef struct {
     float *mean, *log_scale, *quat, *opacity_logit, *rgb, *sem;
     int32_t N, C;
+    float *sh;
+    int32_t sh_degree;
 } sg_gaussian_grads;
 
 /* Rendering constants (3D Gaussian splatting conventions, Sec. III-C) and launch shape. */
@@ -128,6 +140,10 @@ typedef struct {
                        an empty rectangle means the record is culled                    */
     float *ext;     /* R x 2: half extents (pixels) of the region where alpha can reach
                        alpha_min, with margin (8-B aligned)                             */
+    float *rgb;     /* R x 3: colour of each record seen from its view-level, written by
+                       the projection when sh_degree > 0 and read by the compositing
+                       kernels in place of the Gaussian's rgb (may be NULL otherwise);
+                       entries of culled records are left unwritten                    */
 } sg_projected;
 
 /* Per-tile depth-sorted instance lists (the set N of Eq. 7-9, restricted to a tile). */
@@ -206,7 +222,9 @@ sg_status sg_make_views(const sg_camera *cams, int32_t n_cams, int32_t levels, i
 
 /* Eq. 2-3 generalised by the EWA covariance projection: for every view-level and every
  * Gaussian writes the 2D mean, depth, opacity, conic and the tile rectangle covering every
- * pixel where alpha can reach alpha_min.  views: device array of n_views sg_view. */
+ * pixel where alpha can reach alpha_min; with g->sh_degree > 0 also the view-dependent
+ * colour of every visible record into out->rgb (required then).  views: device array of
+ * n_views sg_view. */
 sg_status sg_project_gaussians(const sg_gaussians *g, const sg_view *views, int32_t n_views,
                                const sg_config *cfg, sg_projected *out, sg_stream_t stream);
 
@@ -273,8 +291,10 @@ sg_status sg_pyramid_loss_noalloc(const sg_images *rendered, const sg_targets *g
 /* Backward path                                                                        */
 /* ---------------------------------------------------------------------------------- */
 
-/* Scratch bytes sg_render_pyramid_backward needs.  Zero the workspace once after allocating
- * it; every backward leaves it zero (see sg_render_pyramid_backward_raster below). */
+/* Scratch bytes sg_render_pyramid_backward needs: 12 floats per record (8 for the 2D
+ * gradients, then a block of 4 per record for the view-dependent colour gradients).  Zero the
+ * workspace once after allocating it; every backward leaves it zero (see
+ * sg_render_pyramid_backward_raster below). */
 size_t sg_backward_workspace_size(int64_t n_records);
 
 /* Adjoint of sg_render_pyramid followed by the adjoint of sg_project_gaussians (Sec. III-D
@@ -292,11 +312,13 @@ sg_status sg_render_pyramid_backward(const sg_gaussians *g, const sg_projected *
 /* The two halves of sg_render_pyramid_backward, for callers that time or schedule them
  * apart (same arguments, same workspace):
  *   sg_render_pyramid_backward_raster: the compositing adjoint.  ADDS dL/d(2D mean, conic,
- *     opacity, depth) per record into the workspace (8 floats per record) and dL/d{rgb, sem}
- *     into grads.
+ *     opacity, depth) per record into the workspace (8 floats per record) and dL/dsem into
+ *     grads; dL/drgb goes into grads when sh_degree is 0, else dL/d(record colour) into the
+ *     workspace's colour block (4 floats per record, after the R x 8 block).
  *   sg_project_gaussians_backward: the chain rule through the EWA projection from those
- *     per-record gradients; ADDS dL/d{mean, log_scale, quat, opacity_logit} into grads and
- *     zeroes the per-record slots it consumed.
+ *     per-record gradients; ADDS dL/d{mean, log_scale, quat, opacity_logit} into grads (with
+ *     SH also dL/d{sh, rgb} and the view direction's share of dL/dmean) and zeroes the
+ *     per-record slots it consumed.
  * The workspace must be all zero when the compositing adjoint starts: zero it once after
  * allocating it; each projection adjoint then leaves it zero again (only records visible in
  * some view-level are ever written, and those are the ones it consumes).  Calling both in

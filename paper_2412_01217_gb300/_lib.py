@@ -28,7 +28,7 @@ class SgView(C.Structure):
 
 class SgGaussians(C.Structure):
     _fields_ = [("mean", c_p), ("log_scale", c_p), ("quat", c_p), ("opacity_logit", c_p),
-                ("rgb", c_p), ("sem", c_p), ("N", c_i), ("C", c_i)]
+                ("rgb", c_p), ("sem", c_p), ("N", c_i), ("C", c_i), ("sh", c_p), ("sh_degree", c_i)]
 
 
 SgGaussianGrads = SgGaussians  # same layout (non-const pointers)
@@ -42,7 +42,7 @@ class SgConfig(C.Structure):
 
 
 class SgProjected(C.Structure):
-    _fields_ = [("geo", c_p), ("rect", c_p), ("ext", c_p)]
+    _fields_ = [("geo", c_p), ("rect", c_p), ("ext", c_p), ("rgb", c_p)]
 
 
 class SgTileLists(C.Structure):

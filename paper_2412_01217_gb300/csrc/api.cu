@@ -64,10 +64,19 @@ static sg_status check_gaussians(const sg_gaussians *g) {
     SG_REQUIRE(g, "gaussians is NULL");
     SG_REQUIRE(g->N >= 0, "N = %d < 0", g->N);
     SG_REQUIRE(raster_supports(g->C), "unsupported semantic width C=%d (supported: 4, 8, 16, 32, 40)", g->C);
+    SG_REQUIRE(g->sh_degree >= 0 && g->sh_degree <= 3, "sh_degree = %d not in 0..3", g->sh_degree);
     if (g->N == 0) return SG_OK;
     SG_REQUIRE(g->mean && g->log_scale && g->quat && g->opacity_logit && g->rgb && g->sem,
                "a Gaussian parameter pointer is NULL");
     SG_REQUIRE(aligned16(g->quat) && aligned16(g->sem), "quat and sem must be 16-byte aligned");
+    SG_REQUIRE(g->sh_degree == 0 || g->sh, "sh_degree = %d needs sh coefficients", g->sh_degree);
+    return SG_OK;
+}
+
+// With spherical-harmonic colour the compositing kernels read the per-record colour the
+// projection wrote.
+static sg_status check_record_colour(const sg_gaussians *g, const sg_projected *proj) {
+    SG_REQUIRE(g->sh_degree == 0 || proj->rgb, "sh_degree = %d needs projected->rgb", g->sh_degree);
     return SG_OK;
 }
 
@@ -198,6 +207,7 @@ sg_status sg_project_gaussians(const sg_gaussians *g, const sg_view *views, int3
     SG_TRY(check_views(views, n_views));
     SG_REQUIRE(out && out->geo && out->rect && out->ext, "projected buffers are NULL");
     SG_REQUIRE(aligned16(out->geo), "geo must be 16-byte aligned");
+    SG_TRY(check_record_colour(g, out));
     SG_REQUIRE((int64_t)g->N * n_views < (1ll << 32), "too many records");
     return launch_project_fwd(g, views, n_views, cfg, out, (cudaStream_t)stream);
 }
@@ -233,6 +243,7 @@ sg_status sg_render_pyramid(const sg_gaussians *g, const sg_projected *proj,
     SG_REQUIRE(out->rgb && out->depth && out->sem && saved->T_final && saved->last && saved->n_contrib,
                "output buffers are NULL");
     SG_REQUIRE(!cfg->persistent || work_counter, "persistent launch needs work_counter");
+    SG_TRY(check_record_colour(g, proj));
     RasterArgs a{};
     fill_raster_args(a, g, proj, lists, views, n_views, n_tiles, cfg, work_counter);
     a.img_rgb = out->rgb;
@@ -276,7 +287,7 @@ sg_status sg_pyramid_loss(const sg_images *rendered, const sg_targets *gt, const
 }
 
 size_t sg_backward_workspace_size(int64_t n_records) {
-    return (size_t)n_records * 8 * sizeof(float);
+    return (size_t)n_records * 12 * sizeof(float);
 }
 
 static sg_status check_backward(const sg_gaussians *g, const sg_view *views, int32_t n_views, const sg_config *cfg,
@@ -288,6 +299,9 @@ static sg_status check_backward(const sg_gaussians *g, const sg_view *views, int
     SG_REQUIRE(grads->mean && grads->log_scale && grads->quat && grads->opacity_logit && grads->rgb &&
                    grads->sem, "gradient buffers are NULL");
     SG_REQUIRE(grads->N == g->N && grads->C == g->C, "grads shape differs from gaussians");
+    SG_REQUIRE(grads->sh_degree == g->sh_degree && (g->sh_degree == 0 || grads->sh),
+               "grads sh_degree %d differs from gaussians' %d or its sh is NULL", grads->sh_degree,
+               g->sh_degree);
     SG_REQUIRE(aligned16(workspace), "workspace must be 16-byte aligned");
     const size_t need = sg_backward_workspace_size((int64_t)g->N * n_views);
     if (workspace_bytes < need) {
@@ -307,6 +321,7 @@ sg_status sg_render_pyramid_backward_raster(const sg_gaussians *g, const sg_proj
     SG_TRY(check_backward(g, views, n_views, cfg, workspace, workspace_bytes, grads));
     SG_REQUIRE(proj && lists && saved && dL, "NULL argument");
     SG_REQUIRE(!cfg->persistent || work_counter, "persistent launch needs work_counter");
+    SG_TRY(check_record_colour(g, proj));
     cudaStream_t st = (cudaStream_t)stream;
     float *g2d = (float *)workspace;  // zero on entry (see sg.h)
     RasterArgs a{};
@@ -318,7 +333,14 @@ sg_status sg_render_pyramid_backward_raster(const sg_gaussians *g, const sg_proj
     a.dL_depth = dL->depth;
     a.dL_sem = dL->sem;
     a.g2d = g2d;
-    a.g_rgb = grads->rgb;
+    if (g->sh_degree > 0) {
+        // per-record colour gradients in the workspace's colour block (4 floats per record)
+        a.g_col = g2d + 8 * (size_t)g->N * n_views;
+        a.col_stride = 4;
+    } else {
+        a.g_col = grads->rgb;
+        a.col_stride = 3;
+    }
     a.g_sem = grads->sem;
     a.sem_v2 = ((uintptr_t)grads->sem % 8) == 0 && (g->C % 2) == 0;
     a.ppt = cfg->pixels_per_thread_bwd;

@@ -7,6 +7,11 @@
 // view-levels where it is visible are gathered first (all rectangle loads in flight at once),
 // then the chain rule runs on each with the next one's 2D gradients already loading.  The
 // view table sits in shared memory.
+//
+// View-dependent colour (spherical harmonics of degree D = 1..3) is a template parameter:
+// the forward evaluates each visible record's colour from the camera-to-mean direction, and
+// the adjoint chains the per-record colour gradients to the SH coefficients, rgb and the
+// mean; D = 0 compiles to the plain kernels.
 #include "sg_common.cuh"
 
 namespace sg {
@@ -136,21 +141,106 @@ __device__ __forceinline__ void cov2d_eq2(const sg_view &vw, float tz, const Gau
     det = s00 * s11;
 }
 
+// Real spherical harmonics of degree 1..D at the unit direction (x, y, z), in the graphics
+// order (m = -l..l within each degree, Condon-Shortley signs).  Constants from their closed
+// forms: c1 = sqrt(3/4pi); a2 = sqrt(15/pi)/2, b2 = sqrt(5/pi)/4, c2 = sqrt(15/pi)/4;
+// e3 = sqrt(35/2pi)/4, f3 = sqrt(105/pi)/2, h3 = sqrt(21/2pi)/4, k3 = sqrt(7/pi)/4,
+// m3 = sqrt(105/pi)/4.
+namespace shc {
+constexpr float c1 = 0.48860251190291992f;
+constexpr float a2 = 1.09254843059207907f, b2 = 0.31539156525252005f, c2 = 0.54627421529603959f;
+constexpr float e3 = 0.59004358992664352f, f3 = 2.89061144264055405f, h3 = 0.45704579946446573f;
+constexpr float k3 = 0.37317633259011540f, m3 = 1.44530572132027702f;
+}  // namespace shc
+
+template <int D>
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float *Y) {
+    Y[0] = -shc::c1 * y;
+    Y[1] = shc::c1 * z;
+    Y[2] = -shc::c1 * x;
+    if constexpr (D >= 2) {
+        Y[3] = shc::a2 * x * y;
+        Y[4] = -shc::a2 * y * z;
+        Y[5] = shc::b2 * (2.f * z * z - x * x - y * y);
+        Y[6] = -shc::a2 * x * z;
+        Y[7] = shc::c2 * (x * x - y * y);
+    }
+    if constexpr (D >= 3) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[8] = -shc::e3 * y * (3.f * xx - yy);
+        Y[9] = shc::f3 * x * y * z;
+        Y[10] = -shc::h3 * y * (4.f * zz - xx - yy);
+        Y[11] = shc::k3 * z * (2.f * zz - 3.f * xx - 3.f * yy);
+        Y[12] = -shc::h3 * x * (4.f * zz - xx - yy);
+        Y[13] = shc::m3 * z * (xx - yy);
+        Y[14] = -shc::e3 * x * (xx - 3.f * yy);
+    }
+}
+
+// sum_k w_k grad Y_k at (x, y, z), the gradient of each basis polynomial (before restriction
+// to the sphere).
+template <int D>
+__device__ __forceinline__ void sh_grad(float x, float y, float z, const float *w, float gd[3]) {
+    gd[0] = -shc::c1 * w[2];
+    gd[1] = -shc::c1 * w[0];
+    gd[2] = shc::c1 * w[1];
+    if constexpr (D >= 2) {
+        gd[0] += shc::a2 * (y * w[3] - z * w[6]) - 2.f * shc::b2 * x * w[5] + 2.f * shc::c2 * x * w[7];
+        gd[1] += shc::a2 * (x * w[3] - z * w[4]) - 2.f * shc::b2 * y * w[5] - 2.f * shc::c2 * y * w[7];
+        gd[2] += -shc::a2 * (y * w[4] + x * w[6]) + 4.f * shc::b2 * z * w[5];
+    }
+    if constexpr (D >= 3) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        gd[0] += -6.f * shc::e3 * x * y * w[8] + shc::f3 * y * z * w[9] + 2.f * shc::h3 * x * y * w[10] -
+                 6.f * shc::k3 * x * z * w[11] - shc::h3 * (4.f * zz - 3.f * xx - yy) * w[12] +
+                 2.f * shc::m3 * x * z * w[13] - 3.f * shc::e3 * (xx - yy) * w[14];
+        gd[1] += -3.f * shc::e3 * (xx - yy) * w[8] + shc::f3 * x * z * w[9] -
+                 shc::h3 * (4.f * zz - xx - 3.f * yy) * w[10] - 6.f * shc::k3 * y * z * w[11] +
+                 2.f * shc::h3 * x * y * w[12] - 2.f * shc::m3 * y * z * w[13] + 6.f * shc::e3 * x * y * w[14];
+        gd[2] += shc::f3 * x * y * w[9] - 8.f * shc::h3 * y * z * w[10] +
+                 shc::k3 * (6.f * zz - 3.f * xx - 3.f * yy) * w[11] - 8.f * shc::h3 * x * z * w[12] +
+                 shc::m3 * (xx - yy) * w[13];
+    }
+}
+
+// Camera centre c = -R^T t of every view-level, next to the view table in shared memory.
+__device__ __forceinline__ void view_centres(const sg_view *s_views, int n_views, float3 *s_centre) {
+    for (int i = threadIdx.x; i < n_views; i += blockDim.x) {
+        const float *R = s_views[i].R, *t = s_views[i].t;
+        s_centre[i] = make_float3(-(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]),
+                                  -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]),
+                                  -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2]));
+    }
+}
+
+template <int D>
 __global__ void __launch_bounds__(256) project_fwd_kernel(
     const float *__restrict__ mean, const float *__restrict__ log_scale,
     const float4 *__restrict__ quat, const float *__restrict__ ologit, int N,
     const sg_view *__restrict__ views, int n_views, ProjConsts pc, float4 *__restrict__ geo,
-    uint2 *__restrict__ rect, float2 *__restrict__ ext) {
+    uint2 *__restrict__ rect, float2 *__restrict__ ext, const float *__restrict__ rgb,
+    const float *__restrict__ sh, float *__restrict__ rec_rgb) {
+    constexpr int K = (D + 1) * (D + 1) - 1;
     pdl_begin();
     __shared__ sg_view s_views[SG_MAX_VIEWS];
+    __shared__ float3 s_centre[SG_MAX_VIEWS];
     for (int i = threadIdx.x; i < n_views; i += blockDim.x) s_views[i] = views[i];
     __syncthreads();
+    if constexpr (D > 0) {
+        view_centres(s_views, n_views, s_centre);
+        __syncthreads();
+    }
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N) return;
     const float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
     GaussianFrame f;
     gaussian_frame(log_scale, quat[g], g, f);
     const float o = 1.f / (1.f + expf(-ologit[g]));
+    float shv[3 * K + 1], c0[3];
+    if constexpr (D > 0) {
+        for (int i = 0; i < 3 * K; ++i) shv[i] = sh[(size_t)3 * K * g + i];
+        for (int c = 0; c < 3; ++c) c0[c] = rgb[3 * g + c];
+    }
     for (int v = 0; v < n_views; ++v) {
         const sg_view &vw = s_views[v];
         const size_t r = (size_t)v * N + g;
@@ -207,6 +297,20 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
                     const uint32_t packed = ((uint32_t)(int)ui & 0xffffu) | (((uint32_t)(int)vi & 0xffffu) << 16);
                     g1 = make_float4(m00, m10, m11, __uint_as_float(packed));
                     e2 = make_float2(ex, ey);
+                    if constexpr (D > 0) {
+                        // colour = rgb + sum_k sh_k Y_k(d), d = (mu - c) / |mu - c|
+                        const float3 cc = s_centre[v];
+                        const float dx = mu[0] - cc.x, dy = mu[1] - cc.y, dz = mu[2] - cc.z;
+                        const float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
+                        float Y[K];
+                        sh_eval<D>(dx * rn, dy * rn, dz * rn, Y);
+                        for (int c = 0; c < 3; ++c) {
+                            float col = c0[c];
+#pragma unroll
+                            for (int k = 0; k < K; ++k) col = fmaf(Y[k], shv[3 * k + c], col);
+                            rec_rgb[3 * r + c] = col;
+                        }
+                    }
                 }
             }
         }
@@ -217,17 +321,26 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     }
 }
 
-// Adjoint.  g2d: per record (u, v, conic a, conic b, conic c, opacity, depth, 0).
+// Adjoint.  g2d: per record (u, v, conic a, conic b, conic c, opacity, depth, 0); with SH,
+// gcol: per record dL/d(colour) (r, g, b, 0).
+template <int D>
 __global__ void __launch_bounds__(256) project_bwd_kernel(
     const float *__restrict__ mean, const float *__restrict__ log_scale,
     const float4 *__restrict__ quat, const float *__restrict__ ologit, int N,
     const sg_view *__restrict__ views, int n_views, ProjConsts pc,
     const uint2 *__restrict__ rect, float4 *__restrict__ g2d, float *__restrict__ g_mean, float *__restrict__ g_ls,
-    float *__restrict__ g_quat, float *__restrict__ g_ologit) {
+    float *__restrict__ g_quat, float *__restrict__ g_ologit, const float *__restrict__ sh,
+    float4 *__restrict__ gcol, float *__restrict__ g_rgb, float *__restrict__ g_sh) {
+    constexpr int K = (D + 1) * (D + 1) - 1;
     pdl_begin();
     __shared__ sg_view s_views[SG_MAX_VIEWS];
+    __shared__ float3 s_centre[SG_MAX_VIEWS];
     for (int i = threadIdx.x; i < n_views; i += blockDim.x) s_views[i] = views[i];
     __syncthreads();
+    if constexpr (D > 0) {
+        view_centres(s_views, n_views, s_centre);
+        __syncthreads();
+    }
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N) return;
     const float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
@@ -238,6 +351,13 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     float gSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // full-entry gradient, symmetric
     float go_total = 0.f;
     float gls0 = 0.f;  // Eq. 2 mode: dL/dlog_scale[0]
+    float shv[3 * K + 1], gsh[3 * K + 1], grgb[3] = {0.f, 0.f, 0.f};
+    if constexpr (D > 0) {
+        for (int i = 0; i < 3 * K; ++i) {
+            shv[i] = sh[(size_t)3 * K * g + i];
+            gsh[i] = 0.f;
+        }
+    }
     // Visible view-levels first, 32 at a time, with all tile-rectangle loads in flight
     // together; then the visible ones, each one's 2D gradients loaded one view ahead.
     for (int v0 = 0; v0 < n_views; v0 += 32) {
@@ -248,30 +368,60 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
         const uint2 rc = rect[(size_t)(v0 + i) * N + g];
         vis |= (rc.x != rc.y ? 1u : 0u) << i;  // an empty rectangle means culled
     }
-    float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
+    float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na, nc = na;
     if (vis) {
         const size_t r = (size_t)(v0 + __ffs(vis) - 1) * N + g;
         na = g2d[2 * r];
         nb = g2d[2 * r + 1];
+        if constexpr (D > 0) nc = gcol[r];
     }
     while (vis) {
         const int v = v0 + __ffs(vis) - 1;
         vis &= vis - 1;
-        const float4 a = na, b = nb;
+        const float4 a = na, b = nb, cg = nc;
         {
             // consumed: zero the record's slots, so the workspace is all zero for the next
             // compositing adjoint (only visible records are ever written)
             const size_t r = (size_t)v * N + g;
             g2d[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
             g2d[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (D > 0) gcol[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         if (vis) {
             const size_t rn = (size_t)(v0 + __ffs(vis) - 1) * N + g;
             na = g2d[2 * rn];
             nb = g2d[2 * rn + 1];
+            if constexpr (D > 0) nc = gcol[rn];
         }
         const float gu = a.x, gv = a.y, ga = a.z, gb = a.w, gc = b.x, go = b.y, gd = b.z;
         const sg_view &vw = s_views[v];
+        if constexpr (D > 0) {
+            // colour = rgb + sum_k sh_k Y_k(d): dL/dsh_k += Y_k dL/dcolour, dL/drgb += dL/dcolour,
+            // dL/dmu += (I - d d^T) / |mu - c| sum_k (sh_k . dL/dcolour) grad Y_k(d)
+            const float gcv[3] = {cg.x, cg.y, cg.z};
+            const float3 cc = s_centre[v];
+            const float dx = mu[0] - cc.x, dy = mu[1] - cc.y, dz = mu[2] - cc.z;
+            const float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
+            const float x = dx * rn, y = dy * rn, z = dz * rn;
+            float Y[K], w[K];
+            sh_eval<D>(x, y, z, Y);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                w[k] = 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    gsh[3 * k + c] = fmaf(Y[k], gcv[c], gsh[3 * k + c]);
+                    w[k] = fmaf(shv[3 * k + c], gcv[c], w[k]);
+                }
+            }
+            for (int c = 0; c < 3; ++c) grgb[c] += gcv[c];
+            float gdir[3];
+            sh_grad<D>(x, y, z, w, gdir);
+            const float radial = gdir[0] * x + gdir[1] * y + gdir[2] * z;
+            gmu[0] += (gdir[0] - radial * x) * rn;
+            gmu[1] += (gdir[1] - radial * y) * rn;
+            gmu[2] += (gdir[2] - radial * z) * rn;
+        }
         ViewGeom q;
         view_geom(vw, mu, pc.fov_clamp, q);
         // conic = Sigma2D^{-1} of this view-level, recomputed in float32
@@ -381,6 +531,10 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
         g_ls[3 * g + j] += gls[j];
     }
     g_ologit[g] += go_total * o * (1.f - o);
+    if constexpr (D > 0) {
+        for (int c = 0; c < 3; ++c) g_rgb[3 * g + c] += grgb[c];
+        for (int i = 0; i < 3 * K; ++i) g_sh[(size_t)3 * K * g + i] += gsh[i];
+    }
 }
 
 sg_status launch_project_fwd(const sg_gaussians *g, const sg_view *views, int n_views,
@@ -389,12 +543,17 @@ sg_status launch_project_fwd(const sg_gaussians *g, const sg_view *views, int n_
                   cfg->tile_h, cfg->isotropic};
     const int threads = 256;
     const int blocks = (g->N + threads - 1) / threads;
-    if (blocks > 0)
-        launch_pdl(project_fwd_kernel, blocks, threads, 0, st,
+    if (blocks > 0) {
+        auto kern = g->sh_degree == 3 ? project_fwd_kernel<3>
+                  : g->sh_degree == 2 ? project_fwd_kernel<2>
+                  : g->sh_degree == 1 ? project_fwd_kernel<1> : project_fwd_kernel<0>;
+        launch_pdl(kern, blocks, threads, 0, st,
             g->mean, g->log_scale, reinterpret_cast<const float4 *>(g->quat), g->opacity_logit,
             g->N, views, n_views, pc, reinterpret_cast<float4 *>(out->geo),
-            reinterpret_cast<uint2 *>(out->rect), reinterpret_cast<float2 *>(out->ext));
-    if (blocks > 0) count_launches(1);
+            reinterpret_cast<uint2 *>(out->rect), reinterpret_cast<float2 *>(out->ext), g->rgb, g->sh,
+            out->rgb);
+        count_launches(1);
+    }
     return check_launch("project_fwd");
 }
 
@@ -405,13 +564,19 @@ sg_status launch_project_bwd(const sg_gaussians *g, const sg_view *views, int n_
                   cfg->tile_h, cfg->isotropic};
     const int threads = 256;
     const int blocks = (g->N + threads - 1) / threads;
-    if (blocks > 0)
-        launch_pdl(project_bwd_kernel, blocks, threads, 0, st,
+    if (blocks > 0) {
+        auto kern = g->sh_degree == 3 ? project_bwd_kernel<3>
+                  : g->sh_degree == 2 ? project_bwd_kernel<2>
+                  : g->sh_degree == 1 ? project_bwd_kernel<1> : project_bwd_kernel<0>;
+        // the colour block of the workspace follows the R x 8 floats of 2D gradients
+        float4 *gcol = reinterpret_cast<float4 *>(g2d + 8 * (size_t)g->N * n_views);
+        launch_pdl(kern, blocks, threads, 0, st,
             g->mean, g->log_scale, reinterpret_cast<const float4 *>(g->quat), g->opacity_logit,
             g->N, views, n_views, pc, reinterpret_cast<const uint2 *>(proj->rect),
             reinterpret_cast<float4 *>(g2d),
-            gr->mean, gr->log_scale, gr->quat, gr->opacity_logit);
-    if (blocks > 0) count_launches(1);
+            gr->mean, gr->log_scale, gr->quat, gr->opacity_logit, g->sh, gcol, gr->rgb, gr->sh);
+        count_launches(1);
+    }
     return check_launch("project_bwd");
 }
 

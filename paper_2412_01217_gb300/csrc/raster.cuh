@@ -12,7 +12,8 @@ struct RasterArgs {
     const uint32_t *record;
     const int2 *ranges;
     const int *order;  // work order of the tiles (null: id order)
-    const float *rgb;
+    const float *rgb;  // colour: N x 3 per Gaussian, or R x 3 per record when col_rec
+    int col_rec;       // 1: colour (and its gradient) indexed by record, else by Gaussian
     const float *sem;
     const sg_view *views;
     int n_views, n_tiles, N;
@@ -28,7 +29,9 @@ struct RasterArgs {
     int *last, *n_contrib;
     // backward
     const float *dL_rgb, *dL_depth, *dL_sem;
-    float *g2d, *g_rgb, *g_sem;
+    float *g2d, *g_sem;
+    float *g_col;    // colour gradient: col_stride floats per Gaussian (or record when col_rec)
+    int col_stride;
     int sem_v2;  // g_sem is 8-byte aligned (pairs of semantic gradients in one vector reduction)
 };
 
@@ -40,7 +43,8 @@ inline void fill_raster_args(RasterArgs &a, const sg_gaussians *g, const sg_proj
     a.record = lists->record;
     a.ranges = reinterpret_cast<const int2 *>(lists->ranges);
     a.order = lists->order;
-    a.rgb = g->rgb;
+    a.col_rec = g->sh_degree > 0;
+    a.rgb = a.col_rec ? proj->rgb : g->rgb;
     a.sem = g->sem;
     a.views = views;
     a.n_views = n_views;

@@ -53,10 +53,11 @@ __device__ __forceinline__ void load_batch(const RasterArgs &a, int C, int list_
         s_geo1[j] = make_float4(g1.x, g1.y, g1.z, g0.w);
         s_geo2[j] = make_float4(uI + g0.x, vI + g0.y, ex.x, ex.y);
         const uint32_t gi = rec - rec_base;  // every record of a tile belongs to its view-level
+        const size_t ci = a.col_rec ? rec : gi;
         float *f = s_feat + (size_t)j * NF;
-        f[0] = a.rgb[3 * (size_t)gi];
-        f[1] = a.rgb[3 * (size_t)gi + 1];
-        f[2] = a.rgb[3 * (size_t)gi + 2];
+        f[0] = a.rgb[3 * ci];
+        f[1] = a.rgb[3 * ci + 1];
+        f[2] = a.rgb[3 * ci + 2];
         f[3] = g0.z;  // depth (camera z of the mean, Eq. 8)
         const float4 *s4 = reinterpret_cast<const float4 *>(a.sem + (size_t)gi * C);
         float4 *f4 = reinterpret_cast<float4 *>(f + 4);
@@ -514,7 +515,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
                             const float val = df[nt][2 * hr + c2];
                             if (f >= NF) continue;
                             if (f < 3)
-                                atomicAdd(a.g_rgb + 3 * (size_t)gi + f, val);
+                                atomicAdd(a.g_col + (size_t)a.col_stride * (a.col_rec ? rec : gi) + f, val);
                             else if (f == 3)
                                 atomicAdd(a.g2d + 8 * (size_t)rec + 6, val);
                             else

@@ -19,6 +19,24 @@ from ._lib import (SgCamera, SgConfig, SgGaussians, SgImages, SgLossConfig, SgPr
 PARAM_KEYS = ("mean", "log_scale", "quat", "opacity_logit", "rgb", "sem")
 
 
+def sh_degree(g):
+    """Degree D of the spherical-harmonic colour of a parameter dict: g["sh"] is
+    N x ((D+1)^2 - 1) x 3; 0 without it."""
+    sh = g.get("sh")
+    if sh is None or sh.shape[1] == 0:
+        return 0
+    K = sh.shape[1]
+    D = {3: 1, 8: 2, 15: 3}.get(K)
+    if D is None:
+        raise ValueError(f"sh has {K} coefficients per channel; expected 3, 8 or 15")
+    return D
+
+
+def param_keys(g):
+    """PARAM_KEYS, plus "sh" when the parameters carry spherical-harmonic colour."""
+    return PARAM_KEYS + (("sh",) if sh_degree(g) else ())
+
+
 def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
 
@@ -121,13 +139,17 @@ def gaussians_struct(g, N=None, C_=None):
     s.opacity_logit, s.rgb, s.sem = g["opacity_logit"].data_ptr(), g["rgb"].data_ptr(), g["sem"].data_ptr()
     s.N = g["mean"].shape[0] if N is None else N
     s.C = g["sem"].shape[1] if C_ is None else C_
+    D = sh_degree(g)
+    if D:
+        s.sh, s.sh_degree = g["sh"].data_ptr(), D
     return s
 
 
 def to_device_params(g, device="cuda"):
-    """dict of arrays -> dict of contiguous float32 CUDA tensors (quat/sem 16-B aligned)."""
+    """dict of arrays -> dict of contiguous float32 CUDA tensors (quat/sem 16-B aligned);
+    "sh" (N x K x 3) is carried when present."""
     out = {}
-    for k in PARAM_KEYS:
+    for k in PARAM_KEYS + (("sh",) if g.get("sh") is not None else ()):
         out[k] = torch.as_tensor(np.ascontiguousarray(g[k], dtype=np.float32)).to(device).contiguous()
     return out
 
@@ -141,7 +163,7 @@ class PyramidRasterizer:
     """
 
     def __init__(self, N, C, cams, levels=1, cfg: RenderConfig | None = None, capacity=None,
-                 loss_cfg: LossConfig | None = None, device="cuda"):
+                 loss_cfg: LossConfig | None = None, device="cuda", sh_degree=0):
         require_cuda()
         _lib.load()
         self.N, self.C, self.levels = int(N), int(C), int(levels)
@@ -188,10 +210,25 @@ class PyramidRasterizer:
                                    dtype=torch.uint8, device=dev)
         self.bwd_ws = torch.zeros(lib.sg_backward_workspace_size(max(1, self.R)), dtype=torch.uint8, device=dev)
         self._ccfg = self.cfg.to_c()
-        self._proj = SgProjected(self.geo.data_ptr(), self.rect.data_ptr(), self.ext.data_ptr())
+        # per-record view-dependent colour (spherical-harmonic colour only)
+        self.rec_rgb = None
+        self._proj = SgProjected(self.geo.data_ptr(), self.rect.data_ptr(), self.ext.data_ptr(), 0)
+        if sh_degree:
+            self._alloc_record_colour()
         self._lists = SgTileLists(self.capacity, self.tile.data_ptr(), self.record.data_ptr(),
                                   self.ranges.data_ptr(), self.count.data_ptr(), self.order.data_ptr())
         self._saved = SgSaved(self.T_final.data_ptr(), self.last.data_ptr(), self.n_contrib.data_ptr())
+
+    def _alloc_record_colour(self):
+        self.rec_rgb = torch.zeros(max(1, self.N_max * self.V) * 3, dtype=torch.float32, device=self.device)
+        self._proj.rgb = self.rec_rgb.data_ptr()
+
+    def _check_colour(self, g):
+        if sh_degree(g) and self.rec_rgb is None:
+            if torch.cuda.is_current_stream_capturing():
+                raise RuntimeError("spherical-harmonic colour: build the rasterizer with sh_degree > 0 "
+                                   "before capturing a graph")
+            self._alloc_record_colour()
 
     def set_count(self, N):
         """Use the first N <= capacity Gaussians (buffers keep their maximum size)."""
@@ -220,6 +257,7 @@ class PyramidRasterizer:
 
     # ---- forward -----------------------------------------------------------------------
     def project(self, g):
+        self._check_colour(g)
         gs = gaussians_struct(g)
         call("sg_project_gaussians", C.byref(gs), _ptr(self.views), self.V, C.byref(self._ccfg),
              C.byref(self._proj), _stream())
@@ -324,36 +362,40 @@ class PyramidSplat(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, rast, mean, log_scale, quat, opacity_logit, rgb, sem):
+    def forward(ctx, rast, mean, log_scale, quat, opacity_logit, rgb, sem, sh=None):
         g = dict(mean=mean.contiguous(), log_scale=log_scale.contiguous(), quat=quat.contiguous(),
                  opacity_logit=opacity_logit.contiguous(), rgb=rgb.contiguous(), sem=sem.contiguous())
+        if sh is not None:
+            g["sh"] = sh.contiguous()
         out_rgb = torch.empty(3 * rast.P, dtype=torch.float32, device=rast.device)
         out_depth = torch.empty(rast.P, dtype=torch.float32, device=rast.device)
         out_sem = torch.empty(rast.C * rast.P, dtype=torch.float32, device=rast.device)
         rast.forward(g, out_rgb=out_rgb, out_depth=out_depth, out_sem=out_sem)
         ctx.rast = rast
-        ctx.save_for_backward(*[g[k] for k in PARAM_KEYS])
+        ctx.keys = param_keys(g)
+        ctx.save_for_backward(*[g[k] for k in ctx.keys])
         return out_rgb, out_depth, out_sem
 
     @staticmethod
     def backward(ctx, d_rgb, d_depth, d_sem):
         rast = ctx.rast
-        params = dict(zip(PARAM_KEYS, ctx.saved_tensors))
+        params = dict(zip(ctx.keys, ctx.saved_tensors))
         grads = {k: torch.zeros_like(v) for k, v in params.items()}
         z = lambda t, n: t.contiguous() if t is not None else torch.zeros(n, dtype=torch.float32, device=rast.device)
         rast.backward(params, grads, dL=(z(d_rgb, 3 * rast.P), z(d_depth, rast.P), z(d_sem, rast.C * rast.P)))
-        return (None, *[grads[k] for k in PARAM_KEYS])
+        return (None, *[grads[k] for k in PARAM_KEYS], grads.get("sh"))
 
 
 def pyramid_splat(rast, g):
-    return PyramidSplat.apply(rast, *[g[k] for k in PARAM_KEYS])
+    return PyramidSplat.apply(rast, *[g[k] for k in PARAM_KEYS], g.get("sh"))
 
 
 # ------------------------------------------------------------------------------------------
 # One mapping iteration (project -> lists -> render -> loss -> adjoint -> Adam), capturable
 # ------------------------------------------------------------------------------------------
 
-DEFAULT_LR = dict(mean=1e-4, log_scale=5e-3, quat=1e-3, opacity_logit=5e-2, rgb=2.5e-3, sem=2.5e-3)
+DEFAULT_LR = dict(mean=1e-4, log_scale=5e-3, quat=1e-3, opacity_logit=5e-2, rgb=2.5e-3, sem=2.5e-3,
+                  sh=1.25e-4)
 
 
 class MappingStep:
@@ -381,7 +423,7 @@ class MappingStep:
     def _adam_groups(self):
         from ._lib import SgAdamGroup
         groups = [SgAdamGroup(self.p[k].data_ptr(), self.grads[k].data_ptr(), self.m[k].data_ptr(),
-                              self.v[k].data_ptr(), self.p[k].numel(), self.lr[k]) for k in PARAM_KEYS]
+                              self.v[k].data_ptr(), self.p[k].numel(), self.lr[k]) for k in param_keys(self.p)]
         return (SgAdamGroup * len(groups))(*groups), len(groups)
 
     def _step_kernels(self, t):

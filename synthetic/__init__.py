@@ -87,6 +87,17 @@ def cloud_scene(n=2000, n_sem=8, seed=1):
                 opacity_logit=f32(opacity_logit), rgb=f32(rgb), sem=f32(sem))
 
 
+def sh_coefficients(n, degree, scale=0.2, seed=3):
+    """Seeded view-dependent colour coefficients: N x ((D+1)^2 - 1) x 3 float32, the
+    degree-l rows ~ N(0, (scale / l)^2) (higher degrees carry less energy, as fitted SH
+    colour does)."""
+    rng = np.random.default_rng(seed)
+    K = (degree + 1) ** 2 - 1
+    l = np.floor(np.sqrt(np.arange(1, K + 1))).astype(np.float64)   # degree of row k
+    sh = rng.normal(size=(n, K, 3)) * (scale / l)[None, :, None]
+    return np.ascontiguousarray(sh, dtype=np.float32)
+
+
 def random_targets(H, W, n_classes, seed=2):
     """Seeded target frame: rgb~U[0,1] (3,H,W), depth~U[1,4] (H,W), label~U{0..n-1}."""
     rng = np.random.default_rng(seed)

@@ -30,7 +30,7 @@ def test_struct_sizes_match_header_layout():
     from paper_2412_01217_gb300 import _lib
     assert C.sizeof(_lib.SgCamera) == 72
     assert C.sizeof(_lib.SgView) == 96
-    assert C.sizeof(_lib.SgGaussians) == 56
+    assert C.sizeof(_lib.SgGaussians) == 72
     assert C.sizeof(_lib.SgConfig) == 68
     assert C.sizeof(_lib.SgLossConfig) == 40
 
@@ -81,6 +81,9 @@ def test_host_validation_rejects_bad_arguments():
     g.C = 8
     assert lib.sg_project_gaussians(C.byref(g), None, 1, C.byref(cfg), C.byref(proj), None) == 1
     assert b"NULL" in lib.sg_last_error()
+    g.sh_degree = 4                   # spherical-harmonic colour goes to degree 3
+    assert lib.sg_project_gaussians(C.byref(g), None, 1, C.byref(cfg), C.byref(proj), None) == 1
+    assert b"sh_degree = 4" in lib.sg_last_error()
     assert lib.sg_adam_step(None, None, None, None, 5, 1e-3, 0.9, 0.999, 1e-8, 0, None) == 1
     assert lib.sg_adam_step(None, None, None, None, 0, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 0
 

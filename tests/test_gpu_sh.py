@@ -1,0 +1,169 @@
+"""GPU parity of the view-dependent (spherical-harmonic) colour of Sec. III-B against the FP64
+oracle: the projection's per-record colour feeds the compositing kernels, and the adjoint
+chains the per-record colour gradients to the SH coefficients, rgb and the mean.  Same
+tolerances as the other parity tests (forward 1e-4 rel + 1e-5 abs, gradients 2e-3 rel +
+1e-5 of the group's largest entry)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+from helpers import AMBIGUOUS, AMBIGUOUS_GRAD, FWD_ABS, FWD_REL, check_close, check_grads
+from test_gpu_parity import f32_camera, oracle_cams, room_small, view_images
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("mean", "log_scale", "quat", "opacity_logit", "rgb", "sem", "sh")
+
+
+def make(g, cams, levels=1, **kw):
+    from paper_2412_01217_gb300 import PyramidRasterizer, RenderConfig, to_device_params
+    from paper_2412_01217_gb300.splat import sh_degree
+    p = to_device_params(g)
+    r = PyramidRasterizer(g["mean"].shape[0], g["sem"].shape[1], cams, levels, RenderConfig(**kw),
+                          sh_degree=sh_degree(p))
+    return r, p
+
+
+def sh_cloud(degree, n=2000, seed=1):
+    g = synthetic.cloud_scene(n, 8, seed=seed)
+    g["sh"] = synthetic.sh_coefficients(n, degree, seed=seed + 10)
+    # a camera away from the origin and turned a little, so that the centre -R^T t and the
+    # rotation both enter the view directions
+    cam = synthetic.cloud_camera()
+    a = 0.15
+    R = np.array([[np.cos(a), 0, np.sin(a)], [0, 1, 0], [-np.sin(a), 0, np.cos(a)]])
+    cam = f32_camera(dict(cam, R_cw=R, t_cw=np.array([0.1, -0.05, 0.3])))
+    return g, cam
+
+
+def upstream(ref_f, H, W, C, seed):
+    keep = ((ref_f["flags"] & AMBIGUOUS_GRAD) == 0).astype(np.float64)
+    rng = np.random.default_rng(seed)
+    return (rng.normal(size=(3, H, W)) * keep, rng.normal(size=(H, W)) * keep,
+            rng.normal(size=(C, H, W)) * keep)
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_sh_forward_matches_oracle(degree):
+    g, cam = sh_cloud(degree)
+    r, p = make(g, [cam])
+    r.forward(p)
+    got = view_images(r, 0, 8)
+    ref = oracle.render(g, cam)
+    amb = (ref["flags"] & AMBIGUOUS) != 0
+    assert amb.mean() < 0.02
+    for k in ("rgb", "depth", "sem", "T"):
+        check_close(k, got[k], ref[k], FWD_REL, FWD_ABS, mask=~amb)
+    # the SH term is not negligible in this scene: without it the image differs
+    ref0 = oracle.render({k: v for k, v in g.items() if k != "sh"}, cam)
+    assert np.abs(ref0["rgb"] - ref["rgb"]).max() > 0.05
+
+
+@pytest.mark.parametrize("degree, ppt", [(1, 1), (2, 2), (3, 1), (3, 4)])
+def test_sh_backward_matches_oracle(degree, ppt):
+    g, cam = sh_cloud(degree, seed=degree)
+    r, p = make(g, [cam], pixels_per_thread_bwd=ppt)
+    r.forward(p)
+    ref_f = oracle.render(g, cam)
+    H, W = cam["H"], cam["W"]
+    up = upstream(ref_f, H, W, 8, seed=20 + degree)
+    dl = tuple(torch.tensor(u.reshape(-1), dtype=torch.float32, device="cuda") for u in up)
+    grads = {k: torch.zeros_like(v) for k, v in p.items()}
+    r.backward(p, grads, dL=dl)
+    got = {k: v.cpu().numpy() for k, v in grads.items()}
+    up32 = [t.cpu().numpy().astype(np.float64).reshape(u.shape) for t, u in zip(dl, up)]
+    ref = oracle.render_backward(g, cam, *up32)
+    check_grads(got, ref, KEYS)
+    # both workspace blocks (2D gradients and record colour gradients) are left zero
+    assert not r.bwd_ws.any() and not r.work_counter.any()
+
+
+def test_sh_multiview_pyramid_matches_oracle():
+    """Two keyframes x three levels with degree-3 colour: every view-level's image and the
+    summed gradients; the levels of one keyframe share its camera centre."""
+    room, g, cams = room_small(n=6000, ncam=2, W=160, H=96)
+    g["sh"] = synthetic.sh_coefficients(6000, 3, seed=7)
+    r, p = make(g, cams, levels=3)
+    r.forward(p)
+    ocams = oracle_cams(cams, 3)
+    rng = np.random.default_rng(5)
+    dl = [torch.zeros(3 * r.P, device="cuda"), torch.zeros(r.P, device="cuda"), torch.zeros(16 * r.P, device="cuda")]
+    for v, oc in enumerate(ocams):
+        got = view_images(r, v, 16)
+        ref = oracle.render(g, oc)
+        amb = (ref["flags"] & AMBIGUOUS) != 0
+        assert amb.mean() < 0.03
+        for k in ("rgb", "depth", "sem", "T"):
+            check_close(f"v{v} {k}", got[k], ref[k], FWD_REL, FWD_ABS, mask=~amb)
+        a, b, c = upstream(ref, oc["H"], oc["W"], 16, seed=v)
+        r.view_slice(dl[0], v, 3).copy_(torch.tensor(a, dtype=torch.float32))
+        r.view_slice(dl[1], v, 1).copy_(torch.tensor(b[None], dtype=torch.float32))
+        r.view_slice(dl[2], v, 16).copy_(torch.tensor(c, dtype=torch.float32))
+    grads = {k: torch.zeros_like(t) for k, t in p.items()}
+    r.backward(p, grads, dL=tuple(dl))
+    got = {k: t.cpu().numpy() for k, t in grads.items()}
+    ref = {k: 0.0 for k in KEYS}
+    for v, oc in enumerate(ocams):
+        a = r.view_slice(dl[0], v, 3).cpu().numpy().astype(np.float64)
+        b = r.view_slice(dl[1], v, 1)[0].cpu().numpy().astype(np.float64)
+        c = r.view_slice(dl[2], v, 16).cpu().numpy().astype(np.float64)
+        rv = oracle.render_backward(g, oc, a, b, c)
+        for k in KEYS:
+            ref[k] = ref[k] + rv[k]
+    check_grads(got, ref, KEYS)
+
+
+def test_zero_sh_equals_plain_colour_path():
+    """Zero SH coefficients route colour through the per-record buffers, yet give the plain
+    path's images and gradients (up to the order of the float32 atomic sums)."""
+    g, cam = sh_cloud(2, seed=4)
+    g["sh"] = np.zeros_like(g["sh"])
+    plain = {k: v for k, v in g.items() if k != "sh"}
+    r1, p1 = make(g, [cam])
+    r0, p0 = make(plain, [cam])
+    r1.forward(p1)
+    r0.forward(p0)
+    for k in ("rgb", "depth", "sem", "T", "n_contrib"):
+        assert np.array_equal(view_images(r1, 0, 8)[k], view_images(r0, 0, 8)[k]), k
+    rng = np.random.default_rng(0)
+    dl = (torch.tensor(rng.normal(size=3 * r0.P), dtype=torch.float32, device="cuda"),
+          torch.tensor(rng.normal(size=r0.P), dtype=torch.float32, device="cuda"),
+          torch.tensor(rng.normal(size=8 * r0.P), dtype=torch.float32, device="cuda"))
+    g1 = {k: torch.zeros_like(v) for k, v in p1.items()}
+    g0 = {k: torch.zeros_like(v) for k, v in p0.items()}
+    r1.backward(p1, g1, dL=dl)
+    r0.backward(p0, g0, dL=dl)
+    for k in ("mean", "log_scale", "quat", "opacity_logit", "rgb", "sem"):
+        a, b = g1[k].cpu().numpy(), g0[k].cpu().numpy()
+        assert np.allclose(a, b, rtol=1e-4, atol=1e-6 * (np.abs(b).max() + 1e-12)), k
+
+
+def test_sh_autograd_and_mapping_step():
+    """pyramid_splat returns the SH gradient through autograd, and a captured mapping step
+    updates the SH coefficients with their own Adam group."""
+    from paper_2412_01217_gb300 import MappingStep, build_pyramid, pyramid_splat
+    g, cam = sh_cloud(3, n=3000, seed=6)
+    r, p = make(g, [cam])
+    leaf = {k: v.clone().requires_grad_(True) for k, v in p.items()}
+    rgb, depth, sem = pyramid_splat(r, leaf)
+    (rgb.square().sum() + 0.1 * depth.sum()).backward()
+    assert leaf["sh"].grad is not None and leaf["sh"].grad.abs().max() > 0
+    direct = {k: torch.zeros_like(v) for k, v in p.items()}
+    r.forward(p)
+    r.backward(p, direct, dL=(2 * r.img_rgb, torch.full_like(r.img_depth, 0.1), torch.zeros_like(r.img_sem)))
+    assert torch.allclose(leaf["sh"].grad, direct["sh"], rtol=1e-4, atol=1e-6 * float(direct["sh"].abs().max()))
+
+    tgt = synthetic.random_targets(cam["H"], cam["W"], 8, seed=3)
+    gt = build_pyramid(r, [tgt["rgb"]], [tgt["depth"]], [tgt["label"]])
+    step = MappingStep(r, {k: v.clone() for k, v in p.items()}, gt)
+    sh0 = step.p["sh"].clone()
+    step.step()
+    loss1 = step.total_loss()
+    step.capture()
+    for _ in range(20):
+        step.replay()
+    torch.cuda.synchronize()
+    assert np.isfinite(step.total_loss()) and step.total_loss() < loss1
+    assert not torch.equal(step.p["sh"], sh0)
