@@ -9,10 +9,11 @@ Pieces and the passages they follow:
 * ``project``            Eq. 2-3 (EWA covariance projection; C file ``sg_oracle.c``).
 * ``render``             Eq. 7-9 brute-force compositing per pixel (C).
 * ``render_backward``    hand-derived adjoint of Eq. 7-9 and Eq. 2-3 (Sec. III-D) (C).
-* ``sh_basis``,          view-dependent colour of Sec. III-B: rgb + sum of real spherical
-  ``view_colours``       harmonics of degree 1..3 of the camera-to-mean direction (numpy);
-                         ``render`` and ``render_backward`` take it, and its adjoint to the SH
-                         coefficients, rgb and the mean, when the parameters carry ``sh``.
+* ``sh_basis``,          view-dependent colour and semantic feature of Sec. III-B: rgb (sem)
+  ``view_colours``,      + sum of real spherical harmonics of degree 1..3 of the
+  ``view_semantics``     camera-to-mean direction (numpy); ``render`` and ``render_backward``
+                         take them, and their adjoint to the SH coefficients, rgb, sem and the
+                         mean, when the parameters carry ``sh`` and/or ``sem_sh``.
 * ``ssim``               SSIM of Wang et al. 2004 used by Eq. 10 and 12 (C).
 * ``level_cameras``,     Eq. 4-6 image pyramid: 2x2 box mean for RGB, valid-only mean for
   ``build_pyramid``      depth, 2x2 majority for labels; per-level intrinsics keep pixel
@@ -194,32 +195,51 @@ def sh_basis_grad(d, degree):
 
 
 def sh_degree_of(g):
-    """SH degree D of a parameter dict (g["sh"]: N x ((D+1)^2 - 1) x 3), 0 without "sh"."""
-    sh = g.get("sh")
-    if sh is None or np.asarray(sh).shape[1] == 0:
+    """SH degree D of a parameter dict: g["sh"] is N x ((D+1)^2 - 1) x 3 (colour) and/or
+    g["sem_sh"] is N x ((D+1)^2 - 1) x C (semantic feature), one D for both; 0 without them."""
+    Ks = {np.asarray(g[k]).shape[1] for k in ("sh", "sem_sh") if g.get(k) is not None}
+    Ks.discard(0)
+    if not Ks:
         return 0
-    K = np.asarray(sh).shape[1]
+    assert len(Ks) == 1, "sh and sem_sh must have the same degree"
+    K = Ks.pop()
     D = int(round(np.sqrt(K + 1))) - 1
     assert (D + 1) ** 2 - 1 == K and 1 <= D <= 3, K
     return D
 
 
-def view_colours(g, cam):
-    """Colour of every Gaussian seen from cam: rgb + sum_k sh_k Y_k(d), d the unit direction
-    from the camera centre c = -R_cw^T t_cw to the mean (no offset, no clamp: degree 0 is
-    rgb itself).  Returns (colour (N, 3), d (N, 3), |mean - c| (N,), Y (N, K))."""
+def view_basis(g, cam):
+    """Unit directions d from the camera centre c = -R_cw^T t_cw to the means, |mean - c| and
+    the basis Y_k(d) (N, K); all None when the parameters carry no SH."""
     D = sh_degree_of(g)
-    rgb = np.asarray(g["rgb"], np.float64)
     if D == 0:
-        return rgb, None, None, None
+        return None, None, None
     R = np.asarray(cam["R_cw"], np.float64).reshape(3, 3)
     c = -R.T @ np.asarray(cam["t_cw"], np.float64).reshape(3)
     v = np.asarray(g["mean"], np.float64) - c
     n = np.linalg.norm(v, axis=1)
     d = v / n[:, None]
-    Y = sh_basis(d, D)
-    sh = np.asarray(g["sh"], np.float64)
-    return rgb + np.einsum("nk,nkc->nc", Y, sh), d, n, Y
+    return d, n, sh_basis(d, D)
+
+
+def view_colours(g, cam):
+    """Colour of every Gaussian seen from cam: rgb + sum_k sh_k Y_k(d) (no offset, no clamp:
+    degree 0 is rgb itself).  Returns (colour (N, 3), d (N, 3), |mean - c| (N,), Y (N, K))."""
+    rgb = np.asarray(g["rgb"], np.float64)
+    d, n, Y = view_basis(g, cam)
+    if Y is None or g.get("sh") is None:
+        return rgb, d, n, Y
+    return rgb + np.einsum("nk,nkc->nc", Y, np.asarray(g["sh"], np.float64)), d, n, Y
+
+
+def view_semantics(g, cam):
+    """Semantic feature of every Gaussian seen from cam: sem + sum_k sem_sh_k Y_k(d), the same
+    view dependence as the colour; sem itself without sem_sh."""
+    sem = np.asarray(g["sem"], np.float64).reshape(np.asarray(g["mean"]).shape[0], -1)
+    if g.get("sem_sh") is None:
+        return sem
+    Y = view_basis(g, cam)[2]
+    return sem + np.einsum("nk,nkc->nc", Y, np.asarray(g["sem_sh"], np.float64))
 
 
 def render(g, cam, cfg=None, pixels=None, tol=1e-3):
@@ -236,7 +256,7 @@ def render(g, cam, cfg=None, pixels=None, tol=1e-3):
     N = proj.shape[0]
     C = g["sem"].shape[1]
     colour = view_colours(g, cam)[0]
-    pr, ppr = _d(proj); rgb, prgb = _d(colour); sem, psem = _d(g["sem"].reshape(N, C))
+    pr, ppr = _d(proj); rgb, prgb = _d(colour); sem, psem = _d(view_semantics(g, cam))
     c, pc = _d(pack_camera(cam)); f, pf = _d(pack_cfg(cfg))
     if pixels is None:
         n = cam["W"] * cam["H"]
@@ -269,7 +289,7 @@ def render_backward(g, cam, g_rgb, g_depth, g_sem, cfg=None, pixels=None):
     C = g["sem"].shape[1]
     colour, sh_d, sh_n, sh_Y = view_colours(g, cam)
     m, pm = _d(g["mean"]); s, ps = _d(g["log_scale"]); q, pq = _d(g["quat"])
-    pr, ppr = _d(proj); rgb, prgb = _d(colour); sem, psem = _d(g["sem"].reshape(N, C))
+    pr, ppr = _d(proj); rgb, prgb = _d(colour); sem, psem = _d(view_semantics(g, cam))
     c, pc = _d(pack_camera(cam)); f, pf = _d(pack_cfg(cfg))
     if pixels is None:
         n = cam["W"] * cam["H"]
@@ -287,11 +307,14 @@ def render_backward(g, cam, g_rgb, g_depth, g_sem, cfg=None, pixels=None):
                            P_(out["mean"]), P_(out["log_scale"]), P_(out["quat"]),
                            P_(out["opacity_logit"]), P_(out["rgb"]), P_(out["sem"]), P_(out["g2d"]))
     if sh_Y is not None:
-        # colour = rgb + sum_k sh_k Y_k(d): dL/dsh_k = Y_k dL/dcolour; dL/drgb = dL/dcolour (as
-        # computed); dL/dmean += (I - d d^T) / |v| * sum_k (sh_k . dL/dcolour) grad Y_k(d)
-        gcol = out["rgb"]
-        out["sh"] = np.einsum("nk,nc->nkc", sh_Y, gcol)
-        w = np.einsum("nkc,nc->nk", np.asarray(g["sh"], np.float64), gcol)
+        # f = f0 + sum_k coef_k Y_k(d) for the colour (rgb, sh) and the semantic feature
+        # (sem, sem_sh): dL/dcoef_k = Y_k dL/df; dL/df0 = dL/df (as computed);
+        # dL/dmean += (I - d d^T) / |v| * sum_k (coef_k . dL/df) grad Y_k(d)
+        w = np.zeros_like(sh_Y)
+        for key, gf in (("sh", out["rgb"]), ("sem_sh", out["sem"])):
+            if g.get(key) is not None:
+                out[key] = np.einsum("nk,nc->nkc", sh_Y, gf)
+                w += np.einsum("nkc,nc->nk", np.asarray(g[key], np.float64), gf)
         gdir = np.einsum("nk,nkj->nj", w, sh_basis_grad(sh_d, sh_degree_of(g)))
         gdir -= sh_d * (gdir * sh_d).sum(1, keepdims=True)
         out["mean"] += gdir / sh_n[:, None]

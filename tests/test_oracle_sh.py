@@ -103,12 +103,16 @@ def test_zero_sh_is_degree_zero():
         np.testing.assert_allclose(b0[k], b1[k], rtol=1e-12, atol=1e-12)
 
 
-@pytest.mark.parametrize("degree", [1, 3])
-def test_sh_adjoint_matches_fd(degree):
+@pytest.mark.parametrize("degree, keys", [(1, ("sh",)), (3, ("sh",)), (2, ("sem_sh",)), (2, ("sh", "sem_sh"))])
+def test_sh_adjoint_matches_fd(degree, keys):
     from test_oracle_backward import tiny_scene
     g = tiny_scene(n=8, seed=11)
     K = (degree + 1) ** 2 - 1
-    g["sh"] = np.random.default_rng(4).normal(size=(8, K, 3)) * 0.4
+    rng4 = np.random.default_rng(4)
+    if "sh" in keys:
+        g["sh"] = rng4.normal(size=(8, K, 3)) * 0.4
+    if "sem_sh" in keys:
+        g["sem_sh"] = rng4.normal(size=(8, K, g["sem"].shape[1])) * 0.4
     # a camera off the origin, so that the centre enters the view direction
     cam = synthetic.make_camera(40, 32, 40, 40, 20, 16)
     cam = dict(cam, t_cw=np.array([0.05, -0.03, 0.1]))
@@ -122,7 +126,7 @@ def test_sh_adjoint_matches_fd(degree):
 
     an = oracle.render_backward(g, cam, *up, cfg=cfg)
     h = 1e-5
-    for key in ("sh", "rgb", "mean"):
+    for key in keys + ("rgb", "sem", "mean"):
         for ix in np.ndindex(g[key].shape):
             gp = {k: v.copy() for k, v in g.items()}
             gm = {k: v.copy() for k, v in g.items()}
@@ -130,3 +134,20 @@ def test_sh_adjoint_matches_fd(degree):
             gm[key][ix] -= h
             fd = (L(gp) - L(gm)) / (2 * h)
             assert abs(fd - an[key][ix]) <= 2e-5 * (abs(fd) + 1e-3), (key, ix, fd, an[key][ix])
+
+
+def test_semantic_sh_view_dependence():
+    """The semantic feature follows the same view dependence as the colour: with sem_sh equal
+    to the colour's coefficients on 3 channels, the two agree channel by channel; zero sem_sh
+    renders exactly the plain semantic feature."""
+    g = {k: np.asarray(v, np.float64) for k, v in synthetic.cloud_scene(40, 4, seed=3).items()}
+    sh = np.random.default_rng(9).normal(size=(40, 8, 3)) * 0.3
+    cam = synthetic.make_camera(64, 48, 60, 60, 32, 24, t_cw=[0.2, 0.0, -0.1])
+    g2 = dict(g, sh=sh, sem_sh=np.concatenate([sh, np.zeros((40, 8, 1))], 2),
+              sem=np.concatenate([g["rgb"], np.zeros((40, 1))], 1))
+    col = oracle.view_colours(g2, cam)[0]
+    sem = oracle.view_semantics(g2, cam)
+    np.testing.assert_allclose(sem[:, :3], col, atol=1e-14)
+    r0 = oracle.render(g, cam)
+    r1 = oracle.render(dict(g, sem_sh=np.zeros((40, 3, 4))), cam)
+    np.testing.assert_array_equal(r0["sem"], r1["sem"])
