@@ -91,9 +91,13 @@ typedef struct {
      * d = (mean_i - c) / |mean_i - c| and Y_k are the real spherical harmonics of degree
      * 1..D in the usual graphics order (m = -l..l within a degree, Condon-Shortley signs;
      * Y_1 = -sqrt(3/4pi) y, sqrt(3/4pi) z, -sqrt(3/4pi) x).  The constant term is rgb
-     * itself (no offset, no clamp).  sh_degree 0: sh is unused (may be NULL).        */
+     * itself (no offset, no clamp).  The semantic feature takes the same view dependence
+     * when sem_sh is given: sem_i + sum_k sem_sh[i][k][:] Y_k(d).  With sh_degree > 0 at
+     * least one of sh and sem_sh is non-NULL; a NULL one leaves that feature view-
+     * independent.  sh_degree 0: both are unused (may be NULL).                     */
     const float *sh;            /* N x ((D+1)^2 - 1) x 3                  */
     int32_t sh_degree;          /* D in 0..3                              */
+    const float *sem_sh;        /* N x ((D+1)^2 - 1) x C, 16-byte aligned */
 } sg_gaussians;
 
 /* Gradients with respect to every Gaussian parameter; same layouts as sg_gaussians.
@@ -104,6 +108,7 @@ typedef struct {
     int32_t N, C;
     float *sh;
     int32_t sh_degree;
+    float *sem_sh; /* 16-byte aligned, as is sem when sem_sh is given */
 } sg_gaussian_grads;
 
 /* Rendering constants (3D Gaussian splatting conventions, Sec. III-C) and launch shape. */
@@ -141,9 +146,11 @@ typedef struct {
     float *ext;     /* R x 2: half extents (pixels) of the region where alpha can reach
                        alpha_min, with margin (8-B aligned)                             */
     float *rgb;     /* R x 3: colour of each record seen from its view-level, written by
-                       the projection when sh_degree > 0 and read by the compositing
-                       kernels in place of the Gaussian's rgb (may be NULL otherwise);
-                       entries of culled records are left unwritten                    */
+                       the projection when the Gaussians carry sh and read by the
+                       compositing kernels in place of the Gaussian's rgb (may be NULL
+                       otherwise); entries of culled records are left unwritten       */
+    float *sem;     /* R x C (16-B aligned): the same for the semantic feature when the
+                       Gaussians carry sem_sh                                           */
 } sg_projected;
 
 /* Per-tile depth-sorted instance lists (the set N of Eq. 7-9, restricted to a tile). */
@@ -222,8 +229,9 @@ sg_status sg_make_views(const sg_camera *cams, int32_t n_cams, int32_t levels, i
 
 /* Eq. 2-3 generalised by the EWA covariance projection: for every view-level and every
  * Gaussian writes the 2D mean, depth, opacity, conic and the tile rectangle covering every
- * pixel where alpha can reach alpha_min; with g->sh_degree > 0 also the view-dependent
- * colour of every visible record into out->rgb (required then).  views: device array of
+ * pixel where alpha can reach alpha_min; with spherical-harmonic features also the
+ * view-dependent colour (semantic feature) of every visible record into out->rgb (out->sem),
+ * required when g->sh (g->sem_sh) is given.  views: device array of
  * n_views sg_view. */
 sg_status sg_project_gaussians(const sg_gaussians *g, const sg_view *views, int32_t n_views,
                                const sg_config *cfg, sg_projected *out, sg_stream_t stream);
@@ -291,11 +299,12 @@ sg_status sg_pyramid_loss_noalloc(const sg_images *rendered, const sg_targets *g
 /* Backward path                                                                        */
 /* ---------------------------------------------------------------------------------- */
 
-/* Scratch bytes sg_render_pyramid_backward needs: 12 floats per record (8 for the 2D
- * gradients, then a block of 4 per record for the view-dependent colour gradients).  Zero the
- * workspace once after allocating it; every backward leaves it zero (see
+/* Scratch bytes sg_render_pyramid_backward needs: 12 + sem_channels floats per record, in
+ * three blocks: R x 8 2D gradients, R x 4 view-dependent colour gradients, R x sem_channels
+ * view-dependent semantic gradients.  sem_channels = C when the Gaussians carry sem_sh,
+ * else 0.  Zero the workspace once after allocating it; every backward leaves it zero (see
  * sg_render_pyramid_backward_raster below). */
-size_t sg_backward_workspace_size(int64_t n_records);
+size_t sg_backward_workspace_size(int64_t n_records, int32_t sem_channels);
 
 /* Adjoint of sg_render_pyramid followed by the adjoint of sg_project_gaussians (Sec. III-D
  * backpropagation): back-to-front per tile from each pixel's saved `last`, warp-level
@@ -312,13 +321,13 @@ sg_status sg_render_pyramid_backward(const sg_gaussians *g, const sg_projected *
 /* The two halves of sg_render_pyramid_backward, for callers that time or schedule them
  * apart (same arguments, same workspace):
  *   sg_render_pyramid_backward_raster: the compositing adjoint.  ADDS dL/d(2D mean, conic,
- *     opacity, depth) per record into the workspace (8 floats per record) and dL/dsem into
- *     grads; dL/drgb goes into grads when sh_degree is 0, else dL/d(record colour) into the
- *     workspace's colour block (4 floats per record, after the R x 8 block).
+ *     opacity, depth) per record into the workspace's first block; dL/drgb and dL/dsem go
+ *     into grads, except that with sh (sem_sh) the gradient of the record's colour
+ *     (semantic feature) goes into the workspace's colour (semantic) block instead.
  *   sg_project_gaussians_backward: the chain rule through the EWA projection from those
  *     per-record gradients; ADDS dL/d{mean, log_scale, quat, opacity_logit} into grads (with
- *     SH also dL/d{sh, rgb} and the view direction's share of dL/dmean) and zeroes the
- *     per-record slots it consumed.
+ *     SH also dL/d{sh, rgb} and/or dL/d{sem_sh, sem} and the view direction's share of
+ *     dL/dmean) and zeroes the per-record slots it consumed.
  * The workspace must be all zero when the compositing adjoint starts: zero it once after
  * allocating it; each projection adjoint then leaves it zero again (only records visible in
  * some view-level are ever written, and those are the ones it consumes).  Calling both in

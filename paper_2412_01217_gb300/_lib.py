@@ -28,7 +28,8 @@ class SgView(C.Structure):
 
 class SgGaussians(C.Structure):
     _fields_ = [("mean", c_p), ("log_scale", c_p), ("quat", c_p), ("opacity_logit", c_p),
-                ("rgb", c_p), ("sem", c_p), ("N", c_i), ("C", c_i), ("sh", c_p), ("sh_degree", c_i)]
+                ("rgb", c_p), ("sem", c_p), ("N", c_i), ("C", c_i), ("sh", c_p), ("sh_degree", c_i),
+                ("sem_sh", c_p)]
 
 
 SgGaussianGrads = SgGaussians  # same layout (non-const pointers)
@@ -42,7 +43,7 @@ class SgConfig(C.Structure):
 
 
 class SgProjected(C.Structure):
-    _fields_ = [("geo", c_p), ("rect", c_p), ("ext", c_p), ("rgb", c_p)]
+    _fields_ = [("geo", c_p), ("rect", c_p), ("ext", c_p), ("rgb", c_p), ("sem", c_p)]
 
 
 class SgTileLists(C.Structure):
@@ -110,7 +111,7 @@ SIGNATURES = {
                               P(SgLossConfig), c_p, P(SgImages), c_p, C.c_size_t, c_p]),
     "sg_pyramid_loss_noalloc": (c_i, [P(SgImages), P(SgTargets), c_p, P(SgView), c_i, c_i,
                                       P(SgLossConfig), c_p, P(SgImages), c_p]),
-    "sg_backward_workspace_size": (C.c_size_t, [C.c_int64]),
+    "sg_backward_workspace_size": (C.c_size_t, [C.c_int64, c_i]),
     "sg_render_pyramid_backward": (c_i, [P(SgGaussians), P(SgProjected), P(SgTileLists), c_p, c_i,
                                          c_i, P(SgConfig), P(SgSaved), P(SgImages),
                                          P(SgGaussianGrads), c_p, C.c_size_t, c_p, c_p]),

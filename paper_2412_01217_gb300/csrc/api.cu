@@ -69,14 +69,21 @@ static sg_status check_gaussians(const sg_gaussians *g) {
     SG_REQUIRE(g->mean && g->log_scale && g->quat && g->opacity_logit && g->rgb && g->sem,
                "a Gaussian parameter pointer is NULL");
     SG_REQUIRE(aligned16(g->quat) && aligned16(g->sem), "quat and sem must be 16-byte aligned");
-    SG_REQUIRE(g->sh_degree == 0 || g->sh, "sh_degree = %d needs sh coefficients", g->sh_degree);
+    SG_REQUIRE(g->sh_degree == 0 || g->sh || g->sem_sh, "sh_degree = %d needs sh and/or sem_sh",
+               g->sh_degree);
+    SG_REQUIRE(!g->sem_sh || aligned16(g->sem_sh), "sem_sh must be 16-byte aligned");
     return SG_OK;
 }
 
-// With spherical-harmonic colour the compositing kernels read the per-record colour the
-// projection wrote.
+static bool sh_colour(const sg_gaussians *g) { return g->sh_degree > 0 && g->sh; }
+static bool sh_semantic(const sg_gaussians *g) { return g->sh_degree > 0 && g->sem_sh; }
+
+// With spherical-harmonic features the compositing kernels read the per-record colour and
+// semantic feature the projection wrote.
 static sg_status check_record_colour(const sg_gaussians *g, const sg_projected *proj) {
-    SG_REQUIRE(g->sh_degree == 0 || proj->rgb, "sh_degree = %d needs projected->rgb", g->sh_degree);
+    SG_REQUIRE(!sh_colour(g) || proj->rgb, "sh colour needs projected->rgb");
+    SG_REQUIRE(!sh_semantic(g) || (proj->sem && aligned16(proj->sem)),
+               "sem_sh needs a 16-byte aligned projected->sem");
     return SG_OK;
 }
 
@@ -286,8 +293,9 @@ sg_status sg_pyramid_loss(const sg_images *rendered, const sg_targets *gt, const
                        workspace_bytes, (cudaStream_t)stream);
 }
 
-size_t sg_backward_workspace_size(int64_t n_records) {
-    return (size_t)n_records * 12 * sizeof(float);
+size_t sg_backward_workspace_size(int64_t n_records, int32_t sem_channels) {
+    if (n_records < 0 || sem_channels < 0) return 0;
+    return (size_t)n_records * (12 + (size_t)sem_channels) * sizeof(float);
 }
 
 static sg_status check_backward(const sg_gaussians *g, const sg_view *views, int32_t n_views, const sg_config *cfg,
@@ -299,11 +307,13 @@ static sg_status check_backward(const sg_gaussians *g, const sg_view *views, int
     SG_REQUIRE(grads->mean && grads->log_scale && grads->quat && grads->opacity_logit && grads->rgb &&
                    grads->sem, "gradient buffers are NULL");
     SG_REQUIRE(grads->N == g->N && grads->C == g->C, "grads shape differs from gaussians");
-    SG_REQUIRE(grads->sh_degree == g->sh_degree && (g->sh_degree == 0 || grads->sh),
-               "grads sh_degree %d differs from gaussians' %d or its sh is NULL", grads->sh_degree,
-               g->sh_degree);
+    SG_REQUIRE(grads->sh_degree == g->sh_degree, "grads sh_degree %d differs from gaussians' %d",
+               grads->sh_degree, g->sh_degree);
+    SG_REQUIRE(!sh_colour(g) || grads->sh, "grads->sh is NULL");
+    SG_REQUIRE(!sh_semantic(g) || (grads->sem_sh && aligned16(grads->sem_sh) && aligned16(grads->sem)),
+               "grads->sem_sh is NULL, or it or grads->sem is not 16-byte aligned");
     SG_REQUIRE(aligned16(workspace), "workspace must be 16-byte aligned");
-    const size_t need = sg_backward_workspace_size((int64_t)g->N * n_views);
+    const size_t need = sg_backward_workspace_size((int64_t)g->N * n_views, sh_semantic(g) ? g->C : 0);
     if (workspace_bytes < need) {
         set_error("render_pyramid_backward: workspace %zu bytes < %zu needed", workspace_bytes, need);
         return SG_ERR_CAPACITY;
@@ -333,16 +343,18 @@ sg_status sg_render_pyramid_backward_raster(const sg_gaussians *g, const sg_proj
     a.dL_depth = dL->depth;
     a.dL_sem = dL->sem;
     a.g2d = g2d;
-    if (g->sh_degree > 0) {
+    const size_t R = (size_t)g->N * n_views;
+    if (sh_colour(g)) {
         // per-record colour gradients in the workspace's colour block (4 floats per record)
-        a.g_col = g2d + 8 * (size_t)g->N * n_views;
+        a.g_col = g2d + 8 * R;
         a.col_stride = 4;
     } else {
         a.g_col = grads->rgb;
         a.col_stride = 3;
     }
-    a.g_sem = grads->sem;
-    a.sem_v2 = ((uintptr_t)grads->sem % 8) == 0 && (g->C % 2) == 0;
+    // with sem_sh, per-record semantic gradients in the workspace's semantic block
+    a.g_sem = sh_semantic(g) ? g2d + 12 * R : grads->sem;
+    a.sem_v2 = ((uintptr_t)a.g_sem % 8) == 0 && (g->C % 2) == 0;
     a.ppt = cfg->pixels_per_thread_bwd;
     if (cfg->batch_bwd) a.batch = cfg->batch_bwd;
     return launch_raster(a, g->C, true, st);

@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     const float4 *__restrict__ quat, const float *__restrict__ ologit, int N,
     const sg_view *__restrict__ views, int n_views, ProjConsts pc, float4 *__restrict__ geo,
     uint2 *__restrict__ rect, float2 *__restrict__ ext, const float *__restrict__ rgb,
-    const float *__restrict__ sh, float *__restrict__ rec_rgb) {
+    const float *__restrict__ sh, float *__restrict__ rec_rgb, int C, const float *__restrict__ sem,
+    const float *__restrict__ sem_sh, float *__restrict__ rec_sem) {
     constexpr int K = (D + 1) * (D + 1) - 1;
     pdl_begin();
     __shared__ sg_view s_views[SG_MAX_VIEWS];
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     gaussian_frame(log_scale, quat[g], g, f);
     const float o = 1.f / (1.f + expf(-ologit[g]));
     float shv[3 * K + 1], c0[3];
-    if constexpr (D > 0) {
+    if (D > 0 && sh) {
         for (int i = 0; i < 3 * K; ++i) shv[i] = sh[(size_t)3 * K * g + i];
         for (int c = 0; c < 3; ++c) c0[c] = rgb[3 * g + c];
     }
@@ -298,17 +299,38 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
                     g1 = make_float4(m00, m10, m11, __uint_as_float(packed));
                     e2 = make_float2(ex, ey);
                     if constexpr (D > 0) {
-                        // colour = rgb + sum_k sh_k Y_k(d), d = (mu - c) / |mu - c|
+                        // colour = rgb + sum_k sh_k Y_k(d), d = (mu - c) / |mu - c|; the same
+                        // for the semantic feature with sem_sh
                         const float3 cc = s_centre[v];
                         const float dx = mu[0] - cc.x, dy = mu[1] - cc.y, dz = mu[2] - cc.z;
                         const float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
                         float Y[K];
                         sh_eval<D>(dx * rn, dy * rn, dz * rn, Y);
-                        for (int c = 0; c < 3; ++c) {
-                            float col = c0[c];
+                        if (sh) {
+                            for (int c = 0; c < 3; ++c) {
+                                float col = c0[c];
 #pragma unroll
-                            for (int k = 0; k < K; ++k) col = fmaf(Y[k], shv[3 * k + c], col);
-                            rec_rgb[3 * r + c] = col;
+                                for (int k = 0; k < K; ++k) col = fmaf(Y[k], shv[3 * k + c], col);
+                                rec_rgb[3 * r + c] = col;
+                            }
+                        }
+                        if (sem_sh) {
+                            const int C4 = C / 4;
+                            const float4 *s0 = reinterpret_cast<const float4 *>(sem + (size_t)C * g);
+                            const float4 *ss = reinterpret_cast<const float4 *>(sem_sh + (size_t)K * C * g);
+                            float4 *so = reinterpret_cast<float4 *>(rec_sem + (size_t)C * r);
+                            for (int c4 = 0; c4 < C4; ++c4) {
+                                float4 acc = s0[c4];
+#pragma unroll
+                                for (int k = 0; k < K; ++k) {
+                                    const float4 t = ss[k * C4 + c4];
+                                    acc.x = fmaf(Y[k], t.x, acc.x);
+                                    acc.y = fmaf(Y[k], t.y, acc.y);
+                                    acc.z = fmaf(Y[k], t.z, acc.z);
+                                    acc.w = fmaf(Y[k], t.w, acc.w);
+                                }
+                                so[c4] = acc;
+                            }
                         }
                     }
                 }
@@ -322,7 +344,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
 }
 
 // Adjoint.  g2d: per record (u, v, conic a, conic b, conic c, opacity, depth, 0); with SH,
-// gcol: per record dL/d(colour) (r, g, b, 0).
+// gcol: per record dL/d(colour) (r, g, b, 0) and gsem_rec: per record dL/d(semantic feature).
 template <int D>
 __global__ void __launch_bounds__(256) project_bwd_kernel(
     const float *__restrict__ mean, const float *__restrict__ log_scale,
@@ -330,7 +352,9 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     const sg_view *__restrict__ views, int n_views, ProjConsts pc,
     const uint2 *__restrict__ rect, float4 *__restrict__ g2d, float *__restrict__ g_mean, float *__restrict__ g_ls,
     float *__restrict__ g_quat, float *__restrict__ g_ologit, const float *__restrict__ sh,
-    float4 *__restrict__ gcol, float *__restrict__ g_rgb, float *__restrict__ g_sh) {
+    float4 *__restrict__ gcol, float *__restrict__ g_rgb, float *__restrict__ g_sh, int C,
+    const float *__restrict__ sem_sh, float4 *__restrict__ gsem_rec, float *__restrict__ g_sem,
+    float *__restrict__ g_sem_sh) {
     constexpr int K = (D + 1) * (D + 1) - 1;
     pdl_begin();
     __shared__ sg_view s_views[SG_MAX_VIEWS];
@@ -352,7 +376,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     float go_total = 0.f;
     float gls0 = 0.f;  // Eq. 2 mode: dL/dlog_scale[0]
     float shv[3 * K + 1], gsh[3 * K + 1], grgb[3] = {0.f, 0.f, 0.f};
-    if constexpr (D > 0) {
+    if (D > 0 && sh) {
         for (int i = 0; i < 3 * K; ++i) {
             shv[i] = sh[(size_t)3 * K * g + i];
             gsh[i] = 0.f;
@@ -373,7 +397,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
         const size_t r = (size_t)(v0 + __ffs(vis) - 1) * N + g;
         na = g2d[2 * r];
         nb = g2d[2 * r + 1];
-        if constexpr (D > 0) nc = gcol[r];
+        if (D > 0 && sh) nc = gcol[r];
     }
     while (vis) {
         const int v = v0 + __ffs(vis) - 1;
@@ -385,19 +409,20 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
             const size_t r = (size_t)v * N + g;
             g2d[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
             g2d[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if constexpr (D > 0) gcol[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (D > 0 && sh) gcol[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         if (vis) {
             const size_t rn = (size_t)(v0 + __ffs(vis) - 1) * N + g;
             na = g2d[2 * rn];
             nb = g2d[2 * rn + 1];
-            if constexpr (D > 0) nc = gcol[rn];
+            if (D > 0 && sh) nc = gcol[rn];
         }
         const float gu = a.x, gv = a.y, ga = a.z, gb = a.w, gc = b.x, go = b.y, gd = b.z;
         const sg_view &vw = s_views[v];
         if constexpr (D > 0) {
-            // colour = rgb + sum_k sh_k Y_k(d): dL/dsh_k += Y_k dL/dcolour, dL/drgb += dL/dcolour,
-            // dL/dmu += (I - d d^T) / |mu - c| sum_k (sh_k . dL/dcolour) grad Y_k(d)
+            // feature f = f0 + sum_k coef_k Y_k(d) (colour: rgb, sh; semantic: sem, sem_sh):
+            // dL/dcoef_k += Y_k dL/df, dL/df0 += dL/df,
+            // dL/dmu += (I - d d^T) / |mu - c| sum_k (coef_k . dL/df) grad Y_k(d)
             const float gcv[3] = {cg.x, cg.y, cg.z};
             const float3 cc = s_centre[v];
             const float dx = mu[0] - cc.x, dy = mu[1] - cc.y, dz = mu[2] - cc.z;
@@ -406,15 +431,45 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
             float Y[K], w[K];
             sh_eval<D>(x, y, z, Y);
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                w[k] = 0.f;
+            for (int k = 0; k < K; ++k) w[k] = 0.f;
+            if (sh) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    gsh[3 * k + c] = fmaf(Y[k], gcv[c], gsh[3 * k + c]);
-                    w[k] = fmaf(shv[3 * k + c], gcv[c], w[k]);
+                for (int k = 0; k < K; ++k) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        gsh[3 * k + c] = fmaf(Y[k], gcv[c], gsh[3 * k + c]);
+                        w[k] = fmaf(shv[3 * k + c], gcv[c], w[k]);
+                    }
+                }
+                for (int c = 0; c < 3; ++c) grgb[c] += gcv[c];
+            }
+            if (sem_sh) {
+                // this thread owns Gaussian g's rows of g_sem and g_sem_sh: plain read-modify-
+                // write per view; the record's semantic slots are zeroed once read
+                const int C4 = C / 4;
+                const size_t r = (size_t)v * N + g;
+                float4 *gs = reinterpret_cast<float4 *>(g_sem + (size_t)C * g);
+                float4 *gss = reinterpret_cast<float4 *>(g_sem_sh + (size_t)K * C * g);
+                const float4 *ss = reinterpret_cast<const float4 *>(sem_sh + (size_t)K * C * g);
+                for (int c4 = 0; c4 < C4; ++c4) {
+                    const float4 t = gsem_rec[r * C4 + c4];
+                    gsem_rec[r * C4 + c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 a0 = gs[c4];
+                    a0.x += t.x; a0.y += t.y; a0.z += t.z; a0.w += t.w;
+                    gs[c4] = a0;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        float4 u = gss[k * C4 + c4];
+                        u.x = fmaf(Y[k], t.x, u.x);
+                        u.y = fmaf(Y[k], t.y, u.y);
+                        u.z = fmaf(Y[k], t.z, u.z);
+                        u.w = fmaf(Y[k], t.w, u.w);
+                        gss[k * C4 + c4] = u;
+                        const float4 sv = ss[k * C4 + c4];
+                        w[k] += sv.x * t.x + sv.y * t.y + sv.z * t.z + sv.w * t.w;
+                    }
                 }
             }
-            for (int c = 0; c < 3; ++c) grgb[c] += gcv[c];
             float gdir[3];
             sh_grad<D>(x, y, z, w, gdir);
             const float radial = gdir[0] * x + gdir[1] * y + gdir[2] * z;
@@ -531,7 +586,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
         g_ls[3 * g + j] += gls[j];
     }
     g_ologit[g] += go_total * o * (1.f - o);
-    if constexpr (D > 0) {
+    if (D > 0 && sh) {
         for (int c = 0; c < 3; ++c) g_rgb[3 * g + c] += grgb[c];
         for (int i = 0; i < 3 * K; ++i) g_sh[(size_t)3 * K * g + i] += gsh[i];
     }
@@ -550,8 +605,9 @@ sg_status launch_project_fwd(const sg_gaussians *g, const sg_view *views, int n_
         launch_pdl(kern, blocks, threads, 0, st,
             g->mean, g->log_scale, reinterpret_cast<const float4 *>(g->quat), g->opacity_logit,
             g->N, views, n_views, pc, reinterpret_cast<float4 *>(out->geo),
-            reinterpret_cast<uint2 *>(out->rect), reinterpret_cast<float2 *>(out->ext), g->rgb, g->sh,
-            out->rgb);
+            reinterpret_cast<uint2 *>(out->rect), reinterpret_cast<float2 *>(out->ext), g->rgb,
+            g->sh_degree > 0 ? g->sh : nullptr, out->rgb, g->C, g->sem,
+            g->sh_degree > 0 ? g->sem_sh : nullptr, out->sem);
         count_launches(1);
     }
     return check_launch("project_fwd");
@@ -568,13 +624,16 @@ sg_status launch_project_bwd(const sg_gaussians *g, const sg_view *views, int n_
         auto kern = g->sh_degree == 3 ? project_bwd_kernel<3>
                   : g->sh_degree == 2 ? project_bwd_kernel<2>
                   : g->sh_degree == 1 ? project_bwd_kernel<1> : project_bwd_kernel<0>;
-        // the colour block of the workspace follows the R x 8 floats of 2D gradients
-        float4 *gcol = reinterpret_cast<float4 *>(g2d + 8 * (size_t)g->N * n_views);
+        // workspace blocks: R x 8 2D gradients, R x 4 colour gradients, R x C semantic ones
+        const size_t R = (size_t)g->N * n_views;
+        float4 *gcol = reinterpret_cast<float4 *>(g2d + 8 * R);
+        float4 *gsem = reinterpret_cast<float4 *>(g2d + 12 * R);
         launch_pdl(kern, blocks, threads, 0, st,
             g->mean, g->log_scale, reinterpret_cast<const float4 *>(g->quat), g->opacity_logit,
             g->N, views, n_views, pc, reinterpret_cast<const uint2 *>(proj->rect),
             reinterpret_cast<float4 *>(g2d),
-            gr->mean, gr->log_scale, gr->quat, gr->opacity_logit, g->sh, gcol, gr->rgb, gr->sh);
+            gr->mean, gr->log_scale, gr->quat, gr->opacity_logit, g->sh_degree > 0 ? g->sh : nullptr, gcol,
+            gr->rgb, gr->sh, g->C, g->sh_degree > 0 ? g->sem_sh : nullptr, gsem, gr->sem, gr->sem_sh);
         count_launches(1);
     }
     return check_launch("project_bwd");

@@ -14,7 +14,8 @@ struct RasterArgs {
     const int *order;  // work order of the tiles (null: id order)
     const float *rgb;  // colour: N x 3 per Gaussian, or R x 3 per record when col_rec
     int col_rec;       // 1: colour (and its gradient) indexed by record, else by Gaussian
-    const float *sem;
+    const float *sem;  // semantic feature: N x C per Gaussian, or R x C per record when sem_rec
+    int sem_rec;       // 1: semantic feature (and its gradient) indexed by record
     const sg_view *views;
     int n_views, n_tiles, N;
     float alpha_max, alpha_min, T_min;
@@ -43,9 +44,10 @@ inline void fill_raster_args(RasterArgs &a, const sg_gaussians *g, const sg_proj
     a.record = lists->record;
     a.ranges = reinterpret_cast<const int2 *>(lists->ranges);
     a.order = lists->order;
-    a.col_rec = g->sh_degree > 0;
+    a.col_rec = g->sh_degree > 0 && g->sh;
     a.rgb = a.col_rec ? proj->rgb : g->rgb;
-    a.sem = g->sem;
+    a.sem_rec = g->sh_degree > 0 && g->sem_sh;
+    a.sem = a.sem_rec ? proj->sem : g->sem;
     a.views = views;
     a.n_views = n_views;
     a.n_tiles = n_tiles;

@@ -59,7 +59,7 @@ __device__ __forceinline__ void load_batch(const RasterArgs &a, int C, int list_
         f[1] = a.rgb[3 * ci + 1];
         f[2] = a.rgb[3 * ci + 2];
         f[3] = g0.z;  // depth (camera z of the mean, Eq. 8)
-        const float4 *s4 = reinterpret_cast<const float4 *>(a.sem + (size_t)gi * C);
+        const float4 *s4 = reinterpret_cast<const float4 *>(a.sem + (size_t)(a.sem_rec ? rec : gi) * C);
         float4 *f4 = reinterpret_cast<float4 *>(f + 4);
 #pragma unroll
         for (int k = 0; k < (NF - 4) / 4; ++k) f4[k] = s4[k];
@@ -500,13 +500,14 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
                     if (!(hr ? keep1 : keep0)) continue;
                     const uint32_t rec = s_rec[jc0 + gid + 8 * hr];
                     const uint32_t gi = rec - rec_base;
+                    const size_t si = (size_t)C * (a.sem_rec ? rec : gi);
 #pragma unroll
                     for (int nt = 0; nt < NT; ++nt) {
                         // features 2 tig, 2 tig + 1 of this n-tile: both semantic (C even) ->
                         // one 8-byte vector reduction when the buffer allows it
                         const int f0 = 8 * nt + 2 * tig;
                         if (a.sem_v2 && f0 >= 4 && f0 + 1 < NF) {
-                            red_add_v2(a.g_sem + (size_t)C * gi + (f0 - 4), df[nt][2 * hr], df[nt][2 * hr + 1]);
+                            red_add_v2(a.g_sem + si + (f0 - 4), df[nt][2 * hr], df[nt][2 * hr + 1]);
                             continue;
                         }
 #pragma unroll
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
                             else if (f == 3)
                                 atomicAdd(a.g2d + 8 * (size_t)rec + 6, val);
                             else
-                                atomicAdd(a.g_sem + (size_t)C * gi + (f - 4), val);
+                                atomicAdd(a.g_sem + si + (f - 4), val);
                         }
                     }
                 }

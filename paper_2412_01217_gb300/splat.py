@@ -19,22 +19,28 @@ from ._lib import (SgCamera, SgConfig, SgGaussians, SgImages, SgLossConfig, SgPr
 PARAM_KEYS = ("mean", "log_scale", "quat", "opacity_logit", "rgb", "sem")
 
 
+SH_KEYS = ("sh", "sem_sh")
+
+
 def sh_degree(g):
-    """Degree D of the spherical-harmonic colour of a parameter dict: g["sh"] is
-    N x ((D+1)^2 - 1) x 3; 0 without it."""
-    sh = g.get("sh")
-    if sh is None or sh.shape[1] == 0:
+    """Degree D of the spherical-harmonic features of a parameter dict: g["sh"] is
+    N x ((D+1)^2 - 1) x 3 (colour), g["sem_sh"] N x ((D+1)^2 - 1) x C (semantic feature);
+    one D for both, 0 without them."""
+    Ks = {g[k].shape[1] for k in SH_KEYS if g.get(k) is not None and g[k].shape[1]}
+    if not Ks:
         return 0
-    K = sh.shape[1]
+    if len(Ks) > 1:
+        raise ValueError("sh and sem_sh must have the same degree")
+    K = Ks.pop()
     D = {3: 1, 8: 2, 15: 3}.get(K)
     if D is None:
-        raise ValueError(f"sh has {K} coefficients per channel; expected 3, 8 or 15")
+        raise ValueError(f"{K} SH coefficients per channel; expected 3, 8 or 15")
     return D
 
 
 def param_keys(g):
-    """PARAM_KEYS, plus "sh" when the parameters carry spherical-harmonic colour."""
-    return PARAM_KEYS + (("sh",) if sh_degree(g) else ())
+    """PARAM_KEYS, plus "sh" / "sem_sh" when the parameters carry them."""
+    return PARAM_KEYS + tuple(k for k in SH_KEYS if g.get(k) is not None and g[k].shape[1])
 
 
 def _ptr(t):
@@ -141,15 +147,20 @@ def gaussians_struct(g, N=None, C_=None):
     s.C = g["sem"].shape[1] if C_ is None else C_
     D = sh_degree(g)
     if D:
-        s.sh, s.sh_degree = g["sh"].data_ptr(), D
+        s.sh_degree = D
+        keys = param_keys(g)
+        if "sh" in keys:
+            s.sh = g["sh"].data_ptr()
+        if "sem_sh" in keys:
+            s.sem_sh = g["sem_sh"].data_ptr()
     return s
 
 
 def to_device_params(g, device="cuda"):
     """dict of arrays -> dict of contiguous float32 CUDA tensors (quat/sem 16-B aligned);
-    "sh" (N x K x 3) is carried when present."""
+    "sh" (N x K x 3) and "sem_sh" (N x K x C) are carried when present."""
     out = {}
-    for k in PARAM_KEYS + (("sh",) if g.get("sh") is not None else ()):
+    for k in PARAM_KEYS + tuple(k for k in SH_KEYS if g.get(k) is not None):
         out[k] = torch.as_tensor(np.ascontiguousarray(g[k], dtype=np.float32)).to(device).contiguous()
     return out
 
@@ -163,7 +174,7 @@ class PyramidRasterizer:
     """
 
     def __init__(self, N, C, cams, levels=1, cfg: RenderConfig | None = None, capacity=None,
-                 loss_cfg: LossConfig | None = None, device="cuda", sh_degree=0):
+                 loss_cfg: LossConfig | None = None, device="cuda", sh_degree=0, sem_sh=False):
         require_cuda()
         _lib.load()
         self.N, self.C, self.levels = int(N), int(C), int(levels)
@@ -208,13 +219,15 @@ class PyramidRasterizer:
         self.loss_ws = torch.zeros(lib.sg_loss_workspace_size(self.views_host, self.V, self.C,
                                                               max(self.C, self.loss_cfg.n_classes)),
                                    dtype=torch.uint8, device=dev)
-        self.bwd_ws = torch.zeros(lib.sg_backward_workspace_size(max(1, self.R)), dtype=torch.uint8, device=dev)
+        self.bwd_ws = torch.zeros(lib.sg_backward_workspace_size(max(1, self.R), 0), dtype=torch.uint8, device=dev)
         self._ccfg = self.cfg.to_c()
-        # per-record view-dependent colour (spherical-harmonic colour only)
-        self.rec_rgb = None
-        self._proj = SgProjected(self.geo.data_ptr(), self.rect.data_ptr(), self.ext.data_ptr(), 0)
+        # per-record view-dependent colour / semantic feature (spherical-harmonic features only)
+        self.rec_rgb = self.rec_sem = None
+        self._proj = SgProjected(self.geo.data_ptr(), self.rect.data_ptr(), self.ext.data_ptr(), 0, 0)
         if sh_degree:
             self._alloc_record_colour()
+        if sem_sh:
+            self._alloc_record_semantics()
         self._lists = SgTileLists(self.capacity, self.tile.data_ptr(), self.record.data_ptr(),
                                   self.ranges.data_ptr(), self.count.data_ptr(), self.order.data_ptr())
         self._saved = SgSaved(self.T_final.data_ptr(), self.last.data_ptr(), self.n_contrib.data_ptr())
@@ -223,12 +236,24 @@ class PyramidRasterizer:
         self.rec_rgb = torch.zeros(max(1, self.N_max * self.V) * 3, dtype=torch.float32, device=self.device)
         self._proj.rgb = self.rec_rgb.data_ptr()
 
+    def _alloc_record_semantics(self):
+        R = max(1, self.N_max * self.V)
+        self.rec_sem = torch.zeros(R * self.C, dtype=torch.float32, device=self.device)
+        self._proj.sem = self.rec_sem.data_ptr()
+        # the backward workspace gains its block of C semantic gradients per record
+        self.bwd_ws = torch.zeros(_lib.load().sg_backward_workspace_size(R, self.C), dtype=torch.uint8,
+                                  device=self.device)
+
     def _check_colour(self, g):
-        if sh_degree(g) and self.rec_rgb is None:
-            if torch.cuda.is_current_stream_capturing():
-                raise RuntimeError("spherical-harmonic colour: build the rasterizer with sh_degree > 0 "
-                                   "before capturing a graph")
-            self._alloc_record_colour()
+        keys = param_keys(g)
+        need = [("sh" in keys and self.rec_rgb is None, self._alloc_record_colour),
+                ("sem_sh" in keys and self.rec_sem is None, self._alloc_record_semantics)]
+        for missing, alloc in need:
+            if missing:
+                if torch.cuda.is_current_stream_capturing():
+                    raise RuntimeError("spherical-harmonic features: build the rasterizer with sh_degree > 0 "
+                                       "(and sem_sh=True) before capturing a graph")
+                alloc()
 
     def set_count(self, N):
         """Use the first N <= capacity Gaussians (buffers keep their maximum size)."""
@@ -362,11 +387,13 @@ class PyramidSplat(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, rast, mean, log_scale, quat, opacity_logit, rgb, sem, sh=None):
+    def forward(ctx, rast, mean, log_scale, quat, opacity_logit, rgb, sem, sh=None, sem_sh=None):
         g = dict(mean=mean.contiguous(), log_scale=log_scale.contiguous(), quat=quat.contiguous(),
                  opacity_logit=opacity_logit.contiguous(), rgb=rgb.contiguous(), sem=sem.contiguous())
         if sh is not None:
             g["sh"] = sh.contiguous()
+        if sem_sh is not None:
+            g["sem_sh"] = sem_sh.contiguous()
         out_rgb = torch.empty(3 * rast.P, dtype=torch.float32, device=rast.device)
         out_depth = torch.empty(rast.P, dtype=torch.float32, device=rast.device)
         out_sem = torch.empty(rast.C * rast.P, dtype=torch.float32, device=rast.device)
@@ -383,11 +410,11 @@ class PyramidSplat(torch.autograd.Function):
         grads = {k: torch.zeros_like(v) for k, v in params.items()}
         z = lambda t, n: t.contiguous() if t is not None else torch.zeros(n, dtype=torch.float32, device=rast.device)
         rast.backward(params, grads, dL=(z(d_rgb, 3 * rast.P), z(d_depth, rast.P), z(d_sem, rast.C * rast.P)))
-        return (None, *[grads[k] for k in PARAM_KEYS], grads.get("sh"))
+        return (None, *[grads[k] for k in PARAM_KEYS], grads.get("sh"), grads.get("sem_sh"))
 
 
 def pyramid_splat(rast, g):
-    return PyramidSplat.apply(rast, *[g[k] for k in PARAM_KEYS], g.get("sh"))
+    return PyramidSplat.apply(rast, *[g[k] for k in PARAM_KEYS], g.get("sh"), g.get("sem_sh"))
 
 
 # ------------------------------------------------------------------------------------------
@@ -395,7 +422,7 @@ def pyramid_splat(rast, g):
 # ------------------------------------------------------------------------------------------
 
 DEFAULT_LR = dict(mean=1e-4, log_scale=5e-3, quat=1e-3, opacity_logit=5e-2, rgb=2.5e-3, sem=2.5e-3,
-                  sh=1.25e-4)
+                  sh=1.25e-4, sem_sh=1.25e-4)
 
 
 class MappingStep:

@@ -87,14 +87,14 @@ def cloud_scene(n=2000, n_sem=8, seed=1):
                 opacity_logit=f32(opacity_logit), rgb=f32(rgb), sem=f32(sem))
 
 
-def sh_coefficients(n, degree, scale=0.2, seed=3):
-    """Seeded view-dependent colour coefficients: N x ((D+1)^2 - 1) x 3 float32, the
-    degree-l rows ~ N(0, (scale / l)^2) (higher degrees carry less energy, as fitted SH
-    colour does)."""
+def sh_coefficients(n, degree, scale=0.2, seed=3, channels=3):
+    """Seeded view-dependent feature coefficients: N x ((D+1)^2 - 1) x channels float32
+    (3 for colour, C for the semantic feature), the degree-l rows ~ N(0, (scale / l)^2)
+    (higher degrees carry less energy, as fitted SH colour does)."""
     rng = np.random.default_rng(seed)
     K = (degree + 1) ** 2 - 1
     l = np.floor(np.sqrt(np.arange(1, K + 1))).astype(np.float64)   # degree of row k
-    sh = rng.normal(size=(n, K, 3)) * (scale / l)[None, :, None]
+    sh = rng.normal(size=(n, K, channels)) * (scale / l)[None, :, None]
     return np.ascontiguousarray(sh, dtype=np.float32)
 
 

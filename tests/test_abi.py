@@ -30,7 +30,7 @@ def test_struct_sizes_match_header_layout():
     from paper_2412_01217_gb300 import _lib
     assert C.sizeof(_lib.SgCamera) == 72
     assert C.sizeof(_lib.SgView) == 96
-    assert C.sizeof(_lib.SgGaussians) == 72
+    assert C.sizeof(_lib.SgGaussians) == 80
     assert C.sizeof(_lib.SgConfig) == 68
     assert C.sizeof(_lib.SgLossConfig) == 40
 

@@ -1,6 +1,7 @@
-"""GPU parity of the view-dependent (spherical-harmonic) colour of Sec. III-B against the FP64
-oracle: the projection's per-record colour feeds the compositing kernels, and the adjoint
-chains the per-record colour gradients to the SH coefficients, rgb and the mean.  Same
+"""GPU parity of the view-dependent (spherical-harmonic) colour and semantic feature of
+Sec. III-B against the FP64 oracle: the projection's per-record colour / semantic feature
+feeds the compositing kernels, and the adjoint chains the per-record gradients to the SH
+coefficients, rgb / sem and the mean.  Same
 tolerances as the other parity tests (forward 1e-4 rel + 1e-5 abs, gradients 2e-3 rel +
 1e-5 of the group's largest entry)."""
 import numpy as np
@@ -14,7 +15,8 @@ from test_gpu_parity import f32_camera, oracle_cams, room_small, view_images
 
 pytestmark = pytest.mark.gpu
 
-KEYS = ("mean", "log_scale", "quat", "opacity_logit", "rgb", "sem", "sh")
+BASE = ("mean", "log_scale", "quat", "opacity_logit", "rgb", "sem")
+KEYS = BASE + ("sh",)
 
 
 def make(g, cams, levels=1, **kw):
@@ -22,13 +24,16 @@ def make(g, cams, levels=1, **kw):
     from paper_2412_01217_gb300.splat import sh_degree
     p = to_device_params(g)
     r = PyramidRasterizer(g["mean"].shape[0], g["sem"].shape[1], cams, levels, RenderConfig(**kw),
-                          sh_degree=sh_degree(p))
+                          sh_degree=sh_degree(p), sem_sh="sem_sh" in p)
     return r, p
 
 
-def sh_cloud(degree, n=2000, seed=1):
+def sh_cloud(degree, n=2000, seed=1, colour=True, semantic=False):
     g = synthetic.cloud_scene(n, 8, seed=seed)
-    g["sh"] = synthetic.sh_coefficients(n, degree, seed=seed + 10)
+    if colour:
+        g["sh"] = synthetic.sh_coefficients(n, degree, seed=seed + 10)
+    if semantic:
+        g["sem_sh"] = synthetic.sh_coefficients(n, degree, seed=seed + 20, channels=8, scale=0.5)
     # a camera away from the origin and turned a little, so that the centre -R^T t and the
     # rotation both enter the view directions
     cam = synthetic.cloud_camera()
@@ -61,9 +66,25 @@ def test_sh_forward_matches_oracle(degree):
     assert np.abs(ref0["rgb"] - ref["rgb"]).max() > 0.05
 
 
-@pytest.mark.parametrize("degree, ppt", [(1, 1), (2, 2), (3, 1), (3, 4)])
-def test_sh_backward_matches_oracle(degree, ppt):
-    g, cam = sh_cloud(degree, seed=degree)
+@pytest.mark.parametrize("degree, colour, semantic", [(2, False, True), (3, True, True)])
+def test_semantic_sh_forward_matches_oracle(degree, colour, semantic):
+    g, cam = sh_cloud(degree, seed=5, colour=colour, semantic=semantic)
+    r, p = make(g, [cam])
+    r.forward(p)
+    got = view_images(r, 0, 8)
+    ref = oracle.render(g, cam)
+    amb = (ref["flags"] & AMBIGUOUS) != 0
+    for k in ("rgb", "depth", "sem", "T"):
+        check_close(k, got[k], ref[k], FWD_REL, FWD_ABS, mask=~amb)
+    ref0 = oracle.render({k: v for k, v in g.items() if k != "sem_sh"}, cam)
+    assert np.abs(ref0["sem"] - ref["sem"]).max() > 0.05
+
+
+@pytest.mark.parametrize("degree, ppt, colour, semantic", [(1, 1, True, False), (2, 2, True, False), (3, 1, True, False),
+                                                           (3, 4, True, False), (2, 1, False, True),
+                                                           (1, 2, True, True), (3, 1, True, True)])
+def test_sh_backward_matches_oracle(degree, ppt, colour, semantic):
+    g, cam = sh_cloud(degree, seed=degree, colour=colour, semantic=semantic)
     r, p = make(g, [cam], pixels_per_thread_bwd=ppt)
     r.forward(p)
     ref_f = oracle.render(g, cam)
@@ -75,16 +96,18 @@ def test_sh_backward_matches_oracle(degree, ppt):
     got = {k: v.cpu().numpy() for k, v in grads.items()}
     up32 = [t.cpu().numpy().astype(np.float64).reshape(u.shape) for t, u in zip(dl, up)]
     ref = oracle.render_backward(g, cam, *up32)
-    check_grads(got, ref, KEYS)
-    # both workspace blocks (2D gradients and record colour gradients) are left zero
+    check_grads(got, ref, BASE + tuple(k for k in ("sh", "sem_sh") if k in g))
+    # every workspace block (2D, record colour and record semantic gradients) is left zero
     assert not r.bwd_ws.any() and not r.work_counter.any()
 
 
 def test_sh_multiview_pyramid_matches_oracle():
-    """Two keyframes x three levels with degree-3 colour: every view-level's image and the
-    summed gradients; the levels of one keyframe share its camera centre."""
+    """Two keyframes x three levels with degree-3 colour and semantic feature: every
+    view-level's image and the summed gradients; the levels of one keyframe share its camera
+    centre."""
     room, g, cams = room_small(n=6000, ncam=2, W=160, H=96)
     g["sh"] = synthetic.sh_coefficients(6000, 3, seed=7)
+    g["sem_sh"] = synthetic.sh_coefficients(6000, 3, seed=8, channels=16)
     r, p = make(g, cams, levels=3)
     r.forward(p)
     ocams = oracle_cams(cams, 3)
@@ -104,15 +127,17 @@ def test_sh_multiview_pyramid_matches_oracle():
     grads = {k: torch.zeros_like(t) for k, t in p.items()}
     r.backward(p, grads, dL=tuple(dl))
     got = {k: t.cpu().numpy() for k, t in grads.items()}
-    ref = {k: 0.0 for k in KEYS}
+    keys = KEYS + ("sem_sh",)
+    ref = {k: 0.0 for k in keys}
     for v, oc in enumerate(ocams):
         a = r.view_slice(dl[0], v, 3).cpu().numpy().astype(np.float64)
         b = r.view_slice(dl[1], v, 1)[0].cpu().numpy().astype(np.float64)
         c = r.view_slice(dl[2], v, 16).cpu().numpy().astype(np.float64)
         rv = oracle.render_backward(g, oc, a, b, c)
-        for k in KEYS:
+        for k in keys:
             ref[k] = ref[k] + rv[k]
-    check_grads(got, ref, KEYS)
+    check_grads(got, ref, keys)
+    assert not r.bwd_ws.any()
 
 
 def test_zero_sh_equals_plain_colour_path():
@@ -144,21 +169,22 @@ def test_sh_autograd_and_mapping_step():
     """pyramid_splat returns the SH gradient through autograd, and a captured mapping step
     updates the SH coefficients with their own Adam group."""
     from paper_2412_01217_gb300 import MappingStep, build_pyramid, pyramid_splat
-    g, cam = sh_cloud(3, n=3000, seed=6)
+    g, cam = sh_cloud(3, n=3000, seed=6, semantic=True)
     r, p = make(g, [cam])
     leaf = {k: v.clone().requires_grad_(True) for k, v in p.items()}
     rgb, depth, sem = pyramid_splat(r, leaf)
-    (rgb.square().sum() + 0.1 * depth.sum()).backward()
-    assert leaf["sh"].grad is not None and leaf["sh"].grad.abs().max() > 0
+    (rgb.square().sum() + 0.1 * depth.sum() + sem.square().sum()).backward()
     direct = {k: torch.zeros_like(v) for k, v in p.items()}
     r.forward(p)
-    r.backward(p, direct, dL=(2 * r.img_rgb, torch.full_like(r.img_depth, 0.1), torch.zeros_like(r.img_sem)))
-    assert torch.allclose(leaf["sh"].grad, direct["sh"], rtol=1e-4, atol=1e-6 * float(direct["sh"].abs().max()))
+    r.backward(p, direct, dL=(2 * r.img_rgb, torch.full_like(r.img_depth, 0.1), 2 * r.img_sem))
+    for k in ("sh", "sem_sh"):
+        assert leaf[k].grad is not None and leaf[k].grad.abs().max() > 0
+        assert torch.allclose(leaf[k].grad, direct[k], rtol=1e-4, atol=1e-6 * float(direct[k].abs().max()))
 
     tgt = synthetic.random_targets(cam["H"], cam["W"], 8, seed=3)
     gt = build_pyramid(r, [tgt["rgb"]], [tgt["depth"]], [tgt["label"]])
     step = MappingStep(r, {k: v.clone() for k, v in p.items()}, gt)
-    sh0 = step.p["sh"].clone()
+    sh0, ssh0 = step.p["sh"].clone(), step.p["sem_sh"].clone()
     step.step()
     loss1 = step.total_loss()
     step.capture()
@@ -166,4 +192,4 @@ def test_sh_autograd_and_mapping_step():
         step.replay()
     torch.cuda.synchronize()
     assert np.isfinite(step.total_loss()) and step.total_loss() < loss1
-    assert not torch.equal(step.p["sh"], sh0)
+    assert not torch.equal(step.p["sh"], sh0) and not torch.equal(step.p["sem_sh"], ssh0)
