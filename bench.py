@@ -211,6 +211,14 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout=5.0):
+        """Block until the sampler has printed its first line (NVML is initialised and the
+        sampler is in its steady polling loop), so that its start-up does not overlap the
+        timed steps."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.02)
+
     def stop(self):
         if self.proc is None:
             return None
@@ -425,7 +433,8 @@ def run_ours(args):
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.3)
+    clocks.wait_first()
+    time.sleep(0.2)
     step_ms, fwd_ms, bwd_ms, pre_ms, loss_ms, adam_ms, pbwd_ms = [], [], [], [], [], [], []
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
