@@ -304,13 +304,14 @@ static sg_status check_backward(const sg_gaussians *g, const sg_view *views, int
     SG_TRY(check_cfg(cfg));
     SG_TRY(check_views(views, n_views));
     SG_REQUIRE(grads && workspace, "NULL argument");
-    SG_REQUIRE(grads->mean && grads->log_scale && grads->quat && grads->opacity_logit && grads->rgb &&
-                   grads->sem, "gradient buffers are NULL");
+    SG_REQUIRE(g->N == 0 || (grads->mean && grads->log_scale && grads->quat && grads->opacity_logit &&
+                             grads->rgb && grads->sem),
+               "gradient buffers are NULL");
     SG_REQUIRE(grads->N == g->N && grads->C == g->C, "grads shape differs from gaussians");
     SG_REQUIRE(grads->sh_degree == g->sh_degree, "grads sh_degree %d differs from gaussians' %d",
                grads->sh_degree, g->sh_degree);
-    SG_REQUIRE(!sh_colour(g) || grads->sh, "grads->sh is NULL");
-    SG_REQUIRE(!sh_semantic(g) || (grads->sem_sh && aligned16(grads->sem_sh) && aligned16(grads->sem)),
+    SG_REQUIRE(g->N == 0 || !sh_colour(g) || grads->sh, "grads->sh is NULL");
+    SG_REQUIRE(g->N == 0 || !sh_semantic(g) || (grads->sem_sh && aligned16(grads->sem_sh) && aligned16(grads->sem)),
                "grads->sem_sh is NULL, or it or grads->sem is not 16-byte aligned");
     SG_REQUIRE(aligned16(workspace), "workspace must be 16-byte aligned");
     const size_t need = sg_backward_workspace_size((int64_t)g->N * n_views, sh_semantic(g) ? g->C : 0);

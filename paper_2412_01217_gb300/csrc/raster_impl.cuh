@@ -581,8 +581,10 @@ sg_status launch_raster_cp(RasterArgs &a, bool backward, cudaStream_t st) {
     const int threads = a.tile_w * a.tile_h / PPT;
     const size_t smem = backward ? bwd_smem<C, PPT>(a.batch, threads) : fwd_smem<C>(a.batch);
     const void *fn = backward ? (const void *)raster_bwd_kernel<C, PPT> : (const void *)raster_fwd_kernel<C, PPT>;
+    // opt in to the dynamic size whenever it grows: at 48 KB and just below, the kernel's
+    // static shared variables alone take the total past the default limit
     static size_t configured[2] = {0, 0};
-    if (smem > 48 * 1024 && configured[backward] < smem) {
+    if (configured[backward] < smem) {
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return check_launch("raster smem attribute");
         configured[backward] = smem;

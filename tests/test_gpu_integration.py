@@ -105,9 +105,16 @@ def replica_like():
     return room, g, cam
 
 
-def test_full_size_forward_sampled_pixels(replica_like):
+# the launch configuration bench.py times on this workload (autotuned: 8x8 tiles, forward batch
+# 64, backward batch 16, one pixel per thread in both kernels), and the library default
+BENCH_CFG = dict(tile_w=8, tile_h=8, batch=64, batch_bwd=16, pixels_per_thread=1, pixels_per_thread_bwd=1)
+LAUNCH_CFGS = [pytest.param(BENCH_CFG, id="bench-8x8"), pytest.param(dict(tile_w=16, tile_h=16, batch=128), id="16x16")]
+
+
+@pytest.mark.parametrize("cfg", LAUNCH_CFGS)
+def test_full_size_forward_sampled_pixels(replica_like, cfg):
     room, g, cam = replica_like
-    r, p = make(g, [cam], levels=3, tile_w=16, tile_h=16, batch=128)
+    r, p = make(g, [cam], levels=3, **cfg)
     r.forward(p)
     torch.cuda.synchronize()
     assert int(r.status.item()) == 0
@@ -126,11 +133,12 @@ def test_full_size_forward_sampled_pixels(replica_like):
             check_close(f"level {v} {k}", got[k], ref[k], FWD_REL, FWD_ABS, mask=ok)
 
 
-def test_full_size_backward_sparse_upstream(replica_like):
+@pytest.mark.parametrize("cfg", LAUNCH_CFGS)
+def test_full_size_backward_sparse_upstream(replica_like, cfg):
     """Upstream gradient non-zero only on sampled pixels, so the oracle computes exactly
     the same parameter gradients from those pixels alone."""
     room, g, cam = replica_like
-    r, p = make(g, [cam], levels=3)
+    r, p = make(g, [cam], levels=3, **cfg)
     r.forward(p)
     rng = np.random.default_rng(1)
     ocams = oracle.level_cameras(cam, 3)
