@@ -403,7 +403,41 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
                 uint32_t cmask = __ballot_sync(SG_FULL_MASK, cand);
                 if (!cmask) continue;
                 // ---- gf = G F^T for the chunk (M = pixels, N = entries, K = features) ----
-#pragma unroll(MT <= 2 ? 2 : 1)
+                if constexpr (MT <= 2) {
+                    // features outside, pixel tiles inside: every F fragment is split once
+                    float d[MT][2][4];
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < 2; ++nt) d[mt][nt][0] = d[mt][nt][1] = d[mt][nt][2] = d[mt][nt][3] = 0.f;
+#pragma unroll
+                    for (int kk = 0; kk < NT; ++kk) {
+                        const int f0 = 8 * kk + tig;
+                        uint32_t bh[2][2], bl[2][2];
+#pragma unroll
+                        for (int nt = 0; nt < 2; ++nt) {
+                            const float *fr = s_feat + (size_t)(jc0 + 8 * nt + gid) * NF;
+                            split_tf32(f0 < NF ? fr[f0] : 0.f, bh[nt][0], bl[nt][0]);
+                            split_tf32(f0 + 4 < NF ? fr[f0 + 4] : 0.f, bh[nt][1], bl[nt][1]);
+                        }
+#pragma unroll
+                        for (int mt = 0; mt < MT; ++mt) {
+                            uint32_t ah[4], al[4];
+                            load_a_split(s_G + 16 * mt * GP, GP, 8 * kk, gid, tig, true, true, ah, al);
+#pragma unroll
+                            for (int nt = 0; nt < 2; ++nt)
+                                mma_tf32x3(d[mt][nt], ah, al, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
+                        }
+                    }
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                s_gw[(8 * nt + 2 * tig + (i & 1)) * WQ + 16 * mt + gid + 8 * (i >> 1)] = d[mt][nt][i];
+                } else
+#pragma unroll 1
                 for (int mt = 0; mt < MT; ++mt) {
                     float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
