@@ -243,13 +243,21 @@ def test_pyramid_build_matches_oracle():
             assert np.array_equal(r.view_slice(gt["label"], v, 1)[0].cpu().numpy(), ref[l][2])
 
 
-@pytest.mark.parametrize("mode", ["ce", "ce_decoder", "ce_decoder32", "paper"])
+# (semantic channels, classes, W, H, keyframes, levels) per case; the tensor-core decoder
+# kernel is persistent, so the larger images give its blocks many 256-pixel items each
+LOSS_CASES = {"ce": (8, 8, 100, 70, 2, 2), "ce_decoder": (8, 8, 100, 70, 2, 2),
+              "ce_decoder32": (16, 32, 100, 70, 2, 2), "ce_decoder16_640x480": (16, 16, 640, 480, 1, 2),
+              "ce_decoder32_1200x680": (16, 32, 1200, 680, 1, 3), "ce_decoder32x32_320x240": (32, 32, 320, 240, 2, 2),
+              "paper": (8, 8, 100, 70, 2, 2)}
+
+
+@pytest.mark.parametrize("mode", list(LOSS_CASES))
 def test_loss_matches_oracle(mode):
     from paper_2412_01217_gb300 import LossConfig
     rng = np.random.default_rng(5)
-    Cs, K = (16, 32) if mode == "ce_decoder32" else (8, 8)
-    room, g, cams = room_small(ncam=2, W=100, H=70, C=Cs)
-    r, p = make(g, cams, levels=2)
+    Cs, K, W, H, ncam, levels = LOSS_CASES[mode]
+    room, g, cams = room_small(n=2000, ncam=ncam, W=W, H=H, C=Cs)
+    r, p = make(g, cams, levels=levels)
     P = r.P
     rend = (torch.tensor(rng.uniform(size=3 * P), dtype=torch.float32, device="cuda"),
             torch.tensor(rng.uniform(1, 3, size=P), dtype=torch.float32, device="cuda"),
