@@ -101,6 +101,34 @@ struct WarpTile {
     __device__ __forceinline__ bool misses(const float4 &g2) const {
         return fabsf(g2.x - cxw) > g2.z + 3.5f || fabsf(g2.y - cyw) > g2.w + (2.f * PPT - 0.5f);
     }
+    // The same, exactly for the ellipse: besides the box test, true if the minimum of
+    // sigma = (m00 dx)^2 + (m10 dx + m11 dy)^2 over the rectangle spanned by the sub-tile's
+    // pixel centres exceeds ln(o / alpha_min), so alpha < alpha_min at every pixel of the warp
+    // (g1 = m00, m10, m11, o).  Conservative: the continuous rectangle contains every pixel
+    // centre, and the 1e-3 margin on sigma covers rounding and the fast exponential.
+    __device__ __forceinline__ bool misses(const float4 &g2, const float4 &g1, float ln_alpha_min) const {
+        if (misses(g2)) return true;
+        const float hx = 3.5f, hy = 2.f * PPT - 0.5f;
+        // pixel offsets from the mean: dx in [x0, x1], dy in [y0, y1]
+        const float x0 = cxw - g2.x - hx, x1 = cxw - g2.x + hx;
+        const float y0 = cyw - g2.y - hy, y1 = cyw - g2.y + hy;
+        if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return false;  // the mean is inside
+        // sigma = A dx^2 + 2 B dx dy + Cq dy^2, a convex quadratic: with the mean outside, its
+        // minimum over the rectangle lies on an edge, where it is a clamped 1D minimum
+        const float A = g1.x * g1.x + g1.y * g1.y, B = g1.y * g1.z, Cq = g1.z * g1.z;
+        const float iA = 1.f / A, iC = 1.f / Cq;
+        auto on_x = [&](float dx) {
+            const float dy = fminf(y1, fmaxf(y0, -B * dx * iC));
+            return fmaf(A * dx, dx, fmaf(2.f * B * dx, dy, Cq * dy * dy));
+        };
+        auto on_y = [&](float dy) {
+            const float dx = fminf(x1, fmaxf(x0, -B * dy * iA));
+            return fmaf(A * dx, dx, fmaf(2.f * B * dx, dy, Cq * dy * dy));
+        };
+        const float smin = fminf(fminf(on_x(x0), on_x(x1)), fminf(on_y(y0), on_y(y1)));
+        const float tau = __logf(g1.w) - ln_alpha_min;  // alpha >= alpha_min needs sigma <= tau
+        return smin > tau * 1.0001f + 1e-3f;
+    }
 };
 
 struct TileInfo {
@@ -133,6 +161,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
     const int lane = threadIdx.x & 31;
     const WarpTile<PPT> wt(a.tile_w);
     const float fx = (float)wt.lx;
+    const float ln_amin = __logf(a.alpha_min);
     for (int iter = 0;; ++iter) {
         if (!a.persistent && iter > 0) break;
         const int slot = next_item(a, s_item);
@@ -172,7 +201,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
             for (int j0 = 0; j0 < cnt; j0 += 32) {
                 if (__all_sync(SG_FULL_MASK, n_done == PPT)) break;
                 const int jl = j0 + lane;
-                uint32_t cm = __ballot_sync(SG_FULL_MASK, jl < cnt && !wt.misses(s_geo2[jl]));
+                uint32_t cm = __ballot_sync(SG_FULL_MASK, jl < cnt && !wt.misses(s_geo2[jl], s_geo1[jl], ln_amin));
             while (cm) {
                 const int j = j0 + __ffs(cm) - 1;
                 cm &= cm - 1;
@@ -331,6 +360,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
     const int gid = lane >> 2, tig = lane & 3;
     const WarpTile<PPT> wt(a.tile_w);
     const float fx = (float)wt.lx;
+    const float ln_amin = __logf(a.alpha_min);
     // moment polynomials at the B-fragment pixels: pixel 8 ks + tig (+ 4) has X = tig - 3.5
     // (tig + 0.5), Y = (ks % 4) + 4 (ks / 4) - (2 PPT - 0.5); P_gid = P0 + Y (P1 + Y P2)
     // (all values small multiples of 1/4: exact in TF32, so B needs no split)
@@ -399,7 +429,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
             for (int jc0 = jmax > 0 ? (jmax - 1) & ~(kChunk - 1) : -kChunk; jc0 >= 0; jc0 -= kChunk) {
                 // entries of the chunk whose footprint reaches the warp (lane r tests entry jc0 + r)
                 bool cand = false;
-                if (lane < kChunk) cand = jc0 + lane < jmax && !wt.misses(s_geo2[jc0 + lane]);
+                if (lane < kChunk) cand = jc0 + lane < jmax && !wt.misses(s_geo2[jc0 + lane], s_geo1[jc0 + lane], ln_amin);
                 uint32_t cmask = __ballot_sync(SG_FULL_MASK, cand);
                 if (!cmask) continue;
                 // ---- gf = G F^T for the chunk (M = pixels, N = entries, K = features) ----
