@@ -272,18 +272,33 @@ def oracle_sample_time(g, cams, levels, stride, seed=0):
 
 
 def cpu_baseline(g, cams, levels, target_s):
+    """The oracle's cost of one full iteration, from two pixel samples: every call also pays a
+    fixed cost (projecting all Gaussians), so t(n) = a + b n is fitted to a coarse sample and a
+    fine one of about target_s seconds, and evaluated at the full pixel count."""
     import oracle
     oracle.build()
-    # pick a stride whose sample costs about target_s: probe with a coarse stride
-    t, ns, nt = oracle_sample_time(g, cams, levels, 64)
-    per_px = t / max(1, ns)
-    want = max(1, int(target_s / per_px))
-    stride = max(1, int(np.sqrt(nt / want)))
-    t, ns, nt = oracle_sample_time(g, cams, levels, stride)
-    full = t * nt / ns
+    s1 = 64
+    t1, n1, nt = oracle_sample_time(g, cams, levels, s1)
+
+    def fit(t2, n2):
+        b = (t2 - t1) / max(1, n2 - n1)
+        return max(0.0, t1 - b * n1), max(b, 1e-12)
+
+    # first guess from the coarse sample's cost per pixel (an upper bound: it includes the
+    # fixed cost), then one refit if the fine sample came out far below the target
+    stride = min(s1 // 2, max(1, int(np.sqrt(nt * (t1 / max(1, n1)) / target_s))))
+    t2, n2, _ = oracle_sample_time(g, cams, levels, stride)
+    if t2 < 0.5 * target_s and stride > 1:
+        a, b = fit(t2, n2)
+        s2 = min(stride - 1, max(1, int(np.sqrt(nt * b / max(target_s - a, 0.1 * target_s)))))
+        stride = s2
+        t2, n2, _ = oracle_sample_time(g, cams, levels, stride)
+    a, b = fit(t2, n2)
+    full = a + b * nt
     return {"value": 1.0 / full, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"FP64 oracle forward+backward on every {stride}th row/column of all {levels} levels "
-                      f"({ns} of {nt} pixels, {t:.1f} s), extrapolated linearly to the full iteration",
+                      f"({n2} of {nt} pixels, {t2:.1f} s) and every {s1}th ({n1} pixels, {t1:.1f} s); "
+                      f"fixed cost {a:.2f} s + {b * 1e3:.4f} ms per pixel, evaluated at all {nt} pixels",
             "seconds_per_iter": full}
 
 
