@@ -22,8 +22,10 @@ Pieces and the passages they follow:
                          and either cross-entropy on composited semantic logits or the
                          paper's L1 + D-SSIM on a semantic colour image (numpy + C SSIM).
 * ``tile_lists``         integer reference of the tile-instance lists: every (record, tile)
-                         pair of a record's tile rectangle, ordered by (tile, float32 depth
-                         bits, record index) (numpy lexsort).
+                         pair of a record's tile rectangle (optionally those that
+                         ``tile_reaches_alpha_min`` keeps: a float32 rule taken from the same
+                         records on both sides), ordered by (tile, float32 depth bits, record
+                         index) (numpy lexsort).
 
 Parity pins: the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py`` tie every function
 here to closed forms, invariants, library routines and finite differences.
@@ -475,13 +477,61 @@ def level_loss(r_rgb, r_depth, r_sem, gt_rgb, gt_depth, gt_sem, lambda_r=0.2, la
 # Tile-instance lists (integer reference; the depth sort of Eq. 7-9's set N per tile)
 # ------------------------------------------------------------------------------------------
 
-def tile_lists(rects, depth, n_tiles_x, tile_offset, n_total_tiles, n_per_view):
+def tile_reaches_alpha_min(geo, ext, X0, X1, Y0, Y1):
+    """Float32 tile culling rule of the tile lists, for arrays of (record, tile) pairs.
+
+    geo: (n, 8) float32 records (u_frac, v_frac, depth, opacity, m00, m10, m11, packed
+    int16 (u_int, v_int)); ext: (n, 2) float32 half extents; X0..X1, Y0..Y1: the tile's
+    pixel-centre rectangle (int).  The record's alpha >= alpha_min region is
+    sigma = (m00 dx)^2 + (m10 dx + m11 dy)^2 <= thr, and the projection wrote
+    ex = sqrt(2 thr s00) 1.002 + 0.01 with m00 = 1 / sqrt(2 s00), so
+    thr' = ((ex - 0.01) / 1.002 m00)^2.  The tile is kept when the minimum of sigma over the
+    rectangle (0 if the mean is inside, else the least of the four clamped edge minima of
+    the convex quadratic) is at most thr'.  Each step is one float32 operation with
+    round-to-nearest in a fixed order, so the decision is reproducible bit for bit from the
+    same float32 records.  Returns a bool array.
+    """
+    f = np.float32
+    geo = np.asarray(geo, np.float32)
+    ext = np.asarray(ext, np.float32)
+    packed = geo[:, 7].view(np.uint32)
+    ui = (packed & 0xFFFF).astype(np.uint16).view(np.int16).astype(np.int64)
+    vi = (packed >> 16).astype(np.uint16).view(np.int16).astype(np.int64)
+    uf, vf = geo[:, 0], geo[:, 1]
+    x0 = (np.asarray(X0, np.int64) - ui).astype(np.float32) - uf
+    x1 = (np.asarray(X1, np.int64) - ui).astype(np.float32) - uf
+    y0 = (np.asarray(Y0, np.int64) - vi).astype(np.float32) - vf
+    y1 = (np.asarray(Y1, np.int64) - vi).astype(np.float32) - vf
+    inside = (x0 <= 0) & (x1 >= 0) & (y0 <= 0) & (y1 >= 0)
+    m00, m10, m11 = geo[:, 4], geo[:, 5], geo[:, 6]
+    A = m00 * m00 + m10 * m10
+    B = m10 * m11
+    Cq = m11 * m11
+    with np.errstate(all="ignore"):
+        def sig(dx, dy):
+            return ((A * dx) * dx + ((f(2) * B) * dx) * dy) + (Cq * dy) * dy
+
+        def on_x(dx):
+            return sig(dx, np.fmin(y1, np.fmax(y0, -((B * dx) / Cq))))
+
+        def on_y(dy):
+            return sig(np.fmin(x1, np.fmax(x0, -((B * dy) / A))), dy)
+
+        smin = np.fmin(np.fmin(on_x(x0), on_x(x1)), np.fmin(on_y(y0), on_y(y1)))
+        t = ((ext[:, 0] - f(0.01)) / f(1.002)) * m00
+        thr = t * t
+    return inside | (smin <= thr)
+
+
+def tile_lists(rects, depth, n_tiles_x, tile_offset, n_total_tiles, n_per_view, keep=None):
     """Reference tile-instance lists from per-record tile rectangles.
 
     rects:   (R, 4) int half-open tile rectangles (tx0, ty0, tx1, ty1) of each record
              (record r belongs to view r // n_per_view); empty rectangles emit nothing.
     depth:   (R,) float32 depths (ordering key: their bit patterns, all positive).
     n_tiles_x, tile_offset: per-view tile-grid width and first global tile id.
+    keep:    optional function (records, tx, ty) -> bool array deciding which (record,
+             tile) pairs of the rectangles are listed (all of them without it).
     Returns (tile_ids, record_ids, ranges) with instances ordered by (global tile id,
     depth bits, record id) and ranges (n_total_tiles, 2) = [start, end) per tile.
     """
@@ -500,6 +550,12 @@ def tile_lists(rects, depth, n_tiles_x, tile_offset, n_total_tiles, n_per_view):
                 recs.append(r)
     tiles = np.asarray(tiles, np.int64)
     recs = np.asarray(recs, np.int64)
+    if keep is not None and len(recs):
+        v = view[recs]
+        local = tiles - np.asarray(tile_offset, np.int64)[v]
+        ntx = np.asarray(n_tiles_x, np.int64)[v]
+        k = np.asarray(keep(recs, local % ntx, local // ntx), bool)
+        tiles, recs = tiles[k], recs[k]
     dbits = np.asarray(depth, np.float32).view(np.int32).astype(np.int64)[recs] if len(recs) else np.zeros(0, np.int64)
     order = np.lexsort((recs, dbits, tiles))
     tiles, recs = tiles[order], recs[order]

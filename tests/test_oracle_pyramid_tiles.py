@@ -88,3 +88,80 @@ def test_tile_lists_reference_brute_force():
         s, e = ranges[t]
         assert np.all(tiles[s:e] == t)
         assert (e - s) == np.sum(tiles == t)
+
+
+def _records_f32(pr, cam, T):
+    """Float32 records (u_frac, v_frac, depth, opacity, m00, m10, m11, packed int16 mean),
+    half extents and tile rectangles in the projection's format, from the FP64 projection."""
+    P = oracle.P
+    v = pr[:, P["VALID"]] > 0
+    u, vv = pr[:, P["U"]], pr[:, P["V"]]
+    s00, s01, s11 = pr[:, P["S00"]], pr[:, P["S01"]], pr[:, P["S11"]]
+    o = pr[:, P["OPAC"]]
+    det = s00 * s11 - s01 * s01
+    with np.errstate(all="ignore"):
+        thr = np.log(o * 255.0) + 1e-3
+        ex = np.sqrt(2 * thr * s00) * 1.002 + 0.01
+        ey = np.sqrt(2 * thr * s11) * 1.002 + 0.01
+        ui, vi = np.rint(u), np.rint(vv)
+        geo = np.zeros((len(u), 8), np.float32)
+        geo[:, 0], geo[:, 1], geo[:, 2], geo[:, 3] = u - ui, vv - vi, pr[:, P["TZ"]], o
+        geo[:, 4] = 1 / np.sqrt(2 * s00)
+        geo[:, 5] = -s01 / np.sqrt(2 * s00 * det)
+        geo[:, 6] = np.sqrt(s00 / (2 * det))
+        packed = (ui.astype(np.int64) & 0xFFFF) | ((vi.astype(np.int64) & 0xFFFF) << 16)
+        geo[:, 7] = packed.astype(np.uint32).view(np.float32)
+        x0 = np.maximum(np.ceil(u - ex), 0); x1 = np.minimum(np.floor(u + ex), cam["W"] - 1)
+        y0 = np.maximum(np.ceil(vv - ey), 0); y1 = np.minimum(np.floor(vv + ey), cam["H"] - 1)
+    ok = v & (x0 <= x1) & (y0 <= y1)
+    rects = np.zeros((len(u), 4), np.int64)
+    rects[ok] = np.stack([x0[ok] // T, y0[ok] // T, x1[ok] // T + 1, y1[ok] // T + 1], 1)
+    return geo, np.stack([ex, ey], 1).astype(np.float32), rects
+
+
+def test_tile_culling_rule_keeps_every_tile_a_pixel_reaches():
+    """The float32 culling rule is conservative: every tile holding a pixel centre where the
+    Gaussian (FP64, from the oracle's projection) reaches alpha >= 1/255 is kept; and it is
+    not vacuous: it drops a sizeable share of the rectangle tiles (elongated footprints)."""
+    import synthetic
+    g = {k: np.asarray(v, np.float64) for k, v in synthetic.cloud_scene(800, 4, seed=9).items()}
+    g["log_scale"][:, 0] += 1.0       # elongated, so that rectangles over-cover
+    cam = synthetic.cloud_camera()
+    T = 8
+    pr = oracle.project(g, cam)
+    geo, ext, rects = _records_f32(pr, cam, T)
+    P = oracle.P
+    n_tiles = n_kept = 0
+    for r in np.nonzero(rects[:, 2] > rects[:, 0])[0]:
+        tx0, ty0, tx1, ty1 = rects[r]
+        S = np.array([[pr[r, P["S00"]], pr[r, P["S01"]]], [pr[r, P["S01"]], pr[r, P["S11"]]]])
+        Q = np.linalg.inv(S)
+        txs, tys = np.meshgrid(np.arange(tx0, tx1), np.arange(ty0, ty1))
+        txs, tys = txs.ravel(), tys.ravel()
+        X0, Y0 = txs * T, tys * T
+        X1, Y1 = np.minimum(X0 + T - 1, cam["W"] - 1), np.minimum(Y0 + T - 1, cam["H"] - 1)
+        kept = oracle.tile_reaches_alpha_min(np.repeat(geo[r:r + 1], len(txs), 0), np.repeat(ext[r:r + 1], len(txs), 0),
+                                             X0, X1, Y0, Y1)
+        for k in range(len(txs)):
+            xs, ys = np.meshgrid(np.arange(X0[k], X1[k] + 1) - pr[r, P["U"]], np.arange(Y0[k], Y1[k] + 1) - pr[r, P["V"]])
+            sig = 0.5 * (Q[0, 0] * xs * xs + 2 * Q[0, 1] * xs * ys + Q[1, 1] * ys * ys)
+            reaches = (pr[r, P["OPAC"]] * np.exp(-sig) >= 1 / 255).any()
+            assert kept[k] or not reaches, (r, txs[k], tys[k])
+        n_tiles += len(txs)
+        n_kept += int(kept.sum())
+    assert n_tiles > 2000 and n_kept < 0.9 * n_tiles, (n_kept, n_tiles)
+
+
+def test_tile_lists_with_culling_lists_only_kept_pairs():
+    """With a keep rule the reference lists exactly the kept (record, tile) pairs, in the
+    same (tile, depth, record) order."""
+    rects = np.array([[0, 0, 3, 2], [1, 0, 2, 2], [0, 1, 3, 2]])
+    depth = np.array([2.0, 1.0, 3.0], np.float32)
+    keep = lambda recs, tx, ty: (tx + ty + recs) % 2 == 0
+    tiles, recs, ranges = oracle.tile_lists(rects, depth, [3], [0], 6, 3, keep=keep)
+    full_t, full_r, _ = oracle.tile_lists(rects, depth, [3], [0], 6, 3)
+    sel = [(t, r) for t, r in zip(full_t, full_r) if ((t % 3) + (t // 3) + r) % 2 == 0]
+    assert list(zip(tiles.tolist(), recs.tolist())) == sel
+    for t in range(6):
+        s, e = ranges[t]
+        assert np.all(tiles[s:e] == t) and (e - s) == np.sum(tiles == t)
