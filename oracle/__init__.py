@@ -485,9 +485,10 @@ def tile_reaches_alpha_min(geo, ext, X0, X1, Y0, Y1):
     pixel-centre rectangle (int).  The record's alpha >= alpha_min region is
     sigma = (m00 dx)^2 + (m10 dx + m11 dy)^2 <= thr, and the projection wrote
     ex = sqrt(2 thr s00) 1.002 + 0.01 with m00 = 1 / sqrt(2 s00), so
-    thr' = ((ex - 0.01) / 1.002 m00)^2.  The tile is kept when the minimum of sigma over the
-    rectangle (0 if the mean is inside, else the least of the four clamped edge minima of
-    the convex quadratic) is at most thr'.  Each step is one float32 operation with
+    thr' = ((ex - 0.01) / 1.002 m00)^2.  The tile is kept when sigma at the rectangle's centre
+    point is at most thr', or else when the minimum of sigma over the rectangle (0 if the
+    mean is inside, else the least of the four clamped edge minima of the convex quadratic,
+    with the divisions taken as reciprocal then product) is at most thr'.  Each step is one float32 operation with
     round-to-nearest in a fixed order, so the decision is reproducible bit for bit from the
     same float32 records.  Returns a bool array.
     """
@@ -498,10 +499,12 @@ def tile_reaches_alpha_min(geo, ext, X0, X1, Y0, Y1):
     ui = (packed & 0xFFFF).astype(np.uint16).view(np.int16).astype(np.int64)
     vi = (packed >> 16).astype(np.uint16).view(np.int16).astype(np.int64)
     uf, vf = geo[:, 0], geo[:, 1]
-    x0 = (np.asarray(X0, np.int64) - ui).astype(np.float32) - uf
-    x1 = (np.asarray(X1, np.int64) - ui).astype(np.float32) - uf
-    y0 = (np.asarray(Y0, np.int64) - vi).astype(np.float32) - vf
-    y1 = (np.asarray(Y1, np.int64) - vi).astype(np.float32) - vf
+    X0, X1 = np.asarray(X0, np.int64), np.asarray(X1, np.int64)
+    Y0, Y1 = np.asarray(Y0, np.int64), np.asarray(Y1, np.int64)
+    x0 = (X0 - ui).astype(np.float32) - uf
+    x1 = (X1 - ui).astype(np.float32) - uf
+    y0 = (Y0 - vi).astype(np.float32) - vf
+    y1 = (Y1 - vi).astype(np.float32) - vf
     inside = (x0 <= 0) & (x1 >= 0) & (y0 <= 0) & (y1 >= 0)
     m00, m10, m11 = geo[:, 4], geo[:, 5], geo[:, 6]
     A = m00 * m00 + m10 * m10
@@ -511,16 +514,22 @@ def tile_reaches_alpha_min(geo, ext, X0, X1, Y0, Y1):
         def sig(dx, dy):
             return ((A * dx) * dx + ((f(2) * B) * dx) * dy) + (Cq * dy) * dy
 
-        def on_x(dx):
-            return sig(dx, np.fmin(y1, np.fmax(y0, -((B * dx) / Cq))))
-
-        def on_y(dy):
-            return sig(np.fmin(x1, np.fmax(x0, -((B * dy) / A))), dy)
-
-        smin = np.fmin(np.fmin(on_x(x0), on_x(x1)), np.fmin(on_y(y0), on_y(y1)))
         t = ((ext[:, 0] - f(0.01)) / f(1.002)) * m00
         thr = t * t
-    return inside | (smin <= thr)
+        # the rectangle's centre point first
+        xc = (X0 + X1 - 2 * ui).astype(np.float32) * f(0.5) - uf
+        yc = (Y0 + Y1 - 2 * vi).astype(np.float32) * f(0.5) - vf
+        centre = sig(xc, yc) <= thr
+        rA, rC = f(1) / A, f(1) / Cq
+
+        def on_x(dx):
+            return sig(dx, np.fmin(y1, np.fmax(y0, -((B * dx) * rC))))
+
+        def on_y(dy):
+            return sig(np.fmin(x1, np.fmax(x0, -((B * dy) * rA))), dy)
+
+        smin = np.fmin(np.fmin(on_x(x0), on_x(x1)), np.fmin(on_y(y0), on_y(y1)))
+    return centre | inside | (smin <= thr)
 
 
 def tile_lists(rects, depth, n_tiles_x, tile_offset, n_total_tiles, n_per_view, keep=None):

@@ -35,7 +35,7 @@ sg_status launch_project_fwd(const sg_gaussians *, const sg_view *, int, const s
 sg_status launch_project_bwd(const sg_gaussians *, const sg_view *, int, const sg_config *,
                              const sg_projected *, float *, sg_gaussian_grads *, cudaStream_t);
 size_t tile_lists_workspace_size(int64_t R, int32_t cap);
-sg_status launch_build_tile_lists(const sg_projected *, int, int, const sg_view *, int,
+sg_status launch_build_tile_lists(const sg_projected *, int, int, const sg_view *, int, int, int,
                                   sg_tile_lists *, void *, size_t, uint32_t *, cudaStream_t);
 size_t loss_workspace_size(const sg_view *vh, int n_views, int C, int n_classes);
 sg_status launch_loss(const sg_images *, const sg_targets *, const sg_view *, const sg_view *, int,
@@ -235,7 +235,8 @@ sg_status sg_build_tile_lists(const sg_projected *proj, int32_t N, int32_t n_vie
     SG_REQUIRE(lists->capacity >= 1, "capacity must be >= 1");
     SG_REQUIRE(workspace && status, "workspace/status is NULL");
     SG_REQUIRE(aligned16(workspace), "workspace must be 16-byte aligned");
-    return launch_build_tile_lists(proj, N, n_views, views, n_tiles, lists, workspace, workspace_bytes,
+    return launch_build_tile_lists(proj, N, n_views, views, n_tiles, cfg->tile_w, cfg->tile_h, lists, workspace,
+                                   workspace_bytes,
                                    status, (cudaStream_t)stream);
 }
 

@@ -5,12 +5,14 @@
 //   1. compact:  visible records r (non-empty tile rectangle) -> (depth bits, r), in r order
 //   2. sort:     stable LSD radix sort by the 32 float32 depth bits (depths are > z_near > 0
 //                so their bit patterns order like the values); ties keep record order
-//   3. emit:     exclusive scan of the tile counts in depth order, then each record writes
-//                (global tile id, r) for every tile of its rectangle, row-major
+//   3. emit:     each record in depth order writes (global tile id, r) for every tile of
+//                its rectangle, row-major, that its alpha >= alpha_min region can reach (a
+//                float32 test of the tile's pixel-centre rectangle); a counting pass with the
+//                same test and an exclusive scan give the output offsets
 //   4. sort:     stable LSD radix sort of the instances by global tile id (only the bits
 //                n_tiles needs), which keeps the (depth, record) order inside each tile
 //   5. ranges:   [start, end) of every tile
-// The result equals sorting all instances by (tile, depth bits, record id).  Every radix
+// The result equals sorting all kept instances by (tile, depth bits, record id).  Every radix
 // pass is three kernels: per-block digit histograms, per-digit scans over the blocks, and
 // a stable scatter that ranks equal digits inside a block by warp match + prefix counts.
 #include <cstdio>
@@ -78,7 +80,7 @@ __device__ __forceinline__ uint32_t rect_tiles(uint2 r) {
     return (tx1 > tx0 && ty1 > ty0) ? (tx1 - tx0) * (ty1 - ty0) : 0u;
 }
 
-struct SortedTileCount {  // tiles of the record at sorted position i
+struct SortedTileCount {  // tiles of the rectangle of the record at sorted position i
     const uint2 *rect;
     const uint32_t *rec;
     __device__ uint32_t operator()(int i) const { return rect_tiles(rect[rec[i]]); }
@@ -145,67 +147,176 @@ __global__ void compact_apply_kernel(const uint2 *__restrict__ rect, const float
     }
 }
 
-// Apply for the emission: record at sorted position m writes its tiles at offset.
-__global__ void emit_apply_kernel(const uint2 *__restrict__ rect, const uint32_t *__restrict__ rec,
-                                  const int *__restrict__ m_ptr, const uint32_t *__restrict__ boff,
-                                  int G, int N, const sg_view *__restrict__ views,
-                                  uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval,
-                                  int capacity, uint32_t *__restrict__ status) {
+// Does the record's alpha >= alpha_min region reach the tile?  The projection wrote the half
+// extent ex = sqrt(2 thr s00) 1.002 + 0.01 with thr = ln(o / alpha_min) + 1e-3 and
+// m00 = 1 / sqrt(2 s00), so thr' = ((ex - 0.01) / 1.002 m00)^2 recovers the threshold from the
+// record (to float rounding, far inside its 1e-3 margin).  The tile is kept when the minimum
+// of sigma = (m00 dx)^2 + (m10 dx + m11 dy)^2 over the rectangle [X0, X1] x [Y0, Y1] of its
+// pixel centres is at most thr': a tile whose centre point is inside the footprint is kept at
+// once; otherwise the minimum is 0 when the mean is inside, else the least of the four
+// clamped edge minima of the convex quadratic.  Every step is one correctly rounded float32
+// operation (reciprocals included) in a fixed order, with no contraction, so the decision
+// is reproducible bit for bit.
+__device__ __forceinline__ bool tile_reaches(const float4 g0, const float4 g1, float ex, int X0, int X1, int Y0,
+                                             int Y1) {
+    const uint32_t packed = __float_as_uint(g1.w);
+    const int ui = (int)(short)(packed & 0xffffu), vi = (int)(short)(packed >> 16);
+    const float m00 = g1.x, m10 = g1.y, m11 = g1.z;
+    const float A = __fadd_rn(__fmul_rn(m00, m00), __fmul_rn(m10, m10));
+    const float B = __fmul_rn(m10, m11);
+    const float Cq = __fmul_rn(m11, m11);
+    const float B2 = __fmul_rn(2.f, B);
+    auto sig = [&](float dx, float dy) {  // ((A dx) dx + ((2B) dx) dy) + (Cq dy) dy
+        return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(__fmul_rn(B2, dx), dy)),
+                         __fmul_rn(__fmul_rn(Cq, dy), dy));
+    };
+    const float t = __fmul_rn(__fdiv_rn(__fsub_rn(ex, 0.01f), 1.002f), m00);
+    const float thr = __fmul_rn(t, t);
+    // the rectangle's centre first (most kept tiles are inside the footprint)
+    const float xc = __fsub_rn(__fmul_rn((float)(X0 + X1 - 2 * ui), 0.5f), g0.x);
+    const float yc = __fsub_rn(__fmul_rn((float)(Y0 + Y1 - 2 * vi), 0.5f), g0.y);
+    if (sig(xc, yc) <= thr) return true;
+    const float x0 = __fsub_rn((float)(X0 - ui), g0.x), x1 = __fsub_rn((float)(X1 - ui), g0.x);
+    const float y0 = __fsub_rn((float)(Y0 - vi), g0.y), y1 = __fsub_rn((float)(Y1 - vi), g0.y);
+    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
+    const float rA = __frcp_rn(A), rC = __frcp_rn(Cq);
+    auto on_x = [&](float dx) { return sig(dx, fminf(y1, fmaxf(y0, -__fmul_rn(__fmul_rn(B, dx), rC)))); };
+    auto on_y = [&](float dy) { return sig(fminf(x1, fmaxf(x0, -__fmul_rn(__fmul_rn(B, dy), rA))), dy); };
+    const float smin = fminf(fminf(on_x(x0), on_x(x1)), fminf(on_y(y0), on_y(y1)));
+    return smin <= thr;
+}
+
+// The (record, tile) slots: the tiles of every depth-sorted record's rectangle, row-major,
+// record after record; P[i] is the first slot of sorted record i.  The two culling passes
+// split the S slots evenly over their Gc blocks (a multiple of 256 slots each), so that the
+// few near records with huge rectangles do not serialise one warp.
+__device__ __forceinline__ uint32_t slot_block_size(uint32_t S, int Gc) {
+    const uint32_t chunks = (S + kScanThreads - 1) / kScanThreads;
+    const uint32_t per = (chunks + (uint32_t)Gc - 1) / (uint32_t)Gc;
+    return (per > 0 ? per : 1u) * kScanThreads;
+}
+
+// P[i] = boff[block] + exclusive scan of the rectangle tile counts, and for every block of the
+// slot partition the record that owns its first slot.
+__global__ void slot_prefix_kernel(const uint2 *__restrict__ rect, const uint32_t *__restrict__ rec,
+                                   const int *__restrict__ m_ptr, const uint32_t *__restrict__ boff, int G,
+                                   const int *__restrict__ s_ptr, int Gc, uint32_t *__restrict__ P,
+                                   uint32_t *__restrict__ first_rec) {
     pdl_begin();
     const int n = *m_ptr;
+    const uint64_t per = slot_block_size((uint32_t)*s_ptr, Gc);
     int beg, end;
     block_range(n, G, blockIdx.x, beg, end);
     uint32_t run = boff[blockIdx.x];
-    bool overflow = false;
     for (int base = beg; base < end; base += kScanThreads) {
         const int i = base + threadIdx.x;
-        uint32_t c = 0, r = 0;
-        uint2 rc = make_uint2(0, 0);
-        if (i < end) {
-            r = rec[i];
-            rc = rect[r];
-            c = rect_tiles(rc);
-        }
+        const uint32_t c = i < end ? rect_tiles(rect[rec[i]]) : 0u;
         uint32_t tot;
         const uint32_t ex = block_exclusive_scan(c, tot);
-        // The warp's instances occupy [run + w0, run + w1) in lane order; the warp writes them
-        // together, lane i taking slot i of each 32-slot step (coalesced stores).  The owner of
-        // slot o is the last lane whose offset is <= o (lanes with no instance share their
-        // offset with the next lane, so the last one found owns at least one instance).
-        const int lane = threadIdx.x & 31;
-        const uint32_t w0 = __shfl_sync(SG_FULL_MASK, ex, 0);
-        const uint32_t w1 = __shfl_sync(SG_FULL_MASK, ex + c, 31);
-        uint32_t tile0 = 0, tiles_x = 0, tw = 1;
-        if (c) {
-            const int v = (int)(r / (uint32_t)N);
-            const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16;
-            tiles_x = (uint32_t)views[v].tiles_x;
-            tile0 = (uint32_t)views[v].tile_offset + ty0 * tiles_x + tx0;
-            tw = (rc.y & 0xffffu) - tx0;
+        if (i < end) {
+            const uint64_t p = run + ex;
+            P[i] = (uint32_t)p;
+            for (uint64_t b = (p + per - 1) / per; b * per < p + c && b < (uint64_t)Gc; ++b) first_rec[b] = (uint32_t)i;
         }
-        for (uint32_t ob = w0; ob < w1; ob += 32) {  // warp-uniform trip count
-            const uint32_t o = ob + lane;
-            int own = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1)
-                if (__shfl_sync(SG_FULL_MASK, ex, own + step) <= o) own += step;
-            const uint32_t q = o - __shfl_sync(SG_FULL_MASK, ex, own);
-            const uint32_t ow = __shfl_sync(SG_FULL_MASK, tw, own);
-            const uint32_t ot = __shfl_sync(SG_FULL_MASK, tile0, own);
-            const uint32_t ox = __shfl_sync(SG_FULL_MASK, tiles_x, own);
-            const uint32_t orec = __shfl_sync(SG_FULL_MASK, r, own);
-            if (o < w1) {
-                const uint32_t row = q / ow;
-                const uint32_t g = run + o;
+        run += tot;
+    }
+}
+
+// The culling passes over the slot partition.  Thread t of a 256-slot chunk takes slot
+// s = c0 + t: its record is found by a binary search over the prefixes of the (at most 256)
+// records that can own the chunk, staged in shared memory.
+//   COUNT: tests its pair, stores the chunk's keep bits (one 32-bit word per warp; slot
+//          ranges are 32-aligned, so every word is written by exactly one warp) and writes
+//          the block's kept total to kbsum.
+//   EMIT:  reads its keep bit and writes (global tile id, record) at kbsum[block] (the scanned
+//          block offset) plus its rank among the block's kept slots, i.e. in slot order.
+template <bool EMIT>
+__global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *__restrict__ geo,
+                                 const float2 *__restrict__ ext, const uint32_t *__restrict__ rec,
+                                 const int *__restrict__ m_ptr, const int *__restrict__ s_ptr,
+                                 const uint32_t *__restrict__ P, const uint32_t *__restrict__ first_rec, int Gc,
+                                 int N, const sg_view *__restrict__ views, int n_views, int tile_w, int tile_h,
+                                 uint32_t *__restrict__ bits, uint32_t bit_words, uint32_t *__restrict__ kbsum,
+                                 uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval, int capacity,
+                                 uint32_t *__restrict__ status) {
+    pdl_begin();
+    __shared__ uint32_t s_P[kScanThreads];
+    __shared__ int s_next;
+    __shared__ int4 s_vw[SG_MAX_VIEWS];  // (W, H, tile_offset, tiles_x) of each view-level
+    for (int v = threadIdx.x; v < n_views; v += kScanThreads)
+        s_vw[v] = make_int4(views[v].W, views[v].H, views[v].tile_offset, views[v].tiles_x);
+    const int n = *m_ptr;
+    const uint32_t S = (uint32_t)*s_ptr;
+    const uint64_t per = slot_block_size(S, Gc);
+    const uint64_t s0 = (uint64_t)blockIdx.x * per;
+    const uint64_t s1 = min((uint64_t)S, s0 + per);
+    uint32_t kept = 0;
+    uint32_t run = EMIT ? kbsum[blockIdx.x] : 0u;
+    bool overflow = false;
+    int ic = s0 < s1 ? (int)first_rec[blockIdx.x] : 0;
+    for (uint64_t c0 = s0; c0 < s1; c0 += kScanThreads) {  // block-uniform trip count
+        const int j = ic + (int)threadIdx.x;
+        s_P[threadIdx.x] = j < n ? P[j] : 0xffffffffu;
+        __syncthreads();
+        const uint32_t s = (uint32_t)(c0 + threadIdx.x);
+        const bool valid = c0 + threadIdx.x < s1;
+        bool keep = false;
+        uint32_t tile = 0, orec = 0;
+        int k = 0;
+        if (valid) {
+            int lo = 0, hi = kScanThreads - 1;  // the last k with s_P[k] <= s (s_P[0] <= c0)
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_P[mid] <= s) lo = mid; else hi = mid - 1;
+            }
+            k = lo;
+            orec = rec[ic + k];
+            const uint2 rc = rect[orec];
+            const uint32_t q = s - s_P[k];
+            const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16, tw = (rc.y & 0xffffu) - tx0;
+            const uint32_t row = q / tw;
+            const int tx = (int)(tx0 + (q - row * tw)), ty = (int)(ty0 + row);
+            const int4 vw = s_vw[orec / (uint32_t)N];
+            if (EMIT) {
+                keep = (s >> 5) < bit_words && ((bits[s >> 5] >> (s & 31u)) & 1u);
+                tile = (uint32_t)vw.z + (uint32_t)ty * (uint32_t)vw.w + (uint32_t)tx;
+            } else {
+                const int X0 = tx * tile_w, Y0 = ty * tile_h;
+                keep = tile_reaches(geo[2 * (size_t)orec], geo[2 * (size_t)orec + 1], ext[orec].x, X0,
+                                    min(X0 + tile_w - 1, vw.x - 1), Y0, min(Y0 + tile_h - 1, vw.y - 1));
+            }
+        }
+        if (!EMIT) {
+            const uint32_t word = __ballot_sync(SG_FULL_MASK, keep);
+            if ((threadIdx.x & 31) == 0) {
+                const uint32_t w = (uint32_t)((c0 + threadIdx.x) >> 5);
+                if (w < bit_words) bits[w] = word;
+                else if (word) overflow = true;
+            }
+            kept += keep ? 1u : 0u;
+        } else {
+            uint32_t tot;
+            const uint32_t ex = block_exclusive_scan(keep ? 1u : 0u, tot);
+            if (keep) {
+                const uint32_t g = run + ex;
                 if (g < (uint32_t)capacity) {
-                    tkey[g] = ot + row * ox + (q - row * ow);
+                    tkey[g] = tile;
                     tval[g] = orec;
                 } else {
                     overflow = true;
                 }
             }
+            run += tot;
         }
-        run += tot;
+        // the next chunk starts in the record that owns this chunk's last slot
+        if (threadIdx.x == kScanThreads - 1) s_next = ic + k;
+        __syncthreads();
+        ic = s_next;
+    }
+    if (!EMIT) {
+        uint32_t tot;
+        block_exclusive_scan(kept, tot);
+        if (threadIdx.x == 0) kbsum[blockIdx.x] = tot;
     }
     if (overflow) atomicOr(status, SG_STATUS_CAPACITY);
 }
@@ -419,6 +530,11 @@ __global__ void ranges_kernel(const uint32_t *__restrict__ tile, const int *__re
 
 struct TileWorkspace {
     uint32_t *dkey_in, *dval_in, *dkey_out, *dval_out, *dkey_tmp, *dval_tmp;
+    uint32_t *slot0;      // first (record, tile) slot of each depth-sorted record
+    uint32_t *first_rec;  // record owning the first slot of each block of the slot partition
+    uint32_t *kbsum;      // kept instances per block of the slot partition, then their offsets
+    uint32_t *bits;       // keep bit of every slot
+    uint32_t bit_words;
     uint32_t *tkey_in, *tval_in, *tkey_tmp, *tval_tmp;
     uint32_t *bsum, *hist, *totals;
     int *counts;  // [0] visible records M, [1] K clamped
@@ -453,6 +569,12 @@ static size_t tile_ws_layout(int64_t R, int32_t cap, int G, TileWorkspace *ws, c
     w.dval_out = (uint32_t *)take(r4);
     w.dkey_tmp = (uint32_t *)take(r4);
     w.dval_tmp = (uint32_t *)take(r4);
+    w.slot0 = (uint32_t *)take(r4);
+    w.first_rec = (uint32_t *)take((size_t)4 * G * 4);  // the slot partition has 4 G blocks
+    w.kbsum = (uint32_t *)take((size_t)4 * G * 4);
+    // keep bits for up to twice the lists' capacity in slots (more is reported as overflow)
+    w.bit_words = (uint32_t)(((uint64_t)cap * 2 + 31) / 32);
+    w.bits = (uint32_t *)take((size_t)w.bit_words * 4);
     w.tkey_in = (uint32_t *)take(c4);
     w.tval_in = (uint32_t *)take(c4);
     w.tkey_tmp = (uint32_t *)take(c4);
@@ -470,7 +592,7 @@ size_t tile_lists_workspace_size(int64_t R, int32_t cap) {
 }
 
 sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
-                                  const sg_view *views, int n_tiles, sg_tile_lists *lists,
+                                  const sg_view *views, int n_tiles, int tile_w, int tile_h, sg_tile_lists *lists,
                                   void *workspace, size_t ws_bytes, uint32_t *status,
                                   cudaStream_t st) {
     const int G = sort_grid();
@@ -497,11 +619,22 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     // records): its blocks own ranges of depth-sorted records, and the near (large) ones,
     // which emit most of the instances, come first.
     const int Ge = (int)std::min<int64_t>(4 * G, std::max<int64_t>(G, R / 2048));
+    // slots: the rectangle tiles of the records in depth order
+    const float2 *ext = reinterpret_cast<const float2 *>(proj->ext);
     launch_pdl(scan_reduce_kernel<SortedTileCount>, Ge, kScanThreads, 0, st, SortedTileCount{rect, w.dval_out},
                w.counts + 0, 0, w.bsum, Ge);
-    launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.bsum, Ge, lists->count);
-    launch_pdl(emit_apply_kernel, Ge, kScanThreads, 0, st, rect, w.dval_out, w.counts + 0, w.bsum, Ge, N, views,
-                                                  w.tkey_in, w.tval_in, lists->capacity, status);
+    launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.bsum, Ge, w.counts + 2);
+    const int Gc = 4 * G;  // blocks of the slot partition (each walks a few 256-slot chunks)
+    launch_pdl(slot_prefix_kernel, Ge, kScanThreads, 0, st, rect, w.dval_out, w.counts + 0, w.bsum, Ge,
+               w.counts + 2, Gc, w.slot0, w.first_rec);
+    // culling, evenly over the slots: keep bits and kept counts, their offsets, emission
+    launch_pdl(cull_pass_kernel<false>, Gc, kScanThreads, 0, st, rect, geo, ext, w.dval_out, w.counts + 0,
+               w.counts + 2, w.slot0, w.first_rec, Gc, N, views, n_views, tile_w, tile_h, w.bits, w.bit_words,
+               w.kbsum, (uint32_t *)nullptr, (uint32_t *)nullptr, lists->capacity, status);
+    launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.kbsum, Gc, lists->count);
+    launch_pdl(cull_pass_kernel<true>, Gc, kScanThreads, 0, st, rect, geo, ext, w.dval_out, w.counts + 0,
+               w.counts + 2, w.slot0, w.first_rec, Gc, N, views, n_views, tile_w, tile_h, w.bits, w.bit_words,
+               w.kbsum, w.tkey_in, w.tval_in, lists->capacity, status);
     // 4. stable sort by tile id
     int bits = 1;
     while ((1ll << bits) < (long long)n_tiles) ++bits;
@@ -511,7 +644,7 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     launch_pdl(clamp_count_kernel, 1, 1, 0, st, lists->count, lists->capacity, w.counts + 1);
     launch_pdl(ranges_kernel, (n_tiles + kScanThreads - 1) / kScanThreads, kScanThreads, 0, st, lists->tile,
                w.counts + 1, n_tiles, reinterpret_cast<int2 *>(lists->ranges));
-    count_launches(3 + 3 + 2);  // compaction, emission, clamp + ranges
+    count_launches(3 + 6 + 2);  // compaction, slots + culling + emission, clamp + ranges
     // 6. work order: one stable counting pass over the 6-bit length keys
     if (lists->order) {
         const TileLengthKeys src{reinterpret_cast<const int2 *>(lists->ranges)};

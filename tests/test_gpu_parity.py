@@ -113,7 +113,24 @@ def _lists_vs_reference(r):
     depth = r.geo.view(-1, 8)[:, 2].cpu().numpy()
     tx = [r.views_host[v].tiles_x for v in range(r.V)]
     to = [r.views_host[v].tile_offset for v in range(r.V)]
-    rt, rr, rg = oracle.tile_lists(rects, depth, tx, to, r.n_tiles, r.N)
+    # the culling rule, taken in float32 from the GPU's own records (like the depth order)
+    geo = r.geo.view(-1, 8).cpu().numpy()
+    ext = r.ext.view(-1, 2).cpu().numpy()
+    tw, th = r.cfg.tile_w, r.cfg.tile_h
+    Wv = np.array([r.views_host[v].W for v in range(r.V)])
+    Hv = np.array([r.views_host[v].H for v in range(r.V)])
+
+    def keep(recs, tx_, ty_):
+        v = recs // r.N
+        X0, Y0 = tx_ * tw, ty_ * th
+        return oracle.tile_reaches_alpha_min(geo[recs], ext[recs], X0, np.minimum(X0 + tw - 1, Wv[v] - 1),
+                                             Y0, np.minimum(Y0 + th - 1, Hv[v] - 1))
+
+    rt, rr, rg = oracle.tile_lists(rects, depth, tx, to, r.n_tiles, r.N, keep=keep)
+    # culling removes instances of every rectangle-covered tile that no pixel can reach
+    rr64 = rects.astype(np.int64)
+    n_rect = int((np.maximum(0, rr64[:, 2] - rr64[:, 0]) * np.maximum(0, rr64[:, 3] - rr64[:, 1])).sum())
+    assert K <= n_rect
     assert K == len(rt)
     assert np.array_equal(tiles, rt)
     assert np.array_equal(recs, rr)
