@@ -5,10 +5,12 @@
 //   1. compact:  visible records r (non-empty tile rectangle) -> (depth bits, r), in r order
 //   2. sort:     stable LSD radix sort by the 32 float32 depth bits (depths are > z_near > 0
 //                so their bit patterns order like the values); ties keep record order
-//   3. emit:     each record in depth order writes (global tile id, r) for every tile of
-//                its rectangle, row-major, that its alpha >= alpha_min region can reach (a
-//                float32 test of the tile's pixel-centre rectangle); a counting pass with the
-//                same test and an exclusive scan give the output offsets
+//   3. emit:     the slots are the tiles of each record's rectangle, row-major, record after
+//                record in depth order (a prefix of the rectangle sizes numbers them); a
+//                counting pass, split evenly over the slots, tests whether the record's
+//                alpha >= alpha_min region reaches each slot's tile (a float32 test of the
+//                tile's pixel-centre rectangle) and stores keep bits, and an emission pass
+//                writes (global tile id, r) for the kept slots, compacted in slot order
 //   4. sort:     stable LSD radix sort of the instances by global tile id (only the bits
 //                n_tiles needs), which keeps the (depth, record) order inside each tile
 //   5. ranges:   [start, end) of every tile
