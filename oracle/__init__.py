@@ -485,12 +485,15 @@ def tile_reaches_alpha_min(geo, ext, X0, X1, Y0, Y1):
     pixel-centre rectangle (int).  The record's alpha >= alpha_min region is
     sigma = (m00 dx)^2 + (m10 dx + m11 dy)^2 <= thr, and the projection wrote
     ex = sqrt(2 thr s00) 1.002 + 0.01 with m00 = 1 / sqrt(2 s00), so
-    thr' = ((ex - 0.01) / 1.002 m00)^2.  The tile is kept when sigma at the rectangle's centre
-    point is at most thr', or else when the minimum of sigma over the rectangle (0 if the
-    mean is inside, else the least of the four clamped edge minima of the convex quadratic,
-    with the divisions taken as reciprocal then product) is at most thr'.  Each step is one float32 operation with
-    round-to-nearest in a fixed order, so the decision is reproducible bit for bit from the
-    same float32 records.  Returns a bool array.
+    thr' = ((ex - 0.01) (1 / 1.002) m00)^2.  The tile is kept when sigma <= thr' somewhere on
+    the rectangle: at its centre point, or the mean is inside, or on one of its edges.  On an
+    edge dx = const the minimum over dy is (m00 dx)^2 when the minimiser
+    dy* = -m10 dx / m11 lies on the edge (m11 y0 <= -m10 dx <= m11 y1), else at a corner; on
+    an edge dy = const it is dy^2 (m00 m11)^2 / A (A = m00^2 + m10^2), compared as
+    dy^2 (m00 m11)^2 <= thr' A, when -(m10 m11) dy lies in [A x0, A x1], else at a corner.
+    Each step is one float32 operation with round-to-nearest in a fixed order and no
+    division, so the decision is reproducible bit for bit from the same float32 records.
+    Returns a bool array.
     """
     f = np.float32
     geo = np.asarray(geo, np.float32)
@@ -501,35 +504,36 @@ def tile_reaches_alpha_min(geo, ext, X0, X1, Y0, Y1):
     uf, vf = geo[:, 0], geo[:, 1]
     X0, X1 = np.asarray(X0, np.int64), np.asarray(X1, np.int64)
     Y0, Y1 = np.asarray(Y0, np.int64), np.asarray(Y1, np.int64)
+    m00, m10, m11 = geo[:, 4], geo[:, 5], geo[:, 6]
+
+    def sig(dx, dy):
+        p1 = m00 * dx
+        p2 = m10 * dx + m11 * dy
+        return p1 * p1 + p2 * p2
+
+    t = ((ext[:, 0] - f(0.01)) * f(1.0 / 1.002)) * m00
+    thr = t * t
+    xc = (X0 + X1 - 2 * ui).astype(np.float32) * f(0.5) - uf
+    yc = (Y0 + Y1 - 2 * vi).astype(np.float32) * f(0.5) - vf
     x0 = (X0 - ui).astype(np.float32) - uf
     x1 = (X1 - ui).astype(np.float32) - uf
     y0 = (Y0 - vi).astype(np.float32) - vf
     y1 = (Y1 - vi).astype(np.float32) - vf
-    inside = (x0 <= 0) & (x1 >= 0) & (y0 <= 0) & (y1 >= 0)
-    m00, m10, m11 = geo[:, 4], geo[:, 5], geo[:, 6]
+    keep = (sig(xc, yc) <= thr) | ((x0 <= 0) & (x1 >= 0) & (y0 <= 0) & (y1 >= 0))
     A = m00 * m00 + m10 * m10
     B = m10 * m11
-    Cq = m11 * m11
-    with np.errstate(all="ignore"):
-        def sig(dx, dy):
-            return ((A * dx) * dx + ((f(2) * B) * dx) * dy) + (Cq * dy) * dy
-
-        t = ((ext[:, 0] - f(0.01)) / f(1.002)) * m00
-        thr = t * t
-        # the rectangle's centre point first
-        xc = (X0 + X1 - 2 * ui).astype(np.float32) * f(0.5) - uf
-        yc = (Y0 + Y1 - 2 * vi).astype(np.float32) * f(0.5) - vf
-        centre = sig(xc, yc) <= thr
-        rA, rC = f(1) / A, f(1) / Cq
-
-        def on_x(dx):
-            return sig(dx, np.fmin(y1, np.fmax(y0, -((B * dx) * rC))))
-
-        def on_y(dy):
-            return sig(np.fmin(x1, np.fmax(x0, -((B * dy) * rA))), dy)
-
-        smin = np.fmin(np.fmin(on_x(x0), on_x(x1)), np.fmin(on_y(y0), on_y(y1)))
-    return centre | inside | (smin <= thr)
+    p = m00 * m11
+    p2 = p * p
+    for dx in (x0, x1):
+        tt = -(m10 * dx)
+        on = (m11 * y0 <= tt) & (tt <= m11 * y1)
+        q = m00 * dx
+        keep |= np.where(on, q * q <= thr, (sig(dx, y0) <= thr) | (sig(dx, y1) <= thr))
+    for dy in (y0, y1):
+        tt = -(B * dy)
+        on = (A * x0 <= tt) & (tt <= A * x1)
+        keep |= np.where(on, (dy * dy) * p2 <= thr * A, (sig(x0, dy) <= thr) | (sig(x1, dy) <= thr))
+    return keep
 
 
 def tile_lists(rects, depth, n_tiles_x, tile_offset, n_total_tiles, n_per_view, keep=None):

@@ -151,41 +151,64 @@ __global__ void compact_apply_kernel(const uint2 *__restrict__ rect, const float
 
 // Does the record's alpha >= alpha_min region reach the tile?  The projection wrote the half
 // extent ex = sqrt(2 thr s00) 1.002 + 0.01 with thr = ln(o / alpha_min) + 1e-3 and
-// m00 = 1 / sqrt(2 s00), so thr' = ((ex - 0.01) / 1.002 m00)^2 recovers the threshold from the
-// record (to float rounding, far inside its 1e-3 margin).  The tile is kept when the minimum
-// of sigma = (m00 dx)^2 + (m10 dx + m11 dy)^2 over the rectangle [X0, X1] x [Y0, Y1] of its
-// pixel centres is at most thr': a tile whose centre point is inside the footprint is kept at
-// once; otherwise the minimum is 0 when the mean is inside, else the least of the four
-// clamped edge minima of the convex quadratic.  Every step is one correctly rounded float32
-// operation (reciprocals included) in a fixed order, with no contraction, so the decision
+// m00 = 1 / sqrt(2 s00), so thr' = ((ex - 0.01) (1 / 1.002) m00)^2 recovers the threshold from
+// the record (to float rounding, far inside its 1e-3 margin).  The tile is kept when
+// sigma = (m00 dx)^2 + (m10 dx + m11 dy)^2 <= thr' somewhere on the rectangle [X0, X1] x
+// [Y0, Y1] of its pixel centres: at its centre point, or the mean is inside, or on an edge.
+// On an edge dx = const the minimum over dy is (m00 dx)^2 if the minimiser -m10 dx / m11 lies
+// on the edge (m11 y0 <= -m10 dx <= m11 y1), else at a corner; on an edge dy = const it is
+// dy^2 (m00 m11)^2 / A with A = m00^2 + m10^2 (compared as dy^2 (m00 m11)^2 <= thr' A) if
+// -(m10 m11) dy lies in [A x0, A x1], else at a corner.  Every step is one correctly rounded
+// float32 operation in a fixed order, with no contraction and no division, so the decision
 // is reproducible bit for bit.
 __device__ __forceinline__ bool tile_reaches(const float4 g0, const float4 g1, float ex, int X0, int X1, int Y0,
                                              int Y1) {
     const uint32_t packed = __float_as_uint(g1.w);
     const int ui = (int)(short)(packed & 0xffffu), vi = (int)(short)(packed >> 16);
     const float m00 = g1.x, m10 = g1.y, m11 = g1.z;
-    const float A = __fadd_rn(__fmul_rn(m00, m00), __fmul_rn(m10, m10));
-    const float B = __fmul_rn(m10, m11);
-    const float Cq = __fmul_rn(m11, m11);
-    const float B2 = __fmul_rn(2.f, B);
-    auto sig = [&](float dx, float dy) {  // ((A dx) dx + ((2B) dx) dy) + (Cq dy) dy
-        return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(__fmul_rn(B2, dx), dy)),
-                         __fmul_rn(__fmul_rn(Cq, dy), dy));
+    auto sig = [&](float dx, float dy) {
+        const float p1 = __fmul_rn(m00, dx);
+        const float p2 = __fadd_rn(__fmul_rn(m10, dx), __fmul_rn(m11, dy));
+        return __fadd_rn(__fmul_rn(p1, p1), __fmul_rn(p2, p2));
     };
-    const float t = __fmul_rn(__fdiv_rn(__fsub_rn(ex, 0.01f), 1.002f), m00);
+    const float t = __fmul_rn(__fmul_rn(__fsub_rn(ex, 0x1.47ae14p-7f /* float(0.01) */), 0x1.fefa62p-1f /* float(1/1.002) */),
+                              m00);
     const float thr = __fmul_rn(t, t);
-    // the rectangle's centre first (most kept tiles are inside the footprint)
     const float xc = __fsub_rn(__fmul_rn((float)(X0 + X1 - 2 * ui), 0.5f), g0.x);
     const float yc = __fsub_rn(__fmul_rn((float)(Y0 + Y1 - 2 * vi), 0.5f), g0.y);
     if (sig(xc, yc) <= thr) return true;
     const float x0 = __fsub_rn((float)(X0 - ui), g0.x), x1 = __fsub_rn((float)(X1 - ui), g0.x);
     const float y0 = __fsub_rn((float)(Y0 - vi), g0.y), y1 = __fsub_rn((float)(Y1 - vi), g0.y);
     if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
-    const float rA = __frcp_rn(A), rC = __frcp_rn(Cq);
-    auto on_x = [&](float dx) { return sig(dx, fminf(y1, fmaxf(y0, -__fmul_rn(__fmul_rn(B, dx), rC)))); };
-    auto on_y = [&](float dy) { return sig(fminf(x1, fmaxf(x0, -__fmul_rn(__fmul_rn(B, dy), rA))), dy); };
-    const float smin = fminf(fminf(on_x(x0), on_x(x1)), fminf(on_y(y0), on_y(y1)));
-    return smin <= thr;
+    const float A = __fadd_rn(__fmul_rn(m00, m00), __fmul_rn(m10, m10));
+    const float B = __fmul_rn(m10, m11);
+    const float p = __fmul_rn(m00, m11);
+    const float p2 = __fmul_rn(p, p);
+    const float ly0 = __fmul_rn(m11, y0), ly1 = __fmul_rn(m11, y1);
+    const float lx0 = __fmul_rn(A, x0), lx1 = __fmul_rn(A, x1);
+    const float thrA = __fmul_rn(thr, A);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dx = e ? x1 : x0;
+        const float tt = -__fmul_rn(m10, dx);
+        if (ly0 <= tt && tt <= ly1) {
+            const float q = __fmul_rn(m00, dx);
+            if (__fmul_rn(q, q) <= thr) return true;
+        } else if (sig(dx, y0) <= thr || sig(dx, y1) <= thr) {
+            return true;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dy = e ? y1 : y0;
+        const float tt = -__fmul_rn(B, dy);
+        if (lx0 <= tt && tt <= lx1) {
+            if (__fmul_rn(__fmul_rn(dy, dy), p2) <= thrA) return true;
+        } else if (sig(x0, dy) <= thr || sig(x1, dy) <= thr) {
+            return true;
+        }
+    }
+    return false;
 }
 
 // The (record, tile) slots: the tiles of every depth-sorted record's rectangle, row-major,
@@ -276,7 +299,11 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
             const uint2 rc = rect[orec];
             const uint32_t q = s - s_P[k];
             const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16, tw = (rc.y & 0xffffu) - tx0;
-            const uint32_t row = q / tw;
+            // q / tw: a float estimate, corrected to the exact quotient (off by at most one
+            // while q < 2^24, i.e. for any image of at most 32767 pixels a side)
+            uint32_t row = (uint32_t)__fdividef((float)q, (float)tw);
+            while (row * tw > q) --row;
+            while ((row + 1) * tw <= q) ++row;
             const int tx = (int)(tx0 + (q - row * tw)), ty = (int)(ty0 + row);
             const int4 vw = s_vw[orec / (uint32_t)N];
             if (EMIT) {
