@@ -24,8 +24,8 @@ Pieces and the passages they follow:
 * ``tile_lists``         integer reference of the tile-instance lists: every (record, tile)
                          pair of a record's tile rectangle (optionally those that
                          ``tile_reaches_alpha_min`` keeps: a float32 rule taken from the same
-                         records on both sides), ordered by (tile, float32 depth bits, record
-                         index) (numpy lexsort).
+                         records on both sides, the ellipse's extent within each tile row),
+                         ordered by (tile, float32 depth bits, record index) (numpy lexsort).
 
 Parity pins: the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py`` tie every function
 here to closed forms, invariants, library routines and finite differences.
@@ -482,18 +482,19 @@ def tile_reaches_alpha_min(geo, ext, X0, X1, Y0, Y1):
 
     geo: (n, 8) float32 records (u_frac, v_frac, depth, opacity, m00, m10, m11, packed
     int16 (u_int, v_int)); ext: (n, 2) float32 half extents; X0..X1, Y0..Y1: the tile's
-    pixel-centre rectangle (int).  The record's alpha >= alpha_min region is
+    pixel-centre rectangle (int).  The record's alpha >= alpha_min region is the ellipse
     sigma = (m00 dx)^2 + (m10 dx + m11 dy)^2 <= thr, and the projection wrote
     ex = sqrt(2 thr s00) 1.002 + 0.01 with m00 = 1 / sqrt(2 s00), so
-    thr' = ((ex - 0.01) (1 / 1.002) m00)^2.  The tile is kept when sigma <= thr' somewhere on
-    the rectangle: at its centre point, or the mean is inside, or on one of its edges.  On an
-    edge dx = const the minimum over dy is (m00 dx)^2 when the minimiser
-    dy* = -m10 dx / m11 lies on the edge (m11 y0 <= -m10 dx <= m11 y1), else at a corner; on
-    an edge dy = const it is dy^2 (m00 m11)^2 / A (A = m00^2 + m10^2), compared as
-    dy^2 (m00 m11)^2 <= thr' A, when -(m10 m11) dy lies in [A x0, A x1], else at a corner.
-    Each step is one float32 operation with round-to-nearest in a fixed order and no
-    division, so the decision is reproducible bit for bit from the same float32 records.
-    Returns a bool array.
+    thr' = ((ex - 0.01) (1 / 1.002) m00)^2.  Within the band dy in [y0, y1] of the tile's row
+    the ellipse spans dx in [xl, xr]: with A = m00^2 + m10^2, B = m10 m11, C = m11^2 and
+    p = m00 m11 (A C - B^2 = p^2), the band is cut to |dy| <= sqrt(A thr') / p, the right
+    edge (s(dy) - B dy) / A with s = sqrt(A thr' - (p dy)^2) is largest at
+    dy = -B (sqrt(thr' C) / p) / C and the left edge (-B dy - s) / A smallest at the opposite
+    dy, each clamped to the band.  The tile is kept when its pixel-centre columns meet
+    [xl, xr]: ((X1 - u_int) - u_frac) >= xl and ((X0 - u_int) - u_frac) <= xr.  Every step is
+    one correctly rounded float32 operation (square roots and divisions included) in a fixed
+    order, so the decision is reproducible bit for bit from the same float32 records; the
+    kept tiles of a tile row are contiguous.  Returns a bool array.
     """
     f = np.float32
     geo = np.asarray(geo, np.float32)
@@ -505,34 +506,30 @@ def tile_reaches_alpha_min(geo, ext, X0, X1, Y0, Y1):
     X0, X1 = np.asarray(X0, np.int64), np.asarray(X1, np.int64)
     Y0, Y1 = np.asarray(Y0, np.int64), np.asarray(Y1, np.int64)
     m00, m10, m11 = geo[:, 4], geo[:, 5], geo[:, 6]
+    with np.errstate(all="ignore"):
+        t = ((ext[:, 0] - f(0.01)) * f(1.0 / 1.002)) * m00
+        thr = t * t
+        A = m00 * m00 + m10 * m10
+        B = m10 * m11
+        Cq = m11 * m11
+        p = m00 * m11
+        y0 = (Y0 - vi).astype(np.float32) - vf
+        y1 = (Y1 - vi).astype(np.float32) - vf
+        dymax = np.sqrt(A * thr) / p
+        yb0 = np.fmax(y0, -dymax)
+        yb1 = np.fmin(y1, dymax)
+        dxmax = np.sqrt(thr * Cq) / p
+        dyr = -((B * dxmax) / Cq)
 
-    def sig(dx, dy):
-        p1 = m00 * dx
-        p2 = m10 * dx + m11 * dy
-        return p1 * p1 + p2 * p2
+        def s_of(dy):
+            q = p * dy
+            return np.sqrt(np.fmax(A * thr - q * q, f(0)))
 
-    t = ((ext[:, 0] - f(0.01)) * f(1.0 / 1.002)) * m00
-    thr = t * t
-    xc = (X0 + X1 - 2 * ui).astype(np.float32) * f(0.5) - uf
-    yc = (Y0 + Y1 - 2 * vi).astype(np.float32) * f(0.5) - vf
-    x0 = (X0 - ui).astype(np.float32) - uf
-    x1 = (X1 - ui).astype(np.float32) - uf
-    y0 = (Y0 - vi).astype(np.float32) - vf
-    y1 = (Y1 - vi).astype(np.float32) - vf
-    keep = (sig(xc, yc) <= thr) | ((x0 <= 0) & (x1 >= 0) & (y0 <= 0) & (y1 >= 0))
-    A = m00 * m00 + m10 * m10
-    B = m10 * m11
-    p = m00 * m11
-    p2 = p * p
-    for dx in (x0, x1):
-        tt = -(m10 * dx)
-        on = (m11 * y0 <= tt) & (tt <= m11 * y1)
-        q = m00 * dx
-        keep |= np.where(on, q * q <= thr, (sig(dx, y0) <= thr) | (sig(dx, y1) <= thr))
-    for dy in (y0, y1):
-        tt = -(B * dy)
-        on = (A * x0 <= tt) & (tt <= A * x1)
-        keep |= np.where(on, (dy * dy) * p2 <= thr * A, (sig(x0, dy) <= thr) | (sig(x1, dy) <= thr))
+        dr = np.fmin(yb1, np.fmax(yb0, dyr))
+        dl = np.fmin(yb1, np.fmax(yb0, -dyr))
+        xr = (s_of(dr) - B * dr) / A
+        xl = (-(B * dl) - s_of(dl)) / A
+        keep = (yb0 <= yb1) & (((X1 - ui).astype(np.float32) - uf) >= xl) & (((X0 - ui).astype(np.float32) - uf) <= xr)
     return keep
 
 

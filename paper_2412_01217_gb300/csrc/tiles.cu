@@ -5,12 +5,12 @@
 //   1. compact:  visible records r (non-empty tile rectangle) -> (depth bits, r), in r order
 //   2. sort:     stable LSD radix sort by the 32 float32 depth bits (depths are > z_near > 0
 //                so their bit patterns order like the values); ties keep record order
-//   3. emit:     the slots are the tiles of each record's rectangle, row-major, record after
-//                record in depth order (a prefix of the rectangle sizes numbers them); a
-//                counting pass, split evenly over the slots, tests whether the record's
-//                alpha >= alpha_min region reaches each slot's tile (a float32 test of the
-//                tile's pixel-centre rectangle) and stores keep bits, and an emission pass
-//                writes (global tile id, r) for the kept slots, compacted in slot order
+//   3. emit:     the slots are the tile rows of each record's rectangle, record after
+//                record in depth order (a prefix of the row counts numbers them); for each
+//                slot the span of the record's alpha >= alpha_min region within the row (a
+//                float32 computation) gives the contiguous run of tiles it reaches; a
+//                counting pass, split evenly over the slots, and a scan give the offsets, and
+//                an emission pass writes (global tile id, r) for those tiles, row-major
 //   4. sort:     stable LSD radix sort of the instances by global tile id (only the bits
 //                n_tiles needs), which keeps the (depth, record) order inside each tile
 //   5. ranges:   [start, end) of every tile
@@ -82,10 +82,15 @@ __device__ __forceinline__ uint32_t rect_tiles(uint2 r) {
     return (tx1 > tx0 && ty1 > ty0) ? (tx1 - tx0) * (ty1 - ty0) : 0u;
 }
 
-struct SortedTileCount {  // tiles of the rectangle of the record at sorted position i
+__device__ __forceinline__ uint32_t rect_rows(uint2 r) {
+    const uint32_t ty0 = r.x >> 16, ty1 = r.y >> 16;
+    return rect_tiles(r) ? ty1 - ty0 : 0u;
+}
+
+struct SortedRowCount {  // tile rows of the rectangle of the record at sorted position i
     const uint2 *rect;
     const uint32_t *rec;
-    __device__ uint32_t operator()(int i) const { return rect_tiles(rect[rec[i]]); }
+    __device__ uint32_t operator()(int i) const { return rect_rows(rect[rec[i]]); }
 };
 
 template <class F>
@@ -149,69 +154,61 @@ __global__ void compact_apply_kernel(const uint2 *__restrict__ rect, const float
     }
 }
 
-// Does the record's alpha >= alpha_min region reach the tile?  The projection wrote the half
-// extent ex = sqrt(2 thr s00) 1.002 + 0.01 with thr = ln(o / alpha_min) + 1e-3 and
-// m00 = 1 / sqrt(2 s00), so thr' = ((ex - 0.01) (1 / 1.002) m00)^2 recovers the threshold from
-// the record (to float rounding, far inside its 1e-3 margin).  The tile is kept when
-// sigma = (m00 dx)^2 + (m10 dx + m11 dy)^2 <= thr' somewhere on the rectangle [X0, X1] x
-// [Y0, Y1] of its pixel centres: at its centre point, or the mean is inside, or on an edge.
-// On an edge dx = const the minimum over dy is (m00 dx)^2 if the minimiser -m10 dx / m11 lies
-// on the edge (m11 y0 <= -m10 dx <= m11 y1), else at a corner; on an edge dy = const it is
-// dy^2 (m00 m11)^2 / A with A = m00^2 + m10^2 (compared as dy^2 (m00 m11)^2 <= thr' A) if
-// -(m10 m11) dy lies in [A x0, A x1], else at a corner.  Every step is one correctly rounded
-// float32 operation in a fixed order, with no contraction and no division, so the decision
-// is reproducible bit for bit.
-__device__ __forceinline__ bool tile_reaches(const float4 g0, const float4 g1, float ex, int X0, int X1, int Y0,
-                                             int Y1) {
+// The columns of a tile row that the record's alpha >= alpha_min region reaches.  The
+// projection wrote the half extent ex = sqrt(2 thr s00) 1.002 + 0.01 with
+// thr = ln(o / alpha_min) + 1e-3 and m00 = 1 / sqrt(2 s00), so
+// thr' = ((ex - 0.01) (1 / 1.002) m00)^2 recovers the threshold from the record (to float
+// rounding, far inside its 1e-3 margin).  Within the band dy in [y0, y1] of the row's pixel
+// centres, the ellipse sigma = (m00 dx)^2 + (m10 dx + m11 dy)^2 <= thr' spans dx in
+// [xl, xr]: with A = m00^2 + m10^2, B = m10 m11, C = m11^2 and p = m00 m11 (A C - B^2 = p^2),
+// the band is cut to |dy| <= sqrt(A thr') / p, the right edge (s - B dy) / A with
+// s = sqrt(A thr' - (p dy)^2) is largest at dy = -B (sqrt(thr' C) / p) / C and the left edge
+// (-B dy - s) / A smallest at the opposite dy, each clamped to the band.  A tile is kept when
+// its pixel-centre columns [X0, X1] meet [xl, xr]; the kept tiles of a row are contiguous.
+// Every step is one correctly rounded float32 operation (square roots and divisions
+// included) in a fixed order with no contraction, so the decision is reproducible bit for
+// bit.  Returns false when the band misses the ellipse.
+struct RowSpan {
+    float xl, xr;  // extent of the footprint in the band, relative to the mean
+    float uf;      // fraction of the mean
+    int ui;        // integer part of the mean
+};
+__device__ __forceinline__ bool row_span(const float4 g0, const float4 g1, float ex, int Y0, int Y1, RowSpan &rs) {
     const uint32_t packed = __float_as_uint(g1.w);
-    const int ui = (int)(short)(packed & 0xffffu), vi = (int)(short)(packed >> 16);
+    rs.ui = (int)(short)(packed & 0xffffu);
+    rs.uf = g0.x;
+    const int vi = (int)(short)(packed >> 16);
     const float m00 = g1.x, m10 = g1.y, m11 = g1.z;
-    auto sig = [&](float dx, float dy) {
-        const float p1 = __fmul_rn(m00, dx);
-        const float p2 = __fadd_rn(__fmul_rn(m10, dx), __fmul_rn(m11, dy));
-        return __fadd_rn(__fmul_rn(p1, p1), __fmul_rn(p2, p2));
-    };
     const float t = __fmul_rn(__fmul_rn(__fsub_rn(ex, 0x1.47ae14p-7f /* float(0.01) */), 0x1.fefa62p-1f /* float(1/1.002) */),
                               m00);
     const float thr = __fmul_rn(t, t);
-    const float xc = __fsub_rn(__fmul_rn((float)(X0 + X1 - 2 * ui), 0.5f), g0.x);
-    const float yc = __fsub_rn(__fmul_rn((float)(Y0 + Y1 - 2 * vi), 0.5f), g0.y);
-    if (sig(xc, yc) <= thr) return true;
-    const float x0 = __fsub_rn((float)(X0 - ui), g0.x), x1 = __fsub_rn((float)(X1 - ui), g0.x);
-    const float y0 = __fsub_rn((float)(Y0 - vi), g0.y), y1 = __fsub_rn((float)(Y1 - vi), g0.y);
-    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
     const float A = __fadd_rn(__fmul_rn(m00, m00), __fmul_rn(m10, m10));
     const float B = __fmul_rn(m10, m11);
+    const float Cq = __fmul_rn(m11, m11);
     const float p = __fmul_rn(m00, m11);
-    const float p2 = __fmul_rn(p, p);
-    const float ly0 = __fmul_rn(m11, y0), ly1 = __fmul_rn(m11, y1);
-    const float lx0 = __fmul_rn(A, x0), lx1 = __fmul_rn(A, x1);
-    const float thrA = __fmul_rn(thr, A);
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float dx = e ? x1 : x0;
-        const float tt = -__fmul_rn(m10, dx);
-        if (ly0 <= tt && tt <= ly1) {
-            const float q = __fmul_rn(m00, dx);
-            if (__fmul_rn(q, q) <= thr) return true;
-        } else if (sig(dx, y0) <= thr || sig(dx, y1) <= thr) {
-            return true;
-        }
-    }
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float dy = e ? y1 : y0;
-        const float tt = -__fmul_rn(B, dy);
-        if (lx0 <= tt && tt <= lx1) {
-            if (__fmul_rn(__fmul_rn(dy, dy), p2) <= thrA) return true;
-        } else if (sig(x0, dy) <= thr || sig(x1, dy) <= thr) {
-            return true;
-        }
-    }
-    return false;
+    const float y0 = __fsub_rn((float)(Y0 - vi), g0.y), y1 = __fsub_rn((float)(Y1 - vi), g0.y);
+    const float dymax = __fdiv_rn(__fsqrt_rn(__fmul_rn(A, thr)), p);
+    const float yb0 = fmaxf(y0, -dymax), yb1 = fminf(y1, dymax);
+    if (!(yb0 <= yb1)) return false;
+    const float dxmax = __fdiv_rn(__fsqrt_rn(__fmul_rn(thr, Cq)), p);
+    const float dyr = -__fdiv_rn(__fmul_rn(B, dxmax), Cq);
+    const float At = __fmul_rn(A, thr);
+    auto s_of = [&](float dy) {
+        const float q = __fmul_rn(p, dy);
+        return __fsqrt_rn(fmaxf(__fsub_rn(At, __fmul_rn(q, q)), 0.f));
+    };
+    const float dr = fminf(yb1, fmaxf(yb0, dyr));
+    const float dl = fminf(yb1, fmaxf(yb0, -dyr));
+    rs.xr = __fdiv_rn(__fsub_rn(s_of(dr), __fmul_rn(B, dr)), A);
+    rs.xl = __fdiv_rn(__fsub_rn(-__fmul_rn(B, dl), s_of(dl)), A);
+    return true;
+}
+// does the row's footprint [xl, xr] meet the pixel-centre columns [X0, X1]?
+__device__ __forceinline__ bool span_meets(const RowSpan &rs, int X0, int X1) {
+    return __fsub_rn((float)(X1 - rs.ui), rs.uf) >= rs.xl && __fsub_rn((float)(X0 - rs.ui), rs.uf) <= rs.xr;
 }
 
-// The (record, tile) slots: the tiles of every depth-sorted record's rectangle, row-major,
+// The (record, tile row) slots: the tile rows of every depth-sorted record's rectangle,
 // record after record; P[i] is the first slot of sorted record i.  The two culling passes
 // split the S slots evenly over their Gc blocks (a multiple of 256 slots each), so that the
 // few near records with huge rectangles do not serialise one warp.
@@ -221,7 +218,7 @@ __device__ __forceinline__ uint32_t slot_block_size(uint32_t S, int Gc) {
     return (per > 0 ? per : 1u) * kScanThreads;
 }
 
-// P[i] = boff[block] + exclusive scan of the rectangle tile counts, and for every block of the
+// P[i] = boff[block] + exclusive scan of the rectangle row counts, and for every block of the
 // slot partition the record that owns its first slot.
 __global__ void slot_prefix_kernel(const uint2 *__restrict__ rect, const uint32_t *__restrict__ rec,
                                    const int *__restrict__ m_ptr, const uint32_t *__restrict__ boff, int G,
@@ -235,7 +232,7 @@ __global__ void slot_prefix_kernel(const uint2 *__restrict__ rect, const uint32_
     uint32_t run = boff[blockIdx.x];
     for (int base = beg; base < end; base += kScanThreads) {
         const int i = base + threadIdx.x;
-        const uint32_t c = i < end ? rect_tiles(rect[rec[i]]) : 0u;
+        const uint32_t c = i < end ? rect_rows(rect[rec[i]]) : 0u;
         uint32_t tot;
         const uint32_t ex = block_exclusive_scan(c, tot);
         if (i < end) {
@@ -249,21 +246,20 @@ __global__ void slot_prefix_kernel(const uint2 *__restrict__ rect, const uint32_
 
 // The culling passes over the slot partition.  Thread t of a 256-slot chunk takes slot
 // s = c0 + t: its record is found by a binary search over the prefixes of the (at most 256)
-// records that can own the chunk, staged in shared memory.
-//   COUNT: tests its pair, stores the chunk's keep bits (one 32-bit word per warp; slot
-//          ranges are 32-aligned, so every word is written by exactly one warp) and writes
-//          the block's kept total to kbsum.
-//   EMIT:  reads its keep bit and writes (global tile id, record) at kbsum[block] (the scanned
-//          block offset) plus its rank among the block's kept slots, i.e. in slot order.
+// records that can own the chunk, staged in shared memory; the row's footprint span gives
+// the contiguous run of kept tile columns.
+//   COUNT: adds up the kept tiles of the block's slots (kbsum[block]).
+//   EMIT:  writes (global tile id, record) for the kept tiles, column by column, at
+//          kbsum[block] (the scanned block offset) plus the block's exclusive scan of the
+//          kept counts, i.e. in (record, row, column) order.
 template <bool EMIT>
 __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *__restrict__ geo,
                                  const float2 *__restrict__ ext, const uint32_t *__restrict__ rec,
                                  const int *__restrict__ m_ptr, const int *__restrict__ s_ptr,
                                  const uint32_t *__restrict__ P, const uint32_t *__restrict__ first_rec, int Gc,
                                  int N, const sg_view *__restrict__ views, int n_views, int tile_w, int tile_h,
-                                 uint32_t *__restrict__ bits, uint32_t bit_words, uint32_t *__restrict__ kbsum,
-                                 uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval, int capacity,
-                                 uint32_t *__restrict__ status) {
+                                 uint32_t *__restrict__ kbsum, uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval,
+                                 int capacity, uint32_t *__restrict__ status) {
     pdl_begin();
     __shared__ uint32_t s_P[kScanThreads];
     __shared__ int s_next;
@@ -284,11 +280,9 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
         s_P[threadIdx.x] = j < n ? P[j] : 0xffffffffu;
         __syncthreads();
         const uint32_t s = (uint32_t)(c0 + threadIdx.x);
-        const bool valid = c0 + threadIdx.x < s1;
-        bool keep = false;
-        uint32_t tile = 0, orec = 0;
-        int k = 0;
-        if (valid) {
+        uint32_t cnt = 0, orec = 0, tfirst = 0;
+        int tx_a = 0, k = 0;
+        if (c0 + threadIdx.x < s1) {
             int lo = 0, hi = kScanThreads - 1;  // the last k with s_P[k] <= s (s_P[0] <= c0)
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -297,39 +291,31 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
             k = lo;
             orec = rec[ic + k];
             const uint2 rc = rect[orec];
-            const uint32_t q = s - s_P[k];
-            const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16, tw = (rc.y & 0xffffu) - tx0;
-            // q / tw: a float estimate, corrected to the exact quotient (off by at most one
-            // while q < 2^24, i.e. for any image of at most 32767 pixels a side)
-            uint32_t row = (uint32_t)__fdividef((float)q, (float)tw);
-            while (row * tw > q) --row;
-            while ((row + 1) * tw <= q) ++row;
-            const int tx = (int)(tx0 + (q - row * tw)), ty = (int)(ty0 + row);
+            const int tx0 = (int)(rc.x & 0xffffu), tx1 = (int)(rc.y & 0xffffu);
+            const int ty = (int)(rc.x >> 16) + (int)(s - s_P[k]);
             const int4 vw = s_vw[orec / (uint32_t)N];
-            if (EMIT) {
-                keep = (s >> 5) < bit_words && ((bits[s >> 5] >> (s & 31u)) & 1u);
-                tile = (uint32_t)vw.z + (uint32_t)ty * (uint32_t)vw.w + (uint32_t)tx;
-            } else {
-                const int X0 = tx * tile_w, Y0 = ty * tile_h;
-                keep = tile_reaches(geo[2 * (size_t)orec], geo[2 * (size_t)orec + 1], ext[orec].x, X0,
-                                    min(X0 + tile_w - 1, vw.x - 1), Y0, min(Y0 + tile_h - 1, vw.y - 1));
+            const int Y0 = ty * tile_h;
+            RowSpan rs;
+            if (row_span(geo[2 * (size_t)orec], geo[2 * (size_t)orec + 1], ext[orec].x, Y0,
+                         min(Y0 + tile_h - 1, vw.y - 1), rs)) {
+                // the kept columns are contiguous: skip to the first, count to the last
+                int tx = tx0;
+                while (tx < tx1 && !span_meets(rs, tx * tile_w, min(tx * tile_w + tile_w - 1, vw.x - 1))) ++tx;
+                tx_a = tx;
+                while (tx < tx1 && span_meets(rs, tx * tile_w, min(tx * tile_w + tile_w - 1, vw.x - 1))) ++tx;
+                cnt = (uint32_t)(tx - tx_a);
             }
+            tfirst = (uint32_t)vw.z + (uint32_t)ty * (uint32_t)vw.w + (uint32_t)tx_a;
         }
         if (!EMIT) {
-            const uint32_t word = __ballot_sync(SG_FULL_MASK, keep);
-            if ((threadIdx.x & 31) == 0) {
-                const uint32_t w = (uint32_t)((c0 + threadIdx.x) >> 5);
-                if (w < bit_words) bits[w] = word;
-                else if (word) overflow = true;
-            }
-            kept += keep ? 1u : 0u;
+            kept += cnt;
         } else {
             uint32_t tot;
-            const uint32_t ex = block_exclusive_scan(keep ? 1u : 0u, tot);
-            if (keep) {
-                const uint32_t g = run + ex;
+            const uint32_t ex = block_exclusive_scan(cnt, tot);
+            for (uint32_t q = 0; q < cnt; ++q) {
+                const uint32_t g = run + ex + q;
                 if (g < (uint32_t)capacity) {
-                    tkey[g] = tile;
+                    tkey[g] = tfirst + q;
                     tval[g] = orec;
                 } else {
                     overflow = true;
@@ -559,11 +545,9 @@ __global__ void ranges_kernel(const uint32_t *__restrict__ tile, const int *__re
 
 struct TileWorkspace {
     uint32_t *dkey_in, *dval_in, *dkey_out, *dval_out, *dkey_tmp, *dval_tmp;
-    uint32_t *slot0;      // first (record, tile) slot of each depth-sorted record
+    uint32_t *slot0;      // first (record, tile row) slot of each depth-sorted record
     uint32_t *first_rec;  // record owning the first slot of each block of the slot partition
     uint32_t *kbsum;      // kept instances per block of the slot partition, then their offsets
-    uint32_t *bits;       // keep bit of every slot
-    uint32_t bit_words;
     uint32_t *tkey_in, *tval_in, *tkey_tmp, *tval_tmp;
     uint32_t *bsum, *hist, *totals;
     int *counts;  // [0] visible records M, [1] K clamped
@@ -601,9 +585,7 @@ static size_t tile_ws_layout(int64_t R, int32_t cap, int G, TileWorkspace *ws, c
     w.slot0 = (uint32_t *)take(r4);
     w.first_rec = (uint32_t *)take((size_t)4 * G * 4);  // the slot partition has 4 G blocks
     w.kbsum = (uint32_t *)take((size_t)4 * G * 4);
-    // keep bits for up to twice the lists' capacity in slots (more is reported as overflow)
-    w.bit_words = (uint32_t)(((uint64_t)cap * 2 + 31) / 32);
-    w.bits = (uint32_t *)take((size_t)w.bit_words * 4);
+
     w.tkey_in = (uint32_t *)take(c4);
     w.tval_in = (uint32_t *)take(c4);
     w.tkey_tmp = (uint32_t *)take(c4);
@@ -648,22 +630,22 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     // records): its blocks own ranges of depth-sorted records, and the near (large) ones,
     // which emit most of the instances, come first.
     const int Ge = (int)std::min<int64_t>(4 * G, std::max<int64_t>(G, R / 2048));
-    // slots: the rectangle tiles of the records in depth order
+    // slots: the rectangle tile rows of the records in depth order
     const float2 *ext = reinterpret_cast<const float2 *>(proj->ext);
-    launch_pdl(scan_reduce_kernel<SortedTileCount>, Ge, kScanThreads, 0, st, SortedTileCount{rect, w.dval_out},
+    launch_pdl(scan_reduce_kernel<SortedRowCount>, Ge, kScanThreads, 0, st, SortedRowCount{rect, w.dval_out},
                w.counts + 0, 0, w.bsum, Ge);
     launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.bsum, Ge, w.counts + 2);
     const int Gc = 4 * G;  // blocks of the slot partition (each walks a few 256-slot chunks)
     launch_pdl(slot_prefix_kernel, Ge, kScanThreads, 0, st, rect, w.dval_out, w.counts + 0, w.bsum, Ge,
                w.counts + 2, Gc, w.slot0, w.first_rec);
-    // culling, evenly over the slots: keep bits and kept counts, their offsets, emission
+    // culling, evenly over the slots: kept counts, their offsets, emission
     launch_pdl(cull_pass_kernel<false>, Gc, kScanThreads, 0, st, rect, geo, ext, w.dval_out, w.counts + 0,
-               w.counts + 2, w.slot0, w.first_rec, Gc, N, views, n_views, tile_w, tile_h, w.bits, w.bit_words,
-               w.kbsum, (uint32_t *)nullptr, (uint32_t *)nullptr, lists->capacity, status);
+               w.counts + 2, w.slot0, w.first_rec, Gc, N, views, n_views, tile_w, tile_h, w.kbsum,
+               (uint32_t *)nullptr, (uint32_t *)nullptr, lists->capacity, status);
     launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.kbsum, Gc, lists->count);
     launch_pdl(cull_pass_kernel<true>, Gc, kScanThreads, 0, st, rect, geo, ext, w.dval_out, w.counts + 0,
-               w.counts + 2, w.slot0, w.first_rec, Gc, N, views, n_views, tile_w, tile_h, w.bits, w.bit_words,
-               w.kbsum, w.tkey_in, w.tval_in, lists->capacity, status);
+               w.counts + 2, w.slot0, w.first_rec, Gc, N, views, n_views, tile_w, tile_h, w.kbsum,
+               w.tkey_in, w.tval_in, lists->capacity, status);
     // 4. stable sort by tile id
     int bits = 1;
     while ((1ll << bits) < (long long)n_tiles) ++bits;
