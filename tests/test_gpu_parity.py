@@ -427,3 +427,68 @@ def test_adam_multi_matches_numpy(sizes, offset):
         assert np.allclose(bufs[2].cpu().numpy(), m, rtol=1e-5, atol=1e-7)
         assert np.allclose(bufs[3].cpu().numpy(), v, rtol=1e-5, atol=1e-9)
         assert not bufs[1].any()
+
+
+def test_tile_lists_against_the_oracles_own_projection():
+    """Independent of the kernels' records: the oracle projects in FP64, rounds its own
+    float32 records (record format of sg.h, its own float32 depth key) and builds the lists
+    with the same culling rule.  The GPU lists hold the same (tile, record) pairs except a few
+    at the boundary of an extent or of the culling rule, and each of those is harmless (no
+    pixel of the tile reaches alpha >= 1/255, by FP64 brute force); inside every tile the
+    common records come in the same (depth key, record) order."""
+    from test_oracle_pyramid_tiles import _records_f32
+    room, g, cams = room_small(n=8000, ncam=2, W=200, H=120)
+    T, levels = 8, 3
+    r, p = make(g, cams, levels=levels, tile_w=T, tile_h=T)
+    r.project(p)
+    r.build_lists()
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
+    K = r.instance_count()
+    tiles_g = r.tile[:K].cpu().numpy().view(np.uint32).astype(np.int64)
+    recs_g = r.record[:K].cpu().numpy().view(np.uint32).astype(np.int64)
+    P = oracle.P
+    N = r.N
+    ocams = oracle_cams(cams, levels)
+    prs, geo, ext, rects, dkey = [], [], [], [], []
+    for oc in ocams:
+        pr = oracle.project(g, oc)
+        gv, ev, rv = _records_f32(pr, oc, T)
+        prs.append(pr); geo.append(gv); ext.append(ev); rects.append(rv)
+        dkey.append(pr[:, P["DKEY"]].astype(np.float32))
+    geo, ext, rects, dkey = np.concatenate(geo), np.concatenate(ext), np.concatenate(rects), np.concatenate(dkey)
+    Wv = np.array([oc["W"] for oc in ocams]); Hv = np.array([oc["H"] for oc in ocams])
+    tx = [r.views_host[v].tiles_x for v in range(r.V)]
+    to = [r.views_host[v].tile_offset for v in range(r.V)]
+
+    def keep(recs, tx_, ty_):
+        v = recs // N
+        X0, Y0 = tx_ * T, ty_ * T
+        return oracle.tile_reaches_alpha_min(geo[recs], ext[recs], X0, np.minimum(X0 + T - 1, Wv[v] - 1),
+                                             Y0, np.minimum(Y0 + T - 1, Hv[v] - 1))
+
+    tiles_o, recs_o, _ = oracle.tile_lists(rects, dkey, tx, to, r.n_tiles, N, keep=keep)
+    pairs_g = set(zip(tiles_g.tolist(), recs_g.tolist()))
+    pairs_o = set(zip(tiles_o.tolist(), recs_o.tolist()))
+    assert len(pairs_g) == K  # no duplicates
+    diff = pairs_g ^ pairs_o
+    assert len(diff) <= 0.002 * len(pairs_o), (len(diff), len(pairs_o))
+    for t, rec in diff:  # boundary pairs reach no pixel
+        v = rec // N
+        pr = prs[v][rec % N]
+        loc = t - to[v]
+        X0, Y0 = (loc % tx[v]) * T, (loc // tx[v]) * T
+        xs, ys = np.meshgrid(np.arange(X0, min(X0 + T, Wv[v])) - pr[P["U"]], np.arange(Y0, min(Y0 + T, Hv[v])) - pr[P["V"]])
+        sig = 0.5 * (pr[P["CA"]] * xs * xs + 2 * pr[P["CB"]] * xs * ys + pr[P["CC"]] * ys * ys)
+        assert pr[P["OPAC"]] * np.exp(-sig).max() < 1 / 255, (t, rec)
+    # order inside every tile: the common records in the same order on both sides
+    common = pairs_g & pairs_o
+    seq_g, seq_o = {}, {}
+    for t, rec in zip(tiles_g.tolist(), recs_g.tolist()):
+        if (t, rec) in common:
+            seq_g.setdefault(t, []).append(rec)
+    for t, rec in zip(tiles_o.tolist(), recs_o.tolist()):
+        if (t, rec) in common:
+            seq_o.setdefault(t, []).append(rec)
+    assert seq_g == seq_o
+    assert len(common) > 20000
