@@ -79,6 +79,52 @@ def test_adjoint_matches_fd_with_background_and_dilation_off():
         assert w < 2e-5, (key, w)
 
 
+def rodrigues(axis, angle):
+    """Rotation matrix of angle (rad) about axis (Rodrigues' formula)."""
+    k = np.asarray(axis, np.float64) / np.linalg.norm(axis)
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * K @ K
+
+
+def test_adjoint_matches_fd_rotated_translated_camera():
+    """A general camera pose (rotation about a skew axis, non-zero translation): the chain
+    through t = R_cw mean + t_cw and through the view rotation in the EWA Jacobian is
+    checked with a rotation that is not its own transpose."""
+    g = tiny_scene(seed=13)
+    R = rodrigues([0.3, 1.0, 0.2], 0.25)
+    assert np.abs(R - R.T).max() > 0.1
+    t = np.array([0.06, -0.04, 0.12])
+    # keep the means in view: place them so that R mean + t is where tiny_scene put them
+    g["mean"] = (g["mean"] - t) @ R
+    cam = synthetic.make_camera(64, 48, 60, 60, 32, 24, R_cw=R, t_cw=t)
+    cfg = dict(alpha_min=0.0, T_min=0.0)
+    rng = np.random.default_rng(2)
+    up = (rng.normal(size=(3, 48, 64)), rng.normal(size=(48, 64)), rng.normal(size=(4, 48, 64)))
+    worst = fd_check(g, cam, cfg, up)
+    for key, w in worst.items():
+        assert w < 2e-5, (key, w)
+
+
+def test_adjoint_matches_fd_jacobian_clamped_in_y():
+    """The clamp branch of the Jacobian in y (a Gaussian below the image whose footprint
+    still reaches it) next to the x one, with fx != fy and W != H."""
+    g = tiny_scene(seed=17)
+    # t_y / t_z = 0.71 > 1.3 (H/2) / fy = 0.39; its depth differs from the x-clamped one's
+    # (2.0), so that no finite-difference step swaps the two in the depth order
+    g["mean"][0] = [0.1, 1.5, 2.1]
+    g["log_scale"][0] = np.log([0.25, 0.35, 0.3])
+    cam = synthetic.make_camera(72, 40, 62, 66, 35.5, 19.5)
+    cfg = dict(alpha_min=0.0, T_min=0.0)
+    pr = oracle.project(g, cam, cfg)
+    assert pr[0, oracle.P["CLY"]] == 1 and pr[0, oracle.P["CLX"]] == 0
+    assert pr[-1, oracle.P["CLX"]] == 1
+    rng = np.random.default_rng(3)
+    up = (rng.normal(size=(3, 40, 72)), rng.normal(size=(40, 72)), rng.normal(size=(4, 40, 72)))
+    worst = fd_check(g, cam, cfg, up)
+    for key, w in worst.items():
+        assert w < 2e-5, (key, w)
+
+
 def test_adjoint_per_pixel_default_thresholds():
     """Default alpha_min = 1/255, T_min = 1e-4: per-pixel FD, excluding pixels whose branch
     decisions differ between the +h and -h evaluations."""

@@ -66,6 +66,20 @@ def test_l1_closed_form_and_mask():
     assert oracle.l1(x, y, mask=np.zeros_like(x, bool))[0] == 0.0
 
 
+def test_level_loss_depth_term_masks_invalid_targets():
+    """Eq. 11 through level_loss: the depth L1 is the mean over pixels with a valid target
+    depth (> 0) only, and pixels without one get zero gradient (worked by hand)."""
+    r_d = np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 6.0]])
+    g_d = np.array([[0.0, 2.5, 1.0], [0.0, 5.0, 7.0]])
+    rgb = np.full((3, 2, 3), 0.5)
+    sem = np.zeros((2, 2, 3))
+    lab = np.zeros((2, 3), dtype=np.int32)
+    _, terms, grads = oracle.level_loss(rgb, r_d, sem, rgb, g_d, lab)
+    # valid: |2 - 2.5| + |3 - 1| + |5 - 5| + |6 - 7| = 3.5 over 4 pixels
+    assert terms["L_d"] == pytest.approx(0.875, rel=1e-15)
+    assert np.array_equal(grads["depth"], np.array([[0.0, -0.25, 0.25], [0.0, 0.0, -0.25]]))
+
+
 def test_cross_entropy_matches_torch():
     rng = np.random.default_rng(3)
     z = rng.normal(size=(8, 9, 11)) * 3
@@ -88,10 +102,16 @@ def test_level_loss_gradients_fd():
     r_d = rng.uniform(1, 3, size=(H, W)); g_d = np.where(rng.uniform(size=(H, W)) < 0.2, 0.0, rng.uniform(1, 3, size=(H, W)))
     r_s = rng.normal(size=(C, H, W)); lab = rng.integers(-1, K, size=(H, W))
     dec = rng.normal(size=(K, C))
-    tot, terms, grads = oracle.level_loss(r_rgb, r_d, r_s, g_rgb, g_d, lab, decoder=dec)
+    # term weights other than 1, so that a weight missing from a value or a gradient shows
+    wts = dict(w_depth=0.7, w_sem=1.3)
+    tot, terms, grads = oracle.level_loss(r_rgb, r_d, r_s, g_rgb, g_d, lab, decoder=dec, **wts)
     assert tot == pytest.approx(terms["L_r"] + terms["L_d"] + terms["L_s"])
+    # each weighted term is its weight times the unweighted term
+    _, t1, _ = oracle.level_loss(r_rgb, r_d, r_s, g_rgb, g_d, lab, decoder=dec)
+    assert terms["L_d"] == pytest.approx(0.7 * t1["L_d"], rel=1e-14)
+    assert terms["L_s"] == pytest.approx(1.3 * t1["L_s"], rel=1e-14)
     h = 1e-6
-    f = lambda a, b, c, d: oracle.level_loss(a, b, c, g_rgb, g_d, lab, decoder=d)[0]
+    f = lambda a, b, c, d: oracle.level_loss(a, b, c, g_rgb, g_d, lab, decoder=d, **wts)[0]
     for name, arr, idx in [("rgb", r_rgb, 0), ("depth", r_d, 1), ("sem", r_s, 2), ("decoder", dec, 3)]:
         for _ in range(15):
             ix = tuple(rng.integers(0, s) for s in arr.shape)
@@ -109,9 +129,10 @@ def test_paper_mode_semantic_loss_fd():
     H, W = 11, 13
     r_s = rng.uniform(size=(3, H, W)); g_s = rng.uniform(size=(3, H, W))
     r_rgb = rng.uniform(size=(3, H, W)); r_d = rng.uniform(1, 2, size=(H, W))
-    tot, terms, grads = oracle.level_loss(r_rgb, r_d, r_s, r_rgb, r_d, g_s, sem_mode="paper")
+    kw = dict(sem_mode="paper", lambda_r=0.35, lambda_s=0.15, w_sem=1.25)   # lambda_r != lambda_s
+    tot, terms, grads = oracle.level_loss(r_rgb, r_d, r_s, r_rgb, r_d, g_s, **kw)
     l1 = np.abs(r_s - g_s).mean()
-    assert terms["L_s"] == pytest.approx(0.8 * l1 + 0.2 * (1 - oracle.ssim(r_s, g_s)))
+    assert terms["L_s"] == pytest.approx(1.25 * (0.85 * l1 + 0.15 * (1 - oracle.ssim(r_s, g_s))))
     assert terms["L_r"] == pytest.approx(0.0, abs=1e-12) and terms["L_d"] == 0.0
     h = 1e-6
     for _ in range(10):
@@ -119,6 +140,6 @@ def test_paper_mode_semantic_loss_fd():
         sp, sm = r_s.copy(), r_s.copy()
         sp[ix] += h
         sm[ix] -= h
-        fd = (oracle.level_loss(r_rgb, r_d, sp, r_rgb, r_d, g_s, sem_mode="paper")[0]
-              - oracle.level_loss(r_rgb, r_d, sm, r_rgb, r_d, g_s, sem_mode="paper")[0]) / (2 * h)
+        fd = (oracle.level_loss(r_rgb, r_d, sp, r_rgb, r_d, g_s, **kw)[0]
+              - oracle.level_loss(r_rgb, r_d, sm, r_rgb, r_d, g_s, **kw)[0]) / (2 * h)
         assert grads["sem"][ix] == pytest.approx(fd, rel=1e-5, abs=1e-9)

@@ -85,6 +85,52 @@ def test_ewa_matches_numerical_jacobian_off_axis():
         assert pr[P["U"]] == pytest.approx(uv[0]) and pr[P["V"]] == pytest.approx(uv[1])
 
 
+def test_ewa_clamped_jacobian_is_the_jacobian_at_the_clamped_point():
+    """Reading of the support rules: the Jacobian of Eq. 3 is taken at the mean with t_x/t_z
+    clamped to +-1.3 (W/2)/fx and t_y/t_z to +-1.3 (H/2)/fy.  So Sigma2D = A Sigma A^T + bI
+    with A the numerical Jacobian of the pinhole map at the world point whose camera
+    coordinates are the clamped ones.  A camera with fx != fy and W != H tells the two
+    limits apart; means inside, beyond one limit and beyond both are all checked."""
+    a = 0.3
+    R = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    t0 = np.array([0.1, -0.2, 0.3])
+    cam = synthetic.make_camera(160, 90, 120.0, 150.0, 79.5, 44.5, R_cw=R, t_cw=t0)
+    limx, limy = 1.3 * 80 / 120.0, 1.3 * 45 / 150.0
+    rng = np.random.default_rng(8)
+    seen = set()
+    for rx, ry in [(0.2, 0.1), (0.78, 0.1), (-1.1, 0.2), (0.3, 0.36), (0.1, -0.5), (0.3, 0.6),
+                   (1.0, -0.7), (-0.95, 0.45)]:
+        tz = rng.uniform(1.5, 3.0)
+        tc = np.array([rx * tz, ry * tz, tz])
+        mu = R.T @ (tc - t0)
+        s = rng.uniform(math.log(0.01), math.log(0.1), 3)
+        q = rng.normal(size=4)
+        pr = oracle.project(one(mu, s, q), cam, dict(dilation=0.3))[0]
+        cx_, cy_ = abs(rx) > limx, abs(ry) > limy
+        assert (pr[P["CLX"]], pr[P["CLY"]]) == (cx_, cy_), (rx, ry)
+        seen.add((cx_, cy_))
+        tcl = np.array([np.clip(rx, -limx, limx) * tz, np.clip(ry, -limy, limy) * tz, tz])
+        mcl = R.T @ (tcl - t0)
+        h = 1e-6
+        A = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3); e[k] = h
+            A[:, k] = (_pinhole(cam, mcl + e) - _pinhole(cam, mcl - e)) / (2 * h)
+        qn = q / np.linalg.norm(q)
+        w, x, y, z = qn
+        Rq = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                       [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                       [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+        S2 = A @ (Rq @ np.diag(np.exp(2 * s)) @ Rq.T) @ A.T + 0.3 * np.eye(2)
+        assert pr[P["S00"]] == pytest.approx(S2[0, 0], rel=1e-6), (rx, ry)
+        assert pr[P["S11"]] == pytest.approx(S2[1, 1], rel=1e-6), (rx, ry)
+        assert pr[P["S01"]] == pytest.approx(S2[0, 1], rel=1e-6, abs=1e-9 * abs(S2).max()), (rx, ry)
+        # the 2D mean is the unclamped projection
+        uv = _pinhole(cam, mu)
+        assert pr[P["U"]] == pytest.approx(uv[0]) and pr[P["V"]] == pytest.approx(uv[1])
+    assert seen == {(False, False), (True, False), (False, True), (True, True)}
+
+
 def test_quaternion_sign_and_scale_invariance():
     g = synthetic.cloud_scene(50, 4, seed=9)
     cam = synthetic.cloud_camera()
@@ -101,6 +147,26 @@ def test_near_plane_and_tiny_opacity_cull():
     assert oracle.project(one([0, 0, 0.2001], [-3] * 3), cam)[0][P["VALID"]] == 1
     # o = sigmoid(-6) < 1/255: can never reach the skip threshold
     assert oracle.project(one([0, 0, 2.0], [-3] * 3, logit=-6.0), cam)[0][P["VALID"]] == 0
+
+
+def test_depth_key_is_camera_depth_to_float32_rounding():
+    """The ordering key of the sorted set N (Eq. 7-9) is the camera-space depth t_z, taken in
+    float32: for a general pose it lies within the rounding bound of a five-operation float32
+    evaluation (inputs rounded, three products, three sums) of t_z = R20 x + R21 y + R22 z + t_z0,
+    so two Gaussians whose depths differ by more than twice the bound are keyed in depth order."""
+    rng = np.random.default_rng(6)
+    a = 0.5
+    R = np.array([[1, 0, 0], [0, math.cos(a), -math.sin(a)], [0, math.sin(a), math.cos(a)]]) @ \
+        np.array([[math.cos(0.3), 0, math.sin(0.3)], [0, 1, 0], [-math.sin(0.3), 0, math.cos(0.3)]])
+    t0 = np.array([0.3, -0.2, 0.7])
+    cam = synthetic.make_camera(64, 48, 60, 60, 32, 24, R_cw=R, t_cw=t0)
+    u = 2.0 ** -24
+    for _ in range(200):
+        m = rng.uniform(-3, 3, 3)
+        tz = R[2] @ m + t0[2]
+        key = oracle.project(one(m, [-3] * 3), cam)[0][P["DKEY"]]
+        bound = 8 * u * (np.abs(R[2] * m).sum() + abs(t0[2]))
+        assert abs(key - tz) <= bound, (m, key, tz)
 
 
 def test_extents_are_exact_bounds():

@@ -39,6 +39,17 @@ def test_level_cameras_keep_pixel_centres_consistent():
     assert [c["W"] for c in cams] == [64, 32, 16] and [c["H"] for c in cams] == [48, 24, 12]
 
 
+def test_level_camera_sizes_match_the_downsampled_images_for_odd_sizes():
+    """157 x 91 -> 78 x 45 -> 39 x 22 (floor at every level, worked by hand), and every
+    level's camera has exactly the size of its image in the target pyramid."""
+    cam = synthetic.make_camera(157, 91, 140.0, 140.0, 77.7, 44.6)
+    cams = oracle.level_cameras(cam, 3)
+    assert [(c["W"], c["H"]) for c in cams] == [(157, 91), (78, 45), (39, 22)]
+    pyr = oracle.build_pyramid(np.zeros((3, 91, 157)), np.ones((91, 157)), np.zeros((91, 157), np.int32), 3)
+    for c, (rgb, depth, label) in zip(cams, pyr):
+        assert rgb.shape == (3, c["H"], c["W"]) and depth.shape == label.shape == (c["H"], c["W"])
+
+
 def test_downsample_rules():
     rgb = np.arange(3 * 4 * 6, dtype=float).reshape(3, 4, 6)
     depth = np.array([[1, 0, 2, 2, 0, 0], [3, 0, 2, 2, 0, 0], [0, 0, 1, 5, 4, 4], [0, 0, 1, 1, 4, 4]], float)

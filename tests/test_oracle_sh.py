@@ -86,6 +86,25 @@ def test_view_colour_depends_on_camera_centre_only():
     np.testing.assert_allclose(col, exp, atol=1e-13)
 
 
+def test_view_direction_is_the_camera_ray():
+    """For a general pose the unit view direction d is the camera-space position of the mean
+    (R_cw mean + t_cw), normalised and rotated back to the world frame, and |mean - c| is its
+    length: the camera centre is the point the pose maps to the camera origin."""
+    g = {k: np.asarray(v, np.float64) for k, v in synthetic.cloud_scene(40, 4, seed=3).items()}
+    g["sh"] = np.zeros((40, 3, 3))
+    a, b = 0.35, -0.6
+    Rz = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1]])
+    Rx = np.array([[1, 0, 0], [0, np.cos(b), -np.sin(b)], [0, np.sin(b), np.cos(b)]])
+    R = Rz @ Rx
+    t = np.array([0.4, -0.25, 1.1])
+    cam = synthetic.make_camera(64, 48, 60, 60, 32, 24, R_cw=R, t_cw=t)
+    d, n, _ = oracle.view_basis(g, cam)
+    tc = g["mean"] @ R.T + t
+    nc = np.linalg.norm(tc, axis=1)
+    np.testing.assert_allclose(n, nc, rtol=1e-13)
+    np.testing.assert_allclose(d, (tc / nc[:, None]) @ R, atol=1e-13)
+
+
 def test_zero_sh_is_degree_zero():
     g = {k: np.asarray(v, np.float64) for k, v in synthetic.cloud_scene(60, 4, seed=2).items()}
     cam = synthetic.make_camera(32, 24, 30, 30, 16, 12)
