@@ -65,6 +65,9 @@ MUTANTS = [
     ("comp_background_not_weighted_by_T", "sg_oracle.c", "acc[ch] + T * cfg.bg[ch];", "acc[ch] + cfg.bg[ch];"),
     ("comp_extent_filter_too_tight", "sg_oracle.c", "if (fabs(dx) > p[P_EXTX] || fabs(dy) > p[P_EXTY]) continue;",
      "if (fabs(dx) > 0.5 * p[P_EXTX] || fabs(dy) > p[P_EXTY]) continue;"),
+    ("comp_candidates_prefiltered_too_tight", "sg_oracle.c", "if (alpha < cfg->alpha_min * 0.5) continue;",
+     "if (alpha < cfg->alpha_min * 2.0) continue;"),
+    ("comp_transmittance_update", "sg_oracle.c", "        T = Tn;\n", "        T = T * c->alpha;\n"),
     # ---- adjoint (Sec. III-D) ----
     ("bwd_dalpha_missing_T", "sg_oracle.c", "dalpha *= Ti;", "dalpha *= 1.0;"),
     ("bwd_suffix_not_attenuated", "sg_oracle.c", "A[ch] = al * f[ch] + (1.0 - al) * A[ch];",
@@ -101,6 +104,11 @@ MUTANTS = [
      "gt[2] += gJ[5] * (2.0 * fy * t[0] / tz3);"),
     ("bwd_isotropic_depth_uses_fx_for_y", "sg_oracle.c", "- gS11 * 2.0 * fy * fy * r * r / tz3",
      "- gS11 * 2.0 * fx * fx * r * r / tz3"),
+    ("bwd_conic_inverse_wrong_entry", "sg_oracle.c", "double gS00 = -(a * a * ga + a * b * gb + b * b * gc);",
+     "double gS00 = -(a * a * ga + a * b * gb + b * c * gc);"),
+    ("bwd_symmetric_gradient_not_halved", "sg_oracle.c", "double G[4] = {gS00, 0.5 * gS01, 0.5 * gS01, gS11};",
+     "double G[4] = {gS00, gS01, gS01, gS11};"),
+    ("bwd_dconic_a_factor", "sg_oracle.c", "gsig * 0.5 * dx * dx,", "gsig * dx * dx,"),
     # ---- SSIM (Eq. 10, 12) ----
     ("ssim_C1_for_C2", "sg_oracle.c", "A2 = 2 * sxy + C2;", "A2 = 2 * sxy + C1;"),
     ("ssim_window_sigma", "sg_oracle.c", "/ (2.0 * 1.5 * 1.5));", "/ (2.0 * 1.5));"),
@@ -111,6 +119,8 @@ MUTANTS = [
      "double ds_dmx = 2 * my * A2 / (B1 * B2);"),
     ("ssim_mean_over_one_channel", "sg_oracle.c", "double norm = 1.0 / ((double)nch * (double)P);",
      "double norm = 1.0 / (double)P;"),
+    ("ssim_window_product_index", "sg_oracle.c", "double w = g1[i + 5] * g1[j + 5];\n                        double xv",
+     "double w = g1[i + 5] * g1[i + 5];\n                        double xv"),
     # ---- pyramid (Eq. 4-6) ----
     ("pyr_principal_point_no_half_pixel", "__init__.py", 'cx=(p["cx"] - 0.5) / 2,', 'cx=p["cx"] / 2,'),
     ("pyr_depth_mean_over_invalid", "__init__.py", "(d * valid).sum(axis=(1, 3)) / np.maximum(cnt, 1)",
@@ -132,6 +142,8 @@ MUTANTS = [
     ("loss_rgb_ssim_gradient_sign", "__init__.py", "g_rgb = (1 - lambda_r) * g_l1 - lambda_r * g_s",
      "g_rgb = (1 - lambda_r) * g_l1 + lambda_r * g_s"),
     ("loss_ce_label_zero_ignored", "__init__.py", "valid = lab >= 0", "valid = lab > 0"),
+    ("loss_ce_without_max_shift_in_log", "__init__.py", "logp = z - zmax - np.log(ssum)", "logp = z - np.log(ssum)"),
+    ("loss_l1_mask_count", "__init__.py", "n = int(mask.sum())", "n = mask.size"),
     # ---- SH colour and semantic features (Sec. III-B) ----
     ("sh_l1_without_condon_shortley", "__init__.py", "out += [-c1 * y, c1 * z, -c1 * x]",
      "out += [c1 * y, c1 * z, c1 * x]"),
@@ -146,6 +158,7 @@ MUTANTS = [
     ("sh_l3_gradient_entry", "__init__.py", "(f * y * z, f * x * z, f * x * y)", "(f * y * z, f * x * z, f * x * z)"),
     ("sh_mean_gradient_not_divided_by_distance", "__init__.py", 'out["mean"] += gdir / sh_n[:, None]',
      'out["mean"] += gdir'),
+    ("sh_adjoint_overwrites_colour_part", "__init__.py", "w += np.einsum(\"nkc,nc->nk\"", "w = w * 0 + np.einsum(\"nkc,nc->nk\""),
     # ---- tile lists ----
     ("tiles_record_before_depth", "__init__.py", "order = np.lexsort((recs, dbits, tiles))",
      "order = np.lexsort((dbits, recs, tiles))"),
@@ -154,11 +167,14 @@ MUTANTS = [
      "xl = ((B * dl) - s_of(dl)) / A"),
     ("tiles_culling_extreme_point_sign", "__init__.py", "dyr = -((B * dxmax) / Cq)", "dyr = ((B * dxmax) / Cq)"),
     ("tiles_culling_band_lower_edge", "__init__.py", "yb0 = np.fmax(y0, -dymax)", "yb0 = np.fmax(y0, dymax)"),
+    ("tiles_rectangle_row_past_end", "__init__.py", "for ty in range(ty0, ty1):", "for ty in range(ty0, ty1 + 1):"),
+    ("tiles_culling_band_test_dropped", "__init__.py", "keep = (yb0 <= yb1) & ", "keep = "),
     # ---- learned-initializer MLP ----
     ("mlp_relu_mask_wrong_layer", "mlp.py", "dH1 = r((dH2 @ W2) * (H1 > 0))", "dH1 = r((dH2 @ W2) * (H2 > 0))"),
     ("mlp_weight_gradient_transposed", "mlp.py", "W2=dH2.T @ H1", "W2=H1.T @ dH2"),
     ("mlp_second_layer_weight_transposed", "mlp.py", "H2 = r(np.maximum(H1 @ W2.T + b2, 0.0))",
      "H2 = r(np.maximum(H1 @ W2 + b2, 0.0))"),
+    ("mlp_bias_after_relu", "mlp.py", "H1 = r(np.maximum(X @ W1.T + b1, 0.0))", "H1 = r(np.maximum(X @ W1.T, 0.0) + b1)"),
     ("mlp_loss_weight_missing_in_gradient", "mlp.py", "dY = r(2.0 * w[None] * (Y - T) / B)",
      "dY = r(2.0 * (Y - T) / B)"),
 ]
