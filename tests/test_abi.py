@@ -98,3 +98,27 @@ def test_timeout_probe_validates_on_the_host():
     buf = (C.c_uint16 * 64)()
     fbuf = (C.c_float * 64)()
     assert lib.sg_gemm_bf16_timeout_probe(buf, 64, buf, 64, 128, 32, 64, fbuf, 32, 0, None, None) == 1
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """Without the compiled library the package raises; there is no CPU or eager fallback."""
+    from paper_2412_01217_gb300 import _build, _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "absent" / "libsg.so"))
+    with pytest.raises(RuntimeError, match="libsg.so not found"):
+        _lib.load(build_if_missing=False)
+
+
+def test_product_package_never_imports_the_oracle():
+    """The oracle is test infrastructure: no module of the product package imports it."""
+    pkg = os.path.join(ROOT, "paper_2412_01217_gb300")
+    pat = re.compile(r"^\s*(from\s+oracle\b|import\s+oracle\b|from\s+\.\.\s*oracle|.*importlib.*oracle)", re.M)
+    checked = 0
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not pat.search(text), f
+                assert "sg_oracle" not in text, f
+                checked += 1
+    assert checked > 10
