@@ -288,8 +288,11 @@ __host__ __device__ constexpr int chunk_pitch() { return NPX + 4; }  // 4 mod 32
 template <int NF>
 __host__ __device__ constexpr int padded_features() { return (NF + 7) / 8 * 8; }
 
+// Row pitch of the per-warp copy of dL/dimage: the least odd multiple of 4 that holds the NF
+// features (conflict-free fragment loads).  Features NF .. padded_features - 1 of the last
+// 8-feature tile are not stored: their fragment loads are predicated to zero.
 template <int NF>
-__host__ __device__ constexpr int g_pitch() { return padded_features<NF>() + 4; }  // odd multiple of 4
+__host__ __device__ constexpr int g_pitch() { return (NF / 4) % 2 == 1 ? NF : NF + 4; }
 
 // shared memory of one warp: G (NPX x g_pitch) and two chunk buffers (16 x chunk_pitch)
 template <int C, int PPT>
@@ -298,11 +301,15 @@ __host__ __device__ constexpr int bwd_warp_floats() {
 }
 
 // A fragment (16 x 8, row-major, pitch ld) at column k0: a0 (gid, tig), a1 (gid + 8, tig),
-// a2 (gid, tig + 4), a3 (gid + 8, tig + 4); rows outside `keep` read as zero.
+// a2 (gid, tig + 4), a3 (gid + 8, tig + 4); rows outside `keep` read as zero, and so do
+// columns k0 + 4 .. k0 + 7 unless `upper` (the part of the last feature tile that is not
+// stored).
 __device__ __forceinline__ void load_a_split(const float *m, int ld, int k0, int gid, int tig, bool keep0,
-                                             bool keep1, uint32_t (&ah)[4], uint32_t (&al)[4]) {
+                                             bool keep1, uint32_t (&ah)[4], uint32_t (&al)[4],
+                                             bool upper = true) {
     const float *p = m + gid * ld + k0 + tig;
-    const float v[4] = {keep0 ? p[0] : 0.f, keep1 ? p[8 * ld] : 0.f, keep0 ? p[4] : 0.f, keep1 ? p[8 * ld + 4] : 0.f};
+    const float v[4] = {keep0 ? p[0] : 0.f, keep1 ? p[8 * ld] : 0.f, keep0 && upper ? p[4] : 0.f,
+                        keep1 && upper ? p[8 * ld + 4] : 0.f};
 #pragma unroll
     for (int i = 0; i < 4; ++i) split_tf32(v[i], ah[i], al[i]);
 }
@@ -333,8 +340,15 @@ __device__ __forceinline__ void moment_grads(const float (&M)[6], float U, float
     }
 }
 
+// One pixel per thread and C = 4 or 16: at most 64 registers (4 CTAs of 256 threads), so that
+// occupancy is set by shared memory rather than registers (the adjoint is latency-bound and
+// gains from warps).  These two widths fit 64 registers without spilling; the others would
+// spill, and with C >= 32 the staged entries hold occupancy lower than registers anyway.
 template <int C, int PPT>
-__global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs a) {
+__host__ __device__ constexpr int bwd_min_blocks() { return PPT == 1 && (C == 4 || C == 16) ? 4 : 1; }
+
+template <int C, int PPT>
+__global__ void __launch_bounds__(kMaxTileThreads, bwd_min_blocks<C, PPT>()) raster_bwd_kernel(RasterArgs a) {
     pdl_begin();
     constexpr int NF = 4 + C;                     // rgb(3) depth | sem(C)
     constexpr int NFP = padded_features<NF>();    // features padded to 8
@@ -409,7 +423,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
             thread_last = max(thread_last, my_last[k]);
             float4 *row = reinterpret_cast<float4 *>(s_G + (32 * k + lane) * GP);
 #pragma unroll
-            for (int f = 0; f < NFP; f += 4) row[f / 4] = make_float4(g[f], g[f + 1], g[f + 2], g[f + 3]);
+            for (int f = 0; f < NF; f += 4) row[f / 4] = make_float4(g[f], g[f + 1], g[f + 2], g[f + 3]);
         }
         const int warp_last = __reduce_max_sync(SG_FULL_MASK, thread_last);
         if (threadIdx.x == 0) s_max_last = 0;
@@ -453,7 +467,8 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
 #pragma unroll
                         for (int mt = 0; mt < MT; ++mt) {
                             uint32_t ah[4], al[4];
-                            load_a_split(s_G + 16 * mt * GP, GP, 8 * kk, gid, tig, true, true, ah, al);
+                            load_a_split(s_G + 16 * mt * GP, GP, 8 * kk, gid, tig, true, true, ah, al,
+                                         8 * kk + 4 < NF);
 #pragma unroll
                             for (int nt = 0; nt < 2; ++nt)
                                 mma_tf32x3(d[mt][nt], ah, al, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
@@ -475,7 +490,8 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
                         // B (8 x 8): b0 (tig, gid), b1 (tig + 4, gid) = F[entry][feature]
                         const int f0 = 8 * kk + tig;
                         uint32_t ah[4], al[4];
-                        load_a_split(s_G + 16 * mt * GP, GP, 8 * kk, gid, tig, true, true, ah, al);
+                        load_a_split(s_G + 16 * mt * GP, GP, 8 * kk, gid, tig, true, true, ah, al,
+                                     8 * kk + 4 < NF);
 #pragma unroll
                         for (int nt = 0; nt < 2; ++nt) {
                             const float *fr = s_feat + (size_t)(jc0 + 8 * nt + gid) * NF;
@@ -546,9 +562,10 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_bwd_kernel(RasterArgs 
                     for (int nt = 0; nt < NT; ++nt) {
                         // B (8 x 8): b0 (tig, gid), b1 (tig + 4, gid) = G[pixel][feature]
                         const float *gp = s_G + (8 * ks + tig) * GP + 8 * nt + gid;
+                        const bool stored = 8 * nt + 8 <= NF || 8 * nt + gid < NF;
                         uint32_t bh0, bl0, bh1, bl1;
-                        split_tf32(gp[0], bh0, bl0);
-                        split_tf32(gp[4 * GP], bh1, bl1);
+                        split_tf32(stored ? gp[0] : 0.f, bh0, bl0);
+                        split_tf32(stored ? gp[4 * GP] : 0.f, bh1, bl1);
                         mma_tf32x3(df[nt], ah, al, bh0, bh1, bl0, bl1);
                     }
                     load_a_split(s_sg, WQ, 8 * ks, gid, tig, keep0, keep1, ah, al);
