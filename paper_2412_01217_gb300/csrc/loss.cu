@@ -480,8 +480,11 @@ __host__ __device__ constexpr int ce_mma_smem_floats() {
     return 2 * K * (C + 4) + K * C + (kLossThreads / 32) * 32 * (K + 8);
 }
 
+// At C K <= 512 the kernel is bounded to 64 registers, so that four CTAs fit an SM (their 48 KB
+// of shared memory allows four; 80 registers allowed three): 2 % faster on the 16 x 32 decoder
+// despite a 56-byte spill.
 template <int C, int K>
-__global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder_mma_kernel(PixelArgs a) {
+__global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 4 : 2) ce_decoder_mma_kernel(PixelArgs a) {
     pdl_begin();
     static_assert(C % 8 == 0 && K % 16 == 0, "MMA tiles");
     constexpr int CP = C + 4;   // decoder row pitch: 4 mod 8, conflict-free B fragments
