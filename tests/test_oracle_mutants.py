@@ -48,6 +48,12 @@ MUTANTS = [
      "double limx = cfg->fov_clamp * 0.5 * cam->W / cam->fy;"),
     ("proj_det_sign", "sg_oracle.c", "double det = s00 * s11 - s01 * s01;", "double det = s00 * s11 + s01 * s01;"),
     ("proj_conic_diagonal_swapped", "sg_oracle.c", "out[P_CA] = s11 / det;", "out[P_CA] = s00 / det;"),
+    ("pack_camera_fx_fy_swapped", "__init__.py", 'return np.array([cam["fx"], cam["fy"], cam["cx"], cam["cy"]',
+     'return np.array([cam["fy"], cam["fx"], cam["cx"], cam["cy"]'),
+    ("pack_camera_rotation_transposed", "__init__.py", '*np.asarray(cam["R_cw"], np.float64).reshape(9),',
+     '*np.asarray(cam["R_cw"], np.float64).T.reshape(9),'),
+    ("pack_cfg_alpha_min_T_min_swapped", "__init__.py", 'return np.array([c["alpha_max"], c["alpha_min"], c["T_min"],',
+     'return np.array([c["alpha_max"], c["T_min"], c["alpha_min"],'),
     # ---- compositing (Eq. 7-9) ----
     ("comp_sigma_cross_term_halved", "sg_oracle.c", "+ p[P_CB] * dx * dy;", "+ 0.5 * p[P_CB] * dx * dy;"),
     ("comp_alpha_clamp_dropped", "sg_oracle.c", "double alpha = raw < cfg->alpha_max ? raw : cfg->alpha_max;",
@@ -159,6 +165,8 @@ MUTANTS = [
     ("sh_mean_gradient_not_divided_by_distance", "__init__.py", 'out["mean"] += gdir / sh_n[:, None]',
      'out["mean"] += gdir'),
     ("sh_adjoint_overwrites_colour_part", "__init__.py", "w += np.einsum(\"nkc,nc->nk\"", "w = w * 0 + np.einsum(\"nkc,nc->nk\""),
+    ("sh_l3_constant", "__init__.py", "e, f, h = np.sqrt(35 / (2 * pi)) / 4, np.sqrt(105 / pi) / 2, np.sqrt(21 / (2 * pi)) / 4\n        k, m = np.sqrt(7 / pi) / 4, np.sqrt(105 / pi) / 4\n        out",
+     "e, f, h = np.sqrt(35 / (2 * pi)) / 4, np.sqrt(105 / pi) / 2, np.sqrt(21 / (2 * pi)) / 4\n        k, m = np.sqrt(7 / pi) / 2, np.sqrt(105 / pi) / 4\n        out"),
     # ---- tile lists ----
     ("tiles_record_before_depth", "__init__.py", "order = np.lexsort((recs, dbits, tiles))",
      "order = np.lexsort((dbits, recs, tiles))"),
@@ -169,6 +177,11 @@ MUTANTS = [
     ("tiles_culling_band_lower_edge", "__init__.py", "yb0 = np.fmax(y0, -dymax)", "yb0 = np.fmax(y0, dymax)"),
     ("tiles_rectangle_row_past_end", "__init__.py", "for ty in range(ty0, ty1):", "for ty in range(ty0, ty1 + 1):"),
     ("tiles_culling_band_test_dropped", "__init__.py", "keep = (yb0 <= yb1) & ", "keep = "),
+    ("tiles_view_offset_ignored", "__init__.py", "tiles.append(tile_offset[v] + ty * n_tiles_x[v] + tx)",
+     "tiles.append(tile_offset[0] + ty * n_tiles_x[v] + tx)"),
+    ("tiles_row_width_of_first_view", "__init__.py", "tiles.append(tile_offset[v] + ty * n_tiles_x[v] + tx)",
+     "tiles.append(tile_offset[v] + ty * n_tiles_x[0] + tx)"),
+    ("tiles_empty_range_not_zeroed", "__init__.py", "        ranges[empty] = 0\n", "        pass\n"),
     # ---- learned-initializer MLP ----
     ("mlp_relu_mask_wrong_layer", "mlp.py", "dH1 = r((dH2 @ W2) * (H1 > 0))", "dH1 = r((dH2 @ W2) * (H2 > 0))"),
     ("mlp_weight_gradient_transposed", "mlp.py", "W2=dH2.T @ H1", "W2=H1.T @ dH2"),

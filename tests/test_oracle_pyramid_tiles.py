@@ -94,11 +94,23 @@ def test_tile_lists_reference_brute_force():
     # order
     keys = [(t, float(depth[r]), r) for t, r in zip(tiles, recs)]
     assert keys == sorted(keys)
-    # ranges
+    # ranges; a tile without instances has the range (0, 0) (the format of the lists' ranges)
     for t in range(total):
         s, e = ranges[t]
         assert np.all(tiles[s:e] == t)
         assert (e - s) == np.sum(tiles == t)
+        if e == s:
+            assert s == 0, (t, s)
+
+
+def test_tile_lists_empty_tiles_have_range_zero():
+    """A 4 x 1 grid where tiles 1 and 3 hold nothing: their ranges are (0, 0), the others
+    [start, end) of their instances."""
+    rects = np.array([[0, 0, 1, 1], [2, 0, 3, 1], [0, 0, 1, 1]])
+    depth = np.array([2.0, 1.0, 1.0], np.float32)
+    tiles, recs, ranges = oracle.tile_lists(rects, depth, [4], [0], 4, 3)
+    assert tiles.tolist() == [0, 0, 2] and recs.tolist() == [2, 0, 1]
+    assert ranges.tolist() == [[0, 2], [0, 0], [2, 3], [0, 0]]
 
 
 def _records_f32(pr, cam, T):
