@@ -156,11 +156,21 @@ KERNEL_SOURCES = ["paper_2412_01217_gb300/csrc/raster_impl.cuh", "paper_2412_012
                   "paper_2412_01217_gb300/csrc/sg_common.cuh"]
 
 
+def _code_only(text):
+    """Source text without comments and blank lines (a comment edit leaves the hash alone)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def kernel_source_sha():
+    """Hash of the compositing kernels' code (comments excluded), recorded beside every
+    profile whose counters the benchmark reuses."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

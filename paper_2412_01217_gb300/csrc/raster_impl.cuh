@@ -8,7 +8,7 @@
 // atomic work counter.  Each warp owns an 8 x (4 PPT) pixel sub-tile: lane l has the PPT
 // pixels (l mod 8, l div 8 + 4k), k < PPT.  A whole warp skips a Gaussian whose footprint
 // misses its sub-tile (one uniform test), and with PPT > 1 every per-Gaussian cost
-// (shared-memory loads, the warp reduction of the backward) is shared by PPT pixels.
+// (shared-memory loads, the per-chunk contractions of the backward) is shared by PPT pixels.
 //
 // Forward: the tile's depth-sorted list is walked in batches the CTA stages into shared
 // memory; each pixel composites front to back and stops when T would fall below T_min;
@@ -17,12 +17,12 @@
 //
 // Backward: back to front from the tile's largest `last`.  Each pixel rebuilds T by
 // dividing by (1 - alpha) and tracks only the scalar a = g . A of the background-weighted
-// suffix colour A.  The 6 geometric partials of a Gaussian (2D mean, conic, opacity) are
-// summed per thread over its pixels and over the warp by an 8-value lane-transposed
-// butterfly (9 shuffles).  The 4 + C feature gradients (colour, depth, semantics) are a
-// contraction, dF = W^T G over the warp's pixels: every lane writes its weights w = alpha T
-// into a 16-Gaussian chunk buffer, and each full chunk goes through the tensor cores
-// (mma.m16n8k8, TF32 split into hi + lo parts for FP32-level accuracy).
+// suffix colour A.  Per chunk of 16 list entries every lane writes, for each entry, its
+// weight w = alpha T and s = dL/dsigma into two chunk buffers; the three sums over the
+// warp's pixels -- g . f, the 4 + C feature gradients dF = W^T G (colour, depth, semantics)
+// and the six pixel moments of s, which give the 2D-mean, conic and opacity gradients --
+// then run on the tensor cores (mma.m16n8k8, TF32 split into hi + lo parts for FP32-level
+// accuracy); no shuffles in the per-entry loop.
 #pragma once
 
 #include "raster.cuh"
