@@ -8,10 +8,11 @@
 // then the chain rule runs on each with the next one's 2D gradients already loading.  The
 // view table sits in shared memory.
 //
-// View-dependent colour (spherical harmonics of degree D = 1..3) is a template parameter:
-// the forward evaluates each visible record's colour from the camera-to-mean direction, and
-// the adjoint chains the per-record colour gradients to the SH coefficients, rgb and the
-// mean; D = 0 compiles to the plain kernels.
+// View-dependent colour and semantic feature (spherical harmonics of degree D = 1..3) is a
+// template parameter: the forward evaluates each visible record's colour (and, with sem_sh,
+// its semantic feature) from the camera-to-mean direction, and the adjoint chains the
+// per-record gradients to the SH coefficients, rgb / sem and the mean; D = 0 compiles to the
+// plain kernels.
 #include "sg_common.cuh"
 
 namespace sg {

@@ -14,6 +14,8 @@
 //   4. sort:     stable LSD radix sort of the instances by global tile id (only the bits
 //                n_tiles needs), which keeps the (depth, record) order inside each tile
 //   5. ranges:   [start, end) of every tile
+//   6. order:    (when requested) the tile ids by descending half-octave bucket of their list
+//                length, one stable counting pass: the compositing kernels' work order
 // The result equals sorting all kept instances by (tile, depth bits, record id).  Every radix
 // pass is three kernels: per-block digit histograms, per-digit scans over the blocks, and
 // a stable scatter that ranks equal digits inside a block by warp match + prefix counts.
