@@ -3,7 +3,7 @@
 // RGB term (Eq. 10) and, in semantic-colour mode, the semantic term (Eq. 12):
 //   (1 - lambda) mean|I - I_gt| + lambda (1 - SSIM(I, I_gt)),
 // SSIM with an 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2, zero padding.
-// One CTA owns a 32x16 output tile of one view-level and one group of planes.  It stages
+// One CTA owns a 32x32 output tile of one view-level and one group of planes.  It stages
 // the planes with a 10-pixel halo, forms the five window moments (separable, horizontal
 // then vertical) on the tile plus a 5-pixel halo, turns them into the three per-pixel
 // partials of SSIM (w.r.t. the window mean, E[x^2] and E[xy]), and convolves those once
@@ -26,7 +26,7 @@ constexpr int kLossThreads = 256;
 
 struct LossViews {
     int n;
-    int tile_off[SG_MAX_VIEWS + 1];  // loss tiles (32x16) per view, prefix
+    int tile_off[SG_MAX_VIEWS + 1];  // loss tiles (32x32) per view, prefix
     int pix_blk_off[SG_MAX_VIEWS + 1];  // 256-pixel blocks per view, prefix
 };
 
