@@ -105,28 +105,6 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 }
 
 // ----------------------------------------------------------------------------------------
-// Lane-transposed warp reduction: NV (power of two, >= 32) values per lane are summed over
-// the warp with NV-1 shuffles; afterwards lane l holds the sums of values
-// [l*NV/32, (l+1)*NV/32) in v[0 .. NV/32).
-// ----------------------------------------------------------------------------------------
-template <int NV>
-__device__ __forceinline__ void warp_transpose_reduce(float (&v)[NV], int lane) {
-    static_assert(NV >= 32 && (NV & (NV - 1)) == 0, "NV must be a power of two >= 32");
-#pragma unroll
-    for (int step = 0; step < 5; ++step) {
-        const int s = 16 >> step;
-        const int half = NV >> (step + 1);
-        const bool upper = (lane & s) != 0;
-#pragma unroll
-        for (int i = 0; i < half; ++i) {
-            const float send = upper ? v[i] : v[i + half];
-            const float keep = upper ? v[i + half] : v[i];
-            v[i] = keep + __shfl_xor_sync(SG_FULL_MASK, send, s);
-        }
-    }
-}
-
-// ----------------------------------------------------------------------------------------
 // TF32 tensor-core products with FP32-level accuracy: x = hi + lo with hi = x with its 13
 // low mantissa bits cleared and lo = x - hi (exact); a*b ~ hi*hi + hi*lo + lo*hi keeps about
 // 22 mantissa bits of every product (the dropped lo*lo term is below 2^-22 relative).
