@@ -103,15 +103,6 @@ __device__ __forceinline__ void view_geom(const sg_view &vw, const float mu[3], 
     }
 }
 
-__device__ __forceinline__ float quad3(const float *a, const float *S, const float *b) {
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) s += a[i] * sym3(S, i, j) * b[j];
-    return s;
-}
-
 // Sigma2D = A A^T + dil I with A = T M (M = R diag(S)); det by Cauchy-Binet,
 // det(A A^T) = |a0 x a1|^2, so it is a sum of non-negative terms.
 __device__ __forceinline__ void cov2d(const ViewGeom &q, const GaussianFrame &f, float dil,
