@@ -14,7 +14,7 @@ from __future__ import annotations
 
 import json
 import os
-from dataclasses import asdict, replace
+from dataclasses import replace
 
 import torch
 

@@ -17,8 +17,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import SgCamera, SgGaussians, call
-from .splat import (LossConfig, MappingStep, PARAM_KEYS, PyramidRasterizer, RenderConfig, build_pyramid,
+from ._lib import call
+from .splat import (LossConfig, MappingStep, PyramidRasterizer, RenderConfig, build_pyramid,
                     camera_struct, gaussians_struct)
 
 

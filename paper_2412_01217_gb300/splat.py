@@ -6,8 +6,7 @@ C structs and passes the current stream.
 from __future__ import annotations
 
 import ctypes as C
-import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 import torch

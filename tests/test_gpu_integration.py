@@ -43,7 +43,7 @@ def _room_problem(W=320, H=180, n=30000, ncam=2, levels=3, C=16, K=32):
 
 
 def test_cuda_graph_replay_equals_eager():
-    from paper_2412_01217_gb300 import MappingStep, build_pyramid, to_device_params
+    from paper_2412_01217_gb300 import MappingStep, build_pyramid
     room, g, cams, frames = _room_problem()
     dec = torch.randn(32, 16, device="cuda") * 0.3
     results = []
@@ -164,7 +164,7 @@ def test_full_size_backward_sparse_upstream(replica_like, cfg):
 
 
 def test_autotuner_picks_a_valid_configuration_with_identical_output():
-    from paper_2412_01217_gb300 import LossConfig, RenderConfig, build_pyramid
+    from paper_2412_01217_gb300 import LossConfig, build_pyramid
     from paper_2412_01217_gb300.autotune import autotune
     room, g, cams, frames = _room_problem(n=20000, ncam=1)
     r, p = make(g, cams, levels=3)
