@@ -193,3 +193,30 @@ def test_sh_autograd_and_mapping_step():
     torch.cuda.synchronize()
     assert np.isfinite(step.total_loss()) and step.total_loss() < loss1
     assert not torch.equal(step.p["sh"], sh0) and not torch.equal(step.p["sem_sh"], ssh0)
+
+
+def test_sh_with_eq2_isotropic_projection():
+    """Degree-2 colour and semantic SH together with the Eq. 2 isotropic projection (the
+    projection kernels' SH template and their isotropic branch in one launch): every image
+    channel and all gradient groups against the oracle; the rotation and the unused
+    log-scales get exactly zero."""
+    g, cam = sh_cloud(2, seed=9, colour=True, semantic=True)
+    r, p = make(g, [cam], isotropic=True)
+    r.forward(p)
+    ocfg = dict(isotropic=1)
+    ref_f = oracle.render(g, cam, ocfg)
+    amb = (ref_f["flags"] & AMBIGUOUS) != 0
+    assert amb.mean() < 0.03
+    got = view_images(r, 0, 8)
+    for k in ("rgb", "depth", "sem", "T"):
+        check_close(k, got[k], ref_f[k], FWD_REL, FWD_ABS, mask=~amb)
+    up = upstream(ref_f, cam["H"], cam["W"], 8, seed=31)
+    dl = tuple(torch.tensor(u.reshape(-1), dtype=torch.float32, device="cuda") for u in up)
+    grads = {k: torch.zeros_like(v) for k, v in p.items()}
+    r.backward(p, grads, dL=dl)
+    got = {k: v.cpu().numpy() for k, v in grads.items()}
+    up32 = [t.cpu().numpy().astype(np.float64).reshape(u.shape) for t, u in zip(dl, up)]
+    ref = oracle.render_backward(g, cam, *up32, cfg=ocfg)
+    check_grads(got, ref, BASE + ("sh", "sem_sh"))
+    assert not got["quat"].any() and not got["log_scale"][:, 1:].any()
+    assert not r.bwd_ws.any()
