@@ -315,18 +315,21 @@ def test_loss_matches_oracle(mode):
         check_close("dL/ddecoder", dgrad.cpu().numpy(), dec_ref_total, 1e-4, 1e-6)
 
 
-def test_multiview_pyramid_forward_backward_matches_oracle():
+@pytest.mark.parametrize("isotropic", [False, True])
+def test_multiview_pyramid_forward_backward_matches_oracle(isotropic):
     """Two keyframes x three levels rendered in ONE persistent launch: every pixel of
-    every view-level against the oracle, and all parameter gradients."""
+    every view-level against the oracle, and all parameter gradients; also with the Eq. 2
+    isotropic projection, whose radius f r / d takes each level's own focal length."""
     room, g, cams = room_small(n=6000, ncam=2, W=160, H=96)
-    r, p = make(g, cams, levels=3)
+    r, p = make(g, cams, levels=3, isotropic=isotropic)
     r.forward(p)
     ocams = oracle_cams(cams, 3)
+    ocfg = dict(isotropic=int(isotropic))
     rng = np.random.default_rng(2)
     ups = []
     for v, oc in enumerate(ocams):
         got = view_images(r, v, 16)
-        ref = oracle.render(g, oc)
+        ref = oracle.render(g, oc, ocfg)
         amb = (ref["flags"] & AMBIGUOUS) != 0
         assert amb.mean() < 0.03
         for k in ("rgb", "depth", "sem", "T"):
@@ -348,10 +351,12 @@ def test_multiview_pyramid_forward_backward_matches_oracle():
         a = r.view_slice(dl[0], v, 3).cpu().numpy().astype(np.float64)
         b = r.view_slice(dl[1], v, 1)[0].cpu().numpy().astype(np.float64)
         c = r.view_slice(dl[2], v, 16).cpu().numpy().astype(np.float64)
-        rv = oracle.render_backward(g, oc, a, b, c)
+        rv = oracle.render_backward(g, oc, a, b, c, cfg=ocfg)
         for k in KEYS:
             ref[k] = ref[k] + rv[k]
     check_grads(got, ref, KEYS)
+    if isotropic:
+        assert not got["quat"].any() and not got["log_scale"][:, 1:].any()
 
 
 def test_capacity_overflow_sets_status_and_reports_need(cloud):
