@@ -85,3 +85,41 @@ def test_noalloc_loss_rejects_images_beyond_its_scratch():
     with pytest.raises(SgError) as e:
         _call(x, noalloc=True)
     assert e.value.code == 2 and "scratch" in str(e.value)
+
+
+def test_noalloc_loss_matches_workspace_loss_in_paper_mode():
+    """The paper's semantic term (Eq. 12: L1 + D-SSIM on a semantic colour image, 8 planes)
+    takes its own partial-sum block of the built-in scratch: same terms and image gradients
+    as with a caller workspace, on two calls in a row."""
+    from paper_2412_01217_gb300._lib import SgImages, SgLossConfig, SgTargets, call, load
+    lib = load()
+    for seed in (2, 3):
+        x = _inputs(seed, Cs=8, K=8)
+        rng = np.random.default_rng(seed + 10)
+        g_sem = torch.tensor(rng.uniform(size=8 * x["P"]), dtype=torch.float32, device="cuda")
+        r_sem = torch.tensor(rng.uniform(size=8 * x["P"]), dtype=torch.float32, device="cuda")
+        outs = []
+        for noalloc in (False, True):
+            P, Cs = x["P"], 8
+            rendered = SgImages(x["r_rgb"].data_ptr(), x["r_depth"].data_ptr(), r_sem.data_ptr())
+            gt = SgTargets(x["g_rgb"].data_ptr(), x["g_depth"].data_ptr(), x["g_label"].data_ptr(), g_sem.data_ptr())
+            dL = [torch.full((n * P,), float("nan"), device="cuda") for n in (3, 1, Cs)]
+            dLi = SgImages(*[d.data_ptr() for d in dL])
+            lc = SgLossConfig(0.2, 0.2, 1.0, 1.0, 1, Cs, None, None)
+            terms = torch.full((4 * x["V"],), float("nan"), device="cuda")
+            stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+            if noalloc:
+                call("sg_pyramid_loss_noalloc", C.byref(rendered), C.byref(gt), C.c_void_p(x["dviews"].data_ptr()),
+                     x["views"], x["V"], Cs, C.byref(lc), C.c_void_p(terms.data_ptr()), C.byref(dLi), stream)
+            else:
+                ws = torch.zeros(lib.sg_loss_workspace_size(x["views"], x["V"], Cs, Cs), dtype=torch.uint8,
+                                 device="cuda")
+                call("sg_pyramid_loss", C.byref(rendered), C.byref(gt), C.c_void_p(x["dviews"].data_ptr()),
+                     x["views"], x["V"], Cs, C.byref(lc), C.c_void_p(terms.data_ptr()), C.byref(dLi),
+                     C.c_void_p(ws.data_ptr()), ws.numel(), stream)
+            torch.cuda.synchronize()
+            outs.append([terms.cpu().numpy(), *[d.cpu().numpy() for d in dL]])
+        for name, r, g in zip(("terms", "dL_rgb", "dL_depth", "dL_sem"), *outs):
+            assert np.isfinite(g).all(), (seed, name)
+            assert np.allclose(g, r, rtol=1e-5, atol=1e-6 * np.abs(r).max()), (seed, name)
+        assert np.abs(outs[0][3]).max() > 0   # the semantic term has a gradient
