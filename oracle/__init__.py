@@ -27,6 +27,10 @@ Pieces and the passages they follow:
                          records on both sides, the ellipse's extent within each tile row),
                          ordered by (tile, float32 depth bits, record index) (numpy lexsort).
 
+Submodules: ``mlp`` (the learned initializer's network) and ``init`` (insertion of new
+Gaussians: the heuristic initializer, the network's patch features and the application of
+its outputs).
+
 Parity pins: the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py`` tie every function
 here to closed forms, invariants, library routines and finite differences.
 """

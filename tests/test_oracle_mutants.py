@@ -182,6 +182,17 @@ MUTANTS = [
     ("tiles_row_width_of_first_view", "__init__.py", "tiles.append(tile_offset[v] + ty * n_tiles_x[v] + tx)",
      "tiles.append(tile_offset[v] + ty * n_tiles_x[0] + tx)"),
     ("tiles_empty_range_not_zeroed", "__init__.py", "        ranges[empty] = 0\n", "        pass\n"),
+    # ---- insertion: heuristic initializer, patch features, network outputs ----
+    ("init_mean_rotation_untransposed", "init.py", "mean = (pc - t) @ R            # rows: R^T (p - t)",
+     "mean = (pc - t) @ R.T"),
+    ("init_backprojection_fx_for_y", "init.py", "(ys - cam[\"cy\"]) / cam[\"fy\"] * D, D], 1)",
+     "(ys - cam[\"cy\"]) / cam[\"fx\"] * D, D], 1)"),
+    ("init_scale_not_one_pixel", "init.py", "ls = np.log(D / cam[\"fx\"])", "ls = np.log(D)"),
+    ("patch_neighbours_column_major", "init.py", "x = x0 + n % PATCH - PATCH // 2\n            y = y0 + n // PATCH - PATCH // 2",
+     "x = x0 + n // PATCH - PATCH // 2\n            y = y0 + n % PATCH - PATCH // 2"),
+    ("patch_ray_not_normalised", "init.py", "f[36:39] = ray / np.linalg.norm(ray)", "f[36:39] = ray"),
+    ("patch_label_offset", "init.py", "f[4 + int(label[y, x])] = 1.0", "f[3 + int(label[y, x])] = 1.0"),
+    ("apply_sem_offset", "init.py", "sem[:, :n] = V[:, 4:4 + n]", "sem[:, :n] = V[:, 3:3 + n]"),
     # ---- learned-initializer MLP ----
     ("mlp_relu_mask_wrong_layer", "mlp.py", "dH1 = r((dH2 @ W2) * (H1 > 0))", "dH1 = r((dH2 @ W2) * (H2 > 0))"),
     ("mlp_weight_gradient_transposed", "mlp.py", "W2=dH2.T @ H1", "W2=H1.T @ dH2"),
@@ -198,7 +209,7 @@ PIN_FILES = sorted(f for f in os.listdir(os.path.join(ROOT, "tests"))
 
 def _copy_tree(dst):
     """The oracle, the seeded generators, the pin tests and their configuration."""
-    for sub, names in (("oracle", ["__init__.py", "mlp.py", "sg_oracle.c"]),
+    for sub, names in (("oracle", ["__init__.py", "mlp.py", "init.py", "sg_oracle.c"]),
                        ("synthetic", ["__init__.py"]),
                        ("tests", ["conftest.py", "helpers.py"] + PIN_FILES)):
         os.makedirs(os.path.join(dst, sub), exist_ok=True)
