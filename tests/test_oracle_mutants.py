@@ -54,6 +54,8 @@ MUTANTS = [
      '*np.asarray(cam["R_cw"], np.float64).T.reshape(9),'),
     ("pack_cfg_alpha_min_T_min_swapped", "__init__.py", 'return np.array([c["alpha_max"], c["alpha_min"], c["T_min"],',
      'return np.array([c["alpha_max"], c["T_min"], c["alpha_min"],'),
+    ("proj_v_uses_cx", "sg_oracle.c", "out[P_V] = cam->fy * t[1] / t[2] + cam->cy;",
+     "out[P_V] = cam->fy * t[1] / t[2] + cam->cx;"),
     # ---- compositing (Eq. 7-9) ----
     ("comp_sigma_cross_term_halved", "sg_oracle.c", "+ p[P_CB] * dx * dy;", "+ 0.5 * p[P_CB] * dx * dy;"),
     ("comp_alpha_clamp_dropped", "sg_oracle.c", "double alpha = raw < cfg->alpha_max ? raw : cfg->alpha_max;",
@@ -74,6 +76,11 @@ MUTANTS = [
     ("comp_candidates_prefiltered_too_tight", "sg_oracle.c", "if (alpha < cfg->alpha_min * 0.5) continue;",
      "if (alpha < cfg->alpha_min * 2.0) continue;"),
     ("comp_transmittance_update", "sg_oracle.c", "        T = Tn;\n", "        T = T * c->alpha;\n"),
+    ("comp_transmittance_unclamped_alpha", "sg_oracle.c", "double Tn = T * (1.0 - c->alpha);",
+     "double Tn = T * (1.0 - c->raw);"),
+    ("comp_sigma_conic_diagonal_swapped", "sg_oracle.c",
+     "double sigma = 0.5 * (p[P_CA] * dx * dx + p[P_CC] * dy * dy) + p[P_CB] * dx * dy;",
+     "double sigma = 0.5 * (p[P_CC] * dx * dx + p[P_CA] * dy * dy) + p[P_CB] * dx * dy;"),
     # ---- adjoint (Sec. III-D) ----
     ("bwd_dalpha_missing_T", "sg_oracle.c", "dalpha *= Ti;", "dalpha *= 1.0;"),
     ("bwd_suffix_not_attenuated", "sg_oracle.c", "A[ch] = al * f[ch] + (1.0 - al) * A[ch];",
@@ -115,6 +122,9 @@ MUTANTS = [
     ("bwd_symmetric_gradient_not_halved", "sg_oracle.c", "double G[4] = {gS00, 0.5 * gS01, 0.5 * gS01, gS11};",
      "double G[4] = {gS00, gS01, gS01, gS11};"),
     ("bwd_dconic_a_factor", "sg_oracle.c", "gsig * 0.5 * dx * dx,", "gsig * dx * dx,"),
+    ("bwd_isotropic_v_uses_fx", "sg_oracle.c", "double gt[3] = {gu * fx / tz, gv * fy / tz,",
+     "double gt[3] = {gu * fx / tz, gv * fx / tz,"),
+    ("bwd_dalpha_sign", "sg_oracle.c", "dalpha += g[ch] * (f[ch] - A[ch]);", "dalpha += g[ch] * (A[ch] - f[ch]);"),
     # ---- SSIM (Eq. 10, 12) ----
     ("ssim_C1_for_C2", "sg_oracle.c", "A2 = 2 * sxy + C2;", "A2 = 2 * sxy + C1;"),
     ("ssim_window_sigma", "sg_oracle.c", "/ (2.0 * 1.5 * 1.5));", "/ (2.0 * 1.5));"),
@@ -127,6 +137,9 @@ MUTANTS = [
      "double norm = 1.0 / (double)P;"),
     ("ssim_window_product_index", "sg_oracle.c", "double w = g1[i + 5] * g1[j + 5];\n                        double xv",
      "double w = g1[i + 5] * g1[i + 5];\n                        double xv"),
+    ("ssim_replicate_padding", "sg_oracle.c",
+     "                        int cc = q + j;\n                        if (cc < 0 || cc >= W) continue;\n                        double w = g1[i + 5] * g1[j + 5];\n                        double xv",
+     "                        int cc = q + j;\n                        if (cc < 0 || cc >= W) cc = cc < 0 ? 0 : W - 1;\n                        double w = g1[i + 5] * g1[j + 5];\n                        double xv"),
     # ---- pyramid (Eq. 4-6) ----
     ("pyr_principal_point_no_half_pixel", "__init__.py", 'cx=(p["cx"] - 0.5) / 2,', 'cx=p["cx"] / 2,'),
     ("pyr_depth_mean_over_invalid", "__init__.py", "(d * valid).sum(axis=(1, 3)) / np.maximum(cnt, 1)",
@@ -134,6 +147,7 @@ MUTANTS = [
     ("pyr_label_ties_to_highest", "__init__.py", "if cc > bc:", "if cc >= bc:"),
     ("pyr_subsample_instead_of_mean", "__init__.py", "rgb2 = r.mean(axis=(2, 4))", "rgb2 = r[:, :, 0, :, 0]"),
     ("pyr_size_rounds_up", "__init__.py", 'W=p["W"] // 2,', 'W=(p["W"] + 1) // 2,'),
+    ("pyr_label_ties_sorted_descending", "__init__.py", "for v in sorted(set(vals)):", "for v in sorted(set(vals), reverse=True):"),
     # ---- losses (Eq. 10-13) ----
     ("loss_ssim_not_dissimilarity", "__init__.py", "L_r = (1 - lambda_r) * lr + lambda_r * (1 - s_val)",
      "L_r = (1 - lambda_r) * lr + lambda_r * s_val"),
@@ -167,6 +181,8 @@ MUTANTS = [
     ("sh_adjoint_overwrites_colour_part", "__init__.py", "w += np.einsum(\"nkc,nc->nk\"", "w = w * 0 + np.einsum(\"nkc,nc->nk\""),
     ("sh_l3_constant", "__init__.py", "e, f, h = np.sqrt(35 / (2 * pi)) / 4, np.sqrt(105 / pi) / 2, np.sqrt(21 / (2 * pi)) / 4\n        k, m = np.sqrt(7 / pi) / 4, np.sqrt(105 / pi) / 4\n        out",
      "e, f, h = np.sqrt(35 / (2 * pi)) / 4, np.sqrt(105 / pi) / 2, np.sqrt(21 / (2 * pi)) / 4\n        k, m = np.sqrt(7 / pi) / 2, np.sqrt(105 / pi) / 4\n        out"),
+    ("sh_direction_not_unit", "__init__.py", "    d = v / n[:, None]\n    return d, n, sh_basis(d, D)",
+     "    d = v\n    return d, n, sh_basis(d, D)"),
     # ---- tile lists ----
     ("tiles_record_before_depth", "__init__.py", "order = np.lexsort((recs, dbits, tiles))",
      "order = np.lexsort((dbits, recs, tiles))"),
@@ -182,6 +198,7 @@ MUTANTS = [
     ("tiles_row_width_of_first_view", "__init__.py", "tiles.append(tile_offset[v] + ty * n_tiles_x[v] + tx)",
      "tiles.append(tile_offset[v] + ty * n_tiles_x[0] + tx)"),
     ("tiles_empty_range_not_zeroed", "__init__.py", "        ranges[empty] = 0\n", "        pass\n"),
+    ("tiles_culling_threshold_not_squared", "__init__.py", "        thr = t * t\n", "        thr = t\n"),
     # ---- insertion: heuristic initializer, patch features, network outputs ----
     ("init_mean_rotation_untransposed", "init.py", "mean = (pc - t) @ R            # rows: R^T (p - t)",
      "mean = (pc - t) @ R.T"),
@@ -199,6 +216,8 @@ MUTANTS = [
     ("mlp_second_layer_weight_transposed", "mlp.py", "H2 = r(np.maximum(H1 @ W2.T + b2, 0.0))",
      "H2 = r(np.maximum(H1 @ W2 + b2, 0.0))"),
     ("mlp_bias_after_relu", "mlp.py", "H1 = r(np.maximum(X @ W1.T + b1, 0.0))", "H1 = r(np.maximum(X @ W1.T, 0.0) + b1)"),
+    ("mlp_loss_normalised_per_output", "mlp.py", "L = float((w[None] * (Y - T) ** 2).sum() / B)",
+     "L = float((w[None] * (Y - T) ** 2).sum() / (B * Y.shape[1]))"),
     ("mlp_loss_weight_missing_in_gradient", "mlp.py", "dY = r(2.0 * w[None] * (Y - T) / B)",
      "dY = r(2.0 * (Y - T) / B)"),
 ]
