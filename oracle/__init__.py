@@ -21,11 +21,14 @@ Pieces and the passages they follow:
 * ``level_loss``         Eq. 10-13 per pyramid level with D-SSIM = 1 - SSIM, masked depth L1,
                          and either cross-entropy on composited semantic logits or the
                          paper's L1 + D-SSIM on a semantic colour image (numpy + C SSIM).
-* ``tile_lists``         integer reference of the tile-instance lists: every (record, tile)
-                         pair of a record's tile rectangle (optionally those that
-                         ``tile_reaches_alpha_min`` keeps: a float32 rule taken from the same
-                         records on both sides, the ellipse's extent within each tile row),
-                         ordered by (tile, float32 depth bits, record index) (numpy lexsort).
+* ``tile_reach``,        the set N of Eq. 7-9 restricted to a screen tile, by definition:
+  ``tile_pairs``         a Gaussian belongs to a tile's set when its alpha reaches alpha_min
+                         at one of the tile's pixels (FP64 brute force over the tile's pixel
+                         centres), plus the least exponent over the tile's pixel-centre
+                         rectangle (how close a footprint comes to a tile it misses) (numpy).
+* ``tile_lists``         integer reference of the order of those sets: (record, tile) pairs
+                         ordered by (tile, float32 depth key bits, record index) (numpy
+                         lexsort), with per-tile ranges.
 
 Submodules: ``mlp`` (the learned initializer's network) and ``init`` (insertion of new
 Gaussians: the heuristic initializer, the network's patch features and the application of
@@ -53,7 +56,7 @@ DEFAULT_CFG = dict(alpha_max=0.99, alpha_min=1.0 / 255.0, T_min=1e-4, z_near=0.2
 
 # projection record fields (must match the enum in sg_oracle.c)
 P = dict(VALID=0, U=1, V=2, DEPTH=3, OPAC=4, CA=5, CB=6, CC=7, S00=8, S01=9, S11=10,
-         TX=11, TY=12, TZ=13, CLX=14, CLY=15, EXTX=16, EXTY=17, LIMX=18, LIMY=19, DKEY=20)
+         TX=11, TY=12, TZ=13, CLX=14, CLY=15, EXTX=16, EXTY=17, LIMX=18, LIMY=19, DKEY=20, DAMB=21, GEXTX=22, GEXTY=23)
 FLAG_SKIP, FLAG_STOP, FLAG_DEPTH, FLAG_CLAMP = 1, 2, 4, 8
 
 
@@ -248,14 +251,17 @@ def view_semantics(g, cam):
     return sem + np.einsum("nk,nkc->nc", Y, np.asarray(g["sem_sh"], np.float64))
 
 
-def render(g, cam, cfg=None, pixels=None, tol=1e-3):
+def render(g, cam, cfg=None, pixels=None, tol=1e-5):
     """Render RGB, depth and C semantic channels.
 
     ``pixels``: None for the whole W x H image (outputs shaped (ch, H, W)), else an (n, 2)
     int array of (x, y) pixel coordinates (outputs shaped (ch, n)).  Also returns the final
     transmittance ``T``, the contributor count ``n_contrib`` and per-pixel ambiguity
-    ``flags`` (FLAG_*: some decision of the pixel lies within relative ``tol`` of a
-    threshold, so a float32 evaluation may take the other branch).
+    ``flags`` (FLAG_*): some decision of the pixel is not fixed for an evaluation whose alpha
+    carries a relative error up to ``tol`` -- the exact alpha lies within ``tol`` of the skip
+    threshold (FLAG_SKIP) or of the clamp (FLAG_CLAMP), the transmittance after a contributor
+    within its propagated error of T_min (FLAG_STOP), or a contributor's float32 depth key
+    is undecided next to a neighbouring key (FLAG_DEPTH).
     """
     lib = _load()
     proj = project(g, cam, cfg)
@@ -481,60 +487,73 @@ def level_loss(r_rgb, r_depth, r_sem, gt_rgb, gt_depth, gt_sem, lambda_r=0.2, la
 # Tile-instance lists (integer reference; the depth sort of Eq. 7-9's set N per tile)
 # ------------------------------------------------------------------------------------------
 
-def tile_reaches_alpha_min(geo, ext, X0, X1, Y0, Y1):
-    """Float32 tile culling rule of the tile lists, for arrays of (record, tile) pairs.
+def tile_pairs(proj, cam, tile_w, tile_h):
+    """(Gaussian, tile x, tile y) for every tile of each Gaussian's FP64 support rectangle:
+    the tiles holding a pixel centre within the half extents (EXTX, EXTY) of its 2D mean,
+    outside which alpha < alpha_min (an exact bound).  Culled Gaussians give none."""
+    p = np.asarray(proj, np.float64)
+    gs, txs, tys = [], [], []
+    for i in np.nonzero(p[:, P["VALID"]] > 0)[0]:
+        u, v, ex, ey = p[i, P["U"]], p[i, P["V"]], p[i, P["EXTX"]], p[i, P["EXTY"]]
+        x0, x1 = max(0, int(np.ceil(u - ex))), min(cam["W"] - 1, int(np.floor(u + ex)))
+        y0, y1 = max(0, int(np.ceil(v - ey))), min(cam["H"] - 1, int(np.floor(v + ey)))
+        if x0 > x1 or y0 > y1:
+            continue
+        tx, ty = np.meshgrid(np.arange(x0 // tile_w, x1 // tile_w + 1), np.arange(y0 // tile_h, y1 // tile_h + 1))
+        gs.append(np.full(tx.size, i)); txs.append(tx.ravel()); tys.append(ty.ravel())
+    if not gs:
+        z = np.zeros(0, np.int64)
+        return z, z, z
+    return np.concatenate(gs), np.concatenate(txs), np.concatenate(tys)
 
-    geo: (n, 8) float32 records (u_frac, v_frac, depth, opacity, m00, m10, m11, packed
-    int16 (u_int, v_int)); ext: (n, 2) float32 half extents; X0..X1, Y0..Y1: the tile's
-    pixel-centre rectangle (int).  The record's alpha >= alpha_min region is the ellipse
-    sigma = (m00 dx)^2 + (m10 dx + m11 dy)^2 <= thr, and the projection wrote
-    ex = sqrt(2 thr s00) 1.002 + 0.01 with m00 = 1 / sqrt(2 s00), so
-    thr' = ((ex - 0.01) (1 / 1.002) m00)^2.  Within the band dy in [y0, y1] of the tile's row
-    the ellipse spans dx in [xl, xr]: with A = m00^2 + m10^2, B = m10 m11, C = m11^2 and
-    p = m00 m11 (A C - B^2 = p^2), the band is cut to |dy| <= sqrt(A thr') / p, the right
-    edge (s(dy) - B dy) / A with s = sqrt(A thr' - (p dy)^2) is largest at
-    dy = -B (sqrt(thr' C) / p) / C and the left edge (-B dy - s) / A smallest at the opposite
-    dy, each clamped to the band.  The tile is kept when its pixel-centre columns meet
-    [xl, xr]: ((X1 - u_int) - u_frac) >= xl and ((X0 - u_int) - u_frac) <= xr.  Every step is
-    one correctly rounded float32 operation (square roots and divisions included) in a fixed
-    order, so the decision is reproducible bit for bit from the same float32 records; the
-    kept tiles of a tile row are contiguous.  Returns a bool array.
-    """
-    f = np.float32
-    geo = np.asarray(geo, np.float32)
-    ext = np.asarray(ext, np.float32)
-    packed = geo[:, 7].view(np.uint32)
-    ui = (packed & 0xFFFF).astype(np.uint16).view(np.int16).astype(np.int64)
-    vi = (packed >> 16).astype(np.uint16).view(np.int16).astype(np.int64)
-    uf, vf = geo[:, 0], geo[:, 1]
-    X0, X1 = np.asarray(X0, np.int64), np.asarray(X1, np.int64)
-    Y0, Y1 = np.asarray(Y0, np.int64), np.asarray(Y1, np.int64)
-    m00, m10, m11 = geo[:, 4], geo[:, 5], geo[:, 6]
-    with np.errstate(all="ignore"):
-        t = ((ext[:, 0] - f(0.01)) * f(1.0 / 1.002)) * m00
-        thr = t * t
-        A = m00 * m00 + m10 * m10
-        B = m10 * m11
-        Cq = m11 * m11
-        p = m00 * m11
-        y0 = (Y0 - vi).astype(np.float32) - vf
-        y1 = (Y1 - vi).astype(np.float32) - vf
-        dymax = np.sqrt(A * thr) / p
-        yb0 = np.fmax(y0, -dymax)
-        yb1 = np.fmin(y1, dymax)
-        dxmax = np.sqrt(thr * Cq) / p
-        dyr = -((B * dxmax) / Cq)
 
-        def s_of(dy):
-            q = p * dy
-            return np.sqrt(np.fmax(A * thr - q * q, f(0)))
-
-        dr = np.fmin(yb1, np.fmax(yb0, dyr))
-        dl = np.fmin(yb1, np.fmax(yb0, -dyr))
-        xr = (s_of(dr) - B * dr) / A
-        xl = (-(B * dl) - s_of(dl)) / A
-        keep = (yb0 <= yb1) & (((X1 - ui).astype(np.float32) - uf) >= xl) & (((X0 - ui).astype(np.float32) - uf) <= xr)
-    return keep
+def tile_reach(proj, cam, gauss, tx, ty, tile_w, tile_h, chunk=4096):
+    """For (Gaussian, tile) pairs, from the FP64 projection:
+    ``alpha``: the largest alpha = o exp(-sigma) of the Gaussian over the tile's pixel centres
+    (Eq. 3; the Gaussian belongs to the tile's set N iff this reaches alpha_min; 0 for a culled
+    Gaussian), ``sigma_min``: the least sigma = 1/2 d^T conic d over the continuous rectangle
+    spanned by the tile's pixel centres, and ``thr`` = ln(o / alpha_min) (alpha >= alpha_min
+    needs sigma <= thr).  sigma is a positive definite quadratic: its minimum over the
+    rectangle is 0 when the rectangle holds the mean, else the least of the clamped 1-D
+    minima along the four edges."""
+    p = np.asarray(proj, np.float64)
+    gauss, tx, ty = (np.asarray(a, np.int64) for a in (gauss, tx, ty))
+    n = len(gauss)
+    alpha, smin = np.zeros(n), np.full(n, np.inf)
+    alpha_min = 1.0 / 255.0
+    o = p[gauss, P["OPAC"]]
+    with np.errstate(divide="ignore"):
+        thr = np.where(o > 0, np.log(np.maximum(o, 1e-300) / alpha_min), -np.inf)
+    ox, oy = np.meshgrid(np.arange(tile_w), np.arange(tile_h))
+    ox, oy = ox.ravel(), oy.ravel()
+    for s in range(0, n, chunk):
+        sl = slice(s, min(n, s + chunk))
+        pg = p[gauss[sl]]
+        ok = pg[:, P["VALID"]] > 0
+        a, b, c = pg[:, P["CA"]], pg[:, P["CB"]], pg[:, P["CC"]]
+        X0, Y0 = tx[sl] * tile_w, ty[sl] * tile_h
+        X1 = np.minimum(X0 + tile_w - 1, cam["W"] - 1)
+        Y1 = np.minimum(Y0 + tile_h - 1, cam["H"] - 1)
+        xs, ys = X0[:, None] + ox[None], Y0[:, None] + oy[None]
+        inside = (xs <= X1[:, None]) & (ys <= Y1[:, None])
+        dx, dy = xs - pg[:, P["U"]][:, None], ys - pg[:, P["V"]][:, None]
+        sig = 0.5 * (a[:, None] * dx * dx + c[:, None] * dy * dy) + b[:, None] * dx * dy
+        al = np.where(inside, pg[:, P["OPAC"]][:, None] * np.exp(-np.maximum(sig, 0.0)), 0.0)
+        alpha[sl] = np.where(ok, al.max(1), 0.0)
+        # least sigma over [x0, x1] x [y0, y1] (offsets from the mean), A = a/2, B = b/2, C = c/2
+        x0, x1 = X0 - pg[:, P["U"]], X1 - pg[:, P["U"]]
+        y0, y1 = Y0 - pg[:, P["V"]], Y1 - pg[:, P["V"]]
+        A, B, C = 0.5 * a, 0.5 * b, 0.5 * c
+        with np.errstate(all="ignore"):
+            q = lambda x, y: A * x * x + 2 * B * x * y + C * y * y
+            best = np.full(len(A), np.inf)
+            for x in (x0, x1):
+                best = np.minimum(best, q(x, np.clip(-B * x / C, y0, y1)))
+            for y in (y0, y1):
+                best = np.minimum(best, q(np.clip(-B * y / A, x0, x1), y))
+        holds = (x0 <= 0) & (x1 >= 0) & (y0 <= 0) & (y1 >= 0)
+        smin[sl] = np.where(ok, np.where(holds, 0.0, best), np.inf)
+    return dict(alpha=alpha, sigma_min=smin, thr=thr)
 
 
 def tile_lists(rects, depth, n_tiles_x, tile_offset, n_total_tiles, n_per_view, keep=None):

@@ -15,8 +15,9 @@
  *                       f r / d (fx along x, fy along y), i.e. Sigma2D = diag((fx r/d)^2,
  *                       (fy r/d)^2) + dilation; quaternion and log_scale[1..2] are unused.
  *   oc_render           Eq. 7-9: per-pixel brute force over all Gaussians, sorted by
- *                       depth (the float32 key of depth_key, then ascending Gaussian id),
- *                       front-to-back compositing of RGB, depth and C semantic channels.
+ *                       depth (the camera-space depth t_z rounded to float32, then ascending
+ *                       Gaussian id), front-to-back compositing of RGB, depth and C semantic
+ *                       channels.
  *   oc_render_backward  hand-derived adjoint of oc_render followed by the adjoint of
  *                       oc_project (Sec. III-D "perform backpropagation"), giving
  *                       dL/d{mean, log_scale, quat, opacity_logit, rgb, sem}.
@@ -55,7 +56,11 @@ enum {
     P_CLX, P_CLY,               /* Jacobian clamp active in x / y (0 or 1) */
     P_EXTX, P_EXTY,             /* half extents outside which alpha < alpha_min */
     P_LIMX, P_LIMY,             /* clamp limits of t_x/t_z and t_y/t_z */
-    P_DKEY                      /* depth ordering key (float32, see depth_key) */
+    P_DKEY,                     /* depth ordering key: t_z rounded to float32 */
+    P_DAMB,                     /* 1: t_z lies within DEPTH_KEY_BAND of a float32 rounding
+                                   midpoint, so the key is not decided (see depth_key) */
+    P_GEXTX, P_GEXTY            /* half extents outside which alpha < alpha_min / 2 (the
+                                   candidates gathered per pixel, for the ambiguity flags) */
 };
 
 /* Per-pixel ambiguity flags (reported, never used to change a result). */
@@ -129,18 +134,21 @@ static void jacobian(const cam_t *cam, const double t[3], double limx, double li
             T[3 * i + j] = J[3 * i] * W[j] + J[3 * i + 1] * W[3 + j] + J[3 * i + 2] * W[6 + j];
 }
 
-/* The sorted set N of Eq. 7-9 is ordered by depth.  The order is decided in float32 --
- * the precision of the GPU kernels -- so both sides take the same decision: the key is
- * t_z = ((R20 x + R21 y) + R22 z) + t_z0 evaluated with float32 inputs and a float32
- * rounding after every operation, in exactly this order.  Ties break by Gaussian id.  The
- * depth VALUE composited in Eq. 8 stays the double-precision t_z. */
-static float depth_key(const double *mean, const cam_t *cam) {
-    volatile float a = (float)cam->R[6] * (float)mean[0];
-    volatile float b = (float)cam->R[7] * (float)mean[1];
-    volatile float c = (float)cam->R[8] * (float)mean[2];
-    volatile float ab = a + b;
-    volatile float abc = ab + c;
-    volatile float key = abc + (float)cam->t[2];
+/* The sorted set N of Eq. 7-9 is ordered by depth: the key is the camera-space depth t_z
+ * (computed here in double precision) rounded to the nearest float32, ties broken by
+ * Gaussian id.  Any evaluation of t_z = R20 x + R21 y + R22 z + t_z0 whose error stays
+ * below DEPTH_KEY_BAND times the magnitude of its terms rounds to the same key, unless t_z
+ * itself lies within that distance of a midpoint between two float32 values; such a key
+ * is not decided by the definition and is flagged (*ambiguous = 1). */
+#define DEPTH_KEY_BAND 0x1p-40
+static float depth_key(const double *mean, const cam_t *cam, double tz, int *ambiguous) {
+    const float key = (float)tz;
+    const double lo = 0.5 * ((double)key + (double)nextafterf(key, -INFINITY));
+    const double hi = 0.5 * ((double)key + (double)nextafterf(key, INFINITY));
+    const double mag = fabs(cam->R[6] * mean[0]) + fabs(cam->R[7] * mean[1]) +
+                       fabs(cam->R[8] * mean[2]) + fabs(cam->t[2]);
+    const double band = DEPTH_KEY_BAND * mag;
+    *ambiguous = fabs(tz - lo) <= band || fabs(tz - hi) <= band;
     return key;
 }
 
@@ -153,7 +161,9 @@ static void project_one(const double *mean, const double *log_scale, const doubl
     for (int i = 0; i < 3; ++i)
         t[i] = W[3 * i] * mean[0] + W[3 * i + 1] * mean[1] + W[3 * i + 2] * mean[2] + cam->t[i];
     out[P_TX] = t[0]; out[P_TY] = t[1]; out[P_TZ] = t[2];
-    out[P_DKEY] = (double)depth_key(mean, cam);
+    int damb;
+    out[P_DKEY] = (double)depth_key(mean, cam, t[2], &damb);
+    out[P_DAMB] = damb;
     if (!(t[2] > cfg->z_near)) return;                    /* at or behind the near plane */
     double o = 1.0 / (1.0 + exp(-opacity_logit));
     out[P_OPAC] = o;
@@ -193,6 +203,9 @@ static void project_one(const double *mean, const double *log_scale, const doubl
     double thr = log(o / cfg->alpha_min);
     out[P_EXTX] = sqrt(2.0 * thr * s00) * (1.0 + 1e-9) + 1e-9;
     out[P_EXTY] = sqrt(2.0 * thr * s11) * (1.0 + 1e-9) + 1e-9;
+    double thr2 = log(2.0 * o / cfg->alpha_min);
+    out[P_GEXTX] = sqrt(2.0 * thr2 * s00) * (1.0 + 1e-9) + 1e-9;
+    out[P_GEXTY] = sqrt(2.0 * thr2 * s11) * (1.0 + 1e-9) + 1e-9;
     out[P_VALID] = 1.0;
 }
 
@@ -216,6 +229,9 @@ void oc_project(int N, const double *mean, const double *log_scale, const double
 typedef struct {
     float dkey;        /* depth rounded to float32: the ordering key */
     int id;            /* Gaussian id: tie-break */
+    int damb;          /* the key is undecided (P_DAMB) */
+    int order_amb;     /* an undecided key next to a key within one float32 step: the
+                          order of this candidate is not fixed by the definition */
     double raw;        /* o * exp(-sigma) before the clamp */
     double alpha;      /* min(alpha_max, raw) */
     double G;          /* exp(-sigma) */
@@ -238,7 +254,7 @@ static int gather(double x, double y, int N, const double *proj, const cfg_t *cf
         const double *p = proj + (size_t)OC_PROJ_STRIDE * i;
         if (p[P_VALID] == 0.0) continue;
         double dx = x - p[P_U], dy = y - p[P_V];
-        if (fabs(dx) > p[P_EXTX] || fabs(dy) > p[P_EXTY]) continue;   /* alpha < alpha_min */
+        if (fabs(dx) > p[P_GEXTX] || fabs(dy) > p[P_GEXTY]) continue; /* alpha < alpha_min / 2 */
         double sigma = 0.5 * (p[P_CA] * dx * dx + p[P_CC] * dy * dy) + p[P_CB] * dx * dy;
         if (sigma < 0) continue;
         double G = exp(-sigma);
@@ -248,33 +264,49 @@ static int gather(double x, double y, int N, const double *proj, const cfg_t *cf
         if (alpha < cfg->alpha_min * 0.5) continue;
         cand_t c;
         c.dkey = (float)p[P_DKEY]; c.id = i; c.raw = raw; c.alpha = alpha; c.G = G;
-        c.dx = dx; c.dy = dy;
+        c.dx = dx; c.dy = dy; c.damb = p[P_DAMB] != 0.0; c.order_amb = 0;
         buf[n++] = c;
     }
     qsort(buf, (size_t)n, sizeof(cand_t), cand_cmp);
+    /* an undecided key can move by one float32 step: it may then pass a neighbour whose
+       key is equal or one step away (keys are sorted, so the neighbours suffice) */
+    for (int k = 0; k < n; ++k) {
+        if (!buf[k].damb) continue;
+        const int32_t b = f32_bits(buf[k].dkey);
+        if (k > 0 && abs(b - f32_bits(buf[k - 1].dkey)) <= 1) buf[k].order_amb = buf[k - 1].order_amb = 1;
+        if (k + 1 < n && abs(b - f32_bits(buf[k + 1].dkey)) <= 1) buf[k].order_amb = buf[k + 1].order_amb = 1;
+    }
     return n;
 }
 
 /* Composites the sorted list.  Writes the contributing positions to contrib[] (indices
- * into buf) with their transmittance before them in Tb[]; returns their count.  Sets
- * the ambiguity flags with relative band tol. */
+ * into buf) with their transmittance before them in Tb[]; returns their count.
+ *
+ * Ambiguity flags: `tol` is the relative error of alpha that a float32 evaluation may make
+ * (o exp(-sigma) from float32 records).  A decision is flagged when the exact value lies
+ * within that evaluation's error of its threshold: raw alpha within tol of alpha_min (skip,
+ * F_SKIP) or of alpha_max (clamp, F_CLAMP); the transmittance T' = T (1 - alpha) within its
+ * propagated error of T_min (stop, F_STOP), where a float32 T' carries the relative errors
+ * of T, of (1 - alpha) (tol alpha / (1 - alpha), or the rounding of alpha_max when clamped)
+ * and two roundings; and a contributor whose depth order is undecided (F_DEPTH). */
 static int composite(const cand_t *buf, int n, const cfg_t *cfg, double tol, int *contrib,
                      double *Tb, double *T_out, int *flags) {
-    double T = 1.0;
+    double T = 1.0, eT = 0.0;
     int m = 0, fl = 0;
-    int prev = -1;
     for (int k = 0; k < n; ++k) {
         const cand_t *c = buf + k;
         if (fabs(c->raw - cfg->alpha_min) <= tol * cfg->alpha_min) fl |= F_SKIP;
         if (c->alpha < cfg->alpha_min) continue;
         if (fabs(c->raw - cfg->alpha_max) <= tol * cfg->alpha_max) fl |= F_CLAMP;
-        if (prev >= 0 && abs(f32_bits(c->dkey) - f32_bits(buf[prev].dkey)) <= 4) fl |= F_DEPTH;
-        prev = k;
+        if (c->order_amb) fl |= F_DEPTH;
         double Tn = T * (1.0 - c->alpha);
-        if (fabs(Tn - cfg->T_min) <= tol * cfg->T_min) fl |= F_STOP;
+        double ea = c->raw >= cfg->alpha_max ? 0x1p-24 : tol;
+        double eTn = eT + ea * c->alpha / (1.0 - c->alpha) + 0x1p-23;
+        if (fabs(Tn - cfg->T_min) <= eTn * cfg->T_min) fl |= F_STOP;
         if (Tn < cfg->T_min) break;
         contrib[m] = k; Tb[m] = T; ++m;
         T = Tn;
+        eT = eTn;
     }
     *T_out = T;
     *flags = fl;

@@ -20,7 +20,8 @@ namespace sg {
 struct ProjConsts {
     float z_near, dilation, fov_clamp, alpha_min;
     int tile_w, tile_h;
-    int isotropic;  // Eq. 2 projection instead of EWA
+    int isotropic;     // Eq. 2 projection instead of EWA
+    uint32_t *status;  // non-NULL: flag non-finite parameters (SG_STATUS_NUMERIC)
 };
 
 
@@ -80,11 +81,14 @@ __device__ __forceinline__ void view_geom(const sg_view &vw, const float mu[3], 
                                           ViewGeom &q) {
     for (int i = 0; i < 2; ++i)
         q.t[i] = vw.R[3 * i] * mu[0] + vw.R[3 * i + 1] * mu[1] + vw.R[3 * i + 2] * mu[2] + vw.t[i];
-    // camera z is also the depth ordering key of the tile lists: a fixed float32 evaluation
-    // order, ((R20 x + R21 y) + R22 z) + t_z, rounded after every operation
-    q.t[2] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(vw.R[6], mu[0]), __fmul_rn(vw.R[7], mu[1])),
-                                 __fmul_rn(vw.R[8], mu[2])),
-                       vw.t[2]);
+    // camera z is also the depth ordering key of the tile lists (the order of the set N of
+    // Eq. 7-9): t_z rounded to the nearest float32.  It is summed in double-float (exact
+    // products, error near 2^-46 of the terms), whose rounded head is the nearest float32 of
+    // the exact depth unless that lies within the sum's error of a rounding midpoint.
+    DF z = two_prod(vw.R[6], mu[0]);
+    z = df_add(z, two_prod(vw.R[7], mu[1]));
+    z = df_add(z, two_prod(vw.R[8], mu[2]));
+    q.t[2] = df_add_f(z, vw.t[2]).hi;
     const float tz = q.t[2];
     const float limx = fov_clamp * 0.5f * (float)vw.W / vw.fx;
     const float limy = fov_clamp * 0.5f * (float)vw.H / vw.fy;
@@ -233,6 +237,19 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     if (D > 0 && sh) {
         for (int i = 0; i < 3 * K; ++i) shv[i] = sh[(size_t)3 * K * g + i];
         for (int c = 0; c < 3; ++c) c0[c] = rgb[3 * g + c];
+    }
+    if (pc.status) {
+        // every parameter of the Gaussian the path reads
+        const float4 q = quat[g];
+        bool bad = !isfinite(q.x) || !isfinite(q.y) || !isfinite(q.z) || !isfinite(q.w) || !isfinite(ologit[g]);
+        for (int i = 0; i < 3; ++i)
+            bad |= !isfinite(mu[i]) || !isfinite(log_scale[3 * g + i]) || !isfinite(rgb[3 * g + i]);
+        for (int c = 0; c < C; ++c) bad |= !isfinite(sem[(size_t)C * g + c]);
+        if (D > 0 && sh)
+            for (int i = 0; i < 3 * K; ++i) bad |= !isfinite(shv[i]);
+        if (D > 0 && sem_sh)
+            for (int i = 0; i < K * C; ++i) bad |= !isfinite(sem_sh[(size_t)K * C * g + i]);
+        flag_status(bad, pc.status, SG_STATUS_NUMERIC);
     }
     for (int v = 0; v < n_views; ++v) {
         const sg_view &vw = s_views[v];
@@ -585,9 +602,9 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
 }
 
 sg_status launch_project_fwd(const sg_gaussians *g, const sg_view *views, int n_views,
-                             const sg_config *cfg, sg_projected *out, cudaStream_t st) {
+                             const sg_config *cfg, sg_projected *out, uint32_t *status, cudaStream_t st) {
     ProjConsts pc{cfg->z_near, cfg->dilation, cfg->fov_clamp, cfg->alpha_min, cfg->tile_w,
-                  cfg->tile_h, cfg->isotropic};
+                  cfg->tile_h, cfg->isotropic, status};
     const int threads = 256;
     const int blocks = (g->N + threads - 1) / threads;
     if (blocks > 0) {
@@ -609,7 +626,7 @@ sg_status launch_project_bwd(const sg_gaussians *g, const sg_view *views, int n_
                              const sg_config *cfg, const sg_projected *proj, float *g2d,
                              sg_gaussian_grads *gr, cudaStream_t st) {
     ProjConsts pc{cfg->z_near, cfg->dilation, cfg->fov_clamp, cfg->alpha_min, cfg->tile_w,
-                  cfg->tile_h, cfg->isotropic};
+                  cfg->tile_h, cfg->isotropic, nullptr};
     const int threads = 256;
     const int blocks = (g->N + threads - 1) / threads;
     if (blocks > 0) {

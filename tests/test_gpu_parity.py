@@ -1,11 +1,13 @@
 """GPU parity of the CUDA path (called through the C ABI) against the FP64 oracle.
 
 Forward: |gpu - oracle| <= 1e-4 |oracle| + 1e-5 per pixel and channel.  Gradients:
-|gpu - oracle| <= 2e-3 |oracle| + 1e-5 max|oracle| per element.  Tile lists: bit-exact
-against the oracle's integer reference built from the GPU's own float32 records.  Pixels
-whose skip (alpha vs 1/255), stop (T vs 1e-4) or depth-order decision lies within 1e-3
-(relative) of the threshold in the oracle are excluded (a float32 evaluation may take the
-other branch there); their count is asserted to be small.
+|gpu - oracle| <= 2e-3 |oracle| + 1e-6 max|oracle| per element.  Tile lists: against the
+FP64 definition of the set N per tile (every Gaussian whose alpha reaches 1/255 at a pixel of
+the tile is listed; every listed one comes close to the tile; inside each tile the order is
+(float32 key of the FP64 camera depth, index)).  Pixels where a decision of the method is not
+fixed for a float32 evaluation -- alpha within the measured float32 alpha error of the skip
+threshold, the transmittance within its propagated error of T_min, an undecided depth key
+next to a neighbouring key -- are excluded; their share is asserted to be below 0.1 %.
 """
 import numpy as np
 import pytest
@@ -13,7 +15,9 @@ import torch
 
 import oracle
 import synthetic
-from helpers import AMBIGUOUS, AMBIGUOUS_GRAD, FWD_ABS, FWD_REL, check_close, check_grads
+from helpers import (ALPHA_TOL, AMBIGUOUS, AMBIGUOUS_GRAD, FWD_ABS, FWD_REL, MAX_MASKED, check_close, check_grads,
+                     ref_render, unambiguous)
+from kernel_rules import tile_reaches_alpha_min
 
 pytestmark = pytest.mark.gpu
 
@@ -101,58 +105,122 @@ def test_projection_matches_oracle(cloud):
         assert tx1[i] - tx0[i] <= (x1 // 16 + 1 - x0 // 16) + 1 and ty1[i] - ty0[i] <= (y1 // 16 + 1 - y0 // 16) + 1
 
 
-def _lists_vs_reference(r):
+def _gpu_lists(r):
     torch.cuda.synchronize()
     assert int(r.status.item()) == 0
     K = r.instance_count()
     tiles = r.tile[:K].cpu().numpy().view(np.uint32).astype(np.int64)
     recs = r.record[:K].cpu().numpy().view(np.uint32).astype(np.int64)
     ranges = r.ranges.view(-1, 2).cpu().numpy().astype(np.int64)
+    return K, tiles, recs, ranges
+
+
+def _check_ranges_and_order(r, tiles, ranges):
+    """Ranges hold each tile's [start, end) ((0, 0) when empty); the work order lists every
+    tile once, by descending half-octave bucket of its instance count, ascending id within a
+    bucket."""
+    assert np.all(np.diff(tiles) >= 0)
+    t = np.arange(r.n_tiles)
+    starts, ends = np.searchsorted(tiles, t, "left"), np.searchsorted(tiles, t, "right")
+    expect = np.stack([np.where(starts == ends, 0, starts), np.where(starts == ends, 0, ends)], 1)
+    assert np.array_equal(ranges, expect)
+    n = ranges[:, 1] - ranges[:, 0]
+    lz = np.floor(np.log2(np.maximum(n, 1))).astype(np.int64)
+    sub = np.where(lz >= 1, (n >> np.maximum(lz - 1, 0)) & 1, 0)
+    bucket = np.where(n > 0, 1 + 2 * lz + sub, 0)
+    assert np.array_equal(r.order.cpu().numpy().astype(np.int64), np.argsort(-bucket, kind="stable"))
+
+
+def lists_match_definition(r, g, ocams):
+    """PRIMARY tile-list parity, against the FP64 definition of the set N of Eq. 7-9 per tile
+    (oracle.tile_pairs / tile_reach / the projection's depth key), independent of every float32
+    rule of the kernels:
+      * every (Gaussian, tile) whose alpha reaches 1/255 at a pixel centre of the tile is listed
+        (pairs within the float32 alpha error of the threshold may go either way);
+      * every listed pair comes close to its tile: the least exponent of the footprint over the
+        tile's pixel-centre rectangle is at most ln(o / alpha_min) + 2e-3 (the lists' margin);
+      * inside each tile the records follow (float32 key of the FP64 depth, record index),
+        except next to an undecided key.
+    Returns (instances, pairs that must be listed, listed pairs that reach no pixel)."""
+    K, tiles, recs, ranges = _gpu_lists(r)
+    _check_ranges_and_order(r, tiles, ranges)
+    tw, th, N = r.cfg.tile_w, r.cfg.tile_h, r.N
+    amin = 1.0 / 255.0
+    key = np.zeros(r.V * N, np.float32)
+    damb = np.zeros(r.V * N, bool)
+    n_must = n_extra = 0
+    for v, oc in enumerate(ocams):
+        vh = r.views_host[v]
+        pr = oracle.project(g, oc)
+        key[v * N:(v + 1) * N] = pr[:, oracle.P["DKEY"]]
+        damb[v * N:(v + 1) * N] = pr[:, oracle.P["DAMB"]] > 0
+        sel = (recs // N) == v
+        gi = recs[sel] % N
+        loc = tiles[sel] - vh.tile_offset
+        assert np.all((loc >= 0) & (loc < vh.tiles_x * vh.tiles_y))
+        gtx, gty = loc % vh.tiles_x, loc // vh.tiles_x
+        listed = set(zip(gi.tolist(), gtx.tolist(), gty.tolist()))
+        assert len(listed) == int(sel.sum()), "a (Gaussian, tile) pair is listed twice"
+        fg, ftx, fty = oracle.tile_pairs(pr, oc, tw, th)
+        reach = oracle.tile_reach(pr, oc, fg, ftx, fty, tw, th)
+        must = reach["alpha"] >= amin * (1 + ALPHA_TOL)
+        missing = [p for p in zip(fg[must].tolist(), ftx[must].tolist(), fty[must].tolist()) if p not in listed]
+        assert not missing, f"view {v}: {len(missing)} (Gaussian, tile) pairs reach alpha_min but are not listed: {missing[:5]}"
+        got = oracle.tile_reach(pr, oc, gi, gtx, gty, tw, th)
+        far = ~(got["sigma_min"] <= got["thr"] + 2e-3 + 1e-4 * np.abs(got["thr"]))
+        assert not far.any(), f"view {v}: {int(far.sum())} listed pairs the footprint does not reach"
+        n_must += int(must.sum())
+        n_extra += int((got["alpha"] < amin).sum())
+    same = tiles[1:] == tiles[:-1]
+    a, b = recs[:-1][same], recs[1:][same]
+    ka, kb = key[a].view(np.int32).astype(np.int64), key[b].view(np.int32).astype(np.int64)
+    in_order = (ka < kb) | ((ka == kb) & (a < b))
+    undecided = (damb[a] | damb[b]) & (np.abs(ka - kb) <= 1)
+    assert np.all(in_order | undecided), f"{int((~in_order & ~undecided).sum())} adjacent pairs out of depth order"
+    assert undecided.mean() < 1e-3 if len(undecided) else True
+    return K, n_must, n_extra
+
+
+def lists_match_kernel_rule(r):
+    """KERNEL UNIT TEST (not parity with the paper's definition): given the kernels' own
+    float32 records and their float32 culling rule (kernel_rules.py), the emitted lists are
+    bit-exactly the (tile, depth bits, record) order that oracle.tile_lists defines -- this
+    isolates the sort and emission kernels from the projection's rounding."""
+    K, tiles, recs, ranges = _gpu_lists(r)
     rect = r.rect.view(-1, 2).cpu().numpy().view(np.uint32)
     rects = np.stack([rect[:, 0] & 0xFFFF, rect[:, 0] >> 16, rect[:, 1] & 0xFFFF, rect[:, 1] >> 16], 1)
     depth = r.geo.view(-1, 8)[:, 2].cpu().numpy()
     tx = [r.views_host[v].tiles_x for v in range(r.V)]
     to = [r.views_host[v].tile_offset for v in range(r.V)]
-    # the culling rule, taken in float32 from the GPU's own records (like the depth order)
     geo = r.geo.view(-1, 8).cpu().numpy()
     ext = r.ext.view(-1, 2).cpu().numpy()
     tw, th = r.cfg.tile_w, r.cfg.tile_h
     Wv = np.array([r.views_host[v].W for v in range(r.V)])
     Hv = np.array([r.views_host[v].H for v in range(r.V)])
 
-    def keep(recs, tx_, ty_):
-        v = recs // r.N
+    def keep(recs_, tx_, ty_):
+        v = recs_ // r.N
         X0, Y0 = tx_ * tw, ty_ * th
-        return oracle.tile_reaches_alpha_min(geo[recs], ext[recs], X0, np.minimum(X0 + tw - 1, Wv[v] - 1),
-                                             Y0, np.minimum(Y0 + th - 1, Hv[v] - 1))
+        return tile_reaches_alpha_min(geo[recs_], ext[recs_], X0, np.minimum(X0 + tw - 1, Wv[v] - 1),
+                                      Y0, np.minimum(Y0 + th - 1, Hv[v] - 1))
 
     rt, rr, rg = oracle.tile_lists(rects, depth, tx, to, r.n_tiles, r.N, keep=keep)
-    # culling removes instances of every rectangle-covered tile that no pixel can reach
-    rr64 = rects.astype(np.int64)
-    n_rect = int((np.maximum(0, rr64[:, 2] - rr64[:, 0]) * np.maximum(0, rr64[:, 3] - rr64[:, 1])).sum())
-    assert K <= n_rect
     assert K == len(rt)
     assert np.array_equal(tiles, rt)
     assert np.array_equal(recs, rr)
     assert np.array_equal(ranges, rg)
-    # work order: every tile once, by descending half-octave bucket of its instance count,
-    # ascending tile id within a bucket
-    n = rg[:, 1] - rg[:, 0]
-    lz = np.floor(np.log2(np.maximum(n, 1))).astype(np.int64)
-    sub = np.where(lz >= 1, (n >> np.maximum(lz - 1, 0)) & 1, 0)
-    bucket = np.where(n > 0, 1 + 2 * lz + sub, 0)
-    expected = np.argsort(-bucket, kind="stable")
-    assert np.array_equal(r.order.cpu().numpy().astype(np.int64), expected)
     return K
 
 
-def test_tile_lists_bit_exact_single_view(cloud):
+def test_tile_lists_match_definition_single_view(cloud):
     g, cam = cloud
     for tw, th in ((16, 16), (8, 8), (32, 8)):
         r, p = make(g, [cam], tile_w=tw, tile_h=th)
         r.project(p)
         r.build_lists()
-        assert _lists_vs_reference(r) > 2000
+        K, n_must, n_extra = lists_match_definition(r, g, [cam])
+        assert K > 2000 and n_must > 0.5 * K
+        assert lists_match_kernel_rule(r) == K
 
 
 def room_small(n=20000, C=16, seed=4, ncam=2, W=320, H=180):
@@ -163,12 +231,14 @@ def room_small(n=20000, C=16, seed=4, ncam=2, W=320, H=180):
     return room, g, cams
 
 
-def test_tile_lists_bit_exact_pyramid_multi_view():
+def test_tile_lists_match_definition_pyramid_multi_view():
     room, g, cams = room_small()
     r, p = make(g, cams, levels=3)
     r.project(p)
     r.build_lists()
-    assert _lists_vs_reference(r) > 10000
+    K, n_must, n_extra = lists_match_definition(r, g, oracle_cams(cams, 3))
+    assert K > 10000 and n_must > 0.5 * K
+    assert lists_match_kernel_rule(r) == K
 
 
 @pytest.mark.parametrize("isotropic", [False, True])
@@ -177,10 +247,8 @@ def test_forward_matches_oracle_cloud(cloud, isotropic):
     r, p = make(g, [cam], isotropic=isotropic)
     r.forward(p)
     got = view_images(r, 0, 8)
-    ref = oracle.render(g, cam, dict(isotropic=int(isotropic)))
-    amb = (ref["flags"] & AMBIGUOUS) != 0
-    assert amb.mean() < 0.02
-    ok = ~amb
+    ref = ref_render(g, cam, dict(isotropic=int(isotropic)))
+    ok = unambiguous(ref["flags"])
     for k in ("rgb", "depth", "sem", "T"):
         check_close(k, got[k], ref[k], FWD_REL, FWD_ABS, mask=ok)
     assert np.array_equal(got["n_contrib"][ok], ref["n_contrib"][ok])
@@ -209,8 +277,8 @@ def test_backward_matches_oracle_cloud(cloud, ppt, batch_bwd, isotropic):
     r, p = make(g, [cam], pixels_per_thread_bwd=ppt, batch_bwd=batch_bwd, isotropic=isotropic)
     r.forward(p)
     ocfg = dict(isotropic=int(isotropic))
-    ref_f = oracle.render(g, cam, ocfg)
-    keep = ((ref_f["flags"] & AMBIGUOUS_GRAD) == 0).astype(np.float64)
+    ref_f = ref_render(g, cam, ocfg)
+    keep = unambiguous(ref_f["flags"], AMBIGUOUS_GRAD).astype(np.float64)
     rng = np.random.default_rng(11)
     H, W, C = cam["H"], cam["W"], 8
     up_rgb = rng.normal(size=(3, H, W)) * keep
@@ -329,12 +397,12 @@ def test_multiview_pyramid_forward_backward_matches_oracle(isotropic):
     ups = []
     for v, oc in enumerate(ocams):
         got = view_images(r, v, 16)
-        ref = oracle.render(g, oc, ocfg)
-        amb = (ref["flags"] & AMBIGUOUS) != 0
-        assert amb.mean() < 0.03
+        ref = ref_render(g, oc, ocfg)
+        ok = unambiguous(ref["flags"], limit=max(MAX_MASKED, 1.0 / ref["flags"].size))
         for k in ("rgb", "depth", "sem", "T"):
-            check_close(f"v{v} {k}", got[k], ref[k], FWD_REL, FWD_ABS, mask=~amb)
-        keep = ((ref["flags"] & AMBIGUOUS_GRAD) == 0).astype(np.float64)
+            check_close(f"v{v} {k}", got[k], ref[k], FWD_REL, FWD_ABS, mask=ok)
+        assert np.array_equal(got["n_contrib"][ok], ref["n_contrib"][ok])
+        keep = unambiguous(ref["flags"], AMBIGUOUS_GRAD, limit=max(MAX_MASKED, 1.0 / ref["flags"].size)).astype(np.float64)
         H, W = oc["H"], oc["W"]
         ups.append((rng.normal(size=(3, H, W)) * keep, rng.normal(size=(H, W)) * keep,
                     rng.normal(size=(16, H, W)) * keep))
@@ -434,66 +502,47 @@ def test_adam_multi_matches_numpy(sizes, offset):
         assert not bufs[1].any()
 
 
-def test_tile_lists_against_the_oracles_own_projection():
-    """Independent of the kernels' records: the oracle projects in FP64, rounds its own
-    float32 records (record format of sg.h, its own float32 depth key) and builds the lists
-    with the same culling rule.  The GPU lists hold the same (tile, record) pairs except a few
-    at the boundary of an extent or of the culling rule, and each of those is harmless (no
-    pixel of the tile reaches alpha >= 1/255, by FP64 brute force); inside every tile the
-    common records come in the same (depth key, record) order."""
-    from test_oracle_pyramid_tiles import _records_f32
-    room, g, cams = room_small(n=8000, ncam=2, W=200, H=120)
-    T, levels = 8, 3
-    r, p = make(g, cams, levels=levels, tile_w=T, tile_h=T)
-    r.project(p)
-    r.build_lists()
-    torch.cuda.synchronize()
-    assert int(r.status.item()) == 0
-    K = r.instance_count()
-    tiles_g = r.tile[:K].cpu().numpy().view(np.uint32).astype(np.int64)
-    recs_g = r.record[:K].cpu().numpy().view(np.uint32).astype(np.int64)
-    P = oracle.P
-    N = r.N
-    ocams = oracle_cams(cams, levels)
-    prs, geo, ext, rects, dkey = [], [], [], [], []
-    for oc in ocams:
-        pr = oracle.project(g, oc)
-        gv, ev, rv = _records_f32(pr, oc, T)
-        prs.append(pr); geo.append(gv); ext.append(ev); rects.append(rv)
-        dkey.append(pr[:, P["DKEY"]].astype(np.float32))
-    geo, ext, rects, dkey = np.concatenate(geo), np.concatenate(ext), np.concatenate(rects), np.concatenate(dkey)
-    Wv = np.array([oc["W"] for oc in ocams]); Hv = np.array([oc["H"] for oc in ocams])
-    tx = [r.views_host[v].tiles_x for v in range(r.V)]
-    to = [r.views_host[v].tile_offset for v in range(r.V)]
-
-    def keep(recs, tx_, ty_):
-        v = recs // N
-        X0, Y0 = tx_ * T, ty_ * T
-        return oracle.tile_reaches_alpha_min(geo[recs], ext[recs], X0, np.minimum(X0 + T - 1, Wv[v] - 1),
-                                             Y0, np.minimum(Y0 + T - 1, Hv[v] - 1))
-
-    tiles_o, recs_o, _ = oracle.tile_lists(rects, dkey, tx, to, r.n_tiles, N, keep=keep)
-    pairs_g = set(zip(tiles_g.tolist(), recs_g.tolist()))
-    pairs_o = set(zip(tiles_o.tolist(), recs_o.tolist()))
-    assert len(pairs_g) == K  # no duplicates
-    diff = pairs_g ^ pairs_o
-    assert len(diff) <= 0.002 * len(pairs_o), (len(diff), len(pairs_o))
-    for t, rec in diff:  # boundary pairs reach no pixel
-        v = rec // N
-        pr = prs[v][rec % N]
-        loc = t - to[v]
-        X0, Y0 = (loc % tx[v]) * T, (loc // tx[v]) * T
-        xs, ys = np.meshgrid(np.arange(X0, min(X0 + T, Wv[v])) - pr[P["U"]], np.arange(Y0, min(Y0 + T, Hv[v])) - pr[P["V"]])
-        sig = 0.5 * (pr[P["CA"]] * xs * xs + 2 * pr[P["CB"]] * xs * ys + pr[P["CC"]] * ys * ys)
-        assert pr[P["OPAC"]] * np.exp(-sig).max() < 1 / 255, (t, rec)
-    # order inside every tile: the common records in the same order on both sides
-    common = pairs_g & pairs_o
-    seq_g, seq_o = {}, {}
-    for t, rec in zip(tiles_g.tolist(), recs_g.tolist()):
-        if (t, rec) in common:
-            seq_g.setdefault(t, []).append(rec)
-    for t, rec in zip(tiles_o.tolist(), recs_o.tolist()):
-        if (t, rec) in common:
-            seq_o.setdefault(t, []).append(rec)
-    assert seq_g == seq_o
-    assert len(common) > 20000
+def test_alpha_float32_error_is_within_the_band():
+    """The ambiguity band of every parity test (helpers.ALPHA_TOL) bounds the relative error of
+    the kernels' float32 alpha: isolated Gaussians (rotated, elongated, opacities 0.05-0.98,
+    a general camera pose) with colour (1, 0, 0) render rgb[0] = alpha at every pixel they
+    reach, which the oracle gives in FP64.  Also: no such pixel is skipped or kept on the wrong
+    side of 1/255 outside the band."""
+    rng = np.random.default_rng(31)
+    W, H, cell = 320, 240, 20
+    cam = synthetic.make_camera(W, H, 300.0, 300.0, 159.5, 119.5)
+    a = 0.2
+    R = np.array([[np.cos(a), 0, np.sin(a)], [0, 1, 0], [-np.sin(a), 0, np.cos(a)]])
+    cam = f32_camera(dict(cam, R_cw=R, t_cw=np.array([0.05, -0.02, 0.1])))
+    nx, ny = W // cell, H // cell
+    n = nx * ny
+    z = rng.uniform(2.0, 4.0, n)
+    cx, cy = (np.arange(n) % nx) * cell + cell / 2, (np.arange(n) // nx) * cell + cell / 2
+    u = (cx + rng.uniform(-2, 2, n) - cam["cx"]) / cam["fx"] * z
+    v = (cy + rng.uniform(-2, 2, n) - cam["cy"]) / cam["fy"] * z
+    pc = np.stack([u, v, z], 1)
+    Rc, tc = np.asarray(cam["R_cw"]).reshape(3, 3), np.asarray(cam["t_cw"])
+    mean = (pc - tc) @ Rc          # world point with R mean + t = pc
+    q = rng.normal(size=(n, 4))
+    s = np.stack([rng.uniform(0.004, 0.012, n), rng.uniform(0.0015, 0.006, n), rng.uniform(0.002, 0.008, n)], 1)
+    o = rng.uniform(0.05, 0.98, n)
+    f32 = lambda x: np.ascontiguousarray(x, np.float32)
+    g = dict(mean=f32(mean), log_scale=f32(np.log(s)), quat=f32(q / np.linalg.norm(q, axis=1, keepdims=True)),
+             opacity_logit=f32(np.log(o / (1 - o))), rgb=f32(np.tile([1.0, 0.0, 0.0], (n, 1))),
+             sem=f32(np.zeros((n, 4))))
+    r, p = make(g, [cam])
+    r.forward(p)
+    got = view_images(r, 0, 4)
+    ref = ref_render(g, cam)
+    assert ref["n_contrib"].max() == 1  # isolated footprints
+    al = ref["rgb"][0]
+    amin, amax = 1 / 255, 0.99
+    sel = (al >= amin * (1 + ALPHA_TOL)) & (al <= amax * (1 - ALPHA_TOL))
+    assert sel.sum() > 5000
+    rel = np.abs(got["rgb"][0][sel] - al[sel]) / al[sel]
+    print(f"float32 alpha relative error: max {rel.max():.3e}, p99.9 {np.quantile(rel, 0.999):.3e} "
+          f"over {sel.sum()} pixels")
+    assert rel.max() <= ALPHA_TOL, rel.max()
+    # pixels the oracle skips outside the band are skipped by the kernels too
+    below = (al == 0) & ((ref["flags"] & oracle.FLAG_SKIP) == 0)
+    assert np.all(got["rgb"][0][below] == 0)

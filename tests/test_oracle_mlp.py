@@ -53,3 +53,44 @@ def test_bf16_rounding_is_nearest_even():
     assert mlp.bf16(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
     assert mlp.bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
     assert mlp.bf16(np.array([-3.0]))[0] == -3.0
+
+
+def test_bf16_rounding_ambiguity_marks_exactly_the_undecided_values():
+    """A value at a bf16 midpoint (1 + 2^-8 lies halfway between 1 and 1 + 2^-7) is undecided
+    for any band; 1 + 2^-7 (a bf16 value) only for a band reaching the midpoints 2^-8 away;
+    after a ReLU, -1 is decided (0) and a value within the band of 0 is not."""
+    nb = mlp._near_bf16_boundary
+    assert nb(np.array([1 + 2 ** -8]), 1e-12).all()
+    assert not nb(np.array([1 + 2 ** -7]), 2 ** -9).any()
+    assert nb(np.array([1 + 2 ** -7]), 2 ** -8).all()
+    assert nb(np.array([-(3 + 2 ** -7)]), 1e-12).all()          # 3 + 2^-7: a midpoint in the [2, 4) binade
+    assert not nb(np.array([-(3 + 2 ** -6)]), 1e-12).any()      # 3 + 2^-6: a bf16 value there
+    ru = mlp._relu_bf16_undecided
+    assert not ru(np.array([-1.0]), 1e-6).any()
+    assert ru(np.array([-1e-7, 1e-7]), 1e-6).all()
+    # the band is a rounding band: rounding decided values to bf16 lands on the same bf16 value
+    rng = np.random.default_rng(4)
+    v = rng.normal(size=20000)
+    band = 1e-4 * np.abs(v)
+    ok = ~nb(v, band)
+    assert ok.mean() > 0.9
+    assert np.array_equal(mlp.bf16(v[ok] + band[ok] * 0.999), mlp.bf16(v[ok]))
+    assert np.array_equal(mlp.bf16(v[ok] - band[ok] * 0.999), mlp.bf16(v[ok]))
+
+
+def test_undecided_rows_are_row_local():
+    """Changing one row's input or target changes only that row's flag."""
+    rng = np.random.default_rng(5)
+    W1, b1, W2, b2, W3, b3 = (mlp.bf16(a) for a in small_net(rng, din=64, h=16, dout=8))
+    X = mlp.bf16(rng.normal(size=(32, 64)))
+    T = rng.normal(size=(32, 8))
+    w = np.ones(8)
+    und = mlp.undecided_rows(X, T, w, W1, b1, W2, b2, W3, b3, rel=2e-5)
+    X2, T2 = X.copy(), T.copy()
+    X2[5] = mlp.bf16(rng.normal(size=64))
+    T2[9] = rng.normal(size=8)
+    und2 = mlp.undecided_rows(X2, T2, w, W1, b1, W2, b2, W3, b3, rel=2e-5)
+    keep = np.ones(32, bool)
+    keep[[5, 9]] = False
+    assert np.array_equal(und[keep], und2[keep])
+    assert und.any() and not und.all()

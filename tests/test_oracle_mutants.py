@@ -40,8 +40,10 @@ MUTANTS = [
     ("proj_x_extent_from_y_variance", "sg_oracle.c", "out[P_EXTX] = sqrt(2.0 * thr * s00)",
      "out[P_EXTX] = sqrt(2.0 * thr * s11)"),
     ("proj_isotropic_fx_for_y", "sg_oracle.c", "ry = cam->fy * r / t[2];", "ry = cam->fx * r / t[2];"),
-    ("proj_depth_key_wrong_row", "sg_oracle.c", "volatile float a = (float)cam->R[6] * (float)mean[0];",
-     "volatile float a = (float)cam->R[0] * (float)mean[0];"),
+    ("proj_depth_key_from_tx", "sg_oracle.c", "out[P_DKEY] = (double)depth_key(mean, cam, t[2], &damb);",
+     "out[P_DKEY] = (double)depth_key(mean, cam, t[0], &damb);"),
+    ("proj_depth_midpoint_band_ignored", "sg_oracle.c", "*ambiguous = fabs(tz - lo) <= band || fabs(tz - hi) <= band;",
+     "*ambiguous = 0;"),
     ("proj_fov_limit_y_uses_W", "sg_oracle.c", "double limy = cfg->fov_clamp * 0.5 * cam->H / cam->fy;",
      "double limy = cfg->fov_clamp * 0.5 * cam->W / cam->fy;"),
     ("proj_fov_limit_x_uses_fy", "sg_oracle.c", "double limx = cfg->fov_clamp * 0.5 * cam->W / cam->fx;",
@@ -57,6 +59,13 @@ MUTANTS = [
     ("proj_v_uses_cx", "sg_oracle.c", "out[P_V] = cam->fy * t[1] / t[2] + cam->cy;",
      "out[P_V] = cam->fy * t[1] / t[2] + cam->cx;"),
     # ---- compositing (Eq. 7-9) ----
+    ("comp_depth_order_flag_dropped", "sg_oracle.c", "        if (c->order_amb) fl |= F_DEPTH;\n", "\n"),
+    ("comp_stop_band_without_propagation", "sg_oracle.c",
+     "double eTn = eT + ea * c->alpha / (1.0 - c->alpha) + 0x1p-23;", "double eTn = 0x1p-23;"),
+    ("comp_skip_band_dropped", "sg_oracle.c",
+     "        if (fabs(c->raw - cfg->alpha_min) <= tol * cfg->alpha_min) fl |= F_SKIP;\n", "\n"),
+    ("comp_gather_stops_at_exact_extent", "sg_oracle.c",
+     "if (fabs(dx) > p[P_GEXTX] || fabs(dy) > p[P_GEXTY]) continue;", "if (fabs(dx) > p[P_EXTX] || fabs(dy) > p[P_EXTY]) continue;"),
     ("comp_sigma_cross_term_halved", "sg_oracle.c", "+ p[P_CB] * dx * dy;", "+ 0.5 * p[P_CB] * dx * dy;"),
     ("comp_alpha_clamp_dropped", "sg_oracle.c", "double alpha = raw < cfg->alpha_max ? raw : cfg->alpha_max;",
      "double alpha = raw;"),
@@ -71,8 +80,8 @@ MUTANTS = [
     ("comp_ties_by_descending_id", "sg_oracle.c", "return (a->id > b->id) - (a->id < b->id);",
      "return (a->id < b->id) - (a->id > b->id);"),
     ("comp_background_not_weighted_by_T", "sg_oracle.c", "acc[ch] + T * cfg.bg[ch];", "acc[ch] + cfg.bg[ch];"),
-    ("comp_extent_filter_too_tight", "sg_oracle.c", "if (fabs(dx) > p[P_EXTX] || fabs(dy) > p[P_EXTY]) continue;",
-     "if (fabs(dx) > 0.5 * p[P_EXTX] || fabs(dy) > p[P_EXTY]) continue;"),
+    ("comp_extent_filter_too_tight", "sg_oracle.c", "if (fabs(dx) > p[P_GEXTX] || fabs(dy) > p[P_GEXTY]) continue;",
+     "if (fabs(dx) > 0.5 * p[P_GEXTX] || fabs(dy) > p[P_GEXTY]) continue;"),
     ("comp_candidates_prefiltered_too_tight", "sg_oracle.c", "if (alpha < cfg->alpha_min * 0.5) continue;",
      "if (alpha < cfg->alpha_min * 2.0) continue;"),
     ("comp_transmittance_update", "sg_oracle.c", "        T = Tn;\n", "        T = T * c->alpha;\n"),
@@ -186,19 +195,19 @@ MUTANTS = [
     # ---- tile lists ----
     ("tiles_record_before_depth", "__init__.py", "order = np.lexsort((recs, dbits, tiles))",
      "order = np.lexsort((dbits, recs, tiles))"),
-    ("tiles_culling_threshold_too_tight", "__init__.py", "* f(1.0 / 1.002)) * m00", "* f(1.0 / 1.2)) * m00"),
-    ("tiles_culling_left_edge_sign", "__init__.py", "xl = (-(B * dl) - s_of(dl)) / A",
-     "xl = ((B * dl) - s_of(dl)) / A"),
-    ("tiles_culling_extreme_point_sign", "__init__.py", "dyr = -((B * dxmax) / Cq)", "dyr = ((B * dxmax) / Cq)"),
-    ("tiles_culling_band_lower_edge", "__init__.py", "yb0 = np.fmax(y0, -dymax)", "yb0 = np.fmax(y0, dymax)"),
+    ("tile_reach_cross_term_halved", "__init__.py", "sig = 0.5 * (a[:, None] * dx * dx + c[:, None] * dy * dy) + b[:, None] * dx * dy",
+     "sig = 0.5 * (a[:, None] * dx * dx + c[:, None] * dy * dy) + 0.5 * b[:, None] * dx * dy"),
+    ("tile_reach_last_pixel_column_dropped", "__init__.py", "inside = (xs <= X1[:, None])", "inside = (xs < X1[:, None])"),
+    ("tile_reach_edge_minimum_unclamped", "__init__.py", "best = np.minimum(best, q(x, np.clip(-B * x / C, y0, y1)))",
+     "best = np.minimum(best, q(x, -B * x / C))"),
+    ("tile_pairs_y_extent_from_x", "__init__.py", 'u, v, ex, ey = p[i, P["U"]], p[i, P["V"]], p[i, P["EXTX"]], p[i, P["EXTY"]]',
+     'u, v, ex, ey = p[i, P["U"]], p[i, P["V"]], p[i, P["EXTX"]], p[i, P["EXTX"]]'),
     ("tiles_rectangle_row_past_end", "__init__.py", "for ty in range(ty0, ty1):", "for ty in range(ty0, ty1 + 1):"),
-    ("tiles_culling_band_test_dropped", "__init__.py", "keep = (yb0 <= yb1) & ", "keep = "),
     ("tiles_view_offset_ignored", "__init__.py", "tiles.append(tile_offset[v] + ty * n_tiles_x[v] + tx)",
      "tiles.append(tile_offset[0] + ty * n_tiles_x[v] + tx)"),
     ("tiles_row_width_of_first_view", "__init__.py", "tiles.append(tile_offset[v] + ty * n_tiles_x[v] + tx)",
      "tiles.append(tile_offset[v] + ty * n_tiles_x[0] + tx)"),
     ("tiles_empty_range_not_zeroed", "__init__.py", "        ranges[empty] = 0\n", "        pass\n"),
-    ("tiles_culling_threshold_not_squared", "__init__.py", "        thr = t * t\n", "        thr = t\n"),
     # ---- insertion: heuristic initializer, patch features, network outputs ----
     ("init_mean_rotation_untransposed", "init.py", "mean = (pc - t) @ R            # rows: R^T (p - t)",
      "mean = (pc - t) @ R.T"),

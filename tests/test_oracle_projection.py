@@ -149,24 +149,32 @@ def test_near_plane_and_tiny_opacity_cull():
     assert oracle.project(one([0, 0, 2.0], [-3] * 3, logit=-6.0), cam)[0][P["VALID"]] == 0
 
 
-def test_depth_key_is_camera_depth_to_float32_rounding():
-    """The ordering key of the sorted set N (Eq. 7-9) is the camera-space depth t_z, taken in
-    float32: for a general pose it lies within the rounding bound of a five-operation float32
-    evaluation (inputs rounded, three products, three sums) of t_z = R20 x + R21 y + R22 z + t_z0,
-    so two Gaussians whose depths differ by more than twice the bound are keyed in depth order."""
+def test_depth_key_is_camera_depth_rounded_to_float32():
+    """The ordering key of the sorted set N (Eq. 7-9) is the camera-space depth t_z rounded to
+    the nearest float32: for a general pose it equals float32(R20 x + R21 y + R22 z + t_z0)
+    summed exactly (fractions), and only depths within 2^-40 of their terms' magnitude of a
+    float32 rounding midpoint are flagged as undecided."""
+    from fractions import Fraction as F
     rng = np.random.default_rng(6)
     a = 0.5
     R = np.array([[1, 0, 0], [0, math.cos(a), -math.sin(a)], [0, math.sin(a), math.cos(a)]]) @ \
         np.array([[math.cos(0.3), 0, math.sin(0.3)], [0, 1, 0], [-math.sin(0.3), 0, math.cos(0.3)]])
-    t0 = np.array([0.3, -0.2, 0.7])
+    R = R.astype(np.float32).astype(np.float64)
+    t0 = np.array([0.3, -0.2, 0.7], np.float32).astype(np.float64)
     cam = synthetic.make_camera(64, 48, 60, 60, 32, 24, R_cw=R, t_cw=t0)
-    u = 2.0 ** -24
-    for _ in range(200):
-        m = rng.uniform(-3, 3, 3)
-        tz = R[2] @ m + t0[2]
-        key = oracle.project(one(m, [-3] * 3), cam)[0][P["DKEY"]]
-        bound = 8 * u * (np.abs(R[2] * m).sum() + abs(t0[2]))
-        assert abs(key - tz) <= bound, (m, key, tz)
+    for _ in range(300):
+        m = rng.uniform(-3, 3, 3).astype(np.float32).astype(np.float64)
+        exact = sum(F(float(R[2, i])) * F(float(m[i])) for i in range(3)) + F(float(t0[2]))
+        pr = oracle.project(one(m, [-3] * 3), cam)[0]
+        assert pr[P["DKEY"]] == float(np.float32(float(exact))), (m, pr[P["DKEY"]], float(exact))
+        if float(exact) > 0.5:  # no cancellation: far from any midpoint at this band
+            assert pr[P["DAMB"]] == 0
+    # an exact midpoint between 1.0f and the next float32 is undecided; its neighbours are not
+    cam0 = synthetic.make_camera(64, 48, 60, 60, 32, 24)
+    for z, amb in ((1.0 + 2.0 ** -24, 1), (1.0 + 2.0 ** -23, 0), (1.0, 0), (1.0 + 2.0 ** -24 + 2.0 ** -38, 0)):
+        pr = oracle.project(one([0.0, 0.0, z], [-3] * 3), cam0)[0]
+        assert pr[P["DAMB"]] == amb, z
+        assert pr[P["DKEY"]] == float(np.float32(z))
 
 
 def test_extents_are_exact_bounds():

@@ -113,117 +113,6 @@ def test_tile_lists_empty_tiles_have_range_zero():
     assert ranges.tolist() == [[0, 2], [0, 0], [2, 3], [0, 0]]
 
 
-def _records_f32(pr, cam, T):
-    """Float32 records (u_frac, v_frac, depth, opacity, m00, m10, m11, packed int16 mean),
-    half extents and tile rectangles in the projection's format, from the FP64 projection."""
-    P = oracle.P
-    v = pr[:, P["VALID"]] > 0
-    u, vv = pr[:, P["U"]], pr[:, P["V"]]
-    s00, s01, s11 = pr[:, P["S00"]], pr[:, P["S01"]], pr[:, P["S11"]]
-    o = pr[:, P["OPAC"]]
-    det = s00 * s11 - s01 * s01
-    with np.errstate(all="ignore"):
-        thr = np.log(o * 255.0) + 1e-3
-        ex = np.sqrt(2 * thr * s00) * 1.002 + 0.01
-        ey = np.sqrt(2 * thr * s11) * 1.002 + 0.01
-        ui, vi = np.rint(u), np.rint(vv)
-        geo = np.zeros((len(u), 8), np.float32)
-        geo[:, 0], geo[:, 1], geo[:, 2], geo[:, 3] = u - ui, vv - vi, pr[:, P["TZ"]], o
-        geo[:, 4] = 1 / np.sqrt(2 * s00)
-        geo[:, 5] = -s01 / np.sqrt(2 * s00 * det)
-        geo[:, 6] = np.sqrt(s00 / (2 * det))
-        packed = (ui.astype(np.int64) & 0xFFFF) | ((vi.astype(np.int64) & 0xFFFF) << 16)
-        geo[:, 7] = packed.astype(np.uint32).view(np.float32)
-        x0 = np.maximum(np.ceil(u - ex), 0); x1 = np.minimum(np.floor(u + ex), cam["W"] - 1)
-        y0 = np.maximum(np.ceil(vv - ey), 0); y1 = np.minimum(np.floor(vv + ey), cam["H"] - 1)
-    ok = v & (x0 <= x1) & (y0 <= y1)
-    rects = np.zeros((len(u), 4), np.int64)
-    rects[ok] = np.stack([x0[ok] // T, y0[ok] // T, x1[ok] // T + 1, y1[ok] // T + 1], 1)
-    return geo, np.stack([ex, ey], 1).astype(np.float32), rects
-
-
-def test_tile_culling_rule_keeps_every_tile_a_pixel_reaches():
-    """The float32 culling rule is conservative: every tile holding a pixel centre where the
-    Gaussian (FP64, from the oracle's projection) reaches alpha >= 1/255 is kept; and it is
-    not vacuous: it drops a sizeable share of the rectangle tiles (elongated footprints)."""
-    import synthetic
-    g = {k: np.asarray(v, np.float64) for k, v in synthetic.cloud_scene(800, 4, seed=9).items()}
-    g["log_scale"][:, 0] += 1.0       # elongated, so that rectangles over-cover
-    cam = synthetic.cloud_camera()
-    T = 8
-    pr = oracle.project(g, cam)
-    geo, ext, rects = _records_f32(pr, cam, T)
-    P = oracle.P
-    n_tiles = n_kept = 0
-    for r in np.nonzero(rects[:, 2] > rects[:, 0])[0]:
-        tx0, ty0, tx1, ty1 = rects[r]
-        S = np.array([[pr[r, P["S00"]], pr[r, P["S01"]]], [pr[r, P["S01"]], pr[r, P["S11"]]]])
-        Q = np.linalg.inv(S)
-        txs, tys = np.meshgrid(np.arange(tx0, tx1), np.arange(ty0, ty1))
-        txs, tys = txs.ravel(), tys.ravel()
-        X0, Y0 = txs * T, tys * T
-        X1, Y1 = np.minimum(X0 + T - 1, cam["W"] - 1), np.minimum(Y0 + T - 1, cam["H"] - 1)
-        kept = oracle.tile_reaches_alpha_min(np.repeat(geo[r:r + 1], len(txs), 0), np.repeat(ext[r:r + 1], len(txs), 0),
-                                             X0, X1, Y0, Y1)
-        for k in range(len(txs)):
-            xs, ys = np.meshgrid(np.arange(X0[k], X1[k] + 1) - pr[r, P["U"]], np.arange(Y0[k], Y1[k] + 1) - pr[r, P["V"]])
-            sig = 0.5 * (Q[0, 0] * xs * xs + 2 * Q[0, 1] * xs * ys + Q[1, 1] * ys * ys)
-            reaches = (pr[r, P["OPAC"]] * np.exp(-sig) >= 1 / 255).any()
-            assert kept[k] or not reaches, (r, txs[k], tys[k])
-        n_tiles += len(txs)
-        n_kept += int(kept.sum())
-    assert n_tiles > 2000 and n_kept < 0.9 * n_tiles, (n_kept, n_tiles)
-
-
-def _min_quadratic_over_rect(A, B, C, x0, x1, y0, y1):
-    """min of A x^2 + 2 B x y + C y^2 (positive definite) over [x0, x1] x [y0, y1], FP64:
-    0 if the rectangle holds the origin, else the least of the four edges' clamped 1-D minima."""
-    if x0 <= 0 <= x1 and y0 <= 0 <= y1:
-        return 0.0
-    q = lambda x, y: A * x * x + 2 * B * x * y + C * y * y
-    best = np.inf
-    for x in (x0, x1):
-        best = min(best, q(x, min(y1, max(y0, -B * x / C))))
-    for y in (y0, y1):
-        best = min(best, q(min(x1, max(x0, -B * y / A)), y))
-    return best
-
-
-def test_tile_culling_rule_keeps_only_tiles_the_footprint_reaches():
-    """The other direction of the rule: a kept tile's pixel-centre rectangle meets the
-    footprint sigma <= thr' (thr' recovered from the stored extent), evaluated in FP64 from
-    the same float32 records, up to float32 rounding -- so the rule drops the tiles of a
-    rectangle row that the ellipse's vertical extent misses, and every tile left or right of
-    its span."""
-    import synthetic
-    g = {k: np.asarray(v, np.float64) for k, v in synthetic.cloud_scene(500, 4, seed=10).items()}
-    g["log_scale"][:, 0] += 1.0
-    cam = synthetic.cloud_camera()
-    T = 8
-    pr = oracle.project(g, cam)
-    geo, ext, rects = _records_f32(pr, cam, T)
-    n_kept = 0
-    for r in np.nonzero(rects[:, 2] > rects[:, 0])[0]:
-        tx0, ty0, tx1, ty1 = rects[r]
-        txs, tys = np.meshgrid(np.arange(tx0, tx1), np.arange(ty0, ty1))
-        txs, tys = txs.ravel(), tys.ravel()
-        X0, Y0 = txs * T, tys * T
-        X1, Y1 = np.minimum(X0 + T - 1, cam["W"] - 1), np.minimum(Y0 + T - 1, cam["H"] - 1)
-        kept = oracle.tile_reaches_alpha_min(np.repeat(geo[r:r + 1], len(txs), 0), np.repeat(ext[r:r + 1], len(txs), 0),
-                                             X0, X1, Y0, Y1)
-        uf, vf, m00, m10, m11 = (float(v) for v in geo[r, [0, 1, 4, 5, 6]])
-        packed = int(geo[r:r + 1, 7].view(np.uint32)[0])
-        ui = float(np.int16(np.uint16(packed & 0xFFFF)))
-        vi = float(np.int16(np.uint16(packed >> 16)))
-        thr = ((float(ext[r, 0]) - 0.01) / 1.002 * m00) ** 2
-        A, B, C = m00 * m00 + m10 * m10, m10 * m11, m11 * m11
-        for k in np.nonzero(kept)[0]:
-            smin = _min_quadratic_over_rect(A, B, C, X0[k] - ui - uf, X1[k] - ui - uf, Y0[k] - vi - vf, Y1[k] - vi - vf)
-            assert smin <= thr * (1 + 1e-4) + 1e-4, (r, txs[k], tys[k], smin, thr)
-            n_kept += 1
-    assert n_kept > 1000
-
-
 def test_tile_lists_with_culling_lists_only_kept_pairs():
     """With a keep rule the reference lists exactly the kept (record, tile) pairs, in the
     same (tile, depth, record) order."""
@@ -237,3 +126,85 @@ def test_tile_lists_with_culling_lists_only_kept_pairs():
     for t in range(6):
         s, e = ranges[t]
         assert np.all(tiles[s:e] == t) and (e - s) == np.sum(tiles == t)
+
+
+def _alpha_axis_aligned(cam, mean, s, o, px, py, b=0.3):
+    """alpha of an axis-aligned Gaussian seen by a camera with identity pose, from the
+    closed-form Sigma2D = J diag(exp(2 s)) J^T + b I (matrix inverse by numpy)."""
+    z = mean[2]
+    u, v = cam["fx"] * mean[0] / z + cam["cx"], cam["fy"] * mean[1] / z + cam["cy"]
+    J = np.array([[cam["fx"] / z, 0, -cam["fx"] * mean[0] / z ** 2], [0, cam["fy"] / z, -cam["fy"] * mean[1] / z ** 2]])
+    Q = np.linalg.inv(J @ np.diag(np.exp(2 * np.asarray(s))) @ J.T + b * np.eye(2))
+    d = np.stack([np.asarray(px, float) - u, np.asarray(py, float) - v])
+    return o * np.exp(-0.5 * np.einsum("in,ij,jn->n", d, Q, d))
+
+
+def _axis_aligned_scene(n=60, seed=12):
+    rng = np.random.default_rng(seed)
+    mean = np.stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.45, 0.45, n), rng.uniform(1.5, 3.0, n)], 1)
+    s = np.log(rng.uniform(0.01, 0.08, (n, 3)))
+    logit = rng.normal(0.5, 1.0, n)
+    g = dict(mean=mean, log_scale=s, quat=np.tile([1.0, 0, 0, 0], (n, 1)), opacity_logit=logit,
+             rgb=np.ones((n, 3)), sem=np.zeros((n, 4)))
+    return g, 1 / (1 + np.exp(-logit))
+
+
+@pytest.mark.parametrize("T", [(8, 8), (16, 16), (32, 8)])
+def test_tile_membership_matches_closed_form_alpha(T):
+    """The set N of a tile holds a Gaussian iff its alpha reaches 1/255 at one of the tile's
+    pixel centres: tile_pairs covers every tile with such a pixel, and tile_reach's largest
+    alpha over each tile equals the closed-form alpha maximised over that tile's pixels."""
+    tw, th = T
+    cam = synthetic.cloud_camera()
+    g, o = _axis_aligned_scene()
+    pr = oracle.project(g, cam)
+    gs, tx, ty = oracle.tile_pairs(pr, cam, tw, th)
+    listed = set(zip(gs.tolist(), tx.tolist(), ty.tolist()))
+    reach = oracle.tile_reach(pr, cam, gs, tx, ty, tw, th)
+    ys, xs = np.mgrid[0:cam["H"], 0:cam["W"]]
+    n_in = 0
+    for i in range(len(o)):
+        a = _alpha_axis_aligned(cam, g["mean"][i], g["log_scale"][i], o[i], xs.ravel(), ys.ravel())
+        hit = a >= 1 / 255
+        for x, y in zip(xs.ravel()[hit], ys.ravel()[hit]):
+            assert (i, x // tw, y // th) in listed, (i, x, y)
+        sel = np.nonzero(gs == i)[0]
+        for k in sel:
+            m = (xs.ravel() // tw == tx[k]) & (ys.ravel() // th == ty[k])
+            assert reach["alpha"][k] == pytest.approx(a[m].max(), rel=1e-9, abs=1e-15)
+            n_in += bool(a[m].max() >= 1 / 255)
+        assert np.all(reach["thr"][sel] == pytest.approx(np.log(o[i] * 255.0), rel=1e-12))
+    assert n_in > 100 and len(gs) > n_in  # the rectangles over-cover: some listed tiles are missed
+
+
+def test_tile_reach_sigma_min_is_the_minimum_over_the_pixel_centre_rectangle():
+    """sigma_min against a dense sampling of the tile's continuous pixel-centre rectangle (an
+    upper bound, approached within the grid spacing) for rotated, elongated footprints, and 0
+    on the tile holding the 2D mean."""
+    cam = synthetic.cloud_camera()
+    rng = np.random.default_rng(3)
+    n = 12
+    q = rng.normal(size=(n, 4))
+    g = dict(mean=np.stack([rng.uniform(-0.5, 0.5, n), rng.uniform(-0.4, 0.4, n), rng.uniform(1.5, 3, n)], 1),
+             log_scale=np.log(np.stack([rng.uniform(0.05, 0.15, n), rng.uniform(0.005, 0.01, n),
+                                        rng.uniform(0.005, 0.01, n)], 1)),
+             quat=q / np.linalg.norm(q, axis=1, keepdims=True), opacity_logit=np.full(n, 2.0),
+             rgb=np.ones((n, 3)), sem=np.zeros((n, 4)))
+    pr = oracle.project(g, cam)
+    P = oracle.P
+    tw = th = 8
+    gs, tx, ty = oracle.tile_pairs(pr, cam, tw, th)
+    reach = oracle.tile_reach(pr, cam, gs, tx, ty, tw, th)
+    fine = np.linspace(0, 1, 161)
+    for k in range(0, len(gs), 7):
+        i = gs[k]
+        X0, Y0 = tx[k] * tw, ty[k] * th
+        X1, Y1 = min(X0 + tw - 1, cam["W"] - 1), min(Y0 + th - 1, cam["H"] - 1)
+        xs, ys = np.meshgrid(X0 + fine * (X1 - X0), Y0 + fine * (Y1 - Y0))
+        dx, dy = xs - pr[i, P["U"]], ys - pr[i, P["V"]]
+        sig = 0.5 * (pr[i, P["CA"]] * dx * dx + pr[i, P["CC"]] * dy * dy) + pr[i, P["CB"]] * dx * dy
+        smin = reach["sigma_min"][k]
+        assert smin <= sig.min() * (1 + 1e-12) + 1e-12
+        assert smin >= sig.min() - 0.02 * (1 + sig.min())
+        holds = X0 <= pr[i, P["U"]] <= X1 and Y0 <= pr[i, P["V"]] <= Y1
+        assert (smin == 0.0) == holds

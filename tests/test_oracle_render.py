@@ -149,3 +149,59 @@ def test_pixel_list_equals_full_image():
     part = oracle.render(g, cam, pixels=pix)
     assert np.array_equal(part["rgb"], full["rgb"][:, pix[:, 1], pix[:, 0]])
     assert np.array_equal(part["n_contrib"], full["n_contrib"][pix[:, 1], pix[:, 0]])
+
+
+def _logit(p):
+    return math.log(p / (1 - p))
+
+
+def test_skip_and_clamp_flags_mark_only_the_band_of_the_alpha_error():
+    """At the mean's pixel sigma = 0, so raw alpha = o: alpha within tol (relative) of 1/255
+    or of 0.99 is flagged (a float32 alpha with that error may take the other branch), alpha
+    three tolerances away is not."""
+    cam = synthetic.cloud_camera()  # identity pose, (cx, cy) = (80, 60): the mean (0, 0, z) hits pixel (80, 60)
+    s = np.log([0.05] * 3)
+    tol = 1e-5
+    for o, flag in ((1 / 255 * (1 + 0.5 * tol), oracle.FLAG_SKIP), (1 / 255 * (1 + 3 * tol), 0),
+                    (0.99 * (1 - 0.5 * tol), oracle.FLAG_CLAMP), (0.99 * (1 + 0.5 * tol), oracle.FLAG_CLAMP),
+                    (0.99 * (1 - 3 * tol), 0)):
+        g = gauss([[0, 0, 2.0]], [s], [_logit(o)], [[1, 1, 1]])
+        r = oracle.render(g, cam, pixels=[[80, 60]], tol=tol)
+        assert r["flags"][0] & (oracle.FLAG_SKIP | oracle.FLAG_CLAMP) == flag, (o, r["flags"][0])
+    # one pixel to the right sigma = conic_a / 2: raw alpha just below the skip threshold there
+    # is flagged too (skipped, but a float32 alpha may pass)
+    ca = oracle.project(gauss([[0, 0, 2.0]], [s], [0.0], [[1, 1, 1]]), cam)[0][oracle.P["CA"]]
+    for f, flag in ((1 - 0.5 * tol, oracle.FLAG_SKIP), (1 - 3 * tol, 0)):
+        o = 1 / 255 * f * math.exp(0.5 * ca)
+        g = gauss([[0, 0, 2.0]], [s], [_logit(o)], [[1, 1, 1]])
+        r = oracle.render(g, cam, pixels=[[81, 60]], tol=tol)
+        assert r["flags"][0] & oracle.FLAG_SKIP == flag and r["n_contrib"][0] == 0, (f, r["flags"][0])
+
+
+def test_stop_flag_band_grows_with_the_transmittance_error():
+    """Two layers at one pixel: a clamped front (alpha = 0.99, T = 0.01) and a second with
+    alpha = 0.99 - 0.01 delta, so T' = 1e-4 (1 + delta).  A float32 T' carries the second
+    alpha's error amplified by alpha / (1 - alpha) ~ 99 (plus a few roundings), so with
+    tol = 1e-5 the stop decision is undecided for delta = 5e-4 and decided for delta = 5e-3;
+    with tol = 0 only the roundings remain."""
+    cam = synthetic.cloud_camera()
+    s = np.log([0.05] * 3)
+    for delta, tol, flagged in ((5e-4, 1e-5, True), (5e-3, 1e-5, False), (5e-4, 0.0, False), (5e-8, 0.0, True)):
+        a2 = 0.99 - 0.01 * delta
+        g = gauss([[0, 0, 2.0], [0, 0, 3.0]], [s, s], [8.0, _logit(a2)], [[1, 0, 0], [0, 1, 0]])
+        r = oracle.render(g, cam, pixels=[[80, 60]], tol=tol)
+        assert bool(r["flags"][0] & oracle.FLAG_STOP) == flagged, (delta, tol, r["flags"][0])
+        assert r["n_contrib"][0] == 2
+
+
+def test_depth_flag_marks_an_undecided_key_next_to_a_neighbour():
+    """A depth exactly halfway between two float32 values (1 + 2^-24) has no decided key; the
+    order against a Gaussian whose key is one float32 step away (1 + 2^-23) is then not fixed
+    and the pixel is flagged.  Far apart, or both keys decided, nothing is flagged."""
+    cam = synthetic.cloud_camera()
+    s = np.log([0.05] * 3)
+    for z1, z2, flagged in ((1.0 + 2.0 ** -24, 1.0 + 2.0 ** -23, True), (1.0 + 2.0 ** -24, 1.5, False),
+                            (1.0, 1.0 + 2.0 ** -23, False), (1.0 + 2.0 ** -24, 1.0, True)):
+        g = gauss([[0, 0, z1], [0, 0, z2]], [s, s], [-1.0, -1.0], [[1, 0, 0], [0, 1, 0]])
+        r = oracle.render(g, cam, pixels=[[80, 60]])
+        assert bool(r["flags"][0] & oracle.FLAG_DEPTH) == flagged, (z1, z2)
