@@ -49,7 +49,9 @@ typedef enum {
 
 /* Bits of the caller's device status word (uint32). */
 #define SG_STATUS_CAPACITY 1u /* more tile instances than sg_tile_lists.capacity  */
-#define SG_STATUS_NUMERIC 2u  /* non-finite value met                              */
+#define SG_STATUS_NUMERIC 2u  /* non-finite value met (checks on: sg_config /
+                                 sg_loss_config check_numeric, sg_adam_multi status) */
+#define SG_STATUS_TIMEOUT 4u  /* a bounded wait inside a tensor-core kernel gave up */
 
 #define SG_MAX_VIEWS 64
 
@@ -133,6 +135,10 @@ typedef struct {
                                (fx along x, fy along y), Sigma2D = diag((fx r/d)^2,
                                (fy r/d)^2) + dilation; quat and log_scale[1..2] are unused
                                and get zero gradient                                    */
+    int32_t check_numeric;  /* 1: sg_project_gaussians sets SG_STATUS_NUMERIC in its status
+                               word when a Gaussian parameter it reads (mean, log-scale,
+                               quaternion, opacity logit, rgb, semantic feature, SH
+                               coefficients) is NaN or infinite; 0: no check (the default)  */
 } sg_config;
 
 /* Projected records of all (view-level, Gaussian) pairs: record r = v*N + g. */
@@ -200,6 +206,9 @@ typedef struct {
     int32_t n_classes;     /* K (sem_mode 0)                                              */
     const float *decoder;  /* K x C linear decoder, or NULL for identity (K == C)         */
     float *decoder_grad;   /* K x C gradient (added), or NULL                             */
+    int32_t check_numeric; /* 1: set SG_STATUS_NUMERIC when a view-level's loss terms come
+                              out NaN or infinite (a non-finite rendered or target value
+                              reached the loss); 0: no check (the default)                 */
 } sg_loss_config;
 
 /* ---------------------------------------------------------------------------------- */
@@ -208,6 +217,14 @@ typedef struct {
 
 const char *sg_last_error(void);
 const char *sg_version(void);
+
+/* Reads a device status word after the work queued on `stream` before this call has
+ * completed (it synchronises the stream: call it outside graph capture), writes its bits to
+ * *bits (may be NULL) and maps them to a status: SG_ERR_CAPACITY if SG_STATUS_CAPACITY is
+ * set, else SG_ERR_TIMEOUT for SG_STATUS_TIMEOUT, else SG_ERR_NUMERIC for SG_STATUS_NUMERIC,
+ * else SG_OK; the message (sg_last_error) names every bit that is set.  The word is left as
+ * it is (the caller clears it). */
+sg_status sg_read_status(const uint32_t *status, sg_stream_t stream, uint32_t *bits);
 /* Number of kernels this library has launched (or recorded into a graph) since it was
  * loaded; a diagnostic used by the benchmark to report its launch count. */
 uint64_t sg_kernel_launch_count(void);
@@ -232,9 +249,11 @@ sg_status sg_make_views(const sg_camera *cams, int32_t n_cams, int32_t levels, i
  * pixel where alpha can reach alpha_min; with spherical-harmonic features also the
  * view-dependent colour (semantic feature) of every visible record into out->rgb (out->sem),
  * required when g->sh (g->sem_sh) is given.  views: device array of
- * n_views sg_view. */
+ * n_views sg_view.  status: device status word, required when cfg->check_numeric is set
+ * (see sg_config), else may be NULL. */
 sg_status sg_project_gaussians(const sg_gaussians *g, const sg_view *views, int32_t n_views,
-                               const sg_config *cfg, sg_projected *out, sg_stream_t stream);
+                               const sg_config *cfg, sg_projected *out, uint32_t *status,
+                               sg_stream_t stream);
 
 /* Scratch bytes sg_build_tile_lists needs for n_records = n_views*N records and the
  * lists' capacity. */
@@ -269,11 +288,13 @@ size_t sg_loss_workspace_size(const sg_view *views_host, int32_t n_views, int32_
  * view-level v (device floats) and the gradient of sum_v total_v with respect to the
  * rendered images into dL (same packing as sg_images).  views_host: host copy of the
  * view table (sizes are needed to size the launch).  SSIM uses an 11x11 Gaussian window
- * (sigma 1.5) with zero padding. */
+ * (sigma 1.5) with zero padding.  status: device status word, required when
+ * lcfg->check_numeric is set, else may be NULL. */
 sg_status sg_pyramid_loss(const sg_images *rendered, const sg_targets *gt, const sg_view *views,
                           const sg_view *views_host, int32_t n_views, int32_t C,
                           const sg_loss_config *lcfg, float *terms, sg_images *dL,
-                          void *workspace, size_t workspace_bytes, sg_stream_t stream);
+                          void *workspace, size_t workspace_bytes, uint32_t *status,
+                          sg_stream_t stream);
 
 /* Same as sg_pyramid_loss, for callers that cannot allocate device memory: a host
  * framework that owns the device memory pool and passes this library only its input and
@@ -284,16 +305,18 @@ sg_status sg_pyramid_loss(const sg_images *rendered, const sg_targets *gt, const
  * (16 MiB) built into the library; every GPU that loads the library holds that array
  * until the process exits.  Images whose scratch need exceeds it (roughly P/16 bytes for
  * P pixels, plus P*K*C/64 bytes when a decoder gradient is requested) are rejected with
- * SG_ERR_CAPACITY and a message.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array and leave their contents in it:
- * the call clears what it needs, but calls whose GPU work overlaps race on it.  No
- * allocation or free happens inside the call. */
+ * SG_ERR_CAPACITY and a message (after the same argument checks as sg_pyramid_loss).  The
+ * first call on each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current and keeps it for the life of the process; make that first call before
+ * any stream capture, and do not use this call across a device reset (cudaDeviceReset or a
+ * re-created primary context may move the array and leave the kept address stale).  All
+ * calls share the array and leave their contents in it: the call clears what it needs, but
+ * calls whose GPU work overlaps race on it.  No allocation or free happens inside the call. */
 #define SG_LOSS_NOALLOC_SCRATCH_BYTES (16u << 20)
 sg_status sg_pyramid_loss_noalloc(const sg_images *rendered, const sg_targets *gt,
                                   const sg_view *views, const sg_view *views_host, int32_t n_views,
                                   int32_t C, const sg_loss_config *lcfg, float *terms,
-                                  sg_images *dL, sg_stream_t stream);
+                                  sg_images *dL, uint32_t *status, sg_stream_t stream);
 
 /* ---------------------------------------------------------------------------------- */
 /* Backward path                                                                        */
@@ -364,9 +387,12 @@ typedef struct {
 #define SG_ADAM_MAX_GROUPS 8
 
 /* Adam over up to SG_ADAM_MAX_GROUPS tensors in one launch (same update as sg_adam_step,
- * per-group learning rate); with zero_grad != 0 every gradient is set to 0 after use. */
+ * per-group learning rate); with zero_grad != 0 every gradient is set to 0 after use.
+ * status: NULL, or a device status word in which SG_STATUS_NUMERIC is set when a gradient
+ * it reads is NaN or infinite (the update itself is applied as usual). */
 sg_status sg_adam_multi(const sg_adam_group *groups, int32_t n_groups, float beta1, float beta2,
-                        float eps, int32_t step, int32_t zero_grad, sg_stream_t stream);
+                        float eps, int32_t step, int32_t zero_grad, uint32_t *status,
+                        sg_stream_t stream);
 
 /* Adam (the paper leaves the optimizer unspecified): for i < n
  * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr * mhat / (sqrt(vhat) + eps). */
@@ -382,7 +408,6 @@ sg_status sg_adam_step(float *param, const float *grad, float *m, float *v, int6
 #define SG_MLP_IN 2048
 #define SG_MLP_HIDDEN 128
 #define SG_MLP_OUT 32
-#define SG_STATUS_TIMEOUT 4u /* a bounded wait inside a tensor-core kernel gave up      */
 
 /* bf16 operands are passed as uint16_t bit patterns. */
 typedef struct {

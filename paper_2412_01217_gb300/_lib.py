@@ -39,7 +39,7 @@ class SgConfig(C.Structure):
     _fields_ = [("alpha_max", c_f), ("alpha_min", c_f), ("T_min", c_f), ("z_near", c_f),
                 ("dilation", c_f), ("fov_clamp", c_f), ("bg", c_f * 3), ("tile_w", c_i),
                 ("tile_h", c_i), ("batch", c_i), ("persistent", c_i), ("pixels_per_thread", c_i),
-                ("pixels_per_thread_bwd", c_i), ("batch_bwd", c_i), ("isotropic", c_i)]
+                ("pixels_per_thread_bwd", c_i), ("batch_bwd", c_i), ("isotropic", c_i), ("check_numeric", c_i)]
 
 
 class SgProjected(C.Structure):
@@ -64,7 +64,8 @@ class SgTargets(C.Structure):
 
 class SgLossConfig(C.Structure):
     _fields_ = [("lambda_r", c_f), ("lambda_s", c_f), ("w_depth", c_f), ("w_sem", c_f),
-                ("sem_mode", c_i), ("n_classes", c_i), ("decoder", c_p), ("decoder_grad", c_p)]
+                ("sem_mode", c_i), ("n_classes", c_i), ("decoder", c_p), ("decoder_grad", c_p),
+                ("check_numeric", c_i)]
 
 
 class SgAdamGroup(C.Structure):
@@ -96,11 +97,12 @@ P = C.POINTER
 SIGNATURES = {
     "sg_last_error": (C.c_char_p, []),
     "sg_version": (C.c_char_p, []),
+    "sg_read_status": (c_i, [c_p, c_p, P(C.c_uint32)]),
     "sg_kernel_launch_count": (C.c_uint64, []),
     "sg_default_config": (None, [P(SgConfig)]),
     "sg_default_loss_config": (None, [P(SgLossConfig)]),
     "sg_make_views": (c_i, [P(SgCamera), c_i, c_i, c_i, c_i, P(SgView), P(C.c_int64), P(c_i)]),
-    "sg_project_gaussians": (c_i, [P(SgGaussians), c_p, c_i, P(SgConfig), P(SgProjected), c_p]),
+    "sg_project_gaussians": (c_i, [P(SgGaussians), c_p, c_i, P(SgConfig), P(SgProjected), c_p, c_p]),
     "sg_tile_lists_workspace_size": (C.c_size_t, [C.c_int64, c_i]),
     "sg_build_tile_lists": (c_i, [P(SgProjected), c_i, c_i, c_p, c_i, P(SgConfig), P(SgTileLists),
                                   c_p, C.c_size_t, c_p, c_p]),
@@ -108,9 +110,9 @@ SIGNATURES = {
                                 P(SgConfig), P(SgImages), P(SgSaved), c_p, c_p]),
     "sg_loss_workspace_size": (C.c_size_t, [P(SgView), c_i, c_i, c_i]),
     "sg_pyramid_loss": (c_i, [P(SgImages), P(SgTargets), c_p, P(SgView), c_i, c_i,
-                              P(SgLossConfig), c_p, P(SgImages), c_p, C.c_size_t, c_p]),
+                              P(SgLossConfig), c_p, P(SgImages), c_p, C.c_size_t, c_p, c_p]),
     "sg_pyramid_loss_noalloc": (c_i, [P(SgImages), P(SgTargets), c_p, P(SgView), c_i, c_i,
-                                      P(SgLossConfig), c_p, P(SgImages), c_p]),
+                                      P(SgLossConfig), c_p, P(SgImages), c_p, c_p]),
     "sg_backward_workspace_size": (C.c_size_t, [C.c_int64, c_i]),
     "sg_render_pyramid_backward": (c_i, [P(SgGaussians), P(SgProjected), P(SgTileLists), c_p, c_i,
                                          c_i, P(SgConfig), P(SgSaved), P(SgImages),
@@ -122,7 +124,7 @@ SIGNATURES = {
                                             C.c_size_t, P(SgGaussianGrads), c_p]),
     "sg_build_pyramid": (c_i, [c_p, c_p, c_p, c_p, c_i, P(SgView), c_i, c_p]),
     "sg_adam_step": (c_i, [c_p, c_p, c_p, c_p, C.c_int64, c_f, c_f, c_f, c_f, c_i, c_p]),
-    "sg_adam_multi": (c_i, [P(SgAdamGroup), c_i, c_f, c_f, c_f, c_i, c_i, c_p]),
+    "sg_adam_multi": (c_i, [P(SgAdamGroup), c_i, c_f, c_f, c_f, c_i, c_i, c_p, c_p]),
     "sg_gemm_bf16": (c_i, [c_p, C.c_int64, c_p, C.c_int64, c_i, c_i, c_i, c_p, C.c_int64, c_i, c_p, c_p]),
     "sg_gemm_bf16_timeout_probe": (c_i, [c_p, C.c_int64, c_p, C.c_int64, c_i, c_i, c_i, c_p, C.c_int64, C.c_uint32,
                                          c_p, c_p]),

@@ -31,7 +31,7 @@ sg_status check_launch(const char *what) {
 
 // defined in the kernel files
 sg_status launch_project_fwd(const sg_gaussians *, const sg_view *, int, const sg_config *,
-                             sg_projected *, cudaStream_t);
+                             sg_projected *, uint32_t *, cudaStream_t);
 sg_status launch_project_bwd(const sg_gaussians *, const sg_view *, int, const sg_config *,
                              const sg_projected *, float *, sg_gaussian_grads *, cudaStream_t);
 size_t tile_lists_workspace_size(int64_t R, int32_t cap);
@@ -39,11 +39,13 @@ sg_status launch_build_tile_lists(const sg_projected *, int, int, const sg_view 
                                   sg_tile_lists *, void *, size_t, uint32_t *, cudaStream_t);
 size_t loss_workspace_size(const sg_view *vh, int n_views, int C, int n_classes);
 sg_status launch_loss(const sg_images *, const sg_targets *, const sg_view *, const sg_view *, int,
-                      int, const sg_loss_config *, float *, sg_images *, void *, size_t, cudaStream_t);
+                      int, const sg_loss_config *, float *, sg_images *, void *, size_t, uint32_t *,
+                      cudaStream_t);
 sg_status launch_pyramid(float *, float *, int *, float *, int, const sg_view *, int, cudaStream_t);
 sg_status launch_adam(float *, const float *, float *, float *, int64_t, float, float, float, float, int,
                       cudaStream_t);
-sg_status launch_adam_multi(const sg_adam_group *, int, float, float, float, int, int, cudaStream_t);
+sg_status launch_adam_multi(const sg_adam_group *, int, float, float, float, int, int, uint32_t *,
+                            cudaStream_t);
 
 }  // namespace sg
 
@@ -99,6 +101,7 @@ static sg_status check_cfg(const sg_config *c) {
     SG_REQUIRE(c->batch_bwd == 0 || (c->batch_bwd >= 16 && c->batch_bwd <= 512 && (c->batch_bwd % 16) == 0),
                "batch_bwd %d not 0 or in [16, 512] step 16", c->batch_bwd);
     SG_REQUIRE(c->isotropic == 0 || c->isotropic == 1, "isotropic must be 0 or 1");
+    SG_REQUIRE(c->check_numeric == 0 || c->check_numeric == 1, "check_numeric must be 0 or 1");
     SG_REQUIRE(c->alpha_min > 0.f && c->alpha_max <= 1.f && c->alpha_min < c->alpha_max,
                "need 0 < alpha_min < alpha_max <= 1");
     SG_REQUIRE(c->T_min >= 0.f && c->z_near > 0.f && c->dilation >= 0.f && c->fov_clamp > 0.f,
@@ -122,6 +125,35 @@ static sg_status check_views(const sg_view *views, int n_views) {
         const sg_status _s = (expr);  \
         if (_s != SG_OK) return _s;   \
     } while (0)
+
+namespace sg {
+// Every host-checkable condition of sg_pyramid_loss except the workspace (shared with the
+// entry point that brings its own scratch).
+sg_status check_loss_args(const sg_images *rendered, const sg_targets *gt, const sg_view *views,
+                          const sg_view *views_host, int32_t n_views, int32_t C, const sg_loss_config *lcfg,
+                          float *terms, sg_images *dL, uint32_t *status) {
+    SG_TRY(check_views(views, n_views));
+    SG_REQUIRE(views_host, "views_host is NULL");
+    SG_REQUIRE(rendered && gt && lcfg && terms && dL, "NULL argument");
+    SG_REQUIRE(C >= 1, "C = %d < 1", C);
+    SG_REQUIRE(rendered->rgb && rendered->depth && rendered->sem && gt->rgb && gt->depth,
+               "image buffers are NULL");
+    SG_REQUIRE(dL->rgb && dL->depth && dL->sem, "gradient buffers are NULL");
+    SG_REQUIRE(lcfg->sem_mode == 0 || lcfg->sem_mode == 1, "sem_mode must be 0 or 1");
+    if (lcfg->sem_mode == 0) {
+        SG_REQUIRE(gt->label, "cross-entropy mode needs labels");
+        SG_REQUIRE(lcfg->n_classes >= 1, "n_classes must be >= 1");
+        SG_REQUIRE(lcfg->decoder || lcfg->n_classes == C, "without a decoder n_classes must equal C");
+    } else {
+        SG_REQUIRE(gt->sem, "semantic-colour mode needs gt->sem");
+    }
+    for (int v = 0; v < n_views; ++v)
+        SG_REQUIRE(views_host[v].W >= 1 && views_host[v].H >= 1, "view %d is empty", v);
+    SG_REQUIRE(lcfg->check_numeric == 0 || lcfg->check_numeric == 1, "check_numeric must be 0 or 1");
+    SG_REQUIRE(!lcfg->check_numeric || status, "check_numeric needs a status word");
+    return SG_OK;
+}
+}  // namespace sg
 
 extern "C" {
 
@@ -148,6 +180,7 @@ void sg_default_config(sg_config *c) {
     c->pixels_per_thread_bwd = 2;
     c->batch_bwd = 0;
     c->isotropic = 0;
+    c->check_numeric = 0;
 }
 
 void sg_default_loss_config(sg_loss_config *c) {
@@ -160,6 +193,26 @@ void sg_default_loss_config(sg_loss_config *c) {
     c->n_classes = 0;
     c->decoder = nullptr;
     c->decoder_grad = nullptr;
+    c->check_numeric = 0;
+}
+
+sg_status sg_read_status(const uint32_t *status, sg_stream_t stream, uint32_t *bits) {
+    SG_REQUIRE(status, "status is NULL");
+    uint32_t b = 0;
+    cudaError_t e = cudaMemcpyAsync(&b, status, sizeof(b), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_error("read_status: %s", cudaGetErrorString(e));
+        return SG_ERR_CUDA;
+    }
+    if (bits) *bits = b;
+    set_error("status word 0x%x:%s%s%s", b, (b & SG_STATUS_CAPACITY) ? " capacity exceeded;" : "",
+              (b & SG_STATUS_TIMEOUT) ? " a bounded device wait gave up;" : "",
+              (b & SG_STATUS_NUMERIC) ? " non-finite value met;" : "");
+    if (b & SG_STATUS_CAPACITY) return SG_ERR_CAPACITY;
+    if (b & SG_STATUS_TIMEOUT) return SG_ERR_TIMEOUT;
+    if (b & SG_STATUS_NUMERIC) return SG_ERR_NUMERIC;
+    return SG_OK;
 }
 
 sg_status sg_make_views(const sg_camera *cams, int32_t n_cams, int32_t levels, int32_t tile_w,
@@ -208,7 +261,8 @@ sg_status sg_make_views(const sg_camera *cams, int32_t n_cams, int32_t levels, i
 }
 
 sg_status sg_project_gaussians(const sg_gaussians *g, const sg_view *views, int32_t n_views,
-                               const sg_config *cfg, sg_projected *out, sg_stream_t stream) {
+                               const sg_config *cfg, sg_projected *out, uint32_t *status,
+                               sg_stream_t stream) {
     SG_TRY(check_gaussians(g));
     SG_TRY(check_cfg(cfg));
     SG_TRY(check_views(views, n_views));
@@ -216,7 +270,9 @@ sg_status sg_project_gaussians(const sg_gaussians *g, const sg_view *views, int3
     SG_REQUIRE(aligned16(out->geo), "geo must be 16-byte aligned");
     SG_TRY(check_record_colour(g, out));
     SG_REQUIRE((int64_t)g->N * n_views < (1ll << 32), "too many records");
-    return launch_project_fwd(g, views, n_views, cfg, out, (cudaStream_t)stream);
+    SG_REQUIRE(!cfg->check_numeric || status, "check_numeric needs a status word");
+    return launch_project_fwd(g, views, n_views, cfg, out, cfg->check_numeric ? status : nullptr,
+                              (cudaStream_t)stream);
 }
 
 size_t sg_tile_lists_workspace_size(int64_t n_records, int32_t capacity) {
@@ -273,25 +329,11 @@ size_t sg_loss_workspace_size(const sg_view *views_host, int32_t n_views, int32_
 sg_status sg_pyramid_loss(const sg_images *rendered, const sg_targets *gt, const sg_view *views,
                           const sg_view *views_host, int32_t n_views, int32_t C,
                           const sg_loss_config *lcfg, float *terms, sg_images *dL, void *workspace,
-                          size_t workspace_bytes, sg_stream_t stream) {
-    SG_TRY(check_views(views, n_views));
-    SG_REQUIRE(views_host, "views_host is NULL");
-    SG_REQUIRE(rendered && gt && lcfg && terms && dL && workspace, "NULL argument");
-    SG_REQUIRE(rendered->rgb && rendered->depth && rendered->sem && gt->rgb && gt->depth,
-               "image buffers are NULL");
-    SG_REQUIRE(dL->rgb && dL->depth && dL->sem, "gradient buffers are NULL");
-    SG_REQUIRE(lcfg->sem_mode == 0 || lcfg->sem_mode == 1, "sem_mode must be 0 or 1");
-    if (lcfg->sem_mode == 0) {
-        SG_REQUIRE(gt->label, "cross-entropy mode needs labels");
-        SG_REQUIRE(lcfg->n_classes >= 1, "n_classes must be >= 1");
-        SG_REQUIRE(lcfg->decoder || lcfg->n_classes == C, "without a decoder n_classes must equal C");
-    } else {
-        SG_REQUIRE(gt->sem, "semantic-colour mode needs gt->sem");
-    }
-    for (int v = 0; v < n_views; ++v)
-        SG_REQUIRE(views_host[v].W >= 1 && views_host[v].H >= 1, "view %d is empty", v);
+                          size_t workspace_bytes, uint32_t *status, sg_stream_t stream) {
+    SG_TRY(check_loss_args(rendered, gt, views, views_host, n_views, C, lcfg, terms, dL, status));
+    SG_REQUIRE(workspace, "workspace is NULL");
     return launch_loss(rendered, gt, views, views_host, n_views, C, lcfg, terms, dL, workspace,
-                       workspace_bytes, (cudaStream_t)stream);
+                       workspace_bytes, lcfg->check_numeric ? status : nullptr, (cudaStream_t)stream);
 }
 
 size_t sg_backward_workspace_size(int64_t n_records, int32_t sem_channels) {
@@ -402,7 +444,7 @@ sg_status sg_adam_step(float *param, const float *grad, float *m, float *v, int6
 }
 
 sg_status sg_adam_multi(const sg_adam_group *groups, int32_t n_groups, float beta1, float beta2, float eps,
-                        int32_t step, int32_t zero_grad, sg_stream_t stream) {
+                        int32_t step, int32_t zero_grad, uint32_t *status, sg_stream_t stream) {
     SG_REQUIRE(groups && n_groups >= 1 && n_groups <= SG_ADAM_MAX_GROUPS, "n_groups must be in [1, %d]",
                SG_ADAM_MAX_GROUPS);
     SG_REQUIRE(step >= 1, "step must be >= 1");
@@ -411,7 +453,7 @@ sg_status sg_adam_multi(const sg_adam_group *groups, int32_t n_groups, float bet
         SG_REQUIRE(groups[k].n == 0 || (groups[k].param && groups[k].grad && groups[k].m && groups[k].v),
                    "group %d: NULL pointer", k);
     }
-    return launch_adam_multi(groups, n_groups, beta1, beta2, eps, step, zero_grad, (cudaStream_t)stream);
+    return launch_adam_multi(groups, n_groups, beta1, beta2, eps, step, zero_grad, status, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -721,6 +721,7 @@ struct FinalArgs {
     int C, sem_mode;
     float lambda_r, lambda_s, w_depth, w_sem;
     float *terms;
+    uint32_t *status;  // non-NULL: flag non-finite loss terms (SG_STATUS_NUMERIC)
 };
 
 // Sum of v over the block in double, in a fixed order (warp butterflies, then the warps in
@@ -777,6 +778,7 @@ __global__ void loss_finalize_kernel(FinalArgs a) {
         a.terms[4 * v + 1] = (float)L_d;
         a.terms[4 * v + 2] = (float)L_s;
         a.terms[4 * v + 3] = (float)(L_r + L_d + L_s);
+        if (a.status && !isfinite(L_r + L_d + L_s)) atomicOr(a.status, SG_STATUS_NUMERIC);
     }
 }
 
@@ -800,6 +802,12 @@ static size_t loss_ws_bytes(int n_views, int n_tiles, int n_blocks, int KC) {
     return al(sizeof(int) * 2 * n_views) + 2 * al(sizeof(float) * 2 * n_tiles) +
            al(sizeof(float) * 2 * n_blocks) + al(sizeof(float) * (size_t)n_blocks * KC) +
            al(sizeof(float) * (size_t)kDecChunks * KC);
+}
+
+// Decoder-gradient floats the loss keeps per pixel block: K x C partials in cross-entropy
+// mode when a decoder gradient is requested, none otherwise (paper mode has no decoder).
+int loss_decoder_partials(const sg_loss_config *lc, int C) {
+    return (lc->sem_mode == 0 && lc->decoder_grad) ? lc->n_classes * C : 0;
 }
 
 // Exact scratch bytes when KC decoder-gradient floats per block are needed (0 = none).
@@ -843,7 +851,8 @@ static bool launch_pixel(PixelArgs &pa, int blocks, cudaStream_t st) {
 
 sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *views,
                       const sg_view *vh, int n_views, int C, const sg_loss_config *lc,
-                      float *terms, sg_images *dL, void *ws, size_t ws_bytes, cudaStream_t st) {
+                      float *terms, sg_images *dL, void *ws, size_t ws_bytes, uint32_t *status,
+                      cudaStream_t st) {
     LossViews lv;
     make_loss_views(vh, n_views, lv);
     const int n_tiles = lv.tile_off[n_views], n_blocks = lv.pix_blk_off[n_views];
@@ -856,7 +865,7 @@ sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *v
     float *p_pix = (float *)take(sizeof(float) * 2 * n_blocks);
     const int ce = lc->sem_mode == 0;
     const int K = ce ? lc->n_classes : C;
-    const int KC = lc->decoder_grad ? K * C : 0;
+    const int KC = loss_decoder_partials(lc, C);
     float *p_dec = (float *)take(sizeof(float) * (size_t)n_blocks * KC);
     float *p_dec2 = (float *)take(sizeof(float) * (size_t)kDecChunks * KC);
     if (loss_ws_bytes(n_views, n_tiles, n_blocks, KC) > ws_bytes) {
@@ -879,7 +888,7 @@ sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *v
         launch_pdl(ssim_l1_kernel, n_tiles, kLossThreads, ssim_smem(), st, ss);
     }
     PixelArgs pa{r->depth, gt->depth, r->sem, gt->label, dL->depth, dL->sem, lc->decoder,
-                 lc->decoder_grad, C, K, ce, lc->w_depth, lc->w_sem, counts, views, lv, p_pix, p_dec};
+                 KC ? lc->decoder_grad : nullptr, C, K, ce, lc->w_depth, lc->w_sem, counts, views, lv, p_pix, p_dec};
     if (!launch_pixel(pa, n_blocks, st)) {
         set_error("pyramid_loss: unsupported (C=%d, classes=%d)", C, K);
         return SG_ERR_INVALID_ARG;
@@ -890,7 +899,7 @@ sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *v
         count_launches(2);
     }
     FinalArgs fa{p_rgb, ce ? nullptr : p_sem, p_pix, counts, views, lv, C, lc->sem_mode,
-                 lc->lambda_r, lc->lambda_s, lc->w_depth, lc->w_sem, terms};
+                 lc->lambda_r, lc->lambda_s, lc->w_depth, lc->w_sem, terms, status};
     launch_pdl(loss_finalize_kernel, n_views, kLossThreads, 0, st, fa);
     count_launches(ce ? 3 : 4);
     return check_launch("pyramid_loss");
@@ -984,6 +993,7 @@ struct AdamGroups {
     sg_adam_group g[SG_ADAM_MAX_GROUPS];
     int64_t start[SG_ADAM_MAX_GROUPS + 1];  // prefix of element counts
     int n;
+    uint32_t *status;  // non-NULL: flag non-finite gradients (SG_STATUS_NUMERIC)
 };
 
 __global__ void adam_multi_kernel(AdamGroups G, float b1, float b2, float eps, float bc1, float bc2,
@@ -997,6 +1007,7 @@ __global__ void adam_multi_kernel(AdamGroups G, float b1, float b2, float eps, f
         const sg_adam_group &q = G.g[k];
         const int64_t j = i - G.start[k];
         const float gi = q.grad[j];
+        if (G.status) flag_status(!isfinite(gi), G.status, SG_STATUS_NUMERIC);
         const float mi = b1 * q.m[j] + (1.f - b1) * gi;
         const float vi = b2 * q.v[j] + (1.f - b2) * gi * gi;
         q.m[j] = mi;
@@ -1035,6 +1046,9 @@ __global__ void adam_multi4_kernel(AdamGroups G, float b1, float b2, float eps, 
         float4 *vp = reinterpret_cast<float4 *>(q.v) + j;
         float4 *pp = reinterpret_cast<float4 *>(q.param) + j;
         const float4 g = *gp;
+        if (G.status)
+            flag_status(!isfinite(g.x) || !isfinite(g.y) || !isfinite(g.z) || !isfinite(g.w), G.status,
+                        SG_STATUS_NUMERIC);
         float4 m = *mp, v = *vp, p = *pp;
         p.x = adam_one(m.x, v.x, p.x, g.x, q.lr, b1, b2, eps, ibc1, ibc2);
         p.y = adam_one(m.y, v.y, p.y, g.y, q.lr, b1, b2, eps, ibc1, ibc2);
@@ -1048,9 +1062,10 @@ __global__ void adam_multi4_kernel(AdamGroups G, float b1, float b2, float eps, 
 }
 
 sg_status launch_adam_multi(const sg_adam_group *groups, int n, float b1, float b2, float eps, int step,
-                            int zero_grad, cudaStream_t st) {
+                            int zero_grad, uint32_t *status, cudaStream_t st) {
     AdamGroups G{};
     G.n = n;
+    G.status = status;
     G.start[0] = 0;
     for (int k = 0; k < n; ++k) {
         G.g[k] = groups[k];

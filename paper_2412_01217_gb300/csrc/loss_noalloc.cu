@@ -9,17 +9,23 @@
 // The scratch is a file-scope device array of SG_LOSS_NOALLOC_SCRATCH_BYTES (16 MiB) that
 // every GPU loading the library holds until the process exits.  On the host its name is
 // only a stand-in, so the device address is looked up with cudaGetSymbolAddress once per
-// device (on the first call made with that device current) and cached.  Every call uses
-// the same array and leaves its contents behind; the loss clears the counters it needs
-// (with a memset on the stream) and overwrites every partial sum, so stale contents never
-// matter -- but two calls whose GPU work overlaps (different streams, same device) race on
-// the array.
+// device (on the first call made with that device current) and cached for the life of the
+// process.  A device reset (cudaDeviceReset, or the primary context destroyed and created
+// again) reloads the module, possibly elsewhere, and leaves that cached address stale: do not
+// use this entry point across a device reset.  Every call uses the same array and leaves its
+// contents behind; the loss clears the counters it needs (with a memset on the stream) and
+// overwrites every partial sum, so stale contents never matter -- but two calls whose GPU
+// work overlaps (different streams, same device) race on the array.
 #include <mutex>
 
 #include "sg_common.cuh"
 
 namespace sg {
 size_t loss_workspace_size_kc(const sg_view *vh, int n_views, int KC);
+int loss_decoder_partials(const sg_loss_config *lc, int C);
+sg_status check_loss_args(const sg_images *rendered, const sg_targets *gt, const sg_view *views,
+                          const sg_view *views_host, int32_t n_views, int32_t C, const sg_loss_config *lcfg,
+                          float *terms, sg_images *dL, uint32_t *status);
 }
 
 using namespace sg;
@@ -61,14 +67,13 @@ sg_status scratch_address(void **out) {
 extern "C" sg_status sg_pyramid_loss_noalloc(const sg_images *rendered, const sg_targets *gt,
                                              const sg_view *views, const sg_view *views_host,
                                              int32_t n_views, int32_t C, const sg_loss_config *lcfg,
-                                             float *terms, sg_images *dL, sg_stream_t stream) {
-    if (!views_host || !lcfg || n_views < 1 || n_views > SG_MAX_VIEWS) {
-        set_error("pyramid_loss_noalloc: views_host / loss config missing or n_views out of range");
-        return SG_ERR_INVALID_ARG;
-    }
-    const int K = lcfg->sem_mode == 0 ? lcfg->n_classes : C;
-    const int KC = (lcfg->sem_mode == 0 && lcfg->decoder_grad) ? K * C : 0;
-    const size_t need = loss_workspace_size_kc(views_host, n_views, KC);
+                                             float *terms, sg_images *dL, uint32_t *status,
+                                             sg_stream_t stream) {
+    // the arguments are checked exactly as sg_pyramid_loss checks them before the scratch
+    // need is computed from them
+    const sg_status ok = check_loss_args(rendered, gt, views, views_host, n_views, C, lcfg, terms, dL, status);
+    if (ok != SG_OK) return ok;
+    const size_t need = loss_workspace_size_kc(views_host, n_views, loss_decoder_partials(lcfg, C));
     if (need > (size_t)SG_LOSS_NOALLOC_SCRATCH_BYTES) {
         set_error("pyramid_loss_noalloc: these images need %zu bytes of scratch, more than the "
                   "built-in %u bytes; use sg_pyramid_loss with a workspace",
@@ -79,5 +84,5 @@ extern "C" sg_status sg_pyramid_loss_noalloc(const sg_images *rendered, const sg
     const sg_status s = scratch_address(&scratch);
     if (s != SG_OK) return s;
     return sg_pyramid_loss(rendered, gt, views, views_host, n_views, C, lcfg, terms, dL, scratch,
-                           (size_t)SG_LOSS_NOALLOC_SCRATCH_BYTES, stream);
+                           (size_t)SG_LOSS_NOALLOC_SCRATCH_BYTES, status, stream);
 }

@@ -180,6 +180,13 @@ __device__ __forceinline__ int find_view(const sg_view *views, int n_views, int 
     return lo;
 }
 
+// Sets `bit` in *status when `bad` holds for any active lane of the warp (one atomic per
+// warp).  Safe in divergent code: only the lanes that reach it take part.
+__device__ __forceinline__ void flag_status(bool bad, uint32_t *status, uint32_t bit) {
+    const uint32_t m = __ballot_sync(__activemask(), bad);
+    if (m && (threadIdx.x & 31) == (uint32_t)(__ffs(m) - 1)) atomicOr(status, bit);
+}
+
 __device__ __forceinline__ uint32_t pack16(int a, int b) {
     return (uint32_t)a | ((uint32_t)b << 16);
 }

@@ -105,7 +105,7 @@ class MLPInit:
         groups = (SgAdamGroup * 6)(*[SgAdamGroup(p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(),
                                                   p.numel(), self.lr)
                                      for p, g, m, v in zip(self.params, self.grads, self.m, self.v)])
-        call("sg_adam_multi", groups, 6, 0.9, 0.999, 1e-8, self.step_count, 1, _s())
+        call("sg_adam_multi", groups, 6, 0.9, 0.999, 1e-8, self.step_count, 1, None, _s())
         self.W1[:, 2009:] = 0  # padding features stay inert
         self.pack()
 

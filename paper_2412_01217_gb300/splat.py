@@ -73,6 +73,7 @@ class RenderConfig:
     pixels_per_thread_bwd: int = 2
     batch_bwd: int = 0  # 0: same as batch
     isotropic: bool = False  # Eq. 2 projection (radius f r / d) instead of EWA
+    check_numeric: bool = False  # flag non-finite Gaussian parameters in the status word
 
     def to_c(self):
         c = SgConfig()
@@ -85,6 +86,7 @@ class RenderConfig:
         c.pixels_per_thread_bwd = int(self.pixels_per_thread_bwd)
         c.batch_bwd = int(self.batch_bwd)
         c.isotropic = int(self.isotropic)
+        c.check_numeric = int(self.check_numeric)
         return c
 
 
@@ -98,6 +100,7 @@ class LossConfig:
     w_sem: float = 1.0
     sem_mode: str = "ce"
     n_classes: int = 0
+    check_numeric: bool = False  # flag non-finite loss terms in the status word
 
     def to_c(self, decoder=None, decoder_grad=None):
         c = SgLossConfig()
@@ -106,6 +109,7 @@ class LossConfig:
         c.n_classes = self.n_classes
         c.decoder = decoder.data_ptr() if decoder is not None else None
         c.decoder_grad = decoder_grad.data_ptr() if decoder_grad is not None else None
+        c.check_numeric = int(self.check_numeric)
         return c
 
 
@@ -284,7 +288,7 @@ class PyramidRasterizer:
         self._check_colour(g)
         gs = gaussians_struct(g)
         call("sg_project_gaussians", C.byref(gs), _ptr(self.views), self.V, C.byref(self._ccfg),
-             C.byref(self._proj), _stream())
+             C.byref(self._proj), _ptr(self.status), _stream())
 
     def build_lists(self):
         call("sg_build_tile_lists", C.byref(self._proj), self.N, self.V, _ptr(self.views), self.n_tiles,
@@ -321,7 +325,8 @@ class PyramidRasterizer:
                        gt["sem"].data_ptr() if gt.get("sem") is not None else None)
         di = SgImages(self.dL_rgb.data_ptr(), self.dL_depth.data_ptr(), self.dL_sem.data_ptr())
         call("sg_pyramid_loss", C.byref(ri), C.byref(ti), _ptr(self.views), self.views_host, self.V, self.C,
-             C.byref(lc), _ptr(self.terms), C.byref(di), _ptr(self.loss_ws), self.loss_ws.numel(), _stream())
+             C.byref(lc), _ptr(self.terms), C.byref(di), _ptr(self.loss_ws), self.loss_ws.numel(),
+             _ptr(self.status), _stream())
 
     # ---- backward ------------------------------------------------------------------------
     def backward(self, g, grads, dL=None, between=None):
@@ -346,11 +351,17 @@ class PyramidRasterizer:
         return int(self.count.item())
 
     def check_status(self):
-        s = int(self.status.item())
-        if s & _lib.STATUS_CAPACITY:
+        """Reads the device status word (sg_read_status; synchronises the stream) and raises
+        SgError for a capacity overflow, a timeout or a non-finite value (checks on)."""
+        bits = C.c_uint32(0)
+        lib = _lib.load()
+        code = lib.sg_read_status(_ptr(self.status), _stream(), C.byref(bits))
+        if code == 2:
             raise _lib.SgError("sg_build_tile_lists", 2,
                                f"{self.instance_count()} tile instances exceed capacity {self.capacity}")
-        return s
+        if code != 0:
+            raise _lib.SgError("sg_read_status", code, lib.sg_last_error().decode())
+        return int(bits.value)
 
 
 def build_pyramid(rast: PyramidRasterizer, rgb0, depth0, label0=None, sem0=None):
@@ -462,7 +473,8 @@ class MappingStep:
         r.loss(self.gt, decoder=self.decoder, decoder_grad=self.decoder_grad)
         r.backward(self.p, self.grads)
         groups, n = self._adam_groups()
-        call("sg_adam_multi", groups, n, 0.9, 0.999, 1e-15, t, 1, _stream())
+        check = r.cfg.check_numeric or r.loss_cfg.check_numeric
+        call("sg_adam_multi", groups, n, 0.9, 0.999, 1e-15, t, 1, _ptr(r.status) if check else None, _stream())
 
     def step(self):
         self.t += 1

@@ -31,8 +31,8 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(_lib.SgCamera) == 72
     assert C.sizeof(_lib.SgView) == 96
     assert C.sizeof(_lib.SgGaussians) == 80
-    assert C.sizeof(_lib.SgConfig) == 68
-    assert C.sizeof(_lib.SgLossConfig) == 40
+    assert C.sizeof(_lib.SgConfig) == 72
+    assert C.sizeof(_lib.SgLossConfig) == 48
 
 
 def test_defaults_and_version():
@@ -45,6 +45,7 @@ def test_defaults_and_version():
     lc = _lib.SgLossConfig()
     lib.sg_default_loss_config(C.byref(lc))
     assert lc.lambda_r == pytest.approx(0.2) and lc.lambda_s == pytest.approx(0.2)
+    assert c.check_numeric == 0 and lc.check_numeric == 0  # numeric checks are off by default
     assert b"sm_103a" in lib.sg_version()
 
 
@@ -76,15 +77,16 @@ def test_host_validation_rejects_bad_arguments():
     g = _lib.SgGaussians()
     g.N, g.C = 10, 7                  # C not supported
     proj = _lib.SgProjected()
-    assert lib.sg_project_gaussians(C.byref(g), None, 1, C.byref(cfg), C.byref(proj), None) == 1
+    assert lib.sg_project_gaussians(C.byref(g), None, 1, C.byref(cfg), C.byref(proj), None, None) == 1
     assert b"C=7" in lib.sg_last_error()
     g.C = 8
-    assert lib.sg_project_gaussians(C.byref(g), None, 1, C.byref(cfg), C.byref(proj), None) == 1
+    assert lib.sg_project_gaussians(C.byref(g), None, 1, C.byref(cfg), C.byref(proj), None, None) == 1
     assert b"NULL" in lib.sg_last_error()
     g.sh_degree = 4                   # spherical-harmonic colour goes to degree 3
-    assert lib.sg_project_gaussians(C.byref(g), None, 1, C.byref(cfg), C.byref(proj), None) == 1
+    assert lib.sg_project_gaussians(C.byref(g), None, 1, C.byref(cfg), C.byref(proj), None, None) == 1
     assert b"sh_degree = 4" in lib.sg_last_error()
     assert lib.sg_adam_step(None, None, None, None, 5, 1e-3, 0.9, 0.999, 1e-8, 0, None) == 1
+    assert lib.sg_read_status(None, None, None) == 1
     assert lib.sg_adam_step(None, None, None, None, 0, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 0
 
 
@@ -122,3 +124,22 @@ def test_product_package_never_imports_the_oracle():
                 assert "sg_oracle" not in text, f
                 checked += 1
     assert checked > 10
+
+
+def test_numeric_checks_need_a_status_word():
+    """check_numeric on without a status word is refused on the host (nothing launched)."""
+    import numpy as np
+    from paper_2412_01217_gb300 import _lib
+    lib = _lib.load()
+    cfg = _lib.SgConfig()
+    lib.sg_default_config(C.byref(cfg))
+    cfg.check_numeric = 1
+    buf = (C.c_float * 64)()
+    g = _lib.SgGaussians(C.addressof(buf), C.addressof(buf), C.addressof(buf), C.addressof(buf), C.addressof(buf),
+                         C.addressof(buf), 1, 8)
+    views = (C.c_uint8 * 96)()
+    proj = _lib.SgProjected(C.addressof(buf), C.addressof(buf), C.addressof(buf), None, None)
+    assert lib.sg_project_gaussians(C.byref(g), views, 1, C.byref(cfg), C.byref(proj), None, None) == 1
+    assert b"status" in lib.sg_last_error()
+    cfg.check_numeric = 2
+    assert lib.sg_project_gaussians(C.byref(g), views, 1, C.byref(cfg), C.byref(proj), None, None) == 1
