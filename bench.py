@@ -1,21 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the pyramid-splatting mapping iteration on one GB300 (or N replicas).
 
-Workload (Replica-like, three-level pyramid): one 1200x680 RGB-D-semantic keyframe with
-its 600x340 and 300x170 pyramid levels, 300k Gaussians sampled on the surfaces of a
-seeded 6x5x3 m room with 20 boxes, C = 16 semantic features decoded to 32 classes.  One
-step = one full mapping iteration over every pyramid level: EWA projection, tile lists,
-compositing, loss (L1 + D-SSIM RGB, masked depth L1, cross-entropy), adjoint to every
-Gaussian parameter, Adam -- replayed as one CUDA graph.  L2 is flushed (a 256 MiB write)
-before every timed step; the flush is outside each step's event pair.
+Default workload (the batched mapping step): 8 keyframes of uneven size (4 x 1200x680 and
+4 x 640x480 RGB-D-semantic frames of a seeded 6x5x3 m room with 20 boxes), each with its
+3-level pyramid = 24 images, over 500k Gaussians sampled on the room's surfaces, C = 16
+semantic features decoded to 32 classes.  One step = one full mapping iteration over every
+image: EWA projection, tile lists, compositing, loss (L1 + D-SSIM RGB, masked depth L1,
+cross-entropy), adjoint to every Gaussian parameter, Adam -- one persistent launch per
+kernel, replayed as one CUDA graph.  L2 is flushed (a 256 MiB write) before every timed
+step; the flush is outside each step's event pair.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead (the
 reference arm: a bounded pixel sample of the same workload per step, extrapolated).
 
---workload batched: 8 keyframes of uneven size (4 x 1200x680, 4 x 640x480) x 3 levels = 24
-images over 500k shared Gaussians in one persistent launch per kernel.  --workload scannet:
+--workload replica: one 1200x680 keyframe x 3 levels, 300k Gaussians.  --workload scannet:
 one 640x480 keyframe x 4 levels (down to 80x60), 1M Gaussians, C = 40 class logits (no
-decoder), depth noise 1 cm.  The default is the Replica-like workload above.
+decoder), depth noise 1 cm.
 """
 from __future__ import annotations
 
@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--ppt", type=int, default=1, help="pixels per thread of the forward compositing kernel")
     ap.add_argument("--ppt-bwd", type=int, default=2, help="pixels per thread of the backward kernel")
     ap.add_argument("--batch-bwd", type=int, default=0, help="batch of the backward kernel (0: --batch)")
-    ap.add_argument("--workload", default="replica", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="batched", choices=sorted(WORKLOADS))
     ap.add_argument("--gaussians", type=int, default=None, help="default: the workload's count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -136,6 +136,15 @@ def algorithmic_bytes(s):
     return b
 
 
+def raster_flops_model(s):
+    """Algorithmic flops of the compositing kernels by the survey's model: E list entries
+    examined (pixel, entry pairs) times 15 + 2 (4 + C) in the forward and 40 + 4 (4 + C) in
+    the backward, as if every examined entry contributed."""
+    E, C = s["E"], s["C"]
+    nf = 4 + C
+    return E * (15 + 2 * nf), E * (40 + 4 * nf)
+
+
 def raster_flops(s):
     """Algorithmic flops of the method (independent of how the kernels map them): alpha
     evaluation ~13 per examined (pixel, entry) pair and 3 + 2 (4 + C) per contributor in
@@ -198,13 +207,78 @@ def profiled_traffic(kernel, units_now, workload="replica"):
 # clocks
 # ------------------------------------------------------------------------------------------
 
+# NVML clocks-event reason bits (nvml.h) reported by name
+_NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+                 0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+
+class NvmlClocks:
+    """Reads the SM clock, its maximum and the active clocks-event reasons of one GPU through
+    NVML (libnvidia-ml, read-only queries), fast enough to sample a short timed region every
+    few milliseconds.  `ok` is False when NVML is not available."""
+
+    def __init__(self, device_index=0):
+        import ctypes
+        self.ok = False
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            found = False
+            try:  # match the CUDA device by UUID (NVML may number the GPUs differently)
+                import torch
+                u = str(torch.cuda.get_device_properties(device_index).uuid)
+                u = u if u.startswith("GPU-") else "GPU-" + u
+                found = nv.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(h)) == 0
+            except Exception:
+                found = False
+            if not found and nv.nvmlDeviceGetHandleByIndex_v2(device_index, ctypes.byref(h)) != 0:
+                return
+            self.nv, self.h, self.ct = nv, h, ctypes
+            mx = ctypes.c_uint()
+            self.max_mhz = float(mx.value) if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 else None
+            self.reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            self.ok = self.sample() is not None
+        except Exception:
+            self.ok = False
+
+    def sample(self):
+        """(SM MHz, reason bits) now, or None."""
+        ct = self.ct
+        mhz, bits = ct.c_uint(), ct.c_ulonglong()
+        if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz)) != 0:
+            return None
+        if self.reasons_fn(self.h, ct.byref(bits)) != 0:
+            bits.value = 0
+        return float(mhz.value), int(bits.value)
+
+
 class ClockSampler:
+    """Samples the GPU's SM clock and throttle reasons during the timed region: NVML polled
+    every 5 ms by a thread (so even a timed loop of a few tens of milliseconds has samples),
+    else nvidia-smi every 100 ms.  Every sample carries the host time it was taken."""
+
     def __init__(self, index=0):
         self.index = index
         self.proc = None
         self.lines = []
+        self.samples = []  # (host time, MHz, [reason names]) from NVML
+        self.nvml = NvmlClocks(index)
+        self._stop = threading.Event()
 
     def start(self):
+        if self.nvml.ok:
+            def poll():
+                while not self._stop.is_set():
+                    r = self.nvml.sample()
+                    if r is not None:
+                        self.samples.append((time.time(), r[0], [n for b, n in _NVML_REASONS.items() if r[1] & b]))
+                    time.sleep(0.005)
+            self.t = threading.Thread(target=poll, daemon=True)
+            self.t.start()
+            return
         cmd = ["nvidia-smi", f"--id={self.index}",
                "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -224,16 +298,26 @@ class ClockSampler:
             self.lines.append((time.time(), line.strip()))
 
     def wait_first(self, timeout=5.0):
-        """Block until the sampler has printed its first line (NVML is initialised and the
-        sampler is in its steady polling loop), so that its start-up does not overlap the
-        timed steps."""
+        """Block until the sampler has its first sample (NVML initialised, the poller in its
+        steady loop), so that its start-up does not overlap the timed steps."""
         t0 = time.time()
-        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+        while not (self.lines or self.samples) and (self.proc is not None or self.nvml.ok) and \
+                time.time() - t0 < timeout:
             time.sleep(0.02)
 
     def stop(self, t0=None, t1=None):
         """Median SM clock, maximum clock and the throttle reasons seen by the samples taken
         between host times t0 and t1 (the timed region); all samples if none fell inside."""
+        if self.nvml.ok:
+            self._stop.set()
+            self.t.join(timeout=1.0)
+            inside = [x for x in self.samples if t0 is not None and t0 <= x[0] <= t1]
+            sel = inside if inside else self.samples
+            if not sel:
+                return None
+            return {"sm_mhz": statistics.median(x[1] for x in sel), "sm_max_mhz": self.nvml.max_mhz,
+                    "reasons": sorted({n for x in sel for n in x[2]}), "samples": len(sel),
+                    "during_timed_region": bool(inside), "source": "NVML, polled every 5 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -261,12 +345,31 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm), "during_timed_region": bool(inside)}
+                "samples": len(sm), "during_timed_region": bool(inside), "source": "nvidia-smi, every 100 ms"}
 
 
 # ------------------------------------------------------------------------------------------
 # CPU baseline (the oracle, as it stands)
 # ------------------------------------------------------------------------------------------
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
 
 def oracle_sample_time(g, cams, levels, stride, seed=0):
     """Oracle forward + backward over every stride-th row and column of every level of every
@@ -312,7 +415,8 @@ def cpu_baseline(g, cams, levels, target_s):
         t2, n2, _ = oracle_sample_time(g, cams, levels, stride)
     a, b = fit(t2, n2)
     full = a + b * nt
-    return {"value": 1.0 / full, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    return {"value": 1.0 / full, "unit": UNIT, "cores": oracle.num_threads(), "cpu_model": cpu_model(),
+            "kind": "oracle",
             "sample": f"FP64 oracle forward+backward on every {stride}th row/column of all {levels} levels "
                       f"({n2} of {nt} pixels, {t2:.1f} s) and every {s1}th ({n1} pixels, {t1:.1f} s); "
                       f"fixed cost {a:.2f} s + {b * 1e3:.4f} ms per pixel, evaluated at all {nt} pixels",
@@ -350,7 +454,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(W, l2="n/a (CPU)"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "cpu_model": cpu_model(),
+                             "kind": "oracle",
                              "sample": f"every {stride}th row/column of all {L} levels per step ({ns} of {nt} px); "
                                        f"fixed cost {a:.2f} s per call (from samples at strides 96 and 48) "
                                        f"plus the sample's per-pixel time extrapolated to all pixels"},
@@ -455,7 +560,7 @@ def run_ours(args):
         ev["bwd0"].record()
         r.backward(p, ms.grads, between=ev["bwdr"].record)
         ev["bwd1"].record()
-        call("sg_adam_multi", groups, n_groups, 0.9, 0.999, 1e-15, t, 1, _stream())
+        call("sg_adam_multi", groups, n_groups, 0.9, 0.999, 1e-15, t, 1, None, _stream())
         ev["s1"].record()
 
     with torch.cuda.graph(graph):
@@ -576,17 +681,23 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    f_fwd, f_bwd = raster_flops(stats)
+    f_fwd, f_bwd = raster_flops_model(stats)
+    c_fwd, c_bwd = raster_flops(stats)
     fwd_avg = float(np.mean(fwd_ms)) / 1e3
     bwd_avg = float(np.mean(bwd_ms)) / 1e3
     bytes_model = algorithmic_bytes(stats)
     step_bytes = sum(bytes_model.values())
     dominant = "raster_bwd" if bwd_avg >= fwd_avg else "raster_fwd"
     d_flops = f_bwd if dominant == "raster_bwd" else f_fwd
+    d_strict = c_bwd if dominant == "raster_bwd" else c_fwd
     d_time = bwd_avg if dominant == "raster_bwd" else fwd_avg
     achieved = d_flops / d_time / 1e12
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+                "flops_per_launch": d_flops,
+                "flops_model": "E x (40 + 4 (4 + C)) backward, E x (15 + 2 (4 + C)) forward; E = list entries "
+                               "examined (per-pixel last summed)",
+                "frac_per_contribution": d_strict / d_time / 1e12 / fp32_peak_tflops,
                 "traffic": profiled_traffic(dominant, stats["E"], args.workload),
                 "traffic_unit": "DRAM bytes per launch (ncu), scaled by list entries examined",
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",

@@ -16,9 +16,28 @@ class _Proc:
 
 def _sampler(lines):
     s = bench.ClockSampler()
+    s.nvml.ok = False  # the nvidia-smi path
     s.proc = _Proc()
     s.lines = lines
     return s
+
+
+class _FakeNvml:
+    ok = True
+    max_mhz = 2070.0
+
+
+def test_nvml_samples_windowed_to_the_timed_region():
+    """The NVML poller's samples (host time, MHz, reasons) are windowed like nvidia-smi's."""
+    s = bench.ClockSampler()
+    s.nvml = _FakeNvml()
+    s.t = __import__("threading").Thread(target=lambda: None)
+    s.t.start()
+    s.samples = [(0.5, 1200.0, ["hw_slowdown"]), (1.01, 2070.0, []), (1.02, 2070.0, ["sw_power_cap"]),
+                 (1.03, 2055.0, []), (2.5, 900.0, ["sw_thermal_slowdown"])]
+    clk = s.stop(1.0, 2.0)
+    assert clk["samples"] == 3 and clk["during_timed_region"] and clk["sm_mhz"] == 2070.0
+    assert clk["reasons"] == ["sw_power_cap"] and clk["sm_max_mhz"] == 2070.0
 
 
 def _line(sm, reasons=("Not Active",) * 4):
