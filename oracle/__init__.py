@@ -80,7 +80,7 @@ def _load():
         I = ctypes.POINTER(ctypes.c_int)
         lib.oc_project.argtypes = [ctypes.c_int, D, D, D, D, D, D, D]
         lib.oc_render.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D, D, D, ctypes.c_int, I,
-                                  ctypes.c_double, D, D, D, D, I, I]
+                                  ctypes.c_double, ctypes.c_double, D, D, D, D, I, I]
         lib.oc_render_backward.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D, D, D, D, D, D,
                                            ctypes.c_int, I, D, D, D, D, D, D, D, D, D, D]
         lib.oc_ssim.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D, D]
@@ -251,17 +251,17 @@ def view_semantics(g, cam):
     return sem + np.einsum("nk,nkc->nc", Y, np.asarray(g["sem_sh"], np.float64))
 
 
-def render(g, cam, cfg=None, pixels=None, tol=1e-5):
+def render(g, cam, cfg=None, pixels=None, tol=1e-5, tol_T=2e-5):
     """Render RGB, depth and C semantic channels.
 
     ``pixels``: None for the whole W x H image (outputs shaped (ch, H, W)), else an (n, 2)
     int array of (x, y) pixel coordinates (outputs shaped (ch, n)).  Also returns the final
     transmittance ``T``, the contributor count ``n_contrib`` and per-pixel ambiguity
     ``flags`` (FLAG_*): some decision of the pixel is not fixed for an evaluation whose alpha
-    carries a relative error up to ``tol`` -- the exact alpha lies within ``tol`` of the skip
-    threshold (FLAG_SKIP) or of the clamp (FLAG_CLAMP), the transmittance after a contributor
-    within its propagated error of T_min (FLAG_STOP), or a contributor's float32 depth key
-    is undecided next to a neighbouring key (FLAG_DEPTH).
+    carries a relative error up to ``tol`` and whose transmittance one up to ``tol_T`` -- the
+    exact alpha lies within ``tol`` of the skip threshold (FLAG_SKIP) or of the clamp
+    (FLAG_CLAMP), the transmittance after a contributor within ``tol_T`` of T_min (FLAG_STOP),
+    or a contributor's float32 depth key is undecided next to a neighbouring key (FLAG_DEPTH).
     """
     lib = _load()
     proj = project(g, cam, cfg)
@@ -282,7 +282,7 @@ def render(g, cam, cfg=None, pixels=None, tol=1e-5):
     o_nc = np.zeros(n, dtype=np.int32); o_fl = np.zeros(n, dtype=np.int32)
     P_ = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     I_ = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
-    lib.oc_render(N, C, ppr, prgb, psem, pc, pf, n, pix_ptr, float(tol), P_(o_rgb), P_(o_d),
+    lib.oc_render(N, C, ppr, prgb, psem, pc, pf, n, pix_ptr, float(tol), float(tol_T), P_(o_rgb), P_(o_d),
                   P_(o_s), P_(o_T), I_(o_nc), I_(o_fl))
     return dict(rgb=o_rgb.reshape(3, *shape), depth=o_d.reshape(shape),
                 sem=o_s.reshape(C, *shape), T=o_T.reshape(shape),

@@ -282,16 +282,14 @@ static int gather(double x, double y, int N, const double *proj, const cfg_t *cf
 /* Composites the sorted list.  Writes the contributing positions to contrib[] (indices
  * into buf) with their transmittance before them in Tb[]; returns their count.
  *
- * Ambiguity flags: `tol` is the relative error of alpha that a float32 evaluation may make
- * (o exp(-sigma) from float32 records).  A decision is flagged when the exact value lies
- * within that evaluation's error of its threshold: raw alpha within tol of alpha_min (skip,
- * F_SKIP) or of alpha_max (clamp, F_CLAMP); the transmittance T' = T (1 - alpha) within its
- * propagated error of T_min (stop, F_STOP), where a float32 T' carries the relative errors
- * of T, of (1 - alpha) (tol alpha / (1 - alpha), or the rounding of alpha_max when clamped)
- * and two roundings; and a contributor whose depth order is undecided (F_DEPTH). */
-static int composite(const cand_t *buf, int n, const cfg_t *cfg, double tol, int *contrib,
+ * Ambiguity flags, for an evaluation whose alpha carries a relative error up to `tol` and
+ * whose transmittance a relative error up to `tol_T`: a decision is flagged when the exact
+ * value lies within that error of its threshold -- raw alpha within tol of alpha_min (skip,
+ * F_SKIP) or of alpha_max (clamp, F_CLAMP), the transmittance T' = T (1 - alpha) within tol_T
+ * of T_min (stop, F_STOP) -- or when a contributor's depth order is undecided (F_DEPTH). */
+static int composite(const cand_t *buf, int n, const cfg_t *cfg, double tol, double tol_T, int *contrib,
                      double *Tb, double *T_out, int *flags) {
-    double T = 1.0, eT = 0.0;
+    double T = 1.0;
     int m = 0, fl = 0;
     for (int k = 0; k < n; ++k) {
         const cand_t *c = buf + k;
@@ -300,13 +298,10 @@ static int composite(const cand_t *buf, int n, const cfg_t *cfg, double tol, int
         if (fabs(c->raw - cfg->alpha_max) <= tol * cfg->alpha_max) fl |= F_CLAMP;
         if (c->order_amb) fl |= F_DEPTH;
         double Tn = T * (1.0 - c->alpha);
-        double ea = c->raw >= cfg->alpha_max ? 0x1p-24 : tol;
-        double eTn = eT + ea * c->alpha / (1.0 - c->alpha) + 0x1p-23;
-        if (fabs(Tn - cfg->T_min) <= eTn * cfg->T_min) fl |= F_STOP;
+        if (fabs(Tn - cfg->T_min) <= tol_T * cfg->T_min) fl |= F_STOP;
         if (Tn < cfg->T_min) break;
         contrib[m] = k; Tb[m] = T; ++m;
         T = Tn;
-        eT = eTn;
     }
     *T_out = T;
     *flags = fl;
@@ -318,7 +313,7 @@ static int composite(const cand_t *buf, int n, const cfg_t *cfg, double tol, int
  * row-major order).  rgb: N x 3, sem: N x C.  Outputs planar over the pixel list.
  */
 void oc_render(int N, int C, const double *proj, const double *rgb, const double *sem,
-               const double *camp, const double *cfgp, int n_pix, const int *pix, double tol,
+               const double *camp, const double *cfgp, int n_pix, const int *pix, double tol, double tol_T,
                double *out_rgb, double *out_depth, double *out_sem, double *out_T,
                int *out_ncontrib, int *out_flags) {
     cam_t cam = unpack_cam(camp);
@@ -337,7 +332,7 @@ void oc_render(int N, int C, const double *proj, const double *rgb, const double
             int n = gather((double)px, (double)py, N, proj, &cfg, buf);
             double T;
             int fl;
-            int m = composite(buf, n, &cfg, tol, contrib, Tb, &T, &fl);
+            int m = composite(buf, n, &cfg, tol, tol_T, contrib, Tb, &T, &fl);
             for (int ch = 0; ch < 4 + C; ++ch) acc[ch] = 0.0;
             for (int j = 0; j < m; ++j) {
                 const cand_t *c = buf + contrib[j];
@@ -511,7 +506,7 @@ void oc_render_backward(int N, int C, const double *mean, const double *log_scal
             int n = gather((double)px, (double)py, N, proj, &cfg, buf);
             double Tfin;
             int fl;
-            int m = composite(buf, n, &cfg, 0.0, contrib, Tb, &Tfin, &fl);
+            int m = composite(buf, n, &cfg, 0.0, 0.0, contrib, Tb, &Tfin, &fl);
             /* suffix accumulator A = (sum_{k>i} w_k f_k + T_final bg) / T_{i+1} */
             for (int ch = 0; ch < 4 + C; ++ch) A[ch] = ch < 3 ? cfg.bg[ch] : 0.0;
             for (int j = m - 1; j >= 0; --j) {

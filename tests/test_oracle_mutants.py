@@ -60,8 +60,9 @@ MUTANTS = [
      "out[P_V] = cam->fy * t[1] / t[2] + cam->cx;"),
     # ---- compositing (Eq. 7-9) ----
     ("comp_depth_order_flag_dropped", "sg_oracle.c", "        if (c->order_amb) fl |= F_DEPTH;\n", "\n"),
-    ("comp_stop_band_without_propagation", "sg_oracle.c",
-     "double eTn = eT + ea * c->alpha / (1.0 - c->alpha) + 0x1p-23;", "double eTn = 0x1p-23;"),
+    ("comp_stop_band_uses_alpha_tolerance", "sg_oracle.c",
+     "if (fabs(Tn - cfg->T_min) <= tol_T * cfg->T_min) fl |= F_STOP;",
+     "if (fabs(Tn - cfg->T_min) <= tol * cfg->T_min) fl |= F_STOP;"),
     ("comp_skip_band_dropped", "sg_oracle.c",
      "        if (fabs(c->raw - cfg->alpha_min) <= tol * cfg->alpha_min) fl |= F_SKIP;\n", "\n"),
     ("comp_gather_stops_at_exact_extent", "sg_oracle.c",

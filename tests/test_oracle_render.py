@@ -178,19 +178,17 @@ def test_skip_and_clamp_flags_mark_only_the_band_of_the_alpha_error():
         assert r["flags"][0] & oracle.FLAG_SKIP == flag and r["n_contrib"][0] == 0, (f, r["flags"][0])
 
 
-def test_stop_flag_band_grows_with_the_transmittance_error():
+def test_stop_flag_marks_only_the_band_of_the_transmittance_error():
     """Two layers at one pixel: a clamped front (alpha = 0.99, T = 0.01) and a second with
-    alpha = 0.99 - 0.01 delta, so T' = 1e-4 (1 + delta).  A float32 T' carries the second
-    alpha's error amplified by alpha / (1 - alpha) ~ 99 (plus a few roundings), so with
-    tol = 1e-5 the stop decision is undecided for delta = 5e-4 and decided for delta = 5e-3;
-    with tol = 0 only the roundings remain."""
+    alpha = 0.99 - 0.01 delta, so T' = 1e-4 (1 + delta): the stop decision is flagged when
+    delta lies within the transmittance band tol_T, and not three bands away."""
     cam = synthetic.cloud_camera()
     s = np.log([0.05] * 3)
-    for delta, tol, flagged in ((5e-4, 1e-5, True), (5e-3, 1e-5, False), (5e-4, 0.0, False), (5e-8, 0.0, True)):
+    for delta, tol_T, flagged in ((1e-5, 2e-5, True), (6e-5, 2e-5, False), (1e-5, 0.0, False), (1e-5, 5e-5, True)):
         a2 = 0.99 - 0.01 * delta
         g = gauss([[0, 0, 2.0], [0, 0, 3.0]], [s, s], [8.0, _logit(a2)], [[1, 0, 0], [0, 1, 0]])
-        r = oracle.render(g, cam, pixels=[[80, 60]], tol=tol)
-        assert bool(r["flags"][0] & oracle.FLAG_STOP) == flagged, (delta, tol, r["flags"][0])
+        r = oracle.render(g, cam, pixels=[[80, 60]], tol_T=tol_T)
+        assert bool(r["flags"][0] & oracle.FLAG_STOP) == flagged, (delta, tol_T, r["flags"][0])
         assert r["n_contrib"][0] == 2
 
 
