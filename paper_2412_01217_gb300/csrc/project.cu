@@ -199,9 +199,11 @@ __device__ __forceinline__ void sh_grad(float x, float y, float z, const float *
     }
 }
 
-// Camera centre c = -R^T t of every view-level, next to the view table in shared memory.
-__device__ __forceinline__ void view_centres(const sg_view *s_views, int n_views, float3 *s_centre) {
-    for (int i = threadIdx.x; i < n_views; i += blockDim.x) {
+// Camera centre c = -R^T t of every view-level, next to the view table in shared memory
+// (thread tid of nthr in the block).
+__device__ __forceinline__ void view_centres(const sg_view *s_views, int n_views, float3 *s_centre,
+                                             int tid, int nthr) {
+    for (int i = tid; i < n_views; i += nthr) {
         const float *R = s_views[i].R, *t = s_views[i].t;
         s_centre[i] = make_float3(-(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]),
                                   -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]),
@@ -221,12 +223,14 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     pdl_begin();
     __shared__ sg_view s_views[SG_MAX_VIEWS];
     __shared__ float3 s_centre[SG_MAX_VIEWS];
-    for (int i = threadIdx.x; i < n_views; i += blockDim.x) s_views[i] = views[i];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+    for (int i = tid; i < n_views; i += nthr) s_views[i] = views[i];
     __syncthreads();
     if constexpr (D > 0) {
-        view_centres(s_views, n_views, s_centre);
+        view_centres(s_views, n_views, s_centre, tid, nthr);
         __syncthreads();
     }
+    // threadIdx.x picks the Gaussian, threadIdx.y the view-levels y, y + blockDim.y, ...
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N) return;
     const float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
         for (int i = 0; i < 3 * K; ++i) shv[i] = sh[(size_t)3 * K * g + i];
         for (int c = 0; c < 3; ++c) c0[c] = rgb[3 * g + c];
     }
-    if (pc.status) {
+    if (pc.status && threadIdx.y == 0) {
         // every parameter of the Gaussian the path reads
         const float4 q = quat[g];
         bool bad = !isfinite(q.x) || !isfinite(q.y) || !isfinite(q.z) || !isfinite(q.w) || !isfinite(ologit[g]);
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
             for (int i = 0; i < K * C; ++i) bad |= !isfinite(sem_sh[(size_t)K * C * g + i]);
         flag_status(bad, pc.status, SG_STATUS_NUMERIC);
     }
-    for (int v = 0; v < n_views; ++v) {
+    for (int v = threadIdx.y; v < n_views; v += blockDim.y) {
         const sg_view &vw = s_views[v];
         const size_t r = (size_t)v * N + g;
         ViewGeom q;
@@ -368,10 +372,11 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     pdl_begin();
     __shared__ sg_view s_views[SG_MAX_VIEWS];
     __shared__ float3 s_centre[SG_MAX_VIEWS];
-    for (int i = threadIdx.x; i < n_views; i += blockDim.x) s_views[i] = views[i];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+    for (int i = tid; i < n_views; i += nthr) s_views[i] = views[i];
     __syncthreads();
     if constexpr (D > 0) {
-        view_centres(s_views, n_views, s_centre);
+        view_centres(s_views, n_views, s_centre, tid, nthr);
         __syncthreads();
     }
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -605,13 +610,17 @@ sg_status launch_project_fwd(const sg_gaussians *g, const sg_view *views, int n_
                              const sg_config *cfg, sg_projected *out, uint32_t *status, cudaStream_t st) {
     ProjConsts pc{cfg->z_near, cfg->dilation, cfg->fov_clamp, cfg->alpha_min, cfg->tile_w,
                   cfg->tile_h, cfg->isotropic, status};
-    const int threads = 256;
-    const int blocks = (g->N + threads - 1) / threads;
+    // a block of bx Gaussians x vy view-levels (each thread loops over every vy-th view-level):
+    // with many view-levels, eight short threads per Gaussian instead of one long loop (the
+    // Gaussian's frame is then formed eight times); with few, one thread per Gaussian
+    const int vy = n_views >= 8 ? 8 : 1;
+    const int bx = 256 / vy;
+    const int blocks = (g->N + bx - 1) / bx;
     if (blocks > 0) {
         auto kern = g->sh_degree == 3 ? project_fwd_kernel<3>
                   : g->sh_degree == 2 ? project_fwd_kernel<2>
                   : g->sh_degree == 1 ? project_fwd_kernel<1> : project_fwd_kernel<0>;
-        launch_pdl(kern, blocks, threads, 0, st,
+        launch_pdl(kern, blocks, dim3(bx, vy), 0, st,
             g->mean, g->log_scale, reinterpret_cast<const float4 *>(g->quat), g->opacity_logit,
             g->N, views, n_views, pc, reinterpret_cast<float4 *>(out->geo),
             reinterpret_cast<uint2 *>(out->rect), reinterpret_cast<float2 *>(out->ext), g->rgb,

@@ -363,12 +363,16 @@ struct TileLengthKeys {
     __device__ uint32_t val(int i) const { return (uint32_t)i; }
 };
 
-template <class Src>
+// Radix digits of one pass: up to 8 bits (256 buckets) or 9 bits (512 buckets); each of
+// the 256 threads of a block owns ND / 256 consecutive buckets.
+template <class Src, int ND>
 __global__ void rs_hist_kernel(Src src, const int *__restrict__ n_ptr, int cap, int shift, uint32_t mask,
                                uint32_t *__restrict__ hist, int G) {
     pdl_begin();
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    constexpr int DPT = ND / kScanThreads;
+    __shared__ uint32_t h[ND];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) h[threadIdx.x * DPT + q] = 0;
     __syncthreads();
     const int n = n_ptr ? min(*n_ptr, cap) : cap;
     int beg, end;
@@ -376,7 +380,8 @@ __global__ void rs_hist_kernel(Src src, const int *__restrict__ n_ptr, int cap, 
     for (int i = beg + threadIdx.x; i < end; i += kScanThreads)
         atomicAdd(&h[(src.key(i) >> shift) & mask], 1u);
     __syncthreads();
-    hist[threadIdx.x * G + blockIdx.x] = h[threadIdx.x];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) hist[(threadIdx.x * DPT + q) * G + blockIdx.x] = h[threadIdx.x * DPT + q];
 }
 
 // Block d: exclusive scan of digit d's per-block counts; totals[d] = digit d's count.
@@ -395,6 +400,21 @@ __global__ void rs_digit_scan_kernel(uint32_t *__restrict__ hist, uint32_t *__re
     if (threadIdx.x == 0) totals[d] = run;
 }
 
+// Exclusive scan over ND buckets held DPT per thread (consecutive), block-wide.
+template <int DPT>
+__device__ __forceinline__ void bucket_exclusive_scan(const uint32_t (&v)[DPT], uint32_t (&ex)[DPT]) {
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) sum += v[q];
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(sum, tot);
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        ex[q] = run;
+        run += v[q];
+    }
+}
+
 // Scatter of one digit pass.  Each block walks its input range in chunks of kScatterChunk
 // elements: a stable rank per digit inside the chunk (warp match_any + per-warp counts, 256
 // elements at a time), a reorder of the chunk by digit in shared memory, and a write-out in
@@ -403,31 +423,36 @@ __global__ void rs_digit_scan_kernel(uint32_t *__restrict__ hist, uint32_t *__re
 constexpr int kScatterIPT = 8;
 constexpr int kScatterChunk = kScanThreads * kScatterIPT;
 
-template <class Src>
+template <class Src, int ND>
 __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
     Src src, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ n_ptr, int cap, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, int G) {
     pdl_begin();
     constexpr int kWarps = kScanThreads / 32;
-    __shared__ uint32_t run[256];   // global position of the next element of each digit
-    __shared__ uint32_t sub[256];   // elements of each digit so far in this chunk
-    __shared__ uint32_t loc[256];   // first slot of each digit in the reordered chunk
-    __shared__ uint32_t wcnt[kWarps][256];
+    constexpr int DPT = ND / kScanThreads;  // buckets per thread: tid * DPT + q
+    __shared__ uint32_t run[ND];   // global position of the next element of each digit
+    __shared__ uint32_t sub[ND];   // elements of each digit so far in this chunk
+    __shared__ uint32_t loc[ND];   // first slot of each digit in the reordered chunk
+    __shared__ uint32_t wcnt[kWarps][ND];
     __shared__ uint32_t skey[kScatterChunk], sval[kScatterChunk];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // digit base = exclusive scan of the digit totals (+ this block's offset)
     {
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan(totals[tid], tot);
-        run[tid] = ex + hist[tid * G + blockIdx.x];
+        uint32_t t[DPT], ex[DPT];
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) t[q] = totals[tid * DPT + q];
+        bucket_exclusive_scan<DPT>(t, ex);
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) run[tid * DPT + q] = ex[q] + hist[(tid * DPT + q) * G + blockIdx.x];
     }
     const int n = n_ptr ? min(*n_ptr, cap) : cap;
     int beg, end;
     block_range(n, G, blockIdx.x, beg, end);
     const uint32_t lt_mask = (1u << lane) - 1u;
     for (int cbase = beg; cbase < end; cbase += kScatterChunk) {
-        sub[tid] = 0;
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) sub[tid * DPT + q] = 0;
         const int nit = min(kScatterIPT, (end - cbase + kScanThreads - 1) / kScanThreads);  // block-uniform
         uint32_t key[kScatterIPT], val[kScatterIPT], lrank[kScatterIPT];
         // all of the chunk's loads first (their latencies overlap), then the ranking
@@ -442,31 +467,42 @@ __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
         for (int it = 0; it < kScatterIPT; ++it) {
             if (it >= nit) break;
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+            for (int w = 0; w < kWarps; ++w)
+#pragma unroll
+                for (int q = 0; q < DPT; ++q) wcnt[w][tid * DPT + q] = 0;
             __syncthreads();
             const int i = cbase + it * kScanThreads + tid;
             const bool valid = i < end;
-            const uint32_t d = valid ? ((key[it] >> shift) & mask) : 256u;
+            const uint32_t d = valid ? ((key[it] >> shift) & mask) : (uint32_t)ND;
             const uint32_t peers = __match_any_sync(SG_FULL_MASK, d);
             const uint32_t rank = __popc(peers & lt_mask);
             if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = __popc(peers);
             __syncthreads();
-            uint32_t s = 0;
+            uint32_t s[DPT];
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const uint32_t t = wcnt[w][tid];
-                wcnt[w][tid] = s;
-                s += t;
+            for (int q = 0; q < DPT; ++q) {
+                s[q] = 0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) {
+                    const uint32_t t = wcnt[w][tid * DPT + q];
+                    wcnt[w][tid * DPT + q] = s[q];
+                    s[q] += t;
+                }
             }
             __syncthreads();
             lrank[it] = valid ? sub[d] + wcnt[warp][d] + rank : 0u;
             __syncthreads();
-            sub[tid] += s;
+#pragma unroll
+            for (int q = 0; q < DPT; ++q) sub[tid * DPT + q] += s[q];
         }
         __syncthreads();
         {
-            uint32_t tot;
-            loc[tid] = block_exclusive_scan(sub[tid], tot);
+            uint32_t v[DPT], ex[DPT];
+#pragma unroll
+            for (int q = 0; q < DPT; ++q) v[q] = sub[tid * DPT + q];
+            bucket_exclusive_scan<DPT>(v, ex);
+#pragma unroll
+            for (int q = 0; q < DPT; ++q) loc[tid * DPT + q] = ex[q];
         }
         __syncthreads();
 #pragma unroll
@@ -487,31 +523,44 @@ __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
             vout[pos] = sval[j];
         }
         __syncthreads();
-        run[tid] += sub[tid];
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) run[tid * DPT + q] += sub[tid * DPT + q];
         __syncthreads();
     }
 }
 
 // Sorts n (device count, clamped to cap) pairs on bits [0, bits) from (kin, vin) into
-// (kout, vout) using (ktmp, vtmp) as ping-pong; kin/vin are not modified.
+// (kout, vout) using (ktmp, vtmp) as ping-pong; kin/vin are not modified.  The bits are
+// split into the fewest passes of at most 9 bits (8-bit passes where that takes no more
+// passes: their blocks use less shared memory).
 static void radix_sort(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                        uint32_t *ktmp, uint32_t *vtmp, const int *n_ptr, int cap, int bits,
                        uint32_t *hist, uint32_t *totals, int G, cudaStream_t st) {
-    const int passes = (bits + 7) / 8;
+    const int passes = (bits + 8) / 9;
+    const bool wide = passes < (bits + 7) / 8;  // 9-bit digits save a pass
     const uint32_t *ks = kin, *vs = vin;
+    int shift = 0;
     for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        const int nb = min(8, bits - shift);
+        const int nb = min(wide ? 9 : 8, bits - shift);
         const uint32_t mask = (1u << nb) - 1u;
         uint32_t *kd = ((passes - 1 - p) % 2 == 0) ? kout : ktmp;
         uint32_t *vd = ((passes - 1 - p) % 2 == 0) ? vout : vtmp;
         const ArrayPairs src{ks, vs};
-        launch_pdl(rs_hist_kernel<ArrayPairs>, G, kScanThreads, 0, st, src, n_ptr, cap, shift, mask, hist, G);
-        launch_pdl(rs_digit_scan_kernel, 256, kScanThreads, 0, st, hist, totals, G);
-        launch_pdl(rs_scatter_kernel<ArrayPairs>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap, shift, mask, hist, totals, G);
+        if (nb > 8) {
+            launch_pdl(rs_hist_kernel<ArrayPairs, 512>, G, kScanThreads, 0, st, src, n_ptr, cap, shift, mask, hist, G);
+            launch_pdl(rs_digit_scan_kernel, 512, kScanThreads, 0, st, hist, totals, G);
+            launch_pdl(rs_scatter_kernel<ArrayPairs, 512>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap, shift, mask,
+                       hist, totals, G);
+        } else {
+            launch_pdl(rs_hist_kernel<ArrayPairs, 256>, G, kScanThreads, 0, st, src, n_ptr, cap, shift, mask, hist, G);
+            launch_pdl(rs_digit_scan_kernel, 256, kScanThreads, 0, st, hist, totals, G);
+            launch_pdl(rs_scatter_kernel<ArrayPairs, 256>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap, shift, mask,
+                       hist, totals, G);
+        }
         count_launches(3);
         ks = kd;
         vs = vd;
+        shift += nb;
     }
 }
 
@@ -593,8 +642,8 @@ static size_t tile_ws_layout(int64_t R, int32_t cap, int G, TileWorkspace *ws, c
     w.tkey_tmp = (uint32_t *)take(c4);
     w.tval_tmp = (uint32_t *)take(c4);
     w.bsum = (uint32_t *)take((size_t)4 * G * 4);  // up to 4 G blocks (the emission grid)
-    w.hist = (uint32_t *)take((size_t)G * 256 * 4);
-    w.totals = (uint32_t *)take(256 * 4);
+    w.hist = (uint32_t *)take((size_t)G * 512 * 4);
+    w.totals = (uint32_t *)take(512 * 4);
     w.counts = (int *)take(4 * sizeof(int));
     if (ws) *ws = w;
     return off;
@@ -661,9 +710,9 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     // 6. work order: one stable counting pass over the 6-bit length keys
     if (lists->order) {
         const TileLengthKeys src{reinterpret_cast<const int2 *>(lists->ranges)};
-        launch_pdl(rs_hist_kernel<TileLengthKeys>, G, kScanThreads, 0, st, src, nullptr, n_tiles, 0, 63u, w.hist, G);
+        launch_pdl(rs_hist_kernel<TileLengthKeys, 256>, G, kScanThreads, 0, st, src, nullptr, n_tiles, 0, 63u, w.hist, G);
         launch_pdl(rs_digit_scan_kernel, 256, kScanThreads, 0, st, w.hist, w.totals, G);
-        launch_pdl(rs_scatter_kernel<TileLengthKeys>, G, kScanThreads, 0, st, src, nullptr, reinterpret_cast<uint32_t *>(lists->order),
+        launch_pdl(rs_scatter_kernel<TileLengthKeys, 256>, G, kScanThreads, 0, st, src, nullptr, reinterpret_cast<uint32_t *>(lists->order),
                                                       nullptr, n_tiles, 0, 63u, w.hist, w.totals, G);
         count_launches(3);
     }

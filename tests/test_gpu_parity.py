@@ -223,6 +223,20 @@ def test_tile_lists_match_definition_single_view(cloud):
         assert lists_match_kernel_rule(r) == K
 
 
+def test_tile_lists_with_17_bit_tile_ids():
+    """8 x 8 tiles of a 2400 x 1800 view: 67,500 tiles need 17-bit tile ids, so the tile sort
+    runs a 9-bit and an 8-bit radix pass (the width the batched workload's 92k tiles take)."""
+    g = synthetic.cloud_scene(1500, 8, seed=3)
+    cam = f32_camera(synthetic.make_camera(2400, 1800, 2250.0, 2250.0, 1199.5, 899.5))
+    r, p = make(g, [cam], tile_w=8, tile_h=8, capacity=1 << 20)
+    assert r.n_tiles == 300 * 225 and r.n_tiles > 1 << 16
+    r.project(p)
+    r.build_lists()
+    K, n_must, n_extra = lists_match_definition(r, g, [cam])
+    assert K > 100000 and n_must > 0.5 * K
+    assert lists_match_kernel_rule(r) == K
+
+
 def room_small(n=20000, C=16, seed=4, ncam=2, W=320, H=180):
     room = synthetic.Room(n_classes=32, seed=3)
     intr = dict(W=W, H=H, fx=W / 2.0, fy=W / 2.0, cx=W / 2 - 0.5, cy=H / 2 - 0.5)
