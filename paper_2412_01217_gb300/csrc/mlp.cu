@@ -17,6 +17,7 @@
 // dH2t, dH1t) the later GEMMs need, and the patch extractor writes X and Xt.  The K = B
 // reductions are split over CTAs and atomically added into the FP32 gradients.
 #include <cstdio>
+#include <cstring>
 
 #include "tc_gemm.cuh"
 
@@ -24,20 +25,70 @@ namespace sg {
 
 using bf16 = __nv_bfloat16;
 
-template <int BN, int STAGES>
-static sg_status launch_gemm_t(const tc::GemmParams &p, int splits, cudaStream_t st) {
+// cuTensorMapEncodeTiled from the driver, found through the runtime's entry-point query (the
+// library links only the runtime).  NULL when the driver does not provide it.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor map of a rows x K bf16 operand (K contiguous, leading dimension ld elements) read in
+// boxes of 64 (K) x box_rows with the 128-byte swizzle; rows beyond `rows` read as zero.
+static bool make_operand_map(CUtensorMap *map, const bf16 *base, long long rows, long long K, long long ld,
+                             int box_rows) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES, bool TMA>
+static sg_status launch_gemm_kernel(const tc::GemmParams &p, int splits, const CUtensorMap &ma,
+                                    const CUtensorMap &mb, cudaStream_t st) {
     constexpr size_t smem = tc::gemm_smem_bytes<BN, STAGES>();
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(tc::gemm_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(tc::gemm_kernel<BN, STAGES, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return check_launch("gemm smem attribute");
         attr = true;
     }
     const dim3 grid((p.M + 127) / 128, (p.N + BN - 1) / BN, splits);
-    tc::gemm_kernel<BN, STAGES><<<grid, 128, smem, st>>>(p);
+    tc::gemm_kernel<BN, STAGES, TMA><<<grid, 128, smem, st>>>(p, ma, mb);
     count_launches(1);
     return check_launch("tcgen05 gemm");
+}
+
+template <int BN, int STAGES>
+static sg_status launch_gemm_t(const tc::GemmParams &p, int splits, cudaStream_t st) {
+    // operands staged by TMA (tensor maps, 128-byte swizzle); by cp.async only when the driver
+    // offers no tensor-map encoder
+    CUtensorMap ma, mb;
+    if (make_operand_map(&ma, p.A, p.M, p.K, p.lda, 128) &&
+        make_operand_map(&mb, p.B, p.N, p.K, p.ldb, BN))
+        return launch_gemm_kernel<BN, STAGES, true>(p, splits, ma, mb, st);
+    memset(&ma, 0, sizeof(ma));
+    memset(&mb, 0, sizeof(mb));
+    return launch_gemm_kernel<BN, STAGES, false>(p, splits, ma, mb, st);
 }
 
 // Chooses the tile width from N and splits K so that the grid covers the SMs.
@@ -69,8 +120,10 @@ sg_status launch_gemm(tc::GemmParams p, cudaStream_t st, int max_splits = 64) {
     }
     switch (BN) {
         case 32: return launch_gemm_t<32, 4>(p, splits, st);
-        case 128: return launch_gemm_t<128, 4>(p, splits, st);
-        default: return launch_gemm_t<256, 4>(p, splits, st);
+        // 3 stages of 32 KiB: two CTAs per SM keep twice the operand bytes in flight
+        // (layer 1 at 65536 rows: 133 -> 107 us against 4 stages and one CTA)
+        case 128: return launch_gemm_t<128, 3>(p, splits, st);
+        default: return launch_gemm_t<256, 3>(p, splits, st);
     }
 }
 

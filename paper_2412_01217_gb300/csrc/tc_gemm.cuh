@@ -3,13 +3,19 @@
 //   D[M x N] = alpha * A[M x K] * B[N x K]^T   (A, B bf16 with K contiguous, D fp32 in TMEM)
 //
 // One CTA of 4 warps computes a 128 x BN tile.  Operand tiles of 128 x 64 (A) and BN x 64
-// (B) are staged into shared memory by cp.async in the canonical no-swizzle K-major layout:
-// 8-row x 16-byte core matrices stored as contiguous 128-byte blocks, the 8 core matrices
-// of one 8-row group along K contiguous (leading byte offset 128 B), 8-row groups 1 KiB
-// apart (stride byte offset 1024 B).  One elected thread issues four K=16
-// tcgen05.mma.kind::f16 per stage and tcgen05.commit arrives on the stage's mbarrier when
-// those MMAs have read the stage, which releases it for the next cp.async refill
-// (STAGES-deep pipeline).  The accumulator lives in TMEM (128 lanes x BN fp32 columns);
+// (B) are staged into shared memory in one of two K-major layouts:
+//  - TMA (the default): one thread issues two cp.async.bulk.tensor loads per stage (tensor
+//    maps with 128-byte swizzle: each 128-byte row of 64 bf16 holds its 16-byte chunks XOR-
+//    permuted by the row index mod 8, 8-row groups 1 KiB apart), whose completion is counted
+//    in bytes on the stage's "full" mbarrier; the MMA descriptors use the matching
+//    128-byte-swizzle layout and step 32 bytes along K per K=16 MMA.
+//  - cp.async (the fallback): all threads copy 16-byte chunks into the no-swizzle layout:
+//    8-row x 16-byte core matrices stored as contiguous 128-byte blocks, the 8 core matrices
+//    of one 8-row group along K contiguous (leading byte offset 128 B), 8-row groups 1 KiB
+//    apart (stride byte offset 1024 B).
+// One elected thread issues four K=16 tcgen05.mma.kind::f16 per stage and tcgen05.commit
+// arrives on the stage's "empty" mbarrier when those MMAs have read the stage, which releases
+// it for the next refill (STAGES-deep pipeline).  The accumulator lives in TMEM (128 lanes x BN fp32 columns);
 // the epilogue reads it back with tcgen05.ld.32x32b (warp w owns lanes 32w..32w+31, one
 // output row per thread) and applies bias / ReLU / ReLU-mask before storing bf16 (row-major
 // and/or transposed) or fp32 (stored, or atomically added for split-K).
@@ -19,6 +25,7 @@
 // and returns.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "sg_common.cuh"
@@ -125,6 +132,27 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
+// The same for a K-major tile in the 128-byte swizzle layout (layout type 2 at bits 61-63):
+// 8-row groups 1 KiB apart (stride byte offset), leading byte offset unused (1); the tile base
+// is 1 KiB aligned, and saddr may step by 32 bytes along K inside the 128-byte swizzle row.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+// mbarrier arrive that also announces `bytes` of asynchronous (TMA) transfer to wait for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// 2-D tiled TMA load of the box at (x = inner coordinate, y) into shared memory; completion is
+// counted on bar.  x must be a multiple of 8 bf16 elements (16 bytes).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
 
 struct GemmParams {
     const __nv_bfloat16 *A;
@@ -152,19 +180,23 @@ struct GemmParams {
     uint32_t probe_polls;
 };
 
-template <int BN, int STAGES>
-__global__ void __launch_bounds__(128, 1) gemm_kernel(const GemmParams p) {
+template <int BN, int STAGES, bool TMA>
+__global__ void __launch_bounds__(128, 2) gemm_kernel(const GemmParams p, const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB) {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "BN");
     constexpr int A_BYTES = 128 * 64 * 2;
     constexpr int B_BYTES = BN * 64 * 2;
     constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "swizzled tiles are 1 KiB aligned");
     constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
     constexpr uint32_t IDESC = idesc_bf16_f32(128, BN);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ uint64_t bars[STAGES];
+    __shared__ uint64_t bars[STAGES];  // "empty": the stage's MMAs have read it
+    __shared__ uint64_t full[STAGES];  // "full": the stage's TMA bytes have landed (TMA mode)
     __shared__ uint64_t probe_bar;
     __shared__ uint32_t tmem_base_s;
     __shared__ int s_timeout;
+    __shared__ int s_issued;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
     const int k_begin = blockIdx.z * p.k_per_split;
@@ -174,7 +206,10 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const GemmParams p) {
     sbase = (sbase + 1023u) & ~1023u;
 
     if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&bars[s], 1);
+            mbar_init(&full[s], 1);
+        }
         mbar_init(&probe_bar, 1);
         s_timeout = 0;
         fence_mbar_init();
@@ -196,6 +231,52 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const GemmParams p) {
         __syncthreads();
     }
 
+    int issued = 0;  // MMA batches committed
+    if constexpr (TMA) {
+        // one thread streams the operands (TMA) and issues the MMAs; a stage is refilled once
+        // the MMAs that read it have committed
+        if (tid == 0 && !s_timeout) {
+            auto load_stage = [&](int kc, int s) {
+                const uint32_t a_s = sbase + s * STAGE_BYTES, b_s = a_s + A_BYTES;
+                const int k0 = k_begin + kc * 64;
+                mbar_arrive_expect_tx(&full[s], (uint32_t)STAGE_BYTES);
+                tma_load_2d(a_s, &tmA, k0, m0, &full[s]);
+                tma_load_2d(b_s, &tmB, k0, n0, &full[s]);
+            };
+            int loaded = 0;  // stages whose loads were issued
+            for (int s = 0; s < STAGES - 1 && s < nk; ++s) load_stage(s, s), ++loaded;
+            bool ok = true;
+            for (int kc = 0; kc < nk && ok; ++kc) {
+                const int s = kc % STAGES;
+                if (!mbar_wait(&full[s], (kc / STAGES) & 1)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t a_s = sbase + s * STAGE_BYTES, b_s = a_s + A_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    mma_bf16(tmem, sdesc_sw128(a_s + kk * 32), sdesc_sw128(b_s + kk * 32), IDESC,
+                             (kc > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(&bars[s]);
+                issued = kc + 1;
+                const int nxt = kc + STAGES - 1;
+                if (nxt < nk) {
+                    const int ns = nxt % STAGES;
+                    // the stage held chunk nxt - STAGES (= kc - 1): wait until its MMAs read it
+                    if (nxt >= STAGES && !mbar_wait(&bars[ns], ((nxt - STAGES) / STAGES) & 1)) { ok = false; break; }
+                    load_stage(nxt, ns);
+                    ++loaded;
+                }
+            }
+            if (!ok) {
+                s_timeout = 1;
+                if (p.status) atomicOr(p.status, SG_STATUS_TIMEOUT_BIT);
+                // let every issued TMA load land before the CTA may exit (bounded)
+                for (int c = issued; c < loaded; ++c) mbar_wait(&full[c % STAGES], (c / STAGES) & 1);
+            }
+            s_issued = issued;
+        }
+        __syncthreads();
+        issued = s_issued;
+    } else {
     auto load_stage = [&](int kc, int s) {
         const int k0 = k_begin + kc * 64;
         const uint32_t a_s = sbase + s * STAGE_BYTES, b_s = a_s + A_BYTES;
@@ -219,7 +300,6 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const GemmParams p) {
         if (s < nk) load_stage(s, s);
         cp_async_commit();
     }
-    int issued = 0;  // MMA batches committed
     for (int kc = 0; kc < nk; ++kc) {
         const int s = kc % STAGES;
         cp_async_wait<STAGES - 2>();
@@ -251,6 +331,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const GemmParams p) {
         cp_async_commit();
     }
     cp_async_wait<0>();
+    }
     bool done = true;
     if (issued > 0) {
         const int last = issued - 1;
@@ -296,7 +377,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const GemmParams p) {
 }
 
 template <int BN, int STAGES>
-constexpr size_t gemm_smem_bytes() {
+constexpr size_t gemm_smem_bytes() {  // (both staging modes)
     return (size_t)STAGES * (128 * 64 * 2 + BN * 64 * 2) + 1024;
 }
 

@@ -141,13 +141,12 @@ def run(quick=False, train_rooms=3, iters_per_kf=150, keyframes=8, epochs=4, wor
     n = min(X.shape[0], max_pairs or X.shape[0])
     n = (n // 4096) * 4096
     X, T = X[:n].contiguous(), T[:n].contiguous()
-    Xt = X.T.contiguous()
     t_data = time.time() - t0
     # ---- 2. training ----
     mlp = MLPInit(seed=0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    hist = mlp.fit(X, Xt, T, epochs=epochs, batch=4096)
+    hist = mlp.fit(X, T, epochs=epochs)
     e1.record()
     e1.synchronize()
     train_s = e0.elapsed_time(e1) / 1e3

@@ -109,25 +109,37 @@ class MLPInit:
         self.W1[:, 2009:] = 0  # padding features stay inert
         self.pack()
 
-    def fit(self, X, Xt_full, T, epochs=3, batch=4096, seed=0, log=None):
-        """X: bf16 [n][2048]; Xt_full: bf16 [2048][n]; T: fp32 [n][32] raw targets."""
+    def fit(self, X, T, epochs=3, batch=None, seed=0, log=None):
+        """X: bf16 [n][2048]; T: fp32 [n][32] raw targets.  batch: rows per Adam step (a
+        multiple of 128); default 16384 when that still gives 32 steps per epoch, else 4096
+        (large batches keep the tensor cores and HBM busy: the layer-1 GEMM streams its
+        operand at about 2.8 TB/s at 65536 rows and is latency-bound below 16384).  The
+        learning rate grows with the square root of the batch from 1e-3 at 4096."""
         n = X.shape[0]
+        if batch is None:
+            batch = 16384 if n >= 32 * 16384 else 4096
+        base_lr = self.lr
+        self.lr = base_lr * math.sqrt(batch / 4096)
         self.set_standardisation(T)
         T_std = ((T - self.y_mean) / self.y_std).contiguous()
         loss = torch.zeros(1, device=self.device)
         g = torch.Generator(device="cpu").manual_seed(seed)
         history = []
         n_batches = n // batch
+        # every batch's transposed input [2048][batch] once, contiguous (the weight gradient of
+        # layer 1 reads it K-major)
+        Xb = X[:n_batches * batch].view(n_batches, batch, IN)
+        Xtb = Xb.transpose(1, 2).contiguous()
         for ep in range(epochs):
             perm = torch.randperm(n_batches, generator=g)
             loss.zero_()
             for bi in perm.tolist():
                 sl = slice(bi * batch, (bi + 1) * batch)
-                xt = Xt_full[:, sl].contiguous()
-                self.train_step(X[sl], xt, T_std[sl], batch, loss)
+                self.train_step(Xb[bi], Xtb[bi], T_std[sl], batch, loss)
             history.append(float(loss.item()) / max(1, n_batches))
             if log:
                 log(f"epoch {ep}: loss {history[-1]:.4f}")
+        self.lr = base_lr
         return history
 
     def predict(self, X, B):
