@@ -304,9 +304,13 @@ struct PixelArgs {
     const int *counts;
     const sg_view *views;
     LossViews lv;
-    float *partials;        // per CTA: (sum |D - D_gt| over valid, sum CE over valid)
+    float *partials;        // per pixel block, kPixSlots slots of (sum |D - D_gt| over valid, sum CE over valid)
     float *dec_partials;    // per CTA: K x C share of the decoder gradient
 };
+
+// Loss-sum slots per 256-pixel block: one per warp (the SIMT kernel fills slot 0 with its
+// block sum and zeroes the others).
+constexpr int kPixSlots = kLossThreads / 32;
 
 // Two-level, fixed-order reduction of the per-CTA decoder-gradient shares:
 // level 1: chunk c of kDecChunks sums CTAs [c n / kDecChunks, (c+1) n / kDecChunks);
@@ -461,9 +465,9 @@ __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
     }
     const float t1 = block_sum(l1d, s_red);
     const float t2 = block_sum(ce, s_red);
-    if (threadIdx.x == 0) {
-        a.partials[2 * blk] = t1;
-        a.partials[2 * blk + 1] = t2;
+    if (threadIdx.x < kPixSlots) {
+        a.partials[2 * (kPixSlots * blk + threadIdx.x)] = threadIdx.x == 0 ? t1 : 0.f;
+        a.partials[2 * (kPixSlots * blk + threadIdx.x) + 1] = threadIdx.x == 0 ? t2 : 0.f;
     }
 }
 
@@ -475,242 +479,275 @@ __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
 //   step is permuted so that A column tig / tig + 4 is class 2 tig / 2 tig + 1, and the B
 //   rows follow the same permutation), and dW = dZ^T S with dZ transposed through shared
 //   memory.  All three run as 3xTF32 MMAs (FP32-level accuracy).
+//
+// Persistent: the warps of a resident grid walk the 32-pixel units of the image set, so the
+// decoder is split into shared memory once per CTA and each warp keeps its share of dL/dW in
+// registers across all of its units; no block barrier inside the loop.  Each unit's two loss
+// sums go to its own partial slot (kPixSlots per 256-pixel block); the CTA writes one K x C
+// row of decoder-gradient partials at the end, its warps summed in a fixed order.
 template <int C, int K>
 __host__ __device__ constexpr int ce_mma_smem_floats() {
-    return 2 * K * (C + 4) + K * C + (kLossThreads / 32) * 32 * (K + 8);
+    return 2 * K * (C + 4) + (kLossThreads / 32) * 32 * (K + 8);
 }
 
-// At C K <= 512 the kernel is bounded to 64 registers, so that four CTAs fit an SM (their 48 KB
-// of shared memory allows four; 80 registers allowed three): 2 % faster on the 16 x 32 decoder
-// despite a 56-byte spill.
+// At C K <= 512 the kernel is bounded to 80 registers (three CTAs per SM): measured faster than
+// 64 registers and four CTAs, which spill the warp's decoder-gradient fragments.
 template <int C, int K>
-__global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 4 : 2) ce_decoder_mma_kernel(PixelArgs a) {
+__global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder_mma_kernel(PixelArgs a) {
     pdl_begin();
     static_assert(C % 8 == 0 && K % 16 == 0, "MMA tiles");
+    static_assert(32 * (K + 8) >= K * C, "a warp's dZ stash holds its K x C gradient share");
     constexpr int CP = C + 4;   // decoder row pitch: 4 mod 8, conflict-free B fragments
     constexpr int KP = K + 8;   // dZ row pitch: 8 or 24 mod 32, conflict-free A fragments
     constexpr int NK = K / 8, NC = C / 8;
     extern __shared__ __align__(16) float s_dyn[];
-    __shared__ float s_red[kLossThreads / 32];
     float *s_whi = s_dyn, *s_wlo = s_whi + K * CP;
-    float *s_acc = s_wlo + K * CP;  // K x C: this block's share of dL/dW
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
-    float *s_dz = s_acc + K * C + warp * 32 * KP;
+    float *s_dz = s_wlo + K * CP + warp * 32 * KP;
     for (int i = threadIdx.x; i < K * C; i += kLossThreads) {
         uint32_t h, l;
         split_tf32(a.decoder[i], h, l);
         s_whi[(i / C) * CP + i % C] = __uint_as_float(h);
         s_wlo[(i / C) * CP + i % C] = __uint_as_float(l);
-        s_acc[i] = 0.f;
     }
-    const int blk = blockIdx.x;
-    const int v = find_prefix(a.lv.pix_blk_off, a.lv.n, blk);
-    const sg_view &vw = a.views[v];
-    const int HW = vw.W * vw.H;
-    const int pw = (blk - a.lv.pix_blk_off[v]) * kLossThreads + warp * 32;  // the warp's first pixel
-    const size_t p0 = (size_t)vw.pixel_offset;
-    const float *semv = a.sem + (size_t)C * p0;
-    const int nd = a.counts[2 * v], nl = a.counts[2 * v + 1];
     __syncthreads();
-    float l1d = 0.f, ce = 0.f;
-    {
-        const int p = pw + lane;
-        if (p < HW) {
-            const float gd = a.gt_depth[p0 + p];
-            float gdep = 0.f;
-            if (gd > 0.f) {
-                const float d = a.depth[p0 + p] - gd;
-                l1d = fabsf(d);
-                gdep = a.w_depth * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) / (float)nd;
-            }
-            a.g_depth[p0 + p] = gdep;
-        }
-    }
-    auto S = [&](int px, int f) -> float {
-        const int p = pw + px;
-        return p < HW ? semv[(size_t)f * HW + p] : 0.f;
-    };
-    // ---- Z = S W^T: M = pixels (2 x 16), N = classes, K = features ----
-    // all of the warp's feature loads are issued before the first MMA (memory-level parallelism)
-    float sa[NC][2][4];
+    const bool dec_grad = a.decoder_grad != nullptr;
+    // this warp's share of dW = dZ^T S over all of its pixels (M = classes, N = features)
+    float dw[K / 16][NC][4];
 #pragma unroll
-    for (int ks = 0; ks < NC; ++ks)
+    for (int mt = 0; mt < K / 16; ++mt)
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int r0 = 16 * mt + gid, f0 = 8 * ks + tig;
-            sa[ks][mt][0] = S(r0, f0);
-            sa[ks][mt][1] = S(r0 + 8, f0);
-            sa[ks][mt][2] = S(r0, f0 + 4);
-            sa[ks][mt][3] = S(r0 + 8, f0 + 4);
-        }
-    int labs[2][2];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int p = pw + 16 * mt + gid + 8 * h;
-            labs[mt][h] = p < HW ? a.label[p0 + p] : -1;
-        }
-    float z[2][NK][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < NK; ++nt) z[mt][nt][0] = z[mt][nt][1] = z[mt][nt][2] = z[mt][nt][3] = 0.f;
-#pragma unroll
-    for (int ks = 0; ks < NC; ++ks) {
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            uint32_t ah[4], al[4];
-            const int f0 = 8 * ks + tig;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) split_tf32(sa[ks][mt][i], ah[i], al[i]);
-#pragma unroll
-            for (int nt = 0; nt < NK; ++nt) {
-                const int w0 = (8 * nt + gid) * CP + f0;
-                mma_tf32x3(z[mt][nt], ah, al, __float_as_uint(s_whi[w0]), __float_as_uint(s_whi[w0 + 4]),
-                           __float_as_uint(s_wlo[w0]), __float_as_uint(s_wlo[w0 + 4]));
+        for (int nt = 0; nt < NC; ++nt) dw[mt][nt][0] = dw[mt][nt][1] = dw[mt][nt][2] = dw[mt][nt][3] = 0.f;
+    // work unit u = 32 pixels: slot u % kPixSlots of 256-pixel block u / kPixSlots; the warps
+    // of the grid take units u = w, w + n_warps, ... (w the warp's grid-wide index)
+    const int n_units = kPixSlots * a.lv.pix_blk_off[a.lv.n];
+    const int n_warps = (int)gridDim.x * kPixSlots;
+    for (int u = (int)blockIdx.x * kPixSlots + warp; u < n_units; u += n_warps) {
+        const int blk = u / kPixSlots, slot = u % kPixSlots;
+        const int v = find_prefix(a.lv.pix_blk_off, a.lv.n, blk);
+        const sg_view &vw = a.views[v];
+        const int HW = vw.W * vw.H;
+        const int pw = (blk - a.lv.pix_blk_off[v]) * kLossThreads + slot * 32;  // the unit's first pixel
+        const size_t p0 = (size_t)vw.pixel_offset;
+        const float *semv = a.sem + (size_t)C * p0;
+        const int nd = a.counts[2 * v], nl = a.counts[2 * v + 1];
+        float l1d = 0.f, ce = 0.f;
+        {
+            const int p = pw + lane;
+            if (p < HW) {
+                const float gd = a.gt_depth[p0 + p];
+                float gdep = 0.f;
+                if (gd > 0.f) {
+                    const float d = a.depth[p0 + p] - gd;
+                    l1d = fabsf(d);
+                    gdep = a.w_depth * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) / (float)nd;
+                }
+                a.g_depth[p0 + p] = gdep;
             }
         }
-    }
-    // ---- softmax, CE and dZ per pixel row (row 16 mt + gid + 8 h; classes 8 nt + 2 tig + c) ----
+        auto S = [&](int px, int f) -> float {
+            const int p = pw + px;
+            return p < HW ? semv[(size_t)f * HW + p] : 0.f;
+        };
+        // ---- Z = S W^T: M = pixels (2 x 16), N = classes, K = features ----
+        // all of the warp's feature loads are issued before the first MMA (memory-level parallelism)
+        float sa[NC][2][4];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
+        for (int ks = 0; ks < NC; ++ks)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int lab = labs[mt][h];
-            float m = -INFINITY;
-#pragma unroll
-            for (int nt = 0; nt < NK; ++nt) m = fmaxf(m, fmaxf(z[mt][nt][2 * h], z[mt][nt][2 * h + 1]));
-            m = fmaxf(m, __shfl_xor_sync(SG_FULL_MASK, m, 1));
-            m = fmaxf(m, __shfl_xor_sync(SG_FULL_MASK, m, 2));
-            float se = 0.f, zl = 0.f;
-            bool has_lab = false;
-#pragma unroll
-            for (int nt = 0; nt < NK; ++nt)
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int cls = 8 * nt + 2 * tig + c;
-                    if (cls == lab) {
-                        zl = z[mt][nt][2 * h + c] - m;
-                        has_lab = true;
-                    }
-                    const float e = __expf(z[mt][nt][2 * h + c] - m);
-                    z[mt][nt][2 * h + c] = e;
-                    se += e;
-                }
-            se += __shfl_xor_sync(SG_FULL_MASK, se, 1);
-            se += __shfl_xor_sync(SG_FULL_MASK, se, 2);
-            const bool valid = lab >= 0;
-            if (valid && has_lab) ce += logf(se) - zl;
-            const float sc = valid ? a.w_sem / (float)nl : 0.f;
-            const float inv = 1.f / se;
-#pragma unroll
-            for (int nt = 0; nt < NK; ++nt)
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int cls = 8 * nt + 2 * tig + c;
-                    z[mt][nt][2 * h + c] = sc * (z[mt][nt][2 * h + c] * inv - (cls == lab ? 1.f : 0.f));
-                }
-        }
-    }
-    // ---- dS = dZ W: M = pixels, N = features, K = classes (permuted within each 8-class step) ----
-    {
-        float ds[2][NC][4];
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r0 = 16 * mt + gid, f0 = 8 * ks + tig;
+                sa[ks][mt][0] = S(r0, f0);
+                sa[ks][mt][1] = S(r0 + 8, f0);
+                sa[ks][mt][2] = S(r0, f0 + 4);
+                sa[ks][mt][3] = S(r0 + 8, f0 + 4);
+            }
+        int labs[2][2];
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < NC; ++nt) ds[mt][nt][0] = ds[mt][nt][1] = ds[mt][nt][2] = ds[mt][nt][3] = 0.f;
+            for (int h = 0; h < 2; ++h) {
+                const int p = pw + 16 * mt + gid + 8 * h;
+                labs[mt][h] = p < HW ? a.label[p0 + p] : -1;
+            }
+        float z[2][NK][4];
 #pragma unroll
-        for (int ks = 0; ks < NK; ++ks) {
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NK; ++nt) z[mt][nt][0] = z[mt][nt][1] = z[mt][nt][2] = z[mt][nt][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < NC; ++ks) {
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
                 uint32_t ah[4], al[4];
-                // A column tig = class 8 ks + 2 tig (d0 / d2), column tig + 4 = class 8 ks + 2 tig + 1 (d1 / d3)
-                split_tf32(z[mt][ks][0], ah[0], al[0]);
-                split_tf32(z[mt][ks][2], ah[1], al[1]);
-                split_tf32(z[mt][ks][1], ah[2], al[2]);
-                split_tf32(z[mt][ks][3], ah[3], al[3]);
+                const int f0 = 8 * ks + tig;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) split_tf32(sa[ks][mt][i], ah[i], al[i]);
+#pragma unroll
+                for (int nt = 0; nt < NK; ++nt) {
+                    const int w0 = (8 * nt + gid) * CP + f0;
+                    mma_tf32x3(z[mt][nt], ah, al, __float_as_uint(s_whi[w0]), __float_as_uint(s_whi[w0 + 4]),
+                               __float_as_uint(s_wlo[w0]), __float_as_uint(s_wlo[w0 + 4]));
+                }
+            }
+        }
+        // ---- softmax, CE and dZ per pixel row (row 16 mt + gid + 8 h; classes 8 nt + 2 tig + c) ----
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int lab = labs[mt][h];
+                float m = -INFINITY;
+#pragma unroll
+                for (int nt = 0; nt < NK; ++nt) m = fmaxf(m, fmaxf(z[mt][nt][2 * h], z[mt][nt][2 * h + 1]));
+                m = fmaxf(m, __shfl_xor_sync(SG_FULL_MASK, m, 1));
+                m = fmaxf(m, __shfl_xor_sync(SG_FULL_MASK, m, 2));
+                float se = 0.f, zl = 0.f;
+                bool has_lab = false;
+#pragma unroll
+                for (int nt = 0; nt < NK; ++nt)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const int cls = 8 * nt + 2 * tig + c;
+                        if (cls == lab) {
+                            zl = z[mt][nt][2 * h + c] - m;
+                            has_lab = true;
+                        }
+                        const float e = __expf(z[mt][nt][2 * h + c] - m);
+                        z[mt][nt][2 * h + c] = e;
+                        se += e;
+                    }
+                se += __shfl_xor_sync(SG_FULL_MASK, se, 1);
+                se += __shfl_xor_sync(SG_FULL_MASK, se, 2);
+                const bool valid = lab >= 0;
+                if (valid && has_lab) ce += logf(se) - zl;
+                const float sc = valid ? a.w_sem / (float)nl : 0.f;
+                const float inv = 1.f / se;
+#pragma unroll
+                for (int nt = 0; nt < NK; ++nt)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const int cls = 8 * nt + 2 * tig + c;
+                        z[mt][nt][2 * h + c] = sc * (z[mt][nt][2 * h + c] * inv - (cls == lab ? 1.f : 0.f));
+                    }
+            }
+        }
+        // the two loss sums of this block's warp
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            l1d += __shfl_xor_sync(SG_FULL_MASK, l1d, o);
+            ce += __shfl_xor_sync(SG_FULL_MASK, ce, o);
+        }
+        if (lane == 0) {
+            a.partials[2 * u] = l1d;
+            a.partials[2 * u + 1] = ce;
+        }
+        // ---- dS = dZ W: M = pixels, N = features, K = classes (permuted within each 8-class step) ----
+        {
+            float ds[2][NC][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NC; ++nt) ds[mt][nt][0] = ds[mt][nt][1] = ds[mt][nt][2] = ds[mt][nt][3] = 0.f;
+#pragma unroll
+            for (int ks = 0; ks < NK; ++ks) {
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    uint32_t ah[4], al[4];
+                    // A column tig = class 8 ks + 2 tig (d0 / d2), column tig + 4 = class 8 ks + 2 tig + 1 (d1 / d3)
+                    split_tf32(z[mt][ks][0], ah[0], al[0]);
+                    split_tf32(z[mt][ks][2], ah[1], al[1]);
+                    split_tf32(z[mt][ks][1], ah[2], al[2]);
+                    split_tf32(z[mt][ks][3], ah[3], al[3]);
+#pragma unroll
+                    for (int nt = 0; nt < NC; ++nt) {
+                        const int w0 = (8 * ks + 2 * tig) * CP + 8 * nt + gid;
+                        mma_tf32x3(ds[mt][nt], ah, al, __float_as_uint(s_whi[w0]), __float_as_uint(s_whi[w0 + CP]),
+                                   __float_as_uint(s_wlo[w0]), __float_as_uint(s_wlo[w0 + CP]));
+                    }
+                }
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NC; ++nt)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int p = pw + 16 * mt + gid + 8 * (i >> 1);
+                        const int f = 8 * nt + 2 * tig + (i & 1);
+                        if (p < HW) a.g_sem[(size_t)C * p0 + (size_t)f * HW + p] = ds[mt][nt][i];
+                    }
+        }
+        // ---- dW += dZ^T S: M = classes, N = features, K = pixels ----
+        if (dec_grad) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NK; ++nt)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        s_dz[(16 * mt + gid + 8 * (i >> 1)) * KP + 8 * nt + 2 * tig + (i & 1)] = z[mt][nt][i];
+            __syncwarp();
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                uint32_t bh[NC][2], bl[NC][2];
 #pragma unroll
                 for (int nt = 0; nt < NC; ++nt) {
-                    const int w0 = (8 * ks + 2 * tig) * CP + 8 * nt + gid;
-                    mma_tf32x3(ds[mt][nt], ah, al, __float_as_uint(s_whi[w0]), __float_as_uint(s_whi[w0 + CP]),
-                               __float_as_uint(s_wlo[w0]), __float_as_uint(s_wlo[w0 + CP]));
+                    split_tf32(S(8 * ks + tig, 8 * nt + gid), bh[nt][0], bl[nt][0]);
+                    split_tf32(S(8 * ks + tig + 4, 8 * nt + gid), bh[nt][1], bl[nt][1]);
+                }
+#pragma unroll
+                for (int mt = 0; mt < K / 16; ++mt) {
+                    const float *d0 = s_dz + (8 * ks + tig) * KP + 16 * mt + gid;
+                    uint32_t ah[4], al[4];
+                    split_tf32(d0[0], ah[0], al[0]);
+                    split_tf32(d0[8], ah[1], al[1]);
+                    split_tf32(d0[4 * KP], ah[2], al[2]);
+                    split_tf32(d0[4 * KP + 8], ah[3], al[3]);
+#pragma unroll
+                    for (int nt = 0; nt < NC; ++nt)
+                        mma_tf32x3(dw[mt][nt], ah, al, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
                 }
             }
+            __syncwarp();  // the stash is rewritten by the next unit
         }
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NC; ++nt)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int p = pw + 16 * mt + gid + 8 * (i >> 1);
-                    const int f = 8 * nt + 2 * tig + (i & 1);
-                    if (p < HW) a.g_sem[(size_t)C * p0 + (size_t)f * HW + p] = ds[mt][nt][i];
-                }
     }
-    // ---- dW += dZ^T S: M = classes, N = features, K = pixels ----
-    if (a.decoder_grad) {
+    if (!dec_grad) return;
+    // this CTA's share of dL/dW: every warp's fragments into its own stash, then summed over
+    // the warps in order (deterministic), one K x C row per CTA
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
+    for (int mt = 0; mt < K / 16; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < NK; ++nt)
+        for (int nt = 0; nt < NC; ++nt)
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    s_dz[(16 * mt + gid + 8 * (i >> 1)) * KP + 8 * nt + 2 * tig + (i & 1)] = z[mt][nt][i];
-        __syncwarp();
-        float dw[K / 16][NC][4];
-#pragma unroll
-        for (int mt = 0; mt < K / 16; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NC; ++nt) dw[mt][nt][0] = dw[mt][nt][1] = dw[mt][nt][2] = dw[mt][nt][3] = 0.f;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-            uint32_t bh[NC][2], bl[NC][2];
-#pragma unroll
-            for (int nt = 0; nt < NC; ++nt) {
-                split_tf32(S(8 * ks + tig, 8 * nt + gid), bh[nt][0], bl[nt][0]);
-                split_tf32(S(8 * ks + tig + 4, 8 * nt + gid), bh[nt][1], bl[nt][1]);
-            }
-#pragma unroll
-            for (int mt = 0; mt < K / 16; ++mt) {
-                const float *d0 = s_dz + (8 * ks + tig) * KP + 16 * mt + gid;
-                uint32_t ah[4], al[4];
-                split_tf32(d0[0], ah[0], al[0]);
-                split_tf32(d0[8], ah[1], al[1]);
-                split_tf32(d0[4 * KP], ah[2], al[2]);
-                split_tf32(d0[4 * KP + 8], ah[3], al[3]);
-#pragma unroll
-                for (int nt = 0; nt < NC; ++nt) mma_tf32x3(dw[mt][nt], ah, al, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
-            }
-        }
-#pragma unroll
-        for (int mt = 0; mt < K / 16; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NC; ++nt)
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    atomicAdd(s_acc + (16 * mt + gid + 8 * (i >> 1)) * C + 8 * nt + 2 * tig + (i & 1), dw[mt][nt][i]);
-        __syncthreads();
-        for (int o = threadIdx.x; o < K * C; o += kLossThreads) a.dec_partials[(size_t)blk * K * C + o] = s_acc[o];
-    }
-    const float t1 = block_sum(l1d, s_red);
-    const float t2 = block_sum(ce, s_red);
-    if (threadIdx.x == 0) {
-        a.partials[2 * blk] = t1;
-        a.partials[2 * blk + 1] = t2;
+            for (int i = 0; i < 4; ++i)
+                s_dz[(16 * mt + gid + 8 * (i >> 1)) * C + 8 * nt + 2 * tig + (i & 1)] = dw[mt][nt][i];
+    __syncthreads();
+    const float *s_all = s_wlo + K * CP;
+    for (int o = threadIdx.x; o < K * C; o += kLossThreads) {
+        float s = 0.f;
+        for (int w = 0; w < kLossThreads / 32; ++w) s += s_all[w * 32 * KP + o];
+        a.dec_partials[(size_t)blockIdx.x * K * C + o] = s;
     }
 }
 
+// Resident grid of the persistent decoder kernel (at most one CTA per pixel block); returns
+// the number of CTAs, i.e. of decoder-gradient partial rows.
 template <int C, int K>
-static void launch_ce_mma(PixelArgs &pa, int blocks, cudaStream_t st) {
+static int launch_ce_mma(PixelArgs &pa, int blocks, cudaStream_t st) {
     const size_t smem = sizeof(float) * ce_mma_smem_floats<C, K>();
-    static bool attr = false;
-    if (!attr) {
+    static int resident = 0;
+    if (!resident) {
         cudaFuncSetAttribute(ce_decoder_mma_kernel<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ce_decoder_mma_kernel<C, K>, kLossThreads, smem);
+        resident = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     }
-    launch_pdl(ce_decoder_mma_kernel<C, K>, blocks, kLossThreads, smem, st, pa);
+    const int grid = blocks < resident ? blocks : resident;
+    launch_pdl(ce_decoder_mma_kernel<C, K>, grid, kLossThreads, smem, st, pa);
+    return grid;
 }
 
 struct FinalArgs {
@@ -753,7 +790,8 @@ __global__ void loss_finalize_kernel(FinalArgs a) {
         }
     }
     double b[2] = {0, 0};
-    for (int i = a.lv.pix_blk_off[v] + threadIdx.x; i < a.lv.pix_blk_off[v + 1]; i += kLossThreads) {
+    for (int i = kPixSlots * a.lv.pix_blk_off[v] + threadIdx.x; i < kPixSlots * a.lv.pix_blk_off[v + 1];
+         i += kLossThreads) {
         b[0] += a.pix[2 * i];
         b[1] += a.pix[2 * i + 1];
     }
@@ -800,7 +838,7 @@ static void make_loss_views(const sg_view *vh, int n_views, LossViews &lv) {
 static size_t loss_ws_bytes(int n_views, int n_tiles, int n_blocks, int KC) {
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     return al(sizeof(int) * 2 * n_views) + 2 * al(sizeof(float) * 2 * n_tiles) +
-           al(sizeof(float) * 2 * n_blocks) + al(sizeof(float) * (size_t)n_blocks * KC) +
+           al(sizeof(float) * 2 * kPixSlots * n_blocks) + al(sizeof(float) * (size_t)n_blocks * KC) +
            al(sizeof(float) * (size_t)kDecChunks * KC);
 }
 
@@ -836,17 +874,19 @@ static void launch_pixel_t(PixelArgs &pa, int blocks, cudaStream_t st) {
     launch_pdl(loss_pixel_kernel<C, K>, blocks, kLossThreads, dyn, st, pa);
 }
 
-static bool launch_pixel(PixelArgs &pa, int blocks, cudaStream_t st) {
+// Launches the per-pixel loss kernel; returns the number of decoder-gradient partial rows it
+// writes (its CTAs), or 0 for an unsupported (C, K).
+static int launch_pixel(PixelArgs &pa, int blocks, cudaStream_t st) {
     const int C = pa.C, K = pa.K;
     if (pa.ce && pa.decoder) {
-#define SG_CE(c, k) if (C == c && K == k) { launch_ce_mma<c, k>(pa, blocks, st); return true; }
+#define SG_CE(c, k) if (C == c && K == k) return launch_ce_mma<c, k>(pa, blocks, st);
         SG_CE(16, 16) SG_CE(16, 32) SG_CE(32, 32)
 #undef SG_CE
     }
-#define SG_PIX(c, k) if (C == c && K == k) { launch_pixel_t<c, k>(pa, blocks, st); return true; }
+#define SG_PIX(c, k) if (C == c && K == k) { launch_pixel_t<c, k>(pa, blocks, st); return blocks; }
     SG_PIX(4, 4) SG_PIX(8, 8) SG_PIX(16, 16) SG_PIX(16, 32) SG_PIX(32, 32) SG_PIX(40, 40)
 #undef SG_PIX
-    return false;
+    return 0;
 }
 
 sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *views,
@@ -862,7 +902,7 @@ sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *v
     int *counts = (int *)take(sizeof(int) * 2 * n_views);
     float *p_rgb = (float *)take(sizeof(float) * 2 * n_tiles);
     float *p_sem = (float *)take(sizeof(float) * 2 * n_tiles);
-    float *p_pix = (float *)take(sizeof(float) * 2 * n_blocks);
+    float *p_pix = (float *)take(sizeof(float) * 2 * kPixSlots * n_blocks);
     const int ce = lc->sem_mode == 0;
     const int K = ce ? lc->n_classes : C;
     const int KC = loss_decoder_partials(lc, C);
@@ -889,12 +929,13 @@ sg_status launch_loss(const sg_images *r, const sg_targets *gt, const sg_view *v
     }
     PixelArgs pa{r->depth, gt->depth, r->sem, gt->label, dL->depth, dL->sem, lc->decoder,
                  KC ? lc->decoder_grad : nullptr, C, K, ce, lc->w_depth, lc->w_sem, counts, views, lv, p_pix, p_dec};
-    if (!launch_pixel(pa, n_blocks, st)) {
+    const int dec_rows = launch_pixel(pa, n_blocks, st);
+    if (!dec_rows) {
         set_error("pyramid_loss: unsupported (C=%d, classes=%d)", C, K);
         return SG_ERR_INVALID_ARG;
     }
     if (ce && lc->decoder_grad) {
-        launch_pdl(decoder_reduce1_kernel, dim3((KC + 127) / 128, kDecChunks), 128, 0, st, p_dec, n_blocks, KC, p_dec2);
+        launch_pdl(decoder_reduce1_kernel, dim3((KC + 127) / 128, kDecChunks), 128, 0, st, p_dec, dec_rows, KC, p_dec2);
         launch_pdl(decoder_reduce2_kernel, (KC + 127) / 128, 128, 0, st, p_dec2, KC, lc->decoder_grad);
         count_launches(2);
     }

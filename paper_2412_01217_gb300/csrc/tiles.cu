@@ -129,29 +129,54 @@ __global__ void scan_blocks_kernel(uint32_t *bsum, int G, int *total) {
     if (threadIdx.x == 0) *total = (int)run;
 }
 
-// Apply for the compaction: write (depth bits, record) of every visible record.
+// Apply for the compaction: write (depth bits, record) of every visible record.  Each thread
+// takes 8 consecutive records per round (two 16-byte loads of their rectangles when the
+// array is 16-byte aligned), so a round of the block covers 2048 records with one block scan
+// and all of its loads in flight together.
+constexpr int kCompactPerThread = 8;
 __global__ void compact_apply_kernel(const uint2 *__restrict__ rect, const float4 *__restrict__ geo,
                                      int n, const uint32_t *__restrict__ boff, int G,
                                      uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
     pdl_begin();
+    constexpr int E = kCompactPerThread;
     int beg, end;
     block_range(n, G, blockIdx.x, beg, end);
+    const bool vec = (reinterpret_cast<uintptr_t>(rect) & 15u) == 0;
     uint32_t run = boff[blockIdx.x];
-    for (int base = beg; base < end; base += kScanThreads) {
-        const int i = base + threadIdx.x;
-        uint32_t f = 0;
-        uint2 r = make_uint2(0, 0);
-        if (i < end) {
-            r = rect[i];
-            f = r.x != r.y ? 1u : 0u;
+    for (int base = beg; base < end; base += kScanThreads * E) {
+        const int i0 = base + (int)threadIdx.x * E;  // a multiple of 8 (beg is one of 256)
+        uint2 r[E];
+        if (vec && i0 + E <= end) {
+            const uint4 *p4 = reinterpret_cast<const uint4 *>(rect + i0);
+#pragma unroll
+            for (int q = 0; q < E / 2; ++q) {
+                const uint4 w = p4[q];
+                r[2 * q] = make_uint2(w.x, w.y);
+                r[2 * q + 1] = make_uint2(w.z, w.w);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < E; ++q) r[q] = i0 + q < end ? rect[i0 + q] : make_uint2(0, 0);
         }
+        uint32_t f = 0, bits = 0;
+#pragma unroll
+        for (int q = 0; q < E; ++q)
+            if (r[q].x != r[q].y) {
+                bits |= 1u << q;
+                ++f;
+            }
+        float dep[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) dep[q] = ((bits >> q) & 1u) ? geo[2 * (size_t)(i0 + q)].z : 0.f;
         uint32_t tot;
-        const uint32_t ex = block_exclusive_scan(f, tot);
-        if (f) {
-            const float depth = geo[2 * (size_t)i].z;
-            key[run + ex] = __float_as_uint(depth);
-            val[run + ex] = (uint32_t)i;
-        }
+        uint32_t o = run + block_exclusive_scan(f, tot);
+#pragma unroll
+        for (int q = 0; q < E; ++q)
+            if ((bits >> q) & 1u) {
+                key[o] = __float_as_uint(dep[q]);
+                val[o] = (uint32_t)(i0 + q);
+                ++o;
+            }
         run += tot;
     }
 }
@@ -345,8 +370,10 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
 // Key sources of the radix sort: pairs held in arrays, or the tiles' list lengths.
 struct ArrayPairs {
     const uint32_t *k, *v;
-    __device__ uint32_t key(int i) const { return k[i]; }
-    __device__ uint32_t val(int i) const { return v[i]; }
+    // each pair is read once per kernel: evict-first loads, which leave L2 to the scatter's
+    // partly written output lines
+    __device__ uint32_t key(int i) const { return __ldcs(k + i); }
+    __device__ uint32_t val(int i) const { return __ldcs(v + i); }
 };
 // key = 63 - bucket of the tile's instance count n (bucket 0 for n = 0, else
 // 1 + 2 floor(log2 n) + the bit below the leading one): descending length, 6 bits
@@ -415,27 +442,30 @@ __device__ __forceinline__ void bucket_exclusive_scan(const uint32_t (&v)[DPT], 
     }
 }
 
-// Scatter of one digit pass.  Each block walks its input range in chunks of kScatterChunk
-// elements: a stable rank per digit inside the chunk (warp match_any + per-warp counts, 256
-// elements at a time), a reorder of the chunk by digit in shared memory, and a write-out in
-// which consecutive threads store consecutive elements of one digit run (coalesced stores
-// instead of one scattered sector per element).
-constexpr int kScatterIPT = 8;
-constexpr int kScatterChunk = kScanThreads * kScatterIPT;
+// Scatter of one digit pass.  Each block walks its input range in chunks of 256 IPT
+// elements; warp w owns the chunk's elements [32 IPT w, 32 IPT (w + 1)), lane l element
+// 32 it + l of them.  Ranking needs no block barrier per element row: every warp ranks its
+// own elements against a warp-private digit count (warp match_any + the lanes below), one
+// block pass turns the per-warp counts into per-digit offsets, the chunk is reordered by
+// digit in shared memory, and consecutive threads store consecutive elements of one digit
+// run (coalesced stores instead of one scattered sector per element).
+template <int ND>
+__host__ __device__ constexpr int scatter_ipt() { return 12; }
 
 template <class Src, int ND>
-__global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
+__global__ void __launch_bounds__(kScanThreads, 4) rs_scatter_kernel(
     Src src, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ n_ptr, int cap, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, int G) {
     pdl_begin();
     constexpr int kWarps = kScanThreads / 32;
-    constexpr int DPT = ND / kScanThreads;  // buckets per thread: tid * DPT + q
-    __shared__ uint32_t run[ND];   // global position of the next element of each digit
-    __shared__ uint32_t sub[ND];   // elements of each digit so far in this chunk
-    __shared__ uint32_t loc[ND];   // first slot of each digit in the reordered chunk
-    __shared__ uint32_t wcnt[kWarps][ND];
-    __shared__ uint32_t skey[kScatterChunk], sval[kScatterChunk];
+    constexpr int DPT = ND / kScanThreads;  // digits per thread: tid * DPT + q
+    constexpr int IPT = scatter_ipt<ND>();
+    constexpr int CH = kScanThreads * IPT;
+    __shared__ uint32_t run[ND];            // global position of the next element of each digit
+    __shared__ uint32_t loc[ND];            // first slot of each digit in the reordered chunk
+    __shared__ uint32_t wcnt[kWarps][ND];   // per-warp digit counts, then per-warp offsets
+    __shared__ uint32_t skey[CH], sval[CH];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // digit base = exclusive scan of the digit totals (+ this block's offset)
     {
@@ -450,71 +480,63 @@ __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
     int beg, end;
     block_range(n, G, blockIdx.x, beg, end);
     const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int cbase = beg; cbase < end; cbase += kScatterChunk) {
+    uint32_t *wc = wcnt[warp];
+    for (int cbase = beg; cbase < end; cbase += CH) {
 #pragma unroll
-        for (int q = 0; q < DPT; ++q) sub[tid * DPT + q] = 0;
-        const int nit = min(kScatterIPT, (end - cbase + kScanThreads - 1) / kScanThreads);  // block-uniform
-        uint32_t key[kScatterIPT], val[kScatterIPT], lrank[kScatterIPT];
-        // all of the chunk's loads first (their latencies overlap), then the ranking
+        for (int q = 0; q < ND / 32; ++q) wc[32 * q + lane] = 0;
+        const int wbase = cbase + 32 * IPT * warp;
+        uint32_t key[IPT], val[IPT], rank[IPT];
+        // all of the warp's loads first (their latencies overlap), then the ranking
 #pragma unroll
-        for (int it = 0; it < kScatterIPT; ++it) {
-            const int i = cbase + it * kScanThreads + tid;
-            const bool valid = it < nit && i < end;
+        for (int it = 0; it < IPT; ++it) {
+            const int i = wbase + 32 * it + lane;
+            const bool valid = i < end;
             key[it] = valid ? src.key(i) : 0u;
             val[it] = valid ? src.val(i) : 0u;
         }
+        __syncwarp();
 #pragma unroll
-        for (int it = 0; it < kScatterIPT; ++it) {
-            if (it >= nit) break;
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w)
-#pragma unroll
-                for (int q = 0; q < DPT; ++q) wcnt[w][tid * DPT + q] = 0;
-            __syncthreads();
-            const int i = cbase + it * kScanThreads + tid;
-            const bool valid = i < end;
+        for (int it = 0; it < IPT; ++it) {
+            const bool valid = wbase + 32 * it + lane < end;
             const uint32_t d = valid ? ((key[it] >> shift) & mask) : (uint32_t)ND;
             const uint32_t peers = __match_any_sync(SG_FULL_MASK, d);
-            const uint32_t rank = __popc(peers & lt_mask);
-            if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = __popc(peers);
-            __syncthreads();
-            uint32_t s[DPT];
+            const uint32_t below = __popc(peers & lt_mask);
+            rank[it] = valid ? wc[d] + below : 0u;
+            __syncwarp();
+            if (valid && below == 0) wc[d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit: exclusive offsets of the warps, the chunk's count, and (block scan)
+        // the digit's first slot in the reordered chunk
+        uint32_t cnt[DPT], ex[DPT];
 #pragma unroll
-            for (int q = 0; q < DPT; ++q) {
-                s[q] = 0;
+        for (int q = 0; q < DPT; ++q) {
+            const int d = tid * DPT + q;
+            uint32_t s = 0;
 #pragma unroll
-                for (int w = 0; w < kWarps; ++w) {
-                    const uint32_t t = wcnt[w][tid * DPT + q];
-                    wcnt[w][tid * DPT + q] = s[q];
-                    s[q] += t;
-                }
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t c = wcnt[w][d];
+                wcnt[w][d] = s;
+                s += c;
             }
-            __syncthreads();
-            lrank[it] = valid ? sub[d] + wcnt[warp][d] + rank : 0u;
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < DPT; ++q) sub[tid * DPT + q] += s[q];
+            cnt[q] = s;
         }
-        __syncthreads();
-        {
-            uint32_t v[DPT], ex[DPT];
+        bucket_exclusive_scan<DPT>(cnt, ex);
 #pragma unroll
-            for (int q = 0; q < DPT; ++q) v[q] = sub[tid * DPT + q];
-            bucket_exclusive_scan<DPT>(v, ex);
-#pragma unroll
-            for (int q = 0; q < DPT; ++q) loc[tid * DPT + q] = ex[q];
-        }
+        for (int q = 0; q < DPT; ++q) loc[tid * DPT + q] = ex[q];
         __syncthreads();
 #pragma unroll
-        for (int it = 0; it < kScatterIPT; ++it) {
-            if (it < nit && cbase + it * kScanThreads + tid < end) {
-                const uint32_t li = loc[(key[it] >> shift) & mask] + lrank[it];
+        for (int it = 0; it < IPT; ++it) {
+            if (wbase + 32 * it + lane < end) {
+                const uint32_t d = (key[it] >> shift) & mask;
+                const uint32_t li = loc[d] + wc[d] + rank[it];
                 skey[li] = key[it];
                 sval[li] = val[it];
             }
         }
         __syncthreads();
-        const int cn = min(kScatterChunk, end - cbase);
+        const int cn = min(CH, end - cbase);
         for (int j = tid; j < cn; j += kScanThreads) {
             const uint32_t k = skey[j];
             const uint32_t d = (k >> shift) & mask;
@@ -524,8 +546,8 @@ __global__ void __launch_bounds__(kScanThreads) rs_scatter_kernel(
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < DPT; ++q) run[tid * DPT + q] += sub[tid * DPT + q];
-        __syncthreads();
+        for (int q = 0; q < DPT; ++q) run[tid * DPT + q] += cnt[q];
+        // (the next chunk's first block barrier orders these updates before their reads)
     }
 }
 
@@ -672,8 +694,8 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.bsum, G, w.counts + 0);
     launch_pdl(compact_apply_kernel, G, kScanThreads, 0, st, rect, geo, (int)R, w.bsum, G, w.dkey_in, w.dval_in);
     // 2. depth sort (32 bits).  Its input (the visible records) is a small fraction of R, so it
-    // runs on a grid of about one scatter chunk per block for R / 4, between G / 4 and G.
-    const int Gd = (int)std::min<int64_t>(G, std::max<int64_t>(G / 4, R / (4 * kScatterChunk)));
+    // runs on a grid of about 2048 elements per block for R / 4, between G / 4 and G.
+    const int Gd = (int)std::min<int64_t>(G, std::max<int64_t>(G / 4, R / (4 * 2048)));
     radix_sort(w.dkey_in, w.dval_in, w.dkey_out, w.dval_out, w.dkey_tmp, w.dval_tmp, w.counts + 0,
                (int)R, 32, w.hist, w.totals, Gd, st);
     // 3. emission in depth order (K -> lists->count)
