@@ -478,7 +478,11 @@ __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
 //   dS = dZ W with dZ taken from registers as the A operand (the k index of each 8-class
 //   step is permuted so that A column tig / tig + 4 is class 2 tig / 2 tig + 1, and the B
 //   rows follow the same permutation), and dW = dZ^T S with dZ transposed through shared
-//   memory.  All three run as 3xTF32 MMAs (FP32-level accuracy).
+//   memory.  All three run as 3xTF32 MMAs (FP32-level accuracy).  Shared-memory operands
+//   are read with ldmatrix (a 32-bit 8 x 4 tile is an 8 x 8 tile of 16-bit halves, and
+//   ldmatrix hands thread t the word at row t / 4, column t % 4: exactly the (gid, tig)
+//   element of an m16n8k8 TF32 fragment), and each decoder fragment serves both 16-pixel
+//   tiles.
 //
 // Persistent: the warps of a resident grid walk the 32-pixel units of the image set, so the
 // decoder is split into shared memory once per CTA and each warp keeps its share of dL/dW in
@@ -486,8 +490,27 @@ __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
 // sums go to its own partial slot (kPixSlots per 256-pixel block); the CTA writes one K x C
 // row of decoder-gradient partials at the end, its warps summed in a fixed order.
 template <int C, int K>
+struct CeLayout {
+    static constexpr int CP = C + 4;   // W rows (class-major): 16-byte rows, conflict-free ldmatrix
+    static constexpr int KT = K + 4;   // W^T rows (feature-major, classes permuted)
+    static constexpr int PP = 32 + 4;  // dZ^T rows (class-major over the warp's 32 pixels)
+    static constexpr int W_FLOATS = 2 * K * CP + 2 * C * KT;
+    static constexpr int WARP_FLOATS = K * PP > K * C ? K * PP : K * C;
+};
+
+template <int C, int K>
 __host__ __device__ constexpr int ce_mma_smem_floats() {
-    return 2 * K * (C + 4) + (kLossThreads / 32) * 32 * (K + 8);
+    return CeLayout<C, K>::W_FLOATS + (kLossThreads / 32) * CeLayout<C, K>::WARP_FLOATS;
+}
+
+__device__ __forceinline__ void ldsm_x2(const float *p, uint32_t &r0, uint32_t &r1) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void ldsm_x4(const float *p, uint32_t (&r)[4]) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a) : "memory");
 }
 
 // At C K <= 512 the kernel is bounded to 80 registers (three CTAs per SM): measured faster than
@@ -496,22 +519,30 @@ template <int C, int K>
 __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder_mma_kernel(PixelArgs a) {
     pdl_begin();
     static_assert(C % 8 == 0 && K % 16 == 0, "MMA tiles");
-    static_assert(32 * (K + 8) >= K * C, "a warp's dZ stash holds its K x C gradient share");
-    constexpr int CP = C + 4;   // decoder row pitch: 4 mod 8, conflict-free B fragments
-    constexpr int KP = K + 8;   // dZ row pitch: 8 or 24 mod 32, conflict-free A fragments
+    using L = CeLayout<C, K>;
+    constexpr int CP = L::CP, KT = L::KT, PP = L::PP;
     constexpr int NK = K / 8, NC = C / 8;
     extern __shared__ __align__(16) float s_dyn[];
-    float *s_whi = s_dyn, *s_wlo = s_whi + K * CP;
+    float *s_whi = s_dyn, *s_wlo = s_whi + K * CP;     // W [class][feature]
+    float *s_thi = s_wlo + K * CP, *s_tlo = s_thi + C * KT;  // W^T [feature][permuted class]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
-    float *s_dz = s_wlo + K * CP + warp * 32 * KP;
+    float *s_dz = s_dyn + L::W_FLOATS + warp * L::WARP_FLOATS;  // dZ^T [class][pixel]
     for (int i = threadIdx.x; i < K * C; i += kLossThreads) {
         uint32_t h, l;
         split_tf32(a.decoder[i], h, l);
-        s_whi[(i / C) * CP + i % C] = __uint_as_float(h);
-        s_wlo[(i / C) * CP + i % C] = __uint_as_float(l);
+        const int k = i / C, c = i % C;
+        s_whi[k * CP + c] = __uint_as_float(h);
+        s_wlo[k * CP + c] = __uint_as_float(l);
+        // class k = 8 q + 2 j + e sits at column 8 q + j + 4 e of W^T
+        const int kc = (k & ~7) + ((k & 7) >> 1) + 4 * (k & 1);
+        s_thi[c * KT + kc] = __uint_as_float(h);
+        s_tlo[c * KT + kc] = __uint_as_float(l);
     }
     __syncthreads();
     const bool dec_grad = a.decoder_grad != nullptr;
+    // ldmatrix row addresses: lanes 0-7 give rows 0-7 of the first 8 x 4 tile, lanes 8-15 of
+    // the second (4 columns further), lanes 16-31 (x4 only) the same 8 rows further down
+    const int lr = lane & 7, lc = (lane >> 3) & 1, lh = lane >> 4;
     // this warp's share of dW = dZ^T S over all of its pixels (M = classes, N = features)
     float dw[K / 16][NC][4];
 #pragma unroll
@@ -577,18 +608,20 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
             for (int nt = 0; nt < NK; ++nt) z[mt][nt][0] = z[mt][nt][1] = z[mt][nt][2] = z[mt][nt][3] = 0.f;
 #pragma unroll
         for (int ks = 0; ks < NC; ++ks) {
+            uint32_t ah[2][4], al[2][4];
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                uint32_t ah[4], al[4];
-                const int f0 = 8 * ks + tig;
+            for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-                for (int i = 0; i < 4; ++i) split_tf32(sa[ks][mt][i], ah[i], al[i]);
+                for (int i = 0; i < 4; ++i) split_tf32(sa[ks][mt][i], ah[mt][i], al[mt][i]);
 #pragma unroll
-                for (int nt = 0; nt < NK; ++nt) {
-                    const int w0 = (8 * nt + gid) * CP + f0;
-                    mma_tf32x3(z[mt][nt], ah, al, __float_as_uint(s_whi[w0]), __float_as_uint(s_whi[w0 + 4]),
-                               __float_as_uint(s_wlo[w0]), __float_as_uint(s_wlo[w0 + 4]));
-                }
+            for (int nt = 0; nt < NK; ++nt) {
+                // B (8 x 8): b0 (tig, gid) = W[8 nt + gid][8 ks + tig], b1 four features further
+                const int w0 = (8 * nt + lr) * CP + 8 * ks + 4 * lc;
+                uint32_t bh0, bh1, bl0, bl1;
+                ldsm_x2(s_whi + w0, bh0, bh1);
+                ldsm_x2(s_wlo + w0, bl0, bl1);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) mma_tf32x3(z[mt][nt], ah[mt], al[mt], bh0, bh1, bl0, bl1);
             }
         }
         // ---- softmax, CE and dZ per pixel row (row 16 mt + gid + 8 h; classes 8 nt + 2 tig + c) ----
@@ -632,7 +665,7 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
                     }
             }
         }
-        // the two loss sums of this block's warp
+        // the two loss sums of this unit
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             l1d += __shfl_xor_sync(SG_FULL_MASK, l1d, o);
@@ -651,20 +684,25 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
                 for (int nt = 0; nt < NC; ++nt) ds[mt][nt][0] = ds[mt][nt][1] = ds[mt][nt][2] = ds[mt][nt][3] = 0.f;
 #pragma unroll
             for (int ks = 0; ks < NK; ++ks) {
+                uint32_t ah[2][4], al[2][4];
 #pragma unroll
                 for (int mt = 0; mt < 2; ++mt) {
-                    uint32_t ah[4], al[4];
                     // A column tig = class 8 ks + 2 tig (d0 / d2), column tig + 4 = class 8 ks + 2 tig + 1 (d1 / d3)
-                    split_tf32(z[mt][ks][0], ah[0], al[0]);
-                    split_tf32(z[mt][ks][2], ah[1], al[1]);
-                    split_tf32(z[mt][ks][1], ah[2], al[2]);
-                    split_tf32(z[mt][ks][3], ah[3], al[3]);
+                    split_tf32(z[mt][ks][0], ah[mt][0], al[mt][0]);
+                    split_tf32(z[mt][ks][2], ah[mt][1], al[mt][1]);
+                    split_tf32(z[mt][ks][1], ah[mt][2], al[mt][2]);
+                    split_tf32(z[mt][ks][3], ah[mt][3], al[mt][3]);
+                }
 #pragma unroll
-                    for (int nt = 0; nt < NC; ++nt) {
-                        const int w0 = (8 * ks + 2 * tig) * CP + 8 * nt + gid;
-                        mma_tf32x3(ds[mt][nt], ah, al, __float_as_uint(s_whi[w0]), __float_as_uint(s_whi[w0 + CP]),
-                                   __float_as_uint(s_wlo[w0]), __float_as_uint(s_wlo[w0 + CP]));
-                    }
+                for (int nt = 0; nt < NC; ++nt) {
+                    // B (8 x 8): b0 (tig, gid) = W[8 ks + 2 tig][8 nt + gid], b1 = W[8 ks + 2 tig + 1][..]:
+                    // rows 8 nt + gid, columns 8 ks + tig (+ 4) of the permuted W^T
+                    const int t0 = (8 * nt + lr) * KT + 8 * ks + 4 * lc;
+                    uint32_t bh0, bh1, bl0, bl1;
+                    ldsm_x2(s_thi + t0, bh0, bh1);
+                    ldsm_x2(s_tlo + t0, bl0, bl1);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) mma_tf32x3(ds[mt][nt], ah[mt], al[mt], bh0, bh1, bl0, bl1);
                 }
             }
 #pragma unroll
@@ -686,7 +724,7 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
                 for (int nt = 0; nt < NK; ++nt)
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        s_dz[(16 * mt + gid + 8 * (i >> 1)) * KP + 8 * nt + 2 * tig + (i & 1)] = z[mt][nt][i];
+                        s_dz[(8 * nt + 2 * tig + (i & 1)) * PP + 16 * mt + gid + 8 * (i >> 1)] = z[mt][nt][i];
             __syncwarp();
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
@@ -698,12 +736,11 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
                 }
 #pragma unroll
                 for (int mt = 0; mt < K / 16; ++mt) {
-                    const float *d0 = s_dz + (8 * ks + tig) * KP + 16 * mt + gid;
-                    uint32_t ah[4], al[4];
-                    split_tf32(d0[0], ah[0], al[0]);
-                    split_tf32(d0[8], ah[1], al[1]);
-                    split_tf32(d0[4 * KP], ah[2], al[2]);
-                    split_tf32(d0[4 * KP + 8], ah[3], al[3]);
+                    // A (16 x 8): rows = classes 16 mt .., columns = pixels 8 ks ..
+                    uint32_t ar[4], ah[4], al[4];
+                    ldsm_x4(s_dz + (16 * mt + lr + 8 * lc) * PP + 8 * ks + 4 * lh, ar);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) split_tf32(__uint_as_float(ar[i]), ah[i], al[i]);
 #pragma unroll
                     for (int nt = 0; nt < NC; ++nt)
                         mma_tf32x3(dw[mt][nt], ah, al, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
@@ -723,10 +760,10 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
             for (int i = 0; i < 4; ++i)
                 s_dz[(16 * mt + gid + 8 * (i >> 1)) * C + 8 * nt + 2 * tig + (i & 1)] = dw[mt][nt][i];
     __syncthreads();
-    const float *s_all = s_wlo + K * CP;
+    const float *s_all = s_dyn + L::W_FLOATS;
     for (int o = threadIdx.x; o < K * C; o += kLossThreads) {
         float s = 0.f;
-        for (int w = 0; w < kLossThreads / 32; ++w) s += s_all[w * 32 * KP + o];
+        for (int w = 0; w < kLossThreads / 32; ++w) s += s_all[w * L::WARP_FLOATS + o];
         a.dec_partials[(size_t)blockIdx.x * K * C + o] = s;
     }
 }

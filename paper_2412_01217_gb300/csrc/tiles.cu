@@ -28,6 +28,11 @@
 namespace sg {
 
 constexpr int kScanThreads = 256;
+// Widest digit of the tile sort.  Each pass scatters a block's instances over 2^digit runs
+// of the output; with 9-bit digits (512 runs per block) the partly written output lines no
+// longer stay in L2 and the pass reads and writes twice its bytes in DRAM (measured), so 17 or
+// 18 bits of tile id sort in three passes of 6 bits rather than two of 9 and 8.
+constexpr int kTileDigitBits = 8;
 
 __device__ __forceinline__ void block_range(int n, int G, int b, int &beg, int &end) {
     const int tiles = (n + kScanThreads - 1) / kScanThreads;
@@ -275,10 +280,12 @@ __global__ void slot_prefix_kernel(const uint2 *__restrict__ rect, const uint32_
 // s = c0 + t: its record is found by a binary search over the prefixes of the (at most 256)
 // records that can own the chunk, staged in shared memory; the row's footprint span gives
 // the contiguous run of kept tile columns.
-//   COUNT: adds up the kept tiles of the block's slots (kbsum[block]).
+//   COUNT: adds up the kept tiles of the block's slots (kbsum[block]); when the slots fit the
+//          slot cache (S <= capacity), also stores each slot's first kept tile and count.
 //   EMIT:  writes (global tile id, record) for the kept tiles, column by column, at
 //          kbsum[block] (the scanned block offset) plus the block's exclusive scan of the
-//          kept counts, i.e. in (record, row, column) order.
+//          kept counts, i.e. in (record, row, column) order; the runs come from the slot
+//          cache when the count pass filled it, else from the same span computation.
 template <bool EMIT>
 __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *__restrict__ geo,
                                  const float2 *__restrict__ ext, const uint32_t *__restrict__ rec,
@@ -286,6 +293,7 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
                                  const uint32_t *__restrict__ P, const uint32_t *__restrict__ first_rec, int Gc,
                                  int N, const sg_view *__restrict__ views, int n_views, int tile_w, int tile_h,
                                  uint32_t *__restrict__ kbsum, uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval,
+                                 uint32_t *__restrict__ slot_tf, uint32_t *__restrict__ slot_cnt,
                                  int capacity, uint32_t *__restrict__ status) {
     pdl_begin();
     __shared__ uint32_t s_P[kScanThreads];
@@ -298,6 +306,7 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
     const uint64_t per = slot_block_size(S, Gc);
     const uint64_t s0 = (uint64_t)blockIdx.x * per;
     const uint64_t s1 = min((uint64_t)S, s0 + per);
+    const bool cached = S <= (uint32_t)capacity;  // the slot cache holds every slot
     uint32_t kept = 0;
     uint32_t run = EMIT ? kbsum[blockIdx.x] : 0u;
     bool overflow = false;
@@ -317,6 +326,13 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
             }
             k = lo;
             orec = rec[ic + k];
+        }
+        if (EMIT && cached) {
+            if (c0 + threadIdx.x < s1) {
+                tfirst = __ldcs(slot_tf + s);
+                cnt = __ldcs(slot_cnt + s);
+            }
+        } else if (c0 + threadIdx.x < s1) {
             const uint2 rc = rect[orec];
             const int tx0 = (int)(rc.x & 0xffffu), tx1 = (int)(rc.y & 0xffffu);
             const int ty = (int)(rc.x >> 16) + (int)(s - s_P[k]);
@@ -333,6 +349,10 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
                 cnt = (uint32_t)(tx - tx_a);
             }
             tfirst = (uint32_t)vw.z + (uint32_t)ty * (uint32_t)vw.w + (uint32_t)tx_a;
+            if (!EMIT && cached) {
+                slot_tf[s] = tfirst;
+                slot_cnt[s] = cnt;
+            }
         }
         if (!EMIT) {
             kept += cnt;
@@ -553,17 +573,15 @@ __global__ void __launch_bounds__(kScanThreads, 4) rs_scatter_kernel(
 
 // Sorts n (device count, clamped to cap) pairs on bits [0, bits) from (kin, vin) into
 // (kout, vout) using (ktmp, vtmp) as ping-pong; kin/vin are not modified.  The bits are
-// split into the fewest passes of at most 9 bits (8-bit passes where that takes no more
-// passes: their blocks use less shared memory).
+// split into the fewest passes of at most max_bits (<= 9) bits, as evenly as possible.
 static void radix_sort(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                        uint32_t *ktmp, uint32_t *vtmp, const int *n_ptr, int cap, int bits,
-                       uint32_t *hist, uint32_t *totals, int G, cudaStream_t st) {
-    const int passes = (bits + 8) / 9;
-    const bool wide = passes < (bits + 7) / 8;  // 9-bit digits save a pass
+                       uint32_t *hist, uint32_t *totals, int G, cudaStream_t st, int max_bits) {
+    const int passes = (bits + max_bits - 1) / max_bits;
     const uint32_t *ks = kin, *vs = vin;
     int shift = 0;
     for (int p = 0; p < passes; ++p) {
-        const int nb = min(wide ? 9 : 8, bits - shift);
+        const int nb = (bits - shift + (passes - p) - 1) / (passes - p);
         const uint32_t mask = (1u << nb) - 1u;
         uint32_t *kd = ((passes - 1 - p) % 2 == 0) ? kout : ktmp;
         uint32_t *vd = ((passes - 1 - p) % 2 == 0) ? vout : vtmp;
@@ -697,7 +715,7 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     // runs on a grid of about 2048 elements per block for R / 4, between G / 4 and G.
     const int Gd = (int)std::min<int64_t>(G, std::max<int64_t>(G / 4, R / (4 * 2048)));
     radix_sort(w.dkey_in, w.dval_in, w.dkey_out, w.dval_out, w.dkey_tmp, w.dval_tmp, w.counts + 0,
-               (int)R, 32, w.hist, w.totals, Gd, st);
+               (int)R, 32, w.hist, w.totals, Gd, st, 8);
     // 3. emission in depth order (K -> lists->count)
     // The emission runs on a finer grid for large inputs (up to 4 G blocks, about one per 2048
     // records): its blocks own ranges of depth-sorted records, and the near (large) ones,
@@ -711,19 +729,20 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     const int Gc = 4 * G;  // blocks of the slot partition (each walks a few 256-slot chunks)
     launch_pdl(slot_prefix_kernel, Ge, kScanThreads, 0, st, rect, w.dval_out, w.counts + 0, w.bsum, Ge,
                w.counts + 2, Gc, w.slot0, w.first_rec);
-    // culling, evenly over the slots: kept counts, their offsets, emission
+    // culling, evenly over the slots: kept counts, their offsets, emission (the tile sort's
+    // ping-pong buffers, free until the sort, hold the slot cache)
     launch_pdl(cull_pass_kernel<false>, Gc, kScanThreads, 0, st, rect, geo, ext, w.dval_out, w.counts + 0,
                w.counts + 2, w.slot0, w.first_rec, Gc, N, views, n_views, tile_w, tile_h, w.kbsum,
-               (uint32_t *)nullptr, (uint32_t *)nullptr, lists->capacity, status);
+               (uint32_t *)nullptr, (uint32_t *)nullptr, w.tkey_tmp, w.tval_tmp, lists->capacity, status);
     launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.kbsum, Gc, lists->count);
     launch_pdl(cull_pass_kernel<true>, Gc, kScanThreads, 0, st, rect, geo, ext, w.dval_out, w.counts + 0,
                w.counts + 2, w.slot0, w.first_rec, Gc, N, views, n_views, tile_w, tile_h, w.kbsum,
-               w.tkey_in, w.tval_in, lists->capacity, status);
+               w.tkey_in, w.tval_in, w.tkey_tmp, w.tval_tmp, lists->capacity, status);
     // 4. stable sort by tile id
     int bits = 1;
     while ((1ll << bits) < (long long)n_tiles) ++bits;
     radix_sort(w.tkey_in, w.tval_in, lists->tile, lists->record, w.tkey_tmp, w.tval_tmp,
-               lists->count, lists->capacity, bits, w.hist, w.totals, G, st);
+               lists->count, lists->capacity, bits, w.hist, w.totals, G, st, kTileDigitBits);
     // 5. tile ranges
     launch_pdl(clamp_count_kernel, 1, 1, 0, st, lists->count, lists->capacity, w.counts + 1);
     launch_pdl(ranges_kernel, (n_tiles + kScanThreads - 1) / kScanThreads, kScanThreads, 0, st, lists->tile,
