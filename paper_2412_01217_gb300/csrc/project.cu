@@ -72,13 +72,14 @@ __device__ __forceinline__ float sym3(const float *S, int i, int j) {
 // Camera-space mean, Jacobian rows of T = J W and the clamp flags of one view-level.
 struct ViewGeom {
     float t[3];
+    DF tz;  // camera z in double-float (its rounded head is t[2])
     float T0[3], T1[3];
     float J00, J02, J11, J12;
     bool clx, cly;
 };
 
-__device__ __forceinline__ void view_geom(const sg_view &vw, const float mu[3], float fov_clamp,
-                                          ViewGeom &q) {
+// (limx, limy) = the Jacobian clamp fov_clamp W / (2 fx), fov_clamp H / (2 fy) of the view.
+__device__ __forceinline__ void view_geom(const sg_view &vw, const float mu[3], float2 lim, ViewGeom &q) {
     for (int i = 0; i < 2; ++i)
         q.t[i] = vw.R[3 * i] * mu[0] + vw.R[3 * i + 1] * mu[1] + vw.R[3 * i + 2] * mu[2] + vw.t[i];
     // camera z is also the depth ordering key of the tile lists (the order of the set N of
@@ -88,19 +89,19 @@ __device__ __forceinline__ void view_geom(const sg_view &vw, const float mu[3], 
     DF z = two_prod(vw.R[6], mu[0]);
     z = df_add(z, two_prod(vw.R[7], mu[1]));
     z = df_add(z, two_prod(vw.R[8], mu[2]));
-    q.t[2] = df_add_f(z, vw.t[2]).hi;
-    const float tz = q.t[2];
-    const float limx = fov_clamp * 0.5f * (float)vw.W / vw.fx;
-    const float limy = fov_clamp * 0.5f * (float)vw.H / vw.fy;
-    float rx = q.t[0] / tz, ry = q.t[1] / tz;
+    q.tz = df_add_f(z, vw.t[2]);
+    q.t[2] = q.tz.hi;
+    const float itz = 1.f / q.t[2];
+    const float limx = lim.x, limy = lim.y;
+    float rx = q.t[0] * itz, ry = q.t[1] * itz;
     q.clx = rx > limx || rx < -limx;
     q.cly = ry > limy || ry < -limy;
     rx = fminf(limx, fmaxf(-limx, rx));
     ry = fminf(limy, fmaxf(-limy, ry));
-    q.J00 = vw.fx / tz;
-    q.J11 = vw.fy / tz;
-    q.J02 = -vw.fx * rx / tz;  // = -fx * x~ / tz^2 with x~ = rx * tz
-    q.J12 = -vw.fy * ry / tz;
+    q.J00 = vw.fx * itz;
+    q.J11 = vw.fy * itz;
+    q.J02 = -q.J00 * rx;  // = -fx * x~ / tz^2 with x~ = rx * tz
+    q.J12 = -q.J11 * ry;
     for (int j = 0; j < 3; ++j) {
         q.T0[j] = q.J00 * vw.R[j] + q.J02 * vw.R[6 + j];
         q.T1[j] = q.J11 * vw.R[3 + j] + q.J12 * vw.R[6 + j];
@@ -199,6 +200,14 @@ __device__ __forceinline__ void sh_grad(float x, float y, float z, const float *
     }
 }
 
+// Jacobian clamp limits of every view-level (thread tid of nthr in the block).
+__device__ __forceinline__ void view_limits(const sg_view *s_views, int n_views, float fov_clamp, float2 *s_lim,
+                                            int tid, int nthr) {
+    for (int i = tid; i < n_views; i += nthr)
+        s_lim[i] = make_float2(fov_clamp * 0.5f * (float)s_views[i].W / s_views[i].fx,
+                               fov_clamp * 0.5f * (float)s_views[i].H / s_views[i].fy);
+}
+
 // Camera centre c = -R^T t of every view-level, next to the view table in shared memory
 // (thread tid of nthr in the block).
 __device__ __forceinline__ void view_centres(const sg_view *s_views, int n_views, float3 *s_centre,
@@ -223,13 +232,13 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     pdl_begin();
     __shared__ sg_view s_views[SG_MAX_VIEWS];
     __shared__ float3 s_centre[SG_MAX_VIEWS];
+    __shared__ float2 s_lim[SG_MAX_VIEWS];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
     for (int i = tid; i < n_views; i += nthr) s_views[i] = views[i];
     __syncthreads();
-    if constexpr (D > 0) {
-        view_centres(s_views, n_views, s_centre, tid, nthr);
-        __syncthreads();
-    }
+    view_limits(s_views, n_views, pc.fov_clamp, s_lim, tid, nthr);
+    if constexpr (D > 0) view_centres(s_views, n_views, s_centre, tid, nthr);
+    __syncthreads();
     // threadIdx.x picks the Gaussian, threadIdx.y the view-levels y, y + blockDim.y, ...
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N) return;
@@ -237,6 +246,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     GaussianFrame f;
     gaussian_frame(log_scale, quat[g], g, f);
     const float o = 1.f / (1.f + expf(-ologit[g]));
+    // alpha >= alpha_min needs sigma <= ln(o / alpha_min) (+ 1e-3 margin, see below)
+    const float thr = logf(o / pc.alpha_min) + 1e-3f;
     float shv[3 * K + 1], c0[3];
     if (D > 0 && sh) {
         for (int i = 0; i < 3 * K; ++i) shv[i] = sh[(size_t)3 * K * g + i];
@@ -259,7 +270,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
         const sg_view &vw = s_views[v];
         const size_t r = (size_t)v * N + g;
         ViewGeom q;
-        view_geom(vw, mu, pc.fov_clamp, q);
+        view_geom(vw, mu, s_lim[v], q);
         float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
         uint2 rc = make_uint2(0u, 0u);
         float2 e2 = make_float2(0.f, 0.f);
@@ -268,12 +279,13 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
             // the 2D mean in double-float: t = R mu + t_cw and (fx t_x / t_z + cx, ...)
             // carry ~1e-4 px of float32 error at 1200 px otherwise
             DF tdf[3];
-            for (int i = 0; i < 3; ++i) {
+            for (int i = 0; i < 2; ++i) {
                 DF acc = two_prod(vw.R[3 * i], mu[0]);
                 acc = df_add(acc, two_prod(vw.R[3 * i + 1], mu[1]));
                 acc = df_add(acc, two_prod(vw.R[3 * i + 2], mu[2]));
                 tdf[i] = df_add_f(acc, vw.t[i]);
             }
+            tdf[2] = q.tz;
             const DF udf = df_add_f(df_mul_f(df_div(tdf[0], tdf[2]), vw.fx), vw.cx);
             const DF vdf = df_add_f(df_mul_f(df_div(tdf[1], tdf[2]), vw.fy), vw.cy);
             const float u = udf.hi, vv = vdf.hi;
@@ -287,7 +299,6 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
                 // horizontal offset dx is dx^2/(2 s00): half extents (with float32 slack)
                 // (thr + 1e-3: at the boundary alpha is at least 0.1% below alpha_min, far
                 // beyond float32 rounding, so no pixel outside can pass the alpha test)
-                const float thr = logf(o / pc.alpha_min) + 1e-3f;
                 const float ex = sqrtf(2.f * thr * s00) * 1.002f + 0.01f;
                 const float ey = sqrtf(2.f * thr * s11) * 1.002f + 0.01f;
                 const float xmin = fmaxf(ceilf(u - ex), 0.f);
@@ -372,13 +383,13 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
     pdl_begin();
     __shared__ sg_view s_views[SG_MAX_VIEWS];
     __shared__ float3 s_centre[SG_MAX_VIEWS];
+    __shared__ float2 s_lim[SG_MAX_VIEWS];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
     for (int i = tid; i < n_views; i += nthr) s_views[i] = views[i];
     __syncthreads();
-    if constexpr (D > 0) {
-        view_centres(s_views, n_views, s_centre, tid, nthr);
-        __syncthreads();
-    }
+    view_limits(s_views, n_views, pc.fov_clamp, s_lim, tid, nthr);
+    if constexpr (D > 0) view_centres(s_views, n_views, s_centre, tid, nthr);
+    __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N) return;
     const float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
@@ -492,7 +503,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
             gmu[2] += (gdir[2] - radial * z) * rn;
         }
         ViewGeom q;
-        view_geom(vw, mu, pc.fov_clamp, q);
+        view_geom(vw, mu, s_lim[v], q);
         // conic = Sigma2D^{-1} of this view-level, recomputed in float32
         float ca, cb, cc;
         {
@@ -549,23 +560,25 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
         const float gJ02 = gT0[0] * W[6] + gT0[1] * W[7] + gT0[2] * W[8];
         const float gJ11 = gT1[0] * W[3] + gT1[1] * W[4] + gT1[2] * W[5];
         const float gJ12 = gT1[0] * W[6] + gT1[1] * W[7] + gT1[2] * W[8];
+        // (J00 = fx / tz, J11 = fy / tz: the divisions by tz are products with them)
+        const float itz = 1.f / tz;
         float gt0 = 0.f, gt1 = 0.f, gt2 = 0.f;
-        gt2 += -gJ00 * q.J00 / tz - gJ11 * q.J11 / tz;
+        gt2 += -(gJ00 * q.J00 + gJ11 * q.J11) * itz;
         if (!q.clx) {
-            gt0 += gJ02 * (-vw.fx / tz2);
-            gt2 += gJ02 * (2.f * vw.fx * q.t[0] / (tz2 * tz));
+            gt0 += gJ02 * (-q.J00 * itz);
+            gt2 += gJ02 * (2.f * q.J00 * q.t[0] * itz * itz);
         } else {
-            gt2 += gJ02 * (-q.J02 / tz);
+            gt2 += gJ02 * (-q.J02 * itz);
         }
         if (!q.cly) {
-            gt1 += gJ12 * (-vw.fy / tz2);
-            gt2 += gJ12 * (2.f * vw.fy * q.t[1] / (tz2 * tz));
+            gt1 += gJ12 * (-q.J11 * itz);
+            gt2 += gJ12 * (2.f * q.J11 * q.t[1] * itz * itz);
         } else {
-            gt2 += gJ12 * (-q.J12 / tz);
+            gt2 += gJ12 * (-q.J12 * itz);
         }
-        gt0 += gu * vw.fx / tz;
-        gt1 += gv * vw.fy / tz;
-        gt2 += -gu * vw.fx * q.t[0] / tz2 - gv * vw.fy * q.t[1] / tz2 + gd;
+        gt0 += gu * q.J00;
+        gt1 += gv * q.J11;
+        gt2 += -(gu * q.J00 * q.t[0] + gv * q.J11 * q.t[1]) * itz + gd;
         for (int j = 0; j < 3; ++j) gmu[j] += W[j] * gt0 + W[3 + j] * gt1 + W[6 + j] * gt2;
         go_total += go;
     }

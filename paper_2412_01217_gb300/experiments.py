@@ -107,7 +107,7 @@ def training_pairs(m, inserted, frames_dev_fn):
     return torch.cat(Xs), torch.cat(Ts)
 
 
-def run(quick=False, train_rooms=3, iters_per_kf=150, keyframes=8, epochs=4, workers=16, max_pairs=None, log=None):
+def run(quick=False, train_rooms=3, iters_per_kf=150, keyframes=8, epochs=16, workers=16, max_pairs=None, log=None):
     """The whole experiment; returns the result dict (see module docstring)."""
     import synthetic
     pool = None
@@ -181,7 +181,7 @@ def main():
     ap.add_argument("--train-rooms", type=int, default=3)
     ap.add_argument("--iters-per-kf", type=int, default=150)
     ap.add_argument("--keyframes", type=int, default=8)
-    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=16)
     ap.add_argument("--max-pairs", type=int, default=None, help="train on at most this many pairs")
     args = ap.parse_args()
     out = run(quick=args.quick, train_rooms=args.train_rooms, iters_per_kf=args.iters_per_kf,
