@@ -417,8 +417,8 @@ def cpu_baseline(g, cams, levels, target_s):
     full = a + b * nt
     return {"value": 1.0 / full, "unit": UNIT, "cores": oracle.num_threads(), "cpu_model": cpu_model(),
             "kind": "oracle",
-            "sample": f"FP64 oracle forward+backward on every {stride}th row/column of all {levels} levels "
-                      f"({n2} of {nt} pixels, {t2:.1f} s) and every {s1}th ({n1} pixels, {t1:.1f} s); "
+            "sample": f"FP64 oracle forward+backward on every {stride}-th row and column of all {levels} levels "
+                      f"({n2} of {nt} pixels, {t2:.1f} s) and every {s1}-th ({n1} pixels, {t1:.1f} s); "
                       f"fixed cost {a:.2f} s + {b * 1e3:.4f} ms per pixel, evaluated at all {nt} pixels",
             "seconds_per_iter": full}
 
@@ -456,7 +456,7 @@ def run_reference(args):
             "config": dict(W, l2="n/a (CPU)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "cpu_model": cpu_model(),
                              "kind": "oracle",
-                             "sample": f"every {stride}th row/column of all {L} levels per step ({ns} of {nt} px); "
+                             "sample": f"every {stride}-th row and column of all {L} levels per step ({ns} of {nt} px); "
                                        f"fixed cost {a:.2f} s per call (from samples at strides 96 and 48) "
                                        f"plus the sample's per-pixel time extrapolated to all pixels"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -288,8 +288,9 @@ size_t sg_loss_workspace_size(const sg_view *views_host, int32_t n_views, int32_
  * view-level v (device floats) and the gradient of sum_v total_v with respect to the
  * rendered images into dL (same packing as sg_images).  views_host: host copy of the
  * view table (sizes are needed to size the launch).  SSIM uses an 11x11 Gaussian window
- * (sigma 1.5) with zero padding.  status: device status word, required when
- * lcfg->check_numeric is set, else may be NULL. */
+ * (sigma 1.5) with zero padding.  workspace: sg_loss_workspace_size() bytes, 16-byte
+ * aligned.  status: device status word, required when lcfg->check_numeric is set, else may
+ * be NULL. */
 sg_status sg_pyramid_loss(const sg_images *rendered, const sg_targets *gt, const sg_view *views,
                           const sg_view *views_host, int32_t n_views, int32_t C,
                           const sg_loss_config *lcfg, float *terms, sg_images *dL,

@@ -332,6 +332,7 @@ sg_status sg_pyramid_loss(const sg_images *rendered, const sg_targets *gt, const
                           size_t workspace_bytes, uint32_t *status, sg_stream_t stream) {
     SG_TRY(check_loss_args(rendered, gt, views, views_host, n_views, C, lcfg, terms, dL, status));
     SG_REQUIRE(workspace, "workspace is NULL");
+    SG_REQUIRE(aligned16(workspace), "workspace must be 16-byte aligned");
     return launch_loss(rendered, gt, views, views_host, n_views, C, lcfg, terms, dL, workspace,
                        workspace_bytes, lcfg->check_numeric ? status : nullptr, (cudaStream_t)stream);
 }

@@ -826,11 +826,31 @@ __global__ void loss_finalize_kernel(FinalArgs a) {
             acc[3] += a.ssim_sem[2 * i + 1];
         }
     }
+    // the per-unit (depth L1, CE) sums: two units per 16-byte load, four loads in flight per
+    // thread, summed in a fixed order (a latency-bound chain of dependent adds otherwise)
     double b[2] = {0, 0};
-    for (int i = kPixSlots * a.lv.pix_blk_off[v] + threadIdx.x; i < kPixSlots * a.lv.pix_blk_off[v + 1];
-         i += kLossThreads) {
-        b[0] += a.pix[2 * i];
-        b[1] += a.pix[2 * i + 1];
+    {
+        const float4 *p4 = reinterpret_cast<const float4 *>(a.pix);
+        const int s1 = kPixSlots * a.lv.pix_blk_off[v + 1] / 2;
+        double c[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        int i = kPixSlots * a.lv.pix_blk_off[v] / 2 + threadIdx.x;
+        for (; i + 3 * kLossThreads < s1; i += 4 * kLossThreads) {
+            float4 q[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = p4[i + k * kLossThreads];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                c[k][0] += (double)q[k].x + (double)q[k].z;
+                c[k][1] += (double)q[k].y + (double)q[k].w;
+            }
+        }
+        for (; i < s1; i += kLossThreads) {
+            const float4 q = p4[i];
+            c[0][0] += (double)q.x + (double)q.z;
+            c[0][1] += (double)q.y + (double)q.w;
+        }
+        b[0] = (c[0][0] + c[1][0]) + (c[2][0] + c[3][0]);
+        b[1] = (c[0][1] + c[1][1]) + (c[2][1] + c[3][1]);
     }
     double r[4];
     for (int k = 0; k < 4; ++k) r[k] = block_sum_d(acc[k], s_w);

@@ -240,6 +240,31 @@ __device__ __forceinline__ bool span_meets(const RowSpan &rs, int X0, int X1) {
     return __fsub_rn((float)(X1 - rs.ui), rs.uf) >= rs.xl && __fsub_rn((float)(X0 - rs.ui), rs.uf) <= rs.xr;
 }
 
+// The kept tile columns [a, b) of a row within [tx0, tx1): the tiles whose pixel-centre
+// columns meet the span.  Both halves of span_meets are monotone in the column (the left test
+// turns true once, the right test turns false once; each is a correctly rounded subtraction
+// of an increasing integer), so a is the first column passing the left test and b the first
+// failing the right one.  Each is estimated from the span and then moved to the exact
+// boundary by the tests themselves (a step or two), so the result equals a walk over every
+// column of the rectangle.
+__device__ __forceinline__ void span_run(const RowSpan &rs, int tx0, int tx1, int tile_w, int W, int &a, int &b) {
+    auto left = [&](int tx) {  // the tile's last pixel-centre column reaches xl
+        return __fsub_rn((float)(min(tx * tile_w + tile_w - 1, W - 1) - rs.ui), rs.uf) >= rs.xl;
+    };
+    auto right = [&](int tx) {  // the tile's first pixel-centre column is within xr
+        return __fsub_rn((float)(tx * tile_w - rs.ui), rs.uf) <= rs.xr;
+    };
+    const float ca = ((float)rs.ui + rs.uf + rs.xl - (float)(tile_w - 1)) / (float)tile_w;
+    a = !(ca > (float)tx0) ? tx0 : (!(ca < (float)tx1) ? tx1 : (int)ceilf(ca));  // (NaN: tx0)
+    while (a > tx0 && left(a - 1)) --a;
+    while (a < tx1 && !left(a)) ++a;
+    const float cb = ((float)rs.ui + rs.uf + rs.xr) / (float)tile_w + 1.f;
+    b = !(cb > (float)a) ? a : (!(cb < (float)tx1) ? tx1 : (int)floorf(cb));
+    while (b > a && !right(b - 1)) --b;
+    while (b < tx1 && right(b)) ++b;
+    if (b < a) b = a;
+}
+
 // The (record, tile row) slots: the tile rows of every depth-sorted record's rectangle,
 // record after record; P[i] is the first slot of sorted record i.  The two culling passes
 // split the S slots evenly over their Gc blocks (a multiple of 256 slots each), so that the
@@ -297,6 +322,7 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
                                  int capacity, uint32_t *__restrict__ status) {
     pdl_begin();
     __shared__ uint32_t s_P[kScanThreads];
+    __shared__ uint32_t s_ex[EMIT ? kScanThreads : 1], s_tf[EMIT ? kScanThreads : 1], s_or[EMIT ? kScanThreads : 1];
     __shared__ int s_next;
     __shared__ int4 s_vw[SG_MAX_VIEWS];  // (W, H, tile_offset, tiles_x) of each view-level
     for (int v = threadIdx.x; v < n_views; v += kScanThreads)
@@ -339,14 +365,14 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
             const int4 vw = s_vw[orec / (uint32_t)N];
             const int Y0 = ty * tile_h;
             RowSpan rs;
+            tx_a = tx1;
             if (row_span(geo[2 * (size_t)orec], geo[2 * (size_t)orec + 1], ext[orec].x, Y0,
                          min(Y0 + tile_h - 1, vw.y - 1), rs)) {
-                // the kept columns are contiguous: skip to the first, count to the last
-                int tx = tx0;
-                while (tx < tx1 && !span_meets(rs, tx * tile_w, min(tx * tile_w + tile_w - 1, vw.x - 1))) ++tx;
-                tx_a = tx;
-                while (tx < tx1 && span_meets(rs, tx * tile_w, min(tx * tile_w + tile_w - 1, vw.x - 1))) ++tx;
-                cnt = (uint32_t)(tx - tx_a);
+                // the kept columns are contiguous
+                int tb;
+                span_run(rs, tx0, tx1, tile_w, vw.x, tx_a, tb);
+                cnt = (uint32_t)(tb - tx_a);
+                if (!cnt) tx_a = tx1;
             }
             tfirst = (uint32_t)vw.z + (uint32_t)ty * (uint32_t)vw.w + (uint32_t)tx_a;
             if (!EMIT && cached) {
@@ -357,13 +383,24 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
         if (!EMIT) {
             kept += cnt;
         } else {
+            // the chunk's instances [run, run + tot): consecutive threads write consecutive
+            // instances, each finding its slot by a binary search over the slots' offsets
             uint32_t tot;
             const uint32_t ex = block_exclusive_scan(cnt, tot);
-            for (uint32_t q = 0; q < cnt; ++q) {
-                const uint32_t g = run + ex + q;
+            s_ex[threadIdx.x] = ex;
+            s_tf[threadIdx.x] = tfirst;
+            s_or[threadIdx.x] = orec;
+            __syncthreads();
+            for (uint32_t o = threadIdx.x; o < tot; o += kScanThreads) {
+                int lo = 0, hi = kScanThreads - 1;  // the last slot t with s_ex[t] <= o
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_ex[mid] <= o) lo = mid; else hi = mid - 1;
+                }
+                const uint32_t g = run + o;
                 if (g < (uint32_t)capacity) {
-                    tkey[g] = tfirst + q;
-                    tval[g] = orec;
+                    tkey[g] = s_tf[lo] + (o - s_ex[lo]);
+                    tval[g] = s_or[lo];
                 } else {
                     overflow = true;
                 }

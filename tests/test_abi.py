@@ -143,3 +143,26 @@ def test_numeric_checks_need_a_status_word():
     assert b"status" in lib.sg_last_error()
     cfg.check_numeric = 2
     assert lib.sg_project_gaussians(C.byref(g), views, 1, C.byref(cfg), C.byref(proj), None, None) == 1
+
+
+def test_loss_workspace_must_be_16_byte_aligned():
+    """The loss reads its per-unit partial sums with 16-byte loads: a workspace that is not
+    16-byte aligned is refused on the host, before any launch."""
+    from paper_2412_01217_gb300 import _lib
+    from paper_2412_01217_gb300.splat import make_views
+    import synthetic
+    lib = _lib.load()
+    views, P, nt = make_views([synthetic.make_camera(64, 48, 60.0, 60.0, 31.5, 23.5)], 1)
+    buf = (C.c_float * 64)()
+    a = C.addressof(buf)
+    imgs = _lib.SgImages(a, a, a)
+    dl = _lib.SgImages(a, a, a)
+    gt = _lib.SgTargets(a, a, a, a)
+    lc = _lib.SgLossConfig()
+    lib.sg_default_loss_config(C.byref(lc))
+    lc.n_classes = 8
+    ws = (C.c_uint8 * 256)()
+    base = (C.addressof(ws) + 15) // 16 * 16
+    assert lib.sg_pyramid_loss(C.byref(imgs), C.byref(gt), views, views, 1, 8, C.byref(lc), a, C.byref(dl),
+                               base + 4, 128, None, None) == 1
+    assert b"16-byte" in lib.sg_last_error()

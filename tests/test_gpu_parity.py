@@ -225,7 +225,8 @@ def test_tile_lists_match_definition_single_view(cloud):
 
 def test_tile_lists_with_17_bit_tile_ids():
     """8 x 8 tiles of a 2400 x 1800 view: 67,500 tiles need 17-bit tile ids, so the tile sort
-    runs a 9-bit and an 8-bit radix pass (the width the batched workload's 92k tiles take)."""
+    runs three radix passes of 6, 6 and 5 bits (the width the batched workload's 92k tiles
+    take)."""
     g = synthetic.cloud_scene(1500, 8, seed=3)
     cam = f32_camera(synthetic.make_camera(2400, 1800, 2250.0, 2250.0, 1199.5, 899.5))
     r, p = make(g, [cam], tile_w=8, tile_h=8, capacity=1 << 20)
@@ -235,6 +236,30 @@ def test_tile_lists_with_17_bit_tile_ids():
     K, n_must, n_extra = lists_match_definition(r, g, [cam])
     assert K > 100000 and n_must > 0.5 * K
     assert lists_match_kernel_rule(r) == K
+
+
+def test_tile_lists_overflow_without_the_slot_cache():
+    """The emission pass reads each (record, tile row) slot's kept run from a cache that the
+    count pass fills when the slots fit the instance capacity, and recomputes the run
+    otherwise.  Each slot keeps one or more tiles, so the slots fit whenever the instances do;
+    with a capacity below the slot count the recomputing path runs, the overflow is reported
+    (SG_STATUS_CAPACITY) and the instance count is still the exact K."""
+    room, g, cams = room_small()
+    r, p = make(g, cams, levels=3)
+    r.project(p)
+    r.build_lists()
+    K = _gpu_lists(r)[0]
+    rows = r.rect.view(-1, 2).cpu().numpy().view(np.uint32)
+    ty0, ty1 = rows[:, 0] >> 16, rows[:, 1] >> 16
+    tx0, tx1 = rows[:, 0] & 0xFFFF, rows[:, 1] & 0xFFFF
+    slots = int(np.where((tx1 > tx0) & (ty1 > ty0), ty1.astype(np.int64) - ty0, 0).sum())
+    assert 0 < slots < K
+    r2, p2 = make(g, cams, levels=3, capacity=slots - 1)
+    r2.project(p2)
+    r2.build_lists()
+    torch.cuda.synchronize()
+    assert int(r2.status.item()) & 1  # SG_STATUS_CAPACITY
+    assert r2.instance_count() == K
 
 
 def room_small(n=20000, C=16, seed=4, ncam=2, W=320, H=180):
