@@ -340,15 +340,16 @@ __device__ __forceinline__ void moment_grads(const float (&M)[6], float U, float
     }
 }
 
-// One pixel per thread and C = 4 or 16: at most 64 registers (4 CTAs of 256 threads), so that
-// occupancy is set by shared memory rather than registers (the adjoint is latency-bound and
-// gains from warps).  These two widths fit 64 registers without spilling; the others would
-// spill, and with C >= 32 the staged entries hold occupancy lower than registers anyway.
+// One pixel per thread and C = 4 or 16: at most 72 registers, so that occupancy is set by
+// shared memory rather than registers (the adjoint is latency-bound and gains from warps):
+// 13 CTAs of an 8 x 8 tile fit both (13 x 64 threads x 72 registers); 64 registers spilled
+// nothing but measured 1 % slower, 80 cost a CTA.  The other widths keep the compiler's
+// choice (with C >= 32 the staged entries hold occupancy lower than registers anyway).
 template <int C, int PPT>
-__host__ __device__ constexpr int bwd_min_blocks() { return PPT == 1 && (C == 4 || C == 16) ? 4 : 1; }
+__host__ __device__ constexpr int bwd_max_regs() { return PPT == 1 && (C == 4 || C == 16) ? 72 : 255; }
 
 template <int C, int PPT>
-__global__ void __launch_bounds__(kMaxTileThreads, bwd_min_blocks<C, PPT>()) raster_bwd_kernel(RasterArgs a) {
+__global__ void __maxnreg__((bwd_max_regs<C, PPT>())) raster_bwd_kernel(RasterArgs a) {
     pdl_begin();
     constexpr int NF = 4 + C;                     // rgb(3) depth | sem(C)
     constexpr int NFP = padded_features<NF>();    // features padded to 8
