@@ -171,6 +171,15 @@ typedef struct {
                          bucket); the compositing kernels take tiles in this order, so the
                          longest lists start first and the short ones fill the tail.  NULL:
                          tiles in id order.                                             */
+    uint8_t *half;    /* K_cap or NULL: per instance, which halves of its tile the record's
+                         footprint may reach (bit 0: pixel rows [0, tile_h / 2), bit 1: the
+                         rest), by the culling rule applied to each half; a conservative
+                         superset (a half left out holds no pixel with alpha >= alpha_min).
+                         When given, a tile keeps a record if either half's rule keeps it
+                         (otherwise the rule runs once on the whole tile row), and the
+                         compositing adjoint of 8 x 8 tiles at one pixel per thread runs one
+                         warp per half tile, each staging only its half's entries: faster on
+                         long lists, slower to build.                                     */
 } sg_tile_lists;
 
 /* Rendered images (all view-levels packed, planar). */
@@ -261,9 +270,10 @@ size_t sg_tile_lists_workspace_size(int64_t n_records, int32_t capacity);
 
 /* Sec. III-C "sorted 2D gaussian primitives": instances (tile, record) of every non-culled
  * record, ordered by global tile id, then float32 depth bits, then record id (a stable,
- * deterministic radix sort), plus each tile's [start, end).  n_tiles: total tiles of the
- * views (sg_make_views).  If more than capacity instances arise, the surplus is dropped,
- * *count holds the required number and SG_STATUS_CAPACITY is set in *status. */
+ * deterministic radix sort), plus each tile's [start, end) and (when lists->half is given)
+ * each instance's half mask.  n_tiles: total tiles of the views (sg_make_views); with half
+ * masks N * n_views must be below 2^30.  If more than capacity instances arise, the surplus
+ * is dropped, *count holds the required number and SG_STATUS_CAPACITY is set in *status. */
 sg_status sg_build_tile_lists(const sg_projected *proj, int32_t N, int32_t n_views,
                               const sg_view *views, int32_t n_tiles, const sg_config *cfg,
                               sg_tile_lists *lists, void *workspace, size_t workspace_bytes,

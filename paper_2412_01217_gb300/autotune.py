@@ -3,11 +3,13 @@
 For each screen-tile shape (8x8, 16x8, 16x16, 32x8) one rasterizer is built (the tile
 lists depend on the tile shape); then the shared-memory batch depth (16, 32, 64, 128, 256) and
 the pixels per thread are varied in place, for the forward (1, 2 pixels per thread) and, with
-its own batch depth, for the backward (1, 2, 4).  Every candidate is timed with CUDA events over a few repetitions of the forward
-(render) and the backward on the caller's own Gaussians, cameras and targets; the
-configuration with the smallest forward + backward time wins.  The forward output does
-not depend on any of these choices (bit-identical across them, which the tests check), so
-the tuner changes speed only.  Results are cached in a JSON file keyed by GPU name and a
+its own batch depth, for the backward (1, 2, 4).  For 8x8 tiles the lists are also built
+with per-instance half masks, which run the adjoint at one pixel per thread one warp per
+half tile.  Every candidate is timed with CUDA events over a few repetitions of the tile-list
+build, the forward (render) and the backward on the caller's own Gaussians, cameras and
+targets; the configuration with the smallest lists + forward + backward time wins.  The
+forward output does not depend on any of these choices (bit-identical across them, which
+the tests check), so the tuner changes speed only.  Results are cached in a JSON file keyed by GPU name and a
 workload signature.
 """
 from __future__ import annotations
@@ -73,6 +75,8 @@ def autotune(params, cams, levels, gt, loss_cfg, base: RenderConfig | None = Non
         r.loss(gt, decoder=decoder, decoder_grad=dec_grad)
         torch.cuda.synchronize()
         r.check_status()
+        t_lists = _time(r.build_lists, reps)
+        table.append(dict(tile=f"{tw}x{th}", batch=0, kernel="lists", ppt=0, ms=t_lists))
         # forward: batch x pixels per thread
         fwd_best = None
         for batch in BATCHES:
@@ -101,13 +105,29 @@ def autotune(params, cams, levels, gt, loss_cfg, base: RenderConfig | None = Non
                 table.append(dict(tile=f"{tw}x{th}", batch=batch, kernel="bwd", ppt=ppt, ms=t))
                 if bwd_best is None or t < bwd_best[0]:
                     bwd_best = (t, batch, ppt)
-        total = fwd_best[0] + bwd_best[0]
+        total = t_lists + fwd_best[0] + bwd_best[0]
         if log:
-            log(f"tile {tw}x{th}: fwd {fwd_best[0]:.3f} ms (batch {fwd_best[1]}, ppt {fwd_best[2]}), "
-                f"bwd {bwd_best[0]:.3f} ms (batch {bwd_best[1]}, ppt {bwd_best[2]})")
+            log(f"tile {tw}x{th}: lists {t_lists:.3f} ms, fwd {fwd_best[0]:.3f} ms (batch {fwd_best[1]}, "
+                f"ppt {fwd_best[2]}), bwd {bwd_best[0]:.3f} ms (batch {bwd_best[1]}, ppt {bwd_best[2]})")
+        chosen_fwd = dict(tile_w=tw, tile_h=th, batch=fwd_best[1], pixels_per_thread=fwd_best[2])
         if best is None or total < best[0]:
-            best = (total, dict(tile_w=tw, tile_h=th, batch=fwd_best[1], pixels_per_thread=fwd_best[2],
-                                batch_bwd=bwd_best[1], pixels_per_thread_bwd=bwd_best[2]))
+            best = (total, dict(chosen_fwd, batch_bwd=bwd_best[1], pixels_per_thread_bwd=bwd_best[2],
+                                half_masks=False))
+        if (tw, th) == (8, 8):
+            # lists with half masks, and the adjoint's one-warp-per-half mode they enable
+            r.cfg = replace(cfg0, half_masks=True, batch=fwd_best[1], pixels_per_thread=fwd_best[2],
+                            pixels_per_thread_bwd=1)
+            r._ccfg = r.cfg.to_c()
+            t_lists_h = _time(r.build_lists, reps)
+            r.rasterize(params)
+            t_bwd_h = _time(lambda: r.backward(params, grads), reps)
+            table.append(dict(tile="8x8", batch=0, kernel="lists_half", ppt=0, ms=t_lists_h))
+            table.append(dict(tile="8x8", batch=0, kernel="bwd_half", ppt=1, ms=t_bwd_h))
+            total_h = t_lists_h + fwd_best[0] + t_bwd_h
+            if log:
+                log(f"tile 8x8 with half masks: lists {t_lists_h:.3f} ms, bwd {t_bwd_h:.3f} ms")
+            if total_h < best[0]:
+                best = (total_h, dict(chosen_fwd, batch_bwd=bwd_best[1], pixels_per_thread_bwd=1, half_masks=True))
         del r, grads
         torch.cuda.empty_cache()
     chosen = replace(base, **best[1])

@@ -24,6 +24,9 @@ struct RasterArgs {
     int *work_counter;
     int persistent;
     int ppt;  // pixels per thread (1, 2 or 4)
+    const uint8_t *half;  // per instance: halves of the tile the footprint may reach (or null);
+                          // given, the adjoint of 8 x 8 tiles at one pixel per thread runs
+                          // one warp per half tile
     // forward outputs / backward inputs
     float *img_rgb, *img_depth, *img_sem;
     float *T_final;
@@ -64,6 +67,7 @@ inline void fill_raster_args(RasterArgs &a, const sg_gaussians *g, const sg_proj
     a.work_counter = work_counter;
     a.persistent = cfg->persistent;
     a.ppt = cfg->pixels_per_thread;
+    a.half = lists->half;
 }
 
 sg_status launch_raster(RasterArgs &a, int C, bool backward, cudaStream_t st);

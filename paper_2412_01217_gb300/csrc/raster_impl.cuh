@@ -66,15 +66,49 @@ __device__ __forceinline__ void load_batch(const RasterArgs &a, int C, int list_
         if (s_rec) s_rec[j] = rec;
     }
 }
+// The same rows for one warp and at most 16 entries whose records are known (rec_of(j) is
+// row j's record): lanes 0-15 stage row j = lane's geometry, lanes 16-31 its features.
+template <int NF, class RecOf>
+__device__ __forceinline__ void stage_rows_warp(const RasterArgs &a, int C, RecOf rec_of, int cnt, int px0,
+                                                int py0, uint32_t rec_base, float4 *s_geo0, float4 *s_geo1,
+                                                float4 *s_geo2, float *s_feat, uint32_t *s_rec) {
+    const int lane = threadIdx.x & 31, j = lane & 15;
+    if (j >= cnt) return;
+    const uint32_t rec = rec_of(j);
+    float *f = s_feat + (size_t)j * NF;
+    if (lane < 16) {
+        const float4 g0 = a.geo[2 * (size_t)rec];
+        const float4 g1 = a.geo[2 * (size_t)rec + 1];
+        const float2 ex = a.ext[rec];
+        const uint32_t packed = __float_as_uint(g1.w);
+        const float uI = (float)((int)(short)(packed & 0xffffu) - px0);
+        const float vI = (float)((int)(short)(packed >> 16) - py0);
+        s_geo0[j] = make_float4(uI, vI, g0.x, g0.y);
+        s_geo1[j] = make_float4(g1.x, g1.y, g1.z, g0.w);
+        s_geo2[j] = make_float4(uI + g0.x, vI + g0.y, ex.x, ex.y);
+        s_rec[j] = rec;
+        f[3] = g0.z;  // depth (camera z of the mean, Eq. 8)
+    } else {
+        const uint32_t gi = rec - rec_base;
+        const size_t ci = a.col_rec ? rec : gi;
+        f[0] = a.rgb[3 * ci];
+        f[1] = a.rgb[3 * ci + 1];
+        f[2] = a.rgb[3 * ci + 2];
+        const float4 *s4 = reinterpret_cast<const float4 *>(a.sem + (size_t)(a.sem_rec ? rec : gi) * C);
+        float4 *f4 = reinterpret_cast<float4 *>(f + 4);
+#pragma unroll
+        for (int k = 0; k < (NF - 4) / 4; ++k) f4[k] = s4[k];
+    }
+}
 
 // Persistent work queue: work_counter[0] hands out slots, work_counter[1] counts the CTAs
 // that have drawn their terminating slot; the last of them zeroes both, so the queue is
 // ready for the next launch without a memset.
-__device__ __forceinline__ int next_item(const RasterArgs &a, int &s_item) {
+__device__ __forceinline__ int next_item(const RasterArgs &a, int n_items, int &s_item) {
     if (!a.persistent) return blockIdx.x;
     if (threadIdx.x == 0) {
         const int slot = atomicAdd(a.work_counter, 1);
-        if (slot >= a.n_tiles && atomicAdd(a.work_counter + 1, 1) == (int)gridDim.x - 1) {
+        if (slot >= n_items && atomicAdd(a.work_counter + 1, 1) == (int)gridDim.x - 1) {
             a.work_counter[0] = 0;
             a.work_counter[1] = 0;
         }
@@ -164,7 +198,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
     const float ln_amin = __logf(a.alpha_min);
     for (int iter = 0;; ++iter) {
         if (!a.persistent && iter > 0) break;
-        const int slot = next_item(a, s_item);
+        const int slot = next_item(a, a.n_tiles, s_item);
         if (slot >= a.n_tiles) break;
         const int item = a.order ? a.order[slot] : slot;  // tile id
         const TileInfo ti = tile_info(a, item);
@@ -281,6 +315,7 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
 // with w = alpha T and P = (1, X, Y, X^2, XY, Y^2) the pixel offsets from the warp centre.
 // The 2D-mean, conic and opacity gradients are linear in the moments (see moment_grads).
 constexpr int kChunk = 16;
+constexpr int kHalfQueue = kChunk + 32;  // half mode: list positions pending (< 16 + one 32-entry scan)
 
 template <int NPX>
 __host__ __device__ constexpr int chunk_pitch() { return NPX + 4; }  // 4 mod 32: conflict-free fragments
@@ -348,7 +383,7 @@ __device__ __forceinline__ void moment_grads(const float (&M)[6], float U, float
 template <int C, int PPT>
 __host__ __device__ constexpr int bwd_max_regs() { return PPT == 1 && (C == 4 || C == 16) ? 72 : 255; }
 
-template <int C, int PPT>
+template <int C, int PPT, bool HALF = false>
 __global__ void __maxnreg__((bwd_max_regs<C, PPT>())) raster_bwd_kernel(RasterArgs a) {
     pdl_begin();
     constexpr int NF = 4 + C;                     // rgb(3) depth | sem(C)
@@ -361,15 +396,27 @@ __global__ void __maxnreg__((bwd_max_regs<C, PPT>())) raster_bwd_kernel(RasterAr
     constexpr int GP = g_pitch<NF>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item, s_max_last;
-    const int batch = a.batch;
+    // Half mode (8 x 8 tiles, one pixel per thread, half masks given): a CTA is one warp that
+    // owns one half (8 x 4 pixels) of a tile; it walks the tile's list back to front, keeps
+    // the entries whose half mask holds its half in a queue, and stages and processes them
+    // 16 at a time, so its chunks hold only its own entries; no block barrier.  Otherwise the
+    // CTA's warps share each batch of the list, staged between two block barriers.
+    constexpr bool hm = HALF;
+    static_assert(!HALF || PPT == 1, "half mode runs one pixel per thread");
+    const int batch = hm ? kChunk : a.batch;
     float4 *s_geo0 = reinterpret_cast<float4 *>(smem_raw);
     float4 *s_geo1 = s_geo0 + batch;
     float4 *s_geo2 = s_geo1 + batch;
     float *s_feat = reinterpret_cast<float *>(s_geo2 + batch);
     uint32_t *s_rec = reinterpret_cast<uint32_t *>(s_feat + (size_t)batch * NF);
-    const int nthreads = a.tile_w * a.tile_h / PPT;
+    // half mode: the list position of each staged row, and the queue of pending entries
+    // (list position, record)
+    int *s_pos = reinterpret_cast<int *>(s_rec + batch);
+    int *s_q = s_pos + (hm ? kChunk : 0);
+    uint32_t *s_qr = reinterpret_cast<uint32_t *>(s_q + (hm ? kHalfQueue : 0));
+    const int nthreads = hm ? 32 : a.tile_w * a.tile_h / PPT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float *s_G = reinterpret_cast<float *>(s_rec + batch) + (size_t)warp * bwd_warp_floats<C, PPT>();
+    float *s_G = reinterpret_cast<float *>(s_qr + (hm ? kHalfQueue : 0)) + (size_t)warp * bwd_warp_floats<C, PPT>();
     float *s_gw = s_G + NPX * GP;     // per chunk row: gf, then overwritten with w = alpha T
     float *s_sg = s_gw + kChunk * WQ; // per chunk row: s = dL/dsigma
     const int gid = lane >> 2, tig = lane & 3;
@@ -385,12 +432,15 @@ __global__ void __maxnreg__((bwd_max_regs<C, PPT>())) raster_bwd_kernel(RasterAr
     const float P1a = gid == 2 ? 1.f : gid == 4 ? X0 : 0.f;
     const float P1b = gid == 2 ? 1.f : gid == 4 ? X1 : 0.f;
     const float P2 = gid == 5 ? 1.f : 0.f;
+    const int n_items = hm ? 2 * a.n_tiles : a.n_tiles;
     for (int iter = 0;; ++iter) {
         if (!a.persistent && iter > 0) break;
-        const int slot = next_item(a, s_item);
-        if (slot >= a.n_tiles) break;
-        const int item = a.order ? a.order[slot] : slot;  // tile id
-        const TileInfo ti = tile_info(a, item);
+        const int slot = next_item(a, n_items, s_item);
+        if (slot >= n_items) break;
+        const int tslot = hm ? slot >> 1 : slot, hf = hm ? slot & 1 : 0;
+        const int item = a.order ? a.order[tslot] : tslot;  // tile id
+        TileInfo ti = tile_info(a, item);
+        ti.py0 += hf * (a.tile_h / 2);  // half mode: this warp's half
         const sg_view &vw = *ti.vw;
         const int px = ti.px0 + wt.lx;
         const int2 range = a.ranges[item];
@@ -427,26 +477,14 @@ __global__ void __maxnreg__((bwd_max_regs<C, PPT>())) raster_bwd_kernel(RasterAr
             for (int f = 0; f < NF; f += 4) row[f / 4] = make_float4(g[f], g[f + 1], g[f + 2], g[f + 3]);
         }
         const int warp_last = __reduce_max_sync(SG_FULL_MASK, thread_last);
-        if (threadIdx.x == 0) s_max_last = 0;
-        __syncthreads();
-        if (lane == 0 && warp_last > 0) atomicMax(&s_max_last, warp_last);
-        __syncthreads();
-        const int max_last = s_max_last;
-        const int n_batches = (max_last + batch - 1) / batch;
-        for (int b = n_batches - 1; b >= 0; --b) {
-            const int b0 = b * batch;
-            const int cnt = min(batch, max_last - b0);
-            __syncthreads();
-            load_batch<NF>(a, C, range.x, b0, cnt, ti.px0, ti.py0, rec_base, s_geo0, s_geo1, s_geo2, s_feat,
-                           s_rec, nthreads);
-            __syncthreads();
-            const int jmax = min(cnt, warp_last - b0);  // warp-uniform
-            for (int jc0 = jmax > 0 ? (jmax - 1) & ~(kChunk - 1) : -kChunk; jc0 >= 0; jc0 -= kChunk) {
+        // One chunk of staged rows [jc0, jc0 + 16) (rows past jmax are left out), back to
+        // front; pos_of(j) is the list position of row j.
+        auto chunk = [&](const int jc0, const int jmax, auto pos_of) {
                 // entries of the chunk whose footprint reaches the warp (lane r tests entry jc0 + r)
                 bool cand = false;
                 if (lane < kChunk) cand = jc0 + lane < jmax && !wt.misses(s_geo2[jc0 + lane], s_geo1[jc0 + lane], ln_amin);
                 uint32_t cmask = __ballot_sync(SG_FULL_MASK, cand);
-                if (!cmask) continue;
+                if (!cmask) return;
                 // ---- gf = G F^T for the chunk (M = pixels, N = entries, K = features) ----
                 if constexpr (MT <= 2) {
                     // features outside, pixel tiles inside: every F fragment is split once
@@ -518,7 +556,7 @@ __global__ void __maxnreg__((bwd_max_regs<C, PPT>())) raster_bwd_kernel(RasterAr
                     const int j = jc0 + r;
                     const float4 g0 = s_geo0[j];
                     const float4 g1 = s_geo1[j];
-                    const int pos = b0 + j;
+                    const int pos = pos_of(j);
                     AlphaEval e[PPT];
                     bool hit[PPT];
                     bool any = false;
@@ -548,7 +586,7 @@ __global__ void __maxnreg__((bwd_max_regs<C, PPT>())) raster_bwd_kernel(RasterAr
                         s_sg[r * WQ + 32 * k + lane] = sg;
                     }
                 }
-                if (!mask) continue;  // (warp-uniform)
+                if (!mask) return;  // (warp-uniform)
                 __syncwarp();
                 // ---- dF = W G (M = entries, N = features, K = pixels), moments M = S P ----
                 const bool keep0 = (mask >> gid) & 1u, keep1 = (mask >> (gid + 8)) & 1u;
@@ -632,9 +670,70 @@ __global__ void __maxnreg__((bwd_max_regs<C, PPT>())) raster_bwd_kernel(RasterAr
                     }
                 }
                 __syncwarp();  // the chunk buffers are rewritten next
+        };
+        if (!hm) {
+            if (threadIdx.x == 0) s_max_last = 0;
+            __syncthreads();
+            if (lane == 0 && warp_last > 0) atomicMax(&s_max_last, warp_last);
+            __syncthreads();
+            const int max_last = s_max_last;
+            const int n_batches = (max_last + batch - 1) / batch;
+            for (int b = n_batches - 1; b >= 0; --b) {
+                const int b0 = b * batch;
+                const int cnt = min(batch, max_last - b0);
+                __syncthreads();
+                load_batch<NF>(a, C, range.x, b0, cnt, ti.px0, ti.py0, rec_base, s_geo0, s_geo1, s_geo2, s_feat,
+                               s_rec, nthreads);
+                __syncthreads();
+                const int jmax = min(cnt, warp_last - b0);  // warp-uniform
+                for (int jc0 = jmax > 0 ? (jmax - 1) & ~(kChunk - 1) : -kChunk; jc0 >= 0; jc0 -= kChunk)
+                    chunk(jc0, jmax, [b0](int j) { return b0 + j; });
             }
+            __syncthreads();
+        } else {
+            // list positions < warp_last whose half mask holds this half, in descending order:
+            // (s_q, s_qr)[0 .. qn) is the queue of (position, record), top the next position
+            // scanned (exclusive)
+            const uint32_t lt = (1u << lane) - 1u;
+            int top = warp_last, qn = 0;
+            for (;;) {
+                while (qn < kChunk && top > 0) {
+                    const int pos = top - 1 - lane;
+                    uint32_t rec = 0u;
+                    bool sel = false;
+                    if (pos >= 0) {
+                        rec = a.record[range.x + pos];
+                        sel = (a.half[range.x + pos] >> hf) & 1u;
+                    }
+                    const uint32_t bal = __ballot_sync(SG_FULL_MASK, sel);
+                    if (sel) {
+                        s_q[qn + __popc(bal & lt)] = pos;
+                        s_qr[qn + __popc(bal & lt)] = rec;
+                    }
+                    qn += __popc(bal);
+                    top = max(top - 32, 0);
+                    __syncwarp();
+                }
+                if (qn == 0) break;
+                const int c = min(kChunk, qn);
+                // rows 0 .. c-1 in ascending list position: row r is queue entry c - 1 - r
+                stage_rows_warp<NF>(a, C, [&](int j) { return s_qr[c - 1 - j]; }, c, ti.px0, ti.py0, rec_base, s_geo0,
+                                    s_geo1, s_geo2, s_feat, s_rec);
+                if (lane < c) s_pos[lane] = s_q[c - 1 - lane];
+                const int rest = qn - c;  // (< 32)
+                const int keep = lane < rest ? s_q[c + lane] : 0;
+                const uint32_t keep_rec = lane < rest ? s_qr[c + lane] : 0u;
+                __syncwarp();
+                if (lane < rest) {
+                    s_q[lane] = keep;
+                    s_qr[lane] = keep_rec;
+                }
+                qn = rest;
+                __syncwarp();
+                chunk(0, c, [s_pos](int j) { return s_pos[j]; });
+            }
+            __syncwarp();
         }
-        __syncthreads();
     }
 }
 
@@ -648,6 +747,13 @@ template <int C, int PPT>
 inline size_t bwd_smem(int batch, int threads) {
     return fwd_smem<C>(batch) + (size_t)batch * 4 + sizeof(float) * (threads / 32) * bwd_warp_floats<C, PPT>();
 }
+// half mode: one 16-entry chunk staged (+ its list positions), the (position, record) queue,
+// one warp
+template <int C>
+inline size_t bwd_half_smem() {
+    return fwd_smem<C>(kChunk) + (size_t)kChunk * 4 * 2 + (size_t)kHalfQueue * 4 * 2 +
+           sizeof(float) * bwd_warp_floats<C, 1>();
+}
 
 inline int resident_grid(const void *fn, int threads, size_t smem) {
     int dev = 0, sms = 0, per_sm = 0;
@@ -660,24 +766,33 @@ inline int resident_grid(const void *fn, int threads, size_t smem) {
 
 template <int C, int PPT>
 sg_status launch_raster_cp(RasterArgs &a, bool backward, cudaStream_t st) {
-    const int threads = a.tile_w * a.tile_h / PPT;
-    const size_t smem = backward ? bwd_smem<C, PPT>(a.batch, threads) : fwd_smem<C>(a.batch);
-    const void *fn = backward ? (const void *)raster_bwd_kernel<C, PPT> : (const void *)raster_fwd_kernel<C, PPT>;
+    // the adjoint of 8 x 8 tiles at one pixel per thread runs one warp per half tile when the
+    // lists carry half masks
+    const bool half = backward && a.half && PPT == 1 && a.tile_w == 8 && a.tile_h == 8;
+    const int threads = half ? 32 : a.tile_w * a.tile_h / PPT;
+    const int n_items = half ? 2 * a.n_tiles : a.n_tiles;
+    const size_t smem = half ? bwd_half_smem<C>() : backward ? bwd_smem<C, PPT>(a.batch, threads) : fwd_smem<C>(a.batch);
+    const void *fn = half       ? (const void *)raster_bwd_kernel<C, PPT, PPT == 1>
+                     : backward ? (const void *)raster_bwd_kernel<C, PPT>
+                                : (const void *)raster_fwd_kernel<C, PPT>;
     // opt in to the dynamic size whenever it grows: at 48 KB and just below, the kernel's
     // static shared variables alone take the total past the default limit
-    static size_t configured[2] = {0, 0};
-    if (configured[backward] < smem) {
+    static size_t configured[3] = {0, 0, 0};
+    const int which = half ? 2 : backward ? 1 : 0;
+    if (configured[which] < smem) {
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return check_launch("raster smem attribute");
-        configured[backward] = smem;
+        configured[which] = smem;
     }
-    int grid = a.n_tiles;
+    int grid = n_items;
     if (a.persistent) {
         grid = resident_grid(fn, threads, smem);
-        if (grid > a.n_tiles) grid = a.n_tiles;
+        if (grid > n_items) grid = n_items;
     }
     if (grid <= 0) return SG_OK;
-    if (backward)
+    if (half)
+        launch_pdl(raster_bwd_kernel<C, PPT, PPT == 1>, grid, threads, smem, st, a);
+    else if (backward)
         launch_pdl(raster_bwd_kernel<C, PPT>, grid, threads, smem, st, a);
     else
         launch_pdl(raster_fwd_kernel<C, PPT>, grid, threads, smem, st, a);

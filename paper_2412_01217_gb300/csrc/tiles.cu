@@ -265,6 +265,52 @@ __device__ __forceinline__ void span_run(const RowSpan &rs, int tx0, int tx1, in
     if (b < a) b = a;
 }
 
+// With half masks, the kept tiles [a, a + cnt) of a (record, tile row) slot and which halves
+// of each tile they may reach (without them the rule above runs once on the tile row's band
+// of pixel-centre rows [Y0, Y1]).  The band splits into a top half [Y0, Y0 + tile_h / 2)
+// and a bottom half (clamped to the image), the rule runs on each, and a tile is kept when
+// its columns meet either half's span.  The two runs [a0, b0), [a1, b1) of one convex
+// footprint overlap (their spans cover the whole band's span), so the kept tiles are the
+// contiguous run [a, b) = their hull.  half packs the runs relative to a, one byte each
+// (a0 - a, b0 - a, a1 - a, b1 - a), or is kHalfAll when the run is longer than 255 tiles
+// (every tile then marked as reaching both halves, a conservative superset).
+constexpr uint32_t kHalfAll = 0xffffffffu;
+struct SlotRun {
+    int a, cnt;
+    uint32_t half;
+};
+__device__ __forceinline__ SlotRun slot_run(const float4 g0, const float4 g1, float ex, int Y0, int Y1, int tile_h,
+                                            int tx0, int tx1, int tile_w, int W) {
+    RowSpan rs;
+    const int Yh = Y0 + tile_h / 2;
+    int a0 = tx1, b0 = tx1, a1 = tx1, b1 = tx1;
+    if (row_span(g0, g1, ex, Y0, min(Yh - 1, Y1), rs)) span_run(rs, tx0, tx1, tile_w, W, a0, b0);
+    if (Yh <= Y1 && row_span(g0, g1, ex, Yh, Y1, rs)) span_run(rs, tx0, tx1, tile_w, W, a1, b1);
+    const bool e0 = b0 <= a0, e1 = b1 <= a1;
+    SlotRun r;
+    if (e0 && e1) {
+        r.a = tx1;
+        r.cnt = 0;
+        r.half = 0u;
+        return r;
+    }
+    if (e0) a0 = b0 = a1;
+    if (e1) a1 = b1 = a0;
+    r.a = min(a0, a1);
+    r.cnt = max(b0, b1) - r.a;
+    r.half = r.cnt > 255 ? kHalfAll
+                         : (uint32_t)(a0 - r.a) | ((uint32_t)(b0 - r.a) << 8) | ((uint32_t)(a1 - r.a) << 16) |
+                               ((uint32_t)(b1 - r.a) << 24);
+    return r;
+}
+// Half mask (bit 0 top, bit 1 bottom) of the q-th tile of a slot's run.
+__device__ __forceinline__ uint32_t half_mask(uint32_t half, uint32_t q) {
+    if (half == kHalfAll) return 3u;
+    const uint32_t top = q >= (half & 0xffu) && q < ((half >> 8) & 0xffu);
+    const uint32_t bot = q >= ((half >> 16) & 0xffu) && q < (half >> 24);
+    return top | (bot << 1);
+}
+
 // The (record, tile row) slots: the tile rows of every depth-sorted record's rectangle,
 // record after record; P[i] is the first slot of sorted record i.  The two culling passes
 // split the S slots evenly over their Gc blocks (a multiple of 256 slots each), so that the
@@ -311,7 +357,9 @@ __global__ void slot_prefix_kernel(const uint2 *__restrict__ rect, const uint32_
 //          kbsum[block] (the scanned block offset) plus the block's exclusive scan of the
 //          kept counts, i.e. in (record, row, column) order; the runs come from the slot
 //          cache when the count pass filled it, else from the same span computation.
-template <bool EMIT>
+// HALVES: the rule runs per half tile row (slot_run) and the emitted records carry each
+// tile's half mask in bits 30-31.
+template <bool EMIT, bool HALVES>
 __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *__restrict__ geo,
                                  const float2 *__restrict__ ext, const uint32_t *__restrict__ rec,
                                  const int *__restrict__ m_ptr, const int *__restrict__ s_ptr,
@@ -319,10 +367,11 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
                                  int N, const sg_view *__restrict__ views, int n_views, int tile_w, int tile_h,
                                  uint32_t *__restrict__ kbsum, uint32_t *__restrict__ tkey, uint32_t *__restrict__ tval,
                                  uint32_t *__restrict__ slot_tf, uint32_t *__restrict__ slot_cnt,
-                                 int capacity, uint32_t *__restrict__ status) {
+                                 uint32_t *__restrict__ slot_half, int capacity, uint32_t *__restrict__ status) {
     pdl_begin();
     __shared__ uint32_t s_P[kScanThreads];
-    __shared__ uint32_t s_ex[EMIT ? kScanThreads : 1], s_tf[EMIT ? kScanThreads : 1], s_or[EMIT ? kScanThreads : 1];
+    __shared__ uint32_t s_ex[EMIT ? kScanThreads : 1], s_tf[EMIT ? kScanThreads : 1], s_or[EMIT ? kScanThreads : 1],
+        s_hf[EMIT && HALVES ? kScanThreads : 1];
     __shared__ int s_next;
     __shared__ int4 s_vw[SG_MAX_VIEWS];  // (W, H, tile_offset, tiles_x) of each view-level
     for (int v = threadIdx.x; v < n_views; v += kScanThreads)
@@ -342,8 +391,8 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
         s_P[threadIdx.x] = j < n ? P[j] : 0xffffffffu;
         __syncthreads();
         const uint32_t s = (uint32_t)(c0 + threadIdx.x);
-        uint32_t cnt = 0, orec = 0, tfirst = 0;
-        int tx_a = 0, k = 0;
+        uint32_t cnt = 0, orec = 0, tfirst = 0, half = 0;
+        int k = 0;
         if (c0 + threadIdx.x < s1) {
             int lo = 0, hi = kScanThreads - 1;  // the last k with s_P[k] <= s (s_P[0] <= c0)
             while (lo < hi) {
@@ -357,6 +406,7 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
             if (c0 + threadIdx.x < s1) {
                 tfirst = __ldcs(slot_tf + s);
                 cnt = __ldcs(slot_cnt + s);
+                if (HALVES) half = __ldcs(slot_half + s);
             }
         } else if (c0 + threadIdx.x < s1) {
             const uint2 rc = rect[orec];
@@ -364,20 +414,29 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
             const int ty = (int)(rc.x >> 16) + (int)(s - s_P[k]);
             const int4 vw = s_vw[orec / (uint32_t)N];
             const int Y0 = ty * tile_h;
-            RowSpan rs;
-            tx_a = tx1;
-            if (row_span(geo[2 * (size_t)orec], geo[2 * (size_t)orec + 1], ext[orec].x, Y0,
-                         min(Y0 + tile_h - 1, vw.y - 1), rs)) {
-                // the kept columns are contiguous
-                int tb;
-                span_run(rs, tx0, tx1, tile_w, vw.x, tx_a, tb);
-                cnt = (uint32_t)(tb - tx_a);
-                if (!cnt) tx_a = tx1;
+            const int Y1 = min(Y0 + tile_h - 1, vw.y - 1);
+            int tx_a = tx1;
+            if constexpr (HALVES) {
+                const SlotRun sr = slot_run(geo[2 * (size_t)orec], geo[2 * (size_t)orec + 1], ext[orec].x, Y0, Y1,
+                                            tile_h, tx0, tx1, tile_w, vw.x);
+                cnt = (uint32_t)sr.cnt;
+                half = sr.half;
+                tx_a = sr.a;
+            } else {
+                RowSpan rs;
+                if (row_span(geo[2 * (size_t)orec], geo[2 * (size_t)orec + 1], ext[orec].x, Y0, Y1, rs)) {
+                    // the kept columns are contiguous
+                    int tb;
+                    span_run(rs, tx0, tx1, tile_w, vw.x, tx_a, tb);
+                    cnt = (uint32_t)(tb - tx_a);
+                    if (!cnt) tx_a = tx1;
+                }
             }
             tfirst = (uint32_t)vw.z + (uint32_t)ty * (uint32_t)vw.w + (uint32_t)tx_a;
             if (!EMIT && cached) {
                 slot_tf[s] = tfirst;
                 slot_cnt[s] = cnt;
+                if (HALVES) slot_half[s] = half;
             }
         }
         if (!EMIT) {
@@ -390,6 +449,7 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
             s_ex[threadIdx.x] = ex;
             s_tf[threadIdx.x] = tfirst;
             s_or[threadIdx.x] = orec;
+            if (HALVES) s_hf[threadIdx.x] = half;
             __syncthreads();
             for (uint32_t o = threadIdx.x; o < tot; o += kScanThreads) {
                 int lo = 0, hi = kScanThreads - 1;  // the last slot t with s_ex[t] <= o
@@ -399,8 +459,10 @@ __global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *_
                 }
                 const uint32_t g = run + o;
                 if (g < (uint32_t)capacity) {
-                    tkey[g] = s_tf[lo] + (o - s_ex[lo]);
-                    tval[g] = s_or[lo];
+                    const uint32_t q = o - s_ex[lo];
+                    tkey[g] = s_tf[lo] + q;
+                    // (with halves, records are below 2^30: checked by the caller)
+                    tval[g] = HALVES ? s_or[lo] | (half_mask(s_hf[lo], q) << 30) : s_or[lo];
                 } else {
                     overflow = true;
                 }
@@ -509,11 +571,14 @@ __device__ __forceinline__ void bucket_exclusive_scan(const uint32_t (&v)[DPT], 
 template <int ND>
 __host__ __device__ constexpr int scatter_ipt() { return 12; }
 
-template <class Src, int ND>
+// SPLIT (the tile sort's last pass with half masks): bits 30-31 of each value go to half_out,
+// the rest to vout.
+template <class Src, int ND, bool SPLIT = false>
 __global__ void __launch_bounds__(kScanThreads, 4) rs_scatter_kernel(
     Src src, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ n_ptr, int cap, int shift, uint32_t mask,
-    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, int G) {
+    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, int G,
+    uint8_t *__restrict__ half_out) {
     pdl_begin();
     constexpr int kWarps = kScanThreads / 32;
     constexpr int DPT = ND / kScanThreads;  // digits per thread: tid * DPT + q
@@ -599,7 +664,13 @@ __global__ void __launch_bounds__(kScanThreads, 4) rs_scatter_kernel(
             const uint32_t d = (k >> shift) & mask;
             const uint32_t pos = run[d] + ((uint32_t)j - loc[d]);
             if (kout) kout[pos] = k;
-            vout[pos] = sval[j];
+            const uint32_t v = sval[j];
+            if (SPLIT) {
+                vout[pos] = v & 0x3fffffffu;
+                half_out[pos] = (uint8_t)(v >> 30);
+            } else {
+                vout[pos] = v;
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -613,7 +684,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) rs_scatter_kernel(
 // split into the fewest passes of at most max_bits (<= 9) bits, as evenly as possible.
 static void radix_sort(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                        uint32_t *ktmp, uint32_t *vtmp, const int *n_ptr, int cap, int bits,
-                       uint32_t *hist, uint32_t *totals, int G, cudaStream_t st, int max_bits) {
+                       uint32_t *hist, uint32_t *totals, int G, cudaStream_t st, int max_bits,
+                       bool split_last = false, uint8_t *half_out = nullptr) {
     const int passes = (bits + max_bits - 1) / max_bits;
     const uint32_t *ks = kin, *vs = vin;
     int shift = 0;
@@ -623,16 +695,25 @@ static void radix_sort(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
         uint32_t *kd = ((passes - 1 - p) % 2 == 0) ? kout : ktmp;
         uint32_t *vd = ((passes - 1 - p) % 2 == 0) ? vout : vtmp;
         const ArrayPairs src{ks, vs};
+        const bool split = split_last && half_out && p == passes - 1;
         if (nb > 8) {
             launch_pdl(rs_hist_kernel<ArrayPairs, 512>, G, kScanThreads, 0, st, src, n_ptr, cap, shift, mask, hist, G);
             launch_pdl(rs_digit_scan_kernel, 512, kScanThreads, 0, st, hist, totals, G);
-            launch_pdl(rs_scatter_kernel<ArrayPairs, 512>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap, shift, mask,
-                       hist, totals, G);
+            if (split)
+                launch_pdl(rs_scatter_kernel<ArrayPairs, 512, true>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap,
+                           shift, mask, hist, totals, G, half_out);
+            else
+                launch_pdl(rs_scatter_kernel<ArrayPairs, 512>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap, shift,
+                           mask, hist, totals, G, (uint8_t *)nullptr);
         } else {
             launch_pdl(rs_hist_kernel<ArrayPairs, 256>, G, kScanThreads, 0, st, src, n_ptr, cap, shift, mask, hist, G);
             launch_pdl(rs_digit_scan_kernel, 256, kScanThreads, 0, st, hist, totals, G);
-            launch_pdl(rs_scatter_kernel<ArrayPairs, 256>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap, shift, mask,
-                       hist, totals, G);
+            if (split)
+                launch_pdl(rs_scatter_kernel<ArrayPairs, 256, true>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap,
+                           shift, mask, hist, totals, G, half_out);
+            else
+                launch_pdl(rs_scatter_kernel<ArrayPairs, 256>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap, shift,
+                           mask, hist, totals, G, (uint8_t *)nullptr);
         }
         count_launches(3);
         ks = kd;
@@ -764,22 +845,25 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
                w.counts + 0, 0, w.bsum, Ge);
     launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.bsum, Ge, w.counts + 2);
     const int Gc = 4 * G;  // blocks of the slot partition (each walks a few 256-slot chunks)
+    const bool halves = lists->half != nullptr;  // per-instance half masks wanted
     launch_pdl(slot_prefix_kernel, Ge, kScanThreads, 0, st, rect, w.dval_out, w.counts + 0, w.bsum, Ge,
                w.counts + 2, Gc, w.slot0, w.first_rec);
     // culling, evenly over the slots: kept counts, their offsets, emission (the tile sort's
-    // ping-pong buffers, free until the sort, hold the slot cache)
-    launch_pdl(cull_pass_kernel<false>, Gc, kScanThreads, 0, st, rect, geo, ext, w.dval_out, w.counts + 0,
-               w.counts + 2, w.slot0, w.first_rec, Gc, N, views, n_views, tile_w, tile_h, w.kbsum,
-               (uint32_t *)nullptr, (uint32_t *)nullptr, w.tkey_tmp, w.tval_tmp, lists->capacity, status);
+    // ping-pong buffers and the output tile ids, all free until the sort, hold the slot cache)
+    const auto count_pass = halves ? cull_pass_kernel<false, true> : cull_pass_kernel<false, false>;
+    const auto emit_pass = halves ? cull_pass_kernel<true, true> : cull_pass_kernel<true, false>;
+    launch_pdl(count_pass, Gc, kScanThreads, 0, st, rect, geo, ext, w.dval_out, w.counts + 0, w.counts + 2, w.slot0,
+               w.first_rec, Gc, N, views, n_views, tile_w, tile_h, w.kbsum, (uint32_t *)nullptr,
+               (uint32_t *)nullptr, w.tkey_tmp, w.tval_tmp, lists->tile, lists->capacity, status);
     launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.kbsum, Gc, lists->count);
-    launch_pdl(cull_pass_kernel<true>, Gc, kScanThreads, 0, st, rect, geo, ext, w.dval_out, w.counts + 0,
-               w.counts + 2, w.slot0, w.first_rec, Gc, N, views, n_views, tile_w, tile_h, w.kbsum,
-               w.tkey_in, w.tval_in, w.tkey_tmp, w.tval_tmp, lists->capacity, status);
+    launch_pdl(emit_pass, Gc, kScanThreads, 0, st, rect, geo, ext, w.dval_out, w.counts + 0, w.counts + 2, w.slot0,
+               w.first_rec, Gc, N, views, n_views, tile_w, tile_h, w.kbsum, w.tkey_in, w.tval_in, w.tkey_tmp,
+               w.tval_tmp, lists->tile, lists->capacity, status);
     // 4. stable sort by tile id
     int bits = 1;
     while ((1ll << bits) < (long long)n_tiles) ++bits;
     radix_sort(w.tkey_in, w.tval_in, lists->tile, lists->record, w.tkey_tmp, w.tval_tmp,
-               lists->count, lists->capacity, bits, w.hist, w.totals, G, st, kTileDigitBits);
+               lists->count, lists->capacity, bits, w.hist, w.totals, G, st, kTileDigitBits, halves, lists->half);
     // 5. tile ranges
     launch_pdl(clamp_count_kernel, 1, 1, 0, st, lists->count, lists->capacity, w.counts + 1);
     launch_pdl(ranges_kernel, (n_tiles + kScanThreads - 1) / kScanThreads, kScanThreads, 0, st, lists->tile,
@@ -791,7 +875,7 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
         launch_pdl(rs_hist_kernel<TileLengthKeys, 256>, G, kScanThreads, 0, st, src, nullptr, n_tiles, 0, 63u, w.hist, G);
         launch_pdl(rs_digit_scan_kernel, 256, kScanThreads, 0, st, w.hist, w.totals, G);
         launch_pdl(rs_scatter_kernel<TileLengthKeys, 256>, G, kScanThreads, 0, st, src, nullptr, reinterpret_cast<uint32_t *>(lists->order),
-                                                      nullptr, n_tiles, 0, 63u, w.hist, w.totals, G);
+                                                      nullptr, n_tiles, 0, 63u, w.hist, w.totals, G, (uint8_t *)nullptr);
         count_launches(3);
     }
     return check_launch("build_tile_lists");

@@ -97,3 +97,34 @@ def records_f32(pr, cam, T):
     rects = np.zeros((len(u), 4), np.int64)
     rects[ok] = np.stack([x0[ok] // T, y0[ok] // T, x1[ok] // T + 1, y1[ok] // T + 1], 1)
     return geo, np.stack([ex, ey], 1).astype(np.float32), rects
+
+
+def tile_halves_reach(geo, ext, X0, X1, Y0, Y1, tile_h):
+    """The kernels' rule applied to the two halves of each tile: the pixel-centre rows
+    [Y0, Y0 + tile_h / 2) and [Y0 + tile_h / 2, Y1] (the second empty when the image ends
+    first).  Returns (top, bottom) bool arrays."""
+    Y0, Y1 = np.asarray(Y0, np.int64), np.asarray(Y1, np.int64)
+    Yh = Y0 + tile_h // 2
+    top = tile_reaches_alpha_min(geo, ext, X0, X1, Y0, np.minimum(Yh - 1, Y1))
+    has_bottom = Yh <= Y1
+    bottom = has_bottom & tile_reaches_alpha_min(geo, ext, X0, X1, np.minimum(Yh, Y1), Y1)
+    return top, bottom
+
+
+def kept_and_masks(recs, tx, ty, top, bottom):
+    """Per (record, tile row) the kernels keep the hull of the tiles either half reaches
+    (the two halves' runs overlap for one convex footprint, so this is their union) and mark
+    each kept tile's halves: top | bottom << 1, or 3 on every tile of a run longer than 255
+    tiles.  Returns (keep, mask) over the given (record, tile) pairs."""
+    recs, tx, ty = (np.asarray(a, np.int64) for a in (recs, tx, ty))
+    reach = np.asarray(top, bool) | np.asarray(bottom, bool)
+    key = recs * (1 << 20) + ty
+    groups, inv = np.unique(key, return_inverse=True)
+    lo = np.full(len(groups), np.iinfo(np.int64).max)
+    hi = np.full(len(groups), np.iinfo(np.int64).min)
+    np.minimum.at(lo, inv[reach], tx[reach])
+    np.maximum.at(hi, inv[reach], tx[reach])
+    keep = (tx >= lo[inv]) & (tx <= hi[inv])
+    mask = np.asarray(top, np.int64) | (np.asarray(bottom, np.int64) << 1)
+    mask = np.where(hi[inv] - lo[inv] + 1 > 255, 3, mask)
+    return keep, mask

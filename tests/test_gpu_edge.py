@@ -58,22 +58,27 @@ def parity_all_views(g, cams, levels, seed=0, **cfg):
     return r, got
 
 
-@pytest.mark.parametrize("tile, batch, batch_bwd, ppt, ppt_bwd", [((16, 16), 128, 0, 1, 2), ((8, 8), 64, 16, 1, 1),
-                                                                  ((32, 8), 256, 32, 2, 1), ((16, 8), 32, 0, 2, 2)])
-def test_ragged_image_sizes_every_tile_shape(tile, batch, batch_bwd, ppt, ppt_bwd):
+@pytest.mark.parametrize("tile, batch, batch_bwd, ppt, ppt_bwd, half", [((16, 16), 128, 0, 1, 2, False),
+                                                                        ((8, 8), 64, 16, 1, 1, False),
+                                                                        ((8, 8), 64, 16, 1, 1, True),
+                                                                        ((32, 8), 256, 32, 2, 1, False),
+                                                                        ((16, 8), 32, 0, 2, 2, False)])
+def test_ragged_image_sizes_every_tile_shape(tile, batch, batch_bwd, ppt, ppt_bwd, half):
     """157 x 91 with 3 levels (157x91, 78x45, 39x22): no dimension is a multiple of any tile
-    side, so every view-level ends in partial tiles."""
+    side, so every view-level ends in partial tiles (with half masks: tiles whose bottom half
+    lies below the image, too)."""
     g = synthetic.cloud_scene(2500, 8, seed=21)
     cam = f32_camera(synthetic.make_camera(157, 91, 140.0, 140.0, 77.7, 44.6))
     parity_all_views(g, [cam], 3, tile_w=tile[0], tile_h=tile[1], batch=batch, batch_bwd=batch_bwd,
-                     pixels_per_thread=ppt, pixels_per_thread_bwd=ppt_bwd)
+                     pixels_per_thread=ppt, pixels_per_thread_bwd=ppt_bwd, half_masks=half)
 
 
-@pytest.mark.parametrize("C", [4, 32])
-def test_semantic_widths_4_and_32(C):
+@pytest.mark.parametrize("C, half", [(4, False), (32, False), (4, True), (32, True)])
+def test_semantic_widths_4_and_32(C, half):
     g = synthetic.cloud_scene(2000, C, seed=22)
     cam = f32_camera(synthetic.cloud_camera())
-    parity_all_views(g, [cam], 2)
+    kw = dict(tile_w=8, tile_h=8, pixels_per_thread_bwd=1, half_masks=True) if half else {}
+    parity_all_views(g, [cam], 2, **kw)
 
 
 def test_maximum_view_levels():

@@ -17,7 +17,7 @@ import oracle
 import synthetic
 from helpers import (ALPHA_TOL, T_TOL, AMBIGUOUS, AMBIGUOUS_GRAD, FWD_ABS, FWD_REL, MAX_MASKED, check_close, check_grads,
                      ref_render, unambiguous)
-from kernel_rules import tile_reaches_alpha_min
+from kernel_rules import kept_and_masks, tile_halves_reach, tile_reaches_alpha_min
 
 pytestmark = pytest.mark.gpu
 
@@ -169,6 +169,18 @@ def lists_match_definition(r, g, ocams):
         got = oracle.tile_reach(pr, oc, gi, gtx, gty, tw, th)
         far = ~(got["sigma_min"] <= got["thr"] + 2e-3 + 1e-4 * np.abs(got["thr"]))
         assert not far.any(), f"view {v}: {int(far.sum())} listed pairs the footprint does not reach"
+        # half masks: a half of the tile holding a pixel centre where alpha reaches alpha_min
+        # (FP64) is marked
+        hm = r.half[:K].cpu().numpy()[sel] if r.cfg.half_masks else np.full(len(gi), 3, np.uint8)
+        for h in (0, 1):
+            hty = 2 * gty + h
+            inside = hty * (th // 2) < oc["H"]
+            if not inside.any():
+                continue
+            hr = oracle.tile_reach(pr, oc, gi[inside], gtx[inside], hty[inside], tw, th // 2)
+            need = hr["alpha"] >= amin * (1 + ALPHA_TOL)
+            bit = ((hm[inside] >> h) & 1) == 1
+            assert np.all(bit | ~need), f"view {v}: {int((need & ~bit).sum())} reached halves unmarked"
         n_must += int(must.sum())
         n_extra += int((got["alpha"] < amin).sum())
     same = tiles[1:] == tiles[:-1]
@@ -198,24 +210,45 @@ def lists_match_kernel_rule(r):
     Wv = np.array([r.views_host[v].W for v in range(r.V)])
     Hv = np.array([r.views_host[v].H for v in range(r.V)])
 
-    def keep(recs_, tx_, ty_):
+    half = r.cfg.half_masks
+
+    def band(recs_, tx_, ty_):
         v = recs_ // r.N
         X0, Y0 = tx_ * tw, ty_ * th
-        return tile_reaches_alpha_min(geo[recs_], ext[recs_], X0, np.minimum(X0 + tw - 1, Wv[v] - 1),
-                                      Y0, np.minimum(Y0 + th - 1, Hv[v] - 1))
+        return (geo[recs_], ext[recs_], X0, np.minimum(X0 + tw - 1, Wv[v] - 1), Y0,
+                np.minimum(Y0 + th - 1, Hv[v] - 1))
+
+    def halves(recs_, tx_, ty_):
+        return tile_halves_reach(*band(recs_, tx_, ty_), th)
+
+    def keep(recs_, tx_, ty_):
+        # without half masks the rule runs on the tile row's whole band; with them, a tile
+        # is kept when either half's rule keeps it
+        if not half:
+            return tile_reaches_alpha_min(*band(recs_, tx_, ty_))
+        return kept_and_masks(recs_, tx_, ty_, *halves(recs_, tx_, ty_))[0]
 
     rt, rr, rg = oracle.tile_lists(rects, depth, tx, to, r.n_tiles, r.N, keep=keep)
     assert K == len(rt)
     assert np.array_equal(tiles, rt)
     assert np.array_equal(recs, rr)
     assert np.array_equal(ranges, rg)
+    if not half:
+        return K
+    # each instance's half mask, from the same rule (a run's length is its kept tiles' count)
+    v = rr // r.N
+    local = rt - np.asarray(to, np.int64)[v]
+    ltx, lty = local % np.asarray(tx, np.int64)[v], local // np.asarray(tx, np.int64)[v]
+    _, want = kept_and_masks(rr, ltx, lty, *halves(rr, ltx, lty))
+    got = r.half[:K].cpu().numpy().astype(np.int64)
+    assert np.array_equal(got, want), f"{int((got != want).sum())} of {K} half masks differ"
     return K
 
 
 def test_tile_lists_match_definition_single_view(cloud):
     g, cam = cloud
-    for tw, th in ((16, 16), (8, 8), (32, 8)):
-        r, p = make(g, [cam], tile_w=tw, tile_h=th)
+    for tw, th, half in ((16, 16, False), (8, 8, False), (32, 8, False), (8, 8, True), (16, 16, True)):
+        r, p = make(g, [cam], tile_w=tw, tile_h=th, half_masks=half)
         r.project(p)
         r.build_lists()
         K, n_must, n_extra = lists_match_definition(r, g, [cam])
@@ -223,13 +256,14 @@ def test_tile_lists_match_definition_single_view(cloud):
         assert lists_match_kernel_rule(r) == K
 
 
-def test_tile_lists_with_17_bit_tile_ids():
+@pytest.mark.parametrize("half", [False, True])
+def test_tile_lists_with_17_bit_tile_ids(half):
     """8 x 8 tiles of a 2400 x 1800 view: 67,500 tiles need 17-bit tile ids, so the tile sort
     runs three radix passes of 6, 6 and 5 bits (the width the batched workload's 92k tiles
-    take)."""
+    take); with half masks the last pass splits them from the records."""
     g = synthetic.cloud_scene(1500, 8, seed=3)
     cam = f32_camera(synthetic.make_camera(2400, 1800, 2250.0, 2250.0, 1199.5, 899.5))
-    r, p = make(g, [cam], tile_w=8, tile_h=8, capacity=1 << 20)
+    r, p = make(g, [cam], tile_w=8, tile_h=8, capacity=1 << 20, half_masks=half)
     assert r.n_tiles == 300 * 225 and r.n_tiles > 1 << 16
     r.project(p)
     r.build_lists()
@@ -238,14 +272,15 @@ def test_tile_lists_with_17_bit_tile_ids():
     assert lists_match_kernel_rule(r) == K
 
 
-def test_tile_lists_overflow_without_the_slot_cache():
+@pytest.mark.parametrize("half", [False, True])
+def test_tile_lists_overflow_without_the_slot_cache(half):
     """The emission pass reads each (record, tile row) slot's kept run from a cache that the
     count pass fills when the slots fit the instance capacity, and recomputes the run
     otherwise.  Each slot keeps one or more tiles, so the slots fit whenever the instances do;
     with a capacity below the slot count the recomputing path runs, the overflow is reported
     (SG_STATUS_CAPACITY) and the instance count is still the exact K."""
     room, g, cams = room_small()
-    r, p = make(g, cams, levels=3)
+    r, p = make(g, cams, levels=3, tile_w=8, tile_h=8, half_masks=half)
     r.project(p)
     r.build_lists()
     K = _gpu_lists(r)[0]
@@ -254,7 +289,7 @@ def test_tile_lists_overflow_without_the_slot_cache():
     tx0, tx1 = rows[:, 0] & 0xFFFF, rows[:, 1] & 0xFFFF
     slots = int(np.where((tx1 > tx0) & (ty1 > ty0), ty1.astype(np.int64) - ty0, 0).sum())
     assert 0 < slots < K
-    r2, p2 = make(g, cams, levels=3, capacity=slots - 1)
+    r2, p2 = make(g, cams, levels=3, capacity=slots - 1, tile_w=8, tile_h=8, half_masks=half)
     r2.project(p2)
     r2.build_lists()
     torch.cuda.synchronize()
@@ -270,9 +305,10 @@ def room_small(n=20000, C=16, seed=4, ncam=2, W=320, H=180):
     return room, g, cams
 
 
-def test_tile_lists_match_definition_pyramid_multi_view():
+@pytest.mark.parametrize("tile, half", [((16, 16), False), ((8, 8), True)])
+def test_tile_lists_match_definition_pyramid_multi_view(tile, half):
     room, g, cams = room_small()
-    r, p = make(g, cams, levels=3)
+    r, p = make(g, cams, levels=3, tile_w=tile[0], tile_h=tile[1], half_masks=half)
     r.project(p)
     r.build_lists()
     K, n_must, n_extra = lists_match_definition(r, g, oracle_cams(cams, 3))
@@ -309,11 +345,17 @@ def test_forward_bitwise_identical_across_tiles_batches_and_runs(cloud):
             assert np.array_equal(im[k], base[k]), (k, tw, th, batch, pers, ppt)
 
 
-@pytest.mark.parametrize("ppt, batch_bwd, isotropic", [(1, 0, False), (2, 0, False), (4, 0, False), (1, 16, False),
-                                                     (2, 64, False), (1, 0, True)])
-def test_backward_matches_oracle_cloud(cloud, ppt, batch_bwd, isotropic):
+@pytest.mark.parametrize("ppt, batch_bwd, isotropic, tile", [(1, 0, False, "16x16"), (2, 0, False, "16x16"),
+                                                           (4, 0, False, "16x16"), (1, 16, False, "16x16"),
+                                                           (2, 64, False, "16x16"), (1, 0, True, "16x16"),
+                                                           (1, 16, False, "8x8"), (1, 16, False, "8x8-half"),
+                                                           (1, 0, True, "8x8-half")])
+def test_backward_matches_oracle_cloud(cloud, ppt, batch_bwd, isotropic, tile):
+    """8x8-half: lists with half masks, so the adjoint runs one warp per half tile."""
     g, cam = cloud
-    r, p = make(g, [cam], pixels_per_thread_bwd=ppt, batch_bwd=batch_bwd, isotropic=isotropic)
+    tw, th = (int(x) for x in tile.split("-")[0].split("x"))
+    r, p = make(g, [cam], pixels_per_thread_bwd=ppt, batch_bwd=batch_bwd, isotropic=isotropic, tile_w=tw,
+                tile_h=th, half_masks=tile.endswith("half"))
     r.forward(p)
     ocfg = dict(isotropic=int(isotropic))
     ref_f = ref_render(g, cam, ocfg)
@@ -422,13 +464,15 @@ def test_loss_matches_oracle(mode):
         check_close("dL/ddecoder", dgrad.cpu().numpy(), dec_ref_total, 1e-4, 1e-6)
 
 
-@pytest.mark.parametrize("isotropic", [False, True])
-def test_multiview_pyramid_forward_backward_matches_oracle(isotropic):
+@pytest.mark.parametrize("isotropic, half", [(False, False), (True, False), (False, True)])
+def test_multiview_pyramid_forward_backward_matches_oracle(isotropic, half):
     """Two keyframes x three levels rendered in ONE persistent launch: every pixel of
     every view-level against the oracle, and all parameter gradients; also with the Eq. 2
-    isotropic projection, whose radius f r / d takes each level's own focal length."""
+    isotropic projection, whose radius f r / d takes each level's own focal length, and with
+    8x8 tiles carrying half masks (the adjoint one warp per half tile)."""
     room, g, cams = room_small(n=6000, ncam=2, W=160, H=96)
-    r, p = make(g, cams, levels=3, isotropic=isotropic)
+    kw = dict(tile_w=8, tile_h=8, pixels_per_thread_bwd=1, half_masks=True) if half else {}
+    r, p = make(g, cams, levels=3, isotropic=isotropic, **kw)
     r.forward(p)
     ocams = oracle_cams(cams, 3)
     ocfg = dict(isotropic=int(isotropic))

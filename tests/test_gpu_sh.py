@@ -81,10 +81,14 @@ def test_semantic_sh_forward_matches_oracle(degree, colour, semantic):
 
 @pytest.mark.parametrize("degree, ppt, colour, semantic", [(1, 1, True, False), (2, 2, True, False), (3, 1, True, False),
                                                            (3, 4, True, False), (2, 1, False, True),
-                                                           (1, 2, True, True), (3, 1, True, True)])
+                                                           (1, 2, True, True), (3, 1, True, True), (2, 0, True, True)])
 def test_sh_backward_matches_oracle(degree, ppt, colour, semantic):
+    """ppt 0: 8x8 tiles with half masks (the adjoint one warp per half tile, one pixel per
+    thread)."""
     g, cam = sh_cloud(degree, seed=degree, colour=colour, semantic=semantic)
-    r, p = make(g, [cam], pixels_per_thread_bwd=ppt)
+    kw = dict(tile_w=8, tile_h=8, pixels_per_thread_bwd=1, half_masks=True) if ppt == 0 else \
+        dict(pixels_per_thread_bwd=ppt)
+    r, p = make(g, [cam], **kw)
     r.forward(p)
     ref_f = ref_render(g, cam)
     H, W = cam["H"], cam["W"]
