@@ -163,7 +163,8 @@ typedef struct {
 typedef struct {
     int32_t capacity; /* K_cap: instances the arrays below can hold                      */
     uint32_t *tile;   /* K_cap: global tile id of each instance, ascending               */
-    uint32_t *record; /* K_cap: record id v*N+g; within a tile by (depth, record id)     */
+    uint32_t *record; /* K_cap: record id v*N+g; within a tile by (depth, record id)
+                         (with half_masks, plus the mask in bits 30-31)                  */
     int32_t *ranges;  /* n_tiles x 2: [start, end) of each tile's instances              */
     int32_t *count;   /* device scalar: K = instances emitted (may exceed capacity)      */
     int32_t *order;   /* n_tiles or NULL: every tile id once, by descending instance count
@@ -171,15 +172,17 @@ typedef struct {
                          bucket); the compositing kernels take tiles in this order, so the
                          longest lists start first and the short ones fill the tail.  NULL:
                          tiles in id order.                                             */
-    uint8_t *half;    /* K_cap or NULL: per instance, which halves of its tile the record's
-                         footprint may reach (bit 0: pixel rows [0, tile_h / 2), bit 1: the
-                         rest), by the culling rule applied to each half; a conservative
-                         superset (a half left out holds no pixel with alpha >= alpha_min).
-                         When given, a tile keeps a record if either half's rule keeps it
-                         (otherwise the rule runs once on the whole tile row), and the
-                         compositing adjoint of 8 x 8 tiles at one pixel per thread runs one
-                         warp per half tile, each staging only its half's entries: faster on
-                         long lists, slower to build.                                     */
+    int32_t half_masks; /* nonzero: each listed record also carries, in bits 30-31, which
+                         halves of its tile its footprint may reach (bit 30: pixel rows
+                         [0, tile_h / 2), bit 31: the rest), by the culling rule applied to
+                         each half: a conservative superset (a half left out holds no pixel
+                         with alpha >= alpha_min); a tile then keeps a record if either
+                         half's rule keeps it (otherwise the rule runs once on the whole
+                         tile row), and N * n_views must be below 2^30.  The compositing
+                         kernels take the record id from bits 0-29; the adjoint of 8 x 8
+                         tiles at one pixel per thread runs one warp per half tile, each
+                         staging only its half's entries (faster on long lists; the masks
+                         make the lists slower to build).  0: plain record ids.          */
 } sg_tile_lists;
 
 /* Rendered images (all view-levels packed, planar). */
@@ -270,7 +273,7 @@ size_t sg_tile_lists_workspace_size(int64_t n_records, int32_t capacity);
 
 /* Sec. III-C "sorted 2D gaussian primitives": instances (tile, record) of every non-culled
  * record, ordered by global tile id, then float32 depth bits, then record id (a stable,
- * deterministic radix sort), plus each tile's [start, end) and (when lists->half is given)
+ * deterministic radix sort), plus each tile's [start, end) and (with lists->half_masks)
  * each instance's half mask.  n_tiles: total tiles of the views (sg_make_views); with half
  * masks N * n_views must be below 2^30.  If more than capacity instances arise, the surplus
  * is dropped, *count holds the required number and SG_STATUS_CAPACITY is set in *status. */

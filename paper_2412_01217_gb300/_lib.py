@@ -48,7 +48,7 @@ class SgProjected(C.Structure):
 
 class SgTileLists(C.Structure):
     _fields_ = [("capacity", c_i), ("tile", c_p), ("record", c_p), ("ranges", c_p), ("count", c_p), ("order", c_p),
-                ("half", c_p)]
+                ("half_masks", c_i)]
 
 
 class SgImages(C.Structure):

@@ -287,7 +287,7 @@ sg_status sg_build_tile_lists(const sg_projected *proj, int32_t N, int32_t n_vie
     SG_TRY(check_cfg(cfg));
     SG_TRY(check_views(views, n_views));
     SG_REQUIRE(N >= 0 && n_tiles >= 1, "bad N / n_tiles");
-    SG_REQUIRE(!lists || !lists->half || (int64_t)N * n_views < (int64_t)1 << 30,
+    SG_REQUIRE(!lists || !lists->half_masks || (int64_t)N * n_views < (int64_t)1 << 30,
                "N * n_views = %lld records: with half masks at most 2^30 - 1", (long long)N * n_views);
     SG_REQUIRE(lists && lists->tile && lists->record && lists->ranges && lists->count, "tile-list buffers are NULL");
     SG_REQUIRE(lists->capacity >= 1, "capacity must be >= 1");

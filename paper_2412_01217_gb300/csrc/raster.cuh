@@ -24,9 +24,9 @@ struct RasterArgs {
     int *work_counter;
     int persistent;
     int ppt;  // pixels per thread (1, 2 or 4)
-    const uint8_t *half;  // per instance: halves of the tile the footprint may reach (or null);
-                          // given, the adjoint of 8 x 8 tiles at one pixel per thread runs
-                          // one warp per half tile
+    int half;             // records carry half masks in bits 30-31: the adjoint of 8 x 8
+                          // tiles at one pixel per thread runs one warp per half tile
+    uint32_t rec_mask;    // bits of a list word that hold the record id
     // forward outputs / backward inputs
     float *img_rgb, *img_depth, *img_sem;
     float *T_final;
@@ -67,7 +67,8 @@ inline void fill_raster_args(RasterArgs &a, const sg_gaussians *g, const sg_proj
     a.work_counter = work_counter;
     a.persistent = cfg->persistent;
     a.ppt = cfg->pixels_per_thread;
-    a.half = lists->half;
+    a.half = lists->half_masks != 0;
+    a.rec_mask = a.half ? 0x3fffffffu : 0xffffffffu;
 }
 
 sg_status launch_raster(RasterArgs &a, int C, bool backward, cudaStream_t st);

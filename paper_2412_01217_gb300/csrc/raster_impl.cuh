@@ -42,7 +42,7 @@ __device__ __forceinline__ void load_batch(const RasterArgs &a, int C, int list_
                                            float4 *s_geo1, float4 *s_geo2, float *s_feat, uint32_t *s_rec,
                                            int nthreads) {
     for (int j = threadIdx.x; j < cnt; j += nthreads) {
-        const uint32_t rec = a.record[list_start + b0 + j];
+        const uint32_t rec = a.record[list_start + b0 + j] & a.rec_mask;
         const float4 g0 = a.geo[2 * (size_t)rec];
         const float4 g1 = a.geo[2 * (size_t)rec + 1];
         const uint32_t packed = __float_as_uint(g1.w);
@@ -702,8 +702,9 @@ __global__ void __maxnreg__((bwd_max_regs<C, PPT>())) raster_bwd_kernel(RasterAr
                     uint32_t rec = 0u;
                     bool sel = false;
                     if (pos >= 0) {
-                        rec = a.record[range.x + pos];
-                        sel = (a.half[range.x + pos] >> hf) & 1u;
+                        const uint32_t word = a.record[range.x + pos];  // record | half mask << 30
+                        rec = word & 0x3fffffffu;
+                        sel = (word >> (30 + hf)) & 1u;
                     }
                     const uint32_t bal = __ballot_sync(SG_FULL_MASK, sel);
                     if (sel) {

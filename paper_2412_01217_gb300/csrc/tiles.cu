@@ -205,6 +205,53 @@ struct RowSpan {
     float uf;      // fraction of the mean
     int ui;        // integer part of the mean
 };
+// The band-independent part of the rule: the mean and the ellipse's constants.
+struct Footprint {
+    float uf, vf;            // fractions of the mean
+    int ui, vi;              // integer parts of the mean
+    float A, B, Cq, p, At;   // A thr' = At
+    float dymax, dyr;        // |dy| bound; dy of the right edge's maximum
+};
+__device__ __forceinline__ Footprint footprint(const float4 g0, const float4 g1, float ex) {
+    Footprint f;
+    const uint32_t packed = __float_as_uint(g1.w);
+    f.ui = (int)(short)(packed & 0xffffu);
+    f.vi = (int)(short)(packed >> 16);
+    f.uf = g0.x;
+    f.vf = g0.y;
+    const float m00 = g1.x, m10 = g1.y, m11 = g1.z;
+    const float t = __fmul_rn(__fmul_rn(__fsub_rn(ex, 0x1.47ae14p-7f /* float(0.01) */), 0x1.fefa62p-1f /* float(1/1.002) */),
+                              m00);
+    const float thr = __fmul_rn(t, t);
+    f.A = __fadd_rn(__fmul_rn(m00, m00), __fmul_rn(m10, m10));
+    f.B = __fmul_rn(m10, m11);
+    f.Cq = __fmul_rn(m11, m11);
+    f.p = __fmul_rn(m00, m11);
+    f.dymax = __fdiv_rn(__fsqrt_rn(__fmul_rn(f.A, thr)), f.p);
+    const float dxmax = __fdiv_rn(__fsqrt_rn(__fmul_rn(thr, f.Cq)), f.p);
+    f.dyr = -__fdiv_rn(__fmul_rn(f.B, dxmax), f.Cq);
+    f.At = __fmul_rn(f.A, thr);
+    return f;
+}
+// The span of the footprint within the band of pixel-centre rows [Y0, Y1].
+__device__ __forceinline__ bool band_span(const Footprint &f, int Y0, int Y1, RowSpan &rs) {
+    rs.ui = f.ui;
+    rs.uf = f.uf;
+    const float y0 = __fsub_rn((float)(Y0 - f.vi), f.vf), y1 = __fsub_rn((float)(Y1 - f.vi), f.vf);
+    const float yb0 = fmaxf(y0, -f.dymax), yb1 = fminf(y1, f.dymax);
+    if (!(yb0 <= yb1)) return false;
+    auto s_of = [&](float dy) {
+        const float q = __fmul_rn(f.p, dy);
+        return __fsqrt_rn(fmaxf(__fsub_rn(f.At, __fmul_rn(q, q)), 0.f));
+    };
+    const float dr = fminf(yb1, fmaxf(yb0, f.dyr));
+    const float dl = fminf(yb1, fmaxf(yb0, -f.dyr));
+    rs.xr = __fdiv_rn(__fsub_rn(s_of(dr), __fmul_rn(f.B, dr)), f.A);
+    rs.xl = __fdiv_rn(__fsub_rn(-__fmul_rn(f.B, dl), s_of(dl)), f.A);
+    return true;
+}
+// The same rule in one pass (the band-independent constants after the early exit), for the
+// lists without half masks; identical operations, so identical results.
 __device__ __forceinline__ bool row_span(const float4 g0, const float4 g1, float ex, int Y0, int Y1, RowSpan &rs) {
     const uint32_t packed = __float_as_uint(g1.w);
     rs.ui = (int)(short)(packed & 0xffffu);
@@ -282,10 +329,11 @@ struct SlotRun {
 __device__ __forceinline__ SlotRun slot_run(const float4 g0, const float4 g1, float ex, int Y0, int Y1, int tile_h,
                                             int tx0, int tx1, int tile_w, int W) {
     RowSpan rs;
+    const Footprint f = footprint(g0, g1, ex);
     const int Yh = Y0 + tile_h / 2;
     int a0 = tx1, b0 = tx1, a1 = tx1, b1 = tx1;
-    if (row_span(g0, g1, ex, Y0, min(Yh - 1, Y1), rs)) span_run(rs, tx0, tx1, tile_w, W, a0, b0);
-    if (Yh <= Y1 && row_span(g0, g1, ex, Yh, Y1, rs)) span_run(rs, tx0, tx1, tile_w, W, a1, b1);
+    if (band_span(f, Y0, min(Yh - 1, Y1), rs)) span_run(rs, tx0, tx1, tile_w, W, a0, b0);
+    if (Yh <= Y1 && band_span(f, Yh, Y1, rs)) span_run(rs, tx0, tx1, tile_w, W, a1, b1);
     const bool e0 = b0 <= a0, e1 = b1 <= a1;
     SlotRun r;
     if (e0 && e1) {
@@ -360,7 +408,7 @@ __global__ void slot_prefix_kernel(const uint2 *__restrict__ rect, const uint32_
 // HALVES: the rule runs per half tile row (slot_run) and the emitted records carry each
 // tile's half mask in bits 30-31.
 template <bool EMIT, bool HALVES>
-__global__ void cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *__restrict__ geo,
+__global__ void __launch_bounds__(kScanThreads, 6) cull_pass_kernel(const uint2 *__restrict__ rect, const float4 *__restrict__ geo,
                                  const float2 *__restrict__ ext, const uint32_t *__restrict__ rec,
                                  const int *__restrict__ m_ptr, const int *__restrict__ s_ptr,
                                  const uint32_t *__restrict__ P, const uint32_t *__restrict__ first_rec, int Gc,
@@ -571,14 +619,11 @@ __device__ __forceinline__ void bucket_exclusive_scan(const uint32_t (&v)[DPT], 
 template <int ND>
 __host__ __device__ constexpr int scatter_ipt() { return 12; }
 
-// SPLIT (the tile sort's last pass with half masks): bits 30-31 of each value go to half_out,
-// the rest to vout.
-template <class Src, int ND, bool SPLIT = false>
+template <class Src, int ND>
 __global__ void __launch_bounds__(kScanThreads, 4) rs_scatter_kernel(
     Src src, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ n_ptr, int cap, int shift, uint32_t mask,
-    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, int G,
-    uint8_t *__restrict__ half_out) {
+    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, int G) {
     pdl_begin();
     constexpr int kWarps = kScanThreads / 32;
     constexpr int DPT = ND / kScanThreads;  // digits per thread: tid * DPT + q
@@ -664,13 +709,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) rs_scatter_kernel(
             const uint32_t d = (k >> shift) & mask;
             const uint32_t pos = run[d] + ((uint32_t)j - loc[d]);
             if (kout) kout[pos] = k;
-            const uint32_t v = sval[j];
-            if (SPLIT) {
-                vout[pos] = v & 0x3fffffffu;
-                half_out[pos] = (uint8_t)(v >> 30);
-            } else {
-                vout[pos] = v;
-            }
+            vout[pos] = sval[j];
         }
         __syncthreads();
 #pragma unroll
@@ -684,8 +723,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) rs_scatter_kernel(
 // split into the fewest passes of at most max_bits (<= 9) bits, as evenly as possible.
 static void radix_sort(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                        uint32_t *ktmp, uint32_t *vtmp, const int *n_ptr, int cap, int bits,
-                       uint32_t *hist, uint32_t *totals, int G, cudaStream_t st, int max_bits,
-                       bool split_last = false, uint8_t *half_out = nullptr) {
+                       uint32_t *hist, uint32_t *totals, int G, cudaStream_t st, int max_bits) {
     const int passes = (bits + max_bits - 1) / max_bits;
     const uint32_t *ks = kin, *vs = vin;
     int shift = 0;
@@ -695,25 +733,16 @@ static void radix_sort(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
         uint32_t *kd = ((passes - 1 - p) % 2 == 0) ? kout : ktmp;
         uint32_t *vd = ((passes - 1 - p) % 2 == 0) ? vout : vtmp;
         const ArrayPairs src{ks, vs};
-        const bool split = split_last && half_out && p == passes - 1;
         if (nb > 8) {
             launch_pdl(rs_hist_kernel<ArrayPairs, 512>, G, kScanThreads, 0, st, src, n_ptr, cap, shift, mask, hist, G);
             launch_pdl(rs_digit_scan_kernel, 512, kScanThreads, 0, st, hist, totals, G);
-            if (split)
-                launch_pdl(rs_scatter_kernel<ArrayPairs, 512, true>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap,
-                           shift, mask, hist, totals, G, half_out);
-            else
-                launch_pdl(rs_scatter_kernel<ArrayPairs, 512>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap, shift,
-                           mask, hist, totals, G, (uint8_t *)nullptr);
+            launch_pdl(rs_scatter_kernel<ArrayPairs, 512>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap, shift, mask,
+                       hist, totals, G);
         } else {
             launch_pdl(rs_hist_kernel<ArrayPairs, 256>, G, kScanThreads, 0, st, src, n_ptr, cap, shift, mask, hist, G);
             launch_pdl(rs_digit_scan_kernel, 256, kScanThreads, 0, st, hist, totals, G);
-            if (split)
-                launch_pdl(rs_scatter_kernel<ArrayPairs, 256, true>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap,
-                           shift, mask, hist, totals, G, half_out);
-            else
-                launch_pdl(rs_scatter_kernel<ArrayPairs, 256>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap, shift,
-                           mask, hist, totals, G, (uint8_t *)nullptr);
+            launch_pdl(rs_scatter_kernel<ArrayPairs, 256>, G, kScanThreads, 0, st, src, kd, vd, n_ptr, cap, shift, mask,
+                       hist, totals, G);
         }
         count_launches(3);
         ks = kd;
@@ -845,7 +874,7 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
                w.counts + 0, 0, w.bsum, Ge);
     launch_pdl(scan_blocks_kernel, 1, kScanThreads, 0, st, w.bsum, Ge, w.counts + 2);
     const int Gc = 4 * G;  // blocks of the slot partition (each walks a few 256-slot chunks)
-    const bool halves = lists->half != nullptr;  // per-instance half masks wanted
+    const bool halves = lists->half_masks != 0;  // records carry half masks
     launch_pdl(slot_prefix_kernel, Ge, kScanThreads, 0, st, rect, w.dval_out, w.counts + 0, w.bsum, Ge,
                w.counts + 2, Gc, w.slot0, w.first_rec);
     // culling, evenly over the slots: kept counts, their offsets, emission (the tile sort's
@@ -863,7 +892,7 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
     int bits = 1;
     while ((1ll << bits) < (long long)n_tiles) ++bits;
     radix_sort(w.tkey_in, w.tval_in, lists->tile, lists->record, w.tkey_tmp, w.tval_tmp,
-               lists->count, lists->capacity, bits, w.hist, w.totals, G, st, kTileDigitBits, halves, lists->half);
+               lists->count, lists->capacity, bits, w.hist, w.totals, G, st, kTileDigitBits);
     // 5. tile ranges
     launch_pdl(clamp_count_kernel, 1, 1, 0, st, lists->count, lists->capacity, w.counts + 1);
     launch_pdl(ranges_kernel, (n_tiles + kScanThreads - 1) / kScanThreads, kScanThreads, 0, st, lists->tile,
@@ -875,7 +904,7 @@ sg_status launch_build_tile_lists(const sg_projected *proj, int N, int n_views,
         launch_pdl(rs_hist_kernel<TileLengthKeys, 256>, G, kScanThreads, 0, st, src, nullptr, n_tiles, 0, 63u, w.hist, G);
         launch_pdl(rs_digit_scan_kernel, 256, kScanThreads, 0, st, w.hist, w.totals, G);
         launch_pdl(rs_scatter_kernel<TileLengthKeys, 256>, G, kScanThreads, 0, st, src, nullptr, reinterpret_cast<uint32_t *>(lists->order),
-                                                      nullptr, n_tiles, 0, 63u, w.hist, w.totals, G, (uint8_t *)nullptr);
+                                                      nullptr, n_tiles, 0, 63u, w.hist, w.totals, G);
         count_launches(3);
     }
     return check_launch("build_tile_lists");

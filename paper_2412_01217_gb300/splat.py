@@ -204,8 +204,6 @@ class PyramidRasterizer:
         self.capacity = int(capacity)
         self.tile = torch.zeros(self.capacity, **i32)
         self.record = torch.zeros(self.capacity, **i32)
-        # per-instance half masks, allocated when the config asks for them
-        self.half = torch.zeros(self.capacity, dtype=torch.uint8, device=dev) if self.cfg.half_masks else None
         self.ranges = torch.zeros(self.n_tiles * 2, **i32)
         self.order = torch.zeros(self.n_tiles, **i32)
         self.count = torch.zeros(1, **i32)
@@ -237,7 +235,7 @@ class PyramidRasterizer:
         if sem_sh:
             self._alloc_record_semantics()
         self._lists = SgTileLists(self.capacity, self.tile.data_ptr(), self.record.data_ptr(),
-                                  self.ranges.data_ptr(), self.count.data_ptr(), self.order.data_ptr(), None)
+                                  self.ranges.data_ptr(), self.count.data_ptr(), self.order.data_ptr(), 0)
         self._saved = SgSaved(self.T_final.data_ptr(), self.last.data_ptr(), self.n_contrib.data_ptr())
 
     def _alloc_record_colour(self):
@@ -296,10 +294,9 @@ class PyramidRasterizer:
              C.byref(self._proj), _ptr(self.status), _stream())
 
     def build_lists(self):
-        if self.cfg.half_masks and self.half is None:
-            self.half = torch.zeros(self.capacity, dtype=torch.uint8, device=self.device)
-        # the adjoint reads the masks through the same struct, so it follows this choice
-        self._lists.half = self.half.data_ptr() if self.cfg.half_masks else None
+        # the compositing kernels read the lists through the same struct, so they follow
+        # this choice
+        self._lists.half_masks = int(self.cfg.half_masks)
         call("sg_build_tile_lists", C.byref(self._proj), self.N, self.V, _ptr(self.views), self.n_tiles,
              C.byref(self._ccfg), C.byref(self._lists), _ptr(self.tile_ws), self.tile_ws.numel(),
              _ptr(self.status), _stream())

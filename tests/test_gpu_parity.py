@@ -111,8 +111,15 @@ def _gpu_lists(r):
     K = r.instance_count()
     tiles = r.tile[:K].cpu().numpy().view(np.uint32).astype(np.int64)
     recs = r.record[:K].cpu().numpy().view(np.uint32).astype(np.int64)
+    if r.cfg.half_masks:  # records in bits 0-29, half masks in bits 30-31
+        recs &= (1 << 30) - 1
     ranges = r.ranges.view(-1, 2).cpu().numpy().astype(np.int64)
     return K, tiles, recs, ranges
+
+
+def _gpu_half_masks(r, K):
+    """Each listed instance's half mask (bit 0: top half of the tile, bit 1: bottom)."""
+    return (r.record[:K].cpu().numpy().view(np.uint32) >> 30).astype(np.int64)
 
 
 def _check_ranges_and_order(r, tiles, ranges):
@@ -171,7 +178,7 @@ def lists_match_definition(r, g, ocams):
         assert not far.any(), f"view {v}: {int(far.sum())} listed pairs the footprint does not reach"
         # half masks: a half of the tile holding a pixel centre where alpha reaches alpha_min
         # (FP64) is marked
-        hm = r.half[:K].cpu().numpy()[sel] if r.cfg.half_masks else np.full(len(gi), 3, np.uint8)
+        hm = _gpu_half_masks(r, K)[sel] if r.cfg.half_masks else np.full(len(gi), 3, np.int64)
         for h in (0, 1):
             hty = 2 * gty + h
             inside = hty * (th // 2) < oc["H"]
@@ -240,7 +247,7 @@ def lists_match_kernel_rule(r):
     local = rt - np.asarray(to, np.int64)[v]
     ltx, lty = local % np.asarray(tx, np.int64)[v], local // np.asarray(tx, np.int64)[v]
     _, want = kept_and_masks(rr, ltx, lty, *halves(rr, ltx, lty))
-    got = r.half[:K].cpu().numpy().astype(np.int64)
+    got = _gpu_half_masks(r, K)
     assert np.array_equal(got, want), f"{int((got != want).sum())} of {K} half masks differ"
     return K
 
