@@ -119,13 +119,14 @@ def autotune(params, cams, levels, gt, loss_cfg, base: RenderConfig | None = Non
                             pixels_per_thread_bwd=1)
             r._ccfg = r.cfg.to_c()
             t_lists_h = _time(r.build_lists, reps)
-            r.rasterize(params)
+            t_fwd_h = _time(lambda: r.rasterize(params), reps)  # (on the lists kept by the half rule)
             t_bwd_h = _time(lambda: r.backward(params, grads), reps)
             table.append(dict(tile="8x8", batch=0, kernel="lists_half", ppt=0, ms=t_lists_h))
+            table.append(dict(tile="8x8", batch=fwd_best[1], kernel="fwd_half", ppt=fwd_best[2], ms=t_fwd_h))
             table.append(dict(tile="8x8", batch=0, kernel="bwd_half", ppt=1, ms=t_bwd_h))
-            total_h = t_lists_h + fwd_best[0] + t_bwd_h
+            total_h = t_lists_h + t_fwd_h + t_bwd_h
             if log:
-                log(f"tile 8x8 with half masks: lists {t_lists_h:.3f} ms, bwd {t_bwd_h:.3f} ms")
+                log(f"tile 8x8 with half masks: lists {t_lists_h:.3f} ms, fwd {t_fwd_h:.3f} ms, bwd {t_bwd_h:.3f} ms")
             if total_h < best[0]:
                 best = (total_h, dict(chosen_fwd, batch_bwd=bwd_best[1], pixels_per_thread_bwd=1, half_masks=True))
         del r, grads
