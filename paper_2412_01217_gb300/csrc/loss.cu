@@ -486,7 +486,10 @@ __global__ void __launch_bounds__(kLossThreads) loss_pixel_kernel(PixelArgs a) {
 //
 // Persistent: the warps of a resident grid walk the 32-pixel units of the image set, so the
 // decoder is split into shared memory once per CTA and each warp keeps its share of dL/dW in
-// registers across all of its units; no block barrier inside the loop.  Each unit's two loss
+// registers across all of its units; no block barrier inside the loop.  Each warp stages its
+// units in shared memory with asynchronous copies: the next unit's features, labels and
+// depths are requested as soon as the current unit's last read of them (the dW contraction)
+// is done, so they arrive while dS is computed and stored.  Each unit's two loss
 // sums go to its own partial slot (kPixSlots per 256-pixel block); the CTA writes one K x C
 // row of decoder-gradient partials at the end, its warps summed in a fixed order.
 template <int C, int K>
@@ -494,14 +497,26 @@ struct CeLayout {
     static constexpr int CP = C + 4;   // W rows (class-major): 16-byte rows, conflict-free ldmatrix
     static constexpr int KT = K + 4;   // W^T rows (feature-major, classes permuted)
     static constexpr int PP = 32 + 4;  // dZ^T rows (class-major over the warp's 32 pixels)
+    static constexpr int SP = 32 + 8;  // staged S rows (feature-major): conflict-free A fragments
     static constexpr int W_FLOATS = 2 * K * CP + 2 * C * KT;
     static constexpr int WARP_FLOATS = K * PP > K * C ? K * PP : K * C;
+    // per warp: the unit's S (C x SP), labels, depth and GT depth (32 each)
+    static constexpr int STAGE_FLOATS = C * SP + 3 * 32;
 };
 
 template <int C, int K>
 __host__ __device__ constexpr int ce_mma_smem_floats() {
-    return CeLayout<C, K>::W_FLOATS + (kLossThreads / 32) * CeLayout<C, K>::WARP_FLOATS;
+    return CeLayout<C, K>::W_FLOATS + (kLossThreads / 32) * (CeLayout<C, K>::WARP_FLOATS + CeLayout<C, K>::STAGE_FLOATS);
 }
+
+// 4-byte asynchronous copy global -> shared (zero-filled when !valid; src must still be a
+// mapped address), and its group fences.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_groups() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ void ldsm_x2(const float *p, uint32_t &r0, uint32_t &r1) {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
@@ -520,7 +535,7 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
     pdl_begin();
     static_assert(C % 8 == 0 && K % 16 == 0, "MMA tiles");
     using L = CeLayout<C, K>;
-    constexpr int CP = L::CP, KT = L::KT, PP = L::PP;
+    constexpr int CP = L::CP, KT = L::KT, PP = L::PP, SP = L::SP;
     constexpr int NK = K / 8, NC = C / 8;
     extern __shared__ __align__(16) float s_dyn[];
     float *s_whi = s_dyn, *s_wlo = s_whi + K * CP;     // W [class][feature]
@@ -553,33 +568,62 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
     // of the grid take units u = w, w + n_warps, ... (w the warp's grid-wide index)
     const int n_units = kPixSlots * a.lv.pix_blk_off[a.lv.n];
     const int n_warps = (int)gridDim.x * kPixSlots;
-    for (int u = (int)blockIdx.x * kPixSlots + warp; u < n_units; u += n_warps) {
+    float *s_st = s_dyn + L::W_FLOATS + (kLossThreads / 32) * L::WARP_FLOATS + warp * L::STAGE_FLOATS;
+    int *s_lab = reinterpret_cast<int *>(s_st + C * SP);
+    float *s_dep = s_st + C * SP + 32, *s_gd = s_dep + 32;
+    // unit u: view v, its pixel count and offset, the unit's first pixel pw
+    struct Unit {
+        int v, HW, pw;
+        size_t p0;
+    };
+    auto unit_of = [&](int u) {
+        Unit x;
         const int blk = u / kPixSlots, slot = u % kPixSlots;
-        const int v = find_prefix(a.lv.pix_blk_off, a.lv.n, blk);
-        const sg_view &vw = a.views[v];
-        const int HW = vw.W * vw.H;
-        const int pw = (blk - a.lv.pix_blk_off[v]) * kLossThreads + slot * 32;  // the unit's first pixel
-        const size_t p0 = (size_t)vw.pixel_offset;
-        const float *semv = a.sem + (size_t)C * p0;
+        x.v = find_prefix(a.lv.pix_blk_off, a.lv.n, blk);
+        const sg_view &vw = a.views[x.v];
+        x.HW = vw.W * vw.H;
+        x.pw = (blk - a.lv.pix_blk_off[x.v]) * kLossThreads + slot * 32;
+        x.p0 = (size_t)vw.pixel_offset;
+        return x;
+    };
+    // lane l requests pixel pw + l of every feature plane, its label and both depths
+    auto prefetch = [&](const Unit &x) {
+        const int p = x.pw + lane;
+        const bool ok = p < x.HW;
+        const size_t q = x.p0 + (ok ? p : 0);
+        const float *src = a.sem + (size_t)C * x.p0 + (ok ? p : 0);
+#pragma unroll
+        for (int f = 0; f < C; ++f) cp_async4(s_st + f * SP + lane, src + (size_t)f * x.HW, ok);
+        cp_async4(s_lab + lane, a.label + q, ok);
+        cp_async4(s_dep + lane, a.depth + q, ok);
+        cp_async4(s_gd + lane, a.gt_depth + q, ok);
+        cp_async_commit_group();
+    };
+    int u = (int)blockIdx.x * kPixSlots + warp;
+    if (u < n_units) prefetch(unit_of(u));
+    for (; u < n_units; u += n_warps) {
+        const Unit x = unit_of(u);
+        const int v = x.v, HW = x.HW, pw = x.pw;
+        const size_t p0 = x.p0;
         const int nd = a.counts[2 * v], nl = a.counts[2 * v + 1];
+        cp_async_wait_all_groups();
+        __syncwarp();
         float l1d = 0.f, ce = 0.f;
         {
             const int p = pw + lane;
             if (p < HW) {
-                const float gd = a.gt_depth[p0 + p];
+                const float gd = s_gd[lane];
                 float gdep = 0.f;
                 if (gd > 0.f) {
-                    const float d = a.depth[p0 + p] - gd;
+                    const float d = s_dep[lane] - gd;
                     l1d = fabsf(d);
                     gdep = a.w_depth * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) / (float)nd;
                 }
                 a.g_depth[p0 + p] = gdep;
             }
         }
-        auto S = [&](int px, int f) -> float {
-            const int p = pw + px;
-            return p < HW ? semv[(size_t)f * HW + p] : 0.f;
-        };
+        // staged S (pixels past the view's end read as zero)
+        auto S = [&](int px, int f) -> float { return s_st[f * SP + px]; };
         // ---- Z = S W^T: M = pixels (2 x 16), N = classes, K = features ----
         // all of the warp's feature loads are issued before the first MMA (memory-level parallelism)
         float sa[NC][2][4];
@@ -599,7 +643,7 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int p = pw + 16 * mt + gid + 8 * h;
-                labs[mt][h] = p < HW ? a.label[p0 + p] : -1;
+                labs[mt][h] = p < HW ? s_lab[16 * mt + gid + 8 * h] : -1;
             }
         float z[2][NK][4];
 #pragma unroll
@@ -675,6 +719,41 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
             a.partials[2 * u] = l1d;
             a.partials[2 * u + 1] = ce;
         }
+        // ---- dW += dZ^T S: M = classes, N = features, K = pixels ----
+        if (dec_grad) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NK; ++nt)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        s_dz[(8 * nt + 2 * tig + (i & 1)) * PP + 16 * mt + gid + 8 * (i >> 1)] = z[mt][nt][i];
+            __syncwarp();
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                uint32_t bh[NC][2], bl[NC][2];
+#pragma unroll
+                for (int nt = 0; nt < NC; ++nt) {
+                    split_tf32(S(8 * ks + tig, 8 * nt + gid), bh[nt][0], bl[nt][0]);
+                    split_tf32(S(8 * ks + tig + 4, 8 * nt + gid), bh[nt][1], bl[nt][1]);
+                }
+#pragma unroll
+                for (int mt = 0; mt < K / 16; ++mt) {
+                    // A (16 x 8): rows = classes 16 mt .., columns = pixels 8 ks ..
+                    uint32_t ar[4], ah[4], al[4];
+                    ldsm_x4(s_dz + (16 * mt + lr + 8 * lc) * PP + 8 * ks + 4 * lh, ar);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) split_tf32(__uint_as_float(ar[i]), ah[i], al[i]);
+#pragma unroll
+                    for (int nt = 0; nt < NC; ++nt)
+                        mma_tf32x3(dw[mt][nt], ah, al, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
+                }
+            }
+            __syncwarp();  // the stash is rewritten by the next unit
+        }
+        // the stage's last read is done: request the next unit (it arrives during dS)
+        __syncwarp();
+        if (u + n_warps < n_units) prefetch(unit_of(u + n_warps));
         // ---- dS = dZ W: M = pixels, N = features, K = classes (permuted within each 8-class step) ----
         {
             float ds[2][NC][4];
@@ -715,38 +794,6 @@ __global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder
                         const int f = 8 * nt + 2 * tig + (i & 1);
                         if (p < HW) a.g_sem[(size_t)C * p0 + (size_t)f * HW + p] = ds[mt][nt][i];
                     }
-        }
-        // ---- dW += dZ^T S: M = classes, N = features, K = pixels ----
-        if (dec_grad) {
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < NK; ++nt)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        s_dz[(8 * nt + 2 * tig + (i & 1)) * PP + 16 * mt + gid + 8 * (i >> 1)] = z[mt][nt][i];
-            __syncwarp();
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-                uint32_t bh[NC][2], bl[NC][2];
-#pragma unroll
-                for (int nt = 0; nt < NC; ++nt) {
-                    split_tf32(S(8 * ks + tig, 8 * nt + gid), bh[nt][0], bl[nt][0]);
-                    split_tf32(S(8 * ks + tig + 4, 8 * nt + gid), bh[nt][1], bl[nt][1]);
-                }
-#pragma unroll
-                for (int mt = 0; mt < K / 16; ++mt) {
-                    // A (16 x 8): rows = classes 16 mt .., columns = pixels 8 ks ..
-                    uint32_t ar[4], ah[4], al[4];
-                    ldsm_x4(s_dz + (16 * mt + lr + 8 * lc) * PP + 8 * ks + 4 * lh, ar);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) split_tf32(__uint_as_float(ar[i]), ah[i], al[i]);
-#pragma unroll
-                    for (int nt = 0; nt < NC; ++nt)
-                        mma_tf32x3(dw[mt][nt], ah, al, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
-                }
-            }
-            __syncwarp();  // the stash is rewritten by the next unit
         }
     }
     if (!dec_grad) return;
