@@ -85,7 +85,7 @@ __device__ __forceinline__ void stage_rows_warp(const RasterArgs &a, int C, RecO
         const float vI = (float)((int)(short)(packed >> 16) - py0);
         s_geo0[j] = make_float4(uI, vI, g0.x, g0.y);
         s_geo1[j] = make_float4(g1.x, g1.y, g1.z, g0.w);
-        s_geo2[j] = make_float4(uI + g0.x, vI + g0.y, ex.x, ex.y);
+        if (s_geo2) s_geo2[j] = make_float4(uI + g0.x, vI + g0.y, ex.x, ex.y);
         s_rec[j] = rec;
         f[3] = g0.z;  // depth (camera z of the mean, Eq. 8)
     } else {
@@ -406,8 +406,10 @@ __global__ void __maxnreg__((bwd_max_regs<C, PPT>())) raster_bwd_kernel(RasterAr
     const int batch = hm ? kChunk : a.batch;
     float4 *s_geo0 = reinterpret_cast<float4 *>(smem_raw);
     float4 *s_geo1 = s_geo0 + batch;
-    float4 *s_geo2 = s_geo1 + batch;
-    float *s_feat = reinterpret_cast<float *>(s_geo2 + batch);
+    // (half mode stages no (u, v, ex, ey) rows: its entries passed the half's culling rule,
+    // which rejects what the warp's ellipse test would)
+    float4 *s_geo2 = hm ? nullptr : s_geo1 + batch;
+    float *s_feat = reinterpret_cast<float *>(s_geo1 + (hm ? batch : 2 * batch));
     uint32_t *s_rec = reinterpret_cast<uint32_t *>(s_feat + (size_t)batch * NF);
     // half mode: the list position of each staged row, and the queue of pending entries
     // (list position, record)
@@ -482,7 +484,8 @@ __global__ void __maxnreg__((bwd_max_regs<C, PPT>())) raster_bwd_kernel(RasterAr
         auto chunk = [&](const int jc0, const int jmax, auto pos_of) {
                 // entries of the chunk whose footprint reaches the warp (lane r tests entry jc0 + r)
                 bool cand = false;
-                if (lane < kChunk) cand = jc0 + lane < jmax && !wt.misses(s_geo2[jc0 + lane], s_geo1[jc0 + lane], ln_amin);
+                if (lane < kChunk)
+                    cand = jc0 + lane < jmax && (hm || !wt.misses(s_geo2[jc0 + lane], s_geo1[jc0 + lane], ln_amin));
                 uint32_t cmask = __ballot_sync(SG_FULL_MASK, cand);
                 if (!cmask) return;
                 // ---- gf = G F^T for the chunk (M = pixels, N = entries, K = features) ----
@@ -748,11 +751,11 @@ template <int C, int PPT>
 inline size_t bwd_smem(int batch, int threads) {
     return fwd_smem<C>(batch) + (size_t)batch * 4 + sizeof(float) * (threads / 32) * bwd_warp_floats<C, PPT>();
 }
-// half mode: one 16-entry chunk staged (+ its list positions), the (position, record) queue,
-// one warp
+// half mode: one 16-entry chunk staged without its (u, v, ex, ey) rows (+ its list positions),
+// the (position, record) queue, one warp
 template <int C>
 inline size_t bwd_half_smem() {
-    return fwd_smem<C>(kChunk) + (size_t)kChunk * 4 * 2 + (size_t)kHalfQueue * 4 * 2 +
+    return fwd_smem<C>(kChunk) - (size_t)kChunk * 16 + (size_t)kChunk * 4 * 2 + (size_t)kHalfQueue * 4 * 2 +
            sizeof(float) * bwd_warp_floats<C, 1>();
 }
 
