@@ -78,10 +78,15 @@ struct ViewGeom {
     bool clx, cly;
 };
 
-// (limx, limy) = the Jacobian clamp fov_clamp W / (2 fx), fov_clamp H / (2 fy) of the view.
-__device__ __forceinline__ void view_geom(const sg_view &vw, const float mu[3], float2 lim, ViewGeom &q) {
-    for (int i = 0; i < 2; ++i)
-        q.t[i] = vw.R[3 * i] * mu[0] + vw.R[3 * i + 1] * mu[1] + vw.R[3 * i + 2] * mu[2] + vw.t[i];
+// The pose part: camera-space mean (the view's R, t only, so shared by every pyramid level
+// of a keyframe).
+struct PoseGeom {
+    float t0, t1;
+    DF tz;  // camera z in double-float (its rounded head is the float32 z)
+};
+__device__ __forceinline__ void pose_geom(const sg_view &vw, const float mu[3], PoseGeom &p) {
+    p.t0 = vw.R[0] * mu[0] + vw.R[1] * mu[1] + vw.R[2] * mu[2] + vw.t[0];
+    p.t1 = vw.R[3] * mu[0] + vw.R[4] * mu[1] + vw.R[5] * mu[2] + vw.t[1];
     // camera z is also the depth ordering key of the tile lists (the order of the set N of
     // Eq. 7-9): t_z rounded to the nearest float32.  It is summed in double-float (exact
     // products, error near 2^-46 of the terms), whose rounded head is the nearest float32 of
@@ -89,7 +94,15 @@ __device__ __forceinline__ void view_geom(const sg_view &vw, const float mu[3], 
     DF z = two_prod(vw.R[6], mu[0]);
     z = df_add(z, two_prod(vw.R[7], mu[1]));
     z = df_add(z, two_prod(vw.R[8], mu[2]));
-    q.tz = df_add_f(z, vw.t[2]);
+    p.tz = df_add_f(z, vw.t[2]);
+}
+
+// The level part.  (limx, limy) = the Jacobian clamp fov_clamp W / (2 fx), fov_clamp H / (2 fy)
+// of the view.
+__device__ __forceinline__ void level_geom(const sg_view &vw, const PoseGeom &p, float2 lim, ViewGeom &q) {
+    q.t[0] = p.t0;
+    q.t[1] = p.t1;
+    q.tz = p.tz;
     q.t[2] = q.tz.hi;
     const float itz = 1.f / q.t[2];
     const float limx = lim.x, limy = lim.y;
@@ -208,6 +221,17 @@ __device__ __forceinline__ void view_limits(const sg_view *s_views, int n_views,
                                fov_clamp * 0.5f * (float)s_views[i].H / s_views[i].fy);
 }
 
+// s_same[v]: view-level v has the bit-identical pose (R, t) of view-level v - 1 (the next
+// pyramid level of the same keyframe).
+__device__ __forceinline__ void view_same_pose(const sg_view *s_views, int n_views, bool *s_same, int tid, int nthr) {
+    for (int i = tid; i < n_views; i += nthr) {
+        bool same = i > 0;
+        for (int k = 0; k < 9 && same; ++k) same = __float_as_uint(s_views[i].R[k]) == __float_as_uint(s_views[i - 1].R[k]);
+        for (int k = 0; k < 3 && same; ++k) same = __float_as_uint(s_views[i].t[k]) == __float_as_uint(s_views[i - 1].t[k]);
+        s_same[i] = same;
+    }
+}
+
 // Camera centre c = -R^T t of every view-level, next to the view table in shared memory
 // (thread tid of nthr in the block).
 __device__ __forceinline__ void view_centres(const sg_view *s_views, int n_views, float3 *s_centre,
@@ -221,7 +245,7 @@ __device__ __forceinline__ void view_centres(const sg_view *s_views, int n_views
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) project_fwd_kernel(
+__global__ void __launch_bounds__(256) __maxnreg__((D == 0 ? 64 : D <= 2 ? 128 : 255)) project_fwd_kernel(
     const float *__restrict__ mean, const float *__restrict__ log_scale,
     const float4 *__restrict__ quat, const float *__restrict__ ologit, int N,
     const sg_view *__restrict__ views, int n_views, ProjConsts pc, float4 *__restrict__ geo,
@@ -233,13 +257,16 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
     __shared__ sg_view s_views[SG_MAX_VIEWS];
     __shared__ float3 s_centre[SG_MAX_VIEWS];
     __shared__ float2 s_lim[SG_MAX_VIEWS];
+    __shared__ bool s_same[SG_MAX_VIEWS];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
     for (int i = tid; i < n_views; i += nthr) s_views[i] = views[i];
     __syncthreads();
     view_limits(s_views, n_views, pc.fov_clamp, s_lim, tid, nthr);
+    view_same_pose(s_views, n_views, s_same, tid, nthr);
     if constexpr (D > 0) view_centres(s_views, n_views, s_centre, tid, nthr);
     __syncthreads();
-    // threadIdx.x picks the Gaussian, threadIdx.y the view-levels y, y + blockDim.y, ...
+    // threadIdx.x picks the Gaussian, threadIdx.y a contiguous run of view-levels, so that the
+    // levels of one keyframe share the camera-space mean and its double-float ratios
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N) return;
     const float mu[3] = {mean[3 * g], mean[3 * g + 1], mean[3 * g + 2]};
@@ -266,11 +293,20 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
             for (int i = 0; i < K * C; ++i) bad |= !isfinite(sem_sh[(size_t)K * C * g + i]);
         flag_status(bad, pc.status, SG_STATUS_NUMERIC);
     }
-    for (int v = threadIdx.y; v < n_views; v += blockDim.y) {
+    const int per = (n_views + (int)blockDim.y - 1) / (int)blockDim.y;
+    const int v_begin = (int)threadIdx.y * per, v_end = min(n_views, v_begin + per);
+    PoseGeom pose;
+    DF xz, yz;              // t_x / t_z and t_y / t_z of the pose, in double-float
+    bool have_ratios = false;
+    for (int v = v_begin; v < v_end; ++v) {
         const sg_view &vw = s_views[v];
         const size_t r = (size_t)v * N + g;
+        if (v == v_begin || !s_same[v]) {
+            pose_geom(vw, mu, pose);
+            have_ratios = false;
+        }
         ViewGeom q;
-        view_geom(vw, mu, s_lim[v], q);
+        level_geom(vw, pose, s_lim[v], q);
         float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
         uint2 rc = make_uint2(0u, 0u);
         float2 e2 = make_float2(0.f, 0.f);
@@ -278,16 +314,20 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(
         if (tz > pc.z_near && o >= pc.alpha_min) {
             // the 2D mean in double-float: t = R mu + t_cw and (fx t_x / t_z + cx, ...)
             // carry ~1e-4 px of float32 error at 1200 px otherwise
-            DF tdf[3];
-            for (int i = 0; i < 2; ++i) {
-                DF acc = two_prod(vw.R[3 * i], mu[0]);
-                acc = df_add(acc, two_prod(vw.R[3 * i + 1], mu[1]));
-                acc = df_add(acc, two_prod(vw.R[3 * i + 2], mu[2]));
-                tdf[i] = df_add_f(acc, vw.t[i]);
+            if (!have_ratios) {
+                DF tdf[2];
+                for (int i = 0; i < 2; ++i) {
+                    DF acc = two_prod(vw.R[3 * i], mu[0]);
+                    acc = df_add(acc, two_prod(vw.R[3 * i + 1], mu[1]));
+                    acc = df_add(acc, two_prod(vw.R[3 * i + 2], mu[2]));
+                    tdf[i] = df_add_f(acc, vw.t[i]);
+                }
+                xz = df_div(tdf[0], q.tz);
+                yz = df_div(tdf[1], q.tz);
+                have_ratios = true;
             }
-            tdf[2] = q.tz;
-            const DF udf = df_add_f(df_mul_f(df_div(tdf[0], tdf[2]), vw.fx), vw.cx);
-            const DF vdf = df_add_f(df_mul_f(df_div(tdf[1], tdf[2]), vw.fy), vw.cy);
+            const DF udf = df_add_f(df_mul_f(xz, vw.fx), vw.cx);
+            const DF vdf = df_add_f(df_mul_f(yz, vw.fy), vw.cy);
             const float u = udf.hi, vv = vdf.hi;
             float s00, s01, s11, det;
             if (pc.isotropic)
@@ -502,8 +542,10 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(
             gmu[1] += (gdir[1] - radial * y) * rn;
             gmu[2] += (gdir[2] - radial * z) * rn;
         }
+        PoseGeom pose;
+        pose_geom(vw, mu, pose);
         ViewGeom q;
-        view_geom(vw, mu, s_lim[v], q);
+        level_geom(vw, pose, s_lim[v], q);
         // conic = Sigma2D^{-1} of this view-level, recomputed in float32
         float ca, cb, cc;
         {
