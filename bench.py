@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--batch-bwd", type=int, default=0, help="batch of the backward kernel (0: --batch)")
     ap.add_argument("--half-masks", action="store_true",
                     help="per-instance half masks in the tile lists (one adjoint warp per half of an 8x8 tile)")
+    ap.add_argument("--half-tile-fwd", action="store_true",
+                    help="with --half-masks: the forward also one warp per half tile")
     ap.add_argument("--workload", default="batched", choices=sorted(WORKLOADS))
     ap.add_argument("--gaussians", type=int, default=None, help="default: the workload's count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -511,7 +513,8 @@ def run_ours(args):
     cams, frames, g, dec = build_inputs(args.workload, n_gauss, seed_offset=rank)
     fr = lambda key: [f[key] for f in frames]
     cfg = RenderConfig(tile_w=tw, tile_h=th, batch=args.batch, pixels_per_thread=args.ppt,
-                       pixels_per_thread_bwd=args.ppt_bwd, batch_bwd=args.batch_bwd, half_masks=args.half_masks)
+                       pixels_per_thread_bwd=args.ppt_bwd, batch_bwd=args.batch_bwd, half_masks=args.half_masks,
+                       half_tile_fwd=args.half_tile_fwd)
     p = to_device_params(g, dev)
     decoder = torch.tensor(dec, device=dev) if dec is not None else None
     tune_table = None
@@ -711,7 +714,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(W, tile=f"{cfg.tile_w}x{cfg.tile_h}", batch=cfg.batch,
                        pixels_per_thread=cfg.pixels_per_thread, pixels_per_thread_bwd=cfg.pixels_per_thread_bwd,
-                       batch_bwd=cfg.batch_bwd or cfg.batch, half_masks=bool(cfg.half_masks),
+                       batch_bwd=cfg.batch_bwd or cfg.batch, half_masks=bool(cfg.half_masks), half_tile_fwd=bool(cfg.half_tile_fwd),
                        autotuned=not args.no_autotune, gaussians=n_gauss,
                        l2="flushed (256 MiB write) before every timed step", parallelism="replicas"),
         "gpu_launches": int(launches_per_step * args.steps),

@@ -139,6 +139,12 @@ typedef struct {
                                word when a Gaussian parameter it reads (mean, log-scale,
                                quaternion, opacity logit, rgb, semantic feature, SH
                                coefficients) is NaN or infinite; 0: no check (the default)  */
+    int32_t half_tile_fwd;  /* with half masks in the lists, 8x8 tiles and one pixel per
+                               thread: 1 = the forward compositing also runs one warp per
+                               half tile, each taking only its half's entries with no block
+                               barrier and stopping when its own pixels saturate (faster on
+                               long lists); 0 = the tile's warps share staged batches.  The
+                               output is the same either way.                            */
 } sg_config;
 
 /* Projected records of all (view-level, Gaussian) pairs: record r = v*N + g. */

@@ -39,7 +39,8 @@ class SgConfig(C.Structure):
     _fields_ = [("alpha_max", c_f), ("alpha_min", c_f), ("T_min", c_f), ("z_near", c_f),
                 ("dilation", c_f), ("fov_clamp", c_f), ("bg", c_f * 3), ("tile_w", c_i),
                 ("tile_h", c_i), ("batch", c_i), ("persistent", c_i), ("pixels_per_thread", c_i),
-                ("pixels_per_thread_bwd", c_i), ("batch_bwd", c_i), ("isotropic", c_i), ("check_numeric", c_i)]
+                ("pixels_per_thread_bwd", c_i), ("batch_bwd", c_i), ("isotropic", c_i), ("check_numeric", c_i),
+                ("half_tile_fwd", c_i)]
 
 
 class SgProjected(C.Structure):

@@ -5,7 +5,7 @@ lists depend on the tile shape); then the shared-memory batch depth (16, 32, 64,
 the pixels per thread are varied in place, for the forward (1, 2 pixels per thread) and, with
 its own batch depth, for the backward (1, 2, 4).  For 8x8 tiles the lists are also built
 with per-instance half masks, which run the adjoint at one pixel per thread one warp per
-half tile.  Every candidate is timed with CUDA events over a few repetitions of the tile-list
+half tile, and the forward is timed both with shared batches and one warp per half tile.  Every candidate is timed with CUDA events over a few repetitions of the tile-list
 build, the forward (render) and the backward on the caller's own Gaussians, cameras and
 targets; the configuration with the smallest lists + forward + backward time wins.  The
 forward output does not depend on any of these choices (bit-identical across them, which
@@ -112,7 +112,7 @@ def autotune(params, cams, levels, gt, loss_cfg, base: RenderConfig | None = Non
         chosen_fwd = dict(tile_w=tw, tile_h=th, batch=fwd_best[1], pixels_per_thread=fwd_best[2])
         if best is None or total < best[0]:
             best = (total, dict(chosen_fwd, batch_bwd=bwd_best[1], pixels_per_thread_bwd=bwd_best[2],
-                                half_masks=False))
+                                half_masks=False, half_tile_fwd=False))
         if (tw, th) == (8, 8):
             # lists with half masks, and the adjoint's one-warp-per-half mode they enable
             r.cfg = replace(cfg0, half_masks=True, batch=fwd_best[1], pixels_per_thread=fwd_best[2],
@@ -120,15 +120,30 @@ def autotune(params, cams, levels, gt, loss_cfg, base: RenderConfig | None = Non
             r._ccfg = r.cfg.to_c()
             t_lists_h = _time(r.build_lists, reps)
             t_fwd_h = _time(lambda: r.rasterize(params), reps)  # (on the lists kept by the half rule)
+            # the forward one warp per half tile too (at one pixel per thread)
+            r.cfg = replace(r.cfg, pixels_per_thread=1, half_tile_fwd=True)
+            r._ccfg = r.cfg.to_c()
+            t_fwd_hh = _time(lambda: r.rasterize(params), reps)
+            fwd_half = t_fwd_hh < t_fwd_h
+            if not fwd_half:
+                r.cfg = replace(r.cfg, pixels_per_thread=fwd_best[2], half_tile_fwd=False)
+                r._ccfg = r.cfg.to_c()
+                r.rasterize(params)
             t_bwd_h = _time(lambda: r.backward(params, grads), reps)
             table.append(dict(tile="8x8", batch=0, kernel="lists_half", ppt=0, ms=t_lists_h))
             table.append(dict(tile="8x8", batch=fwd_best[1], kernel="fwd_half", ppt=fwd_best[2], ms=t_fwd_h))
+            table.append(dict(tile="8x8", batch=0, kernel="fwd_half_tile", ppt=1, ms=t_fwd_hh))
             table.append(dict(tile="8x8", batch=0, kernel="bwd_half", ppt=1, ms=t_bwd_h))
-            total_h = t_lists_h + t_fwd_h + t_bwd_h
+            total_h = t_lists_h + min(t_fwd_h, t_fwd_hh) + t_bwd_h
             if log:
-                log(f"tile 8x8 with half masks: lists {t_lists_h:.3f} ms, fwd {t_fwd_h:.3f} ms, bwd {t_bwd_h:.3f} ms")
+                log(f"tile 8x8 with half masks: lists {t_lists_h:.3f} ms, fwd {t_fwd_h:.3f} ms "
+                    f"(one warp per half tile: {t_fwd_hh:.3f} ms), bwd {t_bwd_h:.3f} ms")
             if total_h < best[0]:
-                best = (total_h, dict(chosen_fwd, batch_bwd=bwd_best[1], pixels_per_thread_bwd=1, half_masks=True))
+                cfg_h = dict(chosen_fwd, batch_bwd=bwd_best[1], pixels_per_thread_bwd=1, half_masks=True,
+                             half_tile_fwd=fwd_half)
+                if fwd_half:
+                    cfg_h["pixels_per_thread"] = 1
+                best = (total_h, cfg_h)
         del r, grads
         torch.cuda.empty_cache()
     chosen = replace(base, **best[1])

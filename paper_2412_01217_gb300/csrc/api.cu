@@ -102,6 +102,7 @@ static sg_status check_cfg(const sg_config *c) {
                "batch_bwd %d not 0 or in [16, 512] step 16", c->batch_bwd);
     SG_REQUIRE(c->isotropic == 0 || c->isotropic == 1, "isotropic must be 0 or 1");
     SG_REQUIRE(c->check_numeric == 0 || c->check_numeric == 1, "check_numeric must be 0 or 1");
+    SG_REQUIRE(c->half_tile_fwd == 0 || c->half_tile_fwd == 1, "half_tile_fwd must be 0 or 1");
     SG_REQUIRE(c->alpha_min > 0.f && c->alpha_max <= 1.f && c->alpha_min < c->alpha_max,
                "need 0 < alpha_min < alpha_max <= 1");
     SG_REQUIRE(c->T_min >= 0.f && c->z_near > 0.f && c->dilation >= 0.f && c->fov_clamp > 0.f,
@@ -181,6 +182,7 @@ void sg_default_config(sg_config *c) {
     c->batch_bwd = 0;
     c->isotropic = 0;
     c->check_numeric = 0;
+    c->half_tile_fwd = 0;
 }
 
 void sg_default_loss_config(sg_loss_config *c) {

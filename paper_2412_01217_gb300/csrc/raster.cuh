@@ -26,6 +26,7 @@ struct RasterArgs {
     int ppt;  // pixels per thread (1, 2 or 4)
     int half;             // records carry half masks in bits 30-31: the adjoint of 8 x 8
                           // tiles at one pixel per thread runs one warp per half tile
+    int half_fwd;         // ... and so does the forward (sg_config.half_tile_fwd)
     uint32_t rec_mask;    // bits of a list word that hold the record id
     // forward outputs / backward inputs
     float *img_rgb, *img_depth, *img_sem;
@@ -68,6 +69,7 @@ inline void fill_raster_args(RasterArgs &a, const sg_gaussians *g, const sg_proj
     a.persistent = cfg->persistent;
     a.ppt = cfg->pixels_per_thread;
     a.half = lists->half_masks != 0;
+    a.half_fwd = cfg->half_tile_fwd != 0;
     a.rec_mask = a.half ? 0x3fffffffu : 0xffffffffu;
 }
 

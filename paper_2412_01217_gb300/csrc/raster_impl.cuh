@@ -66,38 +66,42 @@ __device__ __forceinline__ void load_batch(const RasterArgs &a, int C, int list_
         if (s_rec) s_rec[j] = rec;
     }
 }
-// The same rows for one warp and at most 16 entries whose records are known (rec_of(j) is
-// row j's record): lanes 0-15 stage row j = lane's geometry, lanes 16-31 its features.
+// The same rows for one warp and at most 32 entries whose records are known (rec_of(j) is
+// row j's record): lanes 0-15 stage the geometry of rows lane, lane + 16, lanes 16-31 their
+// features.  s_geo2 and s_rec may be null (not staged).
 template <int NF, class RecOf>
 __device__ __forceinline__ void stage_rows_warp(const RasterArgs &a, int C, RecOf rec_of, int cnt, int px0,
                                                 int py0, uint32_t rec_base, float4 *s_geo0, float4 *s_geo1,
                                                 float4 *s_geo2, float *s_feat, uint32_t *s_rec) {
-    const int lane = threadIdx.x & 31, j = lane & 15;
-    if (j >= cnt) return;
-    const uint32_t rec = rec_of(j);
-    float *f = s_feat + (size_t)j * NF;
-    if (lane < 16) {
-        const float4 g0 = a.geo[2 * (size_t)rec];
-        const float4 g1 = a.geo[2 * (size_t)rec + 1];
-        const float2 ex = a.ext[rec];
-        const uint32_t packed = __float_as_uint(g1.w);
-        const float uI = (float)((int)(short)(packed & 0xffffu) - px0);
-        const float vI = (float)((int)(short)(packed >> 16) - py0);
-        s_geo0[j] = make_float4(uI, vI, g0.x, g0.y);
-        s_geo1[j] = make_float4(g1.x, g1.y, g1.z, g0.w);
-        if (s_geo2) s_geo2[j] = make_float4(uI + g0.x, vI + g0.y, ex.x, ex.y);
-        s_rec[j] = rec;
-        f[3] = g0.z;  // depth (camera z of the mean, Eq. 8)
-    } else {
-        const uint32_t gi = rec - rec_base;
-        const size_t ci = a.col_rec ? rec : gi;
-        f[0] = a.rgb[3 * ci];
-        f[1] = a.rgb[3 * ci + 1];
-        f[2] = a.rgb[3 * ci + 2];
-        const float4 *s4 = reinterpret_cast<const float4 *>(a.sem + (size_t)(a.sem_rec ? rec : gi) * C);
-        float4 *f4 = reinterpret_cast<float4 *>(f + 4);
+    const int lane = threadIdx.x & 31;
+    for (int j = lane & 15; j < cnt; j += 16) {
+        const uint32_t rec = rec_of(j);
+        float *f = s_feat + (size_t)j * NF;
+        if (lane < 16) {
+            const float4 g0 = a.geo[2 * (size_t)rec];
+            const float4 g1 = a.geo[2 * (size_t)rec + 1];
+            const uint32_t packed = __float_as_uint(g1.w);
+            const float uI = (float)((int)(short)(packed & 0xffffu) - px0);
+            const float vI = (float)((int)(short)(packed >> 16) - py0);
+            s_geo0[j] = make_float4(uI, vI, g0.x, g0.y);
+            s_geo1[j] = make_float4(g1.x, g1.y, g1.z, g0.w);
+            if (s_geo2) {
+                const float2 ex = a.ext[rec];
+                s_geo2[j] = make_float4(uI + g0.x, vI + g0.y, ex.x, ex.y);
+            }
+            if (s_rec) s_rec[j] = rec;
+            f[3] = g0.z;  // depth (camera z of the mean, Eq. 8)
+        } else {
+            const uint32_t gi = rec - rec_base;
+            const size_t ci = a.col_rec ? rec : gi;
+            f[0] = a.rgb[3 * ci];
+            f[1] = a.rgb[3 * ci + 1];
+            f[2] = a.rgb[3 * ci + 2];
+            const float4 *s4 = reinterpret_cast<const float4 *>(a.sem + (size_t)(a.sem_rec ? rec : gi) * C);
+            float4 *f4 = reinterpret_cast<float4 *>(f + 4);
 #pragma unroll
-        for (int k = 0; k < (NF - 4) / 4; ++k) f4[k] = s4[k];
+            for (int k = 0; k < (NF - 4) / 4; ++k) f4[k] = s4[k];
+        }
     }
 }
 
@@ -180,28 +184,44 @@ __device__ __forceinline__ TileInfo tile_info(const RasterArgs &a, int item) {
     return t;
 }
 
-template <int C, int PPT>
+// Half mode of the forward (8 x 8 tiles, one pixel per thread, lists with half masks): a
+// CTA is one warp that owns one half (8 x 4 pixels) of a tile; it walks the tile's list front
+// to back, queues (position, record) of the entries whose mask holds its half, and stages and
+// composites them 32 at a time with no block barrier, stopping as soon as its own 32 pixels
+// are saturated.  The per-pixel sequence of contributing entries, and so the output, is the
+// same as with shared batches.
+constexpr int kFwdHalfChunk = 32;
+constexpr int kFwdHalfQueue = 2 * kFwdHalfChunk;  // < 32 pending + one 32-entry scan
+
+template <int C, int PPT, bool HALF = false>
 __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs a) {
     pdl_begin();
     constexpr int NF = 4 + C;
+    constexpr bool hm = HALF;
+    static_assert(!HALF || PPT == 1, "half mode runs one pixel per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
-    const int batch = a.batch;
+    const int batch = hm ? kFwdHalfChunk : a.batch;
     float4 *s_geo0 = reinterpret_cast<float4 *>(smem_raw);
     float4 *s_geo1 = s_geo0 + batch;
-    float4 *s_geo2 = s_geo1 + batch;
-    float *s_feat = reinterpret_cast<float *>(s_geo2 + batch);
-    const int nthreads = a.tile_w * a.tile_h / PPT;
+    float4 *s_geo2 = hm ? nullptr : s_geo1 + batch;
+    float *s_feat = reinterpret_cast<float *>(s_geo1 + (hm ? batch : 2 * batch));
+    int *s_q = reinterpret_cast<int *>(s_feat + (size_t)batch * NF);  // half mode: the queue
+    uint32_t *s_qr = reinterpret_cast<uint32_t *>(s_q + kFwdHalfQueue);
+    const int nthreads = hm ? 32 : a.tile_w * a.tile_h / PPT;
     const int lane = threadIdx.x & 31;
     const WarpTile<PPT> wt(a.tile_w);
     const float fx = (float)wt.lx;
     const float ln_amin = __logf(a.alpha_min);
+    const int n_items = hm ? 2 * a.n_tiles : a.n_tiles;
     for (int iter = 0;; ++iter) {
         if (!a.persistent && iter > 0) break;
-        const int slot = next_item(a, a.n_tiles, s_item);
-        if (slot >= a.n_tiles) break;
-        const int item = a.order ? a.order[slot] : slot;  // tile id
-        const TileInfo ti = tile_info(a, item);
+        const int slot = next_item(a, n_items, s_item);
+        if (slot >= n_items) break;
+        const int tslot = hm ? slot >> 1 : slot, hf = hm ? slot & 1 : 0;
+        const int item = a.order ? a.order[tslot] : tslot;  // tile id
+        TileInfo ti = tile_info(a, item);
+        ti.py0 += hf * (a.tile_h / 2);  // half mode: this warp's half
         const sg_view &vw = *ti.vw;
         const int px = ti.px0 + wt.lx;
         const int2 range = a.ranges[item];
@@ -223,60 +243,112 @@ __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs 
             done[k] = !(px < vw.W && py < vw.H);
             n_done += done[k];
         }
-        for (int b0 = 0; b0 < n; b0 += batch) {
-            if (__syncthreads_count(n_done == PPT) == nthreads) break;
-            const int cnt = min(batch, n - b0);
-            load_batch<NF>(a, C, range.x, b0, cnt, ti.px0, ti.py0, rec_base, s_geo0, s_geo1, s_geo2, s_feat,
-                           nullptr, nthreads);
-            __syncthreads();
-            if (__all_sync(SG_FULL_MASK, n_done == PPT)) continue;
-            // 32 entries at a time: lane l tests entry j0 + l against the warp's sub-tile, and
-            // the warp walks the entries that can reach it, front to back
-            for (int j0 = 0; j0 < cnt; j0 += 32) {
-                if (__all_sync(SG_FULL_MASK, n_done == PPT)) break;
-                const int jl = j0 + lane;
-                uint32_t cm = __ballot_sync(SG_FULL_MASK, jl < cnt && !wt.misses(s_geo2[jl], s_geo1[jl], ln_amin));
-            while (cm) {
-                const int j = j0 + __ffs(cm) - 1;
-                cm &= cm - 1;
-                const float4 g0 = s_geo0[j];
-                const float4 g1 = s_geo1[j];
-                float w[PPT];
-                bool any = false;
+        // staged row j, list position pos: alpha at the thread's pixels, front to back
+        auto entry = [&](const int j, const int pos) {
+            const float4 g0 = s_geo0[j];
+            const float4 g1 = s_geo1[j];
+            float w[PPT];
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                w[k] = 0.f;
+                if (done[k]) continue;
+                AlphaEval e;
+                if (!eval_alpha(fx - g0.x, (float)(wt.ly + 4 * k) - g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w,
+                                a.alpha_max, a.alpha_min, e))
+                    continue;
+                const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, e.alpha));
+                if (Tn < a.T_min) {
+                    done[k] = true;
+                    ++n_done;
+                    continue;
+                }
+                w[k] = e.alpha * T[k];
+                T[k] = Tn;
+                last[k] = pos + 1;
+                ++nc[k];
+                any = true;
+            }
+            if (!any) return;
+            const float4 *f4 = reinterpret_cast<const float4 *>(s_feat + (size_t)j * NF);
+#pragma unroll
+            for (int q = 0; q < NF / 4; ++q) {
+                const float4 f = f4[q];
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    w[k] = 0.f;
-                    if (done[k]) continue;
-                    AlphaEval e;
-                    if (!eval_alpha(fx - g0.x, (float)(wt.ly + 4 * k) - g0.y, g0.z, g0.w, g1.x, g1.y, g1.z,
-                                    g1.w, a.alpha_max, a.alpha_min, e))
-                        continue;
-                    const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, e.alpha));
-                    if (Tn < a.T_min) {
-                        done[k] = true;
-                        ++n_done;
-                        continue;
-                    }
-                    w[k] = e.alpha * T[k];
-                    T[k] = Tn;
-                    last[k] = b0 + j + 1;
-                    ++nc[k];
-                    any = true;
+                    acc[k][4 * q + 0] = fmaf(w[k], f.x, acc[k][4 * q + 0]);
+                    acc[k][4 * q + 1] = fmaf(w[k], f.y, acc[k][4 * q + 1]);
+                    acc[k][4 * q + 2] = fmaf(w[k], f.z, acc[k][4 * q + 2]);
+                    acc[k][4 * q + 3] = fmaf(w[k], f.w, acc[k][4 * q + 3]);
                 }
-                if (!any) continue;
-                const float4 *f4 = reinterpret_cast<const float4 *>(s_feat + (size_t)j * NF);
-#pragma unroll
-                for (int q = 0; q < NF / 4; ++q) {
-                    const float4 f = f4[q];
-#pragma unroll
-                    for (int k = 0; k < PPT; ++k) {
-                        acc[k][4 * q + 0] = fmaf(w[k], f.x, acc[k][4 * q + 0]);
-                        acc[k][4 * q + 1] = fmaf(w[k], f.y, acc[k][4 * q + 1]);
-                        acc[k][4 * q + 2] = fmaf(w[k], f.z, acc[k][4 * q + 2]);
-                        acc[k][4 * q + 3] = fmaf(w[k], f.w, acc[k][4 * q + 3]);
+            }
+        };
+        if (!hm) {
+            for (int b0 = 0; b0 < n; b0 += batch) {
+                if (__syncthreads_count(n_done == PPT) == nthreads) break;
+                const int cnt = min(batch, n - b0);
+                load_batch<NF>(a, C, range.x, b0, cnt, ti.px0, ti.py0, rec_base, s_geo0, s_geo1, s_geo2, s_feat,
+                               nullptr, nthreads);
+                __syncthreads();
+                if (__all_sync(SG_FULL_MASK, n_done == PPT)) continue;
+                // 32 entries at a time: lane l tests entry j0 + l against the warp's sub-tile, and
+                // the warp walks the entries that can reach it, front to back
+                for (int j0 = 0; j0 < cnt; j0 += 32) {
+                    if (__all_sync(SG_FULL_MASK, n_done == PPT)) break;
+                    const int jl = j0 + lane;
+                    uint32_t cm = __ballot_sync(SG_FULL_MASK, jl < cnt && !wt.misses(s_geo2[jl], s_geo1[jl], ln_amin));
+                    while (cm) {
+                        const int j = j0 + __ffs(cm) - 1;
+                        cm &= cm - 1;
+                        entry(j, b0 + j);
                     }
                 }
             }
+        } else {
+            // list positions whose half mask holds this half, ascending: (s_q, s_qr)[0 .. qn)
+            // is the queue of (position, record), top the next position scanned
+            const uint32_t lt = (1u << lane) - 1u;
+            int top = 0, qn = 0;
+            while (!__all_sync(SG_FULL_MASK, n_done == PPT)) {
+                while (qn < kFwdHalfChunk && top < n) {
+                    const int pos = top + lane;
+                    uint32_t rec = 0u;
+                    bool sel = false;
+                    if (pos < n) {
+                        const uint32_t word = a.record[range.x + pos];  // record | half mask << 30
+                        rec = word & 0x3fffffffu;
+                        sel = (word >> (30 + hf)) & 1u;
+                    }
+                    const uint32_t bal = __ballot_sync(SG_FULL_MASK, sel);
+                    if (sel) {
+                        s_q[qn + __popc(bal & lt)] = pos;
+                        s_qr[qn + __popc(bal & lt)] = rec;
+                    }
+                    qn += __popc(bal);
+                    top += 32;
+                    __syncwarp();
+                }
+                if (qn == 0) break;
+                const int c = min(kFwdHalfChunk, qn);
+                stage_rows_warp<NF>(a, C, [&](int j) { return s_qr[j]; }, c, ti.px0, ti.py0, rec_base, s_geo0, s_geo1,
+                                    nullptr, s_feat, nullptr);
+                __syncwarp();
+                for (int j = 0; j < c; ++j) {
+                    if (__all_sync(SG_FULL_MASK, n_done == PPT)) break;
+                    entry(j, s_q[j]);
+                }
+                __syncwarp();
+                // drop the staged entries from the queue
+                const int rest = qn - c;  // (< 32)
+                const int keep = lane < rest ? s_q[c + lane] : 0;
+                const uint32_t keep_rec = lane < rest ? s_qr[c + lane] : 0u;
+                __syncwarp();
+                if (lane < rest) {
+                    s_q[lane] = keep;
+                    s_qr[lane] = keep_rec;
+                }
+                qn = rest;
+                __syncwarp();
             }
         }
         const size_t HW = (size_t)vw.W * vw.H;
@@ -759,6 +831,13 @@ inline size_t bwd_half_smem() {
            sizeof(float) * bwd_warp_floats<C, 1>();
 }
 
+// forward half mode: one 32-entry chunk staged without its (u, v, ex, ey) rows, and the
+// (position, record) queue
+template <int C>
+inline size_t fwd_half_smem() {
+    return (size_t)kFwdHalfChunk * (2 * 16 + 4 * (4 + C)) + (size_t)kFwdHalfQueue * 4 * 2;
+}
+
 inline int resident_grid(const void *fn, int threads, size_t smem) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -770,19 +849,21 @@ inline int resident_grid(const void *fn, int threads, size_t smem) {
 
 template <int C, int PPT>
 sg_status launch_raster_cp(RasterArgs &a, bool backward, cudaStream_t st) {
-    // the adjoint of 8 x 8 tiles at one pixel per thread runs one warp per half tile when the
-    // lists carry half masks
-    const bool half = backward && a.half && PPT == 1 && a.tile_w == 8 && a.tile_h == 8;
+    // with half masks, the adjoint of 8 x 8 tiles at one pixel per thread runs one warp per
+    // half tile, and so does the forward when the config asks for it
+    const bool half = a.half && PPT == 1 && a.tile_w == 8 && a.tile_h == 8 && (backward || a.half_fwd);
     const int threads = half ? 32 : a.tile_w * a.tile_h / PPT;
     const int n_items = half ? 2 * a.n_tiles : a.n_tiles;
-    const size_t smem = half ? bwd_half_smem<C>() : backward ? bwd_smem<C, PPT>(a.batch, threads) : fwd_smem<C>(a.batch);
-    const void *fn = half       ? (const void *)raster_bwd_kernel<C, PPT, PPT == 1>
-                     : backward ? (const void *)raster_bwd_kernel<C, PPT>
-                                : (const void *)raster_fwd_kernel<C, PPT>;
+    const size_t smem = backward ? (half ? bwd_half_smem<C>() : bwd_smem<C, PPT>(a.batch, threads))
+                                 : (half ? fwd_half_smem<C>() : fwd_smem<C>(a.batch));
+    const void *fn = backward ? (half ? (const void *)raster_bwd_kernel<C, PPT, PPT == 1>
+                                      : (const void *)raster_bwd_kernel<C, PPT>)
+                              : (half ? (const void *)raster_fwd_kernel<C, PPT, PPT == 1>
+                                      : (const void *)raster_fwd_kernel<C, PPT>);
     // opt in to the dynamic size whenever it grows: at 48 KB and just below, the kernel's
     // static shared variables alone take the total past the default limit
-    static size_t configured[3] = {0, 0, 0};
-    const int which = half ? 2 : backward ? 1 : 0;
+    static size_t configured[4] = {0, 0, 0, 0};
+    const int which = 2 * (int)backward + (int)half;
     if (configured[which] < smem) {
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return check_launch("raster smem attribute");
@@ -794,10 +875,12 @@ sg_status launch_raster_cp(RasterArgs &a, bool backward, cudaStream_t st) {
         if (grid > n_items) grid = n_items;
     }
     if (grid <= 0) return SG_OK;
-    if (half)
+    if (backward && half)
         launch_pdl(raster_bwd_kernel<C, PPT, PPT == 1>, grid, threads, smem, st, a);
     else if (backward)
         launch_pdl(raster_bwd_kernel<C, PPT>, grid, threads, smem, st, a);
+    else if (half)
+        launch_pdl(raster_fwd_kernel<C, PPT, PPT == 1>, grid, threads, smem, st, a);
     else
         launch_pdl(raster_fwd_kernel<C, PPT>, grid, threads, smem, st, a);
     count_launches(1);

@@ -77,6 +77,8 @@ class RenderConfig:
     # per-instance half masks in the tile lists: the adjoint of 8x8 tiles at one pixel per
     # thread then runs one warp per half tile (faster on long lists, lists slower to build)
     half_masks: bool = False
+    # with half masks: the forward also one warp per half tile (faster on long lists)
+    half_tile_fwd: bool = False
 
     def to_c(self):
         c = SgConfig()
@@ -90,6 +92,7 @@ class RenderConfig:
         c.batch_bwd = int(self.batch_bwd)
         c.isotropic = int(self.isotropic)
         c.check_numeric = int(self.check_numeric)
+        c.half_tile_fwd = int(self.half_tile_fwd)
         return c
 
 

@@ -31,7 +31,7 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(_lib.SgCamera) == 72
     assert C.sizeof(_lib.SgView) == 96
     assert C.sizeof(_lib.SgGaussians) == 80
-    assert C.sizeof(_lib.SgConfig) == 72
+    assert C.sizeof(_lib.SgConfig) == 76
     assert C.sizeof(_lib.SgLossConfig) == 48
 
 
@@ -46,6 +46,7 @@ def test_defaults_and_version():
     lib.sg_default_loss_config(C.byref(lc))
     assert lc.lambda_r == pytest.approx(0.2) and lc.lambda_s == pytest.approx(0.2)
     assert c.check_numeric == 0 and lc.check_numeric == 0  # numeric checks are off by default
+    assert c.half_tile_fwd == 0  # the forward shares staged batches by default
     assert b"sm_103a" in lib.sg_version()
 
 
@@ -88,6 +89,21 @@ def test_host_validation_rejects_bad_arguments():
     assert lib.sg_adam_step(None, None, None, None, 5, 1e-3, 0.9, 0.999, 1e-8, 0, None) == 1
     assert lib.sg_read_status(None, None, None) == 1
     assert lib.sg_adam_step(None, None, None, None, 0, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 0
+
+
+def test_half_tile_forward_flag_is_checked_on_the_host():
+    """sg_config.half_tile_fwd takes 0 or 1; anything else is refused before any launch (the
+    buffer pointers below are never dereferenced)."""
+    from paper_2412_01217_gb300 import _lib
+    lib = _lib.load()
+    cfg = _lib.SgConfig()
+    lib.sg_default_config(C.byref(cfg))
+    cfg.half_tile_fwd = 2
+    proj = _lib.SgProjected(16, 16, 16, 0, 0)
+    lists = _lib.SgTileLists()
+    assert lib.sg_build_tile_lists(C.byref(proj), 10, 1, None, 1, C.byref(cfg), C.byref(lists), None, 0, None,
+                                   None) == 1
+    assert b"half_tile_fwd" in lib.sg_last_error()
 
 
 def test_timeout_probe_validates_on_the_host():

@@ -89,12 +89,13 @@ def test_batched_uneven_keyframes_one_launch_matches_oracle():
 
 @pytest.mark.parametrize("half", [False, True])
 def test_scannet_like_1m_gaussians_fd_on_64_gaussian_subset(half):
-    """half: 8x8 tiles with half masks, the adjoint one warp per half tile (C = 40)."""
+    """half: 8x8 tiles with half masks, both compositing kernels one warp per half tile (C = 40)."""
     from paper_2412_01217_gb300 import pyramid_splat
     room = synthetic.Room(n_classes=40, seed=6)
     cam = f32_camera(room.trajectory(3, synthetic.SCANNET_LIKE, seed=9)[1])
     g = room.sample_gaussians(1_000_000, 40, seed=5, sem_mode="random")
-    kw = dict(tile_w=8, tile_h=8, batch=64, pixels_per_thread_bwd=1, half_masks=True) if half else {}
+    kw = (dict(tile_w=8, tile_h=8, batch=64, pixels_per_thread_bwd=1, half_masks=True, half_tile_fwd=True)
+          if half else {})
     r, p = make(g, [cam], levels=4, **kw)
     assert [(r.views_host[v].W, r.views_host[v].H) for v in range(4)] == [(640, 480), (320, 240), (160, 120), (80, 60)]
     rng = np.random.default_rng(5)

@@ -70,14 +70,14 @@ def test_ragged_image_sizes_every_tile_shape(tile, batch, batch_bwd, ppt, ppt_bw
     g = synthetic.cloud_scene(2500, 8, seed=21)
     cam = f32_camera(synthetic.make_camera(157, 91, 140.0, 140.0, 77.7, 44.6))
     parity_all_views(g, [cam], 3, tile_w=tile[0], tile_h=tile[1], batch=batch, batch_bwd=batch_bwd,
-                     pixels_per_thread=ppt, pixels_per_thread_bwd=ppt_bwd, half_masks=half)
+                     pixels_per_thread=ppt, pixels_per_thread_bwd=ppt_bwd, half_masks=half, half_tile_fwd=half)
 
 
 @pytest.mark.parametrize("C, half", [(4, False), (32, False), (4, True), (32, True)])
 def test_semantic_widths_4_and_32(C, half):
     g = synthetic.cloud_scene(2000, C, seed=22)
     cam = f32_camera(synthetic.cloud_camera())
-    kw = dict(tile_w=8, tile_h=8, pixels_per_thread_bwd=1, half_masks=True) if half else {}
+    kw = dict(tile_w=8, tile_h=8, pixels_per_thread_bwd=1, half_masks=True, half_tile_fwd=True) if half else {}
     parity_all_views(g, [cam], 2, **kw)
 
 

@@ -108,7 +108,8 @@ def replica_like():
 # the launch configuration bench.py times on this workload (autotuned: 8x8 tiles, forward batch
 # 64, backward batch 16, one pixel per thread in both kernels), and the library default
 BENCH_CFG = dict(tile_w=8, tile_h=8, batch=64, batch_bwd=16, pixels_per_thread=1, pixels_per_thread_bwd=1)
-LAUNCH_CFGS = [pytest.param(BENCH_CFG, id="bench-8x8"), pytest.param(dict(BENCH_CFG, half_masks=True), id="8x8-half"),
+LAUNCH_CFGS = [pytest.param(BENCH_CFG, id="bench-8x8"),
+               pytest.param(dict(BENCH_CFG, half_masks=True, half_tile_fwd=True), id="8x8-half"),
                pytest.param(dict(tile_w=16, tile_h=16, batch=128), id="16x16")]
 
 

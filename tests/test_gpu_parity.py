@@ -339,17 +339,21 @@ def test_forward_matches_oracle_cloud(cloud, isotropic):
 def test_forward_bitwise_identical_across_tiles_batches_and_runs(cloud):
     g, cam = cloud
     base = None
-    for tw, th, batch, pers, ppt in ((16, 16, 128, True, 1), (8, 8, 32, True, 1), (32, 8, 256, False, 2),
-                                     (16, 8, 64, True, 2), (16, 16, 128, True, 4), (8, 8, 64, False, 2),
-                                     (16, 16, 128, True, 1)):
-        r, p = make(g, [cam], tile_w=tw, tile_h=th, batch=batch, persistent=pers, pixels_per_thread=ppt)
+    # (the 8x8 cases with half masks: persistent ones run the forward one warp per half tile)
+    for tw, th, batch, pers, ppt, half in ((16, 16, 128, True, 1, False), (8, 8, 32, True, 1, False),
+                                           (32, 8, 256, False, 2, False), (16, 8, 64, True, 2, False),
+                                           (16, 16, 128, True, 4, False), (8, 8, 64, False, 2, False),
+                                           (8, 8, 64, True, 1, True), (8, 8, 64, False, 1, True),
+                                           (16, 16, 128, True, 1, False)):
+        r, p = make(g, [cam], tile_w=tw, tile_h=th, batch=batch, persistent=pers, pixels_per_thread=ppt,
+                    half_masks=half, half_tile_fwd=half and pers)
         r.forward(p)
         im = view_images(r, 0, 8)
         if base is None:
             base = im
             continue
         for k in ("rgb", "depth", "sem", "T", "n_contrib"):
-            assert np.array_equal(im[k], base[k]), (k, tw, th, batch, pers, ppt)
+            assert np.array_equal(im[k], base[k]), (k, tw, th, batch, pers, ppt, half)
 
 
 @pytest.mark.parametrize("ppt, batch_bwd, isotropic, tile", [(1, 0, False, "16x16"), (2, 0, False, "16x16"),
@@ -358,11 +362,13 @@ def test_forward_bitwise_identical_across_tiles_batches_and_runs(cloud):
                                                            (1, 16, False, "8x8"), (1, 16, False, "8x8-half"),
                                                            (1, 0, True, "8x8-half")])
 def test_backward_matches_oracle_cloud(cloud, ppt, batch_bwd, isotropic, tile):
-    """8x8-half: lists with half masks, so the adjoint runs one warp per half tile."""
+    """8x8-half: lists with half masks, so the adjoint (and, in the isotropic case, the forward)
+    runs one warp per half tile."""
     g, cam = cloud
     tw, th = (int(x) for x in tile.split("-")[0].split("x"))
+    half = tile.endswith("half")
     r, p = make(g, [cam], pixels_per_thread_bwd=ppt, batch_bwd=batch_bwd, isotropic=isotropic, tile_w=tw,
-                tile_h=th, half_masks=tile.endswith("half"))
+                tile_h=th, half_masks=half, half_tile_fwd=half and isotropic)
     r.forward(p)
     ocfg = dict(isotropic=int(isotropic))
     ref_f = ref_render(g, cam, ocfg)

@@ -86,7 +86,8 @@ def test_sh_backward_matches_oracle(degree, ppt, colour, semantic):
     """ppt 0: 8x8 tiles with half masks (the adjoint one warp per half tile, one pixel per
     thread)."""
     g, cam = sh_cloud(degree, seed=degree, colour=colour, semantic=semantic)
-    kw = dict(tile_w=8, tile_h=8, pixels_per_thread_bwd=1, half_masks=True) if ppt == 0 else \
+    kw = dict(tile_w=8, tile_h=8, pixels_per_thread_bwd=1, half_masks=True,
+              half_tile_fwd=True) if ppt == 0 else \
         dict(pixels_per_thread_bwd=ppt)
     r, p = make(g, [cam], **kw)
     r.forward(p)
