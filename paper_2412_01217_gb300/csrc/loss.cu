@@ -528,10 +528,11 @@ __device__ __forceinline__ void ldsm_x4(const float *p, uint32_t (&r)[4]) {
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a) : "memory");
 }
 
-// At C K <= 512 the kernel is bounded to 80 registers (three CTAs per SM): measured faster than
-// 64 registers and four CTAs, which spill the warp's decoder-gradient fragments.
+// Two CTAs per SM (up to 128 registers): with the per-warp stage, three CTAs at 80 registers
+// spilled the warp's fragments and measured slower (loss 0.975 against 0.954 ms on the batched
+// workload), and four at 64 slower still.
 template <int C, int K>
-__global__ void __launch_bounds__(kLossThreads, C * K <= 512 ? 3 : 2) ce_decoder_mma_kernel(PixelArgs a) {
+__global__ void __launch_bounds__(kLossThreads, 2) ce_decoder_mma_kernel(PixelArgs a) {
     pdl_begin();
     static_assert(C % 8 == 0 && K % 16 == 0, "MMA tiles");
     using L = CeLayout<C, K>;

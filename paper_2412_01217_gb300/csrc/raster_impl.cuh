@@ -191,7 +191,7 @@ __device__ __forceinline__ TileInfo tile_info(const RasterArgs &a, int item) {
 // are saturated.  The per-pixel sequence of contributing entries, and so the output, is the
 // same as with shared batches.
 constexpr int kFwdHalfChunk = 32;
-constexpr int kFwdHalfQueue = 2 * kFwdHalfChunk;  // < 32 pending + one 32-entry scan
+constexpr int kFwdHalfQueue = kFwdHalfChunk + 32;  // < kFwdHalfChunk pending + one 32-entry scan
 
 template <int C, int PPT, bool HALF = false>
 __global__ void __launch_bounds__(kMaxTileThreads) raster_fwd_kernel(RasterArgs a) {
