@@ -27,6 +27,7 @@ struct RasterArgs {
     int half;             // records carry half masks in bits 30-31: the adjoint of 8 x 8
                           // tiles at one pixel per thread runs one warp per half tile
     int half_fwd;         // ... and so does the forward (sg_config.half_tile_fwd)
+    int half_pairs;       // half-tile adjoint: a work item is a whole tile, both halves in turn
     uint32_t rec_mask;    // bits of a list word that hold the record id
     // forward outputs / backward inputs
     float *img_rgb, *img_depth, *img_sem;
