@@ -20,7 +20,15 @@ from test_gpu_parity import KEYS, f32_camera, make
 pytestmark = pytest.mark.gpu
 
 
-def test_batched_uneven_keyframes_one_launch_matches_oracle():
+# the launch configuration bench.py's autotuner picks on this workload: 8x8 tiles with half
+# masks, both compositing kernels one warp per half tile; its 92k tiles are more than 16 per
+# resident CTA of the adjoint, which then takes whole tiles (both halves in turn) as work items
+BATCHED_BENCH_CFG = dict(tile_w=8, tile_h=8, batch=64, batch_bwd=16, pixels_per_thread=1, pixels_per_thread_bwd=1,
+                         half_masks=True, half_tile_fwd=True)
+
+
+@pytest.mark.parametrize("cfg", [pytest.param({}, id="16x16"), pytest.param(BATCHED_BENCH_CFG, id="bench-8x8-half")])
+def test_batched_uneven_keyframes_one_launch_matches_oracle(cfg):
     """The batched workload (8 keyframes of uneven size x 3 levels, 500k Gaussians) in one
     launch per kernel: sampled pixels of 8 view-levels forward, bit-identical graph replay,
     and the adjoint of all 24 view-levels for a sparse upstream gradient."""
@@ -28,7 +36,7 @@ def test_batched_uneven_keyframes_one_launch_matches_oracle():
     cams = [f32_camera(c) for c in room.trajectory(4, synthetic.REPLICA_LIKE, seed=7)]
     cams += [f32_camera(c) for c in room.trajectory(4, synthetic.SCANNET_LIKE, seed=8)]
     g = room.sample_gaussians(500_000, 16, seed=4, sem_mode="random")
-    r, p = make(g, cams, levels=3)
+    r, p = make(g, cams, levels=3, **cfg)
     assert r.V == 24 and abs(r.P - 5_898_000) < 10_000
     r.forward(p)
     torch.cuda.synchronize()
