@@ -141,9 +141,9 @@ def algorithmic_bytes(s):
 
 
 def raster_flops_model(s):
-    """Algorithmic flops of the compositing kernels by the survey's model: E list entries
-    examined (pixel, entry pairs) times 15 + 2 (4 + C) in the forward and 40 + 4 (4 + C) in
-    the backward, as if every examined entry contributed."""
+    """Algorithmic flops of the compositing kernels by the per-entry model of the hot path: E
+    list entries examined (pixel, entry pairs) times 15 + 2 (4 + C) in the forward and
+    40 + 4 (4 + C) in the backward, as if every examined entry contributed."""
     E, C = s["E"], s["C"]
     nf = 4 + C
     return E * (15 + 2 * nf), E * (40 + 4 * nf)
