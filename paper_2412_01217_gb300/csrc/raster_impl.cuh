@@ -469,10 +469,11 @@ __global__ void __maxnreg__((bwd_max_regs<C, PPT>())) raster_bwd_kernel(RasterAr
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item, s_max_last;
     // Half mode (8 x 8 tiles, one pixel per thread, half masks given): a CTA is one warp that
-    // owns one half (8 x 4 pixels) of a tile; it walks the tile's list back to front, keeps
-    // the entries whose half mask holds its half in a queue, and stages and processes them
-    // 16 at a time, so its chunks hold only its own entries; no block barrier.  Otherwise the
-    // CTA's warps share each batch of the list, staged between two block barriers.
+    // works on one half (8 x 4 pixels) of a tile at a time; it walks the tile's list back to
+    // front, keeps the entries whose half mask holds its half in a queue, and stages and
+    // processes them 16 at a time, so its chunks hold only its own entries; no block barrier.
+    // Otherwise the CTA's warps share each batch of the list, staged between two block
+    // barriers.
     constexpr bool hm = HALF;
     static_assert(!HALF || PPT == 1, "half mode runs one pixel per thread");
     const int batch = hm ? kChunk : a.batch;
