@@ -88,3 +88,71 @@ def test_tile_culling_rule_keeps_only_tiles_the_footprint_reaches():
             assert smin <= thr * (1 + 1e-4) + 1e-4, (r, txs[k], tys[k], smin, thr)
             n_kept += 1
     assert n_kept > 1000
+
+
+def test_half_mask_rule_is_conservative_and_splits_tile_rows():
+    """The culling rule applied to each half of a tile row (the half masks of the tile lists):
+    every half holding a pixel centre where the FP64 footprint reaches alpha >= 1/255 is
+    marked (conservative); a sizeable share of kept tiles is marked for one half only (the
+    masks are not vacuous); and the tiles kept by the hull of the two halves' runs are those
+    the rule keeps on the whole row, up to float32 rounding at a run's ends."""
+    import synthetic
+    from kernel_rules import kept_and_masks, tile_halves_reach
+    g = {k: np.asarray(v, np.float64) for k, v in synthetic.cloud_scene(800, 4, seed=11).items()}
+    g["log_scale"][:, 0] += 1.0
+    cam = synthetic.cloud_camera()
+    T = 8
+    pr = oracle.project(g, cam)
+    geo, ext, rects = records_f32(pr, cam, T)
+    P = oracle.P
+    n_kept = n_single = n_diff = 0
+    for r in np.nonzero(rects[:, 2] > rects[:, 0])[0]:
+        tx0, ty0, tx1, ty1 = rects[r]
+        txs, tys = np.meshgrid(np.arange(tx0, tx1), np.arange(ty0, ty1))
+        txs, tys = txs.ravel(), tys.ravel()
+        X0, Y0 = txs * T, tys * T
+        X1, Y1 = np.minimum(X0 + T - 1, cam["W"] - 1), np.minimum(Y0 + T - 1, cam["H"] - 1)
+        g_r, e_r = np.repeat(geo[r:r + 1], len(txs), 0), np.repeat(ext[r:r + 1], len(txs), 0)
+        top, bottom = tile_halves_reach(g_r, e_r, X0, X1, Y0, Y1, T)
+        keep, mask = kept_and_masks(np.full(len(txs), r), txs, tys, top, bottom)
+        whole = tile_reaches_alpha_min(g_r, e_r, X0, X1, Y0, Y1)
+        n_diff += int((keep != whole).sum())
+        S = np.array([[pr[r, P["S00"]], pr[r, P["S01"]]], [pr[r, P["S01"]], pr[r, P["S11"]]]])
+        Q = np.linalg.inv(S)
+        for k in range(len(txs)):
+            for h, (ya, yb) in enumerate(((Y0[k], min(Y0[k] + T // 2 - 1, Y1[k])), (Y0[k] + T // 2, Y1[k]))):
+                if ya > yb:
+                    continue
+                xs, ys = np.meshgrid(np.arange(X0[k], X1[k] + 1) - pr[r, P["U"]], np.arange(ya, yb + 1) - pr[r, P["V"]])
+                sig = 0.5 * (Q[0, 0] * xs * xs + 2 * Q[0, 1] * xs * ys + Q[1, 1] * ys * ys)
+                if (pr[r, P["OPAC"]] * np.exp(-sig) >= (1 / 255) * (1 + 1e-5)).any():
+                    assert keep[k] and (mask[k] >> h) & 1, (r, txs[k], tys[k], h)
+        n_kept += int(keep.sum())
+        n_single += int((keep & ((mask == 1) | (mask == 2))).sum())
+    assert n_kept > 1000 and n_single > 0.1 * n_kept, (n_single, n_kept)
+    assert n_diff <= 0.002 * n_kept, (n_diff, n_kept)
+
+
+def test_kept_and_masks_matches_a_direct_loop():
+    """kept_and_masks against a loop over (record, tile row) runs: the kept tiles are every
+    tile between the leftmost and rightmost reached one, and each carries its halves' bits
+    (3 on every tile of a run longer than 255 tiles)."""
+    from kernel_rules import kept_and_masks
+    rng = np.random.default_rng(3)
+    n = 4000
+    recs = rng.integers(0, 40, n)
+    ty = rng.integers(0, 6, n)
+    tx = rng.integers(0, 300, n)
+    top = rng.random(n) < 0.3
+    bottom = rng.random(n) < 0.3
+    keep, mask = kept_and_masks(recs, tx, ty, top, bottom)
+    for i in range(n):
+        same = (recs == recs[i]) & (ty == ty[i])
+        reached = tx[same & (top | bottom)]
+        if len(reached) == 0:
+            assert not keep[i]
+            continue
+        lo, hi = reached.min(), reached.max()
+        assert keep[i] == (lo <= tx[i] <= hi)
+        want = 3 if hi - lo + 1 > 255 else int(top[i]) | (int(bottom[i]) << 1)
+        assert mask[i] == want
